@@ -1,0 +1,146 @@
+"""Solvers and the coil-sketching outer loop (Sec. 2.1, 2.3, Algorithm 1).
+
+Problem (Eq. 3-4): x* = argmin_x 1/2 ||A x - y||^2 + g(x), g = lambda/2 ||x||^2 (solved by CG)
+or g = lambda ||Psi x||_1 (solved by FISTA).
+
+Sketched sub-problem at outer iteration t (Eq. 9-10, Algorithm 1):
+    x^{t+1} = argmin_x 1/2 ||A_S^t (x - x^t)||^2 + Re<x, d> + g(x),  d = A^H (A x^t - y).
+The paper writes the inner product for real vectors; for complex images we read it as
+Re<x, d>, whose (Wirtinger, A^H-convention) gradient is d.  Hence the sub-problem gradient
+is A_S^H A_S (x - x^t) + d (+ lambda x for the l2 regulariser).
+
+Operators are passed as Python callables so the same solver serves the full-coil and the
+sketched problems, the Cartesian and the non-Cartesian operator.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import coils, wavelet
+
+
+def vdot(a, b):
+    """<a, b> = sum conj(a) b in complex128."""
+    return np.vdot(np.asarray(a, dtype=np.complex128).ravel(), np.asarray(b, dtype=np.complex128).ravel())
+
+
+def nrmse(x, ref):
+    """||x - ref||_2 / ||ref||_2 (the normalised distance of Sec. 3.3)."""
+    return float(np.linalg.norm((x - ref).ravel()) / np.linalg.norm(np.asarray(ref).ravel()))
+
+
+def cg(H, b, x0, iters):
+    """Hestenes-Stiefel conjugate gradients on H x = b (H Hermitian positive definite)."""
+    x = np.array(x0, dtype=np.complex128, copy=True)
+    r = b - H(x)
+    p = r.copy()
+    rr = vdot(r, r).real
+    for _ in range(iters):
+        if rr == 0:
+            break
+        Hp = H(p)
+        alpha = rr / vdot(p, Hp).real
+        x = x + alpha * p
+        r = r - alpha * Hp
+        rr_new = vdot(r, r).real
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+    return x
+
+
+def power_iteration(H, v0, iters=20):
+    """Largest eigenvalue of Hermitian PSD H: v <- H v / ||H v||, L = ||H v|| at the last step."""
+    v = np.asarray(v0, dtype=np.complex128)
+    v = v / np.linalg.norm(v.ravel())
+    L = 0.0
+    for _ in range(iters):
+        w = H(v)
+        L = float(np.linalg.norm(w.ravel()))
+        v = w / L
+    return L
+
+
+def fista(grad, prox, x0, eta, iters):
+    """FISTA (Beck & Teboulle 2009) from z_0 = x_0, t_0 = 1:
+    x_k = prox(z_{k-1} - eta grad(z_{k-1})), t_k = (1 + sqrt(1 + 4 t_{k-1}^2))/2,
+    z_k = x_k + ((t_{k-1} - 1)/t_k)(x_k - x_{k-1})."""
+    x_prev = np.array(x0, dtype=np.complex128, copy=True)
+    z = x_prev.copy()
+    t = 1.0
+    for _ in range(iters):
+        x = prox(z - eta * grad(z))
+        t_new = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
+        z = x + ((t - 1.0) / t_new) * (x - x_prev)
+        x_prev = x
+        t = t_new
+    return x_prev
+
+
+# ---------------------------------------------------------------------------------------
+# Sub-problem solvers (Eq. 9-10)
+
+def sketched_cg(normal_S, d, xt, lam, iters):
+    """l2 sub-problem: (A_S^H A_S + lam I) x = A_S^H A_S x^t - d, CG from x^t."""
+    H = lambda v: normal_S(v) + lam * v
+    b = normal_S(xt) - d
+    return cg(H, b, xt, iters)
+
+
+def sketched_fista(normal_S, d, xt, lam, eta, iters, levels=4):
+    """l1-wavelet sub-problem by FISTA from x^t: grad = A_S^H A_S (z - x^t) + d."""
+    grad = lambda z: normal_S(z - xt) + d
+    prox = lambda v: wavelet.prox_l1_wavelet(v, eta * lam, levels)
+    return fista(grad, prox, xt, eta, iters)
+
+
+def plain_cg(fwd, adj, y, lam, x0, iters):
+    """Full-coil l2 problem: (A^H A + lam I) x = A^H y."""
+    H = lambda v: adj(fwd(v)) + lam * v
+    return cg(H, adj(y), x0, iters)
+
+
+def plain_fista(fwd, adj, y, lam, eta, x0, iters, levels=4):
+    grad = lambda z: adj(fwd(z) - y)
+    prox = lambda v: wavelet.prox_l1_wavelet(v, eta * lam, levels)
+    return fista(grad, prox, x0, eta, iters)
+
+
+# ---------------------------------------------------------------------------------------
+# Algorithm 1
+
+def coil_sketching(op_factory, maps, y, lam, reg, sketches, V, K, x0=None, eta=None,
+                   power_v0=None, power_iters=20, do_pca=True, levels=4, callback=None):
+    """Algorithm 1 (no classical-sketch initialisation).
+
+    op_factory(maps) -> (fwd, adj) builds A for a set of maps (Cartesian or NUFFT).
+    sketches: float [T, S, C-V] random blocks S~_S^t (given as inputs).
+    reg: 'l2' (CG, K iterations) or 'l1wav' (FISTA, K iterations, step eta; if eta is None it
+    is 1/L with L from ``power_iters`` power iterations on the first sketched normal operator,
+    started at power_v0, and reused for every sub-problem).
+    Returns x^T and the list of iterates.
+    """
+    if do_pca:
+        U, _ = coils.coil_pca(y)
+        maps_r = coils.rotate(U, maps)
+        y_r = coils.rotate(U, y)
+    else:
+        maps_r, y_r = maps, y
+    fwd, adj = op_factory(maps_r)
+    x = np.zeros(maps.shape[1:], dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128)
+    iterates = []
+    for t in range(sketches.shape[0]):
+        d = adj(fwd(x) - y_r)                                   # true gradient
+        msk = coils.sketched_maps(sketches[t], maps_r, V)       # sketched model A_S^t
+        fs, ads = op_factory(msk)
+        normal_S = lambda v: ads(fs(v))
+        if reg == "l2":
+            x = sketched_cg(normal_S, d, x, lam, K)
+        else:
+            if eta is None:
+                L = power_iteration(normal_S, power_v0, power_iters)
+                eta = 1.0 / L
+            x = sketched_fista(normal_S, d, x, lam, eta, K, levels)
+        iterates.append(x.copy())
+        if callback is not None:
+            callback(t, x)
+    return x, iterates

@@ -1,0 +1,113 @@
+"""Pins for CG, FISTA, power iteration, the sketched sub-problem (Eq. 9-10) and Algorithm 1:
+direct dense solves, the identity-sketch Newton step, the fixed point of every sketched step,
+the CG first-residual identity, eigvalsh, and prox-gradient optimality."""
+import numpy as np
+
+import synthdata
+from oracle import coils, fourier, nufft, solvers, wavelet, philox
+
+
+def _cart_problem(shape=(8, 8), C=4, seed=0, frac=0.5):
+    rng = np.random.default_rng(seed)
+    maps = synthdata.coil_maps(shape, C)
+    idx = fourier.mask_indices(rng.random(shape) < frac)
+    xt = synthdata.phantom(shape, seed=1)
+    y = fourier.cartesian_fwd(xt, maps, idx) + synthdata.complex_noise((C, idx.size), 1e-3, seed=3)
+    return maps, idx, y
+
+
+def _ops(idx):
+    return lambda m: (lambda v: fourier.cartesian_fwd(v, m, idx), lambda k: fourier.cartesian_adj(k, m, idx))
+
+
+def _dense(maps, idx):
+    return fourier.dense_sense_matrix(maps, fourier.sampled_frequencies(maps.shape[1:], idx))
+
+
+def test_cg_reaches_the_direct_normal_equation_solution():
+    maps, idx, y = _cart_problem()
+    lam = 1e-2
+    A = _dense(maps, idx)
+    xs = np.linalg.solve(A.conj().T @ A + lam * np.eye(64), A.conj().T @ y.ravel())
+    fwd, adj = _ops(idx)(maps)
+    x = solvers.plain_cg(fwd, adj, y, lam, np.zeros((8, 8), complex), 200)
+    assert np.abs(x.ravel() - xs).max() <= 1e-10 * np.abs(xs).max()
+
+
+def test_identity_sketch_gives_the_full_newton_step():
+    maps, idx, y = _cart_problem(seed=4)
+    lam = 1e-2
+    C = maps.shape[0]
+    A = _dense(maps, idx)
+    xs = np.linalg.solve(A.conj().T @ A + lam * np.eye(64), A.conj().T @ y.ravel())
+    x, _ = solvers.coil_sketching(_ops(idx), maps, y, lam, "l2", np.zeros((1, 0, 0)), V=C, K=300, do_pca=False)
+    assert np.abs(x.ravel() - xs).max() <= 1e-10 * np.abs(xs).max()
+
+
+def test_full_solution_is_a_fixed_point_of_every_sketched_step():
+    maps, idx, y = _cart_problem(seed=5)
+    lam = 1e-2
+    A = _dense(maps, idx)
+    xs = np.linalg.solve(A.conj().T @ A + lam * np.eye(64), A.conj().T @ y.ravel()).reshape(8, 8)
+    fwd, adj = _ops(idx)(maps)
+    d = adj(fwd(xs) - y)
+    assert np.abs(d + lam * xs).max() <= 1e-10 * np.abs(xs).max()        # d = -lam x*
+    rng = np.random.default_rng(6)
+    for _ in range(3):
+        S_low = rng.standard_normal((2, 2))
+        msk = coils.sketched_maps(S_low, maps, 2)
+        fs, ads = _ops(idx)(msk)
+        x1 = solvers.sketched_cg(lambda v: ads(fs(v)), d, xs, lam, 20)
+        assert np.abs(x1 - xs).max() <= 1e-10 * np.abs(xs).max()
+
+
+def test_cg_first_residual_is_minus_full_gradient():
+    maps, idx, y = _cart_problem(seed=7)
+    lam = 1e-2
+    fwd, adj = _ops(idx)(maps)
+    xt = synthdata.random_complex((8, 8), 8)
+    d = adj(fwd(xt) - y)
+    msk = coils.sketched_maps(np.random.default_rng(9).standard_normal((2, 2)), maps, 2)
+    fs, ads = _ops(idx)(msk)
+    n = lambda v: ads(fs(v))
+    r0 = (n(xt) - d) - (n(xt) + lam * xt)
+    assert np.abs(r0 + d + lam * xt).max() <= 1e-12 * np.abs(d).max()
+
+
+def test_power_iteration_matches_eigvalsh():
+    _, idx, _ = _cart_problem(seed=10, C=3)
+    maps = synthdata.random_complex((3, 8, 8), 10)        # unnormalised maps: a clear spectral gap
+    A = _dense(maps, idx)
+    ev = np.linalg.eigvalsh(A.conj().T @ A)
+    fwd, adj = _ops(idx)(maps)
+    L = solvers.power_iteration(lambda v: adj(fwd(v)), synthdata.random_complex((8, 8), 11), 200)
+    assert abs(L - ev[-1]) <= 1e-6 * ev[-1]
+
+
+def test_fista_converges_to_a_prox_gradient_fixed_point():
+    maps, idx, y = _cart_problem(shape=(16, 16), seed=12)
+    lam = 5e-3
+    fwd, adj = _ops(idx)(maps)
+    L = solvers.power_iteration(lambda v: adj(fwd(v)), synthdata.random_complex((16, 16), 13), 100)
+    eta = 1 / L
+    x = solvers.plain_fista(fwd, adj, y, lam, eta, np.zeros((16, 16), complex), 3000, levels=2)
+    step = wavelet.prox_l1_wavelet(x - eta * adj(fwd(x) - y), eta * lam, 2)
+    assert np.abs(step - x).max() <= 1e-8
+
+
+def test_coil_sketching_converges_to_the_full_solution():
+    shape = (16, 16)
+    C = 8
+    maps, idx, y = _cart_problem(shape=shape, C=C, seed=14, frac=0.4)
+    lam = 1e-2
+    A = _dense(maps, idx)
+    xs = np.linalg.solve(A.conj().T @ A + lam * np.eye(256), A.conj().T @ y.ravel()).reshape(shape)
+    # V = 4 high-energy virtual coils + S = 2 Gaussian combinations of the other 4: the
+    # sketched Hessian is accurate enough for the geometric convergence of the iterative
+    # Hessian sketch (Sec. 2.2)
+    sk = philox.sketch_draw(99, 0, 20, C, 4, 2)
+    errs = []
+    solvers.coil_sketching(_ops(idx), maps, y, lam, "l2", sk, V=4, K=40,
+                           callback=lambda t, x: errs.append(solvers.nrmse(x, xs)))
+    assert errs[-1] < 1e-10 and errs[-1] < errs[0] * 1e-6, errs
+    assert all(b < a for a, b in zip(errs[:8], errs[1:9]))
