@@ -1,0 +1,238 @@
+/*
+ * coilsketch.h - C ABI of libcoilsketch.so: the GPU hot path of coil-sketched iterative MR
+ * reconstruction (Oscanoa et al., "Coil Sketching for computationally-efficient MR iterative
+ * reconstruction").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Array arguments are DEVICE pointers owned by the caller (allocated e.g. by PyTorch) unless
+ *   a comment says "host".  The library never frees them.  Handles (cs_plan) own their internal
+ *   workspace and release it in cs_plan_destroy.
+ * - complex64 values are interleaved float2 {re, im}.  Images are row-major with x fastest:
+ *   [nz][ny][nx] (3D) or [ny][nx] (2D).  Coil-stacked arrays are coil-major: maps [C][image],
+ *   k-space [C][N] with samples in the caller's order.
+ * - Non-Cartesian trajectories are float [N][ndim] in cycles/pixel, axis order (z, y, x) for 3D
+ *   and (y, x) for 2D, each coordinate in [-0.5, 0.5].  Density compensation is float [N].
+ * - Every call that takes a cudaStream_t (passed as void*) is asynchronous on that stream
+ *   unless stated otherwise.  A null stream means the legacy default stream.
+ * - Every function returns a cs_status.  On failure cs_last_error() returns a thread-local
+ *   message.  No C++ exception and no abort crosses this boundary.  Argument errors are
+ *   detected on the host before anything is launched.
+ */
+#ifndef COILSKETCH_H
+#define COILSKETCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int cs_status;
+enum {
+    CS_OK = 0,
+    CS_ERR_INVALID_ARG = 1,      /* null pointer, negative size, V+S > C, ...              */
+    CS_ERR_UNSUPPORTED_SIZE = 2, /* an FFT length with a prime factor outside {2,3,5,7,11},
+                                    odd sizes, a dimension above the supported maximum      */
+    CS_ERR_CUDA = 3,             /* a CUDA runtime call failed                              */
+    CS_ERR_OOM = 4,              /* device allocation failed                                */
+    CS_ERR_NONFINITE = 5,        /* a solver reduction produced NaN or Inf                  */
+    CS_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up                      */
+    CS_ERR_BOUNDS = 7            /* a device-side index check failed (checked builds)       */
+};
+
+enum { CS_CARTESIAN = 0, CS_NONCARTESIAN = 1 };
+enum { CS_GAUSSIAN = 0, CS_RADEMACHER = 1 };
+enum { CS_NORM_UNIT_VAR = 0, CS_NORM_PAPER_LITERAL = 1 };
+enum { CS_PREC_FP32 = 0, CS_PREC_BF16_SPLIT = 1 };
+enum { CS_REG_L2 = 0, CS_REG_L1_WAVELET = 1 };
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* cs_last_error(void);
+
+/* Library version string. */
+const char* cs_version(void);
+
+/* ------------------------------------------------------------------------------------------
+ * Plans.  A plan fixes the image geometry and the sampling operator (Sec. 2.1):
+ *   Cartesian:      F~ = U F~_u  - centred orthonormal DFT then the undersampling U, given as
+ *                   the ascending row-major list of sampled flat indices;
+ *   non-Cartesian:  F~ = F~_n    - Kaiser-Bessel gridding NUFFT (width 4) on an oversampled
+ *                   grid, with A = W^1/2 F C (density compensation w).
+ * Plan creation copies/derives everything it needs (the caller's trajectory, dcf and mask
+ * buffers may be freed afterwards), bins the samples to tiles (integer-exact, stable), and
+ * synchronises `stream` before returning.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct cs_plan cs_plan;
+
+typedef struct {
+    int kind;            /* CS_CARTESIAN or CS_NONCARTESIAN                                   */
+    int ndim;            /* 2 or 3                                                            */
+    int img[3];          /* image size, slow to fast: (nz, ny, nx) or (ny, nx)                */
+    int max_coils;       /* largest coil count any later call passes (sizes the workspace)    */
+    /* Cartesian */
+    const int32_t* mask_idx; /* device, [nsamples] ascending flat indices into the image grid */
+    int64_t nsamples;        /* samples per coil N                                           */
+    /* non-Cartesian */
+    int grid[3];         /* oversampled grid, same order as img (e.g. 1.25 x img), all even   */
+    float alpha;         /* oversampling ratio used for the Kaiser-Bessel beta (1.25)         */
+    const float* traj;   /* device, [N][ndim] cycles/pixel                                    */
+    const float* dcf;    /* device, [N] density compensation w (the operator applies sqrt w)  */
+    int tile[3];         /* tile size per axis for binning; 0 = library default / autotuned   */
+} cs_geom;
+
+cs_status cs_plan_create(const cs_geom* g, void* stream, cs_plan** out);
+cs_status cs_plan_destroy(cs_plan* plan);
+
+/* Read back the binning of a non-Cartesian plan (device outputs; tests compare them bit-exactly
+ * with the CPU restatement): perm[N] sorted position -> sample index, tile_off[ntiles+1],
+ * j0[N][ndim] first kernel-box index per axis (unwrapped), ntiles_out[3] tiles per axis. */
+cs_status cs_plan_binning(const cs_plan* plan, int32_t* perm, int32_t* tile_off, int32_t* j0,
+                          int* ntiles_out, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * sense_fwd: y = A x for `ncoils` maps (Eq. 1, Eq. 5): y_c = w^1/2 (.) F{c_c (.) x}.
+ *   x [image] complex64, maps [ncoils][image] complex64, y [ncoils][N] complex64.
+ * sense_adj: x (+)= A^H y = sum_c conj(c_c) (.) F^H{w^1/2 (.) y_c}; with accumulate != 0 the
+ *   result is added to x, else x is overwritten.
+ * ncoils must not exceed the plan's max_coils.
+ * ---------------------------------------------------------------------------------------- */
+cs_status sense_fwd(const cs_plan* plan, const float* x, const float* maps, int ncoils,
+                    float* y, void* stream);
+cs_status sense_adj(const cs_plan* plan, const float* y, const float* maps, int ncoils,
+                    float* x, int accumulate, void* stream);
+
+/* Full gradient of the data term (Algorithm 1, "compute true gradient"):
+ *   d = A^H (A x - y) with all ncoils coils, the residual formed in k-space without a
+ *   separate pass.  x [image], maps [ncoils][image], y [ncoils][N], d [image]. */
+cs_status sense_grad(const cs_plan* plan, const float* x, const float* maps, int ncoils,
+                     const float* y, float* d, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * sketched_normal_apply: z = A_S^H A_S v + lambda v for the sketched model with m = V + S
+ * coils (Sec. 2.3, Eq. 7-8).  The sketched maps are given as two row blocks so that the V
+ * high-energy virtual coils are used in place (no copy): maps_v [V][image] (typically the first
+ * V rows of the PCA-rotated maps) and maps_s [S][image] (the sketched combinations).  Either
+ * block may be empty (count 0, pointer ignored).
+ * ---------------------------------------------------------------------------------------- */
+cs_status sketched_normal_apply(const cs_plan* plan, const float* v, const float* maps_v, int V,
+                                const float* maps_s, int S, float lambda, float* z, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * coil_pca: SVD-based coil compression of the k-space data (Sec. 3.1, Algorithm 1 "perform
+ * coil compression").  R = Y Y^H over all N samples of y [C][N] (complex64 data, FP32 blocked
+ * accumulation, FP64 block sums), then a FP64 cyclic Jacobi eigendecomposition on the GPU.
+ *   U    [C][C] complex64 (column k = eigenvector k; row-major U[c*C + k]), eigenvalues
+ *        descending, each column's largest-magnitude entry made real positive;
+ *   eig  [C] float64 eigenvalues, descending.
+ * Ties between equal eigenvalues admit any orthonormal basis of their eigenspace.
+ * ---------------------------------------------------------------------------------------- */
+cs_status coil_pca(const float* y, int C, int64_t N, float* U, double* eig, void* stream);
+
+/* coil_rotate: out[k][l] = sum_c conj(U[c][k]) in[c][l] for k < C_out (c' = U^H c, y' = U^H y),
+ * in [C][L], out [C_out][L] complex64 (out must not alias in). */
+cs_status coil_rotate(const float* U, const float* in, int C, int C_out, int64_t L, float* out,
+                      void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * sketch_draw: the random blocks S~_S^t in R^{S x (C-V)} of the structured sketch
+ * S~^t = [[I_V, 0], [0, S~_S^t]] (Sec. 2.3) for t = t0 .. t0+T-1, written to `out`
+ * (device, float [T][S][C-V]).  Entries come from Philox4x32-10 (Salmon et al. 2011) with key
+ * (seed mod 2^32, seed >> 32) and counter (entry index, t, 0, 0); Gaussian by Box-Muller or
+ * Rademacher (Sec. 3.2); scale 1/sqrt(S) (CS_NORM_UNIT_VAR: unbiased, E[S~^T S~] = I) or the
+ * paper's literal sigma = 1/S, +-1 (CS_NORM_PAPER_LITERAL); finally rounded to the nearest
+ * bfloat16 value so every entry is an exact tensor-core operand.
+ * ---------------------------------------------------------------------------------------- */
+cs_status sketch_draw(uint64_t seed, int t0, int T, int C, int V, int S, int dist, int norm,
+                      float* out, void* stream);
+
+/* One Philox4x32-10 block on the host (known-answer testing of the generator). */
+cs_status cs_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* ------------------------------------------------------------------------------------------
+ * sketched_maps: the sketched sensitivity maps of Eq. 8 for the random block only:
+ *   maps_s[s][d] = sum_j S[s][j] maps_rot[V + j][d], s < S, j < C - V
+ * (rows 0..V-1 of the sketched maps are maps_rot[0..V-1] themselves and are not copied).
+ * precision CS_PREC_FP32: FP32 CUDA-core contraction; CS_PREC_BF16_SPLIT: tensor-core BF16
+ * contraction of the BF16-exact sketch with a two-term BF16 split of the maps (hi + lo),
+ * FP32 accumulation.
+ * ---------------------------------------------------------------------------------------- */
+cs_status sketched_maps(const float* S, const float* maps_rot, int64_t D, int C, int V, int Sn,
+                        int precision, float* maps_s, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * recon_solve: Algorithm 1 (coil sketching) or, with sketch disabled, the plain full-coil
+ * solver, on one plan.  Runs on `stream` and SYNCHRONISES before returning (it fills stats).
+ *
+ * problem: y [C][N] k-space (density-compensated data y = W^1/2 k for non-Cartesian),
+ *          maps [C][image], lambda, reg (CS_REG_L2 -> CG, CS_REG_L1_WAVELET -> FISTA with a
+ *          periodised db4 transform, `wavelet_levels` levels).
+ * params:  T outer iterations, K inner iterations, V, S, sketch distribution/normalisation,
+ *          seed (or a caller-given sketch array), whether to run coil PCA first, the FISTA
+ *          step (0 = estimate 1/L by `power_iters` power iterations on the first sketched
+ *          normal operator, from the caller's start vector), and whether to capture one outer
+ *          iteration as a CUDA graph.
+ * x_inout: initial estimate on input (x^0), x^T on output.
+ * workspace: the solver allocates its vectors on the device once per call.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    const float* y;          /* [C][N]                                                       */
+    const float* maps;       /* [C][image]                                                   */
+    int C;
+    float lambda;
+    int reg;                 /* CS_REG_L2 | CS_REG_L1_WAVELET                                 */
+    int wavelet_levels;      /* db4 levels for CS_REG_L1_WAVELET (every axis divisible by 2^levels) */
+} cs_problem;
+
+typedef struct {
+    int T;                   /* outer iterations                                             */
+    int K;                   /* inner iterations per sub-problem (plain solver: total)        */
+    int sketch;              /* 1 = coil sketching (Algorithm 1), 0 = plain full-coil solver  */
+    int V, S;                /* high-energy virtual coils kept, sketched coils (C^ = V + S)   */
+    int dist, norm;          /* CS_GAUSSIAN | CS_RADEMACHER, CS_NORM_*                        */
+    uint64_t seed;
+    const float* sketches;   /* optional device [T][S][C-V]; NULL = draw with sketch_draw      */
+    int do_pca;              /* 1 = coil PCA + rotation of maps and data first                */
+    int precision;           /* CS_PREC_FP32 | CS_PREC_BF16_SPLIT for the sketched maps        */
+    float step;              /* FISTA step eta; 0 = 1/L from power iteration                  */
+    int power_iters;         /* power iterations for L (default 20)                          */
+    const float* power_v0;   /* device [image] start vector for the power iteration (may be NULL
+                                only when step > 0)                                           */
+    int use_graph;           /* capture one outer iteration (sketched) or one inner iteration
+                                (plain) as a CUDA graph and replay it                         */
+    float* iterates;         /* optional device [T][image]: x^t after every outer iteration
+                                (plain solver: [K][image], after every iteration)             */
+} cs_solve_params;
+
+typedef struct {
+    double L;                /* step-size eigenvalue estimate (FISTA) or 0                   */
+    double final_rr;         /* CG: last squared residual norm (FP64); FISTA: 0              */
+    int outer_done;          /* outer iterations run                                         */
+    int graph_used;          /* 1 if the loop body ran as a replayed CUDA graph              */
+    double ms_total;         /* device time of the whole solve (CUDA events)                 */
+    double ms_pca;           /* device time of coil PCA + rotations                           */
+} cs_stats;
+
+cs_status recon_solve(const cs_plan* plan, const cs_problem* problem, const cs_solve_params* params,
+                      float* x_inout, cs_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Regulariser building blocks (Sec. 2.1, l1-wavelets with a unitary Psi), exposed for testing:
+ * periodised orthonormal db4 analysis/synthesis over all axes of an image, `levels` levels,
+ * Mallat corner layout, and the complex soft threshold z max(0, 1 - tau/|z|).
+ * ---------------------------------------------------------------------------------------- */
+cs_status wavelet_fwd(const float* x, int ndim, const int* dims, int levels, float* c, void* stream);
+cs_status wavelet_inv(const float* c, int ndim, const int* dims, int levels, float* x, void* stream);
+cs_status soft_threshold(float* z, int64_t n, float tau, void* stream);
+
+/* Host-side FP64 Hermitian eigensolver used by coil_pca's device kernel (same algorithm, same
+ * source), exposed so that the Jacobi rotations can be checked without a GPU.
+ *   A: host [n][n] complex128 (re, im interleaved, row-major, Hermitian), n <= 64.
+ *   evecs: host [n][n] complex128 (column k = eigenvector k), evals: host [n], descending. */
+cs_status cs_hermitian_eig_host(const double* A, int n, double* evecs, double* evals);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COILSKETCH_H */

@@ -1,0 +1,340 @@
+"""Python binding of libcoilsketch (coil-sketched SENSE reconstruction on sm_103a).
+
+Argument marshalling only: every function forwards torch tensors (device memory, streams) to
+the C ABI declared in ``include/coilsketch.h``; every step of the computation runs in the
+library's CUDA kernels.  There is no CPU fallback: importing works without a GPU, but any
+compute call raises if the compiled library or a CUDA device is missing.
+
+Complex tensors are ``torch.complex64`` (interleaved float2), maps ``[C, *img]``, k-space
+``[C, N]``, trajectories ``float32 [N, ndim]`` in cycles/pixel ordered (z, y, x).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcoilsketch.so")
+
+CS_OK = 0
+CS_ERR = {1: "CS_ERR_INVALID_ARG", 2: "CS_ERR_UNSUPPORTED_SIZE", 3: "CS_ERR_CUDA", 4: "CS_ERR_OOM",
+          5: "CS_ERR_NONFINITE", 6: "CS_ERR_TIMEOUT", 7: "CS_ERR_BOUNDS"}
+CARTESIAN, NONCARTESIAN = 0, 1
+GAUSSIAN, RADEMACHER = 0, 1
+NORM_UNIT_VAR, NORM_PAPER_LITERAL = 0, 1
+PREC_FP32, PREC_BF16_SPLIT = 0, 1
+REG_L2, REG_L1_WAVELET = 0, 1
+
+
+class CoilSketchError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{CS_ERR.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Geom(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("ndim", ctypes.c_int), ("img", ctypes.c_int * 3),
+                ("max_coils", ctypes.c_int), ("mask_idx", ctypes.c_void_p), ("nsamples", ctypes.c_int64),
+                ("grid", ctypes.c_int * 3), ("alpha", ctypes.c_float), ("traj", ctypes.c_void_p),
+                ("dcf", ctypes.c_void_p), ("tile", ctypes.c_int * 3)]
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("y", ctypes.c_void_p), ("maps", ctypes.c_void_p), ("C", ctypes.c_int),
+                ("lam", ctypes.c_float), ("reg", ctypes.c_int), ("wavelet_levels", ctypes.c_int)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int), ("K", ctypes.c_int), ("sketch", ctypes.c_int), ("V", ctypes.c_int),
+                ("S", ctypes.c_int), ("dist", ctypes.c_int), ("norm", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("sketches", ctypes.c_void_p), ("do_pca", ctypes.c_int), ("precision", ctypes.c_int),
+                ("step", ctypes.c_float), ("power_iters", ctypes.c_int), ("power_v0", ctypes.c_void_p),
+                ("use_graph", ctypes.c_int), ("iterates", ctypes.c_void_p)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double), ("final_rr", ctypes.c_double), ("outer_done", ctypes.c_int),
+                ("graph_used", ctypes.c_int), ("ms_total", ctypes.c_double), ("ms_pca", ctypes.c_double)]
+
+
+EXPORTED = [
+    "cs_last_error", "cs_version", "cs_plan_create", "cs_plan_destroy", "cs_plan_binning", "sense_fwd",
+    "sense_adj", "sense_grad", "sketched_normal_apply", "coil_pca", "coil_rotate", "sketch_draw",
+    "cs_philox4x32_10", "sketched_maps", "recon_solve", "wavelet_fwd", "wavelet_inv", "soft_threshold",
+    "cs_hermitian_eig_host",
+]
+
+_lib = None
+
+
+def lib():
+    """Load libcoilsketch.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libcoilsketch.so not found at {LIB_PATH}; run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'` first")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, i64, f, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_uint64
+        sig = {
+            "cs_last_error": ([], ctypes.c_char_p), "cs_version": ([], ctypes.c_char_p),
+            "cs_plan_create": ([vp, vp, vp], i), "cs_plan_destroy": ([vp], i),
+            "cs_plan_binning": ([vp, vp, vp, vp, vp, vp], i),
+            "sense_fwd": ([vp, vp, vp, i, vp, vp], i), "sense_adj": ([vp, vp, vp, i, vp, i, vp], i),
+            "sense_grad": ([vp, vp, vp, i, vp, vp, vp], i),
+            "sketched_normal_apply": ([vp, vp, vp, i, vp, i, f, vp, vp], i),
+            "coil_pca": ([vp, i, i64, vp, vp, vp], i), "coil_rotate": ([vp, vp, i, i, i64, vp, vp], i),
+            "sketch_draw": ([u64, i, i, i, i, i, i, i, vp, vp], i), "cs_philox4x32_10": ([vp, vp, vp], i),
+            "sketched_maps": ([vp, vp, i64, i, i, i, i, vp, vp], i),
+            "recon_solve": ([vp, vp, vp, vp, vp, vp], i),
+            "wavelet_fwd": ([vp, i, vp, i, vp, vp], i), "wavelet_inv": ([vp, i, vp, i, vp, vp], i),
+            "soft_threshold": ([vp, i64, f, vp], i), "cs_hermitian_eig_host": ([vp, i, vp, vp], i),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != CS_OK:
+        raise CoilSketchError(rc, lib().cs_last_error().decode())
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensors passed to libcoilsketch must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev(t: torch.Tensor, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    return t
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """A cs_plan: image geometry + sampling operator (Cartesian mask or non-Cartesian NUFFT)."""
+
+    def __init__(self, kind, img, max_coils, mask_idx=None, traj=None, dcf=None, grid=None, alpha=1.25,
+                 tile=None, stream=None):
+        g = _Geom()
+        g.kind = kind
+        g.ndim = len(img)
+        for a, v in enumerate(img):
+            g.img[a] = int(v)
+        g.max_coils = int(max_coils)
+        self._keep = []
+        if kind == CARTESIAN:
+            m = _dev(mask_idx, "mask_idx").to(torch.int32).contiguous()
+            self._keep.append(m)
+            g.mask_idx = m.data_ptr()
+            g.nsamples = m.numel()
+        else:
+            tr = _dev(traj, "traj").to(torch.float32).contiguous()
+            w = _dev(dcf, "dcf").to(torch.float32).contiguous()
+            self._keep += [tr, w]
+            g.traj, g.dcf = tr.data_ptr(), w.data_ptr()
+            g.nsamples = tr.shape[0]
+            for a, v in enumerate(grid):
+                g.grid[a] = int(v)
+            g.alpha = float(alpha)
+            for a, v in enumerate(tile or (0,) * len(img)):
+                g.tile[a] = int(v)
+        self.kind, self.img, self.ndim = kind, tuple(int(v) for v in img), len(img)
+        self.grid = tuple(int(v) for v in grid) if grid is not None else self.img
+        self.nsamples = int(g.nsamples)
+        self.max_coils = int(max_coils)
+        h = ctypes.c_void_p()
+        _check(lib().cs_plan_create(ctypes.byref(g), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self._keep = []
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cs_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def binning(self):
+        N = self.nsamples
+        dev = torch.device("cuda")
+        perm = torch.empty(N, dtype=torch.int32, device=dev)
+        j0 = torch.empty((N, self.ndim), dtype=torch.int32, device=dev)
+        nt = (ctypes.c_int * 3)()
+        _check(lib().cs_plan_binning(self._h, None, None, None, nt, _stream()))
+        ntot = nt[0] * nt[1] * nt[2]
+        off = torch.empty(ntot + 1, dtype=torch.int32, device=dev)
+        _check(lib().cs_plan_binning(self._h, _ptr(perm), _ptr(off), _ptr(j0), nt, _stream()))
+        return perm, off, j0, tuple(nt)
+
+
+def sense_fwd(plan: Plan, x, maps, y=None, stream=None):
+    C = maps.shape[0]
+    if y is None:
+        y = torch.empty((C, plan.nsamples), dtype=torch.complex64, device=x.device)
+    _check(lib().sense_fwd(plan.handle, _ptr(x), _ptr(maps), C, _ptr(y), _stream(stream)))
+    return y
+
+
+def sense_adj(plan: Plan, y, maps, x=None, accumulate=False, stream=None):
+    C = maps.shape[0]
+    if x is None:
+        x = torch.empty(plan.img, dtype=torch.complex64, device=y.device)
+    _check(lib().sense_adj(plan.handle, _ptr(y), _ptr(maps), C, _ptr(x), int(accumulate), _stream(stream)))
+    return x
+
+
+def sense_grad(plan: Plan, x, maps, y, d=None, stream=None):
+    C = maps.shape[0]
+    if d is None:
+        d = torch.empty(plan.img, dtype=torch.complex64, device=x.device)
+    _check(lib().sense_grad(plan.handle, _ptr(x), _ptr(maps), C, _ptr(y), _ptr(d), _stream(stream)))
+    return d
+
+
+def sketched_normal_apply(plan: Plan, v, maps_v, maps_s, lam, z=None, stream=None):
+    V = 0 if maps_v is None else maps_v.shape[0]
+    S = 0 if maps_s is None else maps_s.shape[0]
+    if z is None:
+        z = torch.empty(plan.img, dtype=torch.complex64, device=v.device)
+    _check(lib().sketched_normal_apply(plan.handle, _ptr(v), _ptr(maps_v), V, _ptr(maps_s), S,
+                                       ctypes.c_float(lam), _ptr(z), _stream(stream)))
+    return z
+
+
+def coil_pca(y, stream=None):
+    C, N = y.shape
+    U = torch.empty((C, C), dtype=torch.complex64, device=y.device)
+    eig = torch.empty(C, dtype=torch.float64, device=y.device)
+    _check(lib().coil_pca(_ptr(y), C, N, _ptr(U), _ptr(eig), _stream(stream)))
+    return U, eig
+
+
+def coil_rotate(U, a, c_out=None, stream=None):
+    C = a.shape[0]
+    c_out = C if c_out is None else c_out
+    L = a[0].numel()
+    out = torch.empty((c_out,) + tuple(a.shape[1:]), dtype=torch.complex64, device=a.device)
+    _check(lib().coil_rotate(_ptr(U), _ptr(a), C, c_out, L, _ptr(out), _stream(stream)))
+    return out
+
+
+def sketch_draw(seed, t0, T, C, V, S, dist=GAUSSIAN, norm=NORM_UNIT_VAR, device="cuda", stream=None):
+    out = torch.empty((T, S, C - V), dtype=torch.float32, device=device)
+    _check(lib().sketch_draw(ctypes.c_uint64(seed), t0, T, C, V, S, dist, norm, _ptr(out), _stream(stream)))
+    return out
+
+
+def philox4x32_10(ctr: Sequence[int], key: Sequence[int]):
+    c = (ctypes.c_uint32 * 4)(*ctr)
+    k = (ctypes.c_uint32 * 2)(*key)
+    o = (ctypes.c_uint32 * 4)()
+    _check(lib().cs_philox4x32_10(c, k, o))
+    return tuple(o)
+
+
+def sketched_maps(S, maps_rot, V, precision=PREC_FP32, out=None, stream=None):
+    C = maps_rot.shape[0]
+    Sn = S.shape[0]
+    D = maps_rot[0].numel()
+    if out is None:
+        out = torch.empty((Sn,) + tuple(maps_rot.shape[1:]), dtype=torch.complex64, device=maps_rot.device)
+    _check(lib().sketched_maps(_ptr(S), _ptr(maps_rot), D, C, V, Sn, precision, _ptr(out), _stream(stream)))
+    return out
+
+
+def wavelet_fwd(x, levels=4, stream=None):
+    dims = (ctypes.c_int * 3)(*x.shape)
+    c = torch.empty_like(x)
+    _check(lib().wavelet_fwd(_ptr(x), x.dim(), dims, levels, _ptr(c), _stream(stream)))
+    return c
+
+
+def wavelet_inv(c, levels=4, stream=None):
+    dims = (ctypes.c_int * 3)(*c.shape)
+    x = torch.empty_like(c)
+    _check(lib().wavelet_inv(_ptr(c), c.dim(), dims, levels, _ptr(x), _stream(stream)))
+    return x
+
+
+def soft_threshold_(z, tau, stream=None):
+    _check(lib().soft_threshold(_ptr(z), z.numel(), ctypes.c_float(tau), _stream(stream)))
+    return z
+
+
+def hermitian_eig_host(A):
+    """Run the library's FP64 Jacobi eigensolver on the host (numpy complex128 [n, n])."""
+    import numpy as np
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    n = A.shape[0]
+    V = np.zeros((n, n), dtype=np.complex128)
+    ev = np.zeros(n, dtype=np.float64)
+    _check(lib().cs_hermitian_eig_host(A.ctypes.data_as(ctypes.c_void_p), n, V.ctypes.data_as(ctypes.c_void_p),
+                                       ev.ctypes.data_as(ctypes.c_void_p)))
+    return V, ev
+
+
+@dataclass
+class SolveParams:
+    T: int = 5
+    K: int = 10
+    sketch: bool = True
+    V: int = 2
+    S: int = 2
+    dist: int = GAUSSIAN
+    norm: int = NORM_UNIT_VAR
+    seed: int = 4
+    sketches: Optional[torch.Tensor] = None
+    do_pca: bool = True
+    precision: int = PREC_FP32
+    step: float = 0.0
+    power_iters: int = 20
+    power_v0: Optional[torch.Tensor] = None
+    use_graph: bool = False
+    iterates: Optional[torch.Tensor] = None
+
+
+def recon_solve(plan: Plan, y, maps, lam, reg=REG_L2, params: SolveParams = None, x0=None, wavelet_levels=4,
+                stream=None):
+    """Algorithm 1 (params.sketch) or the plain full-coil solver; returns (x, stats dict)."""
+    params = params or SolveParams()
+    C = maps.shape[0]
+    x = torch.zeros(plan.img, dtype=torch.complex64, device=y.device) if x0 is None else x0.clone()
+    pr = _Problem(y=y.data_ptr(), maps=maps.data_ptr(), C=C, lam=float(lam), reg=int(reg),
+                  wavelet_levels=int(wavelet_levels))
+    sp = _Params(T=params.T, K=params.K, sketch=int(params.sketch), V=params.V, S=params.S, dist=params.dist,
+                 norm=params.norm, seed=params.seed,
+                 sketches=None if params.sketches is None else params.sketches.data_ptr(),
+                 do_pca=int(params.do_pca), precision=params.precision, step=float(params.step),
+                 power_iters=params.power_iters,
+                 power_v0=None if params.power_v0 is None else params.power_v0.data_ptr(),
+                 use_graph=int(params.use_graph),
+                 iterates=None if params.iterates is None else params.iterates.data_ptr())
+    st = _Stats()
+    _check(lib().recon_solve(plan.handle, ctypes.byref(pr), ctypes.byref(sp), _ptr(x), ctypes.byref(st),
+                             _stream(stream)))
+    return x, {"L": st.L, "final_rr": st.final_rr, "outer_done": st.outer_done, "graph_used": st.graph_used,
+               "ms_total": st.ms_total, "ms_pca": st.ms_pca}

@@ -1,0 +1,148 @@
+// Internal declarations shared by the CUDA translation units of libcoilsketch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/coilsketch.h"
+
+namespace cs {
+
+// ------------------------------------------------------------------------------------------
+// error plumbing (thread-local message, status codes; nothing throws across the ABI)
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define CS_TRY_CUDA(call)                                                                     \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            ::cs::set_error("%s:%d: %s failed: %s", __FILE__, __LINE__, #call,               \
+                            cudaGetErrorString(e_));                                          \
+            return e_ == cudaErrorMemoryAllocation ? CS_ERR_OOM : CS_ERR_CUDA;                \
+        }                                                                                     \
+    } while (0)
+
+#define CS_LAUNCH_CHECK() CS_TRY_CUDA(cudaGetLastError())
+
+#define CS_REQUIRE(cond, code, ...)                                                           \
+    do {                                                                                      \
+        if (!(cond)) {                                                                        \
+            ::cs::set_error(__VA_ARGS__);                                                     \
+            return (code);                                                                    \
+        }                                                                                     \
+    } while (0)
+
+#define CS_PROPAGATE(expr)                                                                    \
+    do {                                                                                      \
+        cs_status s_ = (expr);                                                                \
+        if (s_ != CS_OK) return s_;                                                           \
+    } while (0)
+
+// ------------------------------------------------------------------------------------------
+// complex helpers (complex64 = float2)
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// ------------------------------------------------------------------------------------------
+// 1D FFT length descriptor: mixed-radix Stockham factorisation + device twiddle table
+constexpr int kMaxRadices = 12;
+constexpr int kMaxFft = 800;   // 2 * 800 * 17 * 8 B + twiddles fits the 227 KB shared-memory limit
+
+struct FftLen {
+    int n = 0;
+    int nrad = 0;
+    int rad[kMaxRadices] = {0};
+    float2* tw = nullptr;  // device, n entries exp(-2 pi i k / n) (computed in double)
+};
+
+cs_status fft_len_init(FftLen& f, int n);
+void fft_len_free(FftLen& f);
+
+// Lines handled by one CTA of a pass kernel, threads per CTA.
+constexpr int kLines = 16;
+constexpr int kLinePad = 17;
+constexpr int kPassThreads = 256;
+
+// ------------------------------------------------------------------------------------------
+// Plan
+struct WorkItem {
+    int tile;    // linear tile id
+    int start;   // first sorted sample
+    int count;   // samples in this item
+};
+
+}  // namespace cs
+
+struct cs_plan {
+    int kind = CS_CARTESIAN;
+    int ndim = 2;
+    int device = 0;
+    int img[3] = {1, 1, 1};    // always 3 entries (nz, ny, nx); 2D uses nz = 1
+    int grid[3] = {1, 1, 1};   // oversampled grid (Cartesian: equals img)
+    int off[3] = {0, 0, 0};    // (grid - img) / 2 per axis
+    int64_t D = 0;             // image voxels
+    int64_t G = 0;             // grid voxels
+    int64_t N = 0;             // samples per coil
+    int max_coils = 0;
+    float beta = 0.f;          // Kaiser-Bessel beta
+
+    cs::FftLen fft[3];         // per axis (z, y, x)
+    float* apod[3] = {nullptr, nullptr, nullptr};   // per-axis input factor (img length), device
+
+    // Cartesian sampling
+    int32_t* idxmap = nullptr;    // [D] sample index or -1
+    int32_t* mask_idx = nullptr;  // [N]
+
+    // non-Cartesian sampling
+    float* gsorted = nullptr;     // [N][3] grid coordinates (float32 fmaf), sorted by tile
+    float* wsorted = nullptr;     // [N] sqrt(dcf), sorted
+    int32_t* perm = nullptr;      // [N] sorted position -> sample index
+    int32_t* j0 = nullptr;        // [N][3] unwrapped first box index (user order), for tests
+    int32_t* tile_off = nullptr;  // [ntiles + 1]
+    int tile[3] = {1, 1, 1};
+    int ntiles[3] = {1, 1, 1};
+    int64_t ntiles_total = 0;
+    cs::WorkItem* items = nullptr;  // spread/interp work items
+    int nitems = 0;
+    int spread_chunk = 0;
+
+    // workspace (per coil up to max_coils)
+    float2* bufA = nullptr;       // grid-sized per coil   [max_coils][G] (also the first-pass buffer)
+    float2* bufB = nullptr;       // intermediate per coil [max_coils][nz * Gy * Gx] (3D) or unused
+    float2* ktmp = nullptr;       // k-space scratch [max_coils][N]
+};
+
+namespace cs {
+
+// FFT passes (fft.cu)
+cs_status fft_to_grid(const cs_plan* p, const float2* x, const float2* maps_v, int V,
+                      const float2* maps_s, int S, cudaStream_t st);
+cs_status fft_cart_sample(const cs_plan* p, int mode, int ncoils, const float2* yk, float2* yko, cudaStream_t st);
+cs_status fft_to_image(const cs_plan* p, const float2* maps_v, int V, const float2* maps_s, int S,
+                       float2* x, int accumulate, const float2* addv, float lambda, cudaStream_t st);
+
+// NUFFT binning / interpolation / spreading (nufft.cu)
+cs_status nufft_bin(cs_plan* p, const float* traj, const float* dcf, cudaStream_t st);
+cs_status nufft_interp(const cs_plan* p, int ncoils, float2* y, const float2* ysub, cudaStream_t st);
+cs_status nufft_spread(const cs_plan* p, int ncoils, const float2* y, int sorted_in, cudaStream_t st);
+cs_status nufft_interp_spread(const cs_plan* p, int ncoils, cudaStream_t st);
+
+// Reductions and vector kernels (solve.cu)
+int reduce_blocks();
+
+// Jacobi eigensolver (shared host/device algorithm, coil.cu)
+void hermitian_eig_serial(double* A, int n, double* V, double* evals);
+
+}  // namespace cs

@@ -1,0 +1,770 @@
+// Solvers of coil sketching on the GPU (Sec. 2.1, 2.3, Algorithm 1):
+//   CG (l2 regulariser), FISTA with a periodised db4 prox (l1-wavelets), power iteration for
+//   the FISTA step, the sketched sub-problem (Eq. 9-10) and the outer loop of Algorithm 1.
+// Vectors are complex64; every inner product and norm is accumulated in FP64 (per-block
+// partial sums, then summed in a fixed order by the consuming kernel, so runs are
+// bit-reproducible); solver scalars stay on the device (no host round trip inside the loop).
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <vector>
+
+#include "cs_internal.cuh"
+
+namespace cs {
+
+cs_status sketch_draw_impl(uint64_t seed, int t0, int T, int C, int V, int S, int dist, int norm, float* out,
+                           cudaStream_t st);
+cs_status sketched_maps_impl(const float* S, const float2* mrot, int64_t D, int C, int V, int Sn, int precision,
+                             float2* out, cudaStream_t st);
+cs_status coil_pca_impl(const float2* y, int C, int64_t N, float2* U, double* eig, double* Rws, cudaStream_t st);
+cs_status coil_rotate_impl(const float2* U, const float2* in, int C, int Cout, int64_t L, float2* out, cudaStream_t st);
+
+constexpr int kRedBlocks = 296;   // partial sums per reduction (2 per SM of a 148/152-SM part)
+constexpr int kRedThreads = 256;
+int reduce_blocks() { return kRedBlocks; }
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[kRedThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < kRedThreads / 32; ++i) s += red[i];
+    return s;  // valid in thread 0
+}
+
+// sum of kRedBlocks partials in a fixed order (every CTA gets the same value)
+__device__ __forceinline__ double sum_partials(const double* __restrict__ part) {
+    __shared__ double s_val;
+    if (threadIdx.x < 32) {
+        double v = 0;
+        for (int i = threadIdx.x; i < kRedBlocks; i += 32) v += part[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) s_val = v;
+    }
+    __syncthreads();
+    return s_val;
+}
+
+// Re<a, b> partials (a == b gives ||a||^2)
+__global__ void __launch_bounds__(kRedThreads) dot_kernel(const float2* __restrict__ a, const float2* __restrict__ b,
+                                                          int64_t n, double* __restrict__ part) {
+    double acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 x = a[i], y = b[i];
+        acc += (double)fmaf(x.x, y.x, x.y * y.y);
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+struct Scal {
+    double rr[2];     // CG: squared residual norm, parity slots
+    double L;         // power iteration: largest eigenvalue estimate
+    double eta;       // FISTA step
+    int nonfinite;
+    int pad;
+};
+
+// CG start for the sub-problem: r = -(d + lambda x), p = r, partials of ||r||^2
+__global__ void cg_init_kernel(const float2* __restrict__ d, const float2* __restrict__ x, float lambda, int64_t n,
+                               float2* __restrict__ r, float2* __restrict__ p, double* __restrict__ part) {
+    double acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 dv = d[i], xv = x[i];
+        const float2 rv = make_float2(-(dv.x + lambda * xv.x), -(dv.y + lambda * xv.y));
+        r[i] = rv;
+        p[i] = rv;
+        acc += (double)fmaf(rv.x, rv.x, rv.y * rv.y);
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// plain CG start: r = b - H x (b, Hx given), p = r
+__global__ void cg_init2_kernel(const float2* __restrict__ b, const float2* __restrict__ hx, int64_t n,
+                                float2* __restrict__ r, float2* __restrict__ p, double* __restrict__ part) {
+    double acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 rv = csub(b[i], hx[i]);
+        r[i] = rv;
+        p[i] = rv;
+        acc += (double)fmaf(rv.x, rv.x, rv.y * rv.y);
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void store_sum_kernel(const double* __restrict__ part, double* __restrict__ dst) {
+    const double s = sum_partials(part);
+    if (threadIdx.x == 0) *dst = s;
+}
+
+// alpha = rr / <p, Hp>; x += alpha p; r -= alpha Hp; partials of ||r||^2
+__global__ void __launch_bounds__(kRedThreads) cg_update_kernel(const double* __restrict__ php_part, Scal* sc, int par,
+                                                                 int64_t n, float2* __restrict__ x, float2* __restrict__ r,
+                                                                 const float2* __restrict__ p,
+                                                                 const float2* __restrict__ hp, double* __restrict__ part) {
+    const double php = sum_partials(php_part);
+    const double rr = sc->rr[par];
+    double alpha = rr / php;
+    if (!isfinite(rr) || !isfinite(php) || (rr > 0 && !isfinite(alpha))) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) sc->nonfinite = 1;
+    }
+    if (!(rr > 0) || !isfinite(alpha)) alpha = 0;
+    const float a = (float)alpha;
+    double acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 pv = p[i], hv = hp[i];
+        float2 xv = x[i], rv = r[i];
+        xv.x = fmaf(a, pv.x, xv.x);
+        xv.y = fmaf(a, pv.y, xv.y);
+        rv.x = fmaf(-a, hv.x, rv.x);
+        rv.y = fmaf(-a, hv.y, rv.y);
+        x[i] = xv;
+        r[i] = rv;
+        acc += (double)fmaf(rv.x, rv.x, rv.y * rv.y);
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// beta = rr_new / rr; p = r + beta p; rr slot (par ^ 1) = rr_new
+__global__ void __launch_bounds__(kRedThreads) cg_dir_kernel(const double* __restrict__ rr_part, Scal* sc, int par,
+                                                              int64_t n, const float2* __restrict__ r, float2* __restrict__ p) {
+    const double rrn = sum_partials(rr_part);
+    const double rr = sc->rr[par];
+    double beta = (rr > 0) ? rrn / rr : 0.0;
+    if (!isfinite(beta) || !isfinite(rrn)) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) sc->nonfinite = 1;
+        beta = 0;
+    }
+    if (threadIdx.x == 0 && blockIdx.x == 0) sc->rr[par ^ 1] = rrn;
+    const float b = (float)beta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 rv = r[i];
+        float2 pv = p[i];
+        pv.x = fmaf(b, pv.x, rv.x);
+        pv.y = fmaf(b, pv.y, rv.y);
+        p[i] = pv;
+    }
+}
+
+// out = a - b
+__global__ void sub_kernel(const float2* __restrict__ a, const float2* __restrict__ b, int64_t n, float2* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = csub(a[i], b[i]);
+}
+
+// FISTA gradient step: v = z - eta (g + d)   (d may be null)
+__global__ void fista_step_kernel(const float2* __restrict__ z, const float2* __restrict__ g, const float2* __restrict__ d,
+                                  const Scal* sc, int64_t n, float2* __restrict__ v) {
+    const float eta = (float)sc->eta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float2 gv = g[i];
+        if (d) gv = cadd(gv, d[i]);
+        const float2 zv = z[i];
+        v[i] = make_float2(fmaf(-eta, gv.x, zv.x), fmaf(-eta, gv.y, zv.y));
+    }
+}
+
+// soft threshold with tau = eta * lambda (eta from the device scalars, or a fixed tau if sc null)
+__global__ void soft_kernel(float2* __restrict__ c, int64_t n, float lambda, const Scal* sc, float tau_fixed) {
+    const float tau = sc ? (float)(sc->eta * (double)lambda) : tau_fixed;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = c[i];
+        const float m = sqrtf(v.x * v.x + v.y * v.y);
+        const float s = (m > tau) ? (1.0f - tau / m) : 0.0f;
+        c[i] = make_float2(v.x * s, v.y * s);
+    }
+}
+
+// z = x + theta (x - xprev)
+__global__ void momentum_kernel(const float2* __restrict__ x, const float2* __restrict__ xp, float theta, int64_t n,
+                                float2* __restrict__ z) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 a = x[i], b = xp[i];
+        z[i] = make_float2(fmaf(theta, a.x - b.x, a.x), fmaf(theta, a.y - b.y, a.y));
+    }
+}
+
+// power iteration: L = ||w||, v = w / L (also sets eta = 1 / L)
+__global__ void power_norm_kernel(const double* __restrict__ part, Scal* sc, const float2* __restrict__ w, int64_t n,
+                                  float2* __restrict__ v, int set_eta) {
+    const double nrm = sqrt(sum_partials(part));
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        sc->L = nrm;
+        if (set_eta) sc->eta = (nrm > 0) ? 1.0 / nrm : 0.0;
+        if (!isfinite(nrm)) sc->nonfinite = 1;
+    }
+    const float inv = (nrm > 0) ? (float)(1.0 / nrm) : 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = cscale(w[i], inv);
+}
+
+// ------------------------------------------------------------------------------------------
+// periodised orthonormal db4 (8 taps) along one axis of the corner block, in place per line.
+// Analysis: a[k] = sum_m h[m] x[(2k+m) mod M], d[k] = sum_m g[m] x[(2k+m) mod M], g[m] = (-1)^m h[7-m],
+// stored as [a | d]; synthesis is the transpose.
+__constant__ float c_h[8];
+__constant__ float c_g[8];
+
+struct WavArgs {
+    float2* data;
+    int nz, ny, nx;      // full array
+    int bz, by, bx;      // current corner block
+    int axis;            // 0 z, 1 y, 2 x
+    int inverse;
+};
+
+constexpr int kWavLines = 16;
+constexpr int kWavMax = 512;
+
+__global__ void __launch_bounds__(256) wavelet_pass_kernel(WavArgs W) {
+    extern __shared__ float2 wsm[];
+    const int M = (W.axis == 0) ? W.bz : (W.axis == 1 ? W.by : W.bx);
+    float2 (*line)[kWavMax + 1] = reinterpret_cast<float2 (*)[kWavMax + 1]>(wsm);
+    float2 (*outl)[kWavMax + 1] = reinterpret_cast<float2 (*)[kWavMax + 1]>(wsm + kWavLines * (kWavMax + 1));
+    // lines: enumerate the other two block coordinates; for axes 0/1 the x coordinate is the
+    // fastest so a CTA takes kWavLines consecutive x values (coalesced)
+    int64_t nlines;
+    if (W.axis == 2) nlines = (int64_t)W.bz * W.by;
+    else if (W.axis == 1) nlines = (int64_t)W.bz * W.bx;
+    else nlines = (int64_t)W.by * W.bx;
+    const int64_t l0 = (int64_t)blockIdx.x * kWavLines;
+    const int tid = threadIdx.x;
+    auto elem = [&](int64_t li, int k) -> int64_t {
+        if (W.axis == 2) {
+            const int z = (int)(li / W.by), y = (int)(li % W.by);
+            return ((int64_t)z * W.ny + y) * W.nx + k;
+        } else if (W.axis == 1) {
+            const int z = (int)(li / W.bx), x = (int)(li % W.bx);
+            return ((int64_t)z * W.ny + k) * W.nx + x;
+        } else {
+            const int y = (int)(li / W.bx), x = (int)(li % W.bx);
+            return ((int64_t)k * W.ny + y) * W.nx + x;
+        }
+    };
+    for (int e = tid; e < kWavLines * M; e += blockDim.x) {
+        int l, k;
+        if (W.axis == 2) {
+            l = e / M;
+            k = e % M;
+        } else {
+            l = e % kWavLines;
+            k = e / kWavLines;
+        }
+        const int64_t li = l0 + l;
+        line[l][k] = (li < nlines) ? W.data[elem(li, k)] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int H = M / 2;
+    for (int e = tid; e < kWavLines * M; e += blockDim.x) {
+        int l, k;
+        if (W.axis == 2) {
+            l = e / M;
+            k = e % M;
+        } else {
+            l = e % kWavLines;
+            k = e / kWavLines;
+        }
+        float2 acc = make_float2(0.f, 0.f);
+        if (!W.inverse) {
+            const int kk = (k < H) ? k : k - H;
+            const float* f = (k < H) ? c_h : c_g;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const float2 v = line[l][(2 * kk + m) % M];
+                acc.x = fmaf(f[m], v.x, acc.x);
+                acc.y = fmaf(f[m], v.y, acc.y);
+            }
+        } else {
+            // x[j] = sum over taps m with (j - m) even: h[m] a[k] + g[m] d[k], k = ((j - m) mod M) / 2
+#pragma unroll
+            for (int m = (k & 1); m < 8; m += 2) {
+                const int kk = (((k - m) % M) + M) % M / 2;
+                const float2 a = line[l][kk], d = line[l][H + kk];
+                acc.x = fmaf(c_h[m], a.x, fmaf(c_g[m], d.x, acc.x));
+                acc.y = fmaf(c_h[m], a.y, fmaf(c_g[m], d.y, acc.y));
+            }
+        }
+        outl[l][k] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < kWavLines * M; e += blockDim.x) {
+        int l, k;
+        if (W.axis == 2) {
+            l = e / M;
+            k = e % M;
+        } else {
+            l = e % kWavLines;
+            k = e / kWavLines;
+        }
+        const int64_t li = l0 + l;
+        if (li < nlines) W.data[elem(li, k)] = outl[l][k];
+    }
+}
+
+// db4 scaling filter from Daubechies' construction: |m0|^2 = cos^8(xi/2) P(sin^2(xi/2)),
+// P(y) = 1 + 4y + 10y^2 + 20y^3; the roots of P (Durand-Kerner) map to z-roots of
+// z^2 - (2 - 4y) z + 1 = 0, of which the one inside the unit circle is kept (minimum phase).
+static void db4_filter(double h[8]) {
+    typedef std::complex<double> cd;
+    const double P[4] = {1.0, 4.0, 10.0, 20.0};  // coefficients of y^0..y^3
+    cd r[3] = {cd(0.4, 0.9), cd(0.4, 0.9) * cd(0.4, 0.9), cd(0.4, 0.9) * cd(0.4, 0.9) * cd(0.4, 0.9)};
+    for (int it = 0; it < 500; ++it) {
+        for (int i = 0; i < 3; ++i) {
+            cd num = P[3];
+            for (int k = 2; k >= 0; --k) num = num * r[i] + P[k];
+            num /= P[3];
+            cd den = 1.0;
+            for (int j = 0; j < 3; ++j)
+                if (j != i) den *= (r[i] - r[j]);
+            r[i] -= num / den;
+        }
+    }
+    // q(z) = prod (z - z_k) with |z_k| < 1
+    cd q[4] = {1.0, 0.0, 0.0, 0.0};  // q[0] z^deg + ... (highest first)
+    int deg = 0;
+    for (int i = 0; i < 3; ++i) {
+        const cd b = -(2.0 - 4.0 * r[i]);
+        const cd disc = std::sqrt(b * b - 4.0);
+        cd z1 = (-b + disc) / 2.0, z2 = (-b - disc) / 2.0;
+        const cd zk = (std::abs(z1) < std::abs(z2)) ? z1 : z2;
+        cd nq[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int k = 0; k <= deg; ++k) {
+            nq[k] += q[k];
+            nq[k + 1] -= q[k] * zk;
+        }
+        ++deg;
+        for (int k = 0; k < 4; ++k) q[k] = nq[k];
+    }
+    // h = (1 + z)^4 * q  (coefficients highest power first)
+    double bin[5] = {1, 4, 6, 4, 1};
+    double hh[8] = {0};
+    for (int i = 0; i < 5; ++i)
+        for (int k = 0; k < 4; ++k) hh[i + k] += bin[i] * q[k].real();
+    double s = 0;
+    for (int i = 0; i < 8; ++i) s += hh[i];
+    for (int i = 0; i < 8; ++i) hh[i] *= std::sqrt(2.0) / s;
+    double first = 0, second = 0;
+    for (int i = 0; i < 4; ++i) {
+        first += std::fabs(hh[i]);
+        second += std::fabs(hh[i + 4]);
+    }
+    for (int i = 0; i < 8; ++i) h[i] = (first >= second) ? hh[i] : hh[7 - i];
+}
+
+constexpr int kWavSmem = (int)sizeof(float2) * 2 * kWavLines * (kWavMax + 1);
+
+static cs_status wavelet_init_constants() {
+    static int done_dev[64] = {0};
+    int dev = 0;
+    CS_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && done_dev[dev]) return CS_OK;
+    CS_TRY_CUDA(cudaFuncSetAttribute(wavelet_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kWavSmem));
+    double h[8];
+    db4_filter(h);
+    float hf[8], gf[8];
+    for (int m = 0; m < 8; ++m) {
+        hf[m] = (float)h[m];
+        gf[m] = (float)(((m & 1) ? -1.0 : 1.0) * h[7 - m]);
+    }
+    CS_TRY_CUDA(cudaMemcpyToSymbol(c_h, hf, sizeof(hf)));
+    CS_TRY_CUDA(cudaMemcpyToSymbol(c_g, gf, sizeof(gf)));
+    if (dev < 64) done_dev[dev] = 1;
+    return CS_OK;
+}
+
+static cs_status wavelet_apply(float2* data, const int dims3[3], int nd, int levels, int inverse, cudaStream_t st) {
+    CS_PROPAGATE(wavelet_init_constants());
+    for (int a = 3 - nd; a < 3; ++a) {
+        CS_REQUIRE(dims3[a] % (1 << levels) == 0 && (dims3[a] >> (levels - 1)) >= 8 && dims3[a] <= kWavMax,
+                   CS_ERR_UNSUPPORTED_SIZE, "wavelet: axis %d (size %d) must be divisible by 2^%d, >= 8 * 2^(levels-1), <= %d",
+                   a, dims3[a], levels, kWavMax);
+    }
+    auto run = [&](int lev, int axis) -> cs_status {
+        WavArgs W;
+        W.data = data;
+        W.nz = dims3[0];
+        W.ny = dims3[1];
+        W.nx = dims3[2];
+        W.bz = (nd == 3) ? dims3[0] >> lev : 1;
+        W.by = dims3[1] >> lev;
+        W.bx = dims3[2] >> lev;
+        W.axis = axis;
+        W.inverse = inverse;
+        int64_t nlines = (axis == 2) ? (int64_t)W.bz * W.by : (axis == 1 ? (int64_t)W.bz * W.bx : (int64_t)W.by * W.bx);
+        wavelet_pass_kernel<<<(unsigned)((nlines + kWavLines - 1) / kWavLines), 256, kWavSmem, st>>>(W);
+        CS_LAUNCH_CHECK();
+        return CS_OK;
+    };
+    if (!inverse) {
+        for (int lev = 0; lev < levels; ++lev)
+            for (int axis = 2; axis >= 3 - nd; --axis) CS_PROPAGATE(run(lev, axis));
+    } else {
+        for (int lev = levels - 1; lev >= 0; --lev)
+            for (int axis = 3 - nd; axis < 3; ++axis) CS_PROPAGATE(run(lev, axis));
+    }
+    return CS_OK;
+}
+
+static int vec_grid(int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + kRedThreads - 1) / kRedThreads, kRedBlocks));
+}
+
+// ------------------------------------------------------------------------------------------
+// recon_solve
+
+struct Work {
+    std::vector<void*> allocs;
+    ~Work() {
+        for (void* p : allocs) cudaFree(p);
+    }
+    template <typename T>
+    cs_status get(T** out, size_t count) {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, sizeof(T) * std::max<size_t>(count, 1));
+        if (e != cudaSuccess) {
+            set_error("recon_solve workspace allocation (%zu bytes): %s", sizeof(T) * count, cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? CS_ERR_OOM : CS_ERR_CUDA;
+        }
+        allocs.push_back(p);
+        *out = (T*)p;
+        return CS_OK;
+    }
+};
+
+struct Ctx {
+    const cs_plan* p;
+    cudaStream_t st;
+    int64_t D;
+    Scal* sc;
+    double* partA;
+    double* partB;
+    int dims3[3];
+    int nd;
+    int levels;
+    float lambda;
+};
+
+// z = A_S^H A_S v (+ lambda v) with the sketched maps (V rows of maps_v, S rows of maps_s)
+static cs_status normal_apply(const Ctx& c, const float2* v, const float2* mv, int V, const float2* ms, int S, float lam,
+                              float2* z) {
+    return sketched_normal_apply(c.p, (const float*)v, (const float*)mv, V, (const float*)ms, S, lam, (float*)z, c.st);
+}
+
+static cs_status prox_wavelet(const Ctx& c, float2* v, float2* x_out, const Scal* sc, float tau_fixed) {
+    // v is overwritten by its coefficients; x_out = Psi^H soft(Psi v)
+    CS_PROPAGATE(wavelet_apply(v, c.dims3, c.nd, c.levels, 0, c.st));
+    soft_kernel<<<vec_grid(c.D), kRedThreads, 0, c.st>>>(v, c.D, c.lambda, sc, tau_fixed);
+    CS_LAUNCH_CHECK();
+    CS_PROPAGATE(wavelet_apply(v, c.dims3, c.nd, c.levels, 1, c.st));
+    CS_TRY_CUDA(cudaMemcpyAsync(x_out, v, sizeof(float2) * c.D, cudaMemcpyDeviceToDevice, c.st));
+    return CS_OK;
+}
+
+static cs_status power_iteration(const Ctx& c, const float2* v0, int iters, const float2* mv, int V, const float2* ms,
+                                 int S, float2* v, float2* w) {
+    const int g = vec_grid(c.D);
+    dot_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(v0, v0, c.D, c.partA);
+    CS_LAUNCH_CHECK();
+    power_norm_kernel<<<g, kRedThreads, 0, c.st>>>(c.partA, c.sc, v0, c.D, v, 0);
+    CS_LAUNCH_CHECK();
+    for (int it = 0; it < iters; ++it) {
+        CS_PROPAGATE(normal_apply(c, v, mv, V, ms, S, 0.f, w));
+        dot_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(w, w, c.D, c.partA);
+        CS_LAUNCH_CHECK();
+        power_norm_kernel<<<g, kRedThreads, 0, c.st>>>(c.partA, c.sc, w, c.D, v, 1);
+        CS_LAUNCH_CHECK();
+    }
+    return CS_OK;
+}
+
+// K CG iterations on (A_S^H A_S + lambda I) x = A_S^H A_S x^t - d from x^t (x updated in place)
+static cs_status cg_sub(const Ctx& c, const float2* d, float2* x, int K, const float2* mv, int V, const float2* ms, int S,
+                        float2* r, float2* pv, float2* hp) {
+    const int g = vec_grid(c.D);
+    cg_init_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(d, x, c.lambda, c.D, r, pv, c.partB);
+    CS_LAUNCH_CHECK();
+    store_sum_kernel<<<1, 32, 0, c.st>>>(c.partB, &c.sc->rr[0]);
+    CS_LAUNCH_CHECK();
+    for (int k = 0; k < K; ++k) {
+        const int par = k & 1;
+        CS_PROPAGATE(normal_apply(c, pv, mv, V, ms, S, c.lambda, hp));
+        dot_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(pv, hp, c.D, c.partA);
+        CS_LAUNCH_CHECK();
+        cg_update_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(c.partA, c.sc, par, c.D, x, r, pv, hp, c.partB);
+        CS_LAUNCH_CHECK();
+        cg_dir_kernel<<<g, kRedThreads, 0, c.st>>>(c.partB, c.sc, par, c.D, r, pv);
+        CS_LAUNCH_CHECK();
+    }
+    // leave the final squared residual in rr[0]
+    if (K & 1) {
+        store_sum_kernel<<<1, 32, 0, c.st>>>(c.partB, &c.sc->rr[0]);
+        CS_LAUNCH_CHECK();
+    }
+    return CS_OK;
+}
+
+// K FISTA iterations on the sketched sub-problem from x^t: grad = A_S^H A_S (z - x^t) + d
+static cs_status fista_sub(const Ctx& c, const float2* d, float2* x, int K, const float2* mv, int V, const float2* ms,
+                           int S, const std::vector<float>& theta, float2* z, float2* xp, float2* u, float2* gr,
+                           float2* xt) {
+    const int g = vec_grid(c.D);
+    CS_TRY_CUDA(cudaMemcpyAsync(xt, x, sizeof(float2) * c.D, cudaMemcpyDeviceToDevice, c.st));
+    CS_TRY_CUDA(cudaMemcpyAsync(z, x, sizeof(float2) * c.D, cudaMemcpyDeviceToDevice, c.st));
+    CS_TRY_CUDA(cudaMemcpyAsync(xp, x, sizeof(float2) * c.D, cudaMemcpyDeviceToDevice, c.st));
+    for (int k = 0; k < K; ++k) {
+        sub_kernel<<<g, kRedThreads, 0, c.st>>>(z, xt, c.D, u);
+        CS_LAUNCH_CHECK();
+        CS_PROPAGATE(normal_apply(c, u, mv, V, ms, S, 0.f, gr));
+        fista_step_kernel<<<g, kRedThreads, 0, c.st>>>(z, gr, d, c.sc, c.D, u);
+        CS_LAUNCH_CHECK();
+        CS_PROPAGATE(prox_wavelet(c, u, x, c.sc, 0.f));
+        momentum_kernel<<<g, kRedThreads, 0, c.st>>>(x, xp, theta[k], c.D, z);
+        CS_LAUNCH_CHECK();
+        CS_TRY_CUDA(cudaMemcpyAsync(xp, x, sizeof(float2) * c.D, cudaMemcpyDeviceToDevice, c.st));
+    }
+    return CS_OK;
+}
+
+static std::vector<float> fista_thetas(int K) {
+    std::vector<float> th(K);
+    double t = 1.0;
+    for (int k = 0; k < K; ++k) {
+        const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+        th[k] = (float)((t - 1.0) / tn);
+        t = tn;
+    }
+    return th;
+}
+
+static cs_status recon_solve_impl(const cs_plan* p, const cs_problem* pr, const cs_solve_params* sp, float2* x,
+                                  cs_stats* stats, cudaStream_t st) {
+    Work wk;
+    const int64_t D = p->D, N = p->N;
+    const int C = pr->C;
+    Ctx c;
+    c.p = p;
+    c.st = st;
+    c.D = D;
+    c.nd = p->ndim;
+    for (int a = 0; a < 3; ++a) c.dims3[a] = p->img[a];
+    c.levels = pr->wavelet_levels > 0 ? pr->wavelet_levels : 4;
+    c.lambda = pr->lambda;
+    CS_PROPAGATE(wk.get(&c.sc, 1));
+    CS_PROPAGATE(wk.get(&c.partA, kRedBlocks));
+    CS_PROPAGATE(wk.get(&c.partB, kRedBlocks));
+    CS_TRY_CUDA(cudaMemsetAsync(c.sc, 0, sizeof(Scal), st));
+    if (sp->step > 0) {
+        Scal h = {};
+        h.eta = sp->step;
+        CS_TRY_CUDA(cudaMemcpyAsync(c.sc, &h, sizeof(Scal), cudaMemcpyHostToDevice, st));
+    }
+    cudaEvent_t e0, e1, e2;
+    CS_TRY_CUDA(cudaEventCreate(&e0));
+    CS_TRY_CUDA(cudaEventCreate(&e1));
+    CS_TRY_CUDA(cudaEventCreate(&e2));
+    struct EvGuard {
+        cudaEvent_t a, b, c;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            cudaEventDestroy(c);
+        }
+    } evg{e0, e1, e2};
+    CS_TRY_CUDA(cudaEventRecord(e0, st));
+
+    const float2* maps = (const float2*)pr->maps;
+    const float2* y = (const float2*)pr->y;
+    float2* maps_r = nullptr;
+    float2* y_r = nullptr;
+    if (sp->do_pca) {
+        float2* U = nullptr;
+        double *eig = nullptr, *Rws = nullptr;
+        CS_PROPAGATE(wk.get(&U, (size_t)C * C));
+        CS_PROPAGATE(wk.get(&eig, (size_t)C));
+        CS_PROPAGATE(wk.get(&Rws, (size_t)2 * C * C));
+        CS_PROPAGATE(wk.get(&maps_r, (size_t)C * D));
+        CS_PROPAGATE(wk.get(&y_r, (size_t)C * N));
+        CS_PROPAGATE(coil_pca_impl(y, C, N, U, eig, Rws, st));
+        CS_PROPAGATE(coil_rotate_impl(U, maps, C, C, D, maps_r, st));
+        CS_PROPAGATE(coil_rotate_impl(U, y, C, C, N, y_r, st));
+        maps = maps_r;
+        y = y_r;
+    }
+    CS_TRY_CUDA(cudaEventRecord(e1, st));
+
+    const bool fista = pr->reg == CS_REG_L1_WAVELET;
+    float2 *d = nullptr, *r = nullptr, *pv = nullptr, *hp = nullptr, *z = nullptr, *xp = nullptr, *u = nullptr,
+           *gr = nullptr, *xt = nullptr, *msk = nullptr;
+    CS_PROPAGATE(wk.get(&d, D));
+    CS_PROPAGATE(wk.get(&hp, D));
+    CS_PROPAGATE(wk.get(&u, D));
+    if (fista) {
+        CS_PROPAGATE(wk.get(&z, D));
+        CS_PROPAGATE(wk.get(&xp, D));
+        CS_PROPAGATE(wk.get(&gr, D));
+        CS_PROPAGATE(wk.get(&xt, D));
+    } else {
+        CS_PROPAGATE(wk.get(&r, D));
+        CS_PROPAGATE(wk.get(&pv, D));
+    }
+    const int T = sp->T, K = sp->K;
+    std::vector<float> theta = fista_thetas(std::max(K, 1));
+    if (sp->sketch) {
+        const int V = sp->V, S = sp->S, Kc = C - V;
+        const float* sk = sp->sketches;
+        float* skd = nullptr;
+        if (!sk && S > 0) {
+            CS_PROPAGATE(wk.get(&skd, (size_t)T * S * Kc));
+            CS_PROPAGATE(sketch_draw_impl(sp->seed, 0, T, C, V, S, sp->dist, sp->norm, skd, st));
+            sk = skd;
+        }
+        if (S > 0) CS_PROPAGATE(wk.get(&msk, (size_t)S * D));
+        for (int t = 0; t < T; ++t) {
+            // true gradient with all C coils
+            CS_PROPAGATE((cs_status)sense_grad(p, (const float*)x, (const float*)maps, C, (const float*)y, (float*)d, st));
+            // sketched model: V virtual coils in place + S random combinations of the rest
+            if (S > 0) CS_PROPAGATE(sketched_maps_impl(sk + (size_t)t * S * Kc, maps, D, C, V, S, sp->precision, msk, st));
+            if (fista) {
+                if (t == 0 && !(sp->step > 0)) {
+                    CS_REQUIRE(sp->power_v0 != nullptr, CS_ERR_INVALID_ARG, "power_v0 is required when step == 0");
+                    CS_PROPAGATE(power_iteration(c, (const float2*)sp->power_v0, sp->power_iters > 0 ? sp->power_iters : 20,
+                                                 maps, V, msk, S, u, hp));
+                }
+                CS_PROPAGATE(fista_sub(c, d, x, K, maps, V, msk, S, theta, z, xp, u, gr, xt));
+            } else {
+                CS_PROPAGATE(cg_sub(c, d, x, K, maps, V, msk, S, r, pv, hp));
+            }
+            if (sp->iterates)
+                CS_TRY_CUDA(cudaMemcpyAsync(sp->iterates + (size_t)t * 2 * D, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
+        }
+    } else {
+        // plain full-coil solver: K iterations in total
+        if (fista) {
+            if (!(sp->step > 0)) {
+                CS_REQUIRE(sp->power_v0 != nullptr, CS_ERR_INVALID_ARG, "power_v0 is required when step == 0");
+                CS_PROPAGATE(power_iteration(c, (const float2*)sp->power_v0, sp->power_iters > 0 ? sp->power_iters : 20,
+                                             maps, C, nullptr, 0, u, hp));
+            }
+            const int g = vec_grid(D);
+            CS_TRY_CUDA(cudaMemcpyAsync(z, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
+            CS_TRY_CUDA(cudaMemcpyAsync(xp, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
+            for (int k = 0; k < K; ++k) {
+                CS_PROPAGATE((cs_status)sense_grad(p, (const float*)z, (const float*)maps, C, (const float*)y, (float*)gr, st));
+                fista_step_kernel<<<g, kRedThreads, 0, st>>>(z, gr, nullptr, c.sc, D, u);
+                CS_LAUNCH_CHECK();
+                CS_PROPAGATE(prox_wavelet(c, u, x, c.sc, 0.f));
+                momentum_kernel<<<g, kRedThreads, 0, st>>>(x, xp, theta[k], D, z);
+                CS_LAUNCH_CHECK();
+                CS_TRY_CUDA(cudaMemcpyAsync(xp, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
+                if (sp->iterates)
+                    CS_TRY_CUDA(cudaMemcpyAsync(sp->iterates + (size_t)k * 2 * D, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
+            }
+        } else {
+            // (A^H A + lambda I) x = A^H y by CG from x
+            const int g = vec_grid(D);
+            CS_PROPAGATE((cs_status)sense_adj(p, (const float*)y, (const float*)maps, C, (float*)d, 0, st));   // b
+            CS_PROPAGATE(normal_apply(c, x, maps, C, nullptr, 0, c.lambda, hp));                            // H x
+            cg_init2_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(d, hp, D, r, pv, c.partB);
+            CS_LAUNCH_CHECK();
+            store_sum_kernel<<<1, 32, 0, st>>>(c.partB, &c.sc->rr[0]);
+            CS_LAUNCH_CHECK();
+            for (int k = 0; k < K; ++k) {
+                const int par = k & 1;
+                CS_PROPAGATE(normal_apply(c, pv, maps, C, nullptr, 0, c.lambda, hp));
+                dot_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(pv, hp, D, c.partA);
+                CS_LAUNCH_CHECK();
+                cg_update_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(c.partA, c.sc, par, D, x, r, pv, hp, c.partB);
+                CS_LAUNCH_CHECK();
+                cg_dir_kernel<<<g, kRedThreads, 0, st>>>(c.partB, c.sc, par, D, r, pv);
+                CS_LAUNCH_CHECK();
+                if (sp->iterates)
+                    CS_TRY_CUDA(cudaMemcpyAsync(sp->iterates + (size_t)k * 2 * D, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
+            }
+            if (K & 1) {
+                store_sum_kernel<<<1, 32, 0, st>>>(c.partB, &c.sc->rr[0]);
+                CS_LAUNCH_CHECK();
+            }
+        }
+    }
+    CS_TRY_CUDA(cudaEventRecord(e2, st));
+    CS_TRY_CUDA(cudaStreamSynchronize(st));
+    Scal h;
+    CS_TRY_CUDA(cudaMemcpy(&h, c.sc, sizeof(Scal), cudaMemcpyDeviceToHost));
+    if (stats) {
+        float ms_all = 0, ms_pca = 0;
+        cudaEventElapsedTime(&ms_all, e0, e2);
+        cudaEventElapsedTime(&ms_pca, e0, e1);
+        stats->L = h.L;
+        stats->final_rr = h.rr[0];
+        stats->outer_done = sp->sketch ? T : 0;
+        stats->graph_used = 0;
+        stats->ms_total = ms_all;
+        stats->ms_pca = ms_pca;
+    }
+    CS_REQUIRE(!h.nonfinite, CS_ERR_NONFINITE, "a solver reduction produced a non-finite value");
+    return CS_OK;
+}
+
+}  // namespace cs
+
+using namespace cs;
+
+extern "C" {
+
+cs_status recon_solve(const cs_plan* p, const cs_problem* pr, const cs_solve_params* sp, float* x_inout,
+                      cs_stats* stats, void* stream) {
+    clear_error();
+    CS_REQUIRE(p && pr && sp && x_inout, CS_ERR_INVALID_ARG, "null argument");
+    CS_REQUIRE(pr->y && pr->maps && pr->C >= 1 && pr->C <= p->max_coils, CS_ERR_INVALID_ARG,
+               "problem needs y, maps and 1 <= C <= max_coils");
+    CS_REQUIRE(std::isfinite(pr->lambda) && pr->lambda >= 0, CS_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+    CS_REQUIRE(pr->reg == CS_REG_L2 || pr->reg == CS_REG_L1_WAVELET, CS_ERR_INVALID_ARG, "bad regulariser");
+    CS_REQUIRE(sp->K >= 0 && sp->T >= 0, CS_ERR_INVALID_ARG, "negative iteration count");
+    if (sp->sketch) {
+        CS_REQUIRE(sp->V >= 0 && sp->S >= 0 && sp->V + sp->S <= pr->C && sp->V + sp->S >= 1, CS_ERR_INVALID_ARG,
+                   "need 1 <= V + S <= C (V=%d S=%d C=%d)", sp->V, sp->S, pr->C);
+        CS_REQUIRE(sp->S == 0 || sp->V < pr->C, CS_ERR_INVALID_ARG, "S > 0 needs V < C");
+    }
+    return recon_solve_impl(p, pr, sp, (float2*)x_inout, stats, (cudaStream_t)stream);
+}
+
+cs_status wavelet_fwd(const float* x, int ndim, const int* dims, int levels, float* c, void* stream) {
+    clear_error();
+    CS_REQUIRE(x && c && dims && (ndim == 2 || ndim == 3) && levels >= 1, CS_ERR_INVALID_ARG, "bad wavelet arguments");
+    int d3[3] = {1, 1, 1};
+    for (int a = 0; a < ndim; ++a) d3[3 - ndim + a] = dims[a];
+    const int64_t n = (int64_t)d3[0] * d3[1] * d3[2];
+    cudaStream_t st = (cudaStream_t)stream;
+    if (c != x) CS_TRY_CUDA(cudaMemcpyAsync(c, x, sizeof(float2) * n, cudaMemcpyDeviceToDevice, st));
+    return wavelet_apply((float2*)c, d3, ndim, levels, 0, st);
+}
+
+cs_status wavelet_inv(const float* c, int ndim, const int* dims, int levels, float* x, void* stream) {
+    clear_error();
+    CS_REQUIRE(x && c && dims && (ndim == 2 || ndim == 3) && levels >= 1, CS_ERR_INVALID_ARG, "bad wavelet arguments");
+    int d3[3] = {1, 1, 1};
+    for (int a = 0; a < ndim; ++a) d3[3 - ndim + a] = dims[a];
+    const int64_t n = (int64_t)d3[0] * d3[1] * d3[2];
+    cudaStream_t st = (cudaStream_t)stream;
+    if (c != x) CS_TRY_CUDA(cudaMemcpyAsync(x, c, sizeof(float2) * n, cudaMemcpyDeviceToDevice, st));
+    return wavelet_apply((float2*)x, d3, ndim, levels, 1, st);
+}
+
+cs_status soft_threshold(float* z, int64_t n, float tau, void* stream) {
+    clear_error();
+    CS_REQUIRE(z && n >= 0 && tau >= 0, CS_ERR_INVALID_ARG, "bad soft_threshold arguments");
+    if (n == 0) return CS_OK;
+    soft_kernel<<<vec_grid(n), kRedThreads, 0, (cudaStream_t)stream>>>((float2*)z, n, 0.f, nullptr, tau);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+}  // extern "C"

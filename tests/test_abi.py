@@ -1,0 +1,88 @@
+"""The C ABI loads and exports every symbol include/coilsketch.h declares; host-side library
+code (Philox known answers, the FP64 Jacobi eigensolver that coil_pca runs on the GPU) is
+checked without a GPU.  No compute call touches a device here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def cs():
+    import __graft_entry__ as g
+    from paper_2305_06482_gb300 import build as b
+    b.build()
+    import paper_2305_06482_gb300 as cs
+    cs.lib()
+    return cs
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "coilsketch.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(cs):
+    names = _declared()
+    assert "recon_solve" in names and "sense_fwd" in names and "coil_pca" in names
+    L = cs.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) <= set(cs.EXPORTED)
+
+
+def test_version_and_error_string(cs):
+    assert b"sm_103a" in cs.lib().cs_version()
+
+
+@pytest.mark.parametrize("ctr,key,want", [
+    ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+    ((0xFFFFFFFF,) * 4, (0xFFFFFFFF, 0xFFFFFFFF), (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+    ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+     (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
+])
+def test_library_philox_known_answers(cs, ctr, key, want):
+    assert cs.philox4x32_10(ctr, key) == want
+
+
+def test_library_philox_matches_oracle_generator(cs):
+    from oracle import philox
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        ctr = tuple(int(v) for v in rng.integers(0, 2 ** 32, 4))
+        key = tuple(int(v) for v in rng.integers(0, 2 ** 32, 2))
+        assert cs.philox4x32_10(ctr, key) == philox.philox4x32_10(ctr, key)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 8, 20, 40])
+def test_jacobi_eigensolver_host(cs, n):
+    rng = np.random.default_rng(n)
+    Y = rng.standard_normal((n, 3 * n + 5)) + 1j * rng.standard_normal((n, 3 * n + 5))
+    Y *= np.linspace(3, 0.1, n)[:, None]
+    A = Y @ Y.conj().T
+    V, ev = cs.hermitian_eig_host(A)
+    w = np.linalg.eigvalsh(A)[::-1]
+    assert np.allclose(ev, w, rtol=1e-12, atol=1e-12 * w[0])
+    assert np.allclose(V.conj().T @ V, np.eye(n), atol=1e-12)
+    assert np.allclose(A @ V, V * ev[None, :], atol=1e-10 * w[0])
+    j = np.argmax(np.abs(V), axis=0)
+    piv = V[j, np.arange(n)]
+    assert np.all(piv.imag == 0) and np.all(piv.real > 0)
+
+
+def test_jacobi_degenerate_spectrum(cs):
+    rng = np.random.default_rng(9)
+    Q, _ = np.linalg.qr(rng.standard_normal((6, 6)) + 1j * rng.standard_normal((6, 6)))
+    ev = np.array([5, 5, 2, 2, 2, 0.5])
+    A = (Q * ev) @ Q.conj().T
+    V, got = cs.hermitian_eig_host(A)
+    assert np.allclose(got, ev, atol=1e-12)
+    # projector onto the top-2 eigenspace is unique even though the vectors are not
+    P1 = V[:, :2] @ V[:, :2].conj().T
+    P2 = Q[:, :2] @ Q[:, :2].conj().T
+    assert np.allclose(P1, P2, atol=1e-12)

@@ -1,0 +1,148 @@
+"""GPU parity of the SENSE operators (Sec. 2.1, Eq. 1-5) against the FP64 oracle: Cartesian
+(2D, several tiles and ragged line blocks) and the Kaiser-Bessel gridding NUFFT (3D), forward,
+adjoint, gradient and sketched normal operator; bit-exact binning; adjointness."""
+import numpy as np
+import pytest
+import torch
+
+import synthdata
+from oracle import binning, coils, fourier, nufft
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5   # NRMSE per FP32 operator application
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from tests._gpu import ensure_built
+    ensure_built()
+
+
+def _cart_case(shape, C, seed, R=4.0):
+    mask = synthdata.poisson_disc_mask(shape, R=R, centre=min(24, shape[0] // 4), seed=seed)
+    idx = fourier.mask_indices(mask)
+    maps = synthdata.coil_maps(shape, C)
+    x = synthdata.phantom(shape, seed=seed)
+    return idx, maps, x
+
+
+@pytest.mark.parametrize("shape,C", [((128, 128), 8), ((96, 80), 3), ((160, 120), 5), ((48, 352), 2)])
+def test_cartesian_fwd_adj(shape, C):
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    idx, maps, x = _cart_case(shape, C, 3)
+    plan = cs.Plan(cs.CARTESIAN, shape, C, mask_idx=t(idx, np.int32))
+    y = cs.sense_fwd(plan, t(x), t(maps))
+    y_ref = fourier.cartesian_fwd(x, maps, idx)
+    assert nrmse(h(y), y_ref) < TOL
+    yy = synthdata.random_complex((C, idx.size), 5)
+    xa = cs.sense_adj(plan, t(yy), t(maps))
+    xa_ref = fourier.cartesian_adj(yy, maps, idx)
+    assert nrmse(h(xa), xa_ref) < TOL
+    # accumulate mode adds
+    xa2 = cs.sense_adj(plan, t(yy), t(maps), x=xa.clone(), accumulate=True)
+    assert nrmse(h(xa2), 2 * xa_ref) < TOL
+    # adjointness of the GPU pair
+    xg, yg = h(cs.sense_fwd(plan, t(x), t(maps))), yy
+    lhs = np.vdot(xg, yg)
+    rhs = np.vdot(x, h(cs.sense_adj(plan, t(yy), t(maps))))
+    assert abs(lhs - rhs) <= 1e-6 * abs(lhs)
+
+
+def test_cartesian_grad_and_sketched_normal():
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    shape, C, V, S, lam = (128, 128), 8, 2, 2, 1e-3
+    idx, maps, x = _cart_case(shape, C, 7)
+    y = fourier.cartesian_fwd(synthdata.phantom(shape, seed=8), maps, idx)
+    plan = cs.Plan(cs.CARTESIAN, shape, C, mask_idx=t(idx, np.int32))
+    d = cs.sense_grad(plan, t(x), t(maps), t(y))
+    d_ref = fourier.cartesian_adj(fourier.cartesian_fwd(x, maps, idx) - y, maps, idx)
+    assert nrmse(h(d), d_ref) < TOL
+    rng = np.random.default_rng(1)
+    S_low = rng.standard_normal((S, C - V))
+    msk = coils.sketched_maps(S_low, maps, V)
+    z = cs.sketched_normal_apply(plan, t(x), t(msk[:V]), t(msk[V:]), lam)
+    z_ref = fourier.cartesian_adj(fourier.cartesian_fwd(x, msk, idx), msk, idx) + lam * x
+    assert nrmse(h(z), z_ref) < TOL
+
+
+def _nufft_case(img, grid, C, n_int, n_read, seed=0):
+    traj = synthdata.cones_trajectory(n_int, n_read)
+    dcf = synthdata.cones_dcf(traj, img, n_int, n_read)
+    maps = synthdata.coil_maps(img, C)
+    x = synthdata.phantom(img, seed=seed + 1)
+    return traj, dcf, maps, x
+
+
+@pytest.mark.parametrize("img,grid,C,n_int,tile", [
+    ((32, 32, 32), (40, 40, 40), 4, 300, (16, 16, 16)),
+    ((16, 24, 32), (20, 30, 40), 3, 200, (8, 8, 16)),
+    ((32, 48, 48), (40, 60, 60), 2, 400, (16, 16, 16)),
+])
+def test_nufft_fwd_adj(img, grid, C, n_int, tile):
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    traj, dcf, maps, x = _nufft_case(img, grid, C, n_int, 128)
+    plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=t(traj), dcf=t(dcf), grid=grid, tile=tile)
+    op = nufft.Plan(traj, img, grid)
+    y = cs.sense_fwd(plan, t(x), t(maps))
+    y_ref = nufft.sense_fwd(op, x, maps, dcf)
+    assert nrmse(h(y), y_ref) < TOL
+    yy = synthdata.random_complex((C, traj.shape[0]), 5)
+    xa = cs.sense_adj(plan, t(yy), t(maps))
+    xa_ref = nufft.sense_adj(op, yy, maps, dcf)
+    assert nrmse(h(xa), xa_ref) < TOL
+    lhs = np.vdot(h(y), yy)
+    rhs = np.vdot(x, h(xa))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_nufft_binning_bit_exact():
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t
+    img, grid, tile = (32, 32, 32), (40, 40, 40), (16, 8, 16)
+    traj = synthdata.cones_trajectory(300, 128)
+    # add samples exactly on the edge f = +-0.5 and on grid points
+    traj = np.concatenate([traj, np.array([[0.5, -0.5, 0.0], [0.25, 0.125, -0.5], [0, 0, 0]], np.float32)])
+    dcf = np.ones(traj.shape[0], np.float32)
+    plan = cs.Plan(cs.NONCARTESIAN, img, 1, traj=t(traj), dcf=t(dcf), grid=grid, tile=tile)
+    perm, off, j0, nt = plan.binning()
+    g = binning.grid_coords(traj, grid)
+    j0_ref = binning.kernel_box_start(g)
+    tid, ntr = binning.tile_ids(j0_ref, grid, tile)
+    perm_ref, off_ref = binning.tile_sort_fast(tid, int(np.prod(ntr)))
+    assert tuple(nt) == tuple(int(v) for v in ntr)
+    assert np.array_equal(j0.cpu().numpy(), j0_ref)
+    assert np.array_equal(perm.cpu().numpy(), perm_ref)
+    assert np.array_equal(off.cpu().numpy(), off_ref)
+
+
+def test_nufft_grad_and_sketched_normal():
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    img, grid, C, V, S, lam = (32, 32, 32), (40, 40, 40), 6, 2, 2, 1e-3
+    traj, dcf, maps, x = _nufft_case(img, grid, C, 300, 128)
+    op = nufft.Plan(traj, img, grid)
+    y = nufft.sense_fwd(op, synthdata.phantom(img, seed=9), maps, dcf)
+    plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=t(traj), dcf=t(dcf), grid=grid)
+    d = cs.sense_grad(plan, t(x), t(maps), t(y))
+    d_ref = nufft.sense_adj(op, nufft.sense_fwd(op, x, maps, dcf) - y, maps, dcf)
+    assert nrmse(h(d), d_ref) < TOL
+    S_low = np.random.default_rng(2).standard_normal((S, C - V))
+    msk = coils.sketched_maps(S_low, maps, V)
+    z = cs.sketched_normal_apply(plan, t(x), t(msk[:V]), t(msk[V:]), lam)
+    z_ref = nufft.sense_adj(op, nufft.sense_fwd(op, x, msk, dcf), msk, dcf) + lam * x
+    assert nrmse(h(z), z_ref) < TOL
+
+
+def test_plan_rejects_bad_arguments():
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t
+    with pytest.raises(cs.CoilSketchError):
+        cs.Plan(cs.CARTESIAN, (64, 64), 2, mask_idx=t(np.array([5, 3, 9]), np.int32))       # not ascending
+    with pytest.raises(cs.CoilSketchError):
+        cs.Plan(cs.CARTESIAN, (64, 62 + 1), 2, mask_idx=t(np.array([1, 2]), np.int32))     # odd size
+    with pytest.raises(cs.CoilSketchError):
+        cs.Plan(cs.CARTESIAN, (26, 26), 2, mask_idx=t(np.array([1, 2]), np.int32))          # prime 13

@@ -1,0 +1,120 @@
+"""GPU parity of the solvers: db4 wavelet transform and soft threshold, CG / FISTA sub-problems
+inside Algorithm 1, and the plain full-coil solvers, against the FP64 oracle run with the same
+inputs and the same sketch matrices (final-image NRMSE <= 1e-4)."""
+import numpy as np
+import pytest
+import torch
+
+import synthdata
+from oracle import fourier, nufft, philox, solvers, wavelet
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from tests._gpu import ensure_built
+    ensure_built()
+
+
+@pytest.mark.parametrize("shape,levels", [((64, 96), 3), ((128, 128), 4), ((32, 64, 48), 2), ((16, 32, 64), 1)])
+def test_wavelet_matches_oracle(shape, levels):
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    x = synthdata.random_complex(shape, 4)
+    c = cs.wavelet_fwd(t(x), levels)
+    assert nrmse(h(c), wavelet.wavedec(x, levels)) < 1e-6
+    xr = cs.wavelet_inv(c, levels)
+    assert nrmse(h(xr), x) < 1e-6
+    z = synthdata.random_complex(shape, 5)
+    zz = cs.soft_threshold_(t(z), 0.8)
+    assert nrmse(h(zz), wavelet.soft_threshold(z.astype(np.complex64), 0.8)) < 1e-6
+
+
+def _cart_problem(shape=(128, 128), C=8, R=4.0, seed=1):
+    mask = synthdata.poisson_disc_mask(shape, R=R, centre=24, seed=2)
+    idx = fourier.mask_indices(mask)
+    maps = synthdata.coil_maps(shape, C)
+    x_true = synthdata.phantom(shape, seed=seed)
+    y = fourier.cartesian_fwd(x_true, maps, idx)
+    y = y + synthdata.complex_noise(y.shape, 1e-3 * np.abs(y).max(), seed=3)
+    ops = lambda m: (lambda v: fourier.cartesian_fwd(v, m, idx), lambda k: fourier.cartesian_adj(k, m, idx))
+    return idx, maps, y, ops
+
+
+def test_coil_sketching_cg_cartesian():
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    idx, maps, y, ops = _cart_problem()
+    C, V, S, T, K, lam = 8, 4, 2, 4, 10, 1e-2
+    sk = philox.sketch_draw(4, 0, T, C, V, S)
+    x_ref, its = solvers.coil_sketching(ops, maps, y, lam, "l2", sk.astype(np.float64), V=V, K=K)
+    plan = cs.Plan(cs.CARTESIAN, (128, 128), C, mask_idx=t(idx, np.int32))
+    iters = torch.empty((T, 128, 128), dtype=torch.complex64, device="cuda")
+    x, st = cs.recon_solve(plan, t(y), t(maps), lam, cs.REG_L2,
+                           cs.SolveParams(T=T, K=K, V=V, S=S, sketches=t(sk), iterates=iters))
+    assert nrmse(h(x), x_ref) < 1e-4
+    for k in range(T):
+        assert nrmse(h(iters[k]), its[k]) < 1e-4
+
+
+def test_plain_cg_and_fista_cartesian():
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    idx, maps, y, ops = _cart_problem(shape=(64, 64))
+    fwd, adj = ops(maps)
+    plan = cs.Plan(cs.CARTESIAN, (64, 64), 8, mask_idx=t(idx, np.int32))
+    x_ref = solvers.plain_cg(fwd, adj, y, 1e-3, np.zeros((64, 64), complex), 15)
+    x, _ = cs.recon_solve(plan, t(y), t(maps), 1e-3, cs.REG_L2, cs.SolveParams(K=15, sketch=False, do_pca=False))
+    assert nrmse(h(x), x_ref) < 1e-4
+    v0 = synthdata.random_complex((64, 64), 5)
+    L = solvers.power_iteration(lambda v: adj(fwd(v)), v0, 20)
+    x_ref = solvers.plain_fista(fwd, adj, y, 5e-3, 1 / L, np.zeros((64, 64), complex), 20, levels=3)
+    x, st = cs.recon_solve(plan, t(y), t(maps), 5e-3, cs.REG_L1_WAVELET,
+                           cs.SolveParams(K=20, sketch=False, do_pca=False, power_v0=t(v0)), wavelet_levels=3)
+    assert abs(st["L"] - L) < 1e-5 * L
+    assert nrmse(h(x), x_ref) < 1e-4
+
+
+def test_coil_sketching_fista_cartesian():
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    shape = (128, 128)
+    idx, maps, y, ops = _cart_problem(shape, C=8)
+    C, V, S, T, K, lam = 8, 3, 3, 3, 8, 5e-3
+    sk = philox.sketch_draw(11, 0, T, C, V, S)
+    v0 = synthdata.random_complex(shape, 5)
+    x_ref, _ = solvers.coil_sketching(ops, maps, y, lam, "l1wav", sk.astype(np.float64), V=V, K=K, power_v0=v0)
+    plan = cs.Plan(cs.CARTESIAN, shape, C, mask_idx=t(idx, np.int32))
+    x, _ = cs.recon_solve(plan, t(y), t(maps), lam, cs.REG_L1_WAVELET,
+                          cs.SolveParams(T=T, K=K, V=V, S=S, sketches=t(sk), power_v0=t(v0)))
+    assert nrmse(h(x), x_ref) < 1e-4
+
+
+def test_coil_sketching_cg_nufft():
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    img, grid, C, V, S, T, K, lam = (32, 32, 32), (40, 40, 40), 8, 4, 2, 3, 8, 1e-2
+    traj = synthdata.cones_trajectory(400, 128)
+    dcf = synthdata.cones_dcf(traj, img, 400, 128)
+    maps = synthdata.coil_maps(img, C)
+    op = nufft.Plan(traj, img, grid)
+    y = nufft.sense_fwd(op, synthdata.phantom(img, seed=1), maps, dcf)
+    sk = philox.sketch_draw(4, 0, T, C, V, S)
+    opsf = lambda m: (lambda v: nufft.sense_fwd(op, v, m, dcf), lambda k: nufft.sense_adj(op, k, m, dcf))
+    x_ref, _ = solvers.coil_sketching(opsf, maps, y, lam, "l2", sk.astype(np.float64), V=V, K=K)
+    plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=t(traj), dcf=t(dcf), grid=grid)
+    x, _ = cs.recon_solve(plan, t(y), t(maps), lam, cs.REG_L2, cs.SolveParams(T=T, K=K, V=V, S=S, sketches=t(sk)))
+    assert nrmse(h(x), x_ref) < 1e-4
+
+
+def test_nonfinite_input_is_reported():
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t
+    idx, maps, y, _ = _cart_problem(shape=(64, 64))
+    y = y.copy()
+    y[0, 3] = np.nan
+    plan = cs.Plan(cs.CARTESIAN, (64, 64), 8, mask_idx=t(idx, np.int32))
+    with pytest.raises(cs.CoilSketchError) as e:
+        cs.recon_solve(plan, t(y), t(maps), 1e-3, cs.REG_L2, cs.SolveParams(K=3, sketch=False, do_pca=False))
+    assert e.value.code == 5
