@@ -116,7 +116,11 @@ struct cs_plan {
     int64_t ntiles_total = 0;
     cs::WorkItem* items = nullptr;  // spread/interp work items
     int nitems = 0;
-    int spread_chunk = 0;
+    int spread_chunk = 0;         // samples per spreading work item
+    int interp_chunk = 0;         // consecutive sorted samples per warp (interp and spread)
+    int interp_coils = 16;        // coils per warp in interpolation (8, 16 or 32)
+    int spread_coils = 16;        // coils per warp in spreading (8 or 16)
+    float* phi = nullptr;         // KB kernel table [2049] on [0, 2]
 
     // workspace (per coil up to max_coils)
     float2* bufA = nullptr;       // grid-sized per coil   [max_coils][G] (also the first-pass buffer)

@@ -2,8 +2,8 @@
 // element-wise work fused into the first and last pass (Sec. 2.1, Eq. 5: y_c = w^1/2 F{c_c x}).
 //
 // A CTA transforms kLines lines of length n held in shared memory as buf[k * kLinePad + l]
-// (line index fastest), so butterfly threads walk consecutive lines and global loads of
-// strided axes are coalesced 16-element rows.  Each radix-r stage of the Stockham autosort
+// (line index fastest), so butterfly threads walk consecutive lines; buffers are coil-
+// interleaved so that the kLines lines of a CTA are contiguous in global memory for every axis.  Each radix-r stage of the Stockham autosort
 // formulation reads a[j + q n/r], twiddles by exp(-+2 pi i q k / (Ns r)) (k = j mod Ns, Ns the
 // product of earlier radices), applies the r-point DFT and writes b[(j/Ns) Ns r + k + q Ns].
 //
@@ -169,23 +169,30 @@ __device__ float2* fft_lines(float2* a, float2* b, const float2* tw, int n, cons
 }
 
 // ------------------------------------------------------------------------------------------
+// Pass kernels.  Coil stacks are stored coil-interleaved: element (..., k, ..., c) of an
+// intermediate or grid buffer sits at ((... * n + k) * inner_rest + ...) * C + c, so a line is
+// (position along the other axes, coil) and kLines consecutive lines are contiguous in memory
+// for every axis, including x.
 enum PassMode { EXPAND_X = 0, PLAIN = 1, GATHER_Y = 2, SCATTER_Y = 3, MASK_Y = 4, REDUCE_X = 5 };
 
 struct PassArgs {
     int n, nrad, rad[kMaxRadices];
     const float2* tw;
     int sign;
-    int64_t outer;   // outer line index count (X modes: rows)
-    int64_t inner;   // stride of the FFT axis (X modes: 1)
+    int64_t outer;   // PLAIN / Y modes: outer index count
+    int64_t inner;   // PLAIN / Y modes: stride of the FFT axis in elements (includes the coil count)
     int n_in, in_off, n_out, out_off;
     const float2* in;
-    int64_t in_cs;
     float2* out;
-    int64_t out_cs;
+    // X modes: image rows and coils
+    int64_t rows;    // nz * ny image rows
+    int C;           // coils (interleave stride)
+    int rows_per_cta;
     // maps / image
     const float2* maps_v;
     const float2* maps_s;
-    int V, ncoils;
+    int V;
+    int64_t D;
     const float2* x;
     float2* xo;
     const float2* addv;
@@ -203,12 +210,16 @@ struct PassArgs {
     int residual;
 };
 
-__device__ __forceinline__ const float2* coil_map(const PassArgs& A, int c, int64_t D) {
-    return c < A.V ? A.maps_v + (int64_t)c * D : A.maps_s + (int64_t)(c - A.V) * D;
+__device__ __forceinline__ const float2* coil_map(const PassArgs& A, int c) {
+    return c < A.V ? A.maps_v + (int64_t)c * A.D : A.maps_s + (int64_t)(c - A.V) * A.D;
+}
+
+__device__ __forceinline__ bool cart_neg(int py, int px, int ny, int nx) {
+    return (py + px + ny / 2 + nx / 2) & 1;
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kPassThreads) fft_pass_kernel(PassArgs A) {
+__global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
     extern __shared__ float2 smem[];
     const int n = A.n;
     float2* bufa = smem;
@@ -217,65 +228,63 @@ __global__ void __launch_bounds__(kPassThreads) fft_pass_kernel(PassArgs A) {
     __shared__ int srad[kMaxRadices];
     if (threadIdx.x < kMaxRadices) srad[threadIdx.x] = A.rad[threadIdx.x];
     for (int e = threadIdx.x; e < n; e += blockDim.x) stw[e] = A.tw[e];
-
     const int tid = threadIdx.x;
-    constexpr bool XMODE = (MODE == EXPAND_X || MODE == REDUCE_X);
-    // line block
-    int64_t o0 = 0, i0 = 0;
-    if (XMODE) {
-        o0 = (int64_t)blockIdx.x * kLines;
-    } else {
-        const int64_t iblocks = (A.inner + kLines - 1) / kLines;
-        o0 = blockIdx.x / iblocks;
-        i0 = (blockIdx.x % iblocks) * kLines;
-    }
+
     if (MODE == REDUCE_X) {
-        // ---- inverse FFT of each coil's rows, crop, apodise, conj(map) and sum over coils ----
+        // ---- rows_per_cta image rows; inverse FFT of every coil's line, crop, conj(map),
+        //      apodisation and the sum over coils (deterministic order) ----
         constexpr int MAXE = 32;
         float2 acc[MAXE];
 #pragma unroll
         for (int e = 0; e < MAXE; ++e) acc[e] = make_float2(0.f, 0.f);
         const int nx = A.nxi;
-        const int64_t Dimg = A.outer * (int64_t)nx;
-        for (int c = 0; c < A.ncoils; ++c) {
-            const float2* src = A.in + (int64_t)c * A.in_cs;
+        const int R = A.rows_per_cta;
+        const int64_t r0 = (int64_t)blockIdx.x * R;
+        const int cwmax = (A.C >= kLines) ? kLines : A.C;
+        for (int c0 = 0; c0 < A.C; c0 += cwmax) {
+            const int cw = min(cwmax, A.C - c0);
+            const int nl = R * cw;
             __syncthreads();
             for (int e = tid; e < kLines * n; e += blockDim.x) {
-                const int l = e / n, k = e % n;
-                const int64_t o = o0 + l;
+                const int l = e % kLines, k = e / kLines;
                 float2 v = make_float2(0.f, 0.f);
-                if (o < A.outer) v = src[o * n + k];
+                if (l < nl) {
+                    const int64_t row = r0 + l / cw;
+                    const int c = c0 + l % cw;
+                    if (row < A.rows) v = A.in[(row * n + k) * A.C + c];
+                }
                 bufa[k * kLinePad + l] = v;
             }
             __syncthreads();
             float2* res = fft_lines(bufa, bufb, stw, n, srad, A.nrad, A.sign);
-            const float2* mp = coil_map(A, c, Dimg);
 #pragma unroll
             for (int e = 0; e < MAXE; ++e) {
                 const int idx = tid + e * kPassThreads;
-                if (idx < kLines * nx) {
-                    const int l = idx / nx, i = idx % nx;
-                    const int64_t o = o0 + l;
-                    if (o < A.outer) {
-                        const float2 v = res[(i + A.out_off) * kLinePad + l];
-                        const float2 m = mp[o * nx + i];
-                        acc[e] = cadd(acc[e], cmulc(m, v));
+                if (idx < R * nx) {
+                    const int rr = idx / nx, i = idx % nx;
+                    const int64_t row = r0 + rr;
+                    if (row < A.rows) {
+                        for (int q = 0; q < cw; ++q) {
+                            const int l = rr * cw + q;
+                            const float2 v = res[(i + A.out_off) * kLinePad + l];
+                            const float2 m = coil_map(A, c0 + q)[row * nx + i];
+                            acc[e] = cadd(acc[e], cmulc(m, v));
+                        }
                     }
                 }
             }
-            // res may be bufa: the next coil's load waits on the barrier at the loop head
         }
 #pragma unroll
         for (int e = 0; e < MAXE; ++e) {
             const int idx = tid + e * kPassThreads;
-            if (idx < kLines * nx) {
-                const int l = idx / nx, i = idx % nx;
-                const int64_t o = o0 + l;
-                if (o < A.outer) {
-                    const int z = (int)(o / A.nyi), yy = (int)(o % A.nyi);
+            if (idx < R * nx) {
+                const int rr = idx / nx, i = idx % nx;
+                const int64_t row = r0 + rr;
+                if (row < A.rows) {
+                    const int z = (int)(row / A.nyi), yy = (int)(row % A.nyi);
                     const float ap = A.apz[z] * A.apy[yy] * A.apx[i];
                     float2 r = cscale(acc[e], ap);
-                    const int64_t g = o * nx + i;
+                    const int64_t g = row * nx + i;
                     if (A.addv) r = cadd(r, cscale(A.addv[g], A.lambda));
                     if (A.accumulate) r = cadd(r, A.xo[g]);
                     A.xo[g] = r;
@@ -285,42 +294,76 @@ __global__ void __launch_bounds__(kPassThreads) fft_pass_kernel(PassArgs A) {
         return;
     }
 
-    const int c = blockIdx.y;
     // ---------------------------------- load ----------------------------------
+    int64_t o0 = 0, i0 = 0;
     if (MODE == EXPAND_X) {
+        i0 = (int64_t)blockIdx.x * kLines;  // first line = row * C + c
         const int nx = A.nxi;
-        const int64_t Dimg = A.outer * (int64_t)nx;
-        const float2* mp = coil_map(A, c, Dimg);
+        const int64_t nlines = A.rows * A.C;
         __syncthreads();
-        for (int e = tid; e < kLines * n; e += blockDim.x) {
-            const int l = e / n, k = e % n;
-            const int64_t o = o0 + l;
-            const int i = k - A.in_off;
+        for (int e = tid; e < kLines * nx; e += blockDim.x) {
+            const int l = e / nx, i = e % nx;
+            const int64_t L = i0 + l;
             float2 v = make_float2(0.f, 0.f);
-            if (o < A.outer && i >= 0 && i < nx) {
-                const int z = (int)(o / A.nyi), yy = (int)(o % A.nyi);
+            if (L < nlines) {
+                const int64_t row = L / A.C;
+                const int c = (int)(L % A.C);
+                const int z = (int)(row / A.nyi), yy = (int)(row % A.nyi);
                 const float ap = A.apz[z] * A.apy[yy] * A.apx[i];
-                v = cscale(cmul(A.x[o * nx + i], mp[o * nx + i]), ap);
+                v = cscale(cmul(A.x[row * nx + i], coil_map(A, c)[row * nx + i]), ap);
             }
-            bufa[k * kLinePad + l] = v;
+            bufa[(i + A.in_off) * kLinePad + l] = v;
+        }
+        for (int e = tid; e < kLines * (n - nx); e += blockDim.x) {
+            const int l = e % kLines, kk = e / kLines;
+            const int k = (kk < A.in_off) ? kk : kk + nx;
+            bufa[k * kLinePad + l] = make_float2(0.f, 0.f);
         }
     } else {
-        const float2* src = A.in + (int64_t)c * A.in_cs;
+        const int64_t iblocks = (A.inner + kLines - 1) / kLines;
+        o0 = blockIdx.x / iblocks;
+        i0 = (blockIdx.x % iblocks) * kLines;
         __syncthreads();
+        if (MODE == PLAIN) {
+            // loads are issued in batches of 8 per thread before the shared-memory stores, so
+            // every thread keeps 8 independent 8-byte loads in flight
+            constexpr int BATCH = 8;
+            constexpr int KSTEP = kPassThreads / kLines;
+            const int l = tid % kLines;
+            const int64_t i = i0 + l;
+            const bool iv = i < A.inner;
+            for (int kb = tid / kLines; kb < n; kb += BATCH * KSTEP) {
+                float2 reg[BATCH];
+#pragma unroll
+                for (int q = 0; q < BATCH; ++q) {
+                    const int k = kb + q * KSTEP;
+                    const int kk = k - A.in_off;
+                    reg[q] = make_float2(0.f, 0.f);
+                    if (k < n && iv && kk >= 0 && kk < A.n_in) reg[q] = A.in[(o0 * A.n_in + kk) * A.inner + i];
+                }
+#pragma unroll
+                for (int q = 0; q < BATCH; ++q) {
+                    const int k = kb + q * KSTEP;
+                    if (k < n) bufa[k * kLinePad + l] = reg[q];
+                }
+            }
+        } else
         for (int e = tid; e < kLines * n; e += blockDim.x) {
             const int l = e % kLines, k = e / kLines;
             const int64_t i = i0 + l;
             float2 v = make_float2(0.f, 0.f);
             if (i < A.inner) {
                 if (MODE == SCATTER_Y) {
-                    const int32_t f = A.idxmap[(int64_t)k * A.inner + i];
+                    const int64_t px = i / A.C;
+                    const int c = (int)(i % A.C);
+                    const int32_t f = A.idxmap[(int64_t)k * A.nxi + px];
                     if (f >= 0) {
                         v = A.yk[(int64_t)c * A.N + f];
-                        if ((k + (int)i + n / 2 + (int)(A.inner / 2)) & 1) v = make_float2(-v.x, -v.y);
+                        if (cart_neg(k, (int)px, n, A.nxi)) v = make_float2(-v.x, -v.y);
                     }
                 } else {
                     const int kk = k - A.in_off;
-                    if (kk >= 0 && kk < A.n_in) v = src[(o0 * A.n_in + kk) * A.inner + i];
+                    if (kk >= 0 && kk < A.n_in) v = A.in[(o0 * A.n_in + kk) * A.inner + i];
                 }
             }
             bufa[k * kLinePad + l] = v;
@@ -337,13 +380,14 @@ __global__ void __launch_bounds__(kPassThreads) fft_pass_kernel(PassArgs A) {
             const int64_t i = i0 + l;
             float2 v = make_float2(0.f, 0.f);
             if (i < A.inner) {
-                const int32_t f = A.idxmap[(int64_t)k * A.inner + i];
+                const int64_t px = i / A.C;
+                const int c = (int)(i % A.C);
+                const int32_t f = A.idxmap[(int64_t)k * A.nxi + px];
                 if (f >= 0) {
                     v = res[k * kLinePad + l];
                     if (A.residual) {
-                        const bool neg = (k + (int)i + n / 2 + (int)(A.inner / 2)) & 1;
                         float2 yv = A.yk[(int64_t)c * A.N + f];
-                        if (neg) yv = make_float2(-yv.x, -yv.y);
+                        if (cart_neg(k, (int)px, n, A.nxi)) yv = make_float2(-yv.x, -yv.y);
                         v = csub(v, yv);
                     }
                 }
@@ -356,31 +400,36 @@ __global__ void __launch_bounds__(kPassThreads) fft_pass_kernel(PassArgs A) {
 
     // ---------------------------------- store ----------------------------------
     if (MODE == EXPAND_X) {
-        float2* dst = A.out + (int64_t)c * A.out_cs;
+        const int64_t nlines = A.rows * A.C;
         for (int e = tid; e < kLines * n; e += blockDim.x) {
-            const int l = e / n, k = e % n;
-            const int64_t o = o0 + l;
-            if (o < A.outer) dst[o * n + k] = res[k * kLinePad + l];
+            const int l = e % kLines, k = e / kLines;
+            const int64_t L = i0 + l;
+            if (L < nlines) {
+                const int64_t row = L / A.C;
+                const int c = (int)(L % A.C);
+                A.out[(row * n + k) * A.C + c] = res[k * kLinePad + l];
+            }
         }
     } else if (MODE == GATHER_Y) {
         for (int e = tid; e < kLines * n; e += blockDim.x) {
             const int l = e % kLines, k = e / kLines;
             const int64_t i = i0 + l;
             if (i < A.inner) {
-                const int32_t f = A.idxmap[(int64_t)k * A.inner + i];
+                const int64_t px = i / A.C;
+                const int c = (int)(i % A.C);
+                const int32_t f = A.idxmap[(int64_t)k * A.nxi + px];
                 if (f >= 0) {
                     float2 v = res[k * kLinePad + l];
-                    if ((k + (int)i + n / 2 + (int)(A.inner / 2)) & 1) v = make_float2(-v.x, -v.y);
+                    if (cart_neg(k, (int)px, n, A.nxi)) v = make_float2(-v.x, -v.y);
                     A.yko[(int64_t)c * A.N + f] = v;
                 }
             }
         }
     } else {
-        float2* dst = A.out + (int64_t)c * A.out_cs;
         for (int e = tid; e < kLines * A.n_out; e += blockDim.x) {
             const int l = e % kLines, kk = e / kLines;
             const int64_t i = i0 + l;
-            if (i < A.inner) dst[(o0 * A.n_out + kk) * A.inner + i] = res[(kk + A.out_off) * kLinePad + l];
+            if (i < A.inner) A.out[(o0 * A.n_out + kk) * A.inner + i] = res[(kk + A.out_off) * kLinePad + l];
         }
     }
 }
@@ -388,7 +437,7 @@ __global__ void __launch_bounds__(kPassThreads) fft_pass_kernel(PassArgs A) {
 static size_t pass_smem(int n) { return sizeof(float2) * (size_t)(2 * n * kLinePad + n); }
 
 template <int MODE>
-static cs_status launch_pass(const PassArgs& A, int ncoils_grid, cudaStream_t st) {
+static cs_status launch_pass(const PassArgs& A, cudaStream_t st) {
     const size_t sm = pass_smem(A.n);
     static bool attr_set[64] = {false};
     int dev = 0;
@@ -398,15 +447,13 @@ static cs_status launch_pass(const PassArgs& A, int ncoils_grid, cudaStream_t st
                                          (int)pass_smem(kMaxFft)));
         attr_set[dev] = true;
     }
-    dim3 grid;
-    if (MODE == EXPAND_X || MODE == REDUCE_X) {
-        grid.x = (unsigned)((A.outer + kLines - 1) / kLines);
-    } else {
-        grid.x = (unsigned)(A.outer * ((A.inner + kLines - 1) / kLines));
-    }
-    grid.y = (MODE == REDUCE_X) ? 1 : ncoils_grid;
-    if (grid.x == 0 || grid.y == 0) return CS_OK;
-    fft_pass_kernel<MODE><<<grid, kPassThreads, sm, st>>>(A);
+    int64_t blocks;
+    if (MODE == EXPAND_X) blocks = (A.rows * A.C + kLines - 1) / kLines;
+    else if (MODE == REDUCE_X) blocks = (A.rows + A.rows_per_cta - 1) / A.rows_per_cta;
+    else blocks = A.outer * ((A.inner + kLines - 1) / kLines);
+    if (blocks == 0) return CS_OK;
+    CS_REQUIRE(blocks < (int64_t)1 << 31, CS_ERR_UNSUPPORTED_SIZE, "pass grid too large");
+    fft_pass_kernel<MODE><<<(unsigned)blocks, kPassThreads, sm, st>>>(A);
     CS_LAUNCH_CHECK();
     return CS_OK;
 }
@@ -423,28 +470,26 @@ static void fill_maps(PassArgs& A, const cs_plan* p, const float2* maps_v, int V
     A.maps_v = maps_v;
     A.maps_s = maps_s;
     A.V = V;
-    A.ncoils = V + S;
+    A.C = V + S;
+    A.D = p->D;
     A.apz = p->apod[0];
     A.apy = p->apod[1];
     A.apx = p->apod[2];
     A.nyi = p->img[1];
     A.nxi = p->img[2];
+    A.rows = (int64_t)p->img[0] * p->img[1];
 }
 
-// x (.) maps (.) apod, zero-padded rows, FFT along x -> bufA [C][nz][ny][Gx]
+// x (.) maps (.) apod, zero-padded rows, FFT along x -> bufA [rows][Gx][C]
 static cs_status pass_expand(const cs_plan* p, const float2* x, const float2* maps_v, int V,
                              const float2* maps_s, int S, cudaStream_t st) {
     PassArgs A = {};
     fill_fft(A, p->fft[2], -1);
     fill_maps(A, p, maps_v, V, maps_s, S);
-    A.outer = (int64_t)p->img[0] * p->img[1];
-    A.inner = 1;
     A.in_off = p->off[2];
-    A.n_in = p->img[2];
     A.x = x;
     A.out = p->bufA;
-    A.out_cs = p->G;
-    return launch_pass<EXPAND_X>(A, V + S, st);
+    return launch_pass<EXPAND_X>(A, st);
 }
 
 static cs_status pass_reduce(const cs_plan* p, const float2* maps_v, int V, const float2* maps_s, int S,
@@ -452,31 +497,29 @@ static cs_status pass_reduce(const cs_plan* p, const float2* maps_v, int V, cons
     PassArgs A = {};
     fill_fft(A, p->fft[2], +1);
     fill_maps(A, p, maps_v, V, maps_s, S);
-    A.outer = (int64_t)p->img[0] * p->img[1];
-    A.inner = 1;
     A.out_off = p->off[2];
-    A.n_out = p->img[2];
     A.in = p->bufA;
-    A.in_cs = p->G;
     A.xo = x;
     A.accumulate = accumulate;
     A.addv = addv;
     A.lambda = lambda;
-    return launch_pass<REDUCE_X>(A, 1, st);
+    const int C = V + S;
+    A.rows_per_cta = (C >= kLines || C == 0) ? 1 : kLines / C;   // C == 0: only lambda v / accumulate
+    return launch_pass<REDUCE_X>(A, st);
 }
 
-// strided-axis pass for 3D plans: axis 0 (z) or 1 (y)
-static cs_status pass_plain(const cs_plan* p, int axis, int sign, const float2* in, int64_t in_cs,
-                            float2* out, int64_t out_cs, int ncoils, cudaStream_t st) {
+// strided-axis pass for 3D plans: axis 0 (z) or 1 (y); coil-interleaved buffers
+static cs_status pass_plain(const cs_plan* p, int axis, int sign, const float2* in, float2* out, int C,
+                            cudaStream_t st) {
     PassArgs A = {};
     fill_fft(A, p->fft[axis], sign);
     const int Gx = p->grid[2], Gy = p->grid[1];
     if (axis == 1) {
-        A.outer = p->img[0];  // z planes present in both the input and the output of this pass
-        A.inner = Gx;
+        A.outer = (p->ndim == 3) ? p->img[0] : 1;
+        A.inner = (int64_t)Gx * C;
     } else {
         A.outer = 1;
-        A.inner = (int64_t)Gy * Gx;
+        A.inner = (int64_t)Gy * Gx * C;
     }
     if (sign < 0) {  // forward: pad img -> grid
         A.n_in = p->img[axis];
@@ -490,36 +533,34 @@ static cs_status pass_plain(const cs_plan* p, int axis, int sign, const float2* 
         A.out_off = p->off[axis];
     }
     A.in = in;
-    A.in_cs = in_cs;
     A.out = out;
-    A.out_cs = out_cs;
-    return launch_pass<PLAIN>(A, ncoils, st);
+    return launch_pass<PLAIN>(A, st);
 }
 
-static cs_status pass_cart_y(const cs_plan* p, int mode, int ncoils, const float2* yk, float2* yko,
-                             int residual, cudaStream_t st) {
+static cs_status pass_cart_y(const cs_plan* p, int mode, int C, const float2* yk, float2* yko, int residual,
+                             cudaStream_t st) {
     PassArgs A = {};
     const int sign = (mode == SCATTER_Y) ? +1 : -1;
     fill_fft(A, p->fft[1], sign);
+    A.C = C;
+    A.nxi = p->img[2];
     A.outer = 1;
-    A.inner = p->img[2];
+    A.inner = (int64_t)p->img[2] * C;
     A.n_in = p->img[1];
     A.in_off = 0;
     A.n_out = p->img[1];
     A.out_off = 0;
     A.in = p->bufA;
-    A.in_cs = p->G;
     A.out = p->bufA;
-    A.out_cs = p->G;
     A.idxmap = p->idxmap;
     A.yk = yk;
     A.yko = yko;
     A.N = p->N;
     A.residual = residual;
     switch (mode) {
-        case GATHER_Y: return launch_pass<GATHER_Y>(A, ncoils, st);
-        case SCATTER_Y: return launch_pass<SCATTER_Y>(A, ncoils, st);
-        default: return launch_pass<MASK_Y>(A, ncoils, st);
+        case GATHER_Y: return launch_pass<GATHER_Y>(A, st);
+        case SCATTER_Y: return launch_pass<SCATTER_Y>(A, st);
+        default: return launch_pass<MASK_Y>(A, st);
     }
 }
 
@@ -527,32 +568,18 @@ static cs_status pass_cart_y(const cs_plan* p, int mode, int ncoils, const float
 // Public to ops.cu
 
 // Forward chain up to the sampling step: Cartesian leaves the x-transformed rows in bufA; the
-// non-Cartesian chain leaves the oversampled k-space grid in the grid buffer.
+// non-Cartesian chain leaves the oversampled k-space grid [G][C] in the grid buffer.
 cs_status fft_to_grid(const cs_plan* p, const float2* x, const float2* maps_v, int V,
                       const float2* maps_s, int S, cudaStream_t st) {
     const int C = V + S;
     CS_PROPAGATE(pass_expand(p, x, maps_v, V, maps_s, S, st));
     if (p->kind == CS_CARTESIAN) return CS_OK;
     if (p->ndim == 3) {
-        const int64_t bstride = (int64_t)p->img[0] * p->grid[1] * p->grid[2];
-        CS_PROPAGATE(pass_plain(p, 1, -1, p->bufA, p->G, p->bufB, bstride, C, st));
-        CS_PROPAGATE(pass_plain(p, 0, -1, p->bufB, bstride, p->bufA, p->G, C, st));
+        CS_PROPAGATE(pass_plain(p, 1, -1, p->bufA, p->bufB, C, st));
+        CS_PROPAGATE(pass_plain(p, 0, -1, p->bufB, p->bufA, C, st));
         return CS_OK;
     }
-    // 2D: the y pass writes the grid into bufB
-    PassArgs A = {};
-    fill_fft(A, p->fft[1], -1);
-    A.outer = 1;
-    A.inner = p->grid[2];
-    A.n_in = p->img[1];
-    A.in_off = p->off[1];
-    A.n_out = p->grid[1];
-    A.out_off = 0;
-    A.in = p->bufA;
-    A.in_cs = p->G;
-    A.out = p->bufB;
-    A.out_cs = p->G;
-    return launch_pass<PLAIN>(A, C, st);
+    return pass_plain(p, 1, -1, p->bufA, p->bufB, C, st);   // 2D: the grid lands in bufB
 }
 
 // Cartesian sampling along y: mode 0 gather (y = U F .), 1 scatter (U^H y then inverse FFT),
@@ -571,25 +598,12 @@ cs_status fft_cart_sample(const cs_plan* p, int mode, int ncoils, const float2* 
 cs_status fft_to_image(const cs_plan* p, const float2* maps_v, int V, const float2* maps_s, int S,
                        float2* x, int accumulate, const float2* addv, float lambda, cudaStream_t st) {
     const int C = V + S;
-    if (p->kind != CS_CARTESIAN) {
+    if (p->kind != CS_CARTESIAN && C > 0) {
         if (p->ndim == 3) {
-            const int64_t bstride = (int64_t)p->img[0] * p->grid[1] * p->grid[2];
-            CS_PROPAGATE(pass_plain(p, 0, +1, p->bufA, p->G, p->bufB, bstride, C, st));
-            CS_PROPAGATE(pass_plain(p, 1, +1, p->bufB, bstride, p->bufA, p->G, C, st));
+            CS_PROPAGATE(pass_plain(p, 0, +1, p->bufA, p->bufB, C, st));
+            CS_PROPAGATE(pass_plain(p, 1, +1, p->bufB, p->bufA, C, st));
         } else {
-            PassArgs A = {};
-            fill_fft(A, p->fft[1], +1);
-            A.outer = 1;
-            A.inner = p->grid[2];
-            A.n_in = p->grid[1];
-            A.in_off = 0;
-            A.n_out = p->img[1];
-            A.out_off = p->off[1];
-            A.in = p->bufB;
-            A.in_cs = p->G;
-            A.out = p->bufA;
-            A.out_cs = p->G;
-            CS_PROPAGATE(launch_pass<PLAIN>(A, C, st));
+            CS_PROPAGATE(pass_plain(p, 1, +1, p->bufB, p->bufA, C, st));
         }
     }
     return pass_reduce(p, maps_v, V, maps_s, S, x, accumulate, addv, lambda, st);

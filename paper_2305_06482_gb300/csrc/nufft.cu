@@ -5,6 +5,7 @@
 //   g   = fmaf(f, G, G/2) in float32 per axis            (grid coordinate of a sample)
 //   j0  = floor(g) - 1                                  (first of the W = 4 box indices)
 //   phi(u) = I0(beta sqrt(1 - (u/2)^2)) / I0(beta),     beta = pi sqrt((W/a)^2 (a-1/2)^2 - 0.8)
+//            (tabulated in double at 2049 points of [0, 2], linearly interpolated)
 //   tile = floor((j0 mod G) / T) per axis, linear id (z, y, x) with x fastest.
 // The forward grid is produced without the output modulation of the centred DFT; the sign
 // (-1)^(j + G/2) of every grid index is folded into the interpolation weights instead.
@@ -16,27 +17,6 @@
 namespace cs {
 
 constexpr int kW = 4;
-
-struct KbAxis {
-    int G;
-    float beta;
-    float inv_i0b;
-};
-
-__device__ __forceinline__ void kb_weights(float g, const KbAxis& ax, int& j0, float w[kW]) {
-    const float fl = floorf(g);
-    j0 = (int)fl - (kW / 2 - 1);
-    const int half = ax.G / 2;
-#pragma unroll
-    for (int a = 0; a < kW; ++a) {
-        const int j = j0 + a;
-        const float u = g - (float)j;               // in [-2, 2)
-        const float t = 1.0f - 0.25f * u * u;
-        float v = (t > 0.f) ? cyl_bessel_i0f(ax.beta * sqrtf(t)) * ax.inv_i0b : ax.inv_i0b * (t == 0.f);
-        if ((j + half) & 1) v = -v;                  // (-1)^(j + G/2) of the centred DFT
-        w[a] = v;
-    }
-}
 
 __device__ __forceinline__ int wrapi(int j, int G) {
     j %= G;
@@ -228,213 +208,464 @@ cs_status nufft_bin(cs_plan* p, const float* traj, const float* dcf, cudaStream_
 }
 
 // ------------------------------------------------------------------------------------------
-// interpolation: one thread per sorted sample, all coils (weights computed once per sample)
+// Sliding-window interpolation and spreading on the coil-interleaved grid [G][C].
+//
+// Samples are sorted by tile and, inside a tile, by acquisition order, so consecutive sorted
+// samples lie a fraction of a grid unit apart along a readout and their W^3 boxes mostly
+// coincide.  One warp walks a run of consecutive samples; its lanes are (coil, z-slice) pairs
+// of one coil chunk, so every lane sees the same sample and the window updates are uniform
+// across the warp.  A lane keeps P of the 4 z-planes of the box (4x4 values each) in registers:
+// planes are held by z residue modulo 4, so a move along z replaces one plane in place; a move
+// along y or x shifts every held plane by one row/column and touches only the entering
+// (interp: loads) or leaving (spread: atomic adds) row/column.  Kernel weights phi come from a
+// 2049-point table of phi on [0, 2] (linear interpolation, relative error below 3e-7, built in
+// double on the host); 12 lanes evaluate one weight each and the warp shares them by shuffles.
 enum { OUT_USER = 0, OUT_RESID = 1, OUT_SORTED = 2 };
+constexpr int kPhiTable = 2048;
 
 struct GridArgs {
-    const float2* grid;    // [C][G]
-    int64_t G;
+    float2* grid;          // [G][C] (coil-interleaved)
+    int C;                 // interleave stride = coils of the operator call
+    int c0, gsize;         // coil chunk handled by this launch
     int Gz, Gy, Gx;
-    KbAxis az, ay, ax;
+    const float* phi;      // [kPhiTable + 1] phi(u) for u = 2 i / kPhiTable
     const float* gs;       // [N][3]
     const float* ws;       // [N]
     const int32_t* perm;
     int64_t N;
-    int ncoils;
+    int chunk;             // samples per warp
 };
 
+__device__ __forceinline__ float phi_lookup(const float* __restrict__ tab, float u) {
+    float p = fabsf(u) * (0.5f * kPhiTable);
+    int i = (int)p;
+    i = min(i, kPhiTable - 1);
+    const float f = p - (float)i;
+    const float a = tab[i], b = tab[i + 1];
+    return fmaf(f, b - a, a);
+}
+
+__device__ __forceinline__ int wrapc(int j, int G) {   // j in [-G, 2G)
+    return j < 0 ? j + G : (j >= G ? j - G : j);
+}
+
 template <int ND>
-__global__ void __launch_bounds__(256) interp_kernel(GridArgs A, int mode, const float2* __restrict__ ysub,
-                                                     float2* __restrict__ out) {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= A.N) return;
-    int jz = 0, jy, jx;
-    float wz[kW] = {1.f, 0.f, 0.f, 0.f}, wy[kW], wx[kW];
-    if (ND == 3) kb_weights(A.gs[s * 3 + 0], A.az, jz, wz);
-    kb_weights(A.gs[s * 3 + 1], A.ay, jy, wy);
-    kb_weights(A.gs[s * 3 + 2], A.ax, jx, wx);
-    int iz[kW], iy[kW], ix[kW];
+struct SampleBox {
+    int jz, jy, jx;        // wrapped box starts
+    float wz[kW], wy[kW], wx[kW];
+};
+
+// lanes 0..4*ND-1 evaluate one weight each (axis = lane / 4, offset = lane % 4); all lanes get
+// every weight by shuffles.  The sign (-1)^(j + G/2) of the centred DFT is folded in.
+template <int ND>
+__device__ __forceinline__ void sample_box(const GridArgs& A, const float* __restrict__ tab, int64_t s, int lane,
+                                           SampleBox<ND>& B) {
+    const int ax = lane >> 2, off = lane & 3;
+    // axis slot 0 = z (3D only), 1 = y, 2 = x
+    const int axis = (ND == 3) ? ax : ax + 1;
+    float w = 0.f;
+    const float gz = (ND == 3) ? A.gs[s * 3 + 0] : 0.f;
+    const float gy = A.gs[s * 3 + 1], gx = A.gs[s * 3 + 2];
+    if (lane < 4 * ND) {
+        const float g = (axis == 0) ? gz : (axis == 1 ? gy : gx);
+        const int G = (axis == 0) ? A.Gz : (axis == 1 ? A.Gy : A.Gx);
+        const int j = (int)floorf(g) - (kW / 2 - 1) + off;
+        w = phi_lookup(tab, g - (float)j);
+        if ((j + G / 2) & 1) w = -w;
+    }
 #pragma unroll
     for (int a = 0; a < kW; ++a) {
-        iz[a] = (ND == 3) ? wrapi(jz + a, A.Gz) : 0;
-        iy[a] = wrapi(jy + a, A.Gy);
-        ix[a] = wrapi(jx + a, A.Gx);
+        if (ND == 3) B.wz[a] = __shfl_sync(0xffffffffu, w, a);
+        else B.wz[a] = (a == 0) ? 1.f : 0.f;
+        B.wy[a] = __shfl_sync(0xffffffffu, w, (ND == 3 ? 4 : 0) + a);
+        B.wx[a] = __shfl_sync(0xffffffffu, w, (ND == 3 ? 8 : 4) + a);
     }
-    const float sw = A.ws[s];
-    const int32_t ps = A.perm[s];
-    for (int c = 0; c < A.ncoils; ++c) {
-        const float2* gc = A.grid + (int64_t)c * A.G;
+    B.jz = (ND == 3) ? wrapc((int)floorf(gz) - (kW / 2 - 1), A.Gz) : 0;
+    B.jy = wrapc((int)floorf(gy) - (kW / 2 - 1), A.Gy);
+    B.jx = wrapc((int)floorf(gx) - (kW / 2 - 1), A.Gx);
+}
+
+__device__ __forceinline__ int64_t gaddr(const GridArgs& A, int z, int y, int x, int c) {
+    return (((int64_t)z * A.Gy + y) * A.Gx + x) * A.C + c;
+}
+
+// Per-lane window: P planes of 4x4 values; plane p holds z residue q + p*s (s = 4 / P lanes per
+// coil).  zc[p] is the (wrapped) z of the plane or -1 when empty.
+template <int P>
+struct Win {
+    float2 v[P][kW][kW];
+    int zc[P];
+};
+
+template <int ND, int P>
+__global__ void __launch_bounds__(128) interp_kernel(GridArgs A, int mode, const float2* __restrict__ ysub,
+                                                     float2* __restrict__ out) {
+    __shared__ float tab[kPhiTable + 1];
+    for (int i = threadIdx.x; i <= kPhiTable; i += blockDim.x) tab[i] = A.phi[i];
+    __syncthreads();
+    constexpr int S = (ND == 3) ? 4 / P : 1;     // lanes per coil
+    const int lane = threadIdx.x & 31;
+    const int coil_l = lane / S, slice = lane % S;
+    const bool active = coil_l < A.gsize;
+    const int c = A.c0 + (active ? coil_l : 0);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t s0 = warp * A.chunk;
+    if (s0 >= A.N) return;                       // whole warp exits together
+    const int64_t s1 = min(A.N, s0 + A.chunk);
+    Win<P> W;
+#pragma unroll
+    for (int p = 0; p < P; ++p) W.zc[p] = -1;
+    int cy = -100, cx = -100;
+    for (int64_t s = s0; s < s1; ++s) {
+        SampleBox<ND> B;
+        sample_box<ND>(A, tab, s, lane, B);
+        const int dy = B.jy - cy, dx = B.jx - cx;
+        if (abs(dy) > 1 || abs(dx) > 1) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) W.zc[p] = -1;    // reload every plane below
+        } else {
+            if (dy != 0) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    if (dy > 0) {
+#pragma unroll
+                        for (int b = 0; b < kW - 1; ++b)
+#pragma unroll
+                            for (int d = 0; d < kW; ++d) W.v[p][b][d] = W.v[p][b + 1][d];
+                    } else {
+#pragma unroll
+                        for (int b = kW - 1; b > 0; --b)
+#pragma unroll
+                            for (int d = 0; d < kW; ++d) W.v[p][b][d] = W.v[p][b - 1][d];
+                    }
+                    if (W.zc[p] >= 0 && active) {
+                        if (dy > 0) {
+                            const int yy = wrapc(B.jy + kW - 1, A.Gy);
+#pragma unroll
+                            for (int d = 0; d < kW; ++d)
+                                W.v[p][kW - 1][d] = __ldg(A.grid + gaddr(A, W.zc[p], yy, wrapc(cx + d, A.Gx), c));
+                        } else {
+                            const int yy = B.jy;
+#pragma unroll
+                            for (int d = 0; d < kW; ++d)
+                                W.v[p][0][d] = __ldg(A.grid + gaddr(A, W.zc[p], yy, wrapc(cx + d, A.Gx), c));
+                        }
+                    }
+                }
+                cy = B.jy;
+            }
+            if (dx != 0) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    if (dx > 0) {
+#pragma unroll
+                        for (int b = 0; b < kW; ++b)
+#pragma unroll
+                            for (int d = 0; d < kW - 1; ++d) W.v[p][b][d] = W.v[p][b][d + 1];
+                    } else {
+#pragma unroll
+                        for (int b = 0; b < kW; ++b)
+#pragma unroll
+                            for (int d = kW - 1; d > 0; --d) W.v[p][b][d] = W.v[p][b][d - 1];
+                    }
+                    if (W.zc[p] >= 0 && active) {
+                        if (dx > 0) {
+                            const int xx = wrapc(B.jx + kW - 1, A.Gx);
+#pragma unroll
+                            for (int b = 0; b < kW; ++b)
+                                W.v[p][b][kW - 1] = __ldg(A.grid + gaddr(A, W.zc[p], wrapc(cy + b, A.Gy), xx, c));
+                        } else {
+                            const int xx = B.jx;
+#pragma unroll
+                            for (int b = 0; b < kW; ++b)
+                                W.v[p][b][0] = __ldg(A.grid + gaddr(A, W.zc[p], wrapc(cy + b, A.Gy), xx, c));
+                        }
+                    }
+                }
+                cx = B.jx;
+            }
+        }
+        cy = B.jy;
+        cx = B.jx;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int a = 0; a < (ND == 3 ? kW : 1); ++a) {
+        for (int p = 0; p < P; ++p) {
+            // z of this plane inside the box [jz, jz+3]
+            int rel = 0, zw = 0;
+            if (ND == 3) {
+                const int q = slice + p * S;                       // residue held by this plane
+                rel = (q - B.jz) & 3;
+                zw = wrapc(B.jz + rel, A.Gz);
+            }
+            if (W.zc[p] != zw) {
+                if (active) {
+#pragma unroll
+                    for (int b = 0; b < kW; ++b) {
+                        const int yy = wrapc(cy + b, A.Gy);
+#pragma unroll
+                        for (int d = 0; d < kW; ++d) W.v[p][b][d] = __ldg(A.grid + gaddr(A, zw, yy, wrapc(cx + d, A.Gx), c));
+                    }
+                }
+                W.zc[p] = zw;
+            }
+            const float wzp = (rel == 0) ? B.wz[0] : (rel == 1 ? B.wz[1] : (rel == 2 ? B.wz[2] : B.wz[3]));
+            float2 pa = make_float2(0.f, 0.f);
 #pragma unroll
             for (int b = 0; b < kW; ++b) {
-                const float2* row = gc + ((int64_t)iz[a] * A.Gy + iy[b]) * A.Gx;
-                const float wab = wz[a] * wy[b];
                 float2 r = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int d = 0; d < kW; ++d) {
-                    const float2 v = __ldg(row + ix[d]);
-                    r.x = fmaf(wx[d], v.x, r.x);
-                    r.y = fmaf(wx[d], v.y, r.y);
+                    r.x = fmaf(B.wx[d], W.v[p][b][d].x, r.x);
+                    r.y = fmaf(B.wx[d], W.v[p][b][d].y, r.y);
                 }
-                acc.x = fmaf(wab, r.x, acc.x);
-                acc.y = fmaf(wab, r.y, acc.y);
+                pa.x = fmaf(B.wy[b], r.x, pa.x);
+                pa.y = fmaf(B.wy[b], r.y, pa.y);
+            }
+            acc.x = fmaf(wzp, pa.x, acc.x);
+            acc.y = fmaf(wzp, pa.y, acc.y);
+        }
+        if (S > 1) {
+#pragma unroll
+            for (int o = 1; o < S; o <<= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
             }
         }
-        acc = cscale(acc, sw);
-        if (mode == OUT_USER) {
-            out[(int64_t)c * A.N + ps] = acc;
-        } else if (mode == OUT_RESID) {
-            out[(int64_t)c * A.N + s] = csub(acc, ysub[(int64_t)c * A.N + ps]);
-        } else {
-            out[(int64_t)c * A.N + s] = acc;
+        if (active && slice == 0) {
+            acc = cscale(acc, A.ws[s]);
+            if (mode == OUT_USER) {
+                out[(int64_t)c * A.N + A.perm[s]] = acc;
+            } else if (mode == OUT_RESID) {
+                out[(int64_t)c * A.N + s] = csub(acc, ysub[(int64_t)c * A.N + A.perm[s]]);
+            } else {
+                out[(int64_t)c * A.N + s] = acc;
+            }
         }
     }
 }
 
-// ------------------------------------------------------------------------------------------
-// spreading: one CTA per (work item, coil); the tile plus its high-side halo of W-1 points is
-// accumulated in shared memory, then added to the grid (wrapping modulo G).
-struct SpreadArgs {
-    GridArgs g;
-    float2* grid;
-    const float2* yin;      // user order [C][N] or sorted [C][N]
-    int sorted_in;
-    const WorkItem* items;
-    int tz, ty, tx;         // tile sizes
-    int ntz, nty, ntx;
-};
+__device__ __forceinline__ void red_add(float2* p, float2 v) {
+    if (v.x != 0.f || v.y != 0.f) atomicAdd(p, v);
+}
 
-template <int ND>
-__global__ void __launch_bounds__(256) spread_kernel(SpreadArgs S) {
-    extern __shared__ float2 reg[];
-    const WorkItem it = S.items[blockIdx.x];
-    const int c = blockIdx.y;
-    const int Rz = (ND == 3) ? S.tz + kW - 1 : 1, Ry = S.ty + kW - 1, Rx = S.tx + kW - 1;
-    const int R = Rz * Ry * Rx;
-    for (int e = threadIdx.x; e < R; e += blockDim.x) reg[e] = make_float2(0.f, 0.f);
-    int t = it.tile;
-    const int tcx = t % S.ntx;
-    t /= S.ntx;
-    const int tcy = t % S.nty;
-    const int tcz = t / S.nty;
-    const int oz = tcz * S.tz, oy = tcy * S.ty, ox = tcx * S.tx;
+template <int ND, int P>
+__global__ void __launch_bounds__(128) spread_kernel(GridArgs A, const float2* __restrict__ yin, int sorted_in) {
+    __shared__ float tab[kPhiTable + 1];
+    for (int i = threadIdx.x; i <= kPhiTable; i += blockDim.x) tab[i] = A.phi[i];
     __syncthreads();
-    const GridArgs& A = S.g;
-    for (int s = it.start + threadIdx.x; s < it.start + it.count; s += blockDim.x) {
-        int jz = 0, jy, jx;
-        float wz[kW] = {1.f, 0.f, 0.f, 0.f}, wy[kW], wx[kW];
-        if (ND == 3) kb_weights(A.gs[s * 3 + 0], A.az, jz, wz);
-        kb_weights(A.gs[s * 3 + 1], A.ay, jy, wy);
-        kb_weights(A.gs[s * 3 + 2], A.ax, jx, wx);
-        const int lz = (ND == 3) ? wrapi(jz, A.Gz) - oz : 0;
-        const int ly = wrapi(jy, A.Gy) - oy;
-        const int lx = wrapi(jx, A.Gx) - ox;
-        float2 v = S.sorted_in ? S.yin[(int64_t)c * A.N + s] : S.yin[(int64_t)c * A.N + A.perm[s]];
-        v = cscale(v, A.ws[s]);
+    constexpr int S = (ND == 3) ? 4 / P : 1;
+    const int lane = threadIdx.x & 31;
+    const int coil_l = lane / S, slice = lane % S;
+    const bool active = coil_l < A.gsize;
+    const int c = A.c0 + (active ? coil_l : 0);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t s0 = warp * A.chunk;
+    if (s0 >= A.N) return;
+    const int64_t s1 = min(A.N, s0 + A.chunk);
+    Win<P> W;
 #pragma unroll
-        for (int a = 0; a < (ND == 3 ? kW : 1); ++a) {
+    for (int p = 0; p < P; ++p) {
+        W.zc[p] = -1;
+#pragma unroll
+        for (int b = 0; b < kW; ++b)
+#pragma unroll
+            for (int d = 0; d < kW; ++d) W.v[p][b][d] = make_float2(0.f, 0.f);
+    }
+    int cy = -100, cx = -100;
+    auto flush_plane = [&](int p) {
+        if (W.zc[p] >= 0 && active) {
 #pragma unroll
             for (int b = 0; b < kW; ++b) {
-                const float wab = wz[a] * wy[b];
-                float2* row = reg + ((lz + a) * Ry + (ly + b)) * Rx + lx;
+                const int yy = wrapc(cy + b, A.Gy);
+#pragma unroll
+                for (int d = 0; d < kW; ++d) red_add(A.grid + gaddr(A, W.zc[p], yy, wrapc(cx + d, A.Gx), c), W.v[p][b][d]);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < kW; ++b)
+#pragma unroll
+            for (int d = 0; d < kW; ++d) W.v[p][b][d] = make_float2(0.f, 0.f);
+    };
+    for (int64_t s = s0; s < s1; ++s) {
+        SampleBox<ND> B;
+        sample_box<ND>(A, tab, s, lane, B);
+        const int dy = B.jy - cy, dx = B.jx - cx;
+        if (abs(dy) > 1 || abs(dx) > 1) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                flush_plane(p);
+                W.zc[p] = -1;
+            }
+        } else {
+            if (dy != 0) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    if (dy > 0) {
+                        if (W.zc[p] >= 0 && active) {
+                            const int yy = cy;   // leaving row 0
+#pragma unroll
+                            for (int d = 0; d < kW; ++d) red_add(A.grid + gaddr(A, W.zc[p], yy, wrapc(cx + d, A.Gx), c), W.v[p][0][d]);
+                        }
+#pragma unroll
+                        for (int b = 0; b < kW - 1; ++b)
+#pragma unroll
+                            for (int d = 0; d < kW; ++d) W.v[p][b][d] = W.v[p][b + 1][d];
+#pragma unroll
+                        for (int d = 0; d < kW; ++d) W.v[p][kW - 1][d] = make_float2(0.f, 0.f);
+                    } else {
+                        if (W.zc[p] >= 0 && active) {
+                            const int yy = wrapc(cy + kW - 1, A.Gy);   // leaving row 3
+#pragma unroll
+                            for (int d = 0; d < kW; ++d) red_add(A.grid + gaddr(A, W.zc[p], yy, wrapc(cx + d, A.Gx), c), W.v[p][kW - 1][d]);
+                        }
+#pragma unroll
+                        for (int b = kW - 1; b > 0; --b)
+#pragma unroll
+                            for (int d = 0; d < kW; ++d) W.v[p][b][d] = W.v[p][b - 1][d];
+#pragma unroll
+                        for (int d = 0; d < kW; ++d) W.v[p][0][d] = make_float2(0.f, 0.f);
+                    }
+                }
+                cy = B.jy;
+            }
+            if (dx != 0) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    if (dx > 0) {
+                        if (W.zc[p] >= 0 && active) {
+                            const int xx = cx;   // leaving column 0
+#pragma unroll
+                            for (int b = 0; b < kW; ++b) red_add(A.grid + gaddr(A, W.zc[p], wrapc(cy + b, A.Gy), xx, c), W.v[p][b][0]);
+                        }
+#pragma unroll
+                        for (int b = 0; b < kW; ++b)
+#pragma unroll
+                            for (int d = 0; d < kW - 1; ++d) W.v[p][b][d] = W.v[p][b][d + 1];
+#pragma unroll
+                        for (int b = 0; b < kW; ++b) W.v[p][b][kW - 1] = make_float2(0.f, 0.f);
+                    } else {
+                        if (W.zc[p] >= 0 && active) {
+                            const int xx = wrapc(cx + kW - 1, A.Gx);   // leaving column 3
+#pragma unroll
+                            for (int b = 0; b < kW; ++b) red_add(A.grid + gaddr(A, W.zc[p], wrapc(cy + b, A.Gy), xx, c), W.v[p][b][kW - 1]);
+                        }
+#pragma unroll
+                        for (int b = 0; b < kW; ++b)
+#pragma unroll
+                            for (int d = kW - 1; d > 0; --d) W.v[p][b][d] = W.v[p][b][d - 1];
+#pragma unroll
+                        for (int b = 0; b < kW; ++b) W.v[p][b][0] = make_float2(0.f, 0.f);
+                    }
+                }
+                cx = B.jx;
+            }
+        }
+        cy = B.jy;
+        cx = B.jx;
+        float2 v = make_float2(0.f, 0.f);
+        if (active) v = sorted_in ? yin[(int64_t)c * A.N + s] : yin[(int64_t)c * A.N + A.perm[s]];
+        v = cscale(v, A.ws[s]);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            int rel = 0, zw = 0;
+            if (ND == 3) {
+                const int q = slice + p * S;
+                rel = (q - B.jz) & 3;
+                zw = wrapc(B.jz + rel, A.Gz);
+            }
+            if (W.zc[p] != zw) {
+                flush_plane(p);
+                W.zc[p] = zw;
+            }
+            const float wzp = (rel == 0) ? B.wz[0] : (rel == 1 ? B.wz[1] : (rel == 2 ? B.wz[2] : B.wz[3]));
+            const float2 va = cscale(v, wzp);
+#pragma unroll
+            for (int b = 0; b < kW; ++b) {
+                const float2 vb = cscale(va, B.wy[b]);
 #pragma unroll
                 for (int d = 0; d < kW; ++d) {
-                    const float w = wab * wx[d];
-                    atomicAdd(&row[d].x, w * v.x);
-                    atomicAdd(&row[d].y, w * v.y);
+                    W.v[p][b][d].x = fmaf(B.wx[d], vb.x, W.v[p][b][d].x);
+                    W.v[p][b][d].y = fmaf(B.wx[d], vb.y, W.v[p][b][d].y);
                 }
             }
         }
     }
-    __syncthreads();
-    float2* gc = S.grid + (int64_t)c * A.G;
-    for (int e = threadIdx.x; e < R; e += blockDim.x) {
-        const float2 v = reg[e];
-        if (v.x == 0.f && v.y == 0.f) continue;
-        const int rx = e % Rx;
-        const int ry = (e / Rx) % Ry;
-        const int rz = e / (Rx * Ry);
-        const int gz = (ND == 3) ? wrapi(oz + rz, A.Gz) : 0;
-        const int gy = wrapi(oy + ry, A.Gy);
-        const int gx = wrapi(ox + rx, A.Gx);
-        atomicAdd(reinterpret_cast<float2*>(gc + ((int64_t)gz * A.Gy + gy) * A.Gx + gx), v);
-    }
-}
-
-static GridArgs make_grid_args(const cs_plan* p, int ncoils, const float2* grid) {
-    GridArgs A;
-    A.grid = grid;
-    A.G = p->G;
-    A.Gz = p->grid[0];
-    A.Gy = p->grid[1];
-    A.Gx = p->grid[2];
-    const float i0b = (float)(1.0 / std::cyl_bessel_i(0.0, (double)p->beta));
-    A.az = KbAxis{p->grid[0], p->beta, i0b};
-    A.ay = KbAxis{p->grid[1], p->beta, i0b};
-    A.ax = KbAxis{p->grid[2], p->beta, i0b};
-    A.gs = p->gsorted;
-    A.ws = p->wsorted;
-    A.perm = p->perm;
-    A.N = p->N;
-    A.ncoils = ncoils;
-    return A;
+#pragma unroll
+    for (int p = 0; p < P; ++p) flush_plane(p);
 }
 
 static float2* grid_buffer(const cs_plan* p) { return p->ndim == 3 ? p->bufA : p->bufB; }
 
-static cs_status launch_interp(const cs_plan* p, int ncoils, int mode, const float2* ysub, float2* out,
-                               cudaStream_t st) {
-    GridArgs A = make_grid_args(p, ncoils, grid_buffer(p));
-    const unsigned nb = (unsigned)((p->N + 255) / 256);
+static GridArgs make_grid_args(const cs_plan* p, int ncoils) {
+    GridArgs A;
+    A.grid = grid_buffer(p);
+    A.C = ncoils;
+    A.c0 = 0;
+    A.gsize = 0;
+    A.Gz = p->grid[0];
+    A.Gy = p->grid[1];
+    A.Gx = p->grid[2];
+    A.phi = p->phi;
+    A.gs = p->gsorted;
+    A.ws = p->wsorted;
+    A.perm = p->perm;
+    A.N = p->N;
+    A.chunk = p->interp_chunk;
+    return A;
+}
+
+// Launch one kernel per coil chunk: a chunk of g <= 8 coils uses 4 lanes per coil holding one
+// plane each (P = 1), g <= 16 two lanes with two planes, g <= 32 one lane with all 4 planes;
+// always one sample stream per warp.
+template <bool SPREAD>
+static cs_status launch_grid_op(const cs_plan* p, int ncoils, int mode, const float2* ysub, float2* out,
+                                const float2* yin, int sorted_in, cudaStream_t st) {
+    GridArgs A = make_grid_args(p, ncoils);
+    const int64_t warps = (p->N + A.chunk - 1) / A.chunk;
+    const unsigned nb = (unsigned)((warps * 32 + 127) / 128);
     if (nb == 0) return CS_OK;
-    if (p->ndim == 3) interp_kernel<3><<<nb, 256, 0, st>>>(A, mode, ysub, out);
-    else interp_kernel<2><<<nb, 256, 0, st>>>(A, mode, ysub, out);
-    CS_LAUNCH_CHECK();
+    const int cmax = SPREAD ? p->spread_coils : p->interp_coils;   // 8, 16 or 32 coils per warp
+    for (int c0 = 0; c0 < ncoils; c0 += cmax) {
+        const int g = std::min(cmax, ncoils - c0);
+        A.c0 = c0;
+        A.gsize = g;
+        int P = 4;
+        if (p->ndim == 3) P = (g <= 8) ? 1 : (g <= 16 ? 2 : 4);
+        if (p->ndim == 2) {
+            if (SPREAD) spread_kernel<2, 1><<<nb, 128, 0, st>>>(A, yin, sorted_in);
+            else interp_kernel<2, 1><<<nb, 128, 0, st>>>(A, mode, ysub, out);
+        } else if (P == 1) {
+            if (SPREAD) spread_kernel<3, 1><<<nb, 128, 0, st>>>(A, yin, sorted_in);
+            else interp_kernel<3, 1><<<nb, 128, 0, st>>>(A, mode, ysub, out);
+        } else if (P == 2) {
+            if (SPREAD) spread_kernel<3, 2><<<nb, 128, 0, st>>>(A, yin, sorted_in);
+            else interp_kernel<3, 2><<<nb, 128, 0, st>>>(A, mode, ysub, out);
+        } else {
+            if (SPREAD) spread_kernel<3, 4><<<nb, 128, 0, st>>>(A, yin, sorted_in);
+            else interp_kernel<3, 4><<<nb, 128, 0, st>>>(A, mode, ysub, out);
+        }
+        CS_LAUNCH_CHECK();
+    }
     return CS_OK;
 }
 
-// y (user order) = sqrt(w) interp(grid)
+// y (user order) = sqrt(w) interp(grid); with ysub: ktmp (sorted) = sqrt(w) interp(grid) - y
 cs_status nufft_interp(const cs_plan* p, int ncoils, float2* y, const float2* ysub, cudaStream_t st) {
-    if (ysub) return launch_interp(p, ncoils, OUT_RESID, ysub, p->ktmp, st);
-    return launch_interp(p, ncoils, OUT_USER, nullptr, y, st);
+    if (ysub) return launch_grid_op<false>(p, ncoils, OUT_RESID, ysub, p->ktmp, nullptr, 0, st);
+    return launch_grid_op<false>(p, ncoils, OUT_USER, nullptr, y, nullptr, 0, st);
 }
 
-// grid = spread(sqrt(w) y); y in user order (sorted_in = 0) or the sorted scratch (ktmp)
+// grid = spread(sqrt(w) y); y in user order (sorted_in = 0) or the sorted scratch ktmp
 cs_status nufft_spread(const cs_plan* p, int ncoils, const float2* y, int sorted_in, cudaStream_t st) {
     float2* grid = grid_buffer(p);
     CS_TRY_CUDA(cudaMemsetAsync(grid, 0, sizeof(float2) * (size_t)p->G * ncoils, st));
-    if (p->nitems == 0 || ncoils == 0) return CS_OK;
-    SpreadArgs S;
-    S.g = make_grid_args(p, ncoils, grid);
-    S.grid = grid;
-    S.yin = sorted_in ? p->ktmp : y;
-    S.sorted_in = sorted_in;
-    S.items = p->items;
-    S.tz = p->tile[0];
-    S.ty = p->tile[1];
-    S.tx = p->tile[2];
-    S.ntz = p->ntiles[0];
-    S.nty = p->ntiles[1];
-    S.ntx = p->ntiles[2];
-    const int Rz = p->ndim == 3 ? p->tile[0] + kW - 1 : 1;
-    const size_t sm = sizeof(float2) * (size_t)Rz * (p->tile[1] + kW - 1) * (p->tile[2] + kW - 1);
-    dim3 grd((unsigned)p->nitems, (unsigned)ncoils);
-    if (p->ndim == 3) {
-        CS_TRY_CUDA(cudaFuncSetAttribute(spread_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        spread_kernel<3><<<grd, 256, sm, st>>>(S);
-    } else {
-        CS_TRY_CUDA(cudaFuncSetAttribute(spread_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        spread_kernel<2><<<grd, 256, sm, st>>>(S);
-    }
-    CS_LAUNCH_CHECK();
-    return CS_OK;
+    if (ncoils == 0) return CS_OK;
+    return launch_grid_op<true>(p, ncoils, 0, nullptr, nullptr, sorted_in ? p->ktmp : y, sorted_in, st);
 }
 
 // normal operator on the grid: ktmp = w^1/2 interp(grid) (sorted), then grid = spread(w^1/2 ktmp)
 cs_status nufft_interp_spread(const cs_plan* p, int ncoils, cudaStream_t st) {
-    CS_PROPAGATE(launch_interp(p, ncoils, OUT_SORTED, nullptr, p->ktmp, st));
+    CS_PROPAGATE(launch_grid_op<false>(p, ncoils, OUT_SORTED, nullptr, p->ktmp, nullptr, 0, st));
     return nufft_spread(p, ncoils, nullptr, 1, st);
 }
 

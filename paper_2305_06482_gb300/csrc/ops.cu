@@ -58,6 +58,7 @@ static void plan_free(cs_plan* p) {
     cudaFree(p->j0);
     cudaFree(p->tile_off);
     cudaFree(p->items);
+    cudaFree(p->phi);
     cudaFree(p->bufA);
     cudaFree(p->bufB);
     cudaFree(p->ktmp);
@@ -144,6 +145,20 @@ static cs_status plan_build(cs_plan* p, const cs_geom* g, cudaStream_t st) {
     }
     p->ntiles_total = (int64_t)p->ntiles[0] * p->ntiles[1] * p->ntiles[2];
     p->spread_chunk = 8192;
+    p->interp_chunk = 64;
+    {
+        // phi(u) = I0(beta sqrt(1 - (u/2)^2)) / I0(beta) on [0, 2], 2049 points
+        const int nt = 2048;
+        std::vector<float> tab(nt + 1);
+        const double i0b = std::cyl_bessel_i(0.0, beta);
+        for (int i = 0; i <= nt; ++i) {
+            const double u = 2.0 * i / nt;
+            const double t = 1.0 - 0.25 * u * u;
+            tab[i] = (float)(std::cyl_bessel_i(0.0, beta * std::sqrt(t > 0 ? t : 0.0)) / i0b);
+        }
+        CS_TRY_CUDA(cudaMalloc(&p->phi, sizeof(float) * (nt + 1)));
+        CS_TRY_CUDA(cudaMemcpy(p->phi, tab.data(), sizeof(float) * (nt + 1), cudaMemcpyHostToDevice));
+    }
     CS_TRY_CUDA(cudaMalloc(&p->gsorted, sizeof(float) * 3 * p->N));
     CS_TRY_CUDA(cudaMalloc(&p->wsorted, sizeof(float) * p->N));
     CS_TRY_CUDA(cudaMalloc(&p->perm, sizeof(int32_t) * p->N));

@@ -21,7 +21,9 @@ Recipes (shapes follow the paper's workloads and the benchmark configurations):
   density (1 - |ky|/(n/2))^2 (2D Cartesian, R=6).
 * cones: a spiral-cones stand-in. Interleave i has axis polar angle
   arccos(1 - (2i+1)/n_int) and azimuth i*pi*(3-sqrt 5); readout point p has radius
-  0.5 p/(n_read-1) and azimuth offset 2 pi 4 s^2 (s = p/(n_read-1)).
+  0.5 p/(n_read-1) and azimuth offset 2 pi t s^2 (s = p/(n_read-1)) with t = 0.25 turns, so
+  consecutive samples along a readout stay below one pixel (1/FOV) apart, as on a scanner
+  readout; a faster twist would undersample the readout itself.
 * dcf: analytic radial density compensation w = D 4 pi max(|f|, kmin)^2 / (n_int
   dk^-1), i.e. the inverse of the sample density of the cones stand-in, so that A^H A is
   close to the identity on the sampled ball.
@@ -179,7 +181,7 @@ def line_mask(n, R=6.0, centre_lines=24, seed=2):
     return mask
 
 
-def cones_trajectory(n_int, n_read=512):
+def cones_trajectory(n_int, n_read=512, turns=0.25):
     """Spiral-cones stand-in, float32 [n_int*n_read, 3] in cycles/pixel, axis order (z, y, x)."""
     i = np.arange(n_int, dtype=np.float64)[:, None]
     p = np.arange(n_read, dtype=np.float64)[None, :]
@@ -187,7 +189,7 @@ def cones_trajectory(n_int, n_read=512):
     phi0 = i * math.pi * (3.0 - math.sqrt(5.0))
     s = p / (n_read - 1)
     kr = 0.5 * s
-    phi = phi0 + 2 * math.pi * 4.0 * s ** 2
+    phi = phi0 + 2 * math.pi * turns * s ** 2
     kx = kr * np.sin(theta) * np.cos(phi)
     ky = kr * np.sin(theta) * np.sin(phi)
     kz = kr * np.cos(theta) * np.ones_like(phi)
