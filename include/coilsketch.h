@@ -53,6 +53,18 @@ const char* cs_last_error(void);
 /* Library version string. */
 const char* cs_version(void);
 
+/* Number of kernels this library has launched in the process so far (all devices). */
+long long cs_launch_count(void);
+
+/* Optional per-stage timing: while enabled, CUDA events are recorded on the launching stream
+ * around every launch of the stages below; cs_profile_read synchronises on those events and
+ * returns the summed device time and the launch count of one stage.  cs_profile resets the
+ * totals (and turns recording on or off). */
+enum { CS_STAGE_SPREAD = 0, CS_STAGE_INTERP = 1, CS_STAGE_FFT_PLAIN = 2, CS_STAGE_EXPAND = 3,
+       CS_STAGE_REDUCE = 4 };
+cs_status cs_profile(int enable);
+cs_status cs_profile_read(int stage, double* total_ms, long long* launches);
+
 /* ------------------------------------------------------------------------------------------
  * Plans.  A plan fixes the image geometry and the sampling operator (Sec. 2.1):
  *   Cartesian:      F~ = U F~_u  - centred orthonormal DFT then the undersampling U, given as

@@ -65,8 +65,9 @@ EXPORTED = [
     "cs_last_error", "cs_version", "cs_plan_create", "cs_plan_destroy", "cs_plan_binning", "sense_fwd",
     "sense_adj", "sense_grad", "sketched_normal_apply", "coil_pca", "coil_rotate", "sketch_draw",
     "cs_philox4x32_10", "sketched_maps", "recon_solve", "wavelet_fwd", "wavelet_inv", "soft_threshold",
-    "cs_hermitian_eig_host",
+    "cs_hermitian_eig_host", "cs_launch_count", "cs_profile", "cs_profile_read",
 ]
+STAGES = {"spread": 0, "interp": 1, "fft_plain": 2, "expand": 3, "reduce": 4}
 
 _lib = None
 
@@ -93,6 +94,8 @@ def lib():
             "recon_solve": ([vp, vp, vp, vp, vp, vp], i),
             "wavelet_fwd": ([vp, i, vp, i, vp, vp], i), "wavelet_inv": ([vp, i, vp, i, vp, vp], i),
             "soft_threshold": ([vp, i64, f, vp], i), "cs_hermitian_eig_host": ([vp, i, vp, vp], i),
+            "cs_launch_count": ([], ctypes.c_longlong), "cs_profile": ([i], i),
+            "cs_profile_read": ([i, vp, vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -295,6 +298,24 @@ def hermitian_eig_host(A):
     _check(lib().cs_hermitian_eig_host(A.ctypes.data_as(ctypes.c_void_p), n, V.ctypes.data_as(ctypes.c_void_p),
                                        ev.ctypes.data_as(ctypes.c_void_p)))
     return V, ev
+
+
+def launch_count():
+    """Kernels launched by the library so far in this process."""
+    return int(lib().cs_launch_count())
+
+
+def profile(enable=True):
+    """Reset the per-stage timers and turn CUDA-event recording on or off."""
+    _check(lib().cs_profile(int(enable)))
+
+
+def profile_read(stage):
+    """(total device ms, launches) of a stage ('spread', 'interp', 'fft_plain', 'expand', 'reduce')."""
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    _check(lib().cs_profile_read(STAGES[stage], ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 @dataclass

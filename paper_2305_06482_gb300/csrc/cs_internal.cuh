@@ -26,7 +26,19 @@ void clear_error();
         }                                                                                     \
     } while (0)
 
-#define CS_LAUNCH_CHECK() CS_TRY_CUDA(cudaGetLastError())
+// every kernel launch of the library is followed by CS_LAUNCH_CHECK, which also counts it
+void count_launch();
+#define CS_LAUNCH_CHECK()                                                                     \
+    do {                                                                                      \
+        ::cs::count_launch();                                                                 \
+        CS_TRY_CUDA(cudaGetLastError());                                                      \
+    } while (0)
+
+// optional per-stage timing with CUDA events (enabled by cs_profile)
+enum { ST_SPREAD = 0, ST_INTERP = 1, ST_FFT_PLAIN = 2, ST_EXPAND = 3, ST_REDUCE = 4, ST_COUNT = 5 };
+bool profiling();
+void prof_begin(int stage, cudaStream_t st);
+void prof_end(int stage, cudaStream_t st);
 
 #define CS_REQUIRE(cond, code, ...)                                                           \
     do {                                                                                      \

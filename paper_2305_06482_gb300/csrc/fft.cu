@@ -453,8 +453,11 @@ static cs_status launch_pass(const PassArgs& A, cudaStream_t st) {
     else blocks = A.outer * ((A.inner + kLines - 1) / kLines);
     if (blocks == 0) return CS_OK;
     CS_REQUIRE(blocks < (int64_t)1 << 31, CS_ERR_UNSUPPORTED_SIZE, "pass grid too large");
+    const int stage = (MODE == EXPAND_X) ? ST_EXPAND : (MODE == REDUCE_X ? ST_REDUCE : ST_FFT_PLAIN);
+    prof_begin(stage, st);
     fft_pass_kernel<MODE><<<(unsigned)blocks, kPassThreads, sm, st>>>(A);
     CS_LAUNCH_CHECK();
+    prof_end(stage, st);
     return CS_OK;
 }
 

@@ -631,6 +631,7 @@ static cs_status launch_grid_op(const cs_plan* p, int ncoils, int mode, const fl
         A.gsize = g;
         int P = 4;
         if (p->ndim == 3) P = (g <= 8) ? 1 : (g <= 16 ? 2 : 4);
+        prof_begin(SPREAD ? ST_SPREAD : ST_INTERP, st);
         if (p->ndim == 2) {
             if (SPREAD) spread_kernel<2, 1><<<nb, 128, 0, st>>>(A, yin, sorted_in);
             else interp_kernel<2, 1><<<nb, 128, 0, st>>>(A, mode, ysub, out);
@@ -645,6 +646,7 @@ static cs_status launch_grid_op(const cs_plan* p, int ncoils, int mode, const fl
             else interp_kernel<3, 4><<<nb, 128, 0, st>>>(A, mode, ysub, out);
         }
         CS_LAUNCH_CHECK();
+        prof_end(SPREAD ? ST_SPREAD : ST_INTERP, st);
     }
     return CS_OK;
 }

@@ -7,6 +7,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
+#include <mutex>
 
 #include "cs_internal.cuh"
 
@@ -21,6 +23,65 @@ void set_error(const char* fmt, ...) {
     va_end(ap);
 }
 void clear_error() { g_err[0] = 0; }
+
+// ---- launch counter and stage profiler ----
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+struct ProfRec {
+    int stage;
+    cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<cudaEvent_t> g_ev_pool;
+static std::vector<ProfRec> g_prof_recs;
+static ProfRec g_open[ST_COUNT];
+static double g_prof_ms[ST_COUNT];
+static long long g_prof_n[ST_COUNT];
+
+bool profiling() { return g_prof_on; }
+
+static cudaEvent_t ev_get() {
+    if (!g_ev_pool.empty()) {
+        cudaEvent_t e = g_ev_pool.back();
+        g_ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(int stage, cudaStream_t st) {
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_open[stage].stage = stage;
+    g_open[stage].a = ev_get();
+    cudaEventRecord(g_open[stage].a, st);
+}
+
+void prof_end(int stage, cudaStream_t st) {
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfRec r = g_open[stage];
+    r.b = ev_get();
+    cudaEventRecord(r.b, st);
+    g_prof_recs.push_back(r);
+}
+
+static void prof_drain() {
+    for (ProfRec& r : g_prof_recs) {
+        cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        g_prof_ms[r.stage] += ms;
+        g_prof_n[r.stage] += 1;
+        g_ev_pool.push_back(r.a);
+        g_ev_pool.push_back(r.b);
+    }
+    g_prof_recs.clear();
+}
 
 // Continuous Fourier transform of the width-W Kaiser-Bessel kernel phi(u) = I0(beta sqrt(1 -
 // (2u/W)^2)) / I0(beta): W sinh(z)/z / I0(beta), z = sqrt(beta^2 - (pi W nu)^2) (sin past zero).
@@ -183,6 +244,30 @@ using namespace cs;
 extern "C" {
 
 const char* cs_last_error(void) { return g_err; }
+
+long long cs_launch_count(void) { return g_launches.load(); }
+
+cs_status cs_profile(int enable) {
+    clear_error();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_drain();
+    for (int i = 0; i < ST_COUNT; ++i) {
+        g_prof_ms[i] = 0;
+        g_prof_n[i] = 0;
+    }
+    g_prof_on = enable != 0;
+    return CS_OK;
+}
+
+cs_status cs_profile_read(int stage, double* total_ms, long long* launches) {
+    clear_error();
+    CS_REQUIRE(stage >= 0 && stage < ST_COUNT && total_ms && launches, CS_ERR_INVALID_ARG, "bad profile query");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    prof_drain();
+    *total_ms = g_prof_ms[stage];
+    *launches = g_prof_n[stage];
+    return CS_OK;
+}
 const char* cs_version(void) { return "coilsketch-gb300 0.1 (sm_103a)"; }
 
 cs_status cs_plan_create(const cs_geom* g, void* stream, cs_plan** out) {

@@ -35,7 +35,7 @@ import math
 import numpy as np
 
 __all__ = [
-    "phantom", "coil_maps", "poisson_disc_mask", "line_mask", "cones_trajectory",
+    "phantom", "phantom_torch", "coil_maps", "coil_maps_torch", "poisson_disc_mask", "line_mask", "cones_trajectory",
     "cones_dcf", "complex_noise", "random_complex", "slice_sizes", "CONFIGS",
 ]
 
@@ -44,34 +44,43 @@ def _rng(seed):
     return np.random.default_rng(seed)
 
 
-def phantom(shape, seed=1, n_obj=12, n_holes=3):
-    """Random-ellipse (2D) or random-ellipsoid (3D) phantom, complex128, max|x| = 1."""
-    shape = tuple(int(s) for s in shape)
+def _phantom_params(shape, seed, n_obj, n_holes):
     nd = len(shape)
     rng = _rng(seed)
-    # normalised coordinates in [-1, 1) per axis, axis order (z, y, x) / (y, x)
-    grids = np.meshgrid(*[(np.arange(n) - n / 2) / (n / 2) for n in shape], indexing="ij")
-    coords = np.stack(grids, axis=-1)  # [..., nd]
-    mag = np.zeros(shape)
+    objs = []
     for k in range(n_obj):
         centre = rng.uniform(-0.8, 0.8, size=nd)
         semi = rng.uniform(0.05, 0.4, size=nd) * 2.0  # FOV spans 2 in these units
-        # random rotation (QR of a Gaussian matrix)
         q, r = np.linalg.qr(rng.standard_normal((nd, nd)))
         q = q * np.sign(np.diag(r))
         amp = rng.uniform(0.1, 1.0)
         if k >= n_obj - n_holes:
             amp = -amp
+        objs.append((centre, semi, q, amp))
+    rng_m = _rng(seed + 1000)
+    modes = []
+    for m in np.stack(np.meshgrid(*([range(-2, 3)] * nd), indexing="ij"), -1).reshape(-1, nd):
+        a = rng_m.standard_normal() + 1j * rng_m.standard_normal()
+        modes.append((m, a))
+    return objs, modes
+
+
+def phantom(shape, seed=1, n_obj=12, n_holes=3):
+    """Random-ellipse (2D) or random-ellipsoid (3D) phantom, complex128, max|x| = 1."""
+    shape = tuple(int(s) for s in shape)
+    nd = len(shape)
+    objs, modes = _phantom_params(shape, seed, n_obj, n_holes)
+    # normalised coordinates in [-1, 1) per axis, axis order (z, y, x) / (y, x)
+    grids = np.meshgrid(*[(np.arange(n) - n / 2) / (n / 2) for n in shape], indexing="ij")
+    coords = np.stack(grids, axis=-1)  # [..., nd]
+    mag = np.zeros(shape)
+    for centre, semi, q, amp in objs:
         rel = (coords - centre) @ q
         inside = np.sum((rel / semi) ** 2, axis=-1) <= 1.0
         mag = mag + amp * inside
     mag = np.abs(mag)
-    # smooth random phase from low-order Fourier modes
     phase = np.zeros(shape)
-    rng_m = _rng(seed + 1000)
-    rng_lists = [range(-2, 3)] * nd
-    for m in np.stack(np.meshgrid(*rng_lists, indexing="ij"), -1).reshape(-1, nd):
-        a = rng_m.standard_normal() + 1j * rng_m.standard_normal()
+    for m, a in modes:
         arg = sum(m[i] * grids[i] * 0.5 for i in range(nd))  # grids in [-1,1): r/n = g/2
         phase = phase + np.real(a * np.exp(2j * np.pi * arg))
     phase = phase * (math.pi / 2) / max(np.abs(phase).max(), 1e-30)
@@ -80,32 +89,77 @@ def phantom(shape, seed=1, n_obj=12, n_holes=3):
     return x.astype(np.complex128)
 
 
+def phantom_torch(shape, seed=1, device="cuda", n_obj=12, n_holes=3):
+    """phantom() evaluated with torch on a device in float32/complex64 (large volumes)."""
+    import torch
+    shape = tuple(int(s) for s in shape)
+    nd = len(shape)
+    objs, modes = _phantom_params(shape, seed, n_obj, n_holes)
+    axes = [(torch.arange(n, device=device, dtype=torch.float32) - n / 2) / (n / 2) for n in shape]
+    grids = torch.meshgrid(*axes, indexing="ij")
+    mag = torch.zeros(shape, device=device)
+    for centre, semi, q, amp in objs:
+        acc = torch.zeros(shape, device=device)
+        for j in range(nd):
+            relj = sum((grids[i] - float(centre[i])) * float(q[i, j]) for i in range(nd))
+            acc += (relj / float(semi[j])) ** 2
+        mag += float(amp) * (acc <= 1.0).float()
+    mag = mag.abs()
+    phase = torch.zeros(shape, device=device)
+    for m, a in modes:
+        arg = sum(float(m[i]) * grids[i] * 0.5 for i in range(nd))
+        phase += float(a.real) * torch.cos(2 * math.pi * arg) - float(a.imag) * torch.sin(2 * math.pi * arg)
+    phase = phase * (math.pi / 2) / phase.abs().max().clamp_min(1e-30)
+    x = torch.polar(mag, phase)
+    return (x / x.abs().max()).to(torch.complex64)
+
+
+def _coil_centres(nd, nc):
+    radius = 0.75 * 0.5
+    out = []
+    for c in range(nc):
+        if nd == 2:
+            ang = 2 * math.pi * c / nc
+            out.append((radius * math.sin(ang), radius * math.cos(ang)))
+        else:
+            per_ring = 8
+            n_rings = max(1, nc // per_ring)
+            ring = min(c // per_ring, n_rings - 1)
+            k = c % per_ring
+            ang = 2 * math.pi * k / per_ring + (math.pi / per_ring) * (ring % 2)
+            pz = ((ring + 0.5) / n_rings - 0.5) * 0.8
+            out.append((pz, radius * math.sin(ang), radius * math.cos(ang)))
+    return out
+
+
 def coil_maps(shape, nc, width=0.35):
     """Gaussian-profile coil sensitivities on a ring, RSS-normalised. complex128 [nc, *shape]."""
     shape = tuple(int(s) for s in shape)
     nd = len(shape)
     grids = np.meshgrid(*[(np.arange(n) - n / 2) / n for n in shape], indexing="ij")  # FOV units
     maps = np.empty((nc,) + shape, dtype=np.complex128)
-    radius = 0.75 * 0.5
-    if nd == 2:
-        for c in range(nc):
-            ang = 2 * math.pi * c / nc
-            py, px = radius * math.sin(ang), radius * math.cos(ang)
-            d2 = (grids[0] - py) ** 2 + (grids[1] - px) ** 2
-            maps[c] = np.exp(-d2 / (2 * width ** 2)) * np.exp(1j * 2 * math.pi * c / nc)
-    else:
-        per_ring = 8
-        n_rings = max(1, nc // per_ring)
-        for c in range(nc):
-            ring = min(c // per_ring, n_rings - 1)
-            k = c % per_ring
-            ang = 2 * math.pi * k / per_ring + (math.pi / per_ring) * (ring % 2)
-            pz = ((ring + 0.5) / n_rings - 0.5) * 0.8
-            py, px = radius * math.sin(ang), radius * math.cos(ang)
-            d2 = (grids[0] - pz) ** 2 + (grids[1] - py) ** 2 + (grids[2] - px) ** 2
-            maps[c] = np.exp(-d2 / (2 * width ** 2)) * np.exp(1j * 2 * math.pi * c / nc)
+    for c, p in enumerate(_coil_centres(nd, nc)):
+        d2 = sum((grids[i] - p[i]) ** 2 for i in range(nd))
+        maps[c] = np.exp(-d2 / (2 * width ** 2)) * np.exp(1j * 2 * math.pi * c / nc)
     rss = np.sqrt(np.sum(np.abs(maps) ** 2, axis=0))
     return maps / rss
+
+
+def coil_maps_torch(shape, nc, width=0.35, device="cuda"):
+    """coil_maps() evaluated with torch on a device, complex64 [nc, *shape]."""
+    import torch
+    shape = tuple(int(s) for s in shape)
+    nd = len(shape)
+    axes = [(torch.arange(n, device=device, dtype=torch.float32) - n / 2) / n for n in shape]
+    grids = torch.meshgrid(*axes, indexing="ij")
+    maps = torch.empty((nc,) + shape, dtype=torch.complex64, device=device)
+    rss = torch.zeros(shape, device=device)
+    for c, p in enumerate(_coil_centres(nd, nc)):
+        d2 = sum((grids[i] - float(p[i])) ** 2 for i in range(nd))
+        mag = torch.exp(-d2 / (2 * width ** 2))
+        maps[c] = torch.polar(mag, torch.full_like(mag, 2 * math.pi * c / nc))
+        rss += mag * mag
+    return maps / rss.sqrt().unsqueeze(0)
 
 
 def _disc_sample(n, r_of, centre, rng):

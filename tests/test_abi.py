@@ -23,13 +23,14 @@ def cs():
 def _declared():
     src = open(os.path.join(ROOT, "include", "coilsketch.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:const\s+)?(?:[a-z_0-9]+\s+)+\*?\s*([a-z_0-9]+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
 def test_every_declared_symbol_is_exported(cs):
     names = _declared()
     assert "recon_solve" in names and "sense_fwd" in names and "coil_pca" in names
+    assert "cs_launch_count" in names and "cs_hermitian_eig_host" in names
     L = cs.lib()
     for n in names:
         assert hasattr(L, n), n
