@@ -141,6 +141,20 @@ cs_status sketched_normal_apply(const cs_plan* plan, const float* v, const float
  * ---------------------------------------------------------------------------------------- */
 cs_status coil_pca(const float* y, int C, int64_t N, float* U, double* eig, void* stream);
 
+/* coil_pca_noalloc: the same computation as coil_pca for callers that cannot allocate device
+ * memory while they run - for example code whose device memory is entirely reserved up front
+ * by another allocator, or a service that must not grow its footprint after start-up.  It calls
+ * no cudaMalloc/cudaFree and no allocating library routine: its covariance scratch is a static
+ * device array of 64 KiB (complex128, at most 64 coils) that every GPU loading the library holds
+ * until the process exits.  The paper has no counterpart; this is a deployment variant.
+ *   y [C][N] complex64, U [C][C] complex64, eig [C] float64 - device buffers owned by the caller.
+ *   C > 64 is rejected with CS_ERR_UNSUPPORTED_SIZE before anything is launched.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All calls share the
+ * one array and clear it on their stream before use, so calls that overlap on the GPU (other
+ * streams, other threads) race: serialise them. */
+cs_status coil_pca_noalloc(const float* y, int C, int64_t N, float* U, double* eig, void* stream);
+
 /* coil_rotate: out[k][l] = sum_c conj(U[c][k]) in[c][l] for k < C_out (c' = U^H c, y' = U^H y),
  * in [C][L], out [C_out][L] complex64 (out must not alias in). */
 cs_status coil_rotate(const float* U, const float* in, int C, int C_out, int64_t L, float* out,

@@ -65,7 +65,7 @@ EXPORTED = [
     "cs_last_error", "cs_version", "cs_plan_create", "cs_plan_destroy", "cs_plan_binning", "sense_fwd",
     "sense_adj", "sense_grad", "sketched_normal_apply", "coil_pca", "coil_rotate", "sketch_draw",
     "cs_philox4x32_10", "sketched_maps", "recon_solve", "wavelet_fwd", "wavelet_inv", "soft_threshold",
-    "cs_hermitian_eig_host", "cs_launch_count", "cs_profile", "cs_profile_read",
+    "cs_hermitian_eig_host", "cs_launch_count", "cs_profile", "cs_profile_read", "coil_pca_noalloc",
 ]
 STAGES = {"spread": 0, "interp": 1, "fft_plain": 2, "expand": 3, "reduce": 4}
 
@@ -95,7 +95,7 @@ def lib():
             "wavelet_fwd": ([vp, i, vp, i, vp, vp], i), "wavelet_inv": ([vp, i, vp, i, vp, vp], i),
             "soft_threshold": ([vp, i64, f, vp], i), "cs_hermitian_eig_host": ([vp, i, vp, vp], i),
             "cs_launch_count": ([], ctypes.c_longlong), "cs_profile": ([i], i),
-            "cs_profile_read": ([i, vp, vp], i),
+            "cs_profile_read": ([i, vp, vp], i), "coil_pca_noalloc": ([vp, i, i64, vp, vp, vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -233,6 +233,18 @@ def coil_pca(y, stream=None):
     U = torch.empty((C, C), dtype=torch.complex64, device=y.device)
     eig = torch.empty(C, dtype=torch.float64, device=y.device)
     _check(lib().coil_pca(_ptr(y), C, N, _ptr(U), _ptr(eig), _stream(stream)))
+    return U, eig
+
+
+def coil_pca_noalloc(y, U=None, eig=None, stream=None):
+    """coil_pca without any device allocation inside the library (static 64 KiB scratch,
+    at most 64 coils; concurrent calls race).  U and eig may be preallocated by the caller."""
+    C, N = y.shape
+    if U is None:
+        U = torch.empty((C, C), dtype=torch.complex64, device=y.device)
+    if eig is None:
+        eig = torch.empty(C, dtype=torch.float64, device=y.device)
+    _check(lib().coil_pca_noalloc(_ptr(y), C, N, _ptr(U), _ptr(eig), _stream(stream)))
     return U, eig
 
 

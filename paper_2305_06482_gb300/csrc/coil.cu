@@ -5,6 +5,7 @@
 //   sketched_maps  c^_{V+s} = sum_j S~_S[s][j] c'_{V+j}   (Eq. 8, random block only)
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 
 #include "cs_internal.cuh"
 
@@ -493,11 +494,51 @@ cs_status sketched_maps_impl(const float* S, const float2* mrot, int64_t D, int 
     return CS_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// Statically allocated scratch for coil_pca_noalloc: the FP64 coil covariance (complex128 C x C)
+// of at most kNoAllocMaxCoils coils, 64 KiB, held by every device that loads the library.
+constexpr int kNoAllocMaxCoils = 64;
+static __device__ __align__(256) double g_pca_scratch[2 * kNoAllocMaxCoils * kNoAllocMaxCoils];
+
+// Device address of g_pca_scratch for the current device.  The name g_pca_scratch in host code
+// is only a host-side stand-in, so the address is looked up once per device with that device
+// current and cached.
+static cs_status pca_scratch_address(double** out) {
+    static std::mutex mu;
+    static double* addr[128] = {nullptr};
+    int dev = 0;
+    CS_TRY_CUDA(cudaGetDevice(&dev));
+    CS_REQUIRE(dev >= 0 && dev < 128, CS_ERR_INVALID_ARG, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_pca_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            set_error("coil_pca_noalloc: cudaGetSymbolAddress failed on device %d: %s", dev, cudaGetErrorString(e));
+            return CS_ERR_CUDA;
+        }
+        addr[dev] = (double*)p;
+    }
+    *out = addr[dev];
+    return CS_OK;
+}
+
 }  // namespace cs
 
 using namespace cs;
 
 extern "C" {
+
+cs_status coil_pca_noalloc(const float* y, int C, int64_t N, float* U, double* eig, void* stream) {
+    clear_error();
+    CS_REQUIRE(y && U && eig && N >= 1, CS_ERR_INVALID_ARG, "bad coil_pca_noalloc arguments");
+    CS_REQUIRE(C >= 1 && C <= kNoAllocMaxCoils, CS_ERR_UNSUPPORTED_SIZE,
+               "coil_pca_noalloc supports at most %d coils (got %d); use coil_pca", kNoAllocMaxCoils, C);
+    double* R = nullptr;
+    CS_PROPAGATE(pca_scratch_address(&R));
+    // coil_pca_impl clears R on `stream` before accumulating into it
+    return coil_pca_impl((const float2*)y, C, N, (float2*)U, eig, R, (cudaStream_t)stream);
+}
 
 cs_status cs_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
     clear_error();
