@@ -244,11 +244,13 @@ def run_native(args, w, rank, world, local_rank):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("cs_timed")
     e0.record(stream)
     x_last = None
     for _ in range(args.steps):
         x_last, _ = cs.recon_solve(plan, y, maps, w["lam"], cs.REG_L1_WAVELET, params_t, wavelet_levels=w["levels"])
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     launches = cs.launch_count() - launches0
     ms_total = e0.elapsed_time(e1)

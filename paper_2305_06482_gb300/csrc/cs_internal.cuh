@@ -131,8 +131,9 @@ struct cs_plan {
     int spread_chunk = 0;         // samples per spreading work item
     int interp_chunk = 0;         // consecutive sorted samples per warp (interp and spread)
     int interp_coils = 16;        // coils per warp in interpolation (8, 16 or 32)
-    int spread_coils = 16;        // coils per warp in spreading (8 or 16)
+    int spread_coils = 8;         // coils per warp in spreading (8 or 16)
     float* phi = nullptr;         // KB kernel table [2049] on [0, 2]
+    float* rec = nullptr;         // [N][16] per-sample gridding records (sorted order)
 
     // workspace (per coil up to max_coils)
     float2* bufA = nullptr;       // grid-sized per coil   [max_coils][G] (also the first-pass buffer)
@@ -151,6 +152,7 @@ cs_status fft_to_image(const cs_plan* p, const float2* maps_v, int V, const floa
 
 // NUFFT binning / interpolation / spreading (nufft.cu)
 cs_status nufft_bin(cs_plan* p, const float* traj, const float* dcf, cudaStream_t st);
+cs_status nufft_records(cs_plan* p, cudaStream_t st);
 cs_status nufft_interp(const cs_plan* p, int ncoils, float2* y, const float2* ysub, cudaStream_t st);
 cs_status nufft_spread(const cs_plan* p, int ncoils, const float2* y, int sorted_in, cudaStream_t st);
 cs_status nufft_interp_spread(const cs_plan* p, int ncoils, cudaStream_t st);

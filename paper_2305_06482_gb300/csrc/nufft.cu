@@ -228,10 +228,7 @@ struct GridArgs {
     int C;                 // interleave stride = coils of the operator call
     int c0, gsize;         // coil chunk handled by this launch
     int Gz, Gy, Gx;
-    const float* phi;      // [kPhiTable + 1] phi(u) for u = 2 i / kPhiTable
-    const float* gs;       // [N][3]
-    const float* ws;       // [N]
-    const int32_t* perm;
+    const float* rec;      // [N][16] per-sample records (weights, box, sqrt(w), user index)
     int64_t N;
     int chunk;             // samples per warp
 };
@@ -253,36 +250,63 @@ template <int ND>
 struct SampleBox {
     int jz, jy, jx;        // wrapped box starts
     float wz[kW], wy[kW], wx[kW];
+    float sw;              // sqrt(w)
+    int perm;              // user index
 };
 
-// lanes 0..4*ND-1 evaluate one weight each (axis = lane / 4, offset = lane % 4); all lanes get
-// every weight by shuffles.  The sign (-1)^(j + G/2) of the centred DFT is folded in.
-template <int ND>
-__device__ __forceinline__ void sample_box(const GridArgs& A, const float* __restrict__ tab, int64_t s, int lane,
-                                           SampleBox<ND>& B) {
-    const int ax = lane >> 2, off = lane & 3;
-    // axis slot 0 = z (3D only), 1 = y, 2 = x
-    const int axis = (ND == 3) ? ax : ax + 1;
-    float w = 0.f;
-    const float gz = (ND == 3) ? A.gs[s * 3 + 0] : 0.f;
-    const float gy = A.gs[s * 3 + 1], gx = A.gs[s * 3 + 2];
-    if (lane < 4 * ND) {
-        const float g = (axis == 0) ? gz : (axis == 1 ? gy : gx);
-        const int G = (axis == 0) ? A.Gz : (axis == 1 ? A.Gy : A.Gx);
-        const int j = (int)floorf(g) - (kW / 2 - 1) + off;
-        w = phi_lookup(tab, g - (float)j);
-        if ((j + G / 2) & 1) w = -w;
+// Per-sample record of 16 words, computed once per plan: the 12 kernel weights (z, y, x, with
+// the (-1)^(j + G/2) sign of the centred DFT folded in), the wrapped box start packed as
+// 10 + 10 + 10 bits, sqrt(w) and the user index of the sample.
+constexpr int kRec = 16;
+
+__global__ void sample_record_kernel(const float* __restrict__ gs, const float* __restrict__ ws,
+                                     const int32_t* __restrict__ perm, const float* __restrict__ tab_g, int64_t N,
+                                     int nd, int Gz, int Gy, int Gx, float* __restrict__ rec) {
+    __shared__ float tab[kPhiTable + 1];
+    for (int i = threadIdx.x; i <= kPhiTable; i += blockDim.x) tab[i] = tab_g[i];
+    __syncthreads();
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    float* r = rec + s * kRec;
+    int jb[3] = {0, 0, 0};
+    const int Gs[3] = {Gz, Gy, Gx};
+    for (int ax = 0; ax < 3; ++ax) {
+        const bool used = ax >= 3 - nd;
+        const float g = gs[s * 3 + ax];
+        const int j0 = used ? (int)floorf(g) - (kW / 2 - 1) : 0;
+        for (int a = 0; a < kW; ++a) {
+            float v = (a == 0) ? 1.f : 0.f;
+            if (used) {
+                const int j = j0 + a;
+                v = phi_lookup(tab, g - (float)j);
+                if ((j + Gs[ax] / 2) & 1) v = -v;
+            }
+            r[ax * kW + a] = v;
+        }
+        jb[ax] = used ? wrapc(j0, Gs[ax]) : 0;
     }
+    r[12] = __int_as_float(jb[0] | (jb[1] << 10) | (jb[2] << 20));
+    r[13] = ws[s];
+    r[14] = __int_as_float(perm[s]);
+    r[15] = 0.f;
+}
+
+// lanes 0..15 load one word of the sample's record; every lane gets the weights by shuffles
+template <int ND>
+__device__ __forceinline__ void sample_box(const GridArgs& A, int64_t s, int lane, SampleBox<ND>& B) {
+    const float w = A.rec[s * kRec + (lane & (kRec - 1))];
 #pragma unroll
     for (int a = 0; a < kW; ++a) {
-        if (ND == 3) B.wz[a] = __shfl_sync(0xffffffffu, w, a);
-        else B.wz[a] = (a == 0) ? 1.f : 0.f;
-        B.wy[a] = __shfl_sync(0xffffffffu, w, (ND == 3 ? 4 : 0) + a);
-        B.wx[a] = __shfl_sync(0xffffffffu, w, (ND == 3 ? 8 : 4) + a);
+        B.wz[a] = __shfl_sync(0xffffffffu, w, a);
+        B.wy[a] = __shfl_sync(0xffffffffu, w, kW + a);
+        B.wx[a] = __shfl_sync(0xffffffffu, w, 2 * kW + a);
     }
-    B.jz = (ND == 3) ? wrapc((int)floorf(gz) - (kW / 2 - 1), A.Gz) : 0;
-    B.jy = wrapc((int)floorf(gy) - (kW / 2 - 1), A.Gy);
-    B.jx = wrapc((int)floorf(gx) - (kW / 2 - 1), A.Gx);
+    const int packed = __float_as_int(__shfl_sync(0xffffffffu, w, 12));
+    B.sw = __shfl_sync(0xffffffffu, w, 13);
+    B.perm = __float_as_int(__shfl_sync(0xffffffffu, w, 14));
+    B.jz = packed & 1023;
+    B.jy = (packed >> 10) & 1023;
+    B.jx = (packed >> 20) & 1023;
 }
 
 __device__ __forceinline__ int64_t gaddr(const GridArgs& A, int z, int y, int x, int c) {
@@ -300,9 +324,6 @@ struct Win {
 template <int ND, int P>
 __global__ void __launch_bounds__(128) interp_kernel(GridArgs A, int mode, const float2* __restrict__ ysub,
                                                      float2* __restrict__ out) {
-    __shared__ float tab[kPhiTable + 1];
-    for (int i = threadIdx.x; i <= kPhiTable; i += blockDim.x) tab[i] = A.phi[i];
-    __syncthreads();
     constexpr int S = (ND == 3) ? 4 / P : 1;     // lanes per coil
     const int lane = threadIdx.x & 31;
     const int coil_l = lane / S, slice = lane % S;
@@ -318,7 +339,7 @@ __global__ void __launch_bounds__(128) interp_kernel(GridArgs A, int mode, const
     int cy = -100, cx = -100;
     for (int64_t s = s0; s < s1; ++s) {
         SampleBox<ND> B;
-        sample_box<ND>(A, tab, s, lane, B);
+        sample_box<ND>(A, s, lane, B);
         const int dy = B.jy - cy, dx = B.jx - cx;
         if (abs(dy) > 1 || abs(dx) > 1) {
 #pragma unroll
@@ -432,13 +453,13 @@ __global__ void __launch_bounds__(128) interp_kernel(GridArgs A, int mode, const
             }
         }
         if (active && slice == 0) {
-            acc = cscale(acc, A.ws[s]);
+            acc = cscale(acc, B.sw);
             if (mode == OUT_USER) {
-                out[(int64_t)c * A.N + A.perm[s]] = acc;
+                out[(int64_t)c * A.N + B.perm] = acc;
             } else if (mode == OUT_RESID) {
-                out[(int64_t)c * A.N + s] = csub(acc, ysub[(int64_t)c * A.N + A.perm[s]]);
+                out[s * A.C + c] = csub(acc, ysub[(int64_t)c * A.N + B.perm]);
             } else {
-                out[(int64_t)c * A.N + s] = acc;
+                out[s * A.C + c] = acc;
             }
         }
     }
@@ -450,9 +471,6 @@ __device__ __forceinline__ void red_add(float2* p, float2 v) {
 
 template <int ND, int P>
 __global__ void __launch_bounds__(128) spread_kernel(GridArgs A, const float2* __restrict__ yin, int sorted_in) {
-    __shared__ float tab[kPhiTable + 1];
-    for (int i = threadIdx.x; i <= kPhiTable; i += blockDim.x) tab[i] = A.phi[i];
-    __syncthreads();
     constexpr int S = (ND == 3) ? 4 / P : 1;
     const int lane = threadIdx.x & 31;
     const int coil_l = lane / S, slice = lane % S;
@@ -488,7 +506,7 @@ __global__ void __launch_bounds__(128) spread_kernel(GridArgs A, const float2* _
     };
     for (int64_t s = s0; s < s1; ++s) {
         SampleBox<ND> B;
-        sample_box<ND>(A, tab, s, lane, B);
+        sample_box<ND>(A, s, lane, B);
         const int dy = B.jy - cy, dx = B.jx - cx;
         if (abs(dy) > 1 || abs(dx) > 1) {
 #pragma unroll
@@ -563,8 +581,8 @@ __global__ void __launch_bounds__(128) spread_kernel(GridArgs A, const float2* _
         cy = B.jy;
         cx = B.jx;
         float2 v = make_float2(0.f, 0.f);
-        if (active) v = sorted_in ? yin[(int64_t)c * A.N + s] : yin[(int64_t)c * A.N + A.perm[s]];
-        v = cscale(v, A.ws[s]);
+        if (active) v = sorted_in ? yin[s * A.C + c] : yin[(int64_t)c * A.N + B.perm];
+        v = cscale(v, B.sw);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             int rel = 0, zw = 0;
@@ -605,10 +623,7 @@ static GridArgs make_grid_args(const cs_plan* p, int ncoils) {
     A.Gz = p->grid[0];
     A.Gy = p->grid[1];
     A.Gx = p->grid[2];
-    A.phi = p->phi;
-    A.gs = p->gsorted;
-    A.ws = p->wsorted;
-    A.perm = p->perm;
+    A.rec = p->rec;
     A.N = p->N;
     A.chunk = p->interp_chunk;
     return A;
@@ -625,8 +640,10 @@ static cs_status launch_grid_op(const cs_plan* p, int ncoils, int mode, const fl
     const unsigned nb = (unsigned)((warps * 32 + 127) / 128);
     if (nb == 0) return CS_OK;
     const int cmax = SPREAD ? p->spread_coils : p->interp_coils;   // 8, 16 or 32 coils per warp
-    for (int c0 = 0; c0 < ncoils; c0 += cmax) {
-        const int g = std::min(cmax, ncoils - c0);
+    const int nch = (ncoils + cmax - 1) / cmax;
+    const int cbal = (ncoils + nch - 1) / nch;                      // balanced chunk size
+    for (int c0 = 0; c0 < ncoils; c0 += cbal) {
+        const int g = std::min(cbal, ncoils - c0);
         A.c0 = c0;
         A.gsize = g;
         int P = 4;
@@ -648,6 +665,14 @@ static cs_status launch_grid_op(const cs_plan* p, int ncoils, int mode, const fl
         CS_LAUNCH_CHECK();
         prof_end(SPREAD ? ST_SPREAD : ST_INTERP, st);
     }
+    return CS_OK;
+}
+
+cs_status nufft_records(cs_plan* p, cudaStream_t st) {
+    CS_TRY_CUDA(cudaMalloc(&p->rec, sizeof(float) * kRec * (size_t)p->N));
+    sample_record_kernel<<<(unsigned)((p->N + 255) / 256), 256, 0, st>>>(p->gsorted, p->wsorted, p->perm, p->phi, p->N,
+                                                                      p->ndim, p->grid[0], p->grid[1], p->grid[2], p->rec);
+    CS_LAUNCH_CHECK();
     return CS_OK;
 }
 

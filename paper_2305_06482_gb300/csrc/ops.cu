@@ -7,6 +7,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 
@@ -120,6 +122,7 @@ static void plan_free(cs_plan* p) {
     cudaFree(p->tile_off);
     cudaFree(p->items);
     cudaFree(p->phi);
+    cudaFree(p->rec);
     cudaFree(p->bufA);
     cudaFree(p->bufB);
     cudaFree(p->ktmp);
@@ -147,6 +150,8 @@ static cs_status plan_build(cs_plan* p, const cs_geom* g, cudaStream_t st) {
         p->off[a] = (p->grid[a] - p->img[a]) / 2;
     }
     CS_REQUIRE(p->img[2] <= 512, CS_ERR_UNSUPPORTED_SIZE, "nx above 512 is not supported");
+    for (int a = 0; a < 3; ++a)
+        CS_REQUIRE(p->grid[a] <= 1023, CS_ERR_UNSUPPORTED_SIZE, "grid size %d above 1023", p->grid[a]);
     p->D = (int64_t)p->img[0] * p->img[1] * p->img[2];
     p->G = (int64_t)p->grid[0] * p->grid[1] * p->grid[2];
     p->N = g->nsamples;
@@ -207,6 +212,10 @@ static cs_status plan_build(cs_plan* p, const cs_geom* g, cudaStream_t st) {
     p->ntiles_total = (int64_t)p->ntiles[0] * p->ntiles[1] * p->ntiles[2];
     p->spread_chunk = 8192;
     p->interp_chunk = 64;
+    // tuning knobs (coils per warp of the gridding kernels, samples per warp)
+    if (const char* e = getenv("CS_INTERP_COILS")) p->interp_coils = std::max(1, std::min(32, atoi(e)));
+    if (const char* e = getenv("CS_SPREAD_COILS")) p->spread_coils = std::max(1, std::min(16, atoi(e)));
+    if (const char* e = getenv("CS_GRID_CHUNK")) p->interp_chunk = std::max(1, atoi(e));
     {
         // phi(u) = I0(beta sqrt(1 - (u/2)^2)) / I0(beta) on [0, 2], 2049 points
         const int nt = 2048;
@@ -226,6 +235,7 @@ static cs_status plan_build(cs_plan* p, const cs_geom* g, cudaStream_t st) {
     CS_TRY_CUDA(cudaMalloc(&p->j0, sizeof(int32_t) * nd * p->N));
     CS_TRY_CUDA(cudaMalloc(&p->tile_off, sizeof(int32_t) * (p->ntiles_total + 1)));
     CS_PROPAGATE(nufft_bin(p, g->traj, g->dcf, st));
+    CS_PROPAGATE(nufft_records(p, st));
     CS_TRY_CUDA(cudaStreamSynchronize(st));
     return CS_OK;
 }
