@@ -42,7 +42,7 @@ def workload_desc(w):
     return (f"{w['name']}: {w['img'][0]}x{w['img'][1]}x{w['img'][2]} image, grid "
             f"{w['grid'][0]}x{w['grid'][1]}x{w['grid'][2]}, {w['nc']} coils, {w['n_int']}x{w['n_read']} cones "
             f"samples/coil, l1-db4 (lambda {w['lam']}) FISTA K={w['K']}, sketch m={w['V'] + w['S']} "
-            f"({w['V']} PCA + {w['S']} Gaussian)")
+            f"({w['V']} PCA + {w['S']} Gaussian), sketched maps BF16 split on tensor cores")
 
 
 def nufft_model_bytes(w, C):
@@ -216,7 +216,7 @@ def run_native(args, w, rank, world, local_rank):
     # logged sketched run: NRMSE after every outer iteration
     T_cap = w["T_cap"]
     sk_its = torch.empty((T_cap,) + img, dtype=torch.complex64, device=dev)
-    sparams = dict(K=w["K"], V=w["V"], S=w["S"], seed=seed + 4, power_v0=v0)
+    sparams = dict(K=w["K"], V=w["V"], S=w["S"], seed=seed + 4, power_v0=v0, precision=cs.PREC_BF16_SPLIT)
     cs.recon_solve(plan, y, maps, w["lam"], cs.REG_L1_WAVELET, cs.SolveParams(T=T_cap, iterates=sk_its, **sparams),
                    wavelet_levels=w["levels"])
     sk_curve = [nrmse(sk_its[t], x_inf) for t in range(T_cap)]

@@ -172,6 +172,9 @@ cs_status coil_rotate(const float* U, const float* in, int C, int C_out, int64_t
 cs_status sketch_draw(uint64_t seed, int t0, int T, int C, int V, int S, int dist, int norm,
                       float* out, void* stream);
 
+/* Synchronise `stream` and report (then clear) a device-side timeout of a bounded wait. */
+cs_status cs_device_status(void* stream);
+
 /* One Philox4x32-10 block on the host (known-answer testing of the generator). */
 cs_status cs_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
@@ -180,8 +183,10 @@ cs_status cs_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_
  *   maps_s[s][d] = sum_j S[s][j] maps_rot[V + j][d], s < S, j < C - V
  * (rows 0..V-1 of the sketched maps are maps_rot[0..V-1] themselves and are not copied).
  * precision CS_PREC_FP32: FP32 CUDA-core contraction; CS_PREC_BF16_SPLIT: tensor-core BF16
- * contraction of the BF16-exact sketch with a two-term BF16 split of the maps (hi + lo),
- * FP32 accumulation.
+ * contraction (tcgen05, accumulator in tensor memory) of the BF16-exact sketch with a two-term
+ * BF16 split of the maps (hi + lo), FP32 accumulation, relative error about 2^-17 per term;
+ * limited to S <= 16 and C - V <= 64.  Its waits on the tensor cores are bounded: a wait that
+ * gives up is reported as CS_ERR_TIMEOUT by the next cs_device_status or recon_solve.
  * ---------------------------------------------------------------------------------------- */
 cs_status sketched_maps(const float* S, const float* maps_rot, int64_t D, int C, int V, int Sn,
                         int precision, float* maps_s, void* stream);

@@ -65,7 +65,7 @@ EXPORTED = [
     "cs_last_error", "cs_version", "cs_plan_create", "cs_plan_destroy", "cs_plan_binning", "sense_fwd",
     "sense_adj", "sense_grad", "sketched_normal_apply", "coil_pca", "coil_rotate", "sketch_draw",
     "cs_philox4x32_10", "sketched_maps", "recon_solve", "wavelet_fwd", "wavelet_inv", "soft_threshold",
-    "cs_hermitian_eig_host", "cs_launch_count", "cs_profile", "cs_profile_read", "coil_pca_noalloc",
+    "cs_hermitian_eig_host", "cs_launch_count", "cs_profile", "cs_profile_read", "coil_pca_noalloc", "cs_device_status",
 ]
 STAGES = {"spread": 0, "interp": 1, "fft_plain": 2, "expand": 3, "reduce": 4}
 
@@ -96,6 +96,7 @@ def lib():
             "soft_threshold": ([vp, i64, f, vp], i), "cs_hermitian_eig_host": ([vp, i, vp, vp], i),
             "cs_launch_count": ([], ctypes.c_longlong), "cs_profile": ([i], i),
             "cs_profile_read": ([i, vp, vp], i), "coil_pca_noalloc": ([vp, i, i64, vp, vp, vp], i),
+            "cs_device_status": ([vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -279,6 +280,11 @@ def sketched_maps(S, maps_rot, V, precision=PREC_FP32, out=None, stream=None):
         out = torch.empty((Sn,) + tuple(maps_rot.shape[1:]), dtype=torch.complex64, device=maps_rot.device)
     _check(lib().sketched_maps(_ptr(S), _ptr(maps_rot), D, C, V, Sn, precision, _ptr(out), _stream(stream)))
     return out
+
+
+def device_status(stream=None):
+    """Synchronise the stream; raise CoilSketchError(CS_ERR_TIMEOUT) if a bounded device wait gave up."""
+    _check(lib().cs_device_status(_stream(stream)))
 
 
 def wavelet_fwd(x, levels=4, stream=None):

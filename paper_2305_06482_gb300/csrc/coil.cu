@@ -422,6 +422,8 @@ __global__ void sketch_maps_fp32_kernel(const float* __restrict__ Sk, const floa
     }
 }
 
+cs_status tc_check_and_clear();
+
 // tensor-core split-precision variant (sketch_tc.cu)
 cs_status sketched_maps_bf16split(const float* S, const float2* mrot, int64_t D, int C, int V, int Sn, float2* out,
                                   cudaStream_t st);
@@ -582,6 +584,12 @@ cs_status coil_rotate(const float* U, const float* in, int C, int C_out, int64_t
     CS_REQUIRE(in != out, CS_ERR_INVALID_ARG, "coil_rotate cannot run in place");
     if (C_out == 0 || L == 0) return CS_OK;
     return coil_rotate_impl((const float2*)U, (const float2*)in, C, C_out, L, (float2*)out, (cudaStream_t)stream);
+}
+
+cs_status cs_device_status(void* stream) {
+    clear_error();
+    CS_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return tc_check_and_clear();
 }
 
 cs_status sketched_maps(const float* S, const float* maps_rot, int64_t D, int C, int V, int Sn, int precision,

@@ -19,6 +19,7 @@ cs_status sketched_maps_impl(const float* S, const float2* mrot, int64_t D, int 
                              float2* out, cudaStream_t st);
 cs_status coil_pca_impl(const float2* y, int C, int64_t N, float2* U, double* eig, double* Rws, cudaStream_t st);
 cs_status coil_rotate_impl(const float2* U, const float2* in, int C, int Cout, int64_t L, float2* out, cudaStream_t st);
+cs_status tc_check_and_clear();
 
 constexpr int kRedBlocks = 296;   // partial sums per reduction (2 per SM of a 148/152-SM part)
 constexpr int kRedThreads = 256;
@@ -709,6 +710,7 @@ static cs_status recon_solve_impl(const cs_plan* p, const cs_problem* pr, const 
         stats->ms_total = ms_all;
         stats->ms_pca = ms_pca;
     }
+    CS_PROPAGATE(tc_check_and_clear());
     CS_REQUIRE(!h.nonfinite, CS_ERR_NONFINITE, "a solver reduction produced a non-finite value");
     return CS_OK;
 }

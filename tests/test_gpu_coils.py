@@ -61,3 +61,20 @@ def test_sketched_maps_fp32():
     out = cs.sketched_maps(t(Sk), t(m), V)
     ref = coils.sketched_maps(Sk.astype(np.float64), m.astype(np.complex64).astype(np.complex128), V)[V:]
     assert nrmse(h(out), ref) < 1e-6
+
+
+@pytest.mark.parametrize("C,V,S,D", [(32, 4, 4, 4096 + 37), (40, 5, 5, 20000), (12, 2, 16, 1000), (20, 4, 3, 64 * 300)])
+def test_sketched_maps_bf16_split_tensor_cores(C, V, S, D):
+    """BF16 x (hi + lo) split on the tensor cores vs the FP64 product: the split keeps about 16
+    mantissa bits of each map entry, so the relative error is of order 2^-17."""
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    m = synthdata.random_complex((C, D), 3)
+    Sk = philox.sketch_draw(7, 0, 1, C, V, S)[0]
+    out = cs.sketched_maps(t(Sk), t(m), V, precision=cs.PREC_BF16_SPLIT)
+    cs.device_status()
+    ref = coils.sketched_maps(Sk.astype(np.float64), m.astype(np.complex64).astype(np.complex128), V)[V:]
+    err = nrmse(h(out), ref)
+    assert err < 2e-5, err
+    fp32 = cs.sketched_maps(t(Sk), t(m), V, precision=cs.PREC_FP32)
+    assert nrmse(h(fp32), ref) < 1e-6

@@ -76,6 +76,21 @@ def test_plain_cg_and_fista_cartesian():
     assert nrmse(h(x), x_ref) < 1e-4
 
 
+def test_coil_sketching_cg_bf16_split_maps():
+    """Algorithm 1 with the sketched maps contracted on the tensor cores (BF16 split) stays
+    within the final-image tolerance of the FP64 oracle."""
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    idx, maps, y, ops = _cart_problem()
+    C, V, S, T, K, lam = 8, 4, 2, 4, 10, 1e-2
+    sk = philox.sketch_draw(4, 0, T, C, V, S)
+    x_ref, _ = solvers.coil_sketching(ops, maps, y, lam, "l2", sk.astype(np.float64), V=V, K=K)
+    plan = cs.Plan(cs.CARTESIAN, (128, 128), C, mask_idx=t(idx, np.int32))
+    x, _ = cs.recon_solve(plan, t(y), t(maps), lam, cs.REG_L2,
+                          cs.SolveParams(T=T, K=K, V=V, S=S, sketches=t(sk), precision=cs.PREC_BF16_SPLIT))
+    assert nrmse(h(x), x_ref) < 1e-4
+
+
 def test_coil_sketching_fista_cartesian():
     import paper_2305_06482_gb300 as cs
     from tests._gpu import t, h, nrmse
