@@ -396,9 +396,10 @@ __global__ void rotate_kernel(const float2* __restrict__ U, const float2* __rest
 // FP32 sketched maps: one thread per voxel, S <= 32 outputs in registers
 constexpr int kMaxSketchRows = 32;
 
-__global__ void sketch_maps_fp32_kernel(const float* __restrict__ Sk, const float2* __restrict__ mrot, int64_t D,
-                                        int V, int K, int Sn, float2* __restrict__ out) {
+__global__ void sketch_maps_fp32_kernel(const float* __restrict__ Sk, const int* __restrict__ tsel, const float2* __restrict__ mrot,
+                                        int64_t D, int V, int K, int Sn, float2* __restrict__ out) {
     __shared__ float sS[kMaxSketchRows * 64];
+    if (tsel) Sk += (int64_t)(*tsel) * Sn * K;
     for (int e = threadIdx.x; e < Sn * K; e += blockDim.x) sS[e] = Sk[e];
     __syncthreads();
     for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < D; d += (int64_t)gridDim.x * blockDim.x) {
@@ -425,8 +426,8 @@ __global__ void sketch_maps_fp32_kernel(const float* __restrict__ Sk, const floa
 cs_status tc_check_and_clear();
 
 // tensor-core split-precision variant (sketch_tc.cu)
-cs_status sketched_maps_bf16split(const float* S, const float2* mrot, int64_t D, int C, int V, int Sn, float2* out,
-                                  cudaStream_t st);
+cs_status sketched_maps_bf16split(const float* S, const int* tsel, const float2* mrot, int64_t D, int C, int V, int Sn,
+                                  float2* out, cudaStream_t st);
 
 static int sm_count() {
     static int n = 0;
@@ -484,14 +485,15 @@ cs_status sketch_draw_impl(uint64_t seed, int t0, int T, int C, int V, int S, in
     return CS_OK;
 }
 
-cs_status sketched_maps_impl(const float* S, const float2* mrot, int64_t D, int C, int V, int Sn, int precision,
-                             float2* out, cudaStream_t st) {
+// tsel (device, nullable): use the sketch block S + (*tsel) * Sn * (C - V)
+cs_status sketched_maps_impl(const float* S, const int* tsel, const float2* mrot, int64_t D, int C, int V, int Sn,
+                             int precision, float2* out, cudaStream_t st) {
     const int K = C - V;
     if (Sn == 0 || D == 0) return CS_OK;
-    if (precision == CS_PREC_BF16_SPLIT) return sketched_maps_bf16split(S, mrot, D, C, V, Sn, out, st);
+    if (precision == CS_PREC_BF16_SPLIT) return sketched_maps_bf16split(S, tsel, mrot, D, C, V, Sn, out, st);
     const int64_t blocks = (D + 255) / 256;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sm_count() * 8));
-    sketch_maps_fp32_kernel<<<grid, 256, 0, st>>>(S, mrot, D, V, K, Sn, out);
+    sketch_maps_fp32_kernel<<<grid, 256, 0, st>>>(S, tsel, mrot, D, V, K, Sn, out);
     CS_LAUNCH_CHECK();
     return CS_OK;
 }
@@ -598,7 +600,8 @@ cs_status sketched_maps(const float* S, const float* maps_rot, int64_t D, int C,
     CS_REQUIRE(S && maps_rot && maps_s && D >= 0 && V >= 0 && Sn >= 0 && V <= C && Sn <= kMaxSketchRows && C - V <= 64,
                CS_ERR_INVALID_ARG, "bad sketched_maps arguments");
     CS_REQUIRE(precision == CS_PREC_FP32 || precision == CS_PREC_BF16_SPLIT, CS_ERR_INVALID_ARG, "bad precision");
-    return sketched_maps_impl(S, (const float2*)maps_rot, D, C, V, Sn, precision, (float2*)maps_s, (cudaStream_t)stream);
+    return sketched_maps_impl(S, nullptr, (const float2*)maps_rot, D, C, V, Sn, precision, (float2*)maps_s,
+                              (cudaStream_t)stream);
 }
 
 }  // extern "C"

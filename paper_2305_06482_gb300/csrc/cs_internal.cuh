@@ -138,7 +138,8 @@ struct cs_plan {
     // workspace (per coil up to max_coils)
     float2* bufA = nullptr;       // grid-sized per coil   [max_coils][G] (also the first-pass buffer)
     float2* bufB = nullptr;       // intermediate per coil [max_coils][nz * Gy * Gx] (3D) or unused
-    float2* ktmp = nullptr;       // k-space scratch [max_coils][N]
+    float2* ktmp = nullptr;       // k-space scratch [N][max_coils] (sorted, coil-interleaved)
+    void* solver_ws = nullptr;    // recon_solve workspace and cached CUDA graph (solve.cu)
 };
 
 namespace cs {
@@ -159,6 +160,13 @@ cs_status nufft_interp_spread(const cs_plan* p, int ncoils, cudaStream_t st);
 
 // Reductions and vector kernels (solve.cu)
 int reduce_blocks();
+
+void solver_ws_free(cs_plan* p);
+
+// one-time per-device set-up (kernel attributes, filter constants), done at plan creation
+cs_status fft_init_attrs();
+cs_status tc_init_attrs();
+cs_status wavelet_init_constants();
 
 // Jacobi eigensolver (shared host/device algorithm, coil.cu)
 void hermitian_eig_serial(double* A, int n, double* V, double* evals);

@@ -436,17 +436,22 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
 
 static size_t pass_smem(int n) { return sizeof(float2) * (size_t)(2 * n * kLinePad + n); }
 
+// dynamic shared-memory limits of every pass kernel (set once per device at plan creation,
+// never inside a stream capture)
+cs_status fft_init_attrs() {
+    const int sm = (int)pass_smem(kMaxFft);
+    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<EXPAND_X>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<GATHER_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<SCATTER_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<MASK_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<REDUCE_X>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    return CS_OK;
+}
+
 template <int MODE>
 static cs_status launch_pass(const PassArgs& A, cudaStream_t st) {
     const size_t sm = pass_smem(A.n);
-    static bool attr_set[64] = {false};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 64 && !attr_set[dev]) {
-        CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)pass_smem(kMaxFft)));
-        attr_set[dev] = true;
-    }
     int64_t blocks;
     if (MODE == EXPAND_X) blocks = (A.rows * A.C + kLines - 1) / kLines;
     else if (MODE == REDUCE_X) blocks = (A.rows + A.rows_per_cta - 1) / A.rows_per_cta;

@@ -55,8 +55,14 @@ static cudaEvent_t ev_get() {
     return e;
 }
 
+static bool capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    return cs != cudaStreamCaptureStatusNone;
+}
+
 void prof_begin(int stage, cudaStream_t st) {
-    if (!g_prof_on) return;
+    if (!g_prof_on || capturing(st)) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_open[stage].stage = stage;
     g_open[stage].a = ev_get();
@@ -64,7 +70,7 @@ void prof_begin(int stage, cudaStream_t st) {
 }
 
 void prof_end(int stage, cudaStream_t st) {
-    if (!g_prof_on) return;
+    if (!g_prof_on || capturing(st)) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     ProfRec r = g_open[stage];
     r.b = ev_get();
@@ -109,6 +115,7 @@ __global__ void idxmap_kernel(const int32_t* __restrict__ idx, int64_t N, int32_
 
 static void plan_free(cs_plan* p) {
     if (!p) return;
+    solver_ws_free(p);
     for (int a = 0; a < 3; ++a) {
         fft_len_free(p->fft[a]);
         cudaFree(p->apod[a]);
@@ -129,8 +136,23 @@ static void plan_free(cs_plan* p) {
     delete p;
 }
 
+static cs_status device_init_once() {
+    static std::mutex mu;
+    static bool done[128] = {false};
+    int dev = 0;
+    CS_TRY_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 128 || done[dev]) return CS_OK;
+    CS_PROPAGATE(fft_init_attrs());
+    CS_PROPAGATE(tc_init_attrs());
+    CS_PROPAGATE(wavelet_init_constants());
+    done[dev] = true;
+    return CS_OK;
+}
+
 static cs_status plan_build(cs_plan* p, const cs_geom* g, cudaStream_t st) {
     CS_TRY_CUDA(cudaGetDevice(&p->device));
+    CS_PROPAGATE(device_init_once());
     const int nd = g->ndim;
     p->kind = g->kind;
     p->ndim = nd;

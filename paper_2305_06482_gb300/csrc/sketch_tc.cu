@@ -55,8 +55,10 @@ __device__ __forceinline__ unsigned short bf16_bits_rn(float f) {
 
 __device__ __forceinline__ float bf16_to_float(unsigned short h) { return __uint_as_float((uint32_t)h << 16); }
 
-__global__ void __launch_bounds__(128) sketch_tc_kernel(const float* __restrict__ Sk, const float2* __restrict__ mrot,
-                                                        int64_t D, int V, int K, int Sn, float2* __restrict__ out) {
+__global__ void __launch_bounds__(128) sketch_tc_kernel(const float* __restrict__ Sk, const int* __restrict__ tsel,
+                                                        const float2* __restrict__ mrot, int64_t D, int V, int K, int Sn,
+                                                        float2* __restrict__ out) {
+    if (tsel) Sk += (int64_t)(*tsel) * Sn * K;
     extern __shared__ __align__(1024) unsigned char tsm[];
     const int kblocks = (K + 15) / 16;
     unsigned char* a_hi = tsm;
@@ -175,6 +177,12 @@ __global__ void __launch_bounds__(128) sketch_tc_kernel(const float* __restrict_
     }
 }
 
+cs_status tc_init_attrs() {
+    CS_TRY_CUDA(cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(2 * 4 * kTcTileBytes + 4 * kTcBBytes)));
+    return CS_OK;
+}
+
 static int sm_count_tc() {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
@@ -182,25 +190,17 @@ static int sm_count_tc() {
     return n > 0 ? n : 148;
 }
 
-cs_status sketched_maps_bf16split(const float* S, const float2* mrot, int64_t D, int C, int V, int Sn, float2* out,
-                                  cudaStream_t st) {
+cs_status sketched_maps_bf16split(const float* S, const int* tsel, const float2* mrot, int64_t D, int C, int V, int Sn,
+                                  float2* out, cudaStream_t st) {
     const int K = C - V;
     CS_REQUIRE(Sn <= kTcN && K <= kTcMaxK, CS_ERR_UNSUPPORTED_SIZE,
                "CS_PREC_BF16_SPLIT supports S <= %d and C - V <= %d", kTcN, kTcMaxK);
     if (K <= 0) return CS_ERR_INVALID_ARG;
     const int kblocks = (K + 15) / 16;
     const size_t sm = (size_t)2 * kblocks * kTcTileBytes + (size_t)kblocks * kTcBBytes;
-    static bool attr[64] = {false};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 64 && !attr[dev]) {
-        CS_TRY_CUDA(cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(2 * 4 * kTcTileBytes + 4 * kTcBBytes)));
-        attr[dev] = true;
-    }
     const int64_t tiles = (D + 63) / 64;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sm_count_tc() * 8));
-    sketch_tc_kernel<<<grid, 128, sm, st>>>(S, mrot, D, V, K, Sn, out);
+    sketch_tc_kernel<<<grid, 128, sm, st>>>(S, tsel, mrot, D, V, K, Sn, out);
     CS_LAUNCH_CHECK();
     return CS_OK;
 }

@@ -15,8 +15,8 @@ namespace cs {
 
 cs_status sketch_draw_impl(uint64_t seed, int t0, int T, int C, int V, int S, int dist, int norm, float* out,
                            cudaStream_t st);
-cs_status sketched_maps_impl(const float* S, const float2* mrot, int64_t D, int C, int V, int Sn, int precision,
-                             float2* out, cudaStream_t st);
+cs_status sketched_maps_impl(const float* S, const int* tsel, const float2* mrot, int64_t D, int C, int V, int Sn,
+                             int precision, float2* out, cudaStream_t st);
 cs_status coil_pca_impl(const float2* y, int C, int64_t N, float2* U, double* eig, double* Rws, cudaStream_t st);
 cs_status coil_rotate_impl(const float2* U, const float2* in, int C, int Cout, int64_t L, float2* out, cudaStream_t st);
 cs_status tc_check_and_clear();
@@ -107,9 +107,11 @@ __global__ void store_sum_kernel(const double* __restrict__ part, double* __rest
 
 // alpha = rr / <p, Hp>; x += alpha p; r -= alpha Hp; partials of ||r||^2
 __global__ void __launch_bounds__(kRedThreads) cg_update_kernel(const double* __restrict__ php_part, Scal* sc, int par,
-                                                                 int64_t n, float2* __restrict__ x, float2* __restrict__ r,
+                                                                 const int* __restrict__ par_dev, int64_t n,
+                                                                 float2* __restrict__ x, float2* __restrict__ r,
                                                                  const float2* __restrict__ p,
                                                                  const float2* __restrict__ hp, double* __restrict__ part) {
+    if (par_dev) par = *par_dev & 1;
     const double php = sum_partials(php_part);
     const double rr = sc->rr[par];
     double alpha = rr / php;
@@ -136,7 +138,9 @@ __global__ void __launch_bounds__(kRedThreads) cg_update_kernel(const double* __
 
 // beta = rr_new / rr; p = r + beta p; rr slot (par ^ 1) = rr_new
 __global__ void __launch_bounds__(kRedThreads) cg_dir_kernel(const double* __restrict__ rr_part, Scal* sc, int par,
-                                                              int64_t n, const float2* __restrict__ r, float2* __restrict__ p) {
+                                                              const int* __restrict__ par_dev, int64_t n,
+                                                              const float2* __restrict__ r, float2* __restrict__ p) {
+    if (par_dev) par = *par_dev & 1;
     const double rrn = sum_partials(rr_part);
     const double rr = sc->rr[par];
     double beta = (rr > 0) ? rrn / rr : 0.0;
@@ -185,8 +189,10 @@ __global__ void soft_kernel(float2* __restrict__ c, int64_t n, float lambda, con
 }
 
 // z = x + theta (x - xprev)
-__global__ void momentum_kernel(const float2* __restrict__ x, const float2* __restrict__ xp, float theta, int64_t n,
+__global__ void momentum_kernel(const float2* __restrict__ x, const float2* __restrict__ xp, float theta,
+                                const float* __restrict__ theta_dev, const int* __restrict__ kdev, int64_t n,
                                 float2* __restrict__ z) {
+    if (theta_dev) theta = theta_dev[*kdev];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float2 a = x[i], b = xp[i];
         z[i] = make_float2(fmaf(theta, a.x - b.x, a.x), fmaf(theta, a.y - b.y, a.y));
@@ -205,6 +211,18 @@ __global__ void power_norm_kernel(const double* __restrict__ part, Scal* sc, con
     const float inv = (nrm > 0) ? (float)(1.0 / nrm) : 0.f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         v[i] = cscale(w[i], inv);
+}
+
+// out[idx] = x with idx = *idev (or the host index when idev is null); then optionally ++*inc
+__global__ void copy_iter_kernel(const float2* __restrict__ x, float2* __restrict__ out, const int* __restrict__ idev,
+                                 int idx, int64_t n) {
+    if (idev) idx = *idev;
+    float2* o = out + (int64_t)idx * n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) o[i] = x[i];
+}
+
+__global__ void inc_kernel(int* c) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *c += 1;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -362,7 +380,7 @@ static void db4_filter(double h[8]) {
 
 constexpr int kWavSmem = (int)sizeof(float2) * 2 * kWavLines * (kWavMax + 1);
 
-static cs_status wavelet_init_constants() {
+cs_status wavelet_init_constants() {
     static int done_dev[64] = {0};
     int dev = 0;
     CS_TRY_CUDA(cudaGetDevice(&dev));
@@ -420,25 +438,83 @@ static int vec_grid(int64_t n) {
 
 // ------------------------------------------------------------------------------------------
 // recon_solve
+//
+// The solver's device vectors live in a per-plan workspace that persists across calls (so that
+// pointers are stable and a captured CUDA graph can be replayed by later calls); all scalars of
+// the iteration stay on the device.  With use_graph, one outer iteration of Algorithm 1 (true
+// gradient, sketched maps selected by a device-side iteration counter, K inner iterations,
+// iterate copy, counter increment) - or, for the plain solver, one iteration - is captured once,
+// cached in the plan under a signature of the call's arguments, and replayed.
 
-struct Work {
+struct SolverWS {
+    int64_t D = 0, N = 0;
+    int C = 0, S = 0, Kc = 0, T = 0, K = 0;
+    Scal* sc = nullptr;
+    double *partA = nullptr, *partB = nullptr, *eig = nullptr, *Rws = nullptr;
+    float2 *U = nullptr, *maps_r = nullptr, *y_r = nullptr, *d = nullptr, *hp = nullptr, *u = nullptr, *z = nullptr,
+           *xp = nullptr, *gr = nullptr, *xt = nullptr, *r = nullptr, *pv = nullptr, *msk = nullptr;
+    float* skd = nullptr;
+    float* theta = nullptr;
+    int* tdev = nullptr;
     std::vector<void*> allocs;
-    ~Work() {
-        for (void* p : allocs) cudaFree(p);
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t gsig = 0;
+    cudaStream_t cap = nullptr;   // non-blocking stream used only for graph capture
+    void free_all() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        gsig = 0;
+        for (void* q : allocs) cudaFree(q);
+        allocs.clear();
     }
-    template <typename T>
-    cs_status get(T** out, size_t count) {
-        void* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, sizeof(T) * std::max<size_t>(count, 1));
+    ~SolverWS() {
+        free_all();
+        if (cap) cudaStreamDestroy(cap);
+    }
+    template <typename T_>
+    cs_status get(T_** out, size_t count) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, sizeof(T_) * std::max<size_t>(count, 1));
         if (e != cudaSuccess) {
-            set_error("recon_solve workspace allocation (%zu bytes): %s", sizeof(T) * count, cudaGetErrorString(e));
+            set_error("recon_solve workspace allocation (%zu bytes): %s", sizeof(T_) * count, cudaGetErrorString(e));
             return e == cudaErrorMemoryAllocation ? CS_ERR_OOM : CS_ERR_CUDA;
         }
-        allocs.push_back(p);
-        *out = (T*)p;
+        allocs.push_back(q);
+        *out = (T_*)q;
+        return CS_OK;
+    }
+    // (re)allocate for the given sizes when the current buffers are too small
+    cs_status ensure(int64_t D_, int64_t N_, int C_, int S_, int Kc_, int T_, int K_) {
+        if (!allocs.empty() && D_ <= D && N_ <= N && C_ <= C && S_ <= S && Kc_ <= Kc && T_ <= T && K_ <= K) return CS_OK;
+        free_all();
+        D = std::max(D_, D);
+        N = std::max(N_, N);
+        C = std::max(C_, C);
+        S = std::max(S_, S);
+        Kc = std::max(Kc_, Kc);
+        T = std::max(T_, T);
+        K = std::max(K_, K);
+        CS_PROPAGATE(get(&sc, 1));
+        CS_PROPAGATE(get(&partA, kRedBlocks));
+        CS_PROPAGATE(get(&partB, kRedBlocks));
+        CS_PROPAGATE(get(&U, (size_t)C * C));
+        CS_PROPAGATE(get(&eig, (size_t)C));
+        CS_PROPAGATE(get(&Rws, (size_t)2 * C * C));
+        CS_PROPAGATE(get(&maps_r, (size_t)C * D));
+        CS_PROPAGATE(get(&y_r, (size_t)C * N));
+        for (float2** v : {&d, &hp, &u, &z, &xp, &gr, &xt, &r, &pv}) CS_PROPAGATE(get(v, (size_t)D));
+        CS_PROPAGATE(get(&msk, (size_t)std::max(S, 1) * D));
+        CS_PROPAGATE(get(&skd, (size_t)std::max(T * S * Kc, 1)));
+        CS_PROPAGATE(get(&theta, (size_t)std::max(K, 1)));
+        CS_PROPAGATE(get(&tdev, 1));
         return CS_OK;
     }
 };
+
+void solver_ws_free(cs_plan* p) {
+    delete static_cast<SolverWS*>(p->solver_ws);
+    p->solver_ws = nullptr;
+}
 
 struct Ctx {
     const cs_plan* p;
@@ -486,29 +562,28 @@ static cs_status power_iteration(const Ctx& c, const float2* v0, int iters, cons
     return CS_OK;
 }
 
-// K CG iterations on (A_S^H A_S + lambda I) x = A_S^H A_S x^t - d from x^t (x updated in place)
+// one CG iteration on H = A^H A + lambda I (sketched or full maps); parity from host k or device counter
+static cs_status cg_iter(const Ctx& c, const float2* mv, int V, const float2* ms, int S, float2* x, float2* r,
+                         float2* pv, float2* hp, int par, const int* par_dev) {
+    CS_PROPAGATE(normal_apply(c, pv, mv, V, ms, S, c.lambda, hp));
+    dot_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(pv, hp, c.D, c.partA);
+    CS_LAUNCH_CHECK();
+    cg_update_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(c.partA, c.sc, par, par_dev, c.D, x, r, pv, hp, c.partB);
+    CS_LAUNCH_CHECK();
+    cg_dir_kernel<<<vec_grid(c.D), kRedThreads, 0, c.st>>>(c.partB, c.sc, par, par_dev, c.D, r, pv);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+// K CG iterations on (A_S^H A_S + lambda I) x = A_S^H A_S x^t - d from x^t (x updated in place);
+// the initial residual is b - H x^t = -(d + lambda x^t)
 static cs_status cg_sub(const Ctx& c, const float2* d, float2* x, int K, const float2* mv, int V, const float2* ms, int S,
                         float2* r, float2* pv, float2* hp) {
-    const int g = vec_grid(c.D);
     cg_init_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(d, x, c.lambda, c.D, r, pv, c.partB);
     CS_LAUNCH_CHECK();
     store_sum_kernel<<<1, 32, 0, c.st>>>(c.partB, &c.sc->rr[0]);
     CS_LAUNCH_CHECK();
-    for (int k = 0; k < K; ++k) {
-        const int par = k & 1;
-        CS_PROPAGATE(normal_apply(c, pv, mv, V, ms, S, c.lambda, hp));
-        dot_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(pv, hp, c.D, c.partA);
-        CS_LAUNCH_CHECK();
-        cg_update_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(c.partA, c.sc, par, c.D, x, r, pv, hp, c.partB);
-        CS_LAUNCH_CHECK();
-        cg_dir_kernel<<<g, kRedThreads, 0, c.st>>>(c.partB, c.sc, par, c.D, r, pv);
-        CS_LAUNCH_CHECK();
-    }
-    // leave the final squared residual in rr[0]
-    if (K & 1) {
-        store_sum_kernel<<<1, 32, 0, c.st>>>(c.partB, &c.sc->rr[0]);
-        CS_LAUNCH_CHECK();
-    }
+    for (int k = 0; k < K; ++k) CS_PROPAGATE(cg_iter(c, mv, V, ms, S, x, r, pv, hp, k & 1, nullptr));
     return CS_OK;
 }
 
@@ -527,7 +602,7 @@ static cs_status fista_sub(const Ctx& c, const float2* d, float2* x, int K, cons
         fista_step_kernel<<<g, kRedThreads, 0, c.st>>>(z, gr, d, c.sc, c.D, u);
         CS_LAUNCH_CHECK();
         CS_PROPAGATE(prox_wavelet(c, u, x, c.sc, 0.f));
-        momentum_kernel<<<g, kRedThreads, 0, c.st>>>(x, xp, theta[k], c.D, z);
+        momentum_kernel<<<g, kRedThreads, 0, c.st>>>(x, xp, theta[k], nullptr, nullptr, c.D, z);
         CS_LAUNCH_CHECK();
         CS_TRY_CUDA(cudaMemcpyAsync(xp, x, sizeof(float2) * c.D, cudaMemcpyDeviceToDevice, c.st));
     }
@@ -545,11 +620,64 @@ static std::vector<float> fista_thetas(int K) {
     return th;
 }
 
-static cs_status recon_solve_impl(const cs_plan* p, const cs_problem* pr, const cs_solve_params* sp, float2* x,
+static uint64_t fnv(uint64_t h, const void* data, size_t n) {
+    const unsigned char* b = (const unsigned char*)data;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+// Run `body(stream)` `reps` times on `st`, or - with use_graph - capture it once on the
+// workspace's capture stream (the caller's stream may be the legacy default stream, which cannot
+// be captured), cache the instantiated graph and launch it `reps` times on `st`.
+template <typename F>
+static cs_status run_body(SolverWS* ws, bool use_graph, uint64_t sig, int reps, cudaStream_t st, F body, int* graph_used) {
+    if (!use_graph) {
+        for (int i = 0; i < reps; ++i) CS_PROPAGATE(body(st));
+        return CS_OK;
+    }
+    if (!ws->gexec || ws->gsig != sig) {
+        if (ws->gexec) cudaGraphExecDestroy(ws->gexec);
+        ws->gexec = nullptr;
+        if (!ws->cap) CS_TRY_CUDA(cudaStreamCreateWithFlags(&ws->cap, cudaStreamNonBlocking));
+        CS_TRY_CUDA(cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal));
+        cs_status rc = body(ws->cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ws->cap, &g);
+        if (rc != CS_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) {
+            set_error("graph capture failed: %s", cudaGetErrorString(e));
+            return CS_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&ws->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ws->gexec = nullptr;
+            set_error("graph instantiation failed: %s", cudaGetErrorString(e));
+            return CS_ERR_CUDA;
+        }
+        ws->gsig = sig;
+    }
+    for (int i = 0; i < reps; ++i) CS_TRY_CUDA(cudaGraphLaunch(ws->gexec, st));
+    *graph_used = 1;
+    return CS_OK;
+}
+
+static cs_status recon_solve_impl(cs_plan* p, const cs_problem* pr, const cs_solve_params* sp, float2* x,
                                   cs_stats* stats, cudaStream_t st) {
-    Work wk;
     const int64_t D = p->D, N = p->N;
     const int C = pr->C;
+    const bool sketch = sp->sketch != 0;
+    const int V = sketch ? sp->V : C, S = sketch ? sp->S : 0, Kc = C - V;
+    const int T = sp->T, K = sp->K;
+    if (!p->solver_ws) p->solver_ws = new SolverWS();
+    SolverWS* ws = static_cast<SolverWS*>(p->solver_ws);
+    CS_PROPAGATE(ws->ensure(D, N, C, S, Kc, T, K));
     Ctx c;
     c.p = p;
     c.st = st;
@@ -558,14 +686,15 @@ static cs_status recon_solve_impl(const cs_plan* p, const cs_problem* pr, const 
     for (int a = 0; a < 3; ++a) c.dims3[a] = p->img[a];
     c.levels = pr->wavelet_levels > 0 ? pr->wavelet_levels : 4;
     c.lambda = pr->lambda;
-    CS_PROPAGATE(wk.get(&c.sc, 1));
-    CS_PROPAGATE(wk.get(&c.partA, kRedBlocks));
-    CS_PROPAGATE(wk.get(&c.partB, kRedBlocks));
-    CS_TRY_CUDA(cudaMemsetAsync(c.sc, 0, sizeof(Scal), st));
+    c.sc = ws->sc;
+    c.partA = ws->partA;
+    c.partB = ws->partB;
+    CS_TRY_CUDA(cudaMemsetAsync(ws->sc, 0, sizeof(Scal), st));
+    CS_TRY_CUDA(cudaMemsetAsync(ws->tdev, 0, sizeof(int), st));
     if (sp->step > 0) {
         Scal h = {};
         h.eta = sp->step;
-        CS_TRY_CUDA(cudaMemcpyAsync(c.sc, &h, sizeof(Scal), cudaMemcpyHostToDevice, st));
+        CS_TRY_CUDA(cudaMemcpyAsync(ws->sc, &h, sizeof(Scal), cudaMemcpyHostToDevice, st));
     }
     cudaEvent_t e0, e1, e2;
     CS_TRY_CUDA(cudaEventCreate(&e0));
@@ -583,117 +712,113 @@ static cs_status recon_solve_impl(const cs_plan* p, const cs_problem* pr, const 
 
     const float2* maps = (const float2*)pr->maps;
     const float2* y = (const float2*)pr->y;
-    float2* maps_r = nullptr;
-    float2* y_r = nullptr;
     if (sp->do_pca) {
-        float2* U = nullptr;
-        double *eig = nullptr, *Rws = nullptr;
-        CS_PROPAGATE(wk.get(&U, (size_t)C * C));
-        CS_PROPAGATE(wk.get(&eig, (size_t)C));
-        CS_PROPAGATE(wk.get(&Rws, (size_t)2 * C * C));
-        CS_PROPAGATE(wk.get(&maps_r, (size_t)C * D));
-        CS_PROPAGATE(wk.get(&y_r, (size_t)C * N));
-        CS_PROPAGATE(coil_pca_impl(y, C, N, U, eig, Rws, st));
-        CS_PROPAGATE(coil_rotate_impl(U, maps, C, C, D, maps_r, st));
-        CS_PROPAGATE(coil_rotate_impl(U, y, C, C, N, y_r, st));
-        maps = maps_r;
-        y = y_r;
+        CS_PROPAGATE(coil_pca_impl(y, C, N, ws->U, ws->eig, ws->Rws, st));
+        CS_PROPAGATE(coil_rotate_impl(ws->U, maps, C, C, D, ws->maps_r, st));
+        CS_PROPAGATE(coil_rotate_impl(ws->U, y, C, C, N, ws->y_r, st));
+        maps = ws->maps_r;
+        y = ws->y_r;
     }
     CS_TRY_CUDA(cudaEventRecord(e1, st));
 
     const bool fista = pr->reg == CS_REG_L1_WAVELET;
-    float2 *d = nullptr, *r = nullptr, *pv = nullptr, *hp = nullptr, *z = nullptr, *xp = nullptr, *u = nullptr,
-           *gr = nullptr, *xt = nullptr, *msk = nullptr;
-    CS_PROPAGATE(wk.get(&d, D));
-    CS_PROPAGATE(wk.get(&hp, D));
-    CS_PROPAGATE(wk.get(&u, D));
-    if (fista) {
-        CS_PROPAGATE(wk.get(&z, D));
-        CS_PROPAGATE(wk.get(&xp, D));
-        CS_PROPAGATE(wk.get(&gr, D));
-        CS_PROPAGATE(wk.get(&xt, D));
-    } else {
-        CS_PROPAGATE(wk.get(&r, D));
-        CS_PROPAGATE(wk.get(&pv, D));
-    }
-    const int T = sp->T, K = sp->K;
-    std::vector<float> theta = fista_thetas(std::max(K, 1));
-    if (sp->sketch) {
-        const int V = sp->V, S = sp->S, Kc = C - V;
+    const std::vector<float> theta = fista_thetas(std::max(K, 1));
+    const bool use_graph = sp->use_graph != 0;
+    int graph_used = 0;
+    // signature of everything a captured body depends on
+    uint64_t sig = 1469598103934665603ull;
+    const void* ptrs[] = {p, x, pr->y, pr->maps, sp->sketches, sp->iterates, sp->power_v0};
+    sig = fnv(sig, ptrs, sizeof(ptrs));
+    const int ints[] = {C, T, K, V, S, sp->dist, sp->norm, sp->do_pca, sp->precision, pr->reg, c.levels, (int)sketch};
+    sig = fnv(sig, ints, sizeof(ints));
+    sig = fnv(sig, &pr->lambda, sizeof(float));
+    sig = fnv(sig, &sp->step, sizeof(float));
+    sig = fnv(sig, &sp->seed, sizeof(uint64_t));
+    const int g = vec_grid(D);
+    float2* iters = (float2*)sp->iterates;
+
+    if (sketch) {
         const float* sk = sp->sketches;
-        float* skd = nullptr;
         if (!sk && S > 0) {
-            CS_PROPAGATE(wk.get(&skd, (size_t)T * S * Kc));
-            CS_PROPAGATE(sketch_draw_impl(sp->seed, 0, T, C, V, S, sp->dist, sp->norm, skd, st));
-            sk = skd;
+            CS_PROPAGATE(sketch_draw_impl(sp->seed, 0, T, C, V, S, sp->dist, sp->norm, ws->skd, st));
+            sk = ws->skd;
         }
-        if (S > 0) CS_PROPAGATE(wk.get(&msk, (size_t)S * D));
-        for (int t = 0; t < T; ++t) {
+        float2* msk = ws->msk;
+        if (fista && !(sp->step > 0) && T > 0) {
+            // FISTA step from the first sub-problem (reused by every sub-problem)
+            CS_REQUIRE(sp->power_v0 != nullptr, CS_ERR_INVALID_ARG, "power_v0 is required when step == 0");
+            if (S > 0) CS_PROPAGATE(sketched_maps_impl(sk, ws->tdev, maps, D, C, V, S, sp->precision, msk, st));
+            CS_PROPAGATE(power_iteration(c, (const float2*)sp->power_v0, sp->power_iters > 0 ? sp->power_iters : 20,
+                                         maps, V, msk, S, ws->u, ws->hp));
+        }
+        auto body = [&](cudaStream_t s) -> cs_status {
+            Ctx cc = c;
+            cc.st = s;
             // true gradient with all C coils
-            CS_PROPAGATE((cs_status)sense_grad(p, (const float*)x, (const float*)maps, C, (const float*)y, (float*)d, st));
+            CS_PROPAGATE((cs_status)sense_grad(p, (const float*)x, (const float*)maps, C, (const float*)y, (float*)ws->d, s));
             // sketched model: V virtual coils in place + S random combinations of the rest
-            if (S > 0) CS_PROPAGATE(sketched_maps_impl(sk + (size_t)t * S * Kc, maps, D, C, V, S, sp->precision, msk, st));
-            if (fista) {
-                if (t == 0 && !(sp->step > 0)) {
-                    CS_REQUIRE(sp->power_v0 != nullptr, CS_ERR_INVALID_ARG, "power_v0 is required when step == 0");
-                    CS_PROPAGATE(power_iteration(c, (const float2*)sp->power_v0, sp->power_iters > 0 ? sp->power_iters : 20,
-                                                 maps, V, msk, S, u, hp));
-                }
-                CS_PROPAGATE(fista_sub(c, d, x, K, maps, V, msk, S, theta, z, xp, u, gr, xt));
-            } else {
-                CS_PROPAGATE(cg_sub(c, d, x, K, maps, V, msk, S, r, pv, hp));
+            if (S > 0) CS_PROPAGATE(sketched_maps_impl(sk, ws->tdev, maps, D, C, V, S, sp->precision, msk, s));
+            if (fista) CS_PROPAGATE(fista_sub(cc, ws->d, x, K, maps, V, msk, S, theta, ws->z, ws->xp, ws->u, ws->gr, ws->xt));
+            else CS_PROPAGATE(cg_sub(cc, ws->d, x, K, maps, V, msk, S, ws->r, ws->pv, ws->hp));
+            if (iters) {
+                copy_iter_kernel<<<g, kRedThreads, 0, s>>>(x, iters, ws->tdev, 0, D);
+                CS_LAUNCH_CHECK();
             }
-            if (sp->iterates)
-                CS_TRY_CUDA(cudaMemcpyAsync(sp->iterates + (size_t)t * 2 * D, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
+            inc_kernel<<<1, 32, 0, s>>>(ws->tdev);
+            CS_LAUNCH_CHECK();
+            return CS_OK;
+        };
+        CS_PROPAGATE(run_body(ws, use_graph, sig, T, st, body, &graph_used));
+    } else if (fista) {
+        // plain full-coil FISTA: K iterations in total
+        if (!(sp->step > 0)) {
+            CS_REQUIRE(sp->power_v0 != nullptr, CS_ERR_INVALID_ARG, "power_v0 is required when step == 0");
+            CS_PROPAGATE(power_iteration(c, (const float2*)sp->power_v0, sp->power_iters > 0 ? sp->power_iters : 20,
+                                         maps, C, nullptr, 0, ws->u, ws->hp));
         }
+        CS_TRY_CUDA(cudaMemcpyAsync(ws->theta, theta.data(), sizeof(float) * theta.size(), cudaMemcpyHostToDevice, st));
+        CS_TRY_CUDA(cudaMemcpyAsync(ws->z, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
+        CS_TRY_CUDA(cudaMemcpyAsync(ws->xp, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
+        auto body = [&](cudaStream_t s) -> cs_status {
+            Ctx cc = c;
+            cc.st = s;
+            CS_PROPAGATE((cs_status)sense_grad(p, (const float*)ws->z, (const float*)maps, C, (const float*)y, (float*)ws->gr, s));
+            fista_step_kernel<<<g, kRedThreads, 0, s>>>(ws->z, ws->gr, nullptr, c.sc, D, ws->u);
+            CS_LAUNCH_CHECK();
+            CS_PROPAGATE(prox_wavelet(cc, ws->u, x, c.sc, 0.f));
+            momentum_kernel<<<g, kRedThreads, 0, s>>>(x, ws->xp, 0.f, ws->theta, ws->tdev, D, ws->z);
+            CS_LAUNCH_CHECK();
+            CS_TRY_CUDA(cudaMemcpyAsync(ws->xp, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, s));
+            if (iters) {
+                copy_iter_kernel<<<g, kRedThreads, 0, s>>>(x, iters, ws->tdev, 0, D);
+                CS_LAUNCH_CHECK();
+            }
+            inc_kernel<<<1, 32, 0, s>>>(ws->tdev);
+            CS_LAUNCH_CHECK();
+            return CS_OK;
+        };
+        CS_PROPAGATE(run_body(ws, use_graph, sig, K, st, body, &graph_used));
     } else {
-        // plain full-coil solver: K iterations in total
-        if (fista) {
-            if (!(sp->step > 0)) {
-                CS_REQUIRE(sp->power_v0 != nullptr, CS_ERR_INVALID_ARG, "power_v0 is required when step == 0");
-                CS_PROPAGATE(power_iteration(c, (const float2*)sp->power_v0, sp->power_iters > 0 ? sp->power_iters : 20,
-                                             maps, C, nullptr, 0, u, hp));
-            }
-            const int g = vec_grid(D);
-            CS_TRY_CUDA(cudaMemcpyAsync(z, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
-            CS_TRY_CUDA(cudaMemcpyAsync(xp, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
-            for (int k = 0; k < K; ++k) {
-                CS_PROPAGATE((cs_status)sense_grad(p, (const float*)z, (const float*)maps, C, (const float*)y, (float*)gr, st));
-                fista_step_kernel<<<g, kRedThreads, 0, st>>>(z, gr, nullptr, c.sc, D, u);
+        // plain full-coil CG: (A^H A + lambda I) x = A^H y from x, K iterations in total
+        CS_PROPAGATE((cs_status)sense_adj(p, (const float*)y, (const float*)maps, C, (float*)ws->d, 0, st));   // b
+        CS_PROPAGATE(normal_apply(c, x, maps, C, nullptr, 0, c.lambda, ws->hp));                            // H x
+        cg_init2_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(ws->d, ws->hp, D, ws->r, ws->pv, c.partB);
+        CS_LAUNCH_CHECK();
+        store_sum_kernel<<<1, 32, 0, st>>>(c.partB, &c.sc->rr[0]);
+        CS_LAUNCH_CHECK();
+        auto body = [&](cudaStream_t s) -> cs_status {
+            Ctx cc = c;
+            cc.st = s;
+            CS_PROPAGATE(cg_iter(cc, maps, C, nullptr, 0, x, ws->r, ws->pv, ws->hp, 0, ws->tdev));
+            if (iters) {
+                copy_iter_kernel<<<g, kRedThreads, 0, s>>>(x, iters, ws->tdev, 0, D);
                 CS_LAUNCH_CHECK();
-                CS_PROPAGATE(prox_wavelet(c, u, x, c.sc, 0.f));
-                momentum_kernel<<<g, kRedThreads, 0, st>>>(x, xp, theta[k], D, z);
-                CS_LAUNCH_CHECK();
-                CS_TRY_CUDA(cudaMemcpyAsync(xp, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
-                if (sp->iterates)
-                    CS_TRY_CUDA(cudaMemcpyAsync(sp->iterates + (size_t)k * 2 * D, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
             }
-        } else {
-            // (A^H A + lambda I) x = A^H y by CG from x
-            const int g = vec_grid(D);
-            CS_PROPAGATE((cs_status)sense_adj(p, (const float*)y, (const float*)maps, C, (float*)d, 0, st));   // b
-            CS_PROPAGATE(normal_apply(c, x, maps, C, nullptr, 0, c.lambda, hp));                            // H x
-            cg_init2_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(d, hp, D, r, pv, c.partB);
+            inc_kernel<<<1, 32, 0, s>>>(ws->tdev);
             CS_LAUNCH_CHECK();
-            store_sum_kernel<<<1, 32, 0, st>>>(c.partB, &c.sc->rr[0]);
-            CS_LAUNCH_CHECK();
-            for (int k = 0; k < K; ++k) {
-                const int par = k & 1;
-                CS_PROPAGATE(normal_apply(c, pv, maps, C, nullptr, 0, c.lambda, hp));
-                dot_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(pv, hp, D, c.partA);
-                CS_LAUNCH_CHECK();
-                cg_update_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(c.partA, c.sc, par, D, x, r, pv, hp, c.partB);
-                CS_LAUNCH_CHECK();
-                cg_dir_kernel<<<g, kRedThreads, 0, st>>>(c.partB, c.sc, par, D, r, pv);
-                CS_LAUNCH_CHECK();
-                if (sp->iterates)
-                    CS_TRY_CUDA(cudaMemcpyAsync(sp->iterates + (size_t)k * 2 * D, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
-            }
-            if (K & 1) {
-                store_sum_kernel<<<1, 32, 0, st>>>(c.partB, &c.sc->rr[0]);
-                CS_LAUNCH_CHECK();
-            }
-        }
+            return CS_OK;
+        };
+        CS_PROPAGATE(run_body(ws, use_graph, sig, K, st, body, &graph_used));
     }
     CS_TRY_CUDA(cudaEventRecord(e2, st));
     CS_TRY_CUDA(cudaStreamSynchronize(st));
@@ -704,9 +829,9 @@ static cs_status recon_solve_impl(const cs_plan* p, const cs_problem* pr, const 
         cudaEventElapsedTime(&ms_all, e0, e2);
         cudaEventElapsedTime(&ms_pca, e0, e1);
         stats->L = h.L;
-        stats->final_rr = h.rr[0];
-        stats->outer_done = sp->sketch ? T : 0;
-        stats->graph_used = 0;
+        stats->final_rr = h.rr[K & 1];
+        stats->outer_done = sketch ? T : 0;
+        stats->graph_used = graph_used;
         stats->ms_total = ms_all;
         stats->ms_pca = ms_pca;
     }
@@ -735,7 +860,7 @@ cs_status recon_solve(const cs_plan* p, const cs_problem* pr, const cs_solve_par
                    "need 1 <= V + S <= C (V=%d S=%d C=%d)", sp->V, sp->S, pr->C);
         CS_REQUIRE(sp->S == 0 || sp->V < pr->C, CS_ERR_INVALID_ARG, "S > 0 needs V < C");
     }
-    return recon_solve_impl(p, pr, sp, (float2*)x_inout, stats, (cudaStream_t)stream);
+    return recon_solve_impl(const_cast<cs_plan*>(p), pr, sp, (float2*)x_inout, stats, (cudaStream_t)stream);
 }
 
 cs_status wavelet_fwd(const float* x, int ndim, const int* dims, int levels, float* c, void* stream) {

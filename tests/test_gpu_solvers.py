@@ -133,3 +133,35 @@ def test_nonfinite_input_is_reported():
     with pytest.raises(cs.CoilSketchError) as e:
         cs.recon_solve(plan, t(y), t(maps), 1e-3, cs.REG_L2, cs.SolveParams(K=3, sketch=False, do_pca=False))
     assert e.value.code == 5
+
+
+@pytest.mark.parametrize("reg,sketch", [("l2", True), ("l1", True), ("l2", False), ("l1", False)])
+def test_graph_replay_matches_eager(reg, sketch):
+    """use_graph captures one outer iteration (or one plain iteration), caches it in the plan and
+    replays it; results equal the eagerly launched solve and a second call reuses the graph."""
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    idx, maps, y, _ = _cart_problem(shape=(64, 64))
+    C, V, S, T, K = 8, 4, 2, 3, 6
+    v0 = t(synthdata.random_complex((64, 64), 5))
+    regc = cs.REG_L2 if reg == "l2" else cs.REG_L1_WAVELET
+    plan = cs.Plan(cs.CARTESIAN, (64, 64), C, mask_idx=t(idx, np.int32))
+    yt, mt = t(y), t(maps)
+    sk = t(philox.sketch_draw(4, 0, T, C, V, S))
+    iters_e = torch.zeros((max(T, K), 64, 64), dtype=torch.complex64, device="cuda")
+    iters_g = torch.zeros_like(iters_e)
+    kw = dict(T=T, K=K, V=V, S=S, sketch=sketch, sketches=sk, power_v0=v0, do_pca=sketch)
+    x_e, st_e = cs.recon_solve(plan, yt, mt, 5e-3, regc, cs.SolveParams(iterates=iters_e, **kw), wavelet_levels=3)
+    x_g, st_g = cs.recon_solve(plan, yt, mt, 5e-3, regc, cs.SolveParams(iterates=iters_g, use_graph=True, **kw),
+                               wavelet_levels=3)
+    assert st_e["graph_used"] == 0 and st_g["graph_used"] == 1
+    assert nrmse(h(x_g), h(x_e)) < 1e-6
+    assert nrmse(h(iters_g), h(iters_e)) < 1e-6
+    # the cached graph is replayed on an identical call
+    x_g2, st_g2 = cs.recon_solve(plan, yt, mt, 5e-3, regc, cs.SolveParams(iterates=iters_g, use_graph=True, **kw),
+                                 wavelet_levels=3)
+    assert st_g2["graph_used"] == 1 and nrmse(h(x_g2), h(x_e)) < 1e-6
+    # a different lambda is a different graph
+    x_l, _ = cs.recon_solve(plan, yt, mt, 1e-2, regc, cs.SolveParams(use_graph=True, **kw), wavelet_levels=3)
+    x_le, _ = cs.recon_solve(plan, yt, mt, 1e-2, regc, cs.SolveParams(**kw), wavelet_levels=3)
+    assert nrmse(h(x_l), h(x_le)) < 1e-6
