@@ -1,0 +1,133 @@
+"""Micro-benchmarks of single operators on synthetic inputs (CUDA-event timing on the current
+stream), for profiling individual kernels with small launch counts.
+
+  python -m paper_2305_06482_gb300.microbench nufft  [--config cones3d_128|cones3d_large] [--warmup W] [--iters N]
+      multicoil NUFFT forward (sense_fwd) and adjoint (sense_adj), all coils
+  python -m paper_2305_06482_gb300.microbench sketch [--voxels D] [--iters N]
+      sketched maps (40 coils, V = 5, S = 5): FP32 CUDA cores vs BF16 split on the tensor cores
+  python -m paper_2305_06482_gb300.microbench cart2d [--iters N]
+      128x128 Cartesian coil-sketched CG reconstruction (8 coils, m = 4, T = 5, K = 10),
+      eager launches vs a replayed CUDA graph
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import paper_2305_06482_gb300 as cs  # noqa: E402
+import synthdata  # noqa: E402
+
+CONFIGS = {
+    "cones3d_128": dict(img=(128, 128, 128), grid=(160, 160, 160), nc=32, n_int=6000),
+    "cones3d_large": dict(img=(160, 256, 256), grid=(200, 320, 320), nc=40, n_int=20000),
+}
+
+
+def _events():
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def nufft(args):
+    cfg = CONFIGS[args.config]
+    dev = torch.device("cuda")
+    img, grid, C = cfg["img"], cfg["grid"], cfg["nc"]
+    traj = synthdata.cones_trajectory(cfg["n_int"], 512)
+    dcf = synthdata.cones_dcf(traj, img, cfg["n_int"], 512)
+    plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=torch.from_numpy(traj).to(dev), dcf=torch.from_numpy(dcf).to(dev),
+                   grid=grid)
+    x = synthdata.phantom_torch(img, seed=1, device=dev)
+    maps = synthdata.coil_maps_torch(img, C, device=dev)
+    y = torch.empty((C, traj.shape[0]), dtype=torch.complex64, device=dev)
+    xa = torch.empty(img, dtype=torch.complex64, device=dev)
+    for _ in range(args.warmup):
+        cs.sense_fwd(plan, x, maps, y)
+        cs.sense_adj(plan, y, maps, xa)
+    torch.cuda.synchronize()
+    a, b = _events()
+    c, d = _events()
+    a.record()
+    for _ in range(args.iters):
+        cs.sense_fwd(plan, x, maps, y)
+    b.record()
+    for _ in range(args.iters):
+        cs.sense_adj(plan, y, maps, xa)
+    d.record()
+    torch.cuda.synchronize()
+    f = a.elapsed_time(b) / args.iters
+    g = b.elapsed_time(d) / args.iters
+    D, G, N = int(np.prod(img)), int(np.prod(grid)), traj.shape[0]
+    model = 2 * C * (8 * D + 48 * G + 8 * N) + 2 * (16 * N + 16 * D)
+    print(f"{args.config}: forward {f:.3f} ms, adjoint {g:.3f} ms, fwd+adj model bytes {model / 1e9:.2f} GB "
+          f"-> {model / ((f + g) * 1e-3) / 1e9:.0f} GB/s")
+
+
+def sketch(args):
+    dev = torch.device("cuda")
+    C, V, S, D = 40, 5, 5, args.voxels
+    m = torch.randn((C, D), dtype=torch.complex64, device=dev)
+    sk = cs.sketch_draw(4, 0, 1, C, V, S)[0].contiguous()
+    out = torch.empty((S, D), dtype=torch.complex64, device=dev)
+    res = {}
+    for prec, name in [(cs.PREC_FP32, "fp32"), (cs.PREC_BF16_SPLIT, "bf16_split")]:
+        for _ in range(2):
+            cs.sketched_maps(sk, m, V, precision=prec, out=out)
+        torch.cuda.synchronize()
+        a, b = _events()
+        a.record()
+        for _ in range(args.iters):
+            cs.sketched_maps(sk, m, V, precision=prec, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.iters
+        byt = (C - V) * D * 8 + S * D * 8
+        res[name] = out.clone()
+        print(f"sketched maps {name}: D={D}: {ms:.3f} ms, {byt / ms / 1e6:.0f} GB/s algorithmic")
+    cs.device_status()
+    err = float((res["bf16_split"] - res["fp32"]).norm() / res["fp32"].norm())
+    print(f"bf16 split vs fp32 NRMSE {err:.2e}")
+
+
+def cart2d(args):
+    dev = torch.device("cuda")
+    shape, C = (128, 128), 8
+    mask = synthdata.poisson_disc_mask(shape, R=4.0, centre=24, seed=2)
+    idx = np.flatnonzero(mask.ravel()).astype(np.int32)
+    maps = torch.from_numpy(synthdata.coil_maps(shape, C).astype(np.complex64)).to(dev)
+    x_true = torch.from_numpy(synthdata.phantom(shape, seed=1).astype(np.complex64)).to(dev)
+    plan = cs.Plan(cs.CARTESIAN, shape, C, mask_idx=torch.from_numpy(idx).to(dev))
+    y = cs.sense_fwd(plan, x_true, maps)
+    for g in (False, True):
+        p = cs.SolveParams(T=5, K=10, V=2, S=2, use_graph=g)
+        for _ in range(3):
+            cs.recon_solve(plan, y, maps, 1e-3, cs.REG_L2, p)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.iters):
+            _, st = cs.recon_solve(plan, y, maps, 1e-3, cs.REG_L2, p)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.iters
+        print(f"cart2d recon use_graph={g}: {dt * 1e3:.3f} ms wall, {st['ms_total']:.3f} ms device")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["nufft", "sketch", "cart2d"])
+    ap.add_argument("--config", default="cones3d_128", choices=list(CONFIGS))
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--iters", type=int, default=5)
+    ap.add_argument("--voxels", type=int, default=160 * 256 * 256)
+    args = ap.parse_args()
+    {"nufft": nufft, "sketch": sketch, "cart2d": cart2d}[args.what](args)
+
+
+if __name__ == "__main__":
+    main()
