@@ -248,6 +248,27 @@ cs_status recon_solve(const cs_plan* plan, const cs_problem* problem, const cs_s
                       float* x_inout, cs_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------------------------------
+ * recon_solve_batched: many independent reconstructions (e.g. the 2D slices of a volume, each
+ * with its own size, plan, maps and data; the paper reconstructs slices separately, Sec. 3.1-3.2)
+ * in one call.  Every item has its own plan (plans must be distinct); the solves share `params`
+ * (sketches are drawn per item from params->seed; params->sketches and params->iterates must be
+ * NULL).  The items are forked onto a pool of streams and joined on `stream`; with
+ * params->use_graph all of them are captured once into ONE CUDA graph (cached for identical
+ * calls) and launched with a single cudaGraphLaunch.  Synchronises; stats (optional) is an array
+ * of nslices entries.  For FISTA with step == 0 every item gives its own power-iteration start
+ * vector (power_v0 of the item, the size of its image).
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    cs_plan* plan;
+    cs_problem problem;
+    float* x_inout;          /* device [image of this plan]                                  */
+    const float* power_v0;   /* device [image of this plan] or NULL                          */
+} cs_batch_item;
+
+cs_status recon_solve_batched(int nslices, const cs_batch_item* items, const cs_solve_params* params,
+                              cs_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------------------------
  * Regulariser building blocks (Sec. 2.1, l1-wavelets with a unitary Psi), exposed for testing:
  * periodised orthonormal db4 analysis/synthesis over all axes of an image, `levels` levels,
  * Mallat corner layout, and the complex soft threshold z max(0, 1 - tau/|z|).

@@ -56,6 +56,11 @@ class _Params(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("iterates", ctypes.c_void_p)]
 
 
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("problem", _Problem), ("x_inout", ctypes.c_void_p),
+                ("power_v0", ctypes.c_void_p)]
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [("L", ctypes.c_double), ("final_rr", ctypes.c_double), ("outer_done", ctypes.c_int),
                 ("graph_used", ctypes.c_int), ("ms_total", ctypes.c_double), ("ms_pca", ctypes.c_double)]
@@ -65,7 +70,7 @@ EXPORTED = [
     "cs_last_error", "cs_version", "cs_plan_create", "cs_plan_destroy", "cs_plan_binning", "sense_fwd",
     "sense_adj", "sense_grad", "sketched_normal_apply", "coil_pca", "coil_rotate", "sketch_draw",
     "cs_philox4x32_10", "sketched_maps", "recon_solve", "wavelet_fwd", "wavelet_inv", "soft_threshold",
-    "cs_hermitian_eig_host", "cs_launch_count", "cs_profile", "cs_profile_read", "coil_pca_noalloc", "cs_device_status",
+    "cs_hermitian_eig_host", "cs_launch_count", "cs_profile", "cs_profile_read", "coil_pca_noalloc", "cs_device_status", "recon_solve_batched",
 ]
 STAGES = {"spread": 0, "interp": 1, "fft_plain": 2, "expand": 3, "reduce": 4}
 
@@ -96,7 +101,7 @@ def lib():
             "soft_threshold": ([vp, i64, f, vp], i), "cs_hermitian_eig_host": ([vp, i, vp, vp], i),
             "cs_launch_count": ([], ctypes.c_longlong), "cs_profile": ([i], i),
             "cs_profile_read": ([i, vp, vp], i), "coil_pca_noalloc": ([vp, i, i64, vp, vp, vp], i),
-            "cs_device_status": ([vp], i),
+            "cs_device_status": ([vp], i), "recon_solve_batched": ([i, vp, vp, vp, vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -377,3 +382,38 @@ def recon_solve(plan: Plan, y, maps, lam, reg=REG_L2, params: SolveParams = None
                              _stream(stream)))
     return x, {"L": st.L, "final_rr": st.final_rr, "outer_done": st.outer_done, "graph_used": st.graph_used,
                "ms_total": st.ms_total, "ms_pca": st.ms_pca}
+
+
+def _params_struct(params: SolveParams):
+    return _Params(T=params.T, K=params.K, sketch=int(params.sketch), V=params.V, S=params.S, dist=params.dist,
+                   norm=params.norm, seed=params.seed,
+                   sketches=None if params.sketches is None else params.sketches.data_ptr(),
+                   do_pca=int(params.do_pca), precision=params.precision, step=float(params.step),
+                   power_iters=params.power_iters,
+                   power_v0=None if params.power_v0 is None else params.power_v0.data_ptr(),
+                   use_graph=int(params.use_graph),
+                   iterates=None if params.iterates is None else params.iterates.data_ptr())
+
+
+def recon_solve_batched(items, lam, reg=REG_L2, params: SolveParams = None, wavelet_levels=4, stream=None):
+    """Independent reconstructions (plan, y, maps[, x0][, power_v0]) in one call; with
+    params.use_graph all of them run as one cached CUDA graph.  Returns (list of x, list of stats)."""
+    params = params or SolveParams()
+    n = len(items)
+    arr = (_BatchItem * n)()
+    xs = []
+    for i, it in enumerate(items):
+        plan, y, maps = it["plan"], it["y"], it["maps"]
+        x = it.get("x0")
+        x = torch.zeros(plan.img, dtype=torch.complex64, device=y.device) if x is None else x.clone()
+        xs.append(x)
+        v0 = it.get("power_v0")
+        arr[i].plan = plan.handle.value
+        arr[i].problem = _Problem(y=y.data_ptr(), maps=maps.data_ptr(), C=maps.shape[0], lam=float(lam), reg=int(reg),
+                                  wavelet_levels=int(wavelet_levels))
+        arr[i].x_inout = x.data_ptr()
+        arr[i].power_v0 = None if v0 is None else v0.data_ptr()
+    sp = _params_struct(params)
+    st = (_Stats * n)()
+    _check(lib().recon_solve_batched(n, arr, ctypes.byref(sp), st, _stream(stream)))
+    return xs, [{"L": s.L, "final_rr": s.final_rr, "graph_used": s.graph_used} for s in st]

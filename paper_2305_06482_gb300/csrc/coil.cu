@@ -440,6 +440,30 @@ static int sm_count() {
     return n;
 }
 
+// dynamic shared-memory limits for up to 64 coils (set once per device at plan creation)
+cs_status coil_init_attrs() {
+    CS_TRY_CUDA(cudaFuncSetAttribute(cov_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(float2) * 64 * kCovTile)));
+    CS_TRY_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(double) * 4 * 64 * 64)));
+    CS_TRY_CUDA(cudaFuncSetAttribute(rotate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(float2) * (64 * 64 + 64 * kRotCols))));
+    return CS_OK;
+}
+
+static cs_status coil_attrs_once() {
+    static std::mutex mu;
+    static bool done[128] = {false};
+    int dev = 0;
+    CS_TRY_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 128 && !done[dev]) {
+        CS_PROPAGATE(coil_init_attrs());
+        done[dev] = true;
+    }
+    return CS_OK;
+}
+
 cs_status coil_pca_impl(const float2* y, int C, int64_t N, float2* U, double* eig, double* Rws, cudaStream_t st) {
     CS_TRY_CUDA(cudaMemsetAsync(Rws, 0, sizeof(double) * 2 * C * C, st));
     const int nb = (C + 3) / 4;
@@ -447,13 +471,11 @@ cs_status coil_pca_impl(const float2* y, int C, int64_t N, float2* U, double* ei
     const int threads = npairs > 256 ? ((npairs + 31) / 32) * 32 : 256;
     CS_REQUIRE(threads <= 1024, CS_ERR_UNSUPPORTED_SIZE, "too many coils for coil_pca");
     const size_t sm = sizeof(float2) * C * kCovTile;
-    CS_TRY_CUDA(cudaFuncSetAttribute(cov_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int64_t tiles = (N + kCovTile - 1) / kCovTile;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sm_count() * 4));
     cov_kernel<<<grid, threads, sm, st>>>(y, C, N, Rws);
     CS_LAUNCH_CHECK();
     const size_t jsm = sizeof(double) * 4 * C * C;
-    CS_TRY_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm));
     jacobi_kernel<<<1, 64, jsm, st>>>(Rws, C, U, eig);
     CS_LAUNCH_CHECK();
     return CS_OK;
@@ -463,7 +485,6 @@ cs_status coil_rotate_impl(const float2* U, const float2* in, int C, int Cout, i
     const int groups = (Cout + 7) / 8;
     const int threads = kRotCols * groups;
     const size_t sm = sizeof(float2) * ((size_t)C * C + (size_t)C * kRotCols);
-    CS_TRY_CUDA(cudaFuncSetAttribute(rotate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int64_t blocks = (L + kRotCols - 1) / kRotCols;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sm_count() * 8));
     rotate_kernel<<<grid, threads, sm, st>>>(U, in, C, Cout, L, out);
@@ -539,6 +560,7 @@ cs_status coil_pca_noalloc(const float* y, int C, int64_t N, float* U, double* e
     CS_REQUIRE(C >= 1 && C <= kNoAllocMaxCoils, CS_ERR_UNSUPPORTED_SIZE,
                "coil_pca_noalloc supports at most %d coils (got %d); use coil_pca", kNoAllocMaxCoils, C);
     double* R = nullptr;
+    CS_PROPAGATE(coil_attrs_once());
     CS_PROPAGATE(pca_scratch_address(&R));
     // coil_pca_impl clears R on `stream` before accumulating into it
     return coil_pca_impl((const float2*)y, C, N, (float2*)U, eig, R, (cudaStream_t)stream);
@@ -572,6 +594,7 @@ cs_status coil_pca(const float* y, int C, int64_t N, float* U, double* eig, void
     clear_error();
     CS_REQUIRE(y && U && eig && C >= 1 && C <= 64 && N >= 1, CS_ERR_INVALID_ARG, "bad coil_pca arguments");
     cudaStream_t st = (cudaStream_t)stream;
+    CS_PROPAGATE(coil_attrs_once());
     double* R = nullptr;
     CS_TRY_CUDA(cudaMallocAsync(&R, sizeof(double) * 2 * C * C, st));
     cs_status rc = coil_pca_impl((const float2*)y, C, N, (float2*)U, eig, R, st);
@@ -585,6 +608,7 @@ cs_status coil_rotate(const float* U, const float* in, int C, int C_out, int64_t
                "bad coil_rotate arguments");
     CS_REQUIRE(in != out, CS_ERR_INVALID_ARG, "coil_rotate cannot run in place");
     if (C_out == 0 || L == 0) return CS_OK;
+    CS_PROPAGATE(coil_attrs_once());
     return coil_rotate_impl((const float2*)U, (const float2*)in, C, C_out, L, (float2*)out, (cudaStream_t)stream);
 }
 

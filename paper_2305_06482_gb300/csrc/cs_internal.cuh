@@ -167,6 +167,7 @@ void solver_ws_free(cs_plan* p);
 cs_status fft_init_attrs();
 cs_status tc_init_attrs();
 cs_status wavelet_init_constants();
+cs_status coil_init_attrs();
 
 // Jacobi eigensolver (shared host/device algorithm, coil.cu)
 void hermitian_eig_serial(double* A, int n, double* V, double* evals);

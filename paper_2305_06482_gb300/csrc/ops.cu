@@ -146,6 +146,7 @@ static cs_status device_init_once() {
     CS_PROPAGATE(fft_init_attrs());
     CS_PROPAGATE(tc_init_attrs());
     CS_PROPAGATE(wavelet_init_constants());
+    CS_PROPAGATE(coil_init_attrs());
     done[dev] = true;
     return CS_OK;
 }

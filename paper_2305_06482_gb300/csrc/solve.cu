@@ -225,6 +225,22 @@ __global__ void inc_kernel(int* c) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *c += 1;
 }
 
+__global__ void set_eta_kernel(Scal* sc, double eta) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) sc->eta = eta;
+}
+
+// FISTA momentum coefficients theta_k = (t_{k-1} - 1) / t_k, t_0 = 1, t_k = (1 + sqrt(1 + 4 t_{k-1}^2)) / 2
+__global__ void theta_kernel(float* theta, int K) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double t = 1.0;
+        for (int k = 0; k < K; ++k) {
+            const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+            theta[k] = (float)((t - 1.0) / tn);
+            t = tn;
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // periodised orthonormal db4 (8 taps) along one axis of the corner block, in place per line.
 // Analysis: a[k] = sum_m h[m] x[(2k+m) mod M], d[k] = sum_m g[m] x[(2k+m) mod M], g[m] = (-1)^m h[7-m],
@@ -668,8 +684,20 @@ static cs_status run_body(SolverWS* ws, bool use_graph, uint64_t sig, int reps, 
     return CS_OK;
 }
 
-static cs_status recon_solve_impl(cs_plan* p, const cs_problem* pr, const cs_solve_params* sp, float2* x,
-                                  cs_stats* stats, cudaStream_t st) {
+// Enqueue a whole solve on `st` (no host synchronisation).  With allow_graph == false the
+// iterations are launched directly even if sp->use_graph is set (used inside an outer capture).
+struct SolveEvents {
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    int graph_used = 0;
+    ~SolveEvents() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (e2) cudaEventDestroy(e2);
+    }
+};
+
+static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_params* sp, float2* x, cudaStream_t st,
+                               bool allow_graph, SolveEvents* ev) {
     const int64_t D = p->D, N = p->N;
     const int C = pr->C;
     const bool sketch = sp->sketch != 0;
@@ -692,23 +720,16 @@ static cs_status recon_solve_impl(cs_plan* p, const cs_problem* pr, const cs_sol
     CS_TRY_CUDA(cudaMemsetAsync(ws->sc, 0, sizeof(Scal), st));
     CS_TRY_CUDA(cudaMemsetAsync(ws->tdev, 0, sizeof(int), st));
     if (sp->step > 0) {
-        Scal h = {};
-        h.eta = sp->step;
-        CS_TRY_CUDA(cudaMemcpyAsync(ws->sc, &h, sizeof(Scal), cudaMemcpyHostToDevice, st));
+        set_eta_kernel<<<1, 32, 0, st>>>(ws->sc, (double)sp->step);
+        CS_LAUNCH_CHECK();
     }
-    cudaEvent_t e0, e1, e2;
-    CS_TRY_CUDA(cudaEventCreate(&e0));
-    CS_TRY_CUDA(cudaEventCreate(&e1));
-    CS_TRY_CUDA(cudaEventCreate(&e2));
-    struct EvGuard {
-        cudaEvent_t a, b, c;
-        ~EvGuard() {
-            cudaEventDestroy(a);
-            cudaEventDestroy(b);
-            cudaEventDestroy(c);
-        }
-    } evg{e0, e1, e2};
-    CS_TRY_CUDA(cudaEventRecord(e0, st));
+    if (ev) {
+        CS_TRY_CUDA(cudaEventCreate(&ev->e0));
+        CS_TRY_CUDA(cudaEventCreate(&ev->e1));
+        CS_TRY_CUDA(cudaEventCreate(&ev->e2));
+        CS_TRY_CUDA(cudaEventRecord(ev->e0, st));
+    }
+
 
     const float2* maps = (const float2*)pr->maps;
     const float2* y = (const float2*)pr->y;
@@ -719,11 +740,11 @@ static cs_status recon_solve_impl(cs_plan* p, const cs_problem* pr, const cs_sol
         maps = ws->maps_r;
         y = ws->y_r;
     }
-    CS_TRY_CUDA(cudaEventRecord(e1, st));
+    if (ev) CS_TRY_CUDA(cudaEventRecord(ev->e1, st));
 
     const bool fista = pr->reg == CS_REG_L1_WAVELET;
     const std::vector<float> theta = fista_thetas(std::max(K, 1));
-    const bool use_graph = sp->use_graph != 0;
+    const bool use_graph = sp->use_graph != 0 && allow_graph;
     int graph_used = 0;
     // signature of everything a captured body depends on
     uint64_t sig = 1469598103934665603ull;
@@ -776,7 +797,8 @@ static cs_status recon_solve_impl(cs_plan* p, const cs_problem* pr, const cs_sol
             CS_PROPAGATE(power_iteration(c, (const float2*)sp->power_v0, sp->power_iters > 0 ? sp->power_iters : 20,
                                          maps, C, nullptr, 0, ws->u, ws->hp));
         }
-        CS_TRY_CUDA(cudaMemcpyAsync(ws->theta, theta.data(), sizeof(float) * theta.size(), cudaMemcpyHostToDevice, st));
+        theta_kernel<<<1, 32, 0, st>>>(ws->theta, std::max(K, 1));
+        CS_LAUNCH_CHECK();
         CS_TRY_CUDA(cudaMemcpyAsync(ws->z, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
         CS_TRY_CUDA(cudaMemcpyAsync(ws->xp, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
         auto body = [&](cudaStream_t s) -> cs_status {
@@ -820,24 +842,153 @@ static cs_status recon_solve_impl(cs_plan* p, const cs_problem* pr, const cs_sol
         };
         CS_PROPAGATE(run_body(ws, use_graph, sig, K, st, body, &graph_used));
     }
-    CS_TRY_CUDA(cudaEventRecord(e2, st));
+    if (ev) {
+        CS_TRY_CUDA(cudaEventRecord(ev->e2, st));
+        ev->graph_used = graph_used;
+    }
+    return CS_OK;
+}
+
+// Synchronise, fill stats, report non-finite reductions and tensor-core timeouts.
+static cs_status recon_finish(cs_plan* p, const cs_solve_params* sp, cudaStream_t st, SolveEvents* ev, cs_stats* stats) {
+    SolverWS* ws = static_cast<SolverWS*>(p->solver_ws);
     CS_TRY_CUDA(cudaStreamSynchronize(st));
     Scal h;
-    CS_TRY_CUDA(cudaMemcpy(&h, c.sc, sizeof(Scal), cudaMemcpyDeviceToHost));
+    CS_TRY_CUDA(cudaMemcpy(&h, ws->sc, sizeof(Scal), cudaMemcpyDeviceToHost));
     if (stats) {
         float ms_all = 0, ms_pca = 0;
-        cudaEventElapsedTime(&ms_all, e0, e2);
-        cudaEventElapsedTime(&ms_pca, e0, e1);
+        if (ev && ev->e0) {
+            cudaEventElapsedTime(&ms_all, ev->e0, ev->e2);
+            cudaEventElapsedTime(&ms_pca, ev->e0, ev->e1);
+        }
         stats->L = h.L;
-        stats->final_rr = h.rr[K & 1];
-        stats->outer_done = sketch ? T : 0;
-        stats->graph_used = graph_used;
+        stats->final_rr = h.rr[sp->K & 1];
+        stats->outer_done = sp->sketch ? sp->T : 0;
+        stats->graph_used = ev ? ev->graph_used : 0;
         stats->ms_total = ms_all;
         stats->ms_pca = ms_pca;
     }
     CS_PROPAGATE(tc_check_and_clear());
     CS_REQUIRE(!h.nonfinite, CS_ERR_NONFINITE, "a solver reduction produced a non-finite value");
     return CS_OK;
+}
+
+static cs_status recon_solve_impl(cs_plan* p, const cs_problem* pr, const cs_solve_params* sp, float2* x,
+                                  cs_stats* stats, cudaStream_t st) {
+    SolveEvents ev;
+    CS_PROPAGATE(recon_enqueue(p, pr, sp, x, st, true, &ev));
+    return recon_finish(p, sp, st, &ev, stats);
+}
+
+// ------------------------------------------------------------------------------------------
+// Batched independent solves (many slices of uneven size): every slice has its own plan and
+// workspace; the solves are forked onto a pool of streams and joined, either launched directly
+// or captured once - all slices in one CUDA graph - cached and replayed.
+struct BatchCache {
+    std::vector<cudaStream_t> pool;
+    cudaStream_t cap = nullptr;
+    std::vector<cudaEvent_t> evs;
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t sig = 0;
+};
+
+static BatchCache& batch_cache() {
+    static BatchCache bc;
+    return bc;
+}
+
+static cs_status batch_streams(BatchCache& bc, int n) {
+    while ((int)bc.pool.size() < n) {
+        cudaStream_t s = nullptr;
+        CS_TRY_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        bc.pool.push_back(s);
+    }
+    while ((int)bc.evs.size() < 2 * n + 2) {
+        cudaEvent_t e = nullptr;
+        CS_TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        bc.evs.push_back(e);
+    }
+    if (!bc.cap) CS_TRY_CUDA(cudaStreamCreateWithFlags(&bc.cap, cudaStreamNonBlocking));
+    return CS_OK;
+}
+
+// fork: every branch waits for `root`; join: root waits for every branch
+static cs_status batch_enqueue(BatchCache& bc, int n, const cs_batch_item* items, const cs_solve_params* sp,
+                               cudaStream_t root) {
+    const int nb = std::min(n, 32);
+    CS_TRY_CUDA(cudaEventRecord(bc.evs[0], root));
+    for (int b = 0; b < nb; ++b) CS_TRY_CUDA(cudaStreamWaitEvent(bc.pool[b], bc.evs[0], 0));
+    for (int i = 0; i < n; ++i) {
+        const cs_batch_item& it = items[i];
+        cs_solve_params one = *sp;
+        one.power_v0 = it.power_v0;
+        CS_PROPAGATE(recon_enqueue(it.plan, &it.problem, &one, (float2*)it.x_inout, bc.pool[i % nb], false, nullptr));
+    }
+    for (int b = 0; b < nb; ++b) {
+        CS_TRY_CUDA(cudaEventRecord(bc.evs[1 + b], bc.pool[b]));
+        CS_TRY_CUDA(cudaStreamWaitEvent(root, bc.evs[1 + b], 0));
+    }
+    return CS_OK;
+}
+
+static cs_status recon_batched_impl(int n, const cs_batch_item* items, const cs_solve_params* sp, cs_stats* stats,
+                                    cudaStream_t st) {
+    BatchCache& bc = batch_cache();
+    CS_PROPAGATE(batch_streams(bc, std::min(n, 32)));
+    // make sure every slice's workspace exists before any capture (allocation is not capturable)
+    for (int i = 0; i < n; ++i) {
+        cs_plan* p = items[i].plan;
+        const int C = items[i].problem.C;
+        const int V = sp->sketch ? sp->V : C, S = sp->sketch ? sp->S : 0;
+        if (!p->solver_ws) p->solver_ws = new SolverWS();
+        CS_PROPAGATE(static_cast<SolverWS*>(p->solver_ws)->ensure(p->D, p->N, C, S, C - V, sp->T, sp->K));
+    }
+    int graph_used = 0;
+    if (sp->use_graph) {
+        uint64_t sig = 1469598103934665603ull;
+        sig = fnv(sig, items, sizeof(cs_batch_item) * n);
+        sig = fnv(sig, sp, sizeof(cs_solve_params));
+        if (!bc.gexec || bc.sig != sig) {
+            if (bc.gexec) cudaGraphExecDestroy(bc.gexec);
+            bc.gexec = nullptr;
+            CS_TRY_CUDA(cudaStreamBeginCapture(bc.cap, cudaStreamCaptureModeThreadLocal));
+            cs_status rc = batch_enqueue(bc, n, items, sp, bc.cap);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(bc.cap, &g);
+            if (rc != CS_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) {
+                set_error("batched graph capture failed: %s", cudaGetErrorString(e));
+                return CS_ERR_CUDA;
+            }
+            e = cudaGraphInstantiate(&bc.gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                bc.gexec = nullptr;
+                set_error("batched graph instantiation failed: %s", cudaGetErrorString(e));
+                return CS_ERR_CUDA;
+            }
+            bc.sig = sig;
+        }
+        CS_TRY_CUDA(cudaGraphLaunch(bc.gexec, st));
+        graph_used = 1;
+    } else {
+        CS_PROPAGATE(batch_enqueue(bc, n, items, sp, st));
+    }
+    CS_TRY_CUDA(cudaStreamSynchronize(st));
+    cs_status worst = CS_OK;
+    for (int i = 0; i < n; ++i) {
+        cs_stats one = {};
+        cs_status rc = recon_finish(items[i].plan, sp, st, nullptr, &one);
+        if (rc != CS_OK && worst == CS_OK) worst = rc;
+        if (stats) {
+            stats[i] = one;
+            stats[i].graph_used = graph_used;
+        }
+    }
+    return worst;
 }
 
 }  // namespace cs
@@ -861,6 +1012,28 @@ cs_status recon_solve(const cs_plan* p, const cs_problem* pr, const cs_solve_par
         CS_REQUIRE(sp->S == 0 || sp->V < pr->C, CS_ERR_INVALID_ARG, "S > 0 needs V < C");
     }
     return recon_solve_impl(const_cast<cs_plan*>(p), pr, sp, (float2*)x_inout, stats, (cudaStream_t)stream);
+}
+
+cs_status recon_solve_batched(int nslices, const cs_batch_item* items, const cs_solve_params* params, cs_stats* stats,
+                              void* stream) {
+    clear_error();
+    CS_REQUIRE(nslices >= 1 && items && params, CS_ERR_INVALID_ARG, "bad batched solve arguments");
+    for (int i = 0; i < nslices; ++i) {
+        const cs_batch_item& it = items[i];
+        CS_REQUIRE(it.plan && it.x_inout && it.problem.y && it.problem.maps && it.problem.C >= 1 &&
+                       it.problem.C <= it.plan->max_coils,
+                   CS_ERR_INVALID_ARG, "batch item %d: bad plan/problem", i);
+        for (int j = 0; j < i; ++j)
+            CS_REQUIRE(items[j].plan != it.plan, CS_ERR_INVALID_ARG, "batch items %d and %d share a plan", j, i);
+    }
+    if (params->sketch) {
+        CS_REQUIRE(params->V >= 0 && params->S >= 0 && params->V + params->S >= 1, CS_ERR_INVALID_ARG, "bad V/S");
+        for (int i = 0; i < nslices; ++i)
+            CS_REQUIRE(params->V + params->S <= items[i].problem.C, CS_ERR_INVALID_ARG, "V + S > C in item %d", i);
+        CS_REQUIRE(params->sketches == nullptr, CS_ERR_INVALID_ARG, "batched solves draw their own sketches");
+    }
+    CS_REQUIRE(params->iterates == nullptr, CS_ERR_INVALID_ARG, "batched solves do not record iterates");
+    return recon_batched_impl(nslices, items, params, stats, (cudaStream_t)stream);
 }
 
 cs_status wavelet_fwd(const float* x, int ndim, const int* dims, int levels, float* c, void* stream) {

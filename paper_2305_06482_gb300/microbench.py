@@ -5,6 +5,10 @@ stream), for profiling individual kernels with small launch counts.
       multicoil NUFFT forward (sense_fwd) and adjoint (sense_adj), all coils
   python -m paper_2305_06482_gb300.microbench sketch [--voxels D] [--iters N]
       sketched maps (40 coils, V = 5, S = 5): FP32 CUDA cores vs BF16 split on the tensor cores
+  python -m paper_2305_06482_gb300.microbench batched [--slices 64] [--iters N]
+      64 2D Cartesian slices of uneven size (256..384 squared), 16 coils, line mask R = 6 with
+      24 centre lines, l1-db4 FISTA (lambda 5e-3), sketch m = 6 (3 PCA + 3 Gaussian), T = 10, K = 10:
+      one slice after another vs all slices forked and joined vs all slices in one CUDA graph
   python -m paper_2305_06482_gb300.microbench cart2d [--iters N]
       128x128 Cartesian coil-sketched CG reconstruction (8 coils, m = 4, T = 5, K = 10),
       eager launches vs a replayed CUDA graph
@@ -118,15 +122,54 @@ def cart2d(args):
         print(f"cart2d recon use_graph={g}: {dt * 1e3:.3f} ms wall, {st['ms_total']:.3f} ms device")
 
 
+def batched(args):
+    dev = torch.device("cuda")
+    C = 16
+    sizes = synthdata.slice_sizes(args.slices)
+    items = []
+    for k, n in enumerate(sizes):
+        shape = (n, n)
+        mask = synthdata.line_mask(shape, R=6.0, centre_lines=24, seed=200 + k)
+        idx = np.flatnonzero(mask.ravel()).astype(np.int32)
+        maps = synthdata.coil_maps_torch(shape, C, device=dev)
+        x_true = synthdata.phantom_torch(shape, seed=300 + k, device=dev)
+        plan = cs.Plan(cs.CARTESIAN, shape, C, mask_idx=torch.from_numpy(idx).to(dev))
+        y = cs.sense_fwd(plan, x_true, maps)
+        y += 1e-3 * y.abs().max() * torch.randn_like(y)
+        items.append(dict(plan=plan, y=y, maps=maps, power_v0=synthdata.phantom_torch(shape, seed=500 + k, device=dev)))
+    D_total = sum(n * n for n in sizes)
+    common = dict(T=10, K=10, V=3, S=3, seed=4)
+
+    def run_seq():
+        for it in items:
+            cs.recon_solve(it["plan"], it["y"], it["maps"], 5e-3, cs.REG_L1_WAVELET,
+                           cs.SolveParams(power_v0=it["power_v0"], **common))
+
+    def run_batch(g):
+        cs.recon_solve_batched(items, 5e-3, cs.REG_L1_WAVELET, cs.SolveParams(use_graph=g, **common))
+
+    for name, fn in [("one slice after another", run_seq), ("forked batch", lambda: run_batch(False)),
+                     ("one CUDA graph", lambda: run_batch(True))]:
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.iters):
+            fn()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.iters
+        print(f"batched slices ({len(sizes)} slices, {D_total / 1e6:.2f} M pixels, 16 coils): {name}: {dt * 1e3:.1f} ms")
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["nufft", "sketch", "cart2d"])
+    ap.add_argument("what", choices=["nufft", "sketch", "cart2d", "batched"])
+    ap.add_argument("--slices", type=int, default=64)
     ap.add_argument("--config", default="cones3d_128", choices=list(CONFIGS))
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--iters", type=int, default=5)
     ap.add_argument("--voxels", type=int, default=160 * 256 * 256)
     args = ap.parse_args()
-    {"nufft": nufft, "sketch": sketch, "cart2d": cart2d}[args.what](args)
+    {"nufft": nufft, "sketch": sketch, "cart2d": cart2d, "batched": batched}[args.what](args)
 
 
 if __name__ == "__main__":
