@@ -291,10 +291,13 @@ __global__ void sample_record_kernel(const float* __restrict__ gs, const float* 
     r[15] = 0.f;
 }
 
-// lanes 0..15 load one word of the sample's record; every lane gets the weights by shuffles
+// lane l holds word (l mod 16) of the sample's record; every lane gets the weights by shuffles
+__device__ __forceinline__ float rec_word(const GridArgs& A, int64_t s, int lane) {
+    return (s < A.N) ? __ldg(A.rec + s * kRec + (lane & (kRec - 1))) : 0.f;
+}
+
 template <int ND>
-__device__ __forceinline__ void sample_box(const GridArgs& A, int64_t s, int lane, SampleBox<ND>& B) {
-    const float w = A.rec[s * kRec + (lane & (kRec - 1))];
+__device__ __forceinline__ void sample_box(float w, int lane, SampleBox<ND>& B) {
 #pragma unroll
     for (int a = 0; a < kW; ++a) {
         B.wz[a] = __shfl_sync(0xffffffffu, w, a);
@@ -337,9 +340,11 @@ __global__ void __launch_bounds__(128) interp_kernel(GridArgs A, int mode, const
 #pragma unroll
     for (int p = 0; p < P; ++p) W.zc[p] = -1;
     int cy = -100, cx = -100;
+    float wnext = rec_word(A, s0, lane);
     for (int64_t s = s0; s < s1; ++s) {
         SampleBox<ND> B;
-        sample_box<ND>(A, s, lane, B);
+        sample_box<ND>(wnext, lane, B);
+        wnext = rec_word(A, s + 1, lane);   // prefetch the next sample's record
         const int dy = B.jy - cy, dx = B.jx - cx;
         if (abs(dy) > 1 || abs(dx) > 1) {
 #pragma unroll
@@ -504,9 +509,19 @@ __global__ void __launch_bounds__(128) spread_kernel(GridArgs A, const float2* _
 #pragma unroll
             for (int d = 0; d < kW; ++d) W.v[p][b][d] = make_float2(0.f, 0.f);
     };
+    float wnext = rec_word(A, s0, lane);
+    // the sample value: sorted scratch [N][C] (prefetched one sample ahead) or user order [C][N]
+    auto load_v = [&](int64_t s, int perm) -> float2 {
+        if (!active || s >= A.N) return make_float2(0.f, 0.f);
+        return sorted_in ? yin[s * A.C + c] : yin[(int64_t)c * A.N + perm];
+    };
+    float2 vnext = sorted_in ? load_v(s0, 0) : make_float2(0.f, 0.f);
     for (int64_t s = s0; s < s1; ++s) {
         SampleBox<ND> B;
-        sample_box<ND>(A, s, lane, B);
+        sample_box<ND>(wnext, lane, B);
+        float2 v = sorted_in ? vnext : load_v(s, B.perm);
+        wnext = rec_word(A, s + 1, lane);
+        if (sorted_in) vnext = load_v(s + 1, 0);
         const int dy = B.jy - cy, dx = B.jx - cx;
         if (abs(dy) > 1 || abs(dx) > 1) {
 #pragma unroll
@@ -580,8 +595,6 @@ __global__ void __launch_bounds__(128) spread_kernel(GridArgs A, const float2* _
         }
         cy = B.jy;
         cx = B.jx;
-        float2 v = make_float2(0.f, 0.f);
-        if (active) v = sorted_in ? yin[s * A.C + c] : yin[(int64_t)c * A.N + B.perm];
         v = cscale(v, B.sw);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
