@@ -269,6 +269,63 @@ cs_status recon_solve_batched(int nslices, const cs_batch_item* items, const cs_
                               cs_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------------------------------
+ * Sub-problem pieces for callers that drive Algorithm 1 themselves (e.g. with a warm start).
+ * sketched_subproblem_solve: K iterations (CG for CS_REG_L2, FISTA with step `step` for
+ *   CS_REG_L1_WAVELET) on the sketched sub-problem of Eq. 9-10,
+ *   min_x 1/2 ||A_S (x - x^t)||^2 + Re<x, d> + g(x),
+ *   starting from x_inout (x^t itself when x_inout == xt, else a warm start); x_inout receives
+ *   the result.  Sketched maps as in sketched_normal_apply.  Asynchronous.
+ * cs_subproblem_objective: the value of that objective at u (host double; synchronises).
+ * cs_power_iteration: largest eigenvalue of A_S^H A_S from v0 (host double; synchronises).
+ * ---------------------------------------------------------------------------------------- */
+cs_status sketched_subproblem_solve(const cs_plan* plan, const float* d, const float* xt, float* x_inout,
+                                    const float* maps_v, int V, const float* maps_s, int S, float lambda,
+                                    int reg, int wavelet_levels, int K, float step, void* stream);
+cs_status cs_subproblem_objective(const cs_plan* plan, const float* u, const float* xt, const float* d,
+                                  const float* maps_v, int V, const float* maps_s, int S, float lambda,
+                                  int reg, int wavelet_levels, double* value, void* stream);
+cs_status cs_power_iteration(const cs_plan* plan, const float* v0, const float* maps_v, int V,
+                             const float* maps_s, int S, int iters, double* L, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Learned warm start (not in the paper): a small 3D CNN maps the sub-problem's (x^t, d) to a
+ * correction of x^t; its prediction is used as the sub-problem's starting point only when the
+ * sub-problem objective confirms it.  Activations are voxel-major, channels fastest, FP32.
+ * cs_nn_conv3d: 3x3x3 convolution, zero padding 1, as a BF16 implicit GEMM on the tensor cores
+ *   (tcgen05, FP32 accumulation in tensor memory): out[v][coff + n] = bias[n] +
+ *   sum_{tap, c} in[v + s off(tap)][c] W[n][tap * cin + c] (+ ReLU), s = -1 when flip (the data
+ *   gradient, with weights packed transposed), else +1.  `packed` is [npad][kpad] BF16 from
+ *   cs_nn_pack_weights (npad in {16, 32, 64}, kpad >= 27 cin, multiple of 16).
+ * cs_nn_conv3d_wgrad: gw[co][tap][ci] += sum_v gout[v][co] in[v + off(tap)][ci]; gb += sum_v gout.
+ * cs_nn_conv1(_bwd): 1x1x1 layer; cs_nn_relu_bwd: g *= (act > 0); cs_nn_mse: loss += mean sq.
+ *   error, g = its gradient; cs_nn_adam: one Adam step (step >= 1).
+ * cs_nn_features / target / apply: network input [x^t / s, d eta / s] with s the RMS of
+ *   (x^t, eta d) (ss receives ||x^t||^2 + eta^2 ||d||^2), training target (x_sub - x^t) / s,
+ *   prediction x^t + s delta.
+ * cs_nn_status: synchronise and report a bounded tensor-core wait that gave up.
+ * ---------------------------------------------------------------------------------------- */
+cs_status cs_nn_pack_weights(const float* w, int cout, int cin, int transpose, unsigned short* packed,
+                             int npad, int kpad, void* stream);
+cs_status cs_nn_conv3d(const float* in, int nz, int ny, int nx, int cin, const unsigned short* packed,
+                       int npad, int kpad, int nout, const float* bias, int relu, int flip, float* out,
+                       int ldo, int coff, void* stream);
+cs_status cs_nn_conv3d_wgrad(const float* in, const float* gout, int nz, int ny, int nx, int cin, int cout,
+                             float* gw, float* gb, void* stream);
+cs_status cs_nn_relu_bwd(const float* act, float* g, int64_t n, void* stream);
+cs_status cs_nn_conv1(const float* in, int64_t nvox, int cin, int cout, const float* w, const float* b,
+                      float* out, void* stream);
+cs_status cs_nn_conv1_bwd(const float* in, const float* gout, int64_t nvox, int cin, int cout, const float* w,
+                          float* gin, float* gw, float* gb, void* stream);
+cs_status cs_nn_mse(const float* out, const float* tgt, int64_t n, float* g, float* loss, void* stream);
+cs_status cs_nn_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
+                     float eps, int step, void* stream);
+cs_status cs_nn_features(const float* xt, const float* d, int64_t n, float eta, float* ss, float* f,
+                         void* stream);
+cs_status cs_nn_target(const float* xt, const float* xs, int64_t n, const float* ss, float* tgt, void* stream);
+cs_status cs_nn_apply(const float* xt, const float* delta, int64_t n, const float* ss, float* out, void* stream);
+cs_status cs_nn_status(void* stream);
+
+/* ------------------------------------------------------------------------------------------
  * Regulariser building blocks (Sec. 2.1, l1-wavelets with a unitary Psi), exposed for testing:
  * periodised orthonormal db4 analysis/synthesis over all axes of an image, `levels` levels,
  * Mallat corner layout, and the complex soft threshold z max(0, 1 - tau/|z|).

@@ -71,6 +71,9 @@ EXPORTED = [
     "sense_adj", "sense_grad", "sketched_normal_apply", "coil_pca", "coil_rotate", "sketch_draw",
     "cs_philox4x32_10", "sketched_maps", "recon_solve", "wavelet_fwd", "wavelet_inv", "soft_threshold",
     "cs_hermitian_eig_host", "cs_launch_count", "cs_profile", "cs_profile_read", "coil_pca_noalloc", "cs_device_status", "recon_solve_batched",
+    "sketched_subproblem_solve", "cs_subproblem_objective", "cs_power_iteration", "cs_nn_pack_weights",
+    "cs_nn_conv3d", "cs_nn_conv3d_wgrad", "cs_nn_relu_bwd", "cs_nn_conv1", "cs_nn_conv1_bwd", "cs_nn_mse",
+    "cs_nn_adam", "cs_nn_features", "cs_nn_target", "cs_nn_apply", "cs_nn_status",
 ]
 STAGES = {"spread": 0, "interp": 1, "fft_plain": 2, "expand": 3, "reduce": 4}
 
@@ -102,6 +105,17 @@ def lib():
             "cs_launch_count": ([], ctypes.c_longlong), "cs_profile": ([i], i),
             "cs_profile_read": ([i, vp, vp], i), "coil_pca_noalloc": ([vp, i, i64, vp, vp, vp], i),
             "cs_device_status": ([vp], i), "recon_solve_batched": ([i, vp, vp, vp, vp], i),
+            "sketched_subproblem_solve": ([vp, vp, vp, vp, vp, i, vp, i, f, i, i, i, f, vp], i),
+            "cs_subproblem_objective": ([vp, vp, vp, vp, vp, i, vp, i, f, i, i, vp, vp], i),
+            "cs_power_iteration": ([vp, vp, vp, i, vp, i, i, vp, vp], i),
+            "cs_nn_pack_weights": ([vp, i, i, i, vp, i, i, vp], i),
+            "cs_nn_conv3d": ([vp, i, i, i, i, vp, i, i, i, vp, i, i, vp, i, i, vp], i),
+            "cs_nn_conv3d_wgrad": ([vp, vp, i, i, i, i, i, vp, vp, vp], i),
+            "cs_nn_relu_bwd": ([vp, vp, i64, vp], i), "cs_nn_conv1": ([vp, i64, i, i, vp, vp, vp, vp], i),
+            "cs_nn_conv1_bwd": ([vp, vp, i64, i, i, vp, vp, vp, vp, vp], i),
+            "cs_nn_mse": ([vp, vp, i64, vp, vp, vp], i), "cs_nn_adam": ([vp, vp, vp, vp, i64, f, f, f, f, i, vp], i),
+            "cs_nn_features": ([vp, vp, i64, f, vp, vp, vp], i), "cs_nn_target": ([vp, vp, i64, vp, vp, vp], i),
+            "cs_nn_apply": ([vp, vp, i64, vp, vp, vp], i), "cs_nn_status": ([vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -417,3 +431,33 @@ def recon_solve_batched(items, lam, reg=REG_L2, params: SolveParams = None, wave
     st = (_Stats * n)()
     _check(lib().recon_solve_batched(n, arr, ctypes.byref(sp), st, _stream(stream)))
     return xs, [{"L": s.L, "final_rr": s.final_rr, "graph_used": s.graph_used} for s in st]
+
+
+def sketched_subproblem_solve(plan: Plan, d, xt, x, maps_v, maps_s, lam, reg, K, step=0.0, wavelet_levels=4,
+                              stream=None):
+    """K solver iterations on the sketched sub-problem (Eq. 9-10) from x (in place); x^t = xt."""
+    V = 0 if maps_v is None else maps_v.shape[0]
+    S = 0 if maps_s is None else maps_s.shape[0]
+    _check(lib().sketched_subproblem_solve(plan.handle, _ptr(d), _ptr(xt), _ptr(x), _ptr(maps_v), V, _ptr(maps_s), S,
+                                           ctypes.c_float(lam), int(reg), int(wavelet_levels), int(K),
+                                           ctypes.c_float(step), _stream(stream)))
+    return x
+
+
+def subproblem_objective(plan: Plan, u, xt, d, maps_v, maps_s, lam, reg, wavelet_levels=4, stream=None):
+    V = 0 if maps_v is None else maps_v.shape[0]
+    S = 0 if maps_s is None else maps_s.shape[0]
+    out = ctypes.c_double()
+    _check(lib().cs_subproblem_objective(plan.handle, _ptr(u), _ptr(xt), _ptr(d), _ptr(maps_v), V, _ptr(maps_s), S,
+                                         ctypes.c_float(lam), int(reg), int(wavelet_levels), ctypes.byref(out),
+                                         _stream(stream)))
+    return out.value
+
+
+def power_iteration(plan: Plan, v0, maps_v, maps_s, iters=20, stream=None):
+    V = 0 if maps_v is None else maps_v.shape[0]
+    S = 0 if maps_s is None else maps_s.shape[0]
+    out = ctypes.c_double()
+    _check(lib().cs_power_iteration(plan.handle, _ptr(v0), _ptr(maps_v), V, _ptr(maps_s), S, int(iters),
+                                    ctypes.byref(out), _stream(stream)))
+    return out.value

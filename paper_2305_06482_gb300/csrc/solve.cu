@@ -86,6 +86,22 @@ __global__ void cg_init_kernel(const float2* __restrict__ d, const float2* __res
     if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// warm-started sub-problem CG: r = -(d + lambda u) - A_S^H A_S (u - x^t) (the last term given), p = r
+__global__ void cg_init_warm_kernel(const float2* __restrict__ d, const float2* __restrict__ u, const float2* __restrict__ hdu,
+                                    float lambda, int64_t n, float2* __restrict__ r, float2* __restrict__ p,
+                                    double* __restrict__ part) {
+    double acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 dv = d[i], uv = u[i], hv = hdu[i];
+        const float2 rv = make_float2(-(dv.x + lambda * uv.x + hv.x), -(dv.y + lambda * uv.y + hv.y));
+        r[i] = rv;
+        p[i] = rv;
+        acc += (double)fmaf(rv.x, rv.x, rv.y * rv.y);
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
 // plain CG start: r = b - H x (b, Hx given), p = r
 __global__ void cg_init2_kernel(const float2* __restrict__ b, const float2* __restrict__ hx, int64_t n,
                                 float2* __restrict__ r, float2* __restrict__ p, double* __restrict__ part) {
@@ -594,8 +610,16 @@ static cs_status cg_iter(const Ctx& c, const float2* mv, int V, const float2* ms
 // K CG iterations on (A_S^H A_S + lambda I) x = A_S^H A_S x^t - d from x^t (x updated in place);
 // the initial residual is b - H x^t = -(d + lambda x^t)
 static cs_status cg_sub(const Ctx& c, const float2* d, float2* x, int K, const float2* mv, int V, const float2* ms, int S,
-                        float2* r, float2* pv, float2* hp) {
-    cg_init_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(d, x, c.lambda, c.D, r, pv, c.partB);
+                        float2* r, float2* pv, float2* hp, const float2* xt_other = nullptr, float2* tmp = nullptr) {
+    if (xt_other) {
+        // warm start: x holds the start u != x^t; r0 = -(d + lambda u) - A_S^H A_S (u - x^t)
+        sub_kernel<<<vec_grid(c.D), kRedThreads, 0, c.st>>>(x, xt_other, c.D, tmp);
+        CS_LAUNCH_CHECK();
+        CS_PROPAGATE(normal_apply(c, tmp, mv, V, ms, S, 0.f, hp));
+        cg_init_warm_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(d, x, hp, c.lambda, c.D, r, pv, c.partB);
+    } else {
+        cg_init_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(d, x, c.lambda, c.D, r, pv, c.partB);
+    }
     CS_LAUNCH_CHECK();
     store_sum_kernel<<<1, 32, 0, c.st>>>(c.partB, &c.sc->rr[0]);
     CS_LAUNCH_CHECK();
@@ -606,9 +630,10 @@ static cs_status cg_sub(const Ctx& c, const float2* d, float2* x, int K, const f
 // K FISTA iterations on the sketched sub-problem from x^t: grad = A_S^H A_S (z - x^t) + d
 static cs_status fista_sub(const Ctx& c, const float2* d, float2* x, int K, const float2* mv, int V, const float2* ms,
                            int S, const std::vector<float>& theta, float2* z, float2* xp, float2* u, float2* gr,
-                           float2* xt) {
+                           float2* xt, const float2* xt_other = nullptr) {
     const int g = vec_grid(c.D);
-    CS_TRY_CUDA(cudaMemcpyAsync(xt, x, sizeof(float2) * c.D, cudaMemcpyDeviceToDevice, c.st));
+    // x^t is x on entry, unless a warm start u = x was given with x^t elsewhere
+    CS_TRY_CUDA(cudaMemcpyAsync(xt, xt_other ? xt_other : x, sizeof(float2) * c.D, cudaMemcpyDeviceToDevice, c.st));
     CS_TRY_CUDA(cudaMemcpyAsync(z, x, sizeof(float2) * c.D, cudaMemcpyDeviceToDevice, c.st));
     CS_TRY_CUDA(cudaMemcpyAsync(xp, x, sizeof(float2) * c.D, cudaMemcpyDeviceToDevice, c.st));
     for (int k = 0; k < K; ++k) {
@@ -1034,6 +1059,134 @@ cs_status recon_solve_batched(int nslices, const cs_batch_item* items, const cs_
     }
     CS_REQUIRE(params->iterates == nullptr, CS_ERR_INVALID_ARG, "batched solves do not record iterates");
     return recon_batched_impl(nslices, items, params, stats, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Sub-problem pieces for callers that drive Algorithm 1 themselves (e.g. with a warm start).
+
+static cs_status make_ctx(cs_plan* p, float lambda, int levels, cudaStream_t st, Ctx& c, SolverWS*& ws, int C, int S, int K) {
+    if (!p->solver_ws) p->solver_ws = new SolverWS();
+    ws = static_cast<SolverWS*>(p->solver_ws);
+    CS_PROPAGATE(ws->ensure(p->D, p->N, C, S, std::max(C - 1, 1), 1, std::max(K, 1)));
+    c.p = p;
+    c.st = st;
+    c.D = p->D;
+    c.nd = p->ndim;
+    for (int a = 0; a < 3; ++a) c.dims3[a] = p->img[a];
+    c.levels = levels > 0 ? levels : 4;
+    c.lambda = lambda;
+    c.sc = ws->sc;
+    c.partA = ws->partA;
+    c.partB = ws->partB;
+    return CS_OK;
+}
+
+cs_status sketched_subproblem_solve(const cs_plan* plan, const float* d, const float* xt, float* x_inout,
+                                    const float* maps_v, int V, const float* maps_s, int S, float lambda, int reg,
+                                    int wavelet_levels, int K, float step, void* stream) {
+    clear_error();
+    CS_REQUIRE(plan && d && xt && x_inout && K >= 0 && V >= 0 && S >= 0 && V + S >= 1 && V + S <= plan->max_coils,
+               CS_ERR_INVALID_ARG, "bad sub-problem arguments");
+    CS_REQUIRE(reg == CS_REG_L2 || step > 0, CS_ERR_INVALID_ARG, "FISTA needs a step > 0");
+    cs_plan* p = const_cast<cs_plan*>(plan);
+    cudaStream_t st = (cudaStream_t)stream;
+    Ctx c;
+    SolverWS* ws = nullptr;
+    CS_PROPAGATE(make_ctx(p, lambda, wavelet_levels, st, c, ws, V + S, S, K));
+    CS_TRY_CUDA(cudaMemsetAsync(ws->sc, 0, sizeof(Scal), st));
+    const float2* mv = (const float2*)maps_v;
+    const float2* ms = (const float2*)maps_s;
+    float2* x = (float2*)x_inout;
+    const bool same = (const float*)x_inout == xt;
+    if (reg == CS_REG_L2) {
+        CS_PROPAGATE(cg_sub(c, (const float2*)d, x, K, mv, V, ms, S, ws->r, ws->pv, ws->hp,
+                            same ? nullptr : (const float2*)xt, ws->u));
+    } else {
+        set_eta_kernel<<<1, 32, 0, st>>>(ws->sc, (double)step);
+        CS_LAUNCH_CHECK();
+        const std::vector<float> theta = fista_thetas(std::max(K, 1));
+        CS_PROPAGATE(fista_sub(c, (const float2*)d, x, K, mv, V, ms, S, theta, ws->z, ws->xp, ws->u, ws->gr, ws->xt,
+                               same ? nullptr : (const float2*)xt));
+    }
+    return CS_OK;
+}
+
+__global__ void l1_kernel(const float2* __restrict__ c, int64_t n, double* __restrict__ part) {
+    double acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = c[i];
+        acc += (double)sqrtf(v.x * v.x + v.y * v.y);
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// F(u) = 1/2 ||A_S (u - x^t)||^2 + Re<u, d> + g(u), g = lambda/2 ||u||^2 or lambda ||Psi u||_1 (Eq. 9-10)
+cs_status cs_subproblem_objective(const cs_plan* plan, const float* u, const float* xt, const float* d, const float* maps_v,
+                                  int V, const float* maps_s, int S, float lambda, int reg, int wavelet_levels,
+                                  double* value, void* stream) {
+    clear_error();
+    CS_REQUIRE(plan && u && xt && d && value && V + S >= 1, CS_ERR_INVALID_ARG, "bad objective arguments");
+    cs_plan* p = const_cast<cs_plan*>(plan);
+    cudaStream_t st = (cudaStream_t)stream;
+    Ctx c;
+    SolverWS* ws = nullptr;
+    CS_PROPAGATE(make_ctx(p, lambda, wavelet_levels, st, c, ws, V + S, S, 1));
+    const int64_t D = p->D;
+    sub_kernel<<<vec_grid(D), kRedThreads, 0, st>>>((const float2*)u, (const float2*)xt, D, ws->z);
+    CS_LAUNCH_CHECK();
+    CS_PROPAGATE(normal_apply(c, ws->z, (const float2*)maps_v, V, (const float2*)maps_s, S, 0.f, ws->hp));
+    std::vector<double> ha(kRedBlocks), hb(kRedBlocks), hc(kRedBlocks);
+    dot_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(ws->z, ws->hp, D, ws->partA);
+    CS_LAUNCH_CHECK();
+    CS_TRY_CUDA(cudaMemcpyAsync(ha.data(), ws->partA, sizeof(double) * kRedBlocks, cudaMemcpyDeviceToHost, st));
+    dot_kernel<<<kRedBlocks, kRedThreads, 0, st>>>((const float2*)u, (const float2*)d, D, ws->partB);
+    CS_LAUNCH_CHECK();
+    CS_TRY_CUDA(cudaMemcpyAsync(hb.data(), ws->partB, sizeof(double) * kRedBlocks, cudaMemcpyDeviceToHost, st));
+    CS_TRY_CUDA(cudaStreamSynchronize(st));
+    double quad = 0, lin = 0, reg_v = 0;
+    for (int i = 0; i < kRedBlocks; ++i) {
+        quad += ha[i];
+        lin += hb[i];
+    }
+    if (reg == CS_REG_L2) {
+        dot_kernel<<<kRedBlocks, kRedThreads, 0, st>>>((const float2*)u, (const float2*)u, D, ws->partA);
+        CS_LAUNCH_CHECK();
+        CS_TRY_CUDA(cudaMemcpyAsync(hc.data(), ws->partA, sizeof(double) * kRedBlocks, cudaMemcpyDeviceToHost, st));
+        CS_TRY_CUDA(cudaStreamSynchronize(st));
+        for (int i = 0; i < kRedBlocks; ++i) reg_v += hc[i];
+        reg_v *= 0.5 * lambda;
+    } else {
+        CS_TRY_CUDA(cudaMemcpyAsync(ws->gr, u, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
+        CS_PROPAGATE(wavelet_apply(ws->gr, c.dims3, c.nd, c.levels, 0, st));
+        l1_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(ws->gr, D, ws->partA);
+        CS_LAUNCH_CHECK();
+        CS_TRY_CUDA(cudaMemcpyAsync(hc.data(), ws->partA, sizeof(double) * kRedBlocks, cudaMemcpyDeviceToHost, st));
+        CS_TRY_CUDA(cudaStreamSynchronize(st));
+        for (int i = 0; i < kRedBlocks; ++i) reg_v += hc[i];
+        reg_v *= lambda;
+    }
+    *value = 0.5 * quad + lin + reg_v;
+    return CS_OK;
+}
+
+// largest eigenvalue of A_S^H A_S by power iteration from v0 (synchronises)
+cs_status cs_power_iteration(const cs_plan* plan, const float* v0, const float* maps_v, int V, const float* maps_s, int S,
+                             int iters, double* L, void* stream) {
+    clear_error();
+    CS_REQUIRE(plan && v0 && L && V + S >= 1 && iters >= 1, CS_ERR_INVALID_ARG, "bad power iteration arguments");
+    cs_plan* p = const_cast<cs_plan*>(plan);
+    cudaStream_t st = (cudaStream_t)stream;
+    Ctx c;
+    SolverWS* ws = nullptr;
+    CS_PROPAGATE(make_ctx(p, 0.f, 4, st, c, ws, V + S, S, 1));
+    CS_PROPAGATE(power_iteration(c, (const float2*)v0, iters, (const float2*)maps_v, V, (const float2*)maps_s, S, ws->u,
+                                 ws->hp));
+    Scal h;
+    CS_TRY_CUDA(cudaMemcpyAsync(&h, ws->sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
+    CS_TRY_CUDA(cudaStreamSynchronize(st));
+    *L = h.L;
+    return CS_OK;
 }
 
 cs_status wavelet_fwd(const float* x, int ndim, const int* dims, int levels, float* c, void* stream) {

@@ -1,0 +1,526 @@
+// Building blocks of the learned warm start: a small 3D CNN that maps (x^t, d) of a sketched
+// sub-problem (Eq. 9-10) to a correction of x^t.  Activations are voxel-major with channels
+// fastest ([nz][ny][nx][C], FP32); 3x3x3 convolutions (zero padding 1, stride 1) run as BF16
+// implicit GEMMs on the tensor cores with FP32 accumulation in tensor memory:
+//   forward:  out[v][co] = b[co] + sum_{tap, ci} in[v + off(tap)][ci] w[co][tap][ci]
+//             (GEMM M = 128 voxels, N = C_out padded to 16/32/64, K = 27 C_in padded to 16)
+//   data gradient: the same kernel with the taps flipped and the weights transposed,
+//             gin[v][ci] = sum_{tap, co} gout[v - off(tap)][co] w[co][tap][ci]
+// Weight gradients, the 1x1x1 output layer, ReLU masks, the loss and Adam run on CUDA cores.
+#include <cstdio>
+
+#include "cs_internal.cuh"
+
+namespace cs {
+
+constexpr int kNnM = 128;
+constexpr int kNnChunk = 8;                 // k-blocks (16 wide) staged per MMA batch
+constexpr int kNnABytes = kNnM * 16 * 2;    // one 128 x 16 bf16 k-block
+constexpr long long kNnSpin = 1ll << 22;
+
+__device__ int g_nn_error = 0;
+
+__device__ __forceinline__ uint32_t nn_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ int nn_kmajor_off(int row, int k) {
+    return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ uint64_t nn_desc(uint32_t addr) {
+    const uint64_t lbo = 128 >> 4, sbo = 256 >> 4;
+    return (uint64_t)((addr >> 4) & 0x3FFF) | (lbo << 16) | (sbo << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ unsigned short nn_bf16(float f) {
+    uint32_t b = __float_as_uint(f);
+    b += 0x7FFFu + ((b >> 16) & 1u);
+    return (unsigned short)(b >> 16);
+}
+
+template <int NPAD>
+__global__ void __launch_bounds__(128) conv3_tc_kernel(const float* __restrict__ in, int nz, int ny, int nx, int cin,
+                                                       const unsigned short* __restrict__ wpk, int kpad, int nout,
+                                                       const float* __restrict__ bias, int relu, int flip,
+                                                       float* __restrict__ out, int ldo, int coff) {
+    constexpr int kBBytes = NPAD * 16 * 2;
+    constexpr uint32_t kCols = NPAD < 32 ? 32u : (uint32_t)NPAD;
+    constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NPAD >> 3) << 17) | ((uint32_t)(kNnM >> 4) << 24);
+    extern __shared__ __align__(1024) unsigned char nsm[];
+    unsigned char* a_sm = nsm;
+    unsigned char* b_sm = nsm + kNnChunk * kNnABytes;
+    __shared__ uint32_t s_taddr;
+    __shared__ __align__(8) uint64_t s_mbar;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(nn_smem_u32(&s_taddr)),
+                     "r"(kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(nn_smem_u32(&s_mbar)), "r"(1u));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = s_taddr, mbar = nn_smem_u32(&s_mbar);
+    uint32_t phase = 0;
+    const int64_t nvox = (int64_t)nz * ny * nx;
+    const int ktot = 27 * cin;
+    const int kblocks = kpad / 16;
+    const int64_t ntiles = (nvox + kNnM - 1) / kNnM;
+    const int sgn = flip ? -1 : 1;
+    bool failed = false;
+    for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+        const int64_t v = tile * kNnM + tid;
+        const bool vv = v < nvox;
+        int x = 0, y = 0, z = 0;
+        if (vv) {
+            x = (int)(v % nx);
+            y = (int)((v / nx) % ny);
+            z = (int)(v / ((int64_t)nx * ny));
+        }
+        for (int c0 = 0; c0 < kblocks; c0 += kNnChunk) {
+            const int nkb = min(kNnChunk, kblocks - c0);
+            // A: this thread's voxel row of the implicit im2col matrix
+            for (int kb = 0; kb < nkb; ++kb) {
+                for (int kk = 0; kk < 16; ++kk) {
+                    const int k = (c0 + kb) * 16 + kk;
+                    float val = 0.f;
+                    if (vv && k < ktot) {
+                        const int tap = k / cin, ci = k - tap * cin;
+                        const int zz = z + sgn * (tap / 9 - 1), yy = y + sgn * ((tap / 3) % 3 - 1), xx = x + sgn * (tap % 3 - 1);
+                        if (zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx)
+                            val = in[(((int64_t)zz * ny + yy) * nx + xx) * cin + ci];
+                    }
+                    *reinterpret_cast<unsigned short*>(a_sm + kb * kNnABytes + nn_kmajor_off(tid, kk)) = nn_bf16(val);
+                }
+            }
+            // B: the packed BF16 weights of these k-blocks
+            for (int e = tid; e < NPAD * nkb * 16; e += blockDim.x) {
+                const int n = e / (nkb * 16), kr = e % (nkb * 16);
+                const int kb = kr / 16, kk = kr % 16;
+                *reinterpret_cast<unsigned short*>(b_sm + kb * kBBytes + nn_kmajor_off(n, kk)) =
+                    wpk[(int64_t)n * kpad + (c0 + kb) * 16 + kk];
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (tid == 0) {
+                for (int kb = 0; kb < nkb; ++kb) {
+                    const uint64_t ad = nn_desc(nn_smem_u32(a_sm + kb * kNnABytes));
+                    const uint64_t bd = nn_desc(nn_smem_u32(b_sm + kb * kBBytes));
+                    const uint32_t acc = (c0 + kb > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+                        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                             : "memory");
+            }
+            long long spins = 0;
+            uint32_t done = 0;
+            while (!done) {
+                asm volatile(
+                    "{\n.reg .pred P1;\nmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\nselp.b32 %0, 1, 0, P1;\n}\n"
+                    : "=r"(done)
+                    : "r"(mbar), "r"(phase)
+                    : "memory");
+                if (!done && ++spins > kNnSpin) break;
+            }
+            if (__syncthreads_or(!done)) {
+                if (tid == 0) atomicExch(&g_nn_error, 1);
+                failed = true;
+                break;
+            }
+            phase ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        if (failed) break;
+        // epilogue: TMEM lane = voxel, columns = output channels
+#pragma unroll
+        for (int j = 0; j < NPAD / 16; ++j) {
+            uint32_t r[16];
+            const uint32_t a = taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j * 16);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(a));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (vv) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int n = j * 16 + q;
+                    if (n < nout) {
+                        float val = __uint_as_float(r[q]) + (bias ? bias[n] : 0.f);
+                        if (relu) val = fmaxf(val, 0.f);
+                        out[v * ldo + coff + n] = val;
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kCols));
+}
+
+// packed BF16 weights [npad][kpad]: forward rows co with k = tap*cin + ci; transposed (data
+// gradient) rows ci with k = tap*cout + co.  Zero padding outside.
+__global__ void pack_weights_kernel(const float* __restrict__ w, int cout, int cin, int transpose, int npad, int kpad,
+                                    unsigned short* __restrict__ pk) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)npad * kpad) return;
+    const int n = (int)(e / kpad), k = (int)(e % kpad);
+    float v = 0.f;
+    if (!transpose) {
+        if (n < cout && k < 27 * cin) v = w[(int64_t)n * 27 * cin + k];   // w[co][tap][ci]
+    } else {
+        if (n < cin && k < 27 * cout) {
+            const int tap = k / cout, co = k % cout;
+            v = w[((int64_t)co * 27 + tap) * cin + n];
+        }
+    }
+    pk[e] = nn_bf16(v);
+}
+
+// weight gradient: gw[co][tap][ci] += sum_v gout[v][co] in[v + off(tap)][ci], gb[co] += sum_v gout[v][co]
+constexpr int kWgVox = 128;
+__global__ void wgrad_kernel(const float* __restrict__ in, const float* __restrict__ gout, int nz, int ny, int nx, int cin,
+                             int cout, float* __restrict__ gw, float* __restrict__ gb) {
+    extern __shared__ float wsm[];
+    float* sg = wsm;                     // [kWgVox][cout]
+    float* si = wsm + kWgVox * cout;     // [kWgVox][cin]
+    const int tap = blockIdx.y;
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const int64_t nvox = (int64_t)nz * ny * nx;
+    const int pairs = cout * cin;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float bacc = 0.f;
+    for (int64_t v0 = (int64_t)blockIdx.x * kWgVox; v0 < nvox; v0 += (int64_t)gridDim.x * kWgVox) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kWgVox * cout; e += blockDim.x) {
+            const int64_t v = v0 + e / cout;
+            sg[e] = (v < nvox) ? gout[v * cout + e % cout] : 0.f;
+        }
+        for (int e = threadIdx.x; e < kWgVox * cin; e += blockDim.x) {
+            const int64_t v = v0 + e / cin;
+            float val = 0.f;
+            if (v < nvox) {
+                const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
+                const int zz = z + dz, yy = y + dy, xx = x + dx;
+                if (zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx)
+                    val = in[(((int64_t)zz * ny + yy) * nx + xx) * cin + e % cin];
+            }
+            si[e] = val;
+        }
+        __syncthreads();
+        for (int q = 0; q < 4; ++q) {
+            const int pr = threadIdx.x + q * blockDim.x;
+            if (pr < pairs) {
+                const int co = pr / cin, ci = pr % cin;
+                float a = 0.f;
+                for (int t = 0; t < kWgVox; ++t) a = fmaf(sg[t * cout + co], si[t * cin + ci], a);
+                acc[q] += a;
+            }
+        }
+        if (tap == 13 && threadIdx.x < cout)
+            for (int t = 0; t < kWgVox; ++t) bacc += sg[t * cout + threadIdx.x];
+    }
+    for (int q = 0; q < 4; ++q) {
+        const int pr = threadIdx.x + q * blockDim.x;
+        if (pr < pairs) {
+            const int co = pr / cin, ci = pr % cin;
+            atomicAdd(&gw[((int64_t)co * 27 + tap) * cin + ci], acc[q]);
+        }
+    }
+    if (tap == 13 && threadIdx.x < cout && gb) atomicAdd(&gb[threadIdx.x], bacc);
+}
+
+// g *= (act > 0)
+__global__ void relu_bwd_kernel(const float* __restrict__ act, float* __restrict__ g, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!(act[i] > 0.f)) g[i] = 0.f;
+}
+
+// 1x1x1 layer: out[v][o] = b[o] + sum_c w[o][c] in[v][c]
+__global__ void conv1_fwd_kernel(const float* __restrict__ in, int64_t nvox, int cin, int cout, const float* __restrict__ w,
+                                 const float* __restrict__ b, float* __restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nvox * cout; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = e / cout;
+        const int o = (int)(e % cout);
+        float a = b[o];
+        for (int c = 0; c < cin; ++c) a = fmaf(w[o * cin + c], in[v * cin + c], a);
+        out[e] = a;
+    }
+}
+
+// 1x1x1 layer backward: gin[v][c] = sum_o w[o][c] gout[v][o]; gw[o][c] += sum_v gout[v][o] in[v][c]; gb[o] += sum_v gout
+__global__ void conv1_bwd_kernel(const float* __restrict__ in, const float* __restrict__ gout, int64_t nvox, int cin,
+                                 int cout, const float* __restrict__ w, float* __restrict__ gin, float* __restrict__ gw,
+                                 float* __restrict__ gb) {
+    __shared__ float part[64 * 4 + 4];
+    for (int i = threadIdx.x; i < cout * cin + cout; i += blockDim.x) part[i] = 0.f;
+    __syncthreads();
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (int64_t)gridDim.x * blockDim.x) {
+        for (int c = 0; c < cin; ++c) {
+            float a = 0.f;
+            for (int o = 0; o < cout; ++o) a = fmaf(w[o * cin + c], gout[v * cout + o], a);
+            gin[v * cin + c] = a;
+        }
+        for (int o = 0; o < cout; ++o) {
+            const float g = gout[v * cout + o];
+            atomicAdd(&part[cout * cin + o], g);
+            for (int c = 0; c < cin; ++c) atomicAdd(&part[o * cin + c], g * in[v * cin + c]);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cout * cin; i += blockDim.x) atomicAdd(&gw[i], part[i]);
+    for (int i = threadIdx.x; i < cout; i += blockDim.x) atomicAdd(&gb[i], part[cout * cin + i]);
+}
+
+// mean squared error: loss += sum (out - tgt)^2 / n, g = 2 (out - tgt) / n
+__global__ void mse_kernel(const float* __restrict__ out, const float* __restrict__ tgt, int64_t n, float* __restrict__ g,
+                           float* __restrict__ loss) {
+    float acc = 0.f;
+    const float inv = 1.0f / (float)n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float d = out[i] - tgt[i];
+        g[i] = 2.f * d * inv;
+        acc += d * d * inv;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
+}
+
+// Adam (Kingma & Ba) with bias correction; step is 1-based
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                            int64_t n, float lr, float b1, float b2, float eps, int step) {
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// network input: [Re x^t, Im x^t] / s and [Re d, Im d] * eta / s with s the RMS of (x^t, eta d)
+// over the voxels (non-zero from the first outer iteration, where x^t = 0)
+__global__ void feat_norm_kernel(const float2* __restrict__ x, const float2* __restrict__ d, float eta, int64_t n,
+                                 float* __restrict__ ss) {
+    float acc = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += x[i].x * x[i].x + x[i].y * x[i].y + eta * eta * (d[i].x * d[i].x + d[i].y * d[i].y);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(ss, acc);
+}
+
+__global__ void features_kernel(const float2* __restrict__ x, const float2* __restrict__ d, int64_t n, float eta,
+                                const float* __restrict__ ss, float* __restrict__ f) {
+    const float s = sqrtf(ss[0] / (float)n) + 1e-12f;
+    const float inv = 1.f / s;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        f[4 * i + 0] = x[i].x * inv;
+        f[4 * i + 1] = x[i].y * inv;
+        f[4 * i + 2] = d[i].x * eta * inv;
+        f[4 * i + 3] = d[i].y * eta * inv;
+    }
+}
+
+// out = x + s * delta (delta [n][2] in units of s)
+__global__ void apply_delta_kernel(const float2* __restrict__ x, const float* __restrict__ delta, int64_t n,
+                                   const float* __restrict__ ss, float2* __restrict__ out) {
+    const float s = sqrtf(ss[0] / (float)n) + 1e-12f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = make_float2(fmaf(s, delta[2 * i], x[i].x), fmaf(s, delta[2 * i + 1], x[i].y));
+}
+
+// target: (x_target - x^t) / s as [n][2]
+__global__ void target_kernel(const float2* __restrict__ xt, const float2* __restrict__ xs, int64_t n,
+                              const float* __restrict__ ss, float* __restrict__ tgt) {
+    const float inv = 1.f / (sqrtf(ss[0] / (float)n) + 1e-12f);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        tgt[2 * i] = (xs[i].x - xt[i].x) * inv;
+        tgt[2 * i + 1] = (xs[i].y - xt[i].y) * inv;
+    }
+}
+
+static int nn_grid(int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
+}
+
+cs_status nn_init_attrs() {
+    CS_TRY_CUDA(cudaFuncSetAttribute(conv3_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kNnChunk * kNnABytes + kNnChunk * 16 * 32));
+    CS_TRY_CUDA(cudaFuncSetAttribute(conv3_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kNnChunk * kNnABytes + kNnChunk * 32 * 32));
+    CS_TRY_CUDA(cudaFuncSetAttribute(conv3_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kNnChunk * kNnABytes + kNnChunk * 64 * 32));
+    return CS_OK;
+}
+
+cs_status nn_check_and_clear() {
+    int v = 0;
+    CS_TRY_CUDA(cudaMemcpyFromSymbol(&v, g_nn_error, sizeof(int)));
+    if (v) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(g_nn_error, &zero, sizeof(int));
+        set_error("a tensor-core convolution gave up waiting for its MMAs (bounded wait)");
+        return CS_ERR_TIMEOUT;
+    }
+    return CS_OK;
+}
+
+}  // namespace cs
+
+using namespace cs;
+
+extern "C" {
+
+cs_status cs_nn_pack_weights(const float* w, int cout, int cin, int transpose, unsigned short* packed, int npad,
+                             int kpad, void* stream) {
+    clear_error();
+    CS_REQUIRE(w && packed && cout >= 1 && cin >= 1, CS_ERR_INVALID_ARG, "bad pack arguments");
+    const int nn = transpose ? cin : cout, kk = 27 * (transpose ? cout : cin);
+    CS_REQUIRE((npad == 16 || npad == 32 || npad == 64) && npad >= nn && kpad % 16 == 0 && kpad >= kk,
+               CS_ERR_INVALID_ARG, "packed shape %d x %d cannot hold %d x %d", npad, kpad, nn, kk);
+    const int64_t n = (int64_t)npad * kpad;
+    pack_weights_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(w, cout, cin, transpose, npad, kpad,
+                                                                                       packed);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status cs_nn_conv3d(const float* in, int nz, int ny, int nx, int cin, const unsigned short* packed, int npad, int kpad,
+                       int nout, const float* bias, int relu, int flip, float* out, int ldo, int coff, void* stream) {
+    clear_error();
+    CS_REQUIRE(in && packed && out && nz > 0 && ny > 0 && nx > 0 && cin >= 1 && nout >= 1 && nout <= npad &&
+                   coff >= 0 && coff + nout <= ldo && kpad >= 27 * cin && kpad % 16 == 0,
+               CS_ERR_INVALID_ARG, "bad conv3d arguments");
+    static bool init[128] = {false};
+    int dev = 0;
+    CS_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 128 && !init[dev]) {
+        CS_PROPAGATE(nn_init_attrs());
+        init[dev] = true;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nvox = (int64_t)nz * ny * nx;
+    const int64_t tiles = (nvox + kNnM - 1) / kNnM;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)std::max(sms, 1) * 4));
+    const size_t sm = (size_t)kNnChunk * kNnABytes + (size_t)kNnChunk * npad * 32;
+    switch (npad) {
+        case 16: conv3_tc_kernel<16><<<grid, 128, sm, st>>>(in, nz, ny, nx, cin, packed, kpad, nout, bias, relu, flip, out, ldo, coff); break;
+        case 32: conv3_tc_kernel<32><<<grid, 128, sm, st>>>(in, nz, ny, nx, cin, packed, kpad, nout, bias, relu, flip, out, ldo, coff); break;
+        case 64: conv3_tc_kernel<64><<<grid, 128, sm, st>>>(in, nz, ny, nx, cin, packed, kpad, nout, bias, relu, flip, out, ldo, coff); break;
+        default: set_error("npad must be 16, 32 or 64"); return CS_ERR_INVALID_ARG;
+    }
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status cs_nn_conv3d_wgrad(const float* in, const float* gout, int nz, int ny, int nx, int cin, int cout, float* gw,
+                             float* gb, void* stream) {
+    clear_error();
+    CS_REQUIRE(in && gout && gw && cin >= 1 && cout >= 1 && cin * cout <= 1024, CS_ERR_INVALID_ARG, "bad wgrad arguments");
+    const int64_t nvox = (int64_t)nz * ny * nx;
+    const size_t sm = sizeof(float) * kWgVox * (cin + cout);
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((nvox + kWgVox - 1) / kWgVox, 64));
+    wgrad_kernel<<<dim3(gx, 27), 256, sm, (cudaStream_t)stream>>>(in, gout, nz, ny, nx, cin, cout, gw, gb);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status cs_nn_relu_bwd(const float* act, float* g, int64_t n, void* stream) {
+    clear_error();
+    CS_REQUIRE(act && g && n >= 0, CS_ERR_INVALID_ARG, "bad relu_bwd arguments");
+    if (n == 0) return CS_OK;
+    relu_bwd_kernel<<<nn_grid(n), 256, 0, (cudaStream_t)stream>>>(act, g, n);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status cs_nn_conv1(const float* in, int64_t nvox, int cin, int cout, const float* w, const float* b, float* out,
+                      void* stream) {
+    clear_error();
+    CS_REQUIRE(in && w && b && out && cin >= 1 && cout >= 1, CS_ERR_INVALID_ARG, "bad conv1 arguments");
+    conv1_fwd_kernel<<<nn_grid(nvox * cout), 256, 0, (cudaStream_t)stream>>>(in, nvox, cin, cout, w, b, out);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status cs_nn_conv1_bwd(const float* in, const float* gout, int64_t nvox, int cin, int cout, const float* w, float* gin,
+                          float* gw, float* gb, void* stream) {
+    clear_error();
+    CS_REQUIRE(in && gout && w && gin && gw && gb && cin * cout + cout <= 64 * 4 + 4, CS_ERR_INVALID_ARG,
+               "bad conv1_bwd arguments");
+    conv1_bwd_kernel<<<nn_grid(nvox), 256, 0, (cudaStream_t)stream>>>(in, gout, nvox, cin, cout, w, gin, gw, gb);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status cs_nn_mse(const float* out, const float* tgt, int64_t n, float* g, float* loss, void* stream) {
+    clear_error();
+    CS_REQUIRE(out && tgt && g && loss && n > 0, CS_ERR_INVALID_ARG, "bad mse arguments");
+    mse_kernel<<<nn_grid(n), 256, 0, (cudaStream_t)stream>>>(out, tgt, n, g, loss);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status cs_nn_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2, float eps,
+                     int step, void* stream) {
+    clear_error();
+    CS_REQUIRE(p && g && m && v && n >= 0 && step >= 1, CS_ERR_INVALID_ARG, "bad adam arguments");
+    if (n == 0) return CS_OK;
+    adam_kernel<<<nn_grid(n), 256, 0, (cudaStream_t)stream>>>(p, g, m, v, n, lr, b1, b2, eps, step);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+// ss (device float, caller-owned): cleared and set to ||x^t||^2; f [n][4]; (targets and the
+// application of a prediction use the same ss)
+cs_status cs_nn_features(const float* xt, const float* d, int64_t n, float eta, float* ss, float* f, void* stream) {
+    clear_error();
+    CS_REQUIRE(xt && d && ss && f && n > 0, CS_ERR_INVALID_ARG, "bad features arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    CS_TRY_CUDA(cudaMemsetAsync(ss, 0, sizeof(float), st));
+    feat_norm_kernel<<<nn_grid(n), 256, 0, st>>>((const float2*)xt, (const float2*)d, eta, n, ss);
+    CS_LAUNCH_CHECK();
+    features_kernel<<<nn_grid(n), 256, 0, st>>>((const float2*)xt, (const float2*)d, n, eta, ss, f);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status cs_nn_target(const float* xt, const float* xs, int64_t n, const float* ss, float* tgt, void* stream) {
+    clear_error();
+    CS_REQUIRE(xt && xs && ss && tgt && n > 0, CS_ERR_INVALID_ARG, "bad target arguments");
+    target_kernel<<<nn_grid(n), 256, 0, (cudaStream_t)stream>>>((const float2*)xt, (const float2*)xs, n, ss, tgt);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status cs_nn_apply(const float* xt, const float* delta, int64_t n, const float* ss, float* out, void* stream) {
+    clear_error();
+    CS_REQUIRE(xt && delta && ss && out && n > 0, CS_ERR_INVALID_ARG, "bad apply arguments");
+    apply_delta_kernel<<<nn_grid(n), 256, 0, (cudaStream_t)stream>>>((const float2*)xt, delta, n, ss, (float2*)out);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status cs_nn_status(void* stream) {
+    clear_error();
+    CS_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return nn_check_and_clear();
+}
+
+}  // extern "C"
