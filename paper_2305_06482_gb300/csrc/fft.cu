@@ -116,15 +116,22 @@ __device__ __forceinline__ void dft_small<8>(float2 (&v)[8], int sign, const flo
     v[7] = csub(e[3], t3);
 }
 
+// q = j / Ns for 0 <= j < 2^16 and 2 <= Ns < 2^16 via a multiply-shift with mag = floor(2^32 / Ns) + 1
+// (the error of j * mag / 2^32 against j / Ns stays below 1 / Ns there); Ns = 1 is passed through
+__device__ __forceinline__ int divmagic(int j, int Ns, uint32_t mag) {
+    return Ns == 1 ? j : (int)__umulhi((uint32_t)j, mag);
+}
+
 template <int R>
 __device__ __forceinline__ void stockham_stage(const float2* __restrict__ a, float2* __restrict__ b,
-                                               const float2* tw, int n, int Ns, int sign) {
+                                               const float2* tw, int n, int Ns, uint32_t mag, int sign) {
     const int nb = n / R;
     const int tstride = n / (Ns * R);
     for (int t = threadIdx.x; t < nb * kLines; t += blockDim.x) {
         const int l = t % kLines;
         const int j = t / kLines;
-        const int k = j % Ns;
+        const int jq = divmagic(j, Ns, mag);
+        const int k = j - jq * Ns;
         float2 v[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) v[q] = a[(j + q * nb) * kLinePad + l];
@@ -137,7 +144,7 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ a, flo
             }
         }
         dft_small<R>(v, sign, tw, n);
-        const int base = (j / Ns) * Ns * R + k;
+        const int base = jq * Ns * R + k;
 #pragma unroll
         for (int q = 0; q < R; ++q) b[(base + q * Ns) * kLinePad + l] = v[q];
     }
@@ -149,14 +156,15 @@ __device__ float2* fft_lines(float2* a, float2* b, const float2* tw, int n, cons
     int Ns = 1;
     for (int s = 0; s < nrad; ++s) {
         const int r = rad[s];
+        const uint32_t mag = (uint32_t)(0x100000000ull / (unsigned long long)Ns) + 1u;
         switch (r) {
-            case 2: stockham_stage<2>(a, b, tw, n, Ns, sign); break;
-            case 3: stockham_stage<3>(a, b, tw, n, Ns, sign); break;
-            case 4: stockham_stage<4>(a, b, tw, n, Ns, sign); break;
-            case 5: stockham_stage<5>(a, b, tw, n, Ns, sign); break;
-            case 7: stockham_stage<7>(a, b, tw, n, Ns, sign); break;
-            case 8: stockham_stage<8>(a, b, tw, n, Ns, sign); break;
-            case 11: stockham_stage<11>(a, b, tw, n, Ns, sign); break;
+            case 2: stockham_stage<2>(a, b, tw, n, Ns, mag, sign); break;
+            case 3: stockham_stage<3>(a, b, tw, n, Ns, mag, sign); break;
+            case 4: stockham_stage<4>(a, b, tw, n, Ns, mag, sign); break;
+            case 5: stockham_stage<5>(a, b, tw, n, Ns, mag, sign); break;
+            case 7: stockham_stage<7>(a, b, tw, n, Ns, mag, sign); break;
+            case 8: stockham_stage<8>(a, b, tw, n, Ns, mag, sign); break;
+            case 11: stockham_stage<11>(a, b, tw, n, Ns, mag, sign); break;
             default: break;
         }
         __syncthreads();
@@ -233,7 +241,7 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
     if (MODE == REDUCE_X) {
         // ---- rows_per_cta image rows; inverse FFT of every coil's line, crop, conj(map),
         //      apodisation and the sum over coils (deterministic order) ----
-        constexpr int MAXE = 32;
+        constexpr int MAXE = 4;     // rows_per_cta * nx <= 4 * kPassThreads (set by pass_reduce)
         float2 acc[MAXE];
 #pragma unroll
         for (int e = 0; e < MAXE; ++e) acc[e] = make_float2(0.f, 0.f);
@@ -513,6 +521,7 @@ static cs_status pass_reduce(const cs_plan* p, const float2* maps_v, int V, cons
     A.lambda = lambda;
     const int C = V + S;
     A.rows_per_cta = (C >= kLines || C == 0) ? 1 : kLines / C;   // C == 0: only lambda v / accumulate
+    A.rows_per_cta = std::max(1, std::min(A.rows_per_cta, 4 * kPassThreads / p->img[2]));
     return launch_pass<REDUCE_X>(A, st);
 }
 

@@ -324,8 +324,28 @@ struct Win {
     int zc[P];
 };
 
+// Minimum resident CTAs per SM requested from the register allocator for the gridding kernels, by
+// planes per lane P (1: 8 coils per warp, 2: 16, 4: 32); 1 leaves the allocator unconstrained. Four
+// CTAs (128 registers, a few spilled words) measured faster for the spread at P = 1 and the
+// interpolation at P = 2 than the unconstrained allocation (3 CTAs) on the 128^3 and
+// 160x256x256 cones workloads.
+#ifndef CS_INTERP_MINB_P1
+#define CS_INTERP_MINB_P1 1
+#endif
+#ifndef CS_INTERP_MINB_P2
+#define CS_INTERP_MINB_P2 4
+#endif
+#ifndef CS_SPREAD_MINB_P1
+#define CS_SPREAD_MINB_P1 4
+#endif
+#ifndef CS_SPREAD_MINB_P2
+#define CS_SPREAD_MINB_P2 1
+#endif
+#define CS_INTERP_MINB(P) ((P) == 1 ? CS_INTERP_MINB_P1 : (P) == 2 ? CS_INTERP_MINB_P2 : 1)
+#define CS_SPREAD_MINB(P) ((P) == 1 ? CS_SPREAD_MINB_P1 : (P) == 2 ? CS_SPREAD_MINB_P2 : 1)
+
 template <int ND, int P>
-__global__ void __launch_bounds__(128) interp_kernel(GridArgs A, int mode, const float2* __restrict__ ysub,
+__global__ void __launch_bounds__(128, CS_INTERP_MINB(P)) interp_kernel(GridArgs A, int mode, const float2* __restrict__ ysub,
                                                      float2* __restrict__ out) {
     constexpr int S = (ND == 3) ? 4 / P : 1;     // lanes per coil
     const int lane = threadIdx.x & 31;
@@ -475,7 +495,7 @@ __device__ __forceinline__ void red_add(float2* p, float2 v) {
 }
 
 template <int ND, int P>
-__global__ void __launch_bounds__(128) spread_kernel(GridArgs A, const float2* __restrict__ yin, int sorted_in) {
+__global__ void __launch_bounds__(128, CS_SPREAD_MINB(P)) spread_kernel(GridArgs A, const float2* __restrict__ yin, int sorted_in) {
     constexpr int S = (ND == 3) ? 4 / P : 1;
     const int lane = threadIdx.x & 31;
     const int coil_l = lane / S, slice = lane % S;
