@@ -92,6 +92,9 @@ typedef struct {
     const float* dcf;    /* device, [N] density compensation w (the operator applies sqrt w)  */
     int tile[3];         /* tile size per axis for binning; 0 = library default / autotuned   */
 } cs_geom;
+/* Size limits: image sizes even, nx <= 512; grid sizes even, >= the image and <= 800 (the FFT
+ * length limit) with prime factors in {2, 3, 5, 7, 11}; non-Cartesian plans need grid points x
+ * max_coils < 2^31.  Violations return CS_ERR_UNSUPPORTED_SIZE. */
 
 cs_status cs_plan_create(const cs_geom* g, void* stream, cs_plan** out);
 cs_status cs_plan_destroy(cs_plan* plan);

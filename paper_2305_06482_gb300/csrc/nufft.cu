@@ -11,6 +11,7 @@
 // (-1)^(j + G/2) of every grid index is folded into the interpolation weights instead.
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 
 #include "cs_internal.cuh"
 
@@ -213,15 +214,25 @@ cs_status nufft_bin(cs_plan* p, const float* traj, const float* dcf, cudaStream_
 // Samples are sorted by tile and, inside a tile, by acquisition order, so consecutive sorted
 // samples lie a fraction of a grid unit apart along a readout and their W^3 boxes mostly
 // coincide.  One warp walks a run of consecutive samples; its lanes are (coil, z-slice) pairs
-// of one coil chunk, so every lane sees the same sample and the window updates are uniform
-// across the warp.  A lane keeps P of the 4 z-planes of the box (4x4 values each) in registers:
-// planes are held by z residue modulo 4, so a move along z replaces one plane in place; a move
-// along y or x shifts every held plane by one row/column and touches only the entering
-// (interp: loads) or leaving (spread: atomic adds) row/column.  Kernel weights phi come from a
-// 2049-point table of phi on [0, 2] (linear interpolation, relative error below 3e-7, built in
-// double on the host); 12 lanes evaluate one weight each and the warp shares them by shuffles.
+// of one coil chunk (S lanes per coil), so every lane sees the same sample and the window
+// updates are uniform across the warp.  A lane keeps P of the 4 z-planes of the box (4x4 values
+// each) in registers.  Every axis of the window is indexed by grid index modulo 4: the value of
+// grid point (z, y, x) sits in plane z & 3 (held by lane slice (z & 3) mod S), row y & 3 and
+// column x & 3.  A move of the box by one along y or x therefore leaves every other register
+// where it is: only the leaving row/column (residue of the old box start for a step up, of the
+// old box end for a step down) is written out (spread: atomic adds) or replaced by the entering
+// one (interp: loads), and it takes the entering position; a move along z does the same for a
+// whole plane.  The per-sample weights are stored rotated the same way, so the accumulation
+// and the dot product use fixed register indices.  Records are staged per warp in shared memory
+// (64 samples at a time), and element offsets are kept as 32-bit row/column/plane offsets
+// (the plan guarantees grid points x coils < 2^31).  Kernel weights phi come from a 2049-point
+// table of phi on [0, 2] (linear interpolation, relative error below 3e-7, built in double on
+// the host).
 enum { OUT_USER = 0, OUT_RESID = 1, OUT_SORTED = 2 };
 constexpr int kPhiTable = 2048;
+constexpr int kStage = 64;          // records staged per warp
+constexpr int kGridWarps = 4;       // warps per CTA of the gridding kernels
+constexpr int kNoPlane = -(1 << 30);
 
 struct GridArgs {
     float2* grid;          // [G][C] (coil-interleaved)
@@ -246,17 +257,10 @@ __device__ __forceinline__ int wrapc(int j, int G) {   // j in [-G, 2G)
     return j < 0 ? j + G : (j >= G ? j - G : j);
 }
 
-template <int ND>
-struct SampleBox {
-    int jz, jy, jx;        // wrapped box starts
-    float wz[kW], wy[kW], wx[kW];
-    float sw;              // sqrt(w)
-    int perm;              // user index
-};
-
-// Per-sample record of 16 words, computed once per plan: the 12 kernel weights (z, y, x, with
-// the (-1)^(j + G/2) sign of the centred DFT folded in), the wrapped box start packed as
-// 10 + 10 + 10 bits, sqrt(w) and the user index of the sample.
+// Per-sample record of 16 words, computed once per plan.  Words 4a .. 4a+3 hold the kernel
+// weights along axis a (z, y, x), the weight of grid index j stored at word 4a + (j & 3), with
+// the (-1)^(j + G/2) sign of the centred DFT folded in; word 12 packs the unwrapped box starts
+// plus 2 (10 bits per axis, z lowest), word 13 is sqrt(w) and word 14 the user index.
 constexpr int kRec = 16;
 
 __global__ void sample_record_kernel(const float* __restrict__ gs, const float* __restrict__ ws,
@@ -275,15 +279,15 @@ __global__ void sample_record_kernel(const float* __restrict__ gs, const float* 
         const float g = gs[s * 3 + ax];
         const int j0 = used ? (int)floorf(g) - (kW / 2 - 1) : 0;
         for (int a = 0; a < kW; ++a) {
+            const int j = j0 + a;
             float v = (a == 0) ? 1.f : 0.f;
             if (used) {
-                const int j = j0 + a;
                 v = phi_lookup(tab, g - (float)j);
                 if ((j + Gs[ax] / 2) & 1) v = -v;
             }
-            r[ax * kW + a] = v;
+            r[ax * kW + (j & 3)] = v;
         }
-        jb[ax] = used ? wrapc(j0, Gs[ax]) : 0;
+        jb[ax] = j0 + 2;
     }
     r[12] = __int_as_float(jb[0] | (jb[1] << 10) | (jb[2] << 20));
     r[13] = ws[s];
@@ -291,46 +295,77 @@ __global__ void sample_record_kernel(const float* __restrict__ gs, const float* 
     r[15] = 0.f;
 }
 
-// lane l holds word (l mod 16) of the sample's record; every lane gets the weights by shuffles
-__device__ __forceinline__ float rec_word(const GridArgs& A, int64_t s, int lane) {
-    return (s < A.N) ? __ldg(A.rec + s * kRec + (lane & (kRec - 1))) : 0.f;
-}
-
-template <int ND>
-__device__ __forceinline__ void sample_box(float w, int lane, SampleBox<ND>& B) {
+// Stage the records of samples [base, base + n) (n <= kStage) into the warp's shared buffer.
+__device__ __forceinline__ void stage_records(const GridArgs& A, int64_t base, int n, float* wrec, int lane) {
+    __syncwarp();
+    const float4* src = reinterpret_cast<const float4*>(A.rec + base * kRec);
+    float4* dst = reinterpret_cast<float4*>(wrec);
+    float4 t[kStage * kRec / 4 / 32];
 #pragma unroll
-    for (int a = 0; a < kW; ++a) {
-        B.wz[a] = __shfl_sync(0xffffffffu, w, a);
-        B.wy[a] = __shfl_sync(0xffffffffu, w, kW + a);
-        B.wx[a] = __shfl_sync(0xffffffffu, w, 2 * kW + a);
+    for (int k = 0; k < kStage * kRec / 4 / 32; ++k) {
+        const int i = lane + 32 * k;
+        if (i < n * (kRec / 4)) t[k] = __ldg(src + i);
     }
-    const int packed = __float_as_int(__shfl_sync(0xffffffffu, w, 12));
-    B.sw = __shfl_sync(0xffffffffu, w, 13);
-    B.perm = __float_as_int(__shfl_sync(0xffffffffu, w, 14));
-    B.jz = packed & 1023;
-    B.jy = (packed >> 10) & 1023;
-    B.jx = (packed >> 20) & 1023;
+#pragma unroll
+    for (int k = 0; k < kStage * kRec / 4 / 32; ++k) {
+        const int i = lane + 32 * k;
+        if (i < n * (kRec / 4)) dst[i] = t[k];
+    }
+    __syncwarp();
 }
 
-__device__ __forceinline__ int64_t gaddr(const GridArgs& A, int z, int y, int x, int c) {
-    return (((int64_t)z * A.Gy + y) * A.Gx + x) * A.C + c;
+struct BoxHead {
+    int jz, jy, jx;   // unwrapped box starts
+    float sw;
+    int perm;
+};
+
+__device__ __forceinline__ BoxHead box_head(const float* r) {
+    const float4 h = *reinterpret_cast<const float4*>(r + 12);
+    const int packed = __float_as_int(h.x);
+    BoxHead b;
+    b.jz = (packed & 1023) - 2;
+    b.jy = ((packed >> 10) & 1023) - 2;
+    b.jx = ((packed >> 20) & 1023) - 2;
+    b.sw = h.y;
+    b.perm = __float_as_int(h.z);
+    return b;
 }
 
-// Per-lane window: P planes of 4x4 values; plane p holds z residue q + p*s (s = 4 / P lanes per
-// coil).  zc[p] is the (wrapped) z of the plane or -1 when empty.
+template <int V>
+using IC = std::integral_constant<int, V>;
+
+// call f(IC<r>) for the runtime residue r in [0, 4) (uniform across the warp)
+template <class F>
+__device__ __forceinline__ void with_residue(int r, F&& f) {
+    switch (r) {
+        case 0: f(IC<0>{}); break;
+        case 1: f(IC<1>{}); break;
+        case 2: f(IC<2>{}); break;
+        default: f(IC<3>{}); break;
+    }
+}
+
+// Window state shared by both kernels: P planes of 4x4 values and the 32-bit element offsets of
+// every plane (zoff), row residue (yoff) and column residue (xoff).
 template <int P>
 struct Win {
     float2 v[P][kW][kW];
-    int zc[P];
+    int zc[P];      // unwrapped z of the plane, kNoPlane when empty
+    int zoff[P];
+    int yoff[kW], xoff[kW];
 };
 
+// offsets of the 4 residues of a box starting at unwrapped j0: position j0 + ((r - j0) & 3)
+__device__ __forceinline__ void set_offsets(int (&off)[kW], int j0, int G, int stride) {
+#pragma unroll
+    for (int r = 0; r < kW; ++r) off[r] = wrapc(j0 + ((r - j0) & 3), G) * stride;
+}
+
 // Minimum resident CTAs per SM requested from the register allocator for the gridding kernels, by
-// planes per lane P (1: 8 coils per warp, 2: 16, 4: 32); 1 leaves the allocator unconstrained. Four
-// CTAs (128 registers, a few spilled words) measured faster for the spread at P = 1 and the
-// interpolation at P = 2 than the unconstrained allocation (3 CTAs) on the 128^3 and
-// 160x256x256 cones workloads.
+// planes per lane P (1: 8 coils per warp, 2: 16, 4: 32); 1 leaves the allocator unconstrained.
 #ifndef CS_INTERP_MINB_P1
-#define CS_INTERP_MINB_P1 1
+#define CS_INTERP_MINB_P1 4
 #endif
 #ifndef CS_INTERP_MINB_P2
 #define CS_INTERP_MINB_P2 4
@@ -339,15 +374,17 @@ struct Win {
 #define CS_SPREAD_MINB_P1 4
 #endif
 #ifndef CS_SPREAD_MINB_P2
-#define CS_SPREAD_MINB_P2 1
+#define CS_SPREAD_MINB_P2 4
 #endif
 #define CS_INTERP_MINB(P) ((P) == 1 ? CS_INTERP_MINB_P1 : (P) == 2 ? CS_INTERP_MINB_P2 : 1)
 #define CS_SPREAD_MINB(P) ((P) == 1 ? CS_SPREAD_MINB_P1 : (P) == 2 ? CS_SPREAD_MINB_P2 : 1)
 
-template <int ND, int P>
-__global__ void __launch_bounds__(128, CS_INTERP_MINB(P)) interp_kernel(GridArgs A, int mode, const float2* __restrict__ ysub,
-                                                     float2* __restrict__ out) {
-    constexpr int S = (ND == 3) ? 4 / P : 1;     // lanes per coil
+// S lanes per coil, P planes per lane: S * P = 4 for 3D plans, S = P = 1 for 2D plans (one plane
+// z = 0 whose z weight is 1).
+template <int S, int P>
+__global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
+    interp_kernel(GridArgs A, int mode, const float2* __restrict__ ysub, float2* __restrict__ out) {
+    __shared__ __align__(16) float srec[kGridWarps * kStage * kRec];
     const int lane = threadIdx.x & 31;
     const int coil_l = lane / S, slice = lane % S;
     const bool active = coil_l < A.gsize;
@@ -356,147 +393,134 @@ __global__ void __launch_bounds__(128, CS_INTERP_MINB(P)) interp_kernel(GridArgs
     const int64_t s0 = warp * A.chunk;
     if (s0 >= A.N) return;                       // whole warp exits together
     const int64_t s1 = min(A.N, s0 + A.chunk);
+    float* wrec = srec + (threadIdx.x >> 5) * (kStage * kRec);
+    const int sy = A.Gx * A.C, sz = A.Gy * A.Gx * A.C;
+    const float2* g = A.grid + c;
     Win<P> W;
 #pragma unroll
-    for (int p = 0; p < P; ++p) W.zc[p] = -1;
-    int cy = -100, cx = -100;
-    float wnext = rec_word(A, s0, lane);
-    for (int64_t s = s0; s < s1; ++s) {
-        SampleBox<ND> B;
-        sample_box<ND>(wnext, lane, B);
-        wnext = rec_word(A, s + 1, lane);   // prefetch the next sample's record
-        const int dy = B.jy - cy, dx = B.jx - cx;
-        if (abs(dy) > 1 || abs(dx) > 1) {
+    for (int p = 0; p < P; ++p) {
+        W.zc[p] = kNoPlane;
+        W.zoff[p] = 0;
 #pragma unroll
-            for (int p = 0; p < P; ++p) W.zc[p] = -1;    // reload every plane below
-        } else {
-            if (dy != 0) {
+        for (int b = 0; b < kW; ++b)
 #pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    if (dy > 0) {
+            for (int d = 0; d < kW; ++d) W.v[p][b][d] = make_float2(0.f, 0.f);
+    }
 #pragma unroll
-                        for (int b = 0; b < kW - 1; ++b)
+    for (int r = 0; r < kW; ++r) W.yoff[r] = W.xoff[r] = 0;
+    int cy = kNoPlane, cx = kNoPlane;
+    for (int64_t base = s0; base < s1; base += kStage) {
+        const int n = (int)min((int64_t)kStage, s1 - base);
+        stage_records(A, base, n, wrec, lane);
+#pragma unroll 1
+        for (int i = 0; i < n; ++i) {
+            const float* r = wrec + i * kRec;
+            const BoxHead B = box_head(r);
+            const int dy = B.jy - cy, dx = B.jx - cx;
+            if ((unsigned)(dy + 1) > 2u || (unsigned)(dx + 1) > 2u) {   // not a step of -1, 0 or +1
+                set_offsets(W.yoff, B.jy, A.Gy, sy);
+                set_offsets(W.xoff, B.jx, A.Gx, A.C);
 #pragma unroll
-                            for (int d = 0; d < kW; ++d) W.v[p][b][d] = W.v[p][b + 1][d];
-                    } else {
-#pragma unroll
-                        for (int b = kW - 1; b > 0; --b)
-#pragma unroll
-                            for (int d = 0; d < kW; ++d) W.v[p][b][d] = W.v[p][b - 1][d];
-                    }
-                    if (W.zc[p] >= 0 && active) {
-                        if (dy > 0) {
-                            const int yy = wrapc(B.jy + kW - 1, A.Gy);
-#pragma unroll
-                            for (int d = 0; d < kW; ++d)
-                                W.v[p][kW - 1][d] = __ldg(A.grid + gaddr(A, W.zc[p], yy, wrapc(cx + d, A.Gx), c));
-                        } else {
-                            const int yy = B.jy;
-#pragma unroll
-                            for (int d = 0; d < kW; ++d)
-                                W.v[p][0][d] = __ldg(A.grid + gaddr(A, W.zc[p], yy, wrapc(cx + d, A.Gx), c));
-                        }
-                    }
-                }
-                cy = B.jy;
-            }
-            if (dx != 0) {
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    if (dx > 0) {
-#pragma unroll
-                        for (int b = 0; b < kW; ++b)
-#pragma unroll
-                            for (int d = 0; d < kW - 1; ++d) W.v[p][b][d] = W.v[p][b][d + 1];
-                    } else {
-#pragma unroll
-                        for (int b = 0; b < kW; ++b)
-#pragma unroll
-                            for (int d = kW - 1; d > 0; --d) W.v[p][b][d] = W.v[p][b][d - 1];
-                    }
-                    if (W.zc[p] >= 0 && active) {
-                        if (dx > 0) {
-                            const int xx = wrapc(B.jx + kW - 1, A.Gx);
-#pragma unroll
-                            for (int b = 0; b < kW; ++b)
-                                W.v[p][b][kW - 1] = __ldg(A.grid + gaddr(A, W.zc[p], wrapc(cy + b, A.Gy), xx, c));
-                        } else {
-                            const int xx = B.jx;
-#pragma unroll
-                            for (int b = 0; b < kW; ++b)
-                                W.v[p][b][0] = __ldg(A.grid + gaddr(A, W.zc[p], wrapc(cy + b, A.Gy), xx, c));
-                        }
-                    }
-                }
-                cx = B.jx;
-            }
-        }
-        cy = B.jy;
-        cx = B.jx;
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            // z of this plane inside the box [jz, jz+3]
-            int rel = 0, zw = 0;
-            if (ND == 3) {
-                const int q = slice + p * S;                       // residue held by this plane
-                rel = (q - B.jz) & 3;
-                zw = wrapc(B.jz + rel, A.Gz);
-            }
-            if (W.zc[p] != zw) {
-                if (active) {
-#pragma unroll
-                    for (int b = 0; b < kW; ++b) {
-                        const int yy = wrapc(cy + b, A.Gy);
-#pragma unroll
-                        for (int d = 0; d < kW; ++d) W.v[p][b][d] = __ldg(A.grid + gaddr(A, zw, yy, wrapc(cx + d, A.Gx), c));
-                    }
-                }
-                W.zc[p] = zw;
-            }
-            const float wzp = (rel == 0) ? B.wz[0] : (rel == 1 ? B.wz[1] : (rel == 2 ? B.wz[2] : B.wz[3]));
-            float2 pa = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int b = 0; b < kW; ++b) {
-                float2 r = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int d = 0; d < kW; ++d) {
-                    r.x = fmaf(B.wx[d], W.v[p][b][d].x, r.x);
-                    r.y = fmaf(B.wx[d], W.v[p][b][d].y, r.y);
-                }
-                pa.x = fmaf(B.wy[b], r.x, pa.x);
-                pa.y = fmaf(B.wy[b], r.y, pa.y);
-            }
-            acc.x = fmaf(wzp, pa.x, acc.x);
-            acc.y = fmaf(wzp, pa.y, acc.y);
-        }
-        if (S > 1) {
-#pragma unroll
-            for (int o = 1; o < S; o <<= 1) {
-                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-            }
-        }
-        if (active && slice == 0) {
-            acc = cscale(acc, B.sw);
-            if (mode == OUT_USER) {
-                out[(int64_t)c * A.N + B.perm] = acc;
-            } else if (mode == OUT_RESID) {
-                out[s * A.C + c] = csub(acc, ysub[(int64_t)c * A.N + B.perm]);
+                for (int p = 0; p < P; ++p) W.zc[p] = kNoPlane;    // every plane reloads below
             } else {
-                out[s * A.C + c] = acc;
+                if (dy != 0) {
+                    // the leaving row (old start for a step up, old end for a step down) takes the
+                    // entering row, whose grid index has the same residue
+                    const int rr = (dy > 0) ? (cy & 3) : ((cy + 3) & 3);
+                    const int ynew = (dy > 0) ? cy + 4 : cy - 1;
+                    with_residue(rr, [&](auto RC) {
+                        constexpr int R = decltype(RC)::value;
+                        W.yoff[R] = wrapc(ynew, A.Gy) * sy;
+                        if (active) {
+#pragma unroll
+                            for (int p = 0; p < P; ++p)
+                                if (W.zc[p] != kNoPlane) {
+#pragma unroll
+                                    for (int d = 0; d < kW; ++d) W.v[p][R][d] = __ldg(g + (W.zoff[p] + W.yoff[R] + W.xoff[d]));
+                                }
+                        }
+                    });
+                }
+                if (dx != 0) {
+                    const int rr = (dx > 0) ? (cx & 3) : ((cx + 3) & 3);
+                    const int xnew = (dx > 0) ? cx + 4 : cx - 1;
+                    with_residue(rr, [&](auto RC) {
+                        constexpr int R = decltype(RC)::value;
+                        W.xoff[R] = wrapc(xnew, A.Gx) * A.C;
+                        if (active) {
+#pragma unroll
+                            for (int p = 0; p < P; ++p)
+                                if (W.zc[p] != kNoPlane) {
+#pragma unroll
+                                    for (int b = 0; b < kW; ++b) W.v[p][b][R] = __ldg(g + (W.zoff[p] + W.yoff[b] + W.xoff[R]));
+                                }
+                        }
+                    });
+                }
+            }
+            cy = B.jy;
+            cx = B.jx;
+            float2 acc = make_float2(0.f, 0.f);
+            const float4 wy = *reinterpret_cast<const float4*>(r + 4);
+            const float4 wx = *reinterpret_cast<const float4*>(r + 8);
+            const float wyv[kW] = {wy.x, wy.y, wy.z, wy.w};
+            const float wxv[kW] = {wx.x, wx.y, wx.z, wx.w};
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const int q = slice + p * S;                    // z residue held by this plane
+                const int zq = B.jz + ((q - B.jz) & 3);
+                if (zq != W.zc[p]) {
+                    W.zc[p] = zq;
+                    W.zoff[p] = wrapc(zq, A.Gz) * sz;
+                    if (active) {
+#pragma unroll
+                        for (int b = 0; b < kW; ++b)
+#pragma unroll
+                            for (int d = 0; d < kW; ++d) W.v[p][b][d] = __ldg(g + (W.zoff[p] + W.yoff[b] + W.xoff[d]));
+                    }
+                }
+                const float wzp = r[q];
+                float2 pa = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int b = 0; b < kW; ++b) {
+                    float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int d = 0; d < kW; ++d) {
+                        t.x = fmaf(wxv[d], W.v[p][b][d].x, t.x);
+                        t.y = fmaf(wxv[d], W.v[p][b][d].y, t.y);
+                    }
+                    pa.x = fmaf(wyv[b], t.x, pa.x);
+                    pa.y = fmaf(wyv[b], t.y, pa.y);
+                }
+                acc.x = fmaf(wzp, pa.x, acc.x);
+                acc.y = fmaf(wzp, pa.y, acc.y);
+            }
+            if (S > 1) {
+#pragma unroll
+                for (int o = 1; o < S; o <<= 1) {
+                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+                }
+            }
+            if (active && slice == 0) {
+                const int64_t s = base + i;
+                acc = cscale(acc, B.sw);
+                if (mode == OUT_USER) {
+                    out[(int64_t)c * A.N + B.perm] = acc;
+                } else if (mode == OUT_RESID) {
+                    out[s * A.C + c] = csub(acc, ysub[(int64_t)c * A.N + B.perm]);
+                } else {
+                    out[s * A.C + c] = acc;
+                }
             }
         }
     }
 }
 
-__device__ __forceinline__ void red_add(float2* p, float2 v) {
-    if (v.x != 0.f || v.y != 0.f) atomicAdd(p, v);
-}
-
-template <int ND, int P>
-__global__ void __launch_bounds__(128, CS_SPREAD_MINB(P)) spread_kernel(GridArgs A, const float2* __restrict__ yin, int sorted_in) {
-    constexpr int S = (ND == 3) ? 4 / P : 1;
+template <int S, int P>
+__global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
+    spread_kernel(GridArgs A, const float2* __restrict__ yin, int sorted_in) {
+    __shared__ __align__(16) float srec[kGridWarps * kStage * kRec];
     const int lane = threadIdx.x & 31;
     const int coil_l = lane / S, slice = lane % S;
     const bool active = coil_l < A.gsize;
@@ -505,138 +529,118 @@ __global__ void __launch_bounds__(128, CS_SPREAD_MINB(P)) spread_kernel(GridArgs
     const int64_t s0 = warp * A.chunk;
     if (s0 >= A.N) return;
     const int64_t s1 = min(A.N, s0 + A.chunk);
+    float* wrec = srec + (threadIdx.x >> 5) * (kStage * kRec);
+    const int sy = A.Gx * A.C, sz = A.Gy * A.Gx * A.C;
+    float2* g = A.grid + c;
     Win<P> W;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        W.zc[p] = -1;
+        W.zc[p] = kNoPlane;
+        W.zoff[p] = 0;
 #pragma unroll
         for (int b = 0; b < kW; ++b)
 #pragma unroll
             for (int d = 0; d < kW; ++d) W.v[p][b][d] = make_float2(0.f, 0.f);
     }
-    int cy = -100, cx = -100;
+#pragma unroll
+    for (int r = 0; r < kW; ++r) W.yoff[r] = W.xoff[r] = 0;
+    int cy = kNoPlane, cx = kNoPlane;
     auto flush_plane = [&](int p) {
-        if (W.zc[p] >= 0 && active) {
+        if (active && W.zc[p] != kNoPlane) {
 #pragma unroll
-            for (int b = 0; b < kW; ++b) {
-                const int yy = wrapc(cy + b, A.Gy);
+            for (int b = 0; b < kW; ++b)
 #pragma unroll
-                for (int d = 0; d < kW; ++d) red_add(A.grid + gaddr(A, W.zc[p], yy, wrapc(cx + d, A.Gx), c), W.v[p][b][d]);
-            }
+                for (int d = 0; d < kW; ++d) atomicAdd(g + (W.zoff[p] + W.yoff[b] + W.xoff[d]), W.v[p][b][d]);
         }
 #pragma unroll
         for (int b = 0; b < kW; ++b)
 #pragma unroll
             for (int d = 0; d < kW; ++d) W.v[p][b][d] = make_float2(0.f, 0.f);
     };
-    float wnext = rec_word(A, s0, lane);
-    // the sample value: sorted scratch [N][C] (prefetched one sample ahead) or user order [C][N]
-    auto load_v = [&](int64_t s, int perm) -> float2 {
-        if (!active || s >= A.N) return make_float2(0.f, 0.f);
-        return sorted_in ? yin[s * A.C + c] : yin[(int64_t)c * A.N + perm];
+    // the sample value: sorted scratch [N][C] or user order [C][N]
+    auto load_v = [&](int64_t s, const float* r) -> float2 {
+        if (!active) return make_float2(0.f, 0.f);
+        return sorted_in ? yin[s * A.C + c] : yin[(int64_t)c * A.N + __float_as_int(r[14])];
     };
-    float2 vnext = sorted_in ? load_v(s0, 0) : make_float2(0.f, 0.f);
-    for (int64_t s = s0; s < s1; ++s) {
-        SampleBox<ND> B;
-        sample_box<ND>(wnext, lane, B);
-        float2 v = sorted_in ? vnext : load_v(s, B.perm);
-        wnext = rec_word(A, s + 1, lane);
-        if (sorted_in) vnext = load_v(s + 1, 0);
-        const int dy = B.jy - cy, dx = B.jx - cx;
-        if (abs(dy) > 1 || abs(dx) > 1) {
+    for (int64_t base = s0; base < s1; base += kStage) {
+        const int n = (int)min((int64_t)kStage, s1 - base);
+        stage_records(A, base, n, wrec, lane);
+        float2 vnext = load_v(base, wrec);
+#pragma unroll 1
+        for (int i = 0; i < n; ++i) {
+            const float* r = wrec + i * kRec;
+            const BoxHead B = box_head(r);
+            float2 v = vnext;
+            if (i + 1 < n) vnext = load_v(base + i + 1, r + kRec);   // one sample ahead
+            const int dy = B.jy - cy, dx = B.jx - cx;
+            if ((unsigned)(dy + 1) > 2u || (unsigned)(dx + 1) > 2u) {   // not a step of -1, 0 or +1
+#pragma unroll
+                for (int p = 0; p < P; ++p) flush_plane(p);
+                set_offsets(W.yoff, B.jy, A.Gy, sy);
+                set_offsets(W.xoff, B.jx, A.Gx, A.C);
+            } else {
+                if (dy != 0) {
+                    // write out the leaving row (old start for a step up, old end for a step down);
+                    // its registers and residue pass to the entering row
+                    const int rr = (dy > 0) ? (cy & 3) : ((cy + 3) & 3);
+                    const int ynew = (dy > 0) ? cy + 4 : cy - 1;
+                    with_residue(rr, [&](auto RC) {
+                        constexpr int R = decltype(RC)::value;
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            if (active && W.zc[p] != kNoPlane) {
+#pragma unroll
+                                for (int d = 0; d < kW; ++d) atomicAdd(g + (W.zoff[p] + W.yoff[R] + W.xoff[d]), W.v[p][R][d]);
+                            }
+#pragma unroll
+                            for (int d = 0; d < kW; ++d) W.v[p][R][d] = make_float2(0.f, 0.f);
+                        }
+                        W.yoff[R] = wrapc(ynew, A.Gy) * sy;
+                    });
+                }
+                if (dx != 0) {
+                    const int rr = (dx > 0) ? (cx & 3) : ((cx + 3) & 3);
+                    const int xnew = (dx > 0) ? cx + 4 : cx - 1;
+                    with_residue(rr, [&](auto RC) {
+                        constexpr int R = decltype(RC)::value;
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            if (active && W.zc[p] != kNoPlane) {
+#pragma unroll
+                                for (int b = 0; b < kW; ++b) atomicAdd(g + (W.zoff[p] + W.yoff[b] + W.xoff[R]), W.v[p][b][R]);
+                            }
+#pragma unroll
+                            for (int b = 0; b < kW; ++b) W.v[p][b][R] = make_float2(0.f, 0.f);
+                        }
+                        W.xoff[R] = wrapc(xnew, A.Gx) * A.C;
+                    });
+                }
+            }
+            cy = B.jy;
+            cx = B.jx;
+            v = cscale(v, B.sw);
+            const float4 wy = *reinterpret_cast<const float4*>(r + 4);
+            const float4 wx = *reinterpret_cast<const float4*>(r + 8);
+            const float wyv[kW] = {wy.x, wy.y, wy.z, wy.w};
+            const float wxv[kW] = {wx.x, wx.y, wx.z, wx.w};
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                flush_plane(p);
-                W.zc[p] = -1;
-            }
-        } else {
-            if (dy != 0) {
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    if (dy > 0) {
-                        if (W.zc[p] >= 0 && active) {
-                            const int yy = cy;   // leaving row 0
-#pragma unroll
-                            for (int d = 0; d < kW; ++d) red_add(A.grid + gaddr(A, W.zc[p], yy, wrapc(cx + d, A.Gx), c), W.v[p][0][d]);
-                        }
-#pragma unroll
-                        for (int b = 0; b < kW - 1; ++b)
-#pragma unroll
-                            for (int d = 0; d < kW; ++d) W.v[p][b][d] = W.v[p][b + 1][d];
-#pragma unroll
-                        for (int d = 0; d < kW; ++d) W.v[p][kW - 1][d] = make_float2(0.f, 0.f);
-                    } else {
-                        if (W.zc[p] >= 0 && active) {
-                            const int yy = wrapc(cy + kW - 1, A.Gy);   // leaving row 3
-#pragma unroll
-                            for (int d = 0; d < kW; ++d) red_add(A.grid + gaddr(A, W.zc[p], yy, wrapc(cx + d, A.Gx), c), W.v[p][kW - 1][d]);
-                        }
-#pragma unroll
-                        for (int b = kW - 1; b > 0; --b)
-#pragma unroll
-                            for (int d = 0; d < kW; ++d) W.v[p][b][d] = W.v[p][b - 1][d];
-#pragma unroll
-                        for (int d = 0; d < kW; ++d) W.v[p][0][d] = make_float2(0.f, 0.f);
-                    }
-                }
-                cy = B.jy;
-            }
-            if (dx != 0) {
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    if (dx > 0) {
-                        if (W.zc[p] >= 0 && active) {
-                            const int xx = cx;   // leaving column 0
-#pragma unroll
-                            for (int b = 0; b < kW; ++b) red_add(A.grid + gaddr(A, W.zc[p], wrapc(cy + b, A.Gy), xx, c), W.v[p][b][0]);
-                        }
-#pragma unroll
-                        for (int b = 0; b < kW; ++b)
-#pragma unroll
-                            for (int d = 0; d < kW - 1; ++d) W.v[p][b][d] = W.v[p][b][d + 1];
-#pragma unroll
-                        for (int b = 0; b < kW; ++b) W.v[p][b][kW - 1] = make_float2(0.f, 0.f);
-                    } else {
-                        if (W.zc[p] >= 0 && active) {
-                            const int xx = wrapc(cx + kW - 1, A.Gx);   // leaving column 3
-#pragma unroll
-                            for (int b = 0; b < kW; ++b) red_add(A.grid + gaddr(A, W.zc[p], wrapc(cy + b, A.Gy), xx, c), W.v[p][b][kW - 1]);
-                        }
-#pragma unroll
-                        for (int b = 0; b < kW; ++b)
-#pragma unroll
-                            for (int d = kW - 1; d > 0; --d) W.v[p][b][d] = W.v[p][b][d - 1];
-#pragma unroll
-                        for (int b = 0; b < kW; ++b) W.v[p][b][0] = make_float2(0.f, 0.f);
-                    }
-                }
-                cx = B.jx;
-            }
-        }
-        cy = B.jy;
-        cx = B.jx;
-        v = cscale(v, B.sw);
-#pragma unroll
-        for (int p = 0; p < P; ++p) {
-            int rel = 0, zw = 0;
-            if (ND == 3) {
                 const int q = slice + p * S;
-                rel = (q - B.jz) & 3;
-                zw = wrapc(B.jz + rel, A.Gz);
-            }
-            if (W.zc[p] != zw) {
-                flush_plane(p);
-                W.zc[p] = zw;
-            }
-            const float wzp = (rel == 0) ? B.wz[0] : (rel == 1 ? B.wz[1] : (rel == 2 ? B.wz[2] : B.wz[3]));
-            const float2 va = cscale(v, wzp);
+                const int zq = B.jz + ((q - B.jz) & 3);
+                if (zq != W.zc[p]) {
+                    flush_plane(p);
+                    W.zc[p] = zq;
+                    W.zoff[p] = wrapc(zq, A.Gz) * sz;
+                }
+                const float2 va = cscale(v, r[q]);
 #pragma unroll
-            for (int b = 0; b < kW; ++b) {
-                const float2 vb = cscale(va, B.wy[b]);
+                for (int b = 0; b < kW; ++b) {
+                    const float2 vb = cscale(va, wyv[b]);
 #pragma unroll
-                for (int d = 0; d < kW; ++d) {
-                    W.v[p][b][d].x = fmaf(B.wx[d], vb.x, W.v[p][b][d].x);
-                    W.v[p][b][d].y = fmaf(B.wx[d], vb.y, W.v[p][b][d].y);
+                    for (int d = 0; d < kW; ++d) {
+                        W.v[p][b][d].x = fmaf(wxv[d], vb.x, W.v[p][b][d].x);
+                        W.v[p][b][d].y = fmaf(wxv[d], vb.y, W.v[p][b][d].y);
+                    }
                 }
             }
         }
@@ -670,7 +674,7 @@ static cs_status launch_grid_op(const cs_plan* p, int ncoils, int mode, const fl
                                 const float2* yin, int sorted_in, cudaStream_t st) {
     GridArgs A = make_grid_args(p, ncoils);
     const int64_t warps = (p->N + A.chunk - 1) / A.chunk;
-    const unsigned nb = (unsigned)((warps * 32 + 127) / 128);
+    const unsigned nb = (unsigned)((warps + kGridWarps - 1) / kGridWarps);
     if (nb == 0) return CS_OK;
     const int cmax = SPREAD ? p->spread_coils : p->interp_coils;   // 8, 16 or 32 coils per warp
     const int nch = (ncoils + cmax - 1) / cmax;
@@ -679,21 +683,21 @@ static cs_status launch_grid_op(const cs_plan* p, int ncoils, int mode, const fl
         const int g = std::min(cbal, ncoils - c0);
         A.c0 = c0;
         A.gsize = g;
-        int P = 4;
+        int P = 1;
         if (p->ndim == 3) P = (g <= 8) ? 1 : (g <= 16 ? 2 : 4);
         prof_begin(SPREAD ? ST_SPREAD : ST_INTERP, st);
         if (p->ndim == 2) {
-            if (SPREAD) spread_kernel<2, 1><<<nb, 128, 0, st>>>(A, yin, sorted_in);
-            else interp_kernel<2, 1><<<nb, 128, 0, st>>>(A, mode, ysub, out);
+            if (SPREAD) spread_kernel<1, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
+            else interp_kernel<1, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
         } else if (P == 1) {
-            if (SPREAD) spread_kernel<3, 1><<<nb, 128, 0, st>>>(A, yin, sorted_in);
-            else interp_kernel<3, 1><<<nb, 128, 0, st>>>(A, mode, ysub, out);
+            if (SPREAD) spread_kernel<4, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
+            else interp_kernel<4, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
         } else if (P == 2) {
-            if (SPREAD) spread_kernel<3, 2><<<nb, 128, 0, st>>>(A, yin, sorted_in);
-            else interp_kernel<3, 2><<<nb, 128, 0, st>>>(A, mode, ysub, out);
+            if (SPREAD) spread_kernel<2, 2><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
+            else interp_kernel<2, 2><<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
         } else {
-            if (SPREAD) spread_kernel<3, 4><<<nb, 128, 0, st>>>(A, yin, sorted_in);
-            else interp_kernel<3, 4><<<nb, 128, 0, st>>>(A, mode, ysub, out);
+            if (SPREAD) spread_kernel<1, 4><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
+            else interp_kernel<1, 4><<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
         }
         CS_LAUNCH_CHECK();
         prof_end(SPREAD ? ST_SPREAD : ST_INTERP, st);

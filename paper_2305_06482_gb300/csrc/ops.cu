@@ -221,6 +221,8 @@ static cs_status plan_build(cs_plan* p, const cs_geom* g, cudaStream_t st) {
         return CS_OK;
     }
     CS_REQUIRE(g->traj != nullptr && g->dcf != nullptr && p->N > 0, CS_ERR_INVALID_ARG, "non-Cartesian plan needs traj, dcf, N > 0");
+    CS_REQUIRE(p->G * (int64_t)p->max_coils < (int64_t)1 << 31, CS_ERR_UNSUPPORTED_SIZE,
+               "grid points x max_coils must stay below 2^31 (32-bit gridding offsets)");
     CS_REQUIRE(p->N < (int64_t)1 << 31, CS_ERR_UNSUPPORTED_SIZE, "more than 2^31 samples");
     const int64_t bsz = (nd == 3) ? (int64_t)p->img[0] * p->grid[1] * p->grid[2] : p->G;
     CS_TRY_CUDA(cudaMalloc(&p->bufB, sizeof(float2) * C * bsz));

@@ -3,6 +3,9 @@ stream), for profiling individual kernels with small launch counts.
 
   python -m paper_2305_06482_gb300.microbench nufft  [--config cones3d_128|cones3d_large] [--warmup W] [--iters N]
       multicoil NUFFT forward (sense_fwd) and adjoint (sense_adj), all coils
+  python -m paper_2305_06482_gb300.microbench normal [--config cones3d_128|cones3d_large] [--warmup W] [--iters N]
+      sketched normal operator A_S^H A_S v + lambda v with V = 5 unsketched and S = 5 sketched coils
+      (the inner-iteration operator of the sketched sub-problem), with the per-stage device times
   python -m paper_2305_06482_gb300.microbench sketch [--voxels D] [--iters N]
       sketched maps (40 coils, V = 5, S = 5): FP32 CUDA cores vs BF16 split on the tensor cores
   python -m paper_2305_06482_gb300.microbench batched [--slices 64] [--iters N]
@@ -72,6 +75,39 @@ def nufft(args):
     model = 2 * C * (8 * D + 48 * G + 8 * N) + 2 * (16 * N + 16 * D)
     print(f"{args.config}: forward {f:.3f} ms, adjoint {g:.3f} ms, fwd+adj model bytes {model / 1e9:.2f} GB "
           f"-> {model / ((f + g) * 1e-3) / 1e9:.0f} GB/s")
+
+
+def normal(args):
+    cfg = CONFIGS[args.config]
+    dev = torch.device("cuda")
+    img, grid, C = cfg["img"], cfg["grid"], cfg["nc"]
+    V, S = 5, 5
+    traj = synthdata.cones_trajectory(cfg["n_int"], 512)
+    dcf = synthdata.cones_dcf(traj, img, cfg["n_int"], 512)
+    plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=torch.from_numpy(traj).to(dev), dcf=torch.from_numpy(dcf).to(dev),
+                   grid=grid)
+    v = synthdata.phantom_torch(img, seed=1, device=dev)
+    maps = synthdata.coil_maps_torch(img, V + S, device=dev)
+    mv, ms = maps[:V].contiguous(), maps[V:].contiguous()
+    z = torch.empty(img, dtype=torch.complex64, device=dev)
+    for _ in range(args.warmup):
+        cs.sketched_normal_apply(plan, v, mv, ms, 1e-3, z)
+    torch.cuda.synchronize()
+    a, b = _events()
+    a.record()
+    for _ in range(args.iters):
+        cs.sketched_normal_apply(plan, v, mv, ms, 1e-3, z)
+    b.record()
+    torch.cuda.synchronize()
+    ms_ = a.elapsed_time(b) / args.iters
+    cs.profile(True)
+    for _ in range(args.iters):
+        cs.sketched_normal_apply(plan, v, mv, ms, 1e-3, z)
+    torch.cuda.synchronize()
+    st = {k: cs.profile_read(k) for k in ("spread", "interp", "fft_plain", "expand", "reduce")}
+    cs.profile(False)
+    parts = ", ".join(f"{k} {t / args.iters:.3f} ms" for k, (t, n) in st.items() if n)
+    print(f"{args.config}: sketched normal apply (V={V}, S={S}): {ms_:.3f} ms; per stage: {parts}")
 
 
 def sketch(args):
@@ -162,14 +198,14 @@ def batched(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["nufft", "sketch", "cart2d", "batched"])
+    ap.add_argument("what", choices=["nufft", "normal", "sketch", "cart2d", "batched"])
     ap.add_argument("--slices", type=int, default=64)
     ap.add_argument("--config", default="cones3d_128", choices=list(CONFIGS))
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--iters", type=int, default=5)
     ap.add_argument("--voxels", type=int, default=160 * 256 * 256)
     args = ap.parse_args()
-    {"nufft": nufft, "sketch": sketch, "cart2d": cart2d, "batched": batched}[args.what](args)
+    {"nufft": nufft, "normal": normal, "sketch": sketch, "cart2d": cart2d, "batched": batched}[args.what](args)
 
 
 if __name__ == "__main__":
