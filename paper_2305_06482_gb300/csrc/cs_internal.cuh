@@ -131,7 +131,7 @@ struct cs_plan {
     int spread_chunk = 0;         // samples per spreading work item
     int interp_chunk = 0;         // consecutive sorted samples per warp (interp and spread)
     int interp_coils = 16;        // coils per warp in interpolation (8, 16 or 32)
-    int spread_coils = 8;         // coils per warp in spreading (8 or 16)
+    int spread_coils = 16;        // coils per warp in spreading (8 or 16)
     float* phi = nullptr;         // KB kernel table [2049] on [0, 2]
     float* rec = nullptr;         // [N][16] per-sample gridding records (sorted order)
 

@@ -52,60 +52,127 @@ void fft_len_free(FftLen& f) {
 }
 
 // ------------------------------------------------------------------------------------------
-// small DFTs (sign = -1 forward, +1 inverse); roots of unity for the generic radices are read
-// from the length-n twiddle table (r divides n, so exp(-2 pi i m / r) = tw[m n / r]).
+// Small DFTs, the direction a template parameter (SIGN = -1 forward, +1 inverse).  Radices 2, 4
+// and 8 are split-radix butterflies; the odd radices use the symmetric form
+//   X_m = x_0 + sum_q cos(2 pi q m / R) (x_q + x_{R-q}) + SIGN i sum_q sin(2 pi q m / R) (x_q - x_{R-q})
+// (q, m = 1 .. (R-1)/2, X_{R-m} with the opposite sign of the second sum), whose cosines and
+// sines are compile-time constants.
+
+// cos and sin of 2 pi k / R evaluated at compile time in double by Taylor series after reducing
+// the angle to [-pi, pi] (30 terms: truncation error far below double rounding there)
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double ct_reduce(double x) {
+    while (x > kTwoPi / 2) x -= kTwoPi;
+    while (x < -kTwoPi / 2) x += kTwoPi;
+    return x;
+}
+constexpr double ct_cos(double x) {
+    x = ct_reduce(x);
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 30; ++k) {
+        term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+        sum += term;
+    }
+    return sum;
+}
+constexpr double ct_sin(double x) {
+    x = ct_reduce(x);
+    double term = x, sum = x;
+    for (int k = 1; k < 30; ++k) {
+        term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+
 template <int R>
-__device__ __forceinline__ void dft_small(float2 (&v)[R], int sign, const float2* tw, int n) {
-    float2 o[R];
-#pragma unroll
-    for (int m = 0; m < R; ++m) {
-        float2 acc = v[0];
-#pragma unroll
-        for (int q = 1; q < R; ++q) {
-            float2 w = tw[((q * m) % R) * (n / R)];
-            if (sign > 0) w.y = -w.y;
-            acc = cadd(acc, cmul(v[q], w));
+struct Roots {
+    float c[R], s[R];
+    constexpr Roots() : c(), s() {
+        for (int k = 0; k < R; ++k) {
+            c[k] = (float)ct_cos(kTwoPi * k / R);
+            s[k] = (float)ct_sin(kTwoPi * k / R);
         }
-        o[m] = acc;
+    }
+};
+
+template <int R, int SIGN>
+__device__ __forceinline__ void dft(float2 (&v)[R]) {
+    static_assert(R % 2 == 1, "odd radix");
+    constexpr int H = (R - 1) / 2;
+    constexpr Roots<R> rt{};
+    float2 t[H], d[H];
+#pragma unroll
+    for (int q = 1; q <= H; ++q) {
+        t[q - 1] = cadd(v[q], v[R - q]);
+        d[q - 1] = csub(v[q], v[R - q]);
+    }
+    float2 o[R];
+    o[0] = v[0];
+#pragma unroll
+    for (int q = 0; q < H; ++q) o[0] = cadd(o[0], t[q]);
+#pragma unroll
+    for (int m = 1; m <= H; ++m) {
+        float2 a = v[0], b = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 1; q <= H; ++q) {
+            const float cq = rt.c[(q * m) % R], sq = rt.s[(q * m) % R];
+            a.x = fmaf(cq, t[q - 1].x, a.x);
+            a.y = fmaf(cq, t[q - 1].y, a.y);
+            b.x = fmaf(sq, d[q - 1].x, b.x);
+            b.y = fmaf(sq, d[q - 1].y, b.y);
+        }
+        // a + SIGN i b and a - SIGN i b
+        o[m] = make_float2(a.x - SIGN * b.y, a.y + SIGN * b.x);
+        o[R - m] = make_float2(a.x + SIGN * b.y, a.y - SIGN * b.x);
     }
 #pragma unroll
     for (int m = 0; m < R; ++m) v[m] = o[m];
 }
 
-__device__ __forceinline__ float2 rot_mi(float2 a, int sign) {
-    // multiply by -i (forward) or +i (inverse)
-    return sign < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+template <int SIGN>
+__device__ __forceinline__ float2 rot_i(float2 a) {   // multiply by SIGN i
+    return SIGN < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
 }
 
 template <>
-__device__ __forceinline__ void dft_small<2>(float2 (&v)[2], int, const float2*, int) {
-    float2 a = v[0], b = v[1];
+__device__ __forceinline__ void dft<2, -1>(float2 (&v)[2]) {
+    const float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+}
+template <>
+__device__ __forceinline__ void dft<2, 1>(float2 (&v)[2]) {
+    const float2 a = v[0], b = v[1];
     v[0] = cadd(a, b);
     v[1] = csub(a, b);
 }
 
-template <>
-__device__ __forceinline__ void dft_small<4>(float2 (&v)[4], int sign, const float2*, int) {
-    float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-    float2 s13 = cadd(v[1], v[3]), d13 = rot_mi(csub(v[1], v[3]), sign);
+template <int SIGN>
+__device__ __forceinline__ void dft4(float2 (&v)[4]) {
+    const float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    const float2 s13 = cadd(v[1], v[3]), d13 = rot_i<SIGN>(csub(v[1], v[3]));
     v[0] = cadd(s02, s13);
     v[2] = csub(s02, s13);
     v[1] = cadd(d02, d13);
     v[3] = csub(d02, d13);
 }
-
 template <>
-__device__ __forceinline__ void dft_small<8>(float2 (&v)[8], int sign, const float2*, int) {
+__device__ __forceinline__ void dft<4, -1>(float2 (&v)[4]) { dft4<-1>(v); }
+template <>
+__device__ __forceinline__ void dft<4, 1>(float2 (&v)[4]) { dft4<1>(v); }
+
+template <int SIGN>
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
     const float h = 0.70710678118654752440f;
-    // radix-2 split into even/odd 4-point DFTs
     float2 e[4] = {v[0], v[2], v[4], v[6]};
     float2 o[4] = {v[1], v[3], v[5], v[7]};
-    dft_small<4>(e, sign, nullptr, 0);
-    dft_small<4>(o, sign, nullptr, 0);
-    // twiddles exp(sign * 2 pi i m / 8), m = 0..3
-    float2 t1 = make_float2(h * (o[1].x - sign * o[1].y) * 1.0f, h * (o[1].y + sign * o[1].x));
-    float2 t2 = rot_mi(o[2], sign);
-    float2 t3 = make_float2(h * (-o[3].x - sign * o[3].y), h * (-o[3].y + sign * o[3].x));
+    dft4<SIGN>(e);
+    dft4<SIGN>(o);
+    // o[m] times exp(SIGN 2 pi i m / 8), m = 1, 2, 3
+    const float2 t1 = make_float2(h * (o[1].x - SIGN * o[1].y), h * (o[1].y + SIGN * o[1].x));
+    const float2 t2 = rot_i<SIGN>(o[2]);
+    const float2 t3 = make_float2(h * (-o[3].x - SIGN * o[3].y), h * (-o[3].y + SIGN * o[3].x));
     v[0] = cadd(e[0], o[0]);
     v[4] = csub(e[0], o[0]);
     v[1] = cadd(e[1], t1);
@@ -115,6 +182,10 @@ __device__ __forceinline__ void dft_small<8>(float2 (&v)[8], int sign, const flo
     v[3] = cadd(e[3], t3);
     v[7] = csub(e[3], t3);
 }
+template <>
+__device__ __forceinline__ void dft<8, -1>(float2 (&v)[8]) { dft8<-1>(v); }
+template <>
+__device__ __forceinline__ void dft<8, 1>(float2 (&v)[8]) { dft8<1>(v); }
 
 // q = j / Ns for 0 <= j < 2^16 and 2 <= Ns < 2^16 via a multiply-shift with mag = floor(2^32 / Ns) + 1
 // (the error of j * mag / 2^32 against j / Ns stays below 1 / Ns there); Ns = 1 is passed through
@@ -122,49 +193,54 @@ __device__ __forceinline__ int divmagic(int j, int Ns, uint32_t mag) {
     return Ns == 1 ? j : (int)__umulhi((uint32_t)j, mag);
 }
 
-template <int R>
+constexpr int kJ = kPassThreads / kLines;   // threads per line
+
+// One radix-R Stockham stage over the kLines lines of a CTA; thread (l, jt) takes butterflies
+// j = jt, jt + kJ, ... of line l.  tw holds exp(-2 pi i k / n); the inverse conjugates it.
+template <int R, int SIGN>
 __device__ __forceinline__ void stockham_stage(const float2* __restrict__ a, float2* __restrict__ b,
-                                               const float2* tw, int n, int Ns, uint32_t mag, int sign) {
+                                               const float2* __restrict__ tw, int n, int Ns, uint32_t mag,
+                                               int tstride, int l, int jt) {
     const int nb = n / R;
-    const int tstride = n / (Ns * R);
-    for (int t = threadIdx.x; t < nb * kLines; t += blockDim.x) {
-        const int l = t % kLines;
-        const int j = t / kLines;
+    for (int j = jt; j < nb; j += kJ) {
         const int jq = divmagic(j, Ns, mag);
         const int k = j - jq * Ns;
         float2 v[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) v[q] = a[(j + q * nb) * kLinePad + l];
         if (Ns > 1) {
+            const int step = k * tstride;
 #pragma unroll
             for (int q = 1; q < R; ++q) {
-                float2 w = tw[q * k * tstride];
-                if (sign > 0) w.y = -w.y;
+                float2 w = tw[q * step];
+                if (SIGN > 0) w.y = -w.y;
                 v[q] = cmul(v[q], w);
             }
         }
-        dft_small<R>(v, sign, tw, n);
+        dft<R, SIGN>(v);
         const int base = jq * Ns * R + k;
 #pragma unroll
         for (int q = 0; q < R; ++q) b[(base + q * Ns) * kLinePad + l] = v[q];
     }
 }
 
-// Transform kLines lines in shared memory; returns the buffer holding the result.
-__device__ float2* fft_lines(float2* a, float2* b, const float2* tw, int n, const int* rad, int nrad,
-                             int sign) {
+// Transform the kLines lines in shared memory; returns the buffer holding the result.
+template <int SIGN>
+__device__ float2* fft_lines(float2* a, float2* b, const float2* tw, int n, const int* rad, int nrad, int l,
+                             int jt) {
     int Ns = 1;
     for (int s = 0; s < nrad; ++s) {
         const int r = rad[s];
         const uint32_t mag = (uint32_t)(0x100000000ull / (unsigned long long)Ns) + 1u;
+        const int tstride = n / (Ns * r);
         switch (r) {
-            case 2: stockham_stage<2>(a, b, tw, n, Ns, mag, sign); break;
-            case 3: stockham_stage<3>(a, b, tw, n, Ns, mag, sign); break;
-            case 4: stockham_stage<4>(a, b, tw, n, Ns, mag, sign); break;
-            case 5: stockham_stage<5>(a, b, tw, n, Ns, mag, sign); break;
-            case 7: stockham_stage<7>(a, b, tw, n, Ns, mag, sign); break;
-            case 8: stockham_stage<8>(a, b, tw, n, Ns, mag, sign); break;
-            case 11: stockham_stage<11>(a, b, tw, n, Ns, mag, sign); break;
+            case 2: stockham_stage<2, SIGN>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
+            case 3: stockham_stage<3, SIGN>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
+            case 4: stockham_stage<4, SIGN>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
+            case 5: stockham_stage<5, SIGN>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
+            case 7: stockham_stage<7, SIGN>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
+            case 8: stockham_stage<8, SIGN>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
+            case 11: stockham_stage<11, SIGN>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
             default: break;
         }
         __syncthreads();
@@ -180,7 +256,9 @@ __device__ float2* fft_lines(float2* a, float2* b, const float2* tw, int n, cons
 // Pass kernels.  Coil stacks are stored coil-interleaved: element (..., k, ..., c) of an
 // intermediate or grid buffer sits at ((... * n + k) * inner_rest + ...) * C + c, so a line is
 // (position along the other axes, coil) and kLines consecutive lines are contiguous in memory
-// for every axis, including x.
+// for every axis, including x.  Thread t of a CTA owns line l = t mod kLines for the loads, the
+// butterflies and the stores (element rows jt = t / kLines, jt + kJ, ...), so its addresses are
+// one base plus a stride; per-line quantities of the x passes are computed once per CTA.
 enum PassMode { EXPAND_X = 0, PLAIN = 1, GATHER_Y = 2, SCATTER_Y = 3, MASK_Y = 4, REDUCE_X = 5 };
 
 struct PassArgs {
@@ -196,6 +274,7 @@ struct PassArgs {
     int64_t rows;    // nz * ny image rows
     int C;           // coils (interleave stride)
     int rows_per_cta;
+    uint32_t nx_mag; // floor(2^32 / nxi) + 1
     // maps / image
     const float2* maps_v;
     const float2* maps_s;
@@ -226,7 +305,10 @@ __device__ __forceinline__ bool cart_neg(int py, int px, int ny, int nx) {
     return (py + px + ny / 2 + nx / 2) & 1;
 }
 
-template <int MODE>
+// i / nxi for 0 <= i < 2^16 (the x-pass element loops stay below 16 * 512)
+__device__ __forceinline__ int div_nx(const PassArgs& A, int i) { return (int)__umulhi((uint32_t)i, A.nx_mag); }
+
+template <int MODE, int SIGN>
 __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
     extern __shared__ float2 smem[];
     const int n = A.n;
@@ -234,69 +316,74 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
     float2* bufb = smem + n * kLinePad;
     float2* stw = smem + 2 * n * kLinePad;
     __shared__ int srad[kMaxRadices];
-    if (threadIdx.x < kMaxRadices) srad[threadIdx.x] = A.rad[threadIdx.x];
-    for (int e = threadIdx.x; e < n; e += blockDim.x) stw[e] = A.tw[e];
+    __shared__ int64_t sbase[kLines];          // x passes: per-line element offset
+    __shared__ int srow[kLines];               // x passes: image row of the line (-1: none)
+    __shared__ int scoil[kLines];
+    __shared__ float sapzy[kLines];
     const int tid = threadIdx.x;
+    const int l = tid % kLines, jt = tid / kLines;
+    if (tid < kMaxRadices) srad[tid] = A.rad[tid];
+    for (int e = tid; e < n; e += blockDim.x) stw[e] = A.tw[e];
 
     if (MODE == REDUCE_X) {
         // ---- rows_per_cta image rows; inverse FFT of every coil's line, crop, conj(map),
         //      apodisation and the sum over coils (deterministic order) ----
         constexpr int MAXE = 4;     // rows_per_cta * nx <= 4 * kPassThreads (set by pass_reduce)
         float2 acc[MAXE];
-#pragma unroll
-        for (int e = 0; e < MAXE; ++e) acc[e] = make_float2(0.f, 0.f);
+        int orow[MAXE], oi[MAXE];
         const int nx = A.nxi;
         const int R = A.rows_per_cta;
-        const int64_t r0 = (int64_t)blockIdx.x * R;
+        const int r0 = blockIdx.x * R;
+#pragma unroll
+        for (int e = 0; e < MAXE; ++e) {
+            acc[e] = make_float2(0.f, 0.f);
+            const int idx = tid + e * kPassThreads;
+            const int rr = div_nx(A, idx);
+            oi[e] = idx - rr * nx;
+            orow[e] = (idx < R * nx && r0 + rr < A.rows) ? r0 + rr : -1;
+            oi[e] = (orow[e] >= 0) ? oi[e] : 0;
+        }
         const int cwmax = (A.C >= kLines) ? kLines : A.C;
         for (int c0 = 0; c0 < A.C; c0 += cwmax) {
             const int cw = min(cwmax, A.C - c0);
-            const int nl = R * cw;
             __syncthreads();
-            for (int e = tid; e < kLines * n; e += blockDim.x) {
-                const int l = e % kLines, k = e / kLines;
-                float2 v = make_float2(0.f, 0.f);
-                if (l < nl) {
-                    const int64_t row = r0 + l / cw;
-                    const int c = c0 + l % cw;
-                    if (row < A.rows) v = A.in[(row * n + k) * A.C + c];
-                }
-                bufa[k * kLinePad + l] = v;
+            if (tid < kLines) {
+                const int row = r0 + tid / cw, c = c0 + tid % cw;
+                const bool ok = tid < R * cw && row < A.rows;
+                srow[tid] = ok ? row : -1;
+                sbase[tid] = ok ? (int64_t)row * n * A.C + c : 0;
             }
             __syncthreads();
-            float2* res = fft_lines(bufa, bufb, stw, n, srad, A.nrad, A.sign);
+            {
+                const bool ok = srow[l] >= 0;
+                const float2* p = A.in + sbase[l];
+#pragma unroll 4
+                for (int k = jt; k < n; k += kJ) bufa[k * kLinePad + l] = ok ? p[(int64_t)k * A.C] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            float2* res = fft_lines<SIGN>(bufa, bufb, stw, n, srad, A.nrad, l, jt);
 #pragma unroll
             for (int e = 0; e < MAXE; ++e) {
-                const int idx = tid + e * kPassThreads;
-                if (idx < R * nx) {
-                    const int rr = idx / nx, i = idx % nx;
-                    const int64_t row = r0 + rr;
-                    if (row < A.rows) {
-                        for (int q = 0; q < cw; ++q) {
-                            const int l = rr * cw + q;
-                            const float2 v = res[(i + A.out_off) * kLinePad + l];
-                            const float2 m = coil_map(A, c0 + q)[row * nx + i];
-                            acc[e] = cadd(acc[e], cmulc(m, v));
-                        }
-                    }
+                if (orow[e] >= 0) {
+                    const int idx = tid + e * kPassThreads;
+                    const int rr = div_nx(A, idx);
+                    const int64_t g = (int64_t)orow[e] * nx + oi[e];
+                    const float2* rp = res + (oi[e] + A.out_off) * kLinePad + rr * cw;
+                    for (int q = 0; q < cw; ++q) acc[e] = cadd(acc[e], cmulc(coil_map(A, c0 + q)[g], rp[q]));
                 }
             }
         }
 #pragma unroll
         for (int e = 0; e < MAXE; ++e) {
-            const int idx = tid + e * kPassThreads;
-            if (idx < R * nx) {
-                const int rr = idx / nx, i = idx % nx;
-                const int64_t row = r0 + rr;
-                if (row < A.rows) {
-                    const int z = (int)(row / A.nyi), yy = (int)(row % A.nyi);
-                    const float ap = A.apz[z] * A.apy[yy] * A.apx[i];
-                    float2 r = cscale(acc[e], ap);
-                    const int64_t g = row * nx + i;
-                    if (A.addv) r = cadd(r, cscale(A.addv[g], A.lambda));
-                    if (A.accumulate) r = cadd(r, A.xo[g]);
-                    A.xo[g] = r;
-                }
+            if (orow[e] >= 0) {
+                const int row = orow[e], i = oi[e];
+                const int z = row / A.nyi, yy = row - (row / A.nyi) * A.nyi;
+                const float ap = A.apz[z] * A.apy[yy] * A.apx[i];
+                float2 r = cscale(acc[e], ap);
+                const int64_t g = (int64_t)row * nx + i;
+                if (A.addv) r = cadd(r, cscale(A.addv[g], A.lambda));
+                if (A.accumulate) r = cadd(r, A.xo[g]);
+                A.xo[g] = r;
             }
         }
         return;
@@ -304,98 +391,86 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
 
     // ---------------------------------- load ----------------------------------
     int64_t o0 = 0, i0 = 0;
+    int px = 0, cc = 0;
+    bool iv = true;
     if (MODE == EXPAND_X) {
         i0 = (int64_t)blockIdx.x * kLines;  // first line = row * C + c
         const int nx = A.nxi;
-        const int64_t nlines = A.rows * A.C;
-        __syncthreads();
-        for (int e = tid; e < kLines * nx; e += blockDim.x) {
-            const int l = e / nx, i = e % nx;
-            const int64_t L = i0 + l;
-            float2 v = make_float2(0.f, 0.f);
-            if (L < nlines) {
-                const int64_t row = L / A.C;
-                const int c = (int)(L % A.C);
-                const int z = (int)(row / A.nyi), yy = (int)(row % A.nyi);
-                const float ap = A.apz[z] * A.apy[yy] * A.apx[i];
-                v = cscale(cmul(A.x[row * nx + i], coil_map(A, c)[row * nx + i]), ap);
-            }
-            bufa[(i + A.in_off) * kLinePad + l] = v;
+        if (tid < kLines) {
+            const int64_t L = i0 + tid;
+            const bool ok = L < A.rows * A.C;
+            const int row = ok ? (int)(L / A.C) : 0;
+            const int c = ok ? (int)(L - (int64_t)row * A.C) : 0;
+            const int z = row / A.nyi, yy = row - z * A.nyi;
+            srow[tid] = ok ? row : -1;
+            scoil[tid] = c;
+            sapzy[tid] = A.apz[z] * A.apy[yy];
+            sbase[tid] = (int64_t)row * n * A.C + c;
         }
-        for (int e = tid; e < kLines * (n - nx); e += blockDim.x) {
-            const int l = e % kLines, kk = e / kLines;
+        // zero padding rows outside [in_off, in_off + nx)
+        for (int kk = jt; kk < n - nx; kk += kJ) {
             const int k = (kk < A.in_off) ? kk : kk + nx;
             bufa[k * kLinePad + l] = make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int e = tid; e < kLines * nx; e += kPassThreads) {
+            const int le = div_nx(A, e), i = e - le * nx;
+            const int row = srow[le];
+            float2 v = make_float2(0.f, 0.f);
+            if (row >= 0) {
+                const int64_t g = (int64_t)row * nx + i;
+                v = cscale(cmul(A.x[g], coil_map(A, scoil[le])[g]), sapzy[le] * A.apx[i]);
+            }
+            bufa[(i + A.in_off) * kLinePad + le] = v;
         }
     } else {
         const int64_t iblocks = (A.inner + kLines - 1) / kLines;
         o0 = blockIdx.x / iblocks;
-        i0 = (blockIdx.x % iblocks) * kLines;
-        __syncthreads();
-        if (MODE == PLAIN) {
-            // loads are issued in batches of 8 per thread before the shared-memory stores, so
-            // every thread keeps 8 independent 8-byte loads in flight
-            constexpr int BATCH = 8;
-            constexpr int KSTEP = kPassThreads / kLines;
-            const int l = tid % kLines;
-            const int64_t i = i0 + l;
-            const bool iv = i < A.inner;
-            for (int kb = tid / kLines; kb < n; kb += BATCH * KSTEP) {
-                float2 reg[BATCH];
-#pragma unroll
-                for (int q = 0; q < BATCH; ++q) {
-                    const int k = kb + q * KSTEP;
-                    const int kk = k - A.in_off;
-                    reg[q] = make_float2(0.f, 0.f);
-                    if (k < n && iv && kk >= 0 && kk < A.n_in) reg[q] = A.in[(o0 * A.n_in + kk) * A.inner + i];
-                }
-#pragma unroll
-                for (int q = 0; q < BATCH; ++q) {
-                    const int k = kb + q * KSTEP;
-                    if (k < n) bufa[k * kLinePad + l] = reg[q];
-                }
-            }
-        } else
-        for (int e = tid; e < kLines * n; e += blockDim.x) {
-            const int l = e % kLines, k = e / kLines;
-            const int64_t i = i0 + l;
-            float2 v = make_float2(0.f, 0.f);
-            if (i < A.inner) {
-                if (MODE == SCATTER_Y) {
-                    const int64_t px = i / A.C;
-                    const int c = (int)(i % A.C);
+        i0 = (blockIdx.x - o0 * iblocks) * kLines;
+        const int64_t i = i0 + l;
+        iv = i < A.inner;
+        if (MODE != PLAIN) {
+            px = (int)(i / A.C);
+            cc = (int)(i - (int64_t)px * A.C);
+        }
+        if (MODE == SCATTER_Y) {
+            for (int k = jt; k < n; k += kJ) {
+                float2 v = make_float2(0.f, 0.f);
+                if (iv) {
                     const int32_t f = A.idxmap[(int64_t)k * A.nxi + px];
                     if (f >= 0) {
-                        v = A.yk[(int64_t)c * A.N + f];
-                        if (cart_neg(k, (int)px, n, A.nxi)) v = make_float2(-v.x, -v.y);
+                        v = A.yk[(int64_t)cc * A.N + f];
+                        if (cart_neg(k, px, n, A.nxi)) v = make_float2(-v.x, -v.y);
                     }
-                } else {
-                    const int kk = k - A.in_off;
-                    if (kk >= 0 && kk < A.n_in) v = A.in[(o0 * A.n_in + kk) * A.inner + i];
                 }
+                bufa[k * kLinePad + l] = v;
             }
-            bufa[k * kLinePad + l] = v;
+        } else {
+            for (int kk = jt; kk < n - A.n_in; kk += kJ) {
+                const int k = (kk < A.in_off) ? kk : kk + A.n_in;
+                bufa[k * kLinePad + l] = make_float2(0.f, 0.f);
+            }
+            const float2* p = A.in + o0 * A.n_in * A.inner + i;
+#pragma unroll 4
+            for (int kk = jt; kk < A.n_in; kk += kJ)
+                bufa[(kk + A.in_off) * kLinePad + l] = iv ? p[(int64_t)kk * A.inner] : make_float2(0.f, 0.f);
         }
     }
     __syncthreads();
-    float2* res = fft_lines(bufa, bufb, stw, n, srad, A.nrad, A.sign);
+    float2* res = fft_lines<SIGN>(bufa, bufb, stw, n, srad, A.nrad, l, jt);
     float2* other = (res == bufa) ? bufb : bufa;
 
     if (MODE == MASK_Y) {
         // U^H U (minus data) between the forward and the inverse transform
-        for (int e = tid; e < kLines * n; e += blockDim.x) {
-            const int l = e % kLines, k = e / kLines;
-            const int64_t i = i0 + l;
+        for (int k = jt; k < n; k += kJ) {
             float2 v = make_float2(0.f, 0.f);
-            if (i < A.inner) {
-                const int64_t px = i / A.C;
-                const int c = (int)(i % A.C);
+            if (iv) {
                 const int32_t f = A.idxmap[(int64_t)k * A.nxi + px];
                 if (f >= 0) {
                     v = res[k * kLinePad + l];
                     if (A.residual) {
-                        float2 yv = A.yk[(int64_t)c * A.N + f];
-                        if (cart_neg(k, (int)px, n, A.nxi)) yv = make_float2(-yv.x, -yv.y);
+                        float2 yv = A.yk[(int64_t)cc * A.N + f];
+                        if (cart_neg(k, px, n, A.nxi)) yv = make_float2(-yv.x, -yv.y);
                         v = csub(v, yv);
                     }
                 }
@@ -403,42 +478,31 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
             res[k * kLinePad + l] = v;
         }
         __syncthreads();
-        res = fft_lines(res, other, stw, n, srad, A.nrad, -A.sign);
+        res = fft_lines<-SIGN>(res, other, stw, n, srad, A.nrad, l, jt);
     }
 
     // ---------------------------------- store ----------------------------------
     if (MODE == EXPAND_X) {
-        const int64_t nlines = A.rows * A.C;
-        for (int e = tid; e < kLines * n; e += blockDim.x) {
-            const int l = e % kLines, k = e / kLines;
-            const int64_t L = i0 + l;
-            if (L < nlines) {
-                const int64_t row = L / A.C;
-                const int c = (int)(L % A.C);
-                A.out[(row * n + k) * A.C + c] = res[k * kLinePad + l];
-            }
+        if (srow[l] >= 0) {
+            float2* p = A.out + sbase[l];
+#pragma unroll 4
+            for (int k = jt; k < n; k += kJ) p[(int64_t)k * A.C] = res[k * kLinePad + l];
         }
     } else if (MODE == GATHER_Y) {
-        for (int e = tid; e < kLines * n; e += blockDim.x) {
-            const int l = e % kLines, k = e / kLines;
-            const int64_t i = i0 + l;
-            if (i < A.inner) {
-                const int64_t px = i / A.C;
-                const int c = (int)(i % A.C);
+        if (iv) {
+            for (int k = jt; k < n; k += kJ) {
                 const int32_t f = A.idxmap[(int64_t)k * A.nxi + px];
                 if (f >= 0) {
                     float2 v = res[k * kLinePad + l];
-                    if (cart_neg(k, (int)px, n, A.nxi)) v = make_float2(-v.x, -v.y);
-                    A.yko[(int64_t)c * A.N + f] = v;
+                    if (cart_neg(k, px, n, A.nxi)) v = make_float2(-v.x, -v.y);
+                    A.yko[(int64_t)cc * A.N + f] = v;
                 }
             }
         }
-    } else {
-        for (int e = tid; e < kLines * A.n_out; e += blockDim.x) {
-            const int l = e % kLines, kk = e / kLines;
-            const int64_t i = i0 + l;
-            if (i < A.inner) A.out[(o0 * A.n_out + kk) * A.inner + i] = res[(kk + A.out_off) * kLinePad + l];
-        }
+    } else if (iv) {
+        float2* p = A.out + o0 * A.n_out * A.inner + i0 + l;
+#pragma unroll 4
+        for (int kk = jt; kk < A.n_out; kk += kJ) p[(int64_t)kk * A.inner] = res[(kk + A.out_off) * kLinePad + l];
     }
 }
 
@@ -448,16 +512,17 @@ static size_t pass_smem(int n) { return sizeof(float2) * (size_t)(2 * n * kLineP
 // never inside a stream capture)
 cs_status fft_init_attrs() {
     const int sm = (int)pass_smem(kMaxFft);
-    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<EXPAND_X>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<GATHER_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<SCATTER_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<MASK_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<REDUCE_X>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<EXPAND_X, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<PLAIN, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<PLAIN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<GATHER_Y, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<SCATTER_Y, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<MASK_Y, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<REDUCE_X, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     return CS_OK;
 }
 
-template <int MODE>
+template <int MODE, int SIGN>
 static cs_status launch_pass(const PassArgs& A, cudaStream_t st) {
     const size_t sm = pass_smem(A.n);
     int64_t blocks;
@@ -468,7 +533,7 @@ static cs_status launch_pass(const PassArgs& A, cudaStream_t st) {
     CS_REQUIRE(blocks < (int64_t)1 << 31, CS_ERR_UNSUPPORTED_SIZE, "pass grid too large");
     const int stage = (MODE == EXPAND_X) ? ST_EXPAND : (MODE == REDUCE_X ? ST_REDUCE : ST_FFT_PLAIN);
     prof_begin(stage, st);
-    fft_pass_kernel<MODE><<<(unsigned)blocks, kPassThreads, sm, st>>>(A);
+    fft_pass_kernel<MODE, SIGN><<<(unsigned)blocks, kPassThreads, sm, st>>>(A);
     CS_LAUNCH_CHECK();
     prof_end(stage, st);
     return CS_OK;
@@ -493,6 +558,7 @@ static void fill_maps(PassArgs& A, const cs_plan* p, const float2* maps_v, int V
     A.apx = p->apod[2];
     A.nyi = p->img[1];
     A.nxi = p->img[2];
+    A.nx_mag = (uint32_t)(0x100000000ull / (unsigned long long)p->img[2]) + 1u;
     A.rows = (int64_t)p->img[0] * p->img[1];
 }
 
@@ -505,7 +571,7 @@ static cs_status pass_expand(const cs_plan* p, const float2* x, const float2* ma
     A.in_off = p->off[2];
     A.x = x;
     A.out = p->bufA;
-    return launch_pass<EXPAND_X>(A, st);
+    return launch_pass<EXPAND_X, -1>(A, st);
 }
 
 static cs_status pass_reduce(const cs_plan* p, const float2* maps_v, int V, const float2* maps_s, int S,
@@ -522,7 +588,7 @@ static cs_status pass_reduce(const cs_plan* p, const float2* maps_v, int V, cons
     const int C = V + S;
     A.rows_per_cta = (C >= kLines || C == 0) ? 1 : kLines / C;   // C == 0: only lambda v / accumulate
     A.rows_per_cta = std::max(1, std::min(A.rows_per_cta, 4 * kPassThreads / p->img[2]));
-    return launch_pass<REDUCE_X>(A, st);
+    return launch_pass<REDUCE_X, 1>(A, st);
 }
 
 // strided-axis pass for 3D plans: axis 0 (z) or 1 (y); coil-interleaved buffers
@@ -551,7 +617,7 @@ static cs_status pass_plain(const cs_plan* p, int axis, int sign, const float2* 
     }
     A.in = in;
     A.out = out;
-    return launch_pass<PLAIN>(A, st);
+    return sign < 0 ? launch_pass<PLAIN, -1>(A, st) : launch_pass<PLAIN, 1>(A, st);
 }
 
 static cs_status pass_cart_y(const cs_plan* p, int mode, int C, const float2* yk, float2* yko, int residual,
@@ -575,9 +641,9 @@ static cs_status pass_cart_y(const cs_plan* p, int mode, int C, const float2* yk
     A.N = p->N;
     A.residual = residual;
     switch (mode) {
-        case GATHER_Y: return launch_pass<GATHER_Y>(A, st);
-        case SCATTER_Y: return launch_pass<SCATTER_Y>(A, st);
-        default: return launch_pass<MASK_Y>(A, st);
+        case GATHER_Y: return launch_pass<GATHER_Y, -1>(A, st);
+        case SCATTER_Y: return launch_pass<SCATTER_Y, 1>(A, st);
+        default: return launch_pass<MASK_Y, -1>(A, st);
     }
 }
 
