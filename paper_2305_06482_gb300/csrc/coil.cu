@@ -615,6 +615,7 @@ cs_status coil_rotate(const float* U, const float* in, int C, int C_out, int64_t
 cs_status cs_device_status(void* stream) {
     clear_error();
     CS_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    CS_PROPAGATE(fft_check_and_clear());
     return tc_check_and_clear();
 }
 

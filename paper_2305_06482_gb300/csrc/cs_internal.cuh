@@ -165,6 +165,7 @@ void solver_ws_free(cs_plan* p);
 
 // one-time per-device set-up (kernel attributes, filter constants), done at plan creation
 cs_status fft_init_attrs();
+cs_status fft_check_and_clear();
 cs_status tc_init_attrs();
 cs_status wavelet_init_constants();
 cs_status coil_init_attrs();

@@ -9,13 +9,17 @@
 //
 // Pass modes
 //   EXPAND_X   x (.) c_c (.) apod -> zero-padded rows -> FFT along x        (first forward pass)
-//   PLAIN      strided axis, zero-pad on input / crop on output            (middle passes)
+//   (strided)  middle passes along z / y: tensor-copy kernel below, zero-pad on input / crop on
+//              output
 //   GATHER_Y   FFT along y, keep the sampled entries U (Cartesian forward)
 //   SCATTER_Y  U^H (zero-fill) then inverse FFT along y (Cartesian adjoint)
 //   MASK_Y     FFT along y, U^H U (optionally minus the data: residual), inverse FFT
 //   REDUCE_X   inverse FFT along x, crop, apod, sum_c conj(c_c) (.) (+ lambda v)  (last adjoint)
 #include <cstdio>
 #include <cmath>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "cs_internal.cuh"
 
@@ -197,7 +201,7 @@ constexpr int kJ = kPassThreads / kLines;   // threads per line
 
 // One radix-R Stockham stage over the kLines lines of a CTA; thread (l, jt) takes butterflies
 // j = jt, jt + kJ, ... of line l.  tw holds exp(-2 pi i k / n); the inverse conjugates it.
-template <int R, int SIGN>
+template <int R, int SIGN, int PITCH>
 __device__ __forceinline__ void stockham_stage(const float2* __restrict__ a, float2* __restrict__ b,
                                                const float2* __restrict__ tw, int n, int Ns, uint32_t mag,
                                                int tstride, int l, int jt) {
@@ -207,7 +211,7 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ a, flo
         const int k = j - jq * Ns;
         float2 v[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) v[q] = a[(j + q * nb) * kLinePad + l];
+        for (int q = 0; q < R; ++q) v[q] = a[(j + q * nb) * PITCH + l];
         if (Ns > 1) {
             const int step = k * tstride;
 #pragma unroll
@@ -220,12 +224,13 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ a, flo
         dft<R, SIGN>(v);
         const int base = jq * Ns * R + k;
 #pragma unroll
-        for (int q = 0; q < R; ++q) b[(base + q * Ns) * kLinePad + l] = v[q];
+        for (int q = 0; q < R; ++q) b[(base + q * Ns) * PITCH + l] = v[q];
     }
 }
 
-// Transform the kLines lines in shared memory; returns the buffer holding the result.
-template <int SIGN>
+// Transform the kLines lines in shared memory (element k of line l at k * PITCH + l); returns the
+// buffer holding the result.
+template <int SIGN, int PITCH = kLinePad>
 __device__ float2* fft_lines(float2* a, float2* b, const float2* tw, int n, const int* rad, int nrad, int l,
                              int jt) {
     int Ns = 1;
@@ -234,13 +239,13 @@ __device__ float2* fft_lines(float2* a, float2* b, const float2* tw, int n, cons
         const uint32_t mag = (uint32_t)(0x100000000ull / (unsigned long long)Ns) + 1u;
         const int tstride = n / (Ns * r);
         switch (r) {
-            case 2: stockham_stage<2, SIGN>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
-            case 3: stockham_stage<3, SIGN>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
-            case 4: stockham_stage<4, SIGN>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
-            case 5: stockham_stage<5, SIGN>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
-            case 7: stockham_stage<7, SIGN>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
-            case 8: stockham_stage<8, SIGN>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
-            case 11: stockham_stage<11, SIGN>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
+            case 2: stockham_stage<2, SIGN, PITCH>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
+            case 3: stockham_stage<3, SIGN, PITCH>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
+            case 4: stockham_stage<4, SIGN, PITCH>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
+            case 5: stockham_stage<5, SIGN, PITCH>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
+            case 7: stockham_stage<7, SIGN, PITCH>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
+            case 8: stockham_stage<8, SIGN, PITCH>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
+            case 11: stockham_stage<11, SIGN, PITCH>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
             default: break;
         }
         __syncthreads();
@@ -510,11 +515,12 @@ static size_t pass_smem(int n) { return sizeof(float2) * (size_t)(2 * n * kLineP
 
 // dynamic shared-memory limits of every pass kernel (set once per device at plan creation,
 // never inside a stream capture)
+static cs_status tma_init_attrs();
+
 cs_status fft_init_attrs() {
+    CS_PROPAGATE(tma_init_attrs());
     const int sm = (int)pass_smem(kMaxFft);
     CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<EXPAND_X, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<PLAIN, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-    CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<PLAIN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<GATHER_Y, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<SCATTER_Y, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
     CS_TRY_CUDA(cudaFuncSetAttribute(fft_pass_kernel<MASK_Y, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
@@ -562,6 +568,206 @@ static void fill_maps(PassArgs& A, const cs_plan* p, const float2* maps_v, int V
     A.rows = (int64_t)p->img[0] * p->img[1];
 }
 
+// ------------------------------------------------------------------------------------------
+// Strided-axis pass with tensor-memory-access copies.  The coil-interleaved buffer is a 3D
+// tensor [outer][rows][inner] of 8-byte elements; a CTA's tile is 16 consecutive lines (128 B of
+// every row) by the n rows of the transform.  One thread issues the tensor loads of the whole
+// tile (boxes of h_in rows; rows outside [0, n_in) after the shift by in_off read as zero, which
+// is the zero padding of the forward transform), every thread waits on the mbarrier (bounded),
+// the FFT runs in shared memory in the dense layout [k][16] (a half-warp touches one 128-byte
+// row: no bank conflicts), and one thread stores the cropped rows [out_off, out_off + n_out)
+// with tensor stores (the ragged last tile is clipped by the copy unit).
+constexpr long long kTmaSpinLimit = 1ll << 24;
+__device__ int g_fft_error = 0;
+
+struct TmaPassArgs {
+    int n, nrad, rad[kMaxRadices];
+    const float2* tw;
+    int64_t iblocks;        // tiles along the line index
+    int in_off, h_in, nbox_in;
+    int out_off, h_out, nbox_out;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+template <int SIGN>
+__global__ void __launch_bounds__(kPassThreads, 3)
+    fft_plain_tma_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
+                         const __grid_constant__ TmaPassArgs A) {
+    extern __shared__ __align__(1024) float2 tsm[];
+    const int n = A.n;
+    float2* bufa = tsm;
+    float2* bufb = tsm + n * kLines;
+    float2* stw = tsm + 2 * n * kLines;
+    __shared__ int srad[kMaxRadices];
+    __shared__ __align__(8) uint64_t mbar;
+    const int tid = threadIdx.x;
+    const int l = tid % kLines, jt = tid / kLines;
+    const int o0 = (int)(blockIdx.x / A.iblocks);
+    const int i0 = (int)(blockIdx.x - (int64_t)o0 * A.iblocks) * kLines;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar)), "r"(1u));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const uint32_t bytes = (uint32_t)n * kLines * sizeof(float2);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&mbar)), "r"(bytes)
+                     : "memory");
+        for (int b = 0; b < A.nbox_in; ++b) {
+            const int y = b * A.h_in - A.in_off;
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                ::"r"(smem_addr(bufa + (size_t)b * A.h_in * kLines)), "l"(&tin), "r"(i0), "r"(y), "r"(o0),
+                  "r"(smem_addr(&mbar))
+                : "memory");
+        }
+    }
+    if (tid < kMaxRadices) srad[tid] = A.rad[tid];
+    for (int e = tid; e < n; e += blockDim.x) stw[e] = A.tw[e];
+    // bounded wait for the tile (phase 0)
+    int done = 0;
+    long long spins = 0;
+    while (!done) {
+        asm volatile(
+            "{\n.reg .pred P1;\nmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\nselp.b32 %0, 1, 0, P1;\n}\n"
+            : "=r"(done)
+            : "r"(smem_addr(&mbar)), "r"(0u)
+            : "memory");
+        if (!done && ++spins > kTmaSpinLimit) break;
+    }
+    if (__syncthreads_or(!done)) {
+        if (tid == 0) atomicExch(&g_fft_error, 1);
+        return;
+    }
+    float2* res = fft_lines<SIGN, kLines>(bufa, bufb, stw, n, srad, A.nrad, l, jt);
+    // make the generic-proxy shared-memory writes visible to the copy unit, then store
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+        for (int b = 0; b < A.nbox_out; ++b) {
+            const int y = b * A.h_out;
+            asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+                         ::"l"(&tout), "r"(i0), "r"(y), "r"(o0),
+                           "r"(smem_addr(res + (size_t)(A.out_off + y) * kLines))
+                         : "memory");
+        }
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    }
+}
+
+static size_t tma_pass_smem(int n) { return sizeof(float2) * (size_t)(2 * n * kLines + n); }
+
+static cs_status tma_init_attrs() {
+    const int sm = (int)tma_pass_smem(kMaxFft);
+    CS_TRY_CUDA(cudaFuncSetAttribute(fft_plain_tma_kernel<-1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    CS_TRY_CUDA(cudaFuncSetAttribute(fft_plain_tma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    return CS_OK;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// smallest divisor h of n with h <= 256 and n / h boxes (the box height limit is 256 rows)
+static int box_rows(int n) {
+    for (int b = 1; b <= n; ++b)
+        if (n % b == 0 && n / b <= 256) return n / b;
+    return 1;
+}
+
+static cs_status encode_3d(CUtensorMap* m, const float2* base, int64_t inner, int rows, int64_t outer, int h) {
+    auto fn = encode_fn();
+    CS_REQUIRE(fn != nullptr, CS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    CS_REQUIRE(inner % 2 == 0, CS_ERR_UNSUPPORTED_SIZE, "tensor copies need an even line count (got %lld)", (long long)inner);
+    const cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)outer};
+    const cuuint64_t strides[2] = {(cuuint64_t)inner * sizeof(float2), (cuuint64_t)inner * rows * sizeof(float2)};
+    const cuuint32_t box[3] = {(cuuint32_t)kLines, (cuuint32_t)h, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, (void*)base, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CS_REQUIRE(r == CUDA_SUCCESS, CS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return CS_OK;
+}
+
+// strided-axis pass for 3D plans (axis 0: z, 1: y) and the y pass of 2D plans; coil-interleaved
+static cs_status pass_plain(const cs_plan* p, int axis, int sign, const float2* in, float2* out, int C,
+                            cudaStream_t st) {
+    const FftLen& f = p->fft[axis];
+    TmaPassArgs A = {};
+    A.n = f.n;
+    A.nrad = f.nrad;
+    for (int i = 0; i < kMaxRadices; ++i) A.rad[i] = f.rad[i];
+    A.tw = f.tw;
+    const int Gx = p->grid[2], Gy = p->grid[1];
+    int64_t outer, inner;
+    if (axis == 1) {
+        outer = (p->ndim == 3) ? p->img[0] : 1;
+        inner = (int64_t)Gx * C;
+    } else {
+        outer = 1;
+        inner = (int64_t)Gy * Gx * C;
+    }
+    int n_in, n_out;
+    if (sign < 0) {  // forward: pad img -> grid
+        n_in = p->img[axis];
+        A.in_off = p->off[axis];
+        n_out = p->grid[axis];
+        A.out_off = 0;
+    } else {  // adjoint: crop grid -> img
+        n_in = p->grid[axis];
+        A.in_off = 0;
+        n_out = p->img[axis];
+        A.out_off = p->off[axis];
+    }
+    A.h_in = box_rows(A.n);
+    A.nbox_in = A.n / A.h_in;
+    A.h_out = box_rows(n_out);
+    A.nbox_out = n_out / A.h_out;
+    A.iblocks = (inner + kLines - 1) / kLines;
+    const int64_t blocks = outer * A.iblocks;
+    if (blocks == 0) return CS_OK;
+    CS_REQUIRE(blocks < (int64_t)1 << 31 && outer < (int64_t)1 << 31 && inner < (int64_t)1 << 31,
+               CS_ERR_UNSUPPORTED_SIZE, "pass grid too large");
+    CUtensorMap tin, tout;
+    CS_PROPAGATE(encode_3d(&tin, in, inner, n_in, outer, A.h_in));
+    CS_PROPAGATE(encode_3d(&tout, out, inner, n_out, outer, A.h_out));
+    prof_begin(ST_FFT_PLAIN, st);
+    if (sign < 0)
+        fft_plain_tma_kernel<-1><<<(unsigned)blocks, kPassThreads, tma_pass_smem(A.n), st>>>(tin, tout, A);
+    else
+        fft_plain_tma_kernel<1><<<(unsigned)blocks, kPassThreads, tma_pass_smem(A.n), st>>>(tin, tout, A);
+    CS_LAUNCH_CHECK();
+    prof_end(ST_FFT_PLAIN, st);
+    return CS_OK;
+}
+
+// reads and clears the flag of a tensor-copy wait that gave up (after the caller synchronised)
+cs_status fft_check_and_clear() {
+    int v = 0;
+    CS_TRY_CUDA(cudaMemcpyFromSymbol(&v, g_fft_error, sizeof(int)));
+    if (v) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(g_fft_error, &zero, sizeof(int));
+        set_error("an FFT pass gave up waiting for its tensor copies (bounded wait)");
+        return CS_ERR_TIMEOUT;
+    }
+    return CS_OK;
+}
+
 // x (.) maps (.) apod, zero-padded rows, FFT along x -> bufA [rows][Gx][C]
 static cs_status pass_expand(const cs_plan* p, const float2* x, const float2* maps_v, int V,
                              const float2* maps_s, int S, cudaStream_t st) {
@@ -589,35 +795,6 @@ static cs_status pass_reduce(const cs_plan* p, const float2* maps_v, int V, cons
     A.rows_per_cta = (C >= kLines || C == 0) ? 1 : kLines / C;   // C == 0: only lambda v / accumulate
     A.rows_per_cta = std::max(1, std::min(A.rows_per_cta, 4 * kPassThreads / p->img[2]));
     return launch_pass<REDUCE_X, 1>(A, st);
-}
-
-// strided-axis pass for 3D plans: axis 0 (z) or 1 (y); coil-interleaved buffers
-static cs_status pass_plain(const cs_plan* p, int axis, int sign, const float2* in, float2* out, int C,
-                            cudaStream_t st) {
-    PassArgs A = {};
-    fill_fft(A, p->fft[axis], sign);
-    const int Gx = p->grid[2], Gy = p->grid[1];
-    if (axis == 1) {
-        A.outer = (p->ndim == 3) ? p->img[0] : 1;
-        A.inner = (int64_t)Gx * C;
-    } else {
-        A.outer = 1;
-        A.inner = (int64_t)Gy * Gx * C;
-    }
-    if (sign < 0) {  // forward: pad img -> grid
-        A.n_in = p->img[axis];
-        A.in_off = p->off[axis];
-        A.n_out = p->grid[axis];
-        A.out_off = 0;
-    } else {  // adjoint: crop grid -> img
-        A.n_in = p->grid[axis];
-        A.in_off = 0;
-        A.n_out = p->img[axis];
-        A.out_off = p->off[axis];
-    }
-    A.in = in;
-    A.out = out;
-    return sign < 0 ? launch_pass<PLAIN, -1>(A, st) : launch_pass<PLAIN, 1>(A, st);
 }
 
 static cs_status pass_cart_y(const cs_plan* p, int mode, int C, const float2* yk, float2* yko, int residual,

@@ -893,6 +893,7 @@ static cs_status recon_finish(cs_plan* p, const cs_solve_params* sp, cudaStream_
         stats->ms_total = ms_all;
         stats->ms_pca = ms_pca;
     }
+    CS_PROPAGATE(fft_check_and_clear());
     CS_PROPAGATE(tc_check_and_clear());
     CS_REQUIRE(!h.nonfinite, CS_ERR_NONFINITE, "a solver reduction produced a non-finite value");
     return CS_OK;
