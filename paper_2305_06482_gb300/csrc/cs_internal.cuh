@@ -76,6 +76,9 @@ struct FftLen {
     int n = 0;
     int nrad = 0;
     int rad[kMaxRadices] = {0};
+    // per Stockham stage: (radix r, Ns = product of the earlier radices, floor(2^32 / Ns) + 1,
+    // twiddle stride n / (Ns r)), so that kernels divide by nothing at run time
+    int4 st[kMaxRadices] = {};
     float2* tw = nullptr;  // device, n entries exp(-2 pi i k / n) (computed in double)
 };
 

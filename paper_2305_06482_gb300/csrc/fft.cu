@@ -40,6 +40,12 @@ cs_status fft_len_init(FftLen& f, int n) {
     }
     CS_REQUIRE(m == 1, CS_ERR_UNSUPPORTED_SIZE,
                "FFT length %d has a prime factor outside {2, 3, 5, 7, 11}", n);
+    int Ns = 1;
+    for (int s = 0; s < f.nrad; ++s) {
+        const int r = f.rad[s];
+        f.st[s] = make_int4(r, Ns, (int)((uint32_t)(0x100000000ull / (unsigned long long)Ns) + 1u), n / (Ns * r));
+        Ns *= r;
+    }
     std::vector<float2> h(n);
     for (int k = 0; k < n; ++k) {
         double a = -2.0 * M_PI * (double)k / (double)n;
@@ -231,13 +237,12 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ a, flo
 // Transform the kLines lines in shared memory (element k of line l at k * PITCH + l); returns the
 // buffer holding the result.
 template <int SIGN, int PITCH = kLinePad>
-__device__ float2* fft_lines(float2* a, float2* b, const float2* tw, int n, const int* rad, int nrad, int l,
+__device__ float2* fft_lines(float2* a, float2* b, const float2* tw, int n, const int4* stages, int nrad, int l,
                              int jt) {
-    int Ns = 1;
     for (int s = 0; s < nrad; ++s) {
-        const int r = rad[s];
-        const uint32_t mag = (uint32_t)(0x100000000ull / (unsigned long long)Ns) + 1u;
-        const int tstride = n / (Ns * r);
+        const int4 g = stages[s];
+        const int r = g.x, Ns = g.y, tstride = g.w;
+        const uint32_t mag = (uint32_t)g.z;
         switch (r) {
             case 2: stockham_stage<2, SIGN, PITCH>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
             case 3: stockham_stage<3, SIGN, PITCH>(a, b, tw, n, Ns, mag, tstride, l, jt); break;
@@ -252,7 +257,6 @@ __device__ float2* fft_lines(float2* a, float2* b, const float2* tw, int n, cons
         float2* t = a;
         a = b;
         b = t;
-        Ns *= r;
     }
     return a;
 }
@@ -267,7 +271,8 @@ __device__ float2* fft_lines(float2* a, float2* b, const float2* tw, int n, cons
 enum PassMode { EXPAND_X = 0, PLAIN = 1, GATHER_Y = 2, SCATTER_Y = 3, MASK_Y = 4, REDUCE_X = 5 };
 
 struct PassArgs {
-    int n, nrad, rad[kMaxRadices];
+    int n, nrad;
+    int4 st[kMaxRadices];
     const float2* tw;
     int sign;
     int64_t outer;   // PLAIN / Y modes: outer index count
@@ -320,14 +325,14 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
     float2* bufa = smem;
     float2* bufb = smem + n * kLinePad;
     float2* stw = smem + 2 * n * kLinePad;
-    __shared__ int srad[kMaxRadices];
+    __shared__ int4 sst[kMaxRadices];
     __shared__ int64_t sbase[kLines];          // x passes: per-line element offset
     __shared__ int srow[kLines];               // x passes: image row of the line (-1: none)
     __shared__ int scoil[kLines];
     __shared__ float sapzy[kLines];
     const int tid = threadIdx.x;
     const int l = tid % kLines, jt = tid / kLines;
-    if (tid < kMaxRadices) srad[tid] = A.rad[tid];
+    if (tid < kMaxRadices) sst[tid] = A.st[tid];
     for (int e = tid; e < n; e += blockDim.x) stw[e] = A.tw[e];
 
     if (MODE == REDUCE_X) {
@@ -362,19 +367,44 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
             {
                 const bool ok = srow[l] >= 0;
                 const float2* p = A.in + sbase[l];
-#pragma unroll 4
-                for (int k = jt; k < n; k += kJ) bufa[k * kLinePad + l] = ok ? p[(int64_t)k * A.C] : make_float2(0.f, 0.f);
+                constexpr int LB = 8;
+                for (int k0 = jt; k0 < n; k0 += kJ * LB) {
+                    float2 t[LB];
+#pragma unroll
+                    for (int b = 0; b < LB; ++b) {
+                        const int k = k0 + b * kJ;
+                        t[b] = (ok && k < n) ? p[(int64_t)k * A.C] : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int b = 0; b < LB; ++b) {
+                        const int k = k0 + b * kJ;
+                        if (k < n) bufa[k * kLinePad + l] = t[b];
+                    }
+                }
             }
             __syncthreads();
-            float2* res = fft_lines<SIGN>(bufa, bufb, stw, n, srad, A.nrad, l, jt);
+            float2* res = fft_lines<SIGN>(bufa, bufb, stw, n, sst, A.nrad, l, jt);
+            // coil maps in batches of QB coils for every output element: MAXE * QB loads in flight
+            constexpr int QB = 4;
+            for (int q0 = 0; q0 < cw; q0 += QB) {
+                float2 m[MAXE][QB];
 #pragma unroll
-            for (int e = 0; e < MAXE; ++e) {
-                if (orow[e] >= 0) {
-                    const int idx = tid + e * kPassThreads;
-                    const int rr = div_nx(A, idx);
+                for (int e = 0; e < MAXE; ++e) {
                     const int64_t g = (int64_t)orow[e] * nx + oi[e];
-                    const float2* rp = res + (oi[e] + A.out_off) * kLinePad + rr * cw;
-                    for (int q = 0; q < cw; ++q) acc[e] = cadd(acc[e], cmulc(coil_map(A, c0 + q)[g], rp[q]));
+#pragma unroll
+                    for (int u = 0; u < QB; ++u)
+                        m[e][u] = (orow[e] >= 0 && q0 + u < cw) ? coil_map(A, c0 + q0 + u)[g] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int e = 0; e < MAXE; ++e) {
+                    if (orow[e] >= 0) {
+                        const int idx = tid + e * kPassThreads;
+                        const int rr = div_nx(A, idx);
+                        const float2* rp = res + (oi[e] + A.out_off) * kLinePad + rr * cw;
+#pragma unroll
+                        for (int u = 0; u < QB; ++u)
+                            if (q0 + u < cw) acc[e] = cadd(acc[e], cmulc(m[e][u], rp[q0 + u]));
+                    }
                 }
             }
         }
@@ -402,10 +432,10 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
         i0 = (int64_t)blockIdx.x * kLines;  // first line = row * C + c
         const int nx = A.nxi;
         if (tid < kLines) {
-            const int64_t L = i0 + tid;
-            const bool ok = L < A.rows * A.C;
-            const int row = ok ? (int)(L / A.C) : 0;
-            const int c = ok ? (int)(L - (int64_t)row * A.C) : 0;
+            const int L = (int)i0 + tid;               // rows * C < 2^31 (checked at launch)
+            const bool ok = L < (int)(A.rows * A.C);
+            const int row = ok ? L / A.C : 0;
+            const int c = ok ? L - row * A.C : 0;
             const int z = row / A.nyi, yy = row - z * A.nyi;
             srow[tid] = ok ? row : -1;
             scoil[tid] = c;
@@ -418,37 +448,57 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
             bufa[k * kLinePad + l] = make_float2(0.f, 0.f);
         }
         __syncthreads();
-        for (int e = tid; e < kLines * nx; e += kPassThreads) {
-            const int le = div_nx(A, e), i = e - le * nx;
-            const int row = srow[le];
-            float2 v = make_float2(0.f, 0.f);
-            if (row >= 0) {
-                const int64_t g = (int64_t)row * nx + i;
-                v = cscale(cmul(A.x[g], coil_map(A, scoil[le])[g]), sapzy[le] * A.apx[i]);
+        // batches of EB elements per thread: all loads of a batch are in flight together
+        constexpr int EB = 8;
+        for (int e0 = tid; e0 < kLines * nx; e0 += kPassThreads * EB) {
+            float2 xv[EB], mv[EB];
+            float av[EB];
+#pragma unroll
+            for (int b = 0; b < EB; ++b) {
+                const int e = e0 + b * kPassThreads;
+                const int le = div_nx(A, e), i = e - le * nx;
+                xv[b] = mv[b] = make_float2(0.f, 0.f);
+                av[b] = 0.f;
+                if (e < kLines * nx && srow[le] >= 0) {
+                    const int64_t g = (int64_t)srow[le] * nx + i;
+                    xv[b] = A.x[g];
+                    mv[b] = coil_map(A, scoil[le])[g];
+                    av[b] = sapzy[le] * A.apx[i];
+                }
             }
-            bufa[(i + A.in_off) * kLinePad + le] = v;
+#pragma unroll
+            for (int b = 0; b < EB; ++b) {
+                const int e = e0 + b * kPassThreads;
+                const int le = div_nx(A, e), i = e - le * nx;
+                if (e < kLines * nx) bufa[(i + A.in_off) * kLinePad + le] = cscale(cmul(xv[b], mv[b]), av[b]);
+            }
         }
     } else {
-        const int64_t iblocks = (A.inner + kLines - 1) / kLines;
-        o0 = blockIdx.x / iblocks;
-        i0 = (blockIdx.x - o0 * iblocks) * kLines;
+        o0 = blockIdx.y;
+        i0 = (int64_t)blockIdx.x * kLines;
         const int64_t i = i0 + l;
         iv = i < A.inner;
         if (MODE != PLAIN) {
             px = (int)(i / A.C);
             cc = (int)(i - (int64_t)px * A.C);
         }
+        constexpr int LB = 8;   // loads in flight per thread
         if (MODE == SCATTER_Y) {
-            for (int k = jt; k < n; k += kJ) {
-                float2 v = make_float2(0.f, 0.f);
-                if (iv) {
-                    const int32_t f = A.idxmap[(int64_t)k * A.nxi + px];
-                    if (f >= 0) {
-                        v = A.yk[(int64_t)cc * A.N + f];
-                        if (cart_neg(k, px, n, A.nxi)) v = make_float2(-v.x, -v.y);
-                    }
+            for (int k0 = jt; k0 < n; k0 += kJ * LB) {
+                int32_t f[LB];
+                float2 t[LB];
+#pragma unroll
+                for (int b = 0; b < LB; ++b) {
+                    const int k = k0 + b * kJ;
+                    f[b] = (iv && k < n) ? A.idxmap[(int64_t)k * A.nxi + px] : -1;
                 }
-                bufa[k * kLinePad + l] = v;
+#pragma unroll
+                for (int b = 0; b < LB; ++b) t[b] = (f[b] >= 0) ? A.yk[(int64_t)cc * A.N + f[b]] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int b = 0; b < LB; ++b) {
+                    const int k = k0 + b * kJ;
+                    if (k < n) bufa[k * kLinePad + l] = cart_neg(k, px, n, A.nxi) ? make_float2(-t[b].x, -t[b].y) : t[b];
+                }
             }
         } else {
             for (int kk = jt; kk < n - A.n_in; kk += kJ) {
@@ -456,13 +506,23 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
                 bufa[k * kLinePad + l] = make_float2(0.f, 0.f);
             }
             const float2* p = A.in + o0 * A.n_in * A.inner + i;
-#pragma unroll 4
-            for (int kk = jt; kk < A.n_in; kk += kJ)
-                bufa[(kk + A.in_off) * kLinePad + l] = iv ? p[(int64_t)kk * A.inner] : make_float2(0.f, 0.f);
+            for (int k0 = jt; k0 < A.n_in; k0 += kJ * LB) {
+                float2 t[LB];
+#pragma unroll
+                for (int b = 0; b < LB; ++b) {
+                    const int kk = k0 + b * kJ;
+                    t[b] = (iv && kk < A.n_in) ? p[(int64_t)kk * A.inner] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int b = 0; b < LB; ++b) {
+                    const int kk = k0 + b * kJ;
+                    if (kk < A.n_in) bufa[(kk + A.in_off) * kLinePad + l] = t[b];
+                }
+            }
         }
     }
     __syncthreads();
-    float2* res = fft_lines<SIGN>(bufa, bufb, stw, n, srad, A.nrad, l, jt);
+    float2* res = fft_lines<SIGN>(bufa, bufb, stw, n, sst, A.nrad, l, jt);
     float2* other = (res == bufa) ? bufb : bufa;
 
     if (MODE == MASK_Y) {
@@ -483,7 +543,7 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
             res[k * kLinePad + l] = v;
         }
         __syncthreads();
-        res = fft_lines<-SIGN>(res, other, stw, n, srad, A.nrad, l, jt);
+        res = fft_lines<-SIGN>(res, other, stw, n, sst, A.nrad, l, jt);
     }
 
     // ---------------------------------- store ----------------------------------
@@ -531,15 +591,21 @@ cs_status fft_init_attrs() {
 template <int MODE, int SIGN>
 static cs_status launch_pass(const PassArgs& A, cudaStream_t st) {
     const size_t sm = pass_smem(A.n);
-    int64_t blocks;
-    if (MODE == EXPAND_X) blocks = (A.rows * A.C + kLines - 1) / kLines;
+    int64_t blocks, outer = 1;
+    if (MODE == EXPAND_X) {
+        CS_REQUIRE(A.rows * A.C < ((int64_t)1 << 31) - kLines, CS_ERR_UNSUPPORTED_SIZE, "too many x lines");
+        blocks = (A.rows * A.C + kLines - 1) / kLines;
+    }
     else if (MODE == REDUCE_X) blocks = (A.rows + A.rows_per_cta - 1) / A.rows_per_cta;
-    else blocks = A.outer * ((A.inner + kLines - 1) / kLines);
-    if (blocks == 0) return CS_OK;
-    CS_REQUIRE(blocks < (int64_t)1 << 31, CS_ERR_UNSUPPORTED_SIZE, "pass grid too large");
+    else {
+        blocks = (A.inner + kLines - 1) / kLines;
+        outer = A.outer;
+    }
+    if (blocks * outer == 0) return CS_OK;
+    CS_REQUIRE(blocks < (int64_t)1 << 31 && outer <= 65535, CS_ERR_UNSUPPORTED_SIZE, "pass grid too large");
     const int stage = (MODE == EXPAND_X) ? ST_EXPAND : (MODE == REDUCE_X ? ST_REDUCE : ST_FFT_PLAIN);
     prof_begin(stage, st);
-    fft_pass_kernel<MODE, SIGN><<<(unsigned)blocks, kPassThreads, sm, st>>>(A);
+    fft_pass_kernel<MODE, SIGN><<<dim3((unsigned)blocks, (unsigned)outer), kPassThreads, sm, st>>>(A);
     CS_LAUNCH_CHECK();
     prof_end(stage, st);
     return CS_OK;
@@ -548,7 +614,7 @@ static cs_status launch_pass(const PassArgs& A, cudaStream_t st) {
 static void fill_fft(PassArgs& A, const FftLen& f, int sign) {
     A.n = f.n;
     A.nrad = f.nrad;
-    for (int i = 0; i < kMaxRadices; ++i) A.rad[i] = f.rad[i];
+    for (int i = 0; i < kMaxRadices; ++i) A.st[i] = f.st[i];
     A.tw = f.tw;
     A.sign = sign;
 }
@@ -581,7 +647,8 @@ constexpr long long kTmaSpinLimit = 1ll << 24;
 __device__ int g_fft_error = 0;
 
 struct TmaPassArgs {
-    int n, nrad, rad[kMaxRadices];
+    int n, nrad;
+    int4 st[kMaxRadices];
     const float2* tw;
     int64_t iblocks;        // tiles along the line index
     int in_off, h_in, nbox_in;
@@ -599,12 +666,12 @@ __global__ void __launch_bounds__(kPassThreads, 3)
     float2* bufa = tsm;
     float2* bufb = tsm + n * kLines;
     float2* stw = tsm + 2 * n * kLines;
-    __shared__ int srad[kMaxRadices];
+    __shared__ int4 sst[kMaxRadices];
     __shared__ __align__(8) uint64_t mbar;
     const int tid = threadIdx.x;
     const int l = tid % kLines, jt = tid / kLines;
-    const int o0 = (int)(blockIdx.x / A.iblocks);
-    const int i0 = (int)(blockIdx.x - (int64_t)o0 * A.iblocks) * kLines;
+    const int o0 = (int)blockIdx.y;
+    const int i0 = (int)blockIdx.x * kLines;
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar)), "r"(1u));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -623,7 +690,7 @@ __global__ void __launch_bounds__(kPassThreads, 3)
                 : "memory");
         }
     }
-    if (tid < kMaxRadices) srad[tid] = A.rad[tid];
+    if (tid < kMaxRadices) sst[tid] = A.st[tid];
     for (int e = tid; e < n; e += blockDim.x) stw[e] = A.tw[e];
     // bounded wait for the tile (phase 0)
     int done = 0;
@@ -640,7 +707,7 @@ __global__ void __launch_bounds__(kPassThreads, 3)
         if (tid == 0) atomicExch(&g_fft_error, 1);
         return;
     }
-    float2* res = fft_lines<SIGN, kLines>(bufa, bufb, stw, n, srad, A.nrad, l, jt);
+    float2* res = fft_lines<SIGN, kLines>(bufa, bufb, stw, n, sst, A.nrad, l, jt);
     // make the generic-proxy shared-memory writes visible to the copy unit, then store
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -710,7 +777,7 @@ static cs_status pass_plain(const cs_plan* p, int axis, int sign, const float2* 
     TmaPassArgs A = {};
     A.n = f.n;
     A.nrad = f.nrad;
-    for (int i = 0; i < kMaxRadices; ++i) A.rad[i] = f.rad[i];
+    for (int i = 0; i < kMaxRadices; ++i) A.st[i] = f.st[i];
     A.tw = f.tw;
     const int Gx = p->grid[2], Gy = p->grid[1];
     int64_t outer, inner;
@@ -738,18 +805,18 @@ static cs_status pass_plain(const cs_plan* p, int axis, int sign, const float2* 
     A.h_out = box_rows(n_out);
     A.nbox_out = n_out / A.h_out;
     A.iblocks = (inner + kLines - 1) / kLines;
-    const int64_t blocks = outer * A.iblocks;
-    if (blocks == 0) return CS_OK;
-    CS_REQUIRE(blocks < (int64_t)1 << 31 && outer < (int64_t)1 << 31 && inner < (int64_t)1 << 31,
+    if (outer * A.iblocks == 0) return CS_OK;
+    CS_REQUIRE(A.iblocks < (int64_t)1 << 31 && outer <= 65535 && inner < (int64_t)1 << 31,
                CS_ERR_UNSUPPORTED_SIZE, "pass grid too large");
+    const dim3 blocks((unsigned)A.iblocks, (unsigned)outer);
     CUtensorMap tin, tout;
     CS_PROPAGATE(encode_3d(&tin, in, inner, n_in, outer, A.h_in));
     CS_PROPAGATE(encode_3d(&tout, out, inner, n_out, outer, A.h_out));
     prof_begin(ST_FFT_PLAIN, st);
     if (sign < 0)
-        fft_plain_tma_kernel<-1><<<(unsigned)blocks, kPassThreads, tma_pass_smem(A.n), st>>>(tin, tout, A);
+        fft_plain_tma_kernel<-1><<<blocks, kPassThreads, tma_pass_smem(A.n), st>>>(tin, tout, A);
     else
-        fft_plain_tma_kernel<1><<<(unsigned)blocks, kPassThreads, tma_pass_smem(A.n), st>>>(tin, tout, A);
+        fft_plain_tma_kernel<1><<<blocks, kPassThreads, tma_pass_smem(A.n), st>>>(tin, tout, A);
     CS_LAUNCH_CHECK();
     prof_end(ST_FFT_PLAIN, st);
     return CS_OK;
