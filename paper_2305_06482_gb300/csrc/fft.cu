@@ -106,6 +106,12 @@ struct Roots {
     }
 };
 
+// paired single-precision add / subtract / fused multiply-add (one instruction for both halves,
+// each half rounded like its scalar counterpart)
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 fma2s(float s, float2 a, float2 b) { return __ffma2_rn(make_float2(s, s), a, b); }
+
 template <int R, int SIGN>
 __device__ __forceinline__ void dft(float2 (&v)[R]) {
     static_assert(R % 2 == 1, "odd radix");
@@ -114,23 +120,20 @@ __device__ __forceinline__ void dft(float2 (&v)[R]) {
     float2 t[H], d[H];
 #pragma unroll
     for (int q = 1; q <= H; ++q) {
-        t[q - 1] = cadd(v[q], v[R - q]);
-        d[q - 1] = csub(v[q], v[R - q]);
+        t[q - 1] = add2(v[q], v[R - q]);
+        d[q - 1] = sub2(v[q], v[R - q]);
     }
     float2 o[R];
     o[0] = v[0];
 #pragma unroll
-    for (int q = 0; q < H; ++q) o[0] = cadd(o[0], t[q]);
+    for (int q = 0; q < H; ++q) o[0] = add2(o[0], t[q]);
 #pragma unroll
     for (int m = 1; m <= H; ++m) {
         float2 a = v[0], b = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 1; q <= H; ++q) {
-            const float cq = rt.c[(q * m) % R], sq = rt.s[(q * m) % R];
-            a.x = fmaf(cq, t[q - 1].x, a.x);
-            a.y = fmaf(cq, t[q - 1].y, a.y);
-            b.x = fmaf(sq, d[q - 1].x, b.x);
-            b.y = fmaf(sq, d[q - 1].y, b.y);
+            a = fma2s(rt.c[(q * m) % R], t[q - 1], a);
+            b = fma2s(rt.s[(q * m) % R], d[q - 1], b);
         }
         // a + SIGN i b and a - SIGN i b
         o[m] = make_float2(a.x - SIGN * b.y, a.y + SIGN * b.x);
@@ -148,24 +151,24 @@ __device__ __forceinline__ float2 rot_i(float2 a) {   // multiply by SIGN i
 template <>
 __device__ __forceinline__ void dft<2, -1>(float2 (&v)[2]) {
     const float2 a = v[0], b = v[1];
-    v[0] = cadd(a, b);
-    v[1] = csub(a, b);
+    v[0] = add2(a, b);
+    v[1] = sub2(a, b);
 }
 template <>
 __device__ __forceinline__ void dft<2, 1>(float2 (&v)[2]) {
     const float2 a = v[0], b = v[1];
-    v[0] = cadd(a, b);
-    v[1] = csub(a, b);
+    v[0] = add2(a, b);
+    v[1] = sub2(a, b);
 }
 
 template <int SIGN>
 __device__ __forceinline__ void dft4(float2 (&v)[4]) {
-    const float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-    const float2 s13 = cadd(v[1], v[3]), d13 = rot_i<SIGN>(csub(v[1], v[3]));
-    v[0] = cadd(s02, s13);
-    v[2] = csub(s02, s13);
-    v[1] = cadd(d02, d13);
-    v[3] = csub(d02, d13);
+    const float2 s02 = add2(v[0], v[2]), d02 = sub2(v[0], v[2]);
+    const float2 s13 = add2(v[1], v[3]), d13 = rot_i<SIGN>(sub2(v[1], v[3]));
+    v[0] = add2(s02, s13);
+    v[2] = sub2(s02, s13);
+    v[1] = add2(d02, d13);
+    v[3] = sub2(d02, d13);
 }
 template <>
 __device__ __forceinline__ void dft<4, -1>(float2 (&v)[4]) { dft4<-1>(v); }
@@ -183,14 +186,14 @@ __device__ __forceinline__ void dft8(float2 (&v)[8]) {
     const float2 t1 = make_float2(h * (o[1].x - SIGN * o[1].y), h * (o[1].y + SIGN * o[1].x));
     const float2 t2 = rot_i<SIGN>(o[2]);
     const float2 t3 = make_float2(h * (-o[3].x - SIGN * o[3].y), h * (-o[3].y + SIGN * o[3].x));
-    v[0] = cadd(e[0], o[0]);
-    v[4] = csub(e[0], o[0]);
-    v[1] = cadd(e[1], t1);
-    v[5] = csub(e[1], t1);
-    v[2] = cadd(e[2], t2);
-    v[6] = csub(e[2], t2);
-    v[3] = cadd(e[3], t3);
-    v[7] = csub(e[3], t3);
+    v[0] = add2(e[0], o[0]);
+    v[4] = sub2(e[0], o[0]);
+    v[1] = add2(e[1], t1);
+    v[5] = sub2(e[1], t1);
+    v[2] = add2(e[2], t2);
+    v[6] = sub2(e[2], t2);
+    v[3] = add2(e[3], t3);
+    v[7] = sub2(e[3], t3);
 }
 template <>
 __device__ __forceinline__ void dft<8, -1>(float2 (&v)[8]) { dft8<-1>(v); }
@@ -658,7 +661,7 @@ struct TmaPassArgs {
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 template <int SIGN>
-__global__ void __launch_bounds__(kPassThreads, 3)
+__global__ void __launch_bounds__(kPassThreads, 4)
     fft_plain_tma_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
                          const __grid_constant__ TmaPassArgs A) {
     extern __shared__ __align__(1024) float2 tsm[];
