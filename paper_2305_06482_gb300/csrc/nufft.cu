@@ -464,7 +464,9 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
             const float4 wy = *reinterpret_cast<const float4*>(r + 4);
             const float4 wx = *reinterpret_cast<const float4*>(r + 8);
             const float wyv[kW] = {wy.x, wy.y, wy.z, wy.w};
-            const float wxv[kW] = {wx.x, wx.y, wx.z, wx.w};
+            // x weights as pairs for the paired single-precision FMA (both halves of a complex value)
+            const float2 wx2[kW] = {make_float2(wx.x, wx.x), make_float2(wx.y, wx.y), make_float2(wx.z, wx.z),
+                                    make_float2(wx.w, wx.w)};
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 const int q = slice + p * S;                    // z residue held by this plane
@@ -485,15 +487,10 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
                 for (int b = 0; b < kW; ++b) {
                     float2 t = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int d = 0; d < kW; ++d) {
-                        t.x = fmaf(wxv[d], W.v[p][b][d].x, t.x);
-                        t.y = fmaf(wxv[d], W.v[p][b][d].y, t.y);
-                    }
-                    pa.x = fmaf(wyv[b], t.x, pa.x);
-                    pa.y = fmaf(wyv[b], t.y, pa.y);
+                    for (int d = 0; d < kW; ++d) t = __ffma2_rn(wx2[d], W.v[p][b][d], t);
+                    pa = __ffma2_rn(make_float2(wyv[b], wyv[b]), t, pa);
                 }
-                acc.x = fmaf(wzp, pa.x, acc.x);
-                acc.y = fmaf(wzp, pa.y, acc.y);
+                acc = __ffma2_rn(make_float2(wzp, wzp), pa, acc);
             }
             if (S > 1) {
 #pragma unroll
@@ -622,7 +619,9 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
             const float4 wy = *reinterpret_cast<const float4*>(r + 4);
             const float4 wx = *reinterpret_cast<const float4*>(r + 8);
             const float wyv[kW] = {wy.x, wy.y, wy.z, wy.w};
-            const float wxv[kW] = {wx.x, wx.y, wx.z, wx.w};
+            // x weights as pairs for the paired single-precision FMA (both halves of a complex value)
+            const float2 wx2[kW] = {make_float2(wx.x, wx.x), make_float2(wx.y, wx.y), make_float2(wx.z, wx.z),
+                                    make_float2(wx.w, wx.w)};
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 const int q = slice + p * S;
@@ -637,10 +636,7 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
                 for (int b = 0; b < kW; ++b) {
                     const float2 vb = cscale(va, wyv[b]);
 #pragma unroll
-                    for (int d = 0; d < kW; ++d) {
-                        W.v[p][b][d].x = fmaf(wxv[d], vb.x, W.v[p][b][d].x);
-                        W.v[p][b][d].y = fmaf(wxv[d], vb.y, W.v[p][b][d].y);
-                    }
+                    for (int d = 0; d < kW; ++d) W.v[p][b][d] = __ffma2_rn(wx2[d], vb, W.v[p][b][d]);
                 }
             }
         }
