@@ -287,6 +287,7 @@ struct PassArgs {
     int64_t rows;    // nz * ny image rows
     int C;           // coils (interleave stride)
     int rows_per_cta;
+    int cw;          // REDUCE_X: coils per chunk (rows_per_cta * cw <= kLines lines)
     uint32_t nx_mag; // floor(2^32 / nxi) + 1
     // maps / image
     const float2* maps_v;
@@ -318,6 +319,18 @@ __device__ __forceinline__ bool cart_neg(int py, int px, int ny, int nx) {
     return (py + px + ny / 2 + nx / 2) & 1;
 }
 
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// asynchronous global -> shared copies of 8 and 4 bytes (every copy of a thread in flight at once;
+// cp.async.wait_all makes them visible to the issuing thread, a barrier to the others)
+__device__ __forceinline__ void cp8(float2* dst, const float2* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp4(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // i / nxi for 0 <= i < 2^16 (the x-pass element loops stay below 16 * 512)
 __device__ __forceinline__ int div_nx(const PassArgs& A, int i) { return (int)__umulhi((uint32_t)i, A.nx_mag); }
 
@@ -333,6 +346,7 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
     __shared__ int srow[kLines];               // x passes: image row of the line (-1: none)
     __shared__ int scoil[kLines];
     __shared__ float sapzy[kLines];
+    __shared__ float sapx[MODE == EXPAND_X ? 512 : 1];   // nx <= 512
     const int tid = threadIdx.x;
     const int l = tid % kLines, jt = tid / kLines;
     if (tid < kMaxRadices) sst[tid] = A.st[tid];
@@ -356,7 +370,7 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
             orow[e] = (idx < R * nx && r0 + rr < A.rows) ? r0 + rr : -1;
             oi[e] = (orow[e] >= 0) ? oi[e] : 0;
         }
-        const int cwmax = (A.C >= kLines) ? kLines : A.C;
+        const int cwmax = A.cw;
         for (int c0 = 0; c0 < A.C; c0 += cwmax) {
             const int cw = min(cwmax, A.C - c0);
             __syncthreads();
@@ -370,44 +384,31 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
             {
                 const bool ok = srow[l] >= 0;
                 const float2* p = A.in + sbase[l];
-                constexpr int LB = 8;
-                for (int k0 = jt; k0 < n; k0 += kJ * LB) {
-                    float2 t[LB];
-#pragma unroll
-                    for (int b = 0; b < LB; ++b) {
-                        const int k = k0 + b * kJ;
-                        t[b] = (ok && k < n) ? p[(int64_t)k * A.C] : make_float2(0.f, 0.f);
-                    }
-#pragma unroll
-                    for (int b = 0; b < LB; ++b) {
-                        const int k = k0 + b * kJ;
-                        if (k < n) bufa[k * kLinePad + l] = t[b];
-                    }
+                for (int k = jt; k < n; k += kJ) {
+                    if (ok) cp8(&bufa[k * kLinePad + l], p + (int64_t)k * A.C);
+                    else bufa[k * kLinePad + l] = make_float2(0.f, 0.f);
                 }
+                cp_wait_all();
             }
             __syncthreads();
             float2* res = fft_lines<SIGN>(bufa, bufb, stw, n, sst, A.nrad, l, jt);
-            // coil maps in batches of QB coils for every output element: MAXE * QB loads in flight
-            constexpr int QB = 4;
-            for (int q0 = 0; q0 < cw; q0 += QB) {
-                float2 m[MAXE][QB];
+            // the coil maps of the chunk's lines, staged in the buffer the FFT left free:
+            // mp[line * nx + i] (line = rr * cw + q)
+            float2* mp = (res == bufa) ? bufb : bufa;
+            for (int e = tid; e < R * cw * nx; e += kPassThreads) {
+                const int ln = div_nx(A, e), i = e - ln * nx;
+                if (srow[ln] >= 0) cp8(&mp[e], coil_map(A, c0 + ln % cw) + (int64_t)srow[ln] * nx + i);
+            }
+            cp_wait_all();
+            __syncthreads();
 #pragma unroll
-                for (int e = 0; e < MAXE; ++e) {
-                    const int64_t g = (int64_t)orow[e] * nx + oi[e];
-#pragma unroll
-                    for (int u = 0; u < QB; ++u)
-                        m[e][u] = (orow[e] >= 0 && q0 + u < cw) ? coil_map(A, c0 + q0 + u)[g] : make_float2(0.f, 0.f);
-                }
-#pragma unroll
-                for (int e = 0; e < MAXE; ++e) {
-                    if (orow[e] >= 0) {
-                        const int idx = tid + e * kPassThreads;
-                        const int rr = div_nx(A, idx);
-                        const float2* rp = res + (oi[e] + A.out_off) * kLinePad + rr * cw;
-#pragma unroll
-                        for (int u = 0; u < QB; ++u)
-                            if (q0 + u < cw) acc[e] = cadd(acc[e], cmulc(m[e][u], rp[q0 + u]));
-                    }
+            for (int e = 0; e < MAXE; ++e) {
+                if (orow[e] >= 0) {
+                    const int idx = tid + e * kPassThreads;
+                    const int rr = div_nx(A, idx);
+                    const float2* rp = res + (oi[e] + A.out_off) * kLinePad + rr * cw;
+                    const float2* mq = mp + rr * cw * nx + oi[e];
+                    for (int q = 0; q < cw; ++q) acc[e] = cadd(acc[e], cmulc(mq[q * nx], rp[q]));
                 }
             }
         }
@@ -451,29 +452,27 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
             bufa[k * kLinePad + l] = make_float2(0.f, 0.f);
         }
         __syncthreads();
-        // batches of EB elements per thread: all loads of a batch are in flight together
-        constexpr int EB = 8;
-        for (int e0 = tid; e0 < kLines * nx; e0 += kPassThreads * EB) {
-            float2 xv[EB], mv[EB];
-            float av[EB];
-#pragma unroll
-            for (int b = 0; b < EB; ++b) {
-                const int e = e0 + b * kPassThreads;
-                const int le = div_nx(A, e), i = e - le * nx;
-                xv[b] = mv[b] = make_float2(0.f, 0.f);
-                av[b] = 0.f;
-                if (e < kLines * nx && srow[le] >= 0) {
-                    const int64_t g = (int64_t)srow[le] * nx + i;
-                    xv[b] = A.x[g];
-                    mv[b] = coil_map(A, scoil[le])[g];
-                    av[b] = sapzy[le] * A.apx[i];
-                }
+        // x (per line) -> bufa rows in_off.., maps -> bufb, apodisation along x -> sapx, all
+        // asynchronous; then each thread forms the products of the elements it copied
+        for (int i = tid; i < nx; i += kPassThreads) cp4(&sapx[i], A.apx + i);
+        for (int e = tid; e < kLines * nx; e += kPassThreads) {
+            const int le = div_nx(A, e), i = e - le * nx;
+            const int row = srow[le];
+            if (row >= 0) {
+                const int64_t g = (int64_t)row * nx + i;
+                cp8(&bufa[(i + A.in_off) * kLinePad + le], A.x + g);
+                cp8(&bufb[i * kLinePad + le], coil_map(A, scoil[le]) + g);
+            } else {
+                bufa[(i + A.in_off) * kLinePad + le] = make_float2(0.f, 0.f);
             }
-#pragma unroll
-            for (int b = 0; b < EB; ++b) {
-                const int e = e0 + b * kPassThreads;
-                const int le = div_nx(A, e), i = e - le * nx;
-                if (e < kLines * nx) bufa[(i + A.in_off) * kLinePad + le] = cscale(cmul(xv[b], mv[b]), av[b]);
+        }
+        cp_wait_all();
+        __syncthreads();
+        for (int e = tid; e < kLines * nx; e += kPassThreads) {
+            const int le = div_nx(A, e), i = e - le * nx;
+            if (srow[le] >= 0) {
+                float2* d = &bufa[(i + A.in_off) * kLinePad + le];
+                *d = cscale(cmul(*d, bufb[i * kLinePad + le]), sapzy[le] * sapx[i]);
             }
         }
     } else {
@@ -657,8 +656,6 @@ struct TmaPassArgs {
     int in_off, h_in, nbox_in;
     int out_off, h_out, nbox_out;
 };
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 template <int SIGN>
 __global__ void __launch_bounds__(kPassThreads, 4)
@@ -862,8 +859,23 @@ static cs_status pass_reduce(const cs_plan* p, const float2* maps_v, int V, cons
     A.addv = addv;
     A.lambda = lambda;
     const int C = V + S;
-    A.rows_per_cta = (C >= kLines || C == 0) ? 1 : kLines / C;   // C == 0: only lambda v / accumulate
-    A.rows_per_cta = std::max(1, std::min(A.rows_per_cta, 4 * kPassThreads / p->img[2]));
+    // coils per chunk cw and rows per CTA R = kLines / cw chosen to waste the fewest of the
+    // kLines transform lines per image row (ceil(C / cw) chunks of R rows each), the widest
+    // chunk among equals
+    const int rmax = std::max(1, 4 * kPassThreads / p->img[2]);   // output elements per thread <= 4
+    int best_cw = 1, best_R = 1;
+    double best = 1e300;
+    for (int cw = std::min(std::max(C, 1), kLines); cw >= 1; --cw) {   // ties: the widest chunk
+        const int R = std::min(kLines / cw, rmax);
+        const double slots = (double)((C + cw - 1) / cw) * kLines / R;
+        if (slots < best - 1e-9) {
+            best = slots;
+            best_cw = cw;
+            best_R = R;
+        }
+    }
+    A.cw = best_cw;
+    A.rows_per_cta = best_R;
     return launch_pass<REDUCE_X, 1>(A, st);
 }
 
