@@ -309,8 +309,12 @@ def run_native(args, w, rank, world, local_rank):
     avg_ms = dom_ms / max(dom_n, 1)
     per_launch_bytes = dom_bytes / max(dom_n_model, 1)
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else None
+    ratio = TRAFFIC_RATIO.get(dom)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
+                "frac": (achieved / hbm_peak) if achieved else None,
+                "traffic": ratio * per_launch_bytes if ratio else None,
+                "traffic_source": ("ncu DRAM read+write / algorithmic bytes of one launch on the 128^3 cones, "
+                                   f"10-coil case ({ratio}), scaled to this launch size") if ratio else None,
                 "launches": dom_n, "launches_model": dom_n_model, "avg_launch_ms": avg_ms,
                 "bytes_per_launch": per_launch_bytes,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
@@ -368,12 +372,20 @@ def run_native(args, w, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+# DRAM bytes (read + write) over algorithmic bytes of one launch, measured with ncu on the 128^3
+# cones, 10-coil sketched normal operator (spread and interpolation: the whole launch; strided
+# passes: mean of the forward y and z passes; writes still dirty in L2 at kernel end are not
+# counted there).  Traffic grows in proportion to the algorithmic bytes, so the bench scales it.
+TRAFFIC_RATIO = {"spread": 1.040, "interp": 0.832, "fft_plain": 0.90}
+
+
 def stage_bytes(stage, w, T, steps):
     """Algorithmic bytes moved by all launches of one stage during the timed reconstructions.
 
     Per call with c coils (coil-interleaved buffers, complex64 = 8 B):
-      interp / spread : c (8G + 8N) + 16N per launch (sample coordinates, sqrt(w), permutation)
-                        and one launch per chunk of <= 16 coils;
+      interp / spread : c (8G + 8N) + 64N per launch (the 64-byte per-sample record: rotated
+                        weights, box start, sqrt(w), user index) and one launch per chunk of
+                        <= 16 coils;
       fft_plain       : the four strided passes of a forward + adjoint read and write
                         2 c 8 (nz ny Gx + 2 nz Gy Gx + G);
       expand / reduce : 8D + c (8D + 8 nz ny Gx).
@@ -389,7 +401,7 @@ def stage_bytes(stage, w, T, steps):
     for c, n in calls:
         if stage in ("interp", "spread"):
             nl = -(-c // 16)
-            tot += n * (c * (8 * G + 8 * N) + nl * 16 * N)
+            tot += n * (c * (8 * G + 8 * N) + nl * 64 * N)
             launches += n * nl
         elif stage == "fft_plain":
             tot += n * 2 * c * 8 * (nz * ny * Gx + 2 * nz * Gy * Gx + G)

@@ -270,93 +270,108 @@ struct WavArgs {
     int bz, by, bx;      // current corner block
     int axis;            // 0 z, 1 y, 2 x
     int inverse;
+    uint32_t m_mag;      // floor(2^32 / M) + 1 for the line length M of this pass
 };
 
 constexpr int kWavLines = 16;
 constexpr int kWavMax = 512;
 
+// One CTA filters kWavLines lines of length M held in shared memory (pitch M + 1).  x lines
+// (axis 2) are read and written along the line (consecutive threads, consecutive elements); for
+// the strided axes a thread keeps one line (t mod kWavLines) and walks its elements, so the
+// kWavLines consecutive x positions of a row are one coalesced segment.  Periodic indices are
+// reduced by one conditional subtraction (every tap index lies below M + 8 <= 2M).
 __global__ void __launch_bounds__(256) wavelet_pass_kernel(WavArgs W) {
     extern __shared__ float2 wsm[];
     const int M = (W.axis == 0) ? W.bz : (W.axis == 1 ? W.by : W.bx);
-    float2 (*line)[kWavMax + 1] = reinterpret_cast<float2 (*)[kWavMax + 1]>(wsm);
-    float2 (*outl)[kWavMax + 1] = reinterpret_cast<float2 (*)[kWavMax + 1]>(wsm + kWavLines * (kWavMax + 1));
-    // lines: enumerate the other two block coordinates; for axes 0/1 the x coordinate is the
-    // fastest so a CTA takes kWavLines consecutive x values (coalesced)
-    int64_t nlines;
-    if (W.axis == 2) nlines = (int64_t)W.bz * W.by;
-    else if (W.axis == 1) nlines = (int64_t)W.bz * W.bx;
-    else nlines = (int64_t)W.by * W.bx;
-    const int64_t l0 = (int64_t)blockIdx.x * kWavLines;
+    const int P = M + 1;
+    float2* line = wsm;
+    float2* outl = wsm + kWavLines * P;
+    __shared__ int64_t sbase[kWavLines];
     const int tid = threadIdx.x;
-    auto elem = [&](int64_t li, int k) -> int64_t {
+    const int64_t stride = (W.axis == 2) ? 1 : (W.axis == 1 ? (int64_t)W.nx : (int64_t)W.nx * W.ny);
+    if (tid < kWavLines) {
+        const int64_t li = (int64_t)blockIdx.x * kWavLines + tid;
+        int64_t nlines, base = -1;
         if (W.axis == 2) {
-            const int z = (int)(li / W.by), y = (int)(li % W.by);
-            return ((int64_t)z * W.ny + y) * W.nx + k;
+            nlines = (int64_t)W.bz * W.by;
+            if (li < nlines) base = ((li / W.by) * W.ny + li % W.by) * W.nx;
         } else if (W.axis == 1) {
-            const int z = (int)(li / W.bx), x = (int)(li % W.bx);
-            return ((int64_t)z * W.ny + k) * W.nx + x;
+            nlines = (int64_t)W.bz * W.bx;
+            if (li < nlines) base = (li / W.bx) * W.ny * W.nx + li % W.bx;
         } else {
-            const int y = (int)(li / W.bx), x = (int)(li % W.bx);
-            return ((int64_t)k * W.ny + y) * W.nx + x;
+            nlines = (int64_t)W.by * W.bx;
+            if (li < nlines) base = (li / W.bx) * W.nx + li % W.bx;
         }
-    };
-    for (int e = tid; e < kWavLines * M; e += blockDim.x) {
-        int l, k;
-        if (W.axis == 2) {
-            l = e / M;
-            k = e % M;
-        } else {
-            l = e % kWavLines;
-            k = e / kWavLines;
-        }
-        const int64_t li = l0 + l;
-        line[l][k] = (li < nlines) ? W.data[elem(li, k)] : make_float2(0.f, 0.f);
+        sbase[tid] = base;
     }
     __syncthreads();
     const int H = M / 2;
-    for (int e = tid; e < kWavLines * M; e += blockDim.x) {
-        int l, k;
+    // element e of the CTA's kWavLines x M block -> (line l, position k)
+    auto lk = [&](int e, int& l, int& k) {
         if (W.axis == 2) {
-            l = e / M;
-            k = e % M;
+            l = (int)__umulhi((uint32_t)e, W.m_mag);
+            k = e - l * M;
         } else {
             l = e % kWavLines;
             k = e / kWavLines;
         }
+    };
+    constexpr int LB = 8;
+    for (int e0 = tid; e0 < kWavLines * M; e0 += 256 * LB) {
+        float2 t[LB];
+#pragma unroll
+        for (int b = 0; b < LB; ++b) {
+            const int e = e0 + 256 * b;
+            int l, k;
+            lk(e, l, k);
+            t[b] = (e < kWavLines * M && sbase[l] >= 0) ? W.data[sbase[l] + k * stride] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int b = 0; b < LB; ++b) {
+            const int e = e0 + 256 * b;
+            int l, k;
+            lk(e, l, k);
+            if (e < kWavLines * M) line[l * P + k] = t[b];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < kWavLines * M; e += 256) {
+        int l, k;
+        lk(e, l, k);
+        const float2* x = line + l * P;
         float2 acc = make_float2(0.f, 0.f);
         if (!W.inverse) {
             const int kk = (k < H) ? k : k - H;
             const float* f = (k < H) ? c_h : c_g;
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
-                const float2 v = line[l][(2 * kk + m) % M];
+                int idx = 2 * kk + m;
+                if (idx >= M) idx -= M;
+                const float2 v = x[idx];
                 acc.x = fmaf(f[m], v.x, acc.x);
                 acc.y = fmaf(f[m], v.y, acc.y);
             }
         } else {
             // x[j] = sum over taps m with (j - m) even: h[m] a[k] + g[m] d[k], k = ((j - m) mod M) / 2
 #pragma unroll
-            for (int m = (k & 1); m < 8; m += 2) {
-                const int kk = (((k - m) % M) + M) % M / 2;
-                const float2 a = line[l][kk], d = line[l][H + kk];
+            for (int mm = 0; mm < 4; ++mm) {
+                const int m = 2 * mm + (k & 1);
+                int t = k - m;
+                if (t < 0) t += M;
+                const int kk = t >> 1;
+                const float2 a = x[kk], d = x[H + kk];
                 acc.x = fmaf(c_h[m], a.x, fmaf(c_g[m], d.x, acc.x));
                 acc.y = fmaf(c_h[m], a.y, fmaf(c_g[m], d.y, acc.y));
             }
         }
-        outl[l][k] = acc;
+        outl[l * P + k] = acc;
     }
     __syncthreads();
-    for (int e = tid; e < kWavLines * M; e += blockDim.x) {
+    for (int e = tid; e < kWavLines * M; e += 256) {
         int l, k;
-        if (W.axis == 2) {
-            l = e / M;
-            k = e % M;
-        } else {
-            l = e % kWavLines;
-            k = e / kWavLines;
-        }
-        const int64_t li = l0 + l;
-        if (li < nlines) W.data[elem(li, k)] = outl[l][k];
+        lk(e, l, k);
+        if (sbase[l] >= 0) W.data[sbase[l] + k * stride] = outl[l * P + k];
     }
 }
 
@@ -449,8 +464,11 @@ static cs_status wavelet_apply(float2* data, const int dims3[3], int nd, int lev
         W.bx = dims3[2] >> lev;
         W.axis = axis;
         W.inverse = inverse;
+        const int M = (axis == 0) ? W.bz : (axis == 1 ? W.by : W.bx);
+        W.m_mag = (uint32_t)(0x100000000ull / (unsigned long long)M) + 1u;
+        const size_t smem = sizeof(float2) * 2 * kWavLines * (size_t)(M + 1);
         int64_t nlines = (axis == 2) ? (int64_t)W.bz * W.by : (axis == 1 ? (int64_t)W.bz * W.bx : (int64_t)W.by * W.bx);
-        wavelet_pass_kernel<<<(unsigned)((nlines + kWavLines - 1) / kWavLines), 256, kWavSmem, st>>>(W);
+        wavelet_pass_kernel<<<(unsigned)((nlines + kWavLines - 1) / kWavLines), 256, smem, st>>>(W);
         CS_LAUNCH_CHECK();
         return CS_OK;
     };
