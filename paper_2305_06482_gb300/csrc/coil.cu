@@ -291,12 +291,19 @@ void hermitian_eig_serial(double* A, int n, double* V, double* ev) {
 }
 
 // One CTA: the same sweeps with the O(n) row/column updates spread over threads.
+// Parallel ordering of the same rotations (Brent and Luk's round robin): a sweep is m - 1 rounds
+// (m = n rounded up to even; the pairs with the extra index of odd n are skipped), each of m/2
+// disjoint pivot pairs.  All rotation angles of a round come from the matrix before the round;
+// because the pairs are disjoint, applying every column rotation and then every row rotation is
+// J^H A J for J the product of the round's rotations, and it zeroes each pivot entry exactly as
+// the single rotation would.  A sweep still visits every pair once.
 __global__ void jacobi_kernel(const double* __restrict__ Rin, int n, float2* __restrict__ Uout,
                               double* __restrict__ evout) {
     extern __shared__ double sm[];
     double* A = sm;
     double* V = sm + 2 * n * n;
-    __shared__ Rot rot;
+    __shared__ Rot rots[32];
+    __shared__ int pp[32], pq[32];
     __shared__ double s_off, s_fro;
     __shared__ double ev[64];
     const int tid = threadIdx.x;
@@ -320,30 +327,57 @@ __global__ void jacobi_kernel(const double* __restrict__ Rin, int n, float2* __r
         s_fro = f;
     }
     __syncthreads();
+    const int m = (n + 1) & ~1;
+    const int half = m / 2;
     for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
         if (tid == 0) s_off = offdiag2(A, n);
         __syncthreads();
         if (s_off <= 1e-30 * s_fro) break;
-        for (int p = 0; p < n - 1; ++p)
-            for (int q = p + 1; q < n; ++q) {
-                if (tid == 0) rot = jacobi_rot(A, n, p, q);
-                __syncthreads();
-                const Rot r = rot;
-                if (!r.skip) {
-                    if (tid < n) {
-                        rot_cols(A, n, tid, p, q, r);
-                        rot_cols(V, n, tid, p, q, r);
-                    }
-                    __syncthreads();
-                    if (tid < n) rot_rows(A, n, tid, p, q, r);
-                    __syncthreads();
-                    if (tid == 0) {
-                        A[2 * (p * n + q)] = A[2 * (p * n + q) + 1] = 0;
-                        A[2 * (q * n + p)] = A[2 * (q * n + p) + 1] = 0;
-                    }
+        for (int round = 0; round < m - 1; ++round) {
+            if (tid < half) {
+                // player at seat k in this round: seat 0 fixed, the others rotate
+                auto player = [&](int k) { return k == 0 ? 0 : 1 + (k - 1 + round) % (m - 1); };
+                int p = player(tid), q = player(m - 1 - tid);
+                if (p > q) {
+                    const int t = p;
+                    p = q;
+                    q = t;
                 }
-                __syncthreads();
+                Rot r;
+                if (q >= n) {
+                    r.cs = 1;
+                    r.sn = 0;
+                    r.er = 1;
+                    r.ei = 0;
+                    r.skip = true;
+                } else {
+                    r = jacobi_rot(A, n, p, q);
+                }
+                rots[tid] = r;
+                pp[tid] = p;
+                pq[tid] = q;
             }
+            __syncthreads();
+            for (int e = tid; e < half * n; e += blockDim.x) {   // columns p, q of A and V
+                const int i = e / n, k = e - (e / n) * n;
+                if (!rots[i].skip) {
+                    rot_cols(A, n, k, pp[i], pq[i], rots[i]);
+                    rot_cols(V, n, k, pp[i], pq[i], rots[i]);
+                }
+            }
+            __syncthreads();
+            for (int e = tid; e < half * n; e += blockDim.x) {   // rows p, q of A
+                const int i = e / n, k = e - (e / n) * n;
+                if (!rots[i].skip) rot_rows(A, n, k, pp[i], pq[i], rots[i]);
+            }
+            __syncthreads();
+            if (tid < half && !rots[tid].skip) {
+                const int p = pp[tid], q = pq[tid];
+                A[2 * (p * n + q)] = A[2 * (p * n + q) + 1] = 0;
+                A[2 * (q * n + p)] = A[2 * (q * n + p) + 1] = 0;
+            }
+            __syncthreads();
+        }
     }
     if (tid == 0) eig_finish(A, n, V, ev);
     __syncthreads();
@@ -476,7 +510,7 @@ cs_status coil_pca_impl(const float2* y, int C, int64_t N, float2* U, double* ei
     cov_kernel<<<grid, threads, sm, st>>>(y, C, N, Rws);
     CS_LAUNCH_CHECK();
     const size_t jsm = sizeof(double) * 4 * C * C;
-    jacobi_kernel<<<1, 64, jsm, st>>>(Rws, C, U, eig);
+    jacobi_kernel<<<1, 256, jsm, st>>>(Rws, C, U, eig);
     CS_LAUNCH_CHECK();
     return CS_OK;
 }

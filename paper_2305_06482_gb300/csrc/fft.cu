@@ -344,7 +344,8 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
     __shared__ int4 sst[kMaxRadices];
     __shared__ int64_t sbase[kLines];          // x passes: per-line element offset
     __shared__ int srow[kLines];               // x passes: image row of the line (-1: none)
-    __shared__ int scoil[kLines];
+    __shared__ const float2* sxp[kLines];      // x passes: row pointers of x / the line's map
+    __shared__ const float2* smp[kLines];
     __shared__ float sapzy[kLines];
     __shared__ float sapx[MODE == EXPAND_X ? 512 : 1];   // nx <= 512
     const int tid = threadIdx.x;
@@ -379,13 +380,15 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
                 const bool ok = tid < R * cw && row < A.rows;
                 srow[tid] = ok ? row : -1;
                 sbase[tid] = ok ? (int64_t)row * n * A.C + c : 0;
+                smp[tid] = ok ? coil_map(A, c) + (int64_t)row * nx : nullptr;
             }
             __syncthreads();
             {
                 const bool ok = srow[l] >= 0;
-                const float2* p = A.in + sbase[l];
-                for (int k = jt; k < n; k += kJ) {
-                    if (ok) cp8(&bufa[k * kLinePad + l], p + (int64_t)k * A.C);
+                const float2* p = A.in + sbase[l] + (int64_t)jt * A.C;
+                const int64_t step = (int64_t)kJ * A.C;
+                for (int k = jt; k < n; k += kJ, p += step) {
+                    if (ok) cp8(&bufa[k * kLinePad + l], p);
                     else bufa[k * kLinePad + l] = make_float2(0.f, 0.f);
                 }
                 cp_wait_all();
@@ -397,7 +400,7 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
             float2* mp = (res == bufa) ? bufb : bufa;
             for (int e = tid; e < R * cw * nx; e += kPassThreads) {
                 const int ln = div_nx(A, e), i = e - ln * nx;
-                if (srow[ln] >= 0) cp8(&mp[e], coil_map(A, c0 + ln % cw) + (int64_t)srow[ln] * nx + i);
+                if (smp[ln]) cp8(&mp[e], smp[ln] + i);
             }
             cp_wait_all();
             __syncthreads();
@@ -442,9 +445,10 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
             const int c = ok ? L - row * A.C : 0;
             const int z = row / A.nyi, yy = row - z * A.nyi;
             srow[tid] = ok ? row : -1;
-            scoil[tid] = c;
             sapzy[tid] = A.apz[z] * A.apy[yy];
             sbase[tid] = (int64_t)row * n * A.C + c;
+            sxp[tid] = ok ? A.x + (int64_t)row * nx : nullptr;
+            smp[tid] = ok ? coil_map(A, c) + (int64_t)row * nx : nullptr;
         }
         // zero padding rows outside [in_off, in_off + nx)
         for (int kk = jt; kk < n - nx; kk += kJ) {
@@ -457,20 +461,19 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
         for (int i = tid; i < nx; i += kPassThreads) cp4(&sapx[i], A.apx + i);
         for (int e = tid; e < kLines * nx; e += kPassThreads) {
             const int le = div_nx(A, e), i = e - le * nx;
-            const int row = srow[le];
-            if (row >= 0) {
-                const int64_t g = (int64_t)row * nx + i;
-                cp8(&bufa[(i + A.in_off) * kLinePad + le], A.x + g);
-                cp8(&bufb[i * kLinePad + le], coil_map(A, scoil[le]) + g);
+            float2* da = &bufa[(i + A.in_off) * kLinePad + le];
+            if (sxp[le]) {
+                cp8(da, sxp[le] + i);
+                cp8(&bufb[i * kLinePad + le], smp[le] + i);
             } else {
-                bufa[(i + A.in_off) * kLinePad + le] = make_float2(0.f, 0.f);
+                *da = make_float2(0.f, 0.f);
             }
         }
         cp_wait_all();
         __syncthreads();
         for (int e = tid; e < kLines * nx; e += kPassThreads) {
             const int le = div_nx(A, e), i = e - le * nx;
-            if (srow[le] >= 0) {
+            if (sxp[le]) {
                 float2* d = &bufa[(i + A.in_off) * kLinePad + le];
                 *d = cscale(cmul(*d, bufb[i * kLinePad + le]), sapzy[le] * sapx[i]);
             }
@@ -510,10 +513,11 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
             const float2* p = A.in + o0 * A.n_in * A.inner + i;
             for (int k0 = jt; k0 < A.n_in; k0 += kJ * LB) {
                 float2 t[LB];
+                const float2* pk = p + (int64_t)k0 * A.inner;
 #pragma unroll
                 for (int b = 0; b < LB; ++b) {
                     const int kk = k0 + b * kJ;
-                    t[b] = (iv && kk < A.n_in) ? p[(int64_t)kk * A.inner] : make_float2(0.f, 0.f);
+                    t[b] = (iv && kk < A.n_in) ? pk[(int64_t)b * kJ * A.inner] : make_float2(0.f, 0.f);
                 }
 #pragma unroll
                 for (int b = 0; b < LB; ++b) {
@@ -551,9 +555,10 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
     // ---------------------------------- store ----------------------------------
     if (MODE == EXPAND_X) {
         if (srow[l] >= 0) {
-            float2* p = A.out + sbase[l];
+            float2* p = A.out + sbase[l] + (int64_t)jt * A.C;
+            const int64_t step = (int64_t)kJ * A.C;
 #pragma unroll 4
-            for (int k = jt; k < n; k += kJ) p[(int64_t)k * A.C] = res[k * kLinePad + l];
+            for (int k = jt; k < n; k += kJ, p += step) *p = res[k * kLinePad + l];
         }
     } else if (MODE == GATHER_Y) {
         if (iv) {

@@ -261,6 +261,27 @@ def cones_dcf(traj, img_shape, n_int, n_read=512):
     return w.astype(np.float32)
 
 
+def radial_trajectory(n_spokes, n_read=256):
+    """2D golden-angle radial stand-in (full spokes through the centre), float32
+    [n_spokes*n_read, 2] in cycles/pixel, axis order (y, x), radius in [-0.5, 0.5)."""
+    i = np.arange(n_spokes, dtype=np.float64)[:, None]
+    p = np.arange(n_read, dtype=np.float64)[None, :]
+    ang = i * math.pi * (math.sqrt(5.0) - 1.0) / 2.0
+    kr = (p - n_read / 2) / n_read
+    traj = np.stack([kr * np.sin(ang), kr * np.cos(ang)], axis=-1).reshape(-1, 2)
+    return traj.astype(np.float32)
+
+
+def radial_dcf(traj, img_shape, n_spokes, n_read=256):
+    """Analytic density compensation of the radial stand-in (ring spacing pi |k| / n_spokes
+    times the readout spacing), float32 [N]."""
+    D = float(np.prod(img_shape))
+    kr = np.sqrt(np.sum(traj.astype(np.float64) ** 2, axis=-1))
+    dk = 1.0 / n_read
+    w = D * math.pi * np.maximum(kr, 0.25 * dk) * dk / n_spokes
+    return w.astype(np.float32)
+
+
 def complex_noise(shape, sigma, seed=3):
     rng = _rng(seed)
     return (sigma / math.sqrt(2)) * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))

@@ -99,6 +99,42 @@ def test_nufft_fwd_adj(img, grid, C, n_int, tile):
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
 
 
+@pytest.mark.parametrize("img,grid,C,spokes", [((240, 240), (300, 300), 5, 96), ((64, 48), (80, 60), 3, 40)])
+def test_nufft_2d_fwd_adj(img, grid, C, spokes):
+    """2D radial plans: one lane per coil in the gridding kernels; a 300-point grid axis takes
+    two 150-row tensor-copy boxes in the strided pass and the 240-row crop one box."""
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    traj = synthdata.radial_trajectory(spokes, 256)
+    dcf = synthdata.radial_dcf(traj, img, spokes, 256)
+    maps = synthdata.coil_maps(img, C)
+    x = synthdata.phantom(img, seed=4)
+    plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=t(traj), dcf=t(dcf), grid=grid)
+    op = nufft.Plan(traj, img, grid)
+    y = cs.sense_fwd(plan, t(x), t(maps))
+    assert nrmse(h(y), nufft.sense_fwd(op, x, maps, dcf)) < TOL
+    yy = synthdata.random_complex((C, traj.shape[0]), 6)
+    xa = cs.sense_adj(plan, t(yy), t(maps))
+    assert nrmse(h(xa), nufft.sense_adj(op, yy, maps, dcf)) < TOL
+
+
+@pytest.mark.parametrize("C", [7, 33])
+def test_nufft_coil_chunks(C):
+    """Coil counts that split the gridding into several chunks (33: three chunks of 11 coils)
+    and an odd count for the coil-combining pass's chunk choice."""
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    img, grid = (16, 16, 16), (20, 20, 20)
+    traj, dcf, maps, x = _nufft_case(img, grid, C, 60, 64)
+    plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=t(traj), dcf=t(dcf), grid=grid)
+    op = nufft.Plan(traj, img, grid)
+    y = cs.sense_fwd(plan, t(x), t(maps))
+    assert nrmse(h(y), nufft.sense_fwd(op, x, maps, dcf)) < TOL
+    yy = synthdata.random_complex((C, traj.shape[0]), 7)
+    xa = cs.sense_adj(plan, t(yy), t(maps))
+    assert nrmse(h(xa), nufft.sense_adj(op, yy, maps, dcf)) < TOL
+
+
 def test_nufft_binning_bit_exact():
     import paper_2305_06482_gb300 as cs
     from tests._gpu import t
