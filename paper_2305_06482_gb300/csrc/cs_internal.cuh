@@ -92,12 +92,6 @@ constexpr int kPassThreads = 256;
 
 // ------------------------------------------------------------------------------------------
 // Plan
-struct WorkItem {
-    int tile;    // linear tile id
-    int start;   // first sorted sample
-    int count;   // samples in this item
-};
-
 }  // namespace cs
 
 struct cs_plan {
@@ -129,10 +123,8 @@ struct cs_plan {
     int tile[3] = {1, 1, 1};
     int ntiles[3] = {1, 1, 1};
     int64_t ntiles_total = 0;
-    cs::WorkItem* items = nullptr;  // spread/interp work items
-    int nitems = 0;
-    int spread_chunk = 0;         // samples per spreading work item
-    int interp_chunk = 0;         // consecutive sorted samples per warp (interp and spread)
+    int interp_chunk = 0;         // consecutive sorted samples per warp, interpolation
+    int spread_chunk = 0;         // consecutive sorted samples per warp, spreading
     int interp_coils = 16;        // coils per warp in interpolation (8, 16 or 32)
     int spread_coils = 16;        // coils per warp in spreading (8 or 16)
     float* phi = nullptr;         // KB kernel table [2049] on [0, 2]

@@ -183,26 +183,7 @@ cs_status nufft_bin(cs_plan* p, const float* traj, const float* dcf, cudaStream_
     bin_scatter_kernel<<<nb, 256, 0, st>>>(key, lrank, counts, p->tile_off, ntiles, g, dcf, N, p->perm,
                                            p->gsorted, p->wsorted);
     BIN_TRY(cudaGetLastError());
-    // work items on the host (plan time): split every tile into chunks of <= spread_chunk samples
-    std::vector<int32_t> off(ntiles + 1);
-    BIN_TRY(cudaMemcpyAsync(off.data(), p->tile_off, sizeof(int32_t) * (ntiles + 1), cudaMemcpyDeviceToHost, st));
-    BIN_TRY(cudaStreamSynchronize(st));
-    std::vector<WorkItem> items;
-    const int M = p->spread_chunk;
-    for (int t = 0; t < ntiles; ++t) {
-        for (int s = off[t]; s < off[t + 1]; s += M) {
-            WorkItem w;
-            w.tile = t;
-            w.start = s;
-            w.count = std::min(M, off[t + 1] - s);
-            items.push_back(w);
-        }
-    }
-    p->nitems = (int)items.size();
-    if (p->nitems > 0) {
-        BIN_TRY(cudaMalloc(&p->items, sizeof(WorkItem) * items.size()));
-        BIN_TRY(cudaMemcpy(p->items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice));
-    }
+    BIN_TRY(cudaStreamSynchronize(st));   // the scratch buffers are freed below
     cleanup();
 #undef BIN_TRY
     return rc;
@@ -376,6 +357,14 @@ __device__ __forceinline__ void set_offsets(int (&off)[kW], int j0, int G, int s
 #ifndef CS_SPREAD_MINB_P2
 #define CS_SPREAD_MINB_P2 4
 #endif
+// decode the next sample's record head one sample ahead (measured: helps the spreading, not the
+// interpolation, whose registers are tighter)
+#ifndef CS_INTERP_HEAD_PREFETCH
+#define CS_INTERP_HEAD_PREFETCH 0
+#endif
+#ifndef CS_SPREAD_HEAD_PREFETCH
+#define CS_SPREAD_HEAD_PREFETCH 1
+#endif
 #define CS_INTERP_MINB(P) ((P) == 1 ? CS_INTERP_MINB_P1 : (P) == 2 ? CS_INTERP_MINB_P2 : 1)
 #define CS_SPREAD_MINB(P) ((P) == 1 ? CS_SPREAD_MINB_P1 : (P) == 2 ? CS_SPREAD_MINB_P2 : 1)
 
@@ -390,9 +379,10 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
     const bool active = coil_l < A.gsize;
     const int c = A.c0 + (active ? coil_l : 0);
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t s0 = warp * A.chunk;
-    if (s0 >= A.N) return;                       // whole warp exits together
-    const int64_t s1 = min(A.N, s0 + A.chunk);
+    const int64_t s0l = warp * A.chunk;
+    if (s0l >= A.N) return;                      // whole warp exits together
+    // sample indices fit in 32 bits (plans hold fewer than 2^31 samples)
+    const int s0 = (int)s0l, s1 = (int)min(A.N, s0l + A.chunk);
     float* wrec = srec + (threadIdx.x >> 5) * (kStage * kRec);
     const int sy = A.Gx * A.C, sz = A.Gy * A.Gx * A.C;
     const float2* g = A.grid + c;
@@ -409,13 +399,21 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
 #pragma unroll
     for (int r = 0; r < kW; ++r) W.yoff[r] = W.xoff[r] = 0;
     int cy = kNoPlane, cx = kNoPlane;
-    for (int64_t base = s0; base < s1; base += kStage) {
-        const int n = (int)min((int64_t)kStage, s1 - base);
+    for (int base = s0; base < s1; base += kStage) {
+        const int n = min(kStage, s1 - base);
         stage_records(A, base, n, wrec, lane);
+#if CS_INTERP_HEAD_PREFETCH
+        BoxHead Bn = box_head(wrec);
+#endif
 #pragma unroll 1
         for (int i = 0; i < n; ++i) {
             const float* r = wrec + i * kRec;
+#if CS_INTERP_HEAD_PREFETCH
+            const BoxHead B = Bn;
+            if (i + 1 < n) Bn = box_head(r + kRec);
+#else
             const BoxHead B = box_head(r);
+#endif
             const int dy = B.jy - cy, dx = B.jx - cx;
             if ((unsigned)(dy + 1) > 2u || (unsigned)(dx + 1) > 2u) {   // not a step of -1, 0 or +1
                 set_offsets(W.yoff, B.jy, A.Gy, sy);
@@ -500,7 +498,7 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
                 }
             }
             if (active && slice == 0) {
-                const int64_t s = base + i;
+                const int64_t s = (int64_t)base + i;
                 acc = cscale(acc, B.sw);
                 if (mode == OUT_USER) {
                     out[(int64_t)c * A.N + B.perm] = acc;
@@ -523,9 +521,9 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
     const bool active = coil_l < A.gsize;
     const int c = A.c0 + (active ? coil_l : 0);
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t s0 = warp * A.chunk;
-    if (s0 >= A.N) return;
-    const int64_t s1 = min(A.N, s0 + A.chunk);
+    const int64_t s0l = warp * A.chunk;
+    if (s0l >= A.N) return;
+    const int s0 = (int)s0l, s1 = (int)min(A.N, s0l + A.chunk);
     float* wrec = srec + (threadIdx.x >> 5) * (kStage * kRec);
     const int sy = A.Gx * A.C, sz = A.Gy * A.Gx * A.C;
     float2* g = A.grid + c;
@@ -555,18 +553,26 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
             for (int d = 0; d < kW; ++d) W.v[p][b][d] = make_float2(0.f, 0.f);
     };
     // the sample value: sorted scratch [N][C] or user order [C][N]
-    auto load_v = [&](int64_t s, const float* r) -> float2 {
+    auto load_v = [&](int s, const float* r) -> float2 {
         if (!active) return make_float2(0.f, 0.f);
-        return sorted_in ? yin[s * A.C + c] : yin[(int64_t)c * A.N + __float_as_int(r[14])];
+        return sorted_in ? yin[(int64_t)s * A.C + c] : yin[(int64_t)c * A.N + __float_as_int(r[14])];
     };
-    for (int64_t base = s0; base < s1; base += kStage) {
-        const int n = (int)min((int64_t)kStage, s1 - base);
+    for (int base = s0; base < s1; base += kStage) {
+        const int n = min(kStage, s1 - base);
         stage_records(A, base, n, wrec, lane);
         float2 vnext = load_v(base, wrec);
+#if CS_SPREAD_HEAD_PREFETCH
+        BoxHead Bn = box_head(wrec);
+#endif
 #pragma unroll 1
         for (int i = 0; i < n; ++i) {
             const float* r = wrec + i * kRec;
+#if CS_SPREAD_HEAD_PREFETCH
+            const BoxHead B = Bn;
+            if (i + 1 < n) Bn = box_head(r + kRec);
+#else
             const BoxHead B = box_head(r);
+#endif
             float2 v = vnext;
             if (i + 1 < n) vnext = load_v(base + i + 1, r + kRec);   // one sample ahead
             const int dy = B.jy - cy, dx = B.jx - cx;
@@ -669,6 +675,7 @@ template <bool SPREAD>
 static cs_status launch_grid_op(const cs_plan* p, int ncoils, int mode, const float2* ysub, float2* out,
                                 const float2* yin, int sorted_in, cudaStream_t st) {
     GridArgs A = make_grid_args(p, ncoils);
+    A.chunk = SPREAD ? p->spread_chunk : p->interp_chunk;
     const int64_t warps = (p->N + A.chunk - 1) / A.chunk;
     const unsigned nb = (unsigned)((warps + kGridWarps - 1) / kGridWarps);
     if (nb == 0) return CS_OK;

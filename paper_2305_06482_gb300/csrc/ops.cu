@@ -127,7 +127,6 @@ static void plan_free(cs_plan* p) {
     cudaFree(p->perm);
     cudaFree(p->j0);
     cudaFree(p->tile_off);
-    cudaFree(p->items);
     cudaFree(p->phi);
     cudaFree(p->rec);
     cudaFree(p->bufA);
@@ -235,12 +234,12 @@ static cs_status plan_build(cs_plan* p, const cs_geom* g, cudaStream_t st) {
         p->ntiles[a] = (p->grid[a] + t - 1) / t;
     }
     p->ntiles_total = (int64_t)p->ntiles[0] * p->ntiles[1] * p->ntiles[2];
-    p->spread_chunk = 8192;
+    p->spread_chunk = 64;
     p->interp_chunk = 64;
     // tuning knobs (coils per warp of the gridding kernels, samples per warp)
     if (const char* e = getenv("CS_INTERP_COILS")) p->interp_coils = std::max(1, std::min(32, atoi(e)));
     if (const char* e = getenv("CS_SPREAD_COILS")) p->spread_coils = std::max(1, std::min(16, atoi(e)));
-    if (const char* e = getenv("CS_GRID_CHUNK")) p->interp_chunk = std::max(1, atoi(e));
+    if (const char* e = getenv("CS_GRID_CHUNK")) p->interp_chunk = p->spread_chunk = std::max(1, atoi(e));
     {
         // phi(u) = I0(beta sqrt(1 - (u/2)^2)) / I0(beta) on [0, 2], 2049 points
         const int nt = 2048;
