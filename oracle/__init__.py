@@ -17,7 +17,8 @@ coils     Coil PCA (SVD-based coil compression, Sec. 3.1 and Alg. 1), structured
           (Sec. 2.3, S^t = S~^t (x) I_N with the virtual-coil block form) and sketched maps.
 philox    Philox4x32-10 counter-based generator and the sketch entry distributions (Sec. 3.2).
 wavelet   Periodised orthonormal Daubechies-4 (db4, 8 taps) multi-level DWT (Sec. 2.1, l1-wavelets).
-solvers   CG, FISTA, power iteration, the sketched sub-problem (Eq. 9-10) and Algorithm 1.
+tv        Periodic first-order differences and the dual projection of l1-TV (Sec. 2.1).
+solvers   CG, FISTA, PDHG, power iteration, the sketched sub-problem (Eq. 9-10) and Algorithm 1.
 
 Parity pins live in ``tests/test_oracle_*.py``: each function here is checked against
 something other than itself (dense matrices built from Eq. 1, closed forms, invariants,

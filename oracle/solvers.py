@@ -1,7 +1,8 @@
 """Solvers and the coil-sketching outer loop (Sec. 2.1, 2.3, Algorithm 1).
 
-Problem (Eq. 3-4): x* = argmin_x 1/2 ||A x - y||^2 + g(x), g = lambda/2 ||x||^2 (solved by CG)
-or g = lambda ||Psi x||_1 (solved by FISTA).
+Problem (Eq. 3-4): x* = argmin_x 1/2 ||A x - y||^2 + g(x), g = lambda/2 ||x||^2 (solved by CG),
+g = lambda ||Psi x||_1 (solved by FISTA) or g = lambda ||T x||_1 (l1-TV, solved by PDHG whose
+data step solves an l2-regularised least-squares problem with CG, Sec. 2.1 and Sec. 4).
 
 Sketched sub-problem at outer iteration t (Eq. 9-10, Algorithm 1):
     x^{t+1} = argmin_x 1/2 ||A_S^t (x - x^t)||^2 + Re<x, d> + g(x),  d = A^H (A x^t - y).
@@ -16,7 +17,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import coils, wavelet
+from . import coils, tv, wavelet
 
 
 def vdot(a, b):
@@ -76,6 +77,31 @@ def fista(grad, prox, x0, eta, iters):
     return x_prev
 
 
+def pdhg(prox_f, lam, x0, z0, tau, sigma, iters):
+    """Primal-dual hybrid gradient (Chambolle & Pock 2011, their Algorithm 1 with theta = 1) on
+    min_x f(x) + lam ||T x||_1:
+        z_{k+1} = proj_lam(z_k + sigma T xbar_k)
+        x_{k+1} = prox_{tau f}(x_k - tau T^H z_{k+1}, warm start x_k)
+        xbar_{k+1} = 2 x_{k+1} - x_k,          xbar_0 = x_0.
+    Returns (x_K, z_K)."""
+    x = np.array(x0, dtype=np.complex128, copy=True)
+    z = np.array(z0, dtype=np.complex128, copy=True)
+    xbar = x.copy()
+    for _ in range(iters):
+        z = tv.project_disc(z + sigma * tv.tv_fwd(xbar), lam)
+        x_new = prox_f(x - tau * tv.tv_adj(z), x)
+        xbar = 2.0 * x_new - x
+        x = x_new
+    return x, z
+
+
+def pdhg_steps(ndim):
+    """Default step sizes (reading; the paper gives none): tau = sigma = 0.99 / ||T||, so that
+    tau sigma ||T||^2 < 1 as PDHG's convergence requires."""
+    s = 0.99 / np.sqrt(tv.tv_norm_sq(ndim))
+    return float(s), float(s)
+
+
 # ---------------------------------------------------------------------------------------
 # Sub-problem solvers (Eq. 9-10)
 
@@ -91,6 +117,25 @@ def sketched_fista(normal_S, d, xt, lam, eta, iters, levels=4):
     grad = lambda z: normal_S(z - xt) + d
     prox = lambda v: wavelet.prox_l1_wavelet(v, eta * lam, levels)
     return fista(grad, prox, xt, eta, iters)
+
+
+def sketched_pdhg(normal_S, d, xt, lam, z0, tau, sigma, iters, cg_iters):
+    """l1-TV sub-problem by PDHG from x^t.  f(x) = 1/2 ||A_S (x - x^t)||^2 + Re<x, d>, so
+    prox_{tau f}(v) solves (A_S^H A_S + I/tau) x = A_S^H A_S x^t - d + v/tau, here by
+    ``cg_iters`` CG iterations started at the current primal iterate.  The dual variable z is
+    passed in and returned (carried from one sub-problem to the next)."""
+    b0 = normal_S(xt) - d
+    H = lambda v: normal_S(v) + v / tau
+    prox_f = lambda v, xw: cg(H, b0 + v / tau, xw, cg_iters)
+    return pdhg(prox_f, lam, xt, z0, tau, sigma, iters)
+
+
+def plain_pdhg(fwd, adj, y, lam, x0, z0, tau, sigma, iters, cg_iters):
+    """Full-coil l1-TV by PDHG: prox_{tau f}(v) solves (A^H A + I/tau) x = A^H y + v/tau by CG."""
+    b0 = adj(y)
+    H = lambda v: adj(fwd(v)) + v / tau
+    prox_f = lambda v, xw: cg(H, b0 + v / tau, xw, cg_iters)
+    return pdhg(prox_f, lam, x0, z0, tau, sigma, iters)
 
 
 def plain_cg(fwd, adj, y, lam, x0, iters):
@@ -109,14 +154,17 @@ def plain_fista(fwd, adj, y, lam, eta, x0, iters, levels=4):
 # Algorithm 1
 
 def coil_sketching(op_factory, maps, y, lam, reg, sketches, V, K, x0=None, eta=None,
-                   power_v0=None, power_iters=20, do_pca=True, levels=4, callback=None):
+                   power_v0=None, power_iters=20, do_pca=True, levels=4, callback=None,
+                   cg_iters=5, tau=None, sigma=None):
     """Algorithm 1 (no classical-sketch initialisation).
 
     op_factory(maps) -> (fwd, adj) builds A for a set of maps (Cartesian or NUFFT).
     sketches: float [T, S, C-V] random blocks S~_S^t (given as inputs).
-    reg: 'l2' (CG, K iterations) or 'l1wav' (FISTA, K iterations, step eta; if eta is None it
+    reg: 'l2' (CG, K iterations), 'l1wav' (FISTA, K iterations, step eta; if eta is None it
     is 1/L with L from ``power_iters`` power iterations on the first sketched normal operator,
-    started at power_v0, and reused for every sub-problem).
+    started at power_v0, and reused for every sub-problem) or 'l1tv' (PDHG, K iterations with
+    ``cg_iters`` CG iterations in each data step, steps tau/sigma (default ``pdhg_steps``); the
+    dual variable starts at zero and is carried from one sub-problem to the next).
     Returns x^T and the list of iterates.
     """
     if do_pca:
@@ -128,6 +176,11 @@ def coil_sketching(op_factory, maps, y, lam, reg, sketches, V, K, x0=None, eta=N
     fwd, adj = op_factory(maps_r)
     x = np.zeros(maps.shape[1:], dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128)
     iterates = []
+    if reg == "l1tv":
+        t0, s0 = pdhg_steps(x.ndim)
+        tau = t0 if tau is None else tau
+        sigma = s0 if sigma is None else sigma
+        zdual = np.zeros((x.ndim,) + x.shape, dtype=np.complex128)
     for t in range(sketches.shape[0]):
         d = adj(fwd(x) - y_r)                                   # true gradient
         msk = coils.sketched_maps(sketches[t], maps_r, V)       # sketched model A_S^t
@@ -135,6 +188,8 @@ def coil_sketching(op_factory, maps, y, lam, reg, sketches, V, K, x0=None, eta=N
         normal_S = lambda v: ads(fs(v))
         if reg == "l2":
             x = sketched_cg(normal_S, d, x, lam, K)
+        elif reg == "l1tv":
+            x, zdual = sketched_pdhg(normal_S, d, x, lam, zdual, tau, sigma, K, cg_iters)
         else:
             if eta is None:
                 L = power_iteration(normal_S, power_v0, power_iters)
