@@ -45,7 +45,7 @@ enum { CS_CARTESIAN = 0, CS_NONCARTESIAN = 1 };
 enum { CS_GAUSSIAN = 0, CS_RADEMACHER = 1 };
 enum { CS_NORM_UNIT_VAR = 0, CS_NORM_PAPER_LITERAL = 1 };
 enum { CS_PREC_FP32 = 0, CS_PREC_BF16_SPLIT = 1 };
-enum { CS_REG_L2 = 0, CS_REG_L1_WAVELET = 1 };
+enum { CS_REG_L2 = 0, CS_REG_L1_WAVELET = 1, CS_REG_L1_TV = 2 };
 
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* cs_last_error(void);
@@ -175,6 +175,20 @@ cs_status coil_rotate(const float* U, const float* in, int C, int C_out, int64_t
 cs_status sketch_draw(uint64_t seed, int t0, int T, int C, int V, int S, int dist, int norm,
                       float* out, void* stream);
 
+/* ------------------------------------------------------------------------------------------
+ * The two element-wise steps of PDHG for l1-TV (Sec. 2.1, Chambolle & Pock 2011) around its
+ * data step, as run inside recon_solve; T = forward differences with periodic wrap along every
+ * axis of the image dims (slow to fast, ndim 2 or 3).  All arrays device complex64.
+ * tv_dual_update: z_a <- proj(z_a + sigma (T xbar)_a), xbar = 2 x - x_prev (x_prev NULL: x),
+ *   proj scaling every entry of modulus above lambda down to lambda; z [ndim][image], in place.
+ * tv_rhs: rhs = b0 + inv_tau x - T^H z, (T^H z)[r] = sum_a z_a[r - e_a] - z_a[r]; b0 may be NULL
+ *   (zero); x_prev_out (may be NULL) receives a copy of x.
+ * ---------------------------------------------------------------------------------------- */
+cs_status tv_dual_update(const float* x, const float* x_prev, float* z, int ndim, const int* dims, float sigma,
+                         float lambda, void* stream);
+cs_status tv_rhs(const float* b0, const float* x, const float* z, int ndim, const int* dims, float inv_tau,
+                 float* rhs, float* x_prev_out, void* stream);
+
 /* Synchronise `stream` and report (then clear) a device-side timeout of a bounded wait. */
 cs_status cs_device_status(void* stream);
 
@@ -200,7 +214,12 @@ cs_status sketched_maps(const float* S, const float* maps_rot, int64_t D, int C,
  *
  * problem: y [C][N] k-space (density-compensated data y = W^1/2 k for non-Cartesian),
  *          maps [C][image], lambda, reg (CS_REG_L2 -> CG, CS_REG_L1_WAVELET -> FISTA with a
- *          periodised db4 transform, `wavelet_levels` levels).
+ *          periodised db4 transform, `wavelet_levels` levels, CS_REG_L1_TV -> PDHG
+ *          (Chambolle & Pock 2011, theta = 1) on lambda ||T x||_1, T the forward differences
+ *          along every image axis with periodic wrap, the l1 norm summing complex moduli
+ *          (Sec. 2.1); each PDHG data step prox_{tau f} is solved by `cg_iters` CG iterations
+ *          started at the current iterate; the dual variable starts at zero and is carried
+ *          from one sketched sub-problem to the next).
  * params:  T outer iterations, K inner iterations, V, S, sketch distribution/normalisation,
  *          seed (or a caller-given sketch array), whether to run coil PCA first, the FISTA
  *          step (0 = estimate 1/L by `power_iters` power iterations on the first sketched
@@ -236,6 +255,9 @@ typedef struct {
                                 (plain) as a CUDA graph and replay it                         */
     float* iterates;         /* optional device [T][image]: x^t after every outer iteration
                                 (plain solver: [K][image], after every iteration)             */
+    int cg_iters;            /* CS_REG_L1_TV: CG iterations per PDHG data step (0 = 5)         */
+    float tv_tau, tv_sigma;  /* CS_REG_L1_TV: PDHG primal/dual steps; 0 = 0.99 / sqrt(4 ndim)
+                                each (tau sigma ||T||^2 < 1 with ||T||^2 = 4 ndim)            */
 } cs_solve_params;
 
 typedef struct {

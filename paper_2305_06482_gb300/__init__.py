@@ -27,7 +27,7 @@ CARTESIAN, NONCARTESIAN = 0, 1
 GAUSSIAN, RADEMACHER = 0, 1
 NORM_UNIT_VAR, NORM_PAPER_LITERAL = 0, 1
 PREC_FP32, PREC_BF16_SPLIT = 0, 1
-REG_L2, REG_L1_WAVELET = 0, 1
+REG_L2, REG_L1_WAVELET, REG_L1_TV = 0, 1, 2
 
 
 class CoilSketchError(RuntimeError):
@@ -53,7 +53,8 @@ class _Params(ctypes.Structure):
                 ("S", ctypes.c_int), ("dist", ctypes.c_int), ("norm", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("sketches", ctypes.c_void_p), ("do_pca", ctypes.c_int), ("precision", ctypes.c_int),
                 ("step", ctypes.c_float), ("power_iters", ctypes.c_int), ("power_v0", ctypes.c_void_p),
-                ("use_graph", ctypes.c_int), ("iterates", ctypes.c_void_p)]
+                ("use_graph", ctypes.c_int), ("iterates", ctypes.c_void_p), ("cg_iters", ctypes.c_int),
+                ("tv_tau", ctypes.c_float), ("tv_sigma", ctypes.c_float)]
 
 
 class _BatchItem(ctypes.Structure):
@@ -73,7 +74,7 @@ EXPORTED = [
     "cs_hermitian_eig_host", "cs_launch_count", "cs_profile", "cs_profile_read", "coil_pca_noalloc", "cs_device_status", "recon_solve_batched",
     "sketched_subproblem_solve", "cs_subproblem_objective", "cs_power_iteration", "cs_nn_pack_weights",
     "cs_nn_conv3d", "cs_nn_conv3d_wgrad", "cs_nn_relu_bwd", "cs_nn_conv1", "cs_nn_conv1_bwd", "cs_nn_mse",
-    "cs_nn_adam", "cs_nn_features", "cs_nn_target", "cs_nn_apply", "cs_nn_status",
+    "cs_nn_adam", "cs_nn_features", "cs_nn_target", "cs_nn_apply", "cs_nn_status", "tv_dual_update", "tv_rhs",
 ]
 STAGES = {"spread": 0, "interp": 1, "fft_plain": 2, "expand": 3, "reduce": 4}
 
@@ -116,6 +117,8 @@ def lib():
             "cs_nn_mse": ([vp, vp, i64, vp, vp, vp], i), "cs_nn_adam": ([vp, vp, vp, vp, i64, f, f, f, f, i, vp], i),
             "cs_nn_features": ([vp, vp, i64, f, vp, vp, vp], i), "cs_nn_target": ([vp, vp, i64, vp, vp, vp], i),
             "cs_nn_apply": ([vp, vp, i64, vp, vp, vp], i), "cs_nn_status": ([vp], i),
+            "tv_dual_update": ([vp, vp, vp, i, vp, f, f, vp], i),
+            "tv_rhs": ([vp, vp, vp, i, vp, f, vp, vp, vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -325,6 +328,39 @@ def soft_threshold_(z, tau, stream=None):
     return z
 
 
+def _require_c64(*ts):
+    for v in ts:
+        if v is not None and (v.dtype != torch.complex64 or not v.is_contiguous() or not v.is_cuda):
+            raise ValueError("expected contiguous complex64 CUDA tensors")
+
+
+def _dims(x, ndim):
+    return (ctypes.c_int * ndim)(*[int(v) for v in x.shape[-ndim:]])
+
+
+def tv_dual_update(x, z, sigma, lam, x_prev=None, stream=None):
+    """In place: z <- proj_lam(z + sigma T (2 x - x_prev)) (x_prev None: T x); z [ndim, *x.shape]."""
+    nd = x.dim()
+    _require_c64(x, z, x_prev)
+    if tuple(z.shape) != (nd,) + tuple(x.shape) or (x_prev is not None and x_prev.shape != x.shape):
+        raise ValueError("tv_dual_update: z must be [ndim, *x.shape] and x_prev like x")
+    _check(lib().tv_dual_update(_ptr(x), None if x_prev is None else _ptr(x_prev), _ptr(z), nd, _dims(x, nd),
+                                float(sigma), float(lam), _stream(stream)))
+    return z
+
+
+def tv_rhs(x, z, inv_tau, b0=None, x_prev_out=None, stream=None):
+    """rhs = b0 + inv_tau x - T^H z (b0 None: zero); x_prev_out (if given) receives x."""
+    nd = x.dim()
+    _require_c64(x, z, b0, x_prev_out)
+    if tuple(z.shape) != (nd,) + tuple(x.shape) or any(v is not None and v.shape != x.shape for v in (b0, x_prev_out)):
+        raise ValueError("tv_rhs: z must be [ndim, *x.shape], b0 and x_prev_out like x")
+    rhs = torch.empty_like(x)
+    _check(lib().tv_rhs(None if b0 is None else _ptr(b0), _ptr(x), _ptr(z), nd, _dims(x, nd), float(inv_tau),
+                        _ptr(rhs), None if x_prev_out is None else _ptr(x_prev_out), _stream(stream)))
+    return rhs
+
+
 def hermitian_eig_host(A):
     """Run the library's FP64 Jacobi eigensolver on the host (numpy complex128 [n, n])."""
     import numpy as np
@@ -373,6 +409,9 @@ class SolveParams:
     power_v0: Optional[torch.Tensor] = None
     use_graph: bool = False
     iterates: Optional[torch.Tensor] = None
+    cg_iters: int = 0          # l1-TV: CG iterations per PDHG data step (0 = 5)
+    tv_tau: float = 0.0        # l1-TV: PDHG steps (0 = 0.99 / sqrt(4 ndim))
+    tv_sigma: float = 0.0
 
 
 def recon_solve(plan: Plan, y, maps, lam, reg=REG_L2, params: SolveParams = None, x0=None, wavelet_levels=4,
@@ -383,14 +422,7 @@ def recon_solve(plan: Plan, y, maps, lam, reg=REG_L2, params: SolveParams = None
     x = torch.zeros(plan.img, dtype=torch.complex64, device=y.device) if x0 is None else x0.clone()
     pr = _Problem(y=y.data_ptr(), maps=maps.data_ptr(), C=C, lam=float(lam), reg=int(reg),
                   wavelet_levels=int(wavelet_levels))
-    sp = _Params(T=params.T, K=params.K, sketch=int(params.sketch), V=params.V, S=params.S, dist=params.dist,
-                 norm=params.norm, seed=params.seed,
-                 sketches=None if params.sketches is None else params.sketches.data_ptr(),
-                 do_pca=int(params.do_pca), precision=params.precision, step=float(params.step),
-                 power_iters=params.power_iters,
-                 power_v0=None if params.power_v0 is None else params.power_v0.data_ptr(),
-                 use_graph=int(params.use_graph),
-                 iterates=None if params.iterates is None else params.iterates.data_ptr())
+    sp = _params_struct(params)
     st = _Stats()
     _check(lib().recon_solve(plan.handle, ctypes.byref(pr), ctypes.byref(sp), _ptr(x), ctypes.byref(st),
                              _stream(stream)))
@@ -406,7 +438,8 @@ def _params_struct(params: SolveParams):
                    power_iters=params.power_iters,
                    power_v0=None if params.power_v0 is None else params.power_v0.data_ptr(),
                    use_graph=int(params.use_graph),
-                   iterates=None if params.iterates is None else params.iterates.data_ptr())
+                   iterates=None if params.iterates is None else params.iterates.data_ptr(),
+                   cg_iters=int(params.cg_iters), tv_tau=float(params.tv_tau), tv_sigma=float(params.tv_sigma))
 
 
 def recon_solve_batched(items, lam, reg=REG_L2, params: SolveParams = None, wavelet_levels=4, stream=None):

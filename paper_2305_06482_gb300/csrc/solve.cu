@@ -482,6 +482,104 @@ static cs_status wavelet_apply(float2* data, const int dims3[3], int nd, int lev
     return CS_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// l1 total variation (Sec. 2.1: g(x) = lambda ||T x||_1, T the forward differences along every
+// image axis with periodic wrap; anisotropic: the l1 norm sums the complex moduli of all
+// differences) and the two element-wise steps of PDHG (Chambolle & Pock 2011) around its data
+// step.  The dual variable is stored [ndim][image], component a for the a-th image axis (slow to
+// fast: z, y, x; 2D images: y, x).
+
+struct TvDims {
+    int nd;            // image axes (2 or 3)
+    int n[3];          // sizes slow to fast, n[0] = 1 for 2D
+    int64_t D;
+};
+
+// dual step: z_a <- proj_lambda(z_a + sigma (T xbar)_a), xbar = 2 x - x_prev (x_prev null: xbar = x);
+// proj_lambda scales an entry down to modulus lambda when it is larger.  One CTA per image row
+// (z, y), threads along x.
+__global__ void tv_dual_kernel(const float2* __restrict__ x, const float2* __restrict__ xp, float2* __restrict__ z,
+                               TvDims t, float sigma, float lam) {
+    const float lam2 = lam * lam;
+    const int rows = t.n[0] * t.n[1];
+    const int64_t sy = t.n[2], sz = (int64_t)t.n[1] * t.n[2];
+    auto xbar = [&](int64_t j) {
+        float2 v = x[j];
+        if (xp) v = make_float2(2.f * v.x - xp[j].x, 2.f * v.y - xp[j].y);
+        return v;
+    };
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int iz = row / t.n[1], iy = row - iz * t.n[1];
+        const int64_t base = (int64_t)row * t.n[2];
+        // offsets of the +1 neighbour along z and y (periodic)
+        const int64_t dz = (iz + 1 < t.n[0]) ? sz : -(int64_t)(t.n[0] - 1) * sz;
+        const int64_t dy = (iy + 1 < t.n[1]) ? sy : -(int64_t)(t.n[1] - 1) * sy;
+        for (int ix = threadIdx.x; ix < t.n[2]; ix += blockDim.x) {
+            const int64_t i = base + ix;
+            const int64_t nx1 = (ix + 1 < t.n[2]) ? i + 1 : base;
+            const float2 xc = xbar(i);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a < 3 - t.nd) continue;
+                const int c = a - (3 - t.nd);
+                const float2 xn = xbar(a == 0 ? i + dz : (a == 1 ? i + dy : nx1));
+                float2 v = z[c * t.D + i];
+                v.x = fmaf(sigma, xn.x - xc.x, v.x);
+                v.y = fmaf(sigma, xn.y - xc.y, v.y);
+                const float m2 = fmaf(v.x, v.x, v.y * v.y);
+                if (m2 > lam2) {
+                    const float sc = lam * rsqrtf(m2);
+                    v.x *= sc;
+                    v.y *= sc;
+                }
+                z[c * t.D + i] = v;
+            }
+        }
+    }
+}
+
+// data-step right-hand side: rhs = b0 + x / tau - T^H z, (T^H z)[r] = sum_a z_a[r - e_a] - z_a[r];
+// x_prev (if given) receives x.  b0 may be null (zero).
+__global__ void tv_rhs_kernel(const float2* __restrict__ b0, const float2* __restrict__ x, const float2* __restrict__ z,
+                              TvDims t, float inv_tau, float2* __restrict__ rhs, float2* __restrict__ xp) {
+    const int rows = t.n[0] * t.n[1];
+    const int64_t sy = t.n[2], sz = (int64_t)t.n[1] * t.n[2];
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int iz = row / t.n[1], iy = row - iz * t.n[1];
+        const int64_t base = (int64_t)row * t.n[2];
+        // offsets of the -1 neighbour along z and y (periodic)
+        const int64_t dz = (iz > 0) ? -sz : (int64_t)(t.n[0] - 1) * sz;
+        const int64_t dy = (iy > 0) ? -sy : (int64_t)(t.n[1] - 1) * sy;
+        for (int ix = threadIdx.x; ix < t.n[2]; ix += blockDim.x) {
+            const int64_t i = base + ix;
+            const int64_t nx1 = (ix > 0) ? i - 1 : base + t.n[2] - 1;
+            float2 div = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a < 3 - t.nd) continue;
+                const int c = a - (3 - t.nd);
+                const float2 zp = z[c * t.D + (a == 0 ? i + dz : (a == 1 ? i + dy : nx1))], zc = z[c * t.D + i];
+                div.x += zp.x - zc.x;
+                div.y += zp.y - zc.y;
+            }
+            const float2 xv = x[i];
+            const float2 bv = b0 ? b0[i] : make_float2(0.f, 0.f);
+            rhs[i] = make_float2(fmaf(inv_tau, xv.x, bv.x) - div.x, fmaf(inv_tau, xv.y, bv.y) - div.y);
+            if (xp) xp[i] = xv;
+        }
+    }
+}
+
+static int tv_grid(const TvDims& t) { return (int)std::min<int64_t>((int64_t)t.n[0] * t.n[1], 152 * 16); }
+
+static TvDims tv_dims(int nd, const int dims3[3]) {
+    TvDims t;
+    t.nd = nd;
+    for (int a = 0; a < 3; ++a) t.n[a] = dims3[a];
+    t.D = (int64_t)dims3[0] * dims3[1] * dims3[2];
+    return t;
+}
+
 static int vec_grid(int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + kRedThreads - 1) / kRedThreads, kRedBlocks));
 }
@@ -506,6 +604,8 @@ struct SolverWS {
     float* skd = nullptr;
     float* theta = nullptr;
     int* tdev = nullptr;
+    float2* tvz = nullptr;   // l1-TV dual variable [ndim][image] (PDHG), allocated on first use
+    int64_t tvz_n = 0;
     std::vector<void*> allocs;
     cudaGraphExec_t gexec = nullptr;
     uint64_t gsig = 0;
@@ -516,6 +616,17 @@ struct SolverWS {
         gsig = 0;
         for (void* q : allocs) cudaFree(q);
         allocs.clear();
+        tvz = nullptr;
+        tvz_n = 0;
+    }
+    cs_status ensure_tv(int64_t n) {
+        if (tvz && tvz_n >= n) return CS_OK;
+        if (gexec) cudaGraphExecDestroy(gexec);   // a cached graph may refer to the old buffer
+        gexec = nullptr;
+        gsig = 0;
+        CS_PROPAGATE(get(&tvz, (size_t)n));
+        tvz_n = n;
+        return CS_OK;
     }
     ~SolverWS() {
         free_all();
@@ -668,6 +779,53 @@ static cs_status fista_sub(const Ctx& c, const float2* d, float2* x, int K, cons
     return CS_OK;
 }
 
+// K PDHG iterations (Chambolle & Pock 2011, theta = 1) on min_x f(x) + lambda ||T x||_1 with the
+// data step prox_{tau f}(v) solved by M CG iterations on (A^H A + I/tau) u = b0 + v/tau started at
+// the current iterate (A: the sketched or the full model given by the maps).  For the sketched
+// sub-problem f(x) = 1/2 ||A_S (x - x^t)||^2 + Re<x, d> and b0 = A_S^H A_S x^t - d (formed here
+// when d is given); for the plain problem b0 = A^H y is passed in.  zd is the dual variable,
+// carried in and out.  Buffers: b0, xp (previous iterate), rhs, and the CG vectors r, pv, hp.
+struct PdhgArgs {
+    int K, M;
+    float tau, sigma, lam_tv;
+    float2 *zd, *b0, *xp, *rhs, *r, *pv, *hp;
+};
+
+static cs_status pdhg_sub(const Ctx& c, const float2* d, float2* x, const float2* mv, int V, const float2* ms, int S,
+                          const PdhgArgs& P) {
+    const TvDims t = tv_dims(c.nd, c.dims3);
+    if (d) {
+        CS_PROPAGATE(normal_apply(c, x, mv, V, ms, S, 0.f, P.hp));
+        sub_kernel<<<vec_grid(c.D), kRedThreads, 0, c.st>>>(P.hp, d, c.D, P.b0);
+        CS_LAUNCH_CHECK();
+    }
+    // xbar_0 = x: the dual step of the first iteration reads 2 x - x_prev with x_prev = x
+    CS_TRY_CUDA(cudaMemcpyAsync(P.xp, x, sizeof(float2) * c.D, cudaMemcpyDeviceToDevice, c.st));
+    Ctx cc = c;
+    cc.lambda = 1.0f / P.tau;
+    for (int k = 0; k < P.K; ++k) {
+        tv_dual_kernel<<<tv_grid(t), 128, 0, c.st>>>(x, P.xp, P.zd, t, P.sigma, P.lam_tv);
+        CS_LAUNCH_CHECK();
+        tv_rhs_kernel<<<tv_grid(t), 128, 0, c.st>>>(P.b0, x, P.zd, t, cc.lambda, P.rhs, P.xp);
+        CS_LAUNCH_CHECK();
+        // CG from the current iterate: r = rhs - (A^H A + I/tau) x
+        CS_PROPAGATE(normal_apply(cc, x, mv, V, ms, S, cc.lambda, P.hp));
+        cg_init2_kernel<<<kRedBlocks, kRedThreads, 0, c.st>>>(P.rhs, P.hp, c.D, P.r, P.pv, c.partB);
+        CS_LAUNCH_CHECK();
+        store_sum_kernel<<<1, 32, 0, c.st>>>(c.partB, &c.sc->rr[0]);
+        CS_LAUNCH_CHECK();
+        for (int m = 0; m < P.M; ++m) CS_PROPAGATE(cg_iter(cc, mv, V, ms, S, x, P.r, P.pv, P.hp, m & 1, nullptr));
+    }
+    return CS_OK;
+}
+
+static void pdhg_default_steps(int nd, float* tau, float* sigma) {
+    // tau = sigma = 0.99 / ||T||, ||T||^2 = 4 ndim, so that tau sigma ||T||^2 < 1
+    const float s = (float)(0.99 / std::sqrt(4.0 * nd));
+    if (!(*tau > 0)) *tau = s;
+    if (!(*sigma > 0)) *sigma = s;
+}
+
 static std::vector<float> fista_thetas(int K) {
     std::vector<float> th(K);
     double t = 1.0;
@@ -786,6 +944,26 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
     if (ev) CS_TRY_CUDA(cudaEventRecord(ev->e1, st));
 
     const bool fista = pr->reg == CS_REG_L1_WAVELET;
+    const bool tvreg = pr->reg == CS_REG_L1_TV;
+    PdhgArgs pd = {};
+    if (tvreg) {
+        CS_REQUIRE(K >= 1 && sp->cg_iters >= 0, CS_ERR_INVALID_ARG, "l1-TV needs K >= 1 and cg_iters >= 0");
+        CS_PROPAGATE(ws->ensure_tv((int64_t)c.nd * D));
+        CS_TRY_CUDA(cudaMemsetAsync(ws->tvz, 0, sizeof(float2) * c.nd * D, st));
+        pd.K = K;
+        pd.M = sp->cg_iters > 0 ? sp->cg_iters : 5;
+        pd.tau = sp->tv_tau;
+        pd.sigma = sp->tv_sigma;
+        pdhg_default_steps(c.nd, &pd.tau, &pd.sigma);
+        pd.lam_tv = pr->lambda;
+        pd.zd = ws->tvz;
+        pd.b0 = ws->u;
+        pd.xp = ws->xp;
+        pd.rhs = ws->gr;
+        pd.r = ws->r;
+        pd.pv = ws->pv;
+        pd.hp = ws->hp;
+    }
     const std::vector<float> theta = fista_thetas(std::max(K, 1));
     const bool use_graph = sp->use_graph != 0 && allow_graph;
     int graph_used = 0;
@@ -797,6 +975,12 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
     sig = fnv(sig, ints, sizeof(ints));
     sig = fnv(sig, &pr->lambda, sizeof(float));
     sig = fnv(sig, &sp->step, sizeof(float));
+    if (tvreg) {
+        const int tvi[] = {pd.M};
+        const float tvf[] = {pd.tau, pd.sigma};
+        sig = fnv(sig, tvi, sizeof(tvi));
+        sig = fnv(sig, tvf, sizeof(tvf));
+    }
     sig = fnv(sig, &sp->seed, sizeof(uint64_t));
     const int g = vec_grid(D);
     float2* iters = (float2*)sp->iterates;
@@ -823,6 +1007,7 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
             // sketched model: V virtual coils in place + S random combinations of the rest
             if (S > 0) CS_PROPAGATE(sketched_maps_impl(sk, ws->tdev, maps, D, C, V, S, sp->precision, msk, s));
             if (fista) CS_PROPAGATE(fista_sub(cc, ws->d, x, K, maps, V, msk, S, theta, ws->z, ws->xp, ws->u, ws->gr, ws->xt));
+            else if (tvreg) CS_PROPAGATE(pdhg_sub(cc, ws->d, x, maps, V, msk, S, pd));
             else CS_PROPAGATE(cg_sub(cc, ws->d, x, K, maps, V, msk, S, ws->r, ws->pv, ws->hp));
             if (iters) {
                 copy_iter_kernel<<<g, kRedThreads, 0, s>>>(x, iters, ws->tdev, 0, D);
@@ -833,6 +1018,37 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
             return CS_OK;
         };
         CS_PROPAGATE(run_body(ws, use_graph, sig, T, st, body, &graph_used));
+    } else if (tvreg) {
+        // plain full-coil l1-TV: K PDHG iterations in total, each with M CG iterations on the
+        // full normal operator; b0 = A^H y
+        CS_PROPAGATE((cs_status)sense_adj(p, (const float*)y, (const float*)maps, C, (float*)ws->d, 0, st));
+        pd.b0 = ws->d;
+        pd.K = 1;
+        CS_TRY_CUDA(cudaMemcpyAsync(ws->xp, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
+        const TvDims tvd = tv_dims(c.nd, c.dims3);
+        auto body = [&](cudaStream_t s) -> cs_status {
+            Ctx cc = c;
+            cc.st = s;
+            cc.lambda = 1.0f / pd.tau;
+            tv_dual_kernel<<<tv_grid(tvd), 128, 0, s>>>(x, ws->xp, pd.zd, tvd, pd.sigma, pd.lam_tv);
+            CS_LAUNCH_CHECK();
+            tv_rhs_kernel<<<tv_grid(tvd), 128, 0, s>>>(pd.b0, x, pd.zd, tvd, cc.lambda, pd.rhs, ws->xp);
+            CS_LAUNCH_CHECK();
+            CS_PROPAGATE(normal_apply(cc, x, maps, C, nullptr, 0, cc.lambda, ws->hp));
+            cg_init2_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(pd.rhs, ws->hp, D, ws->r, ws->pv, c.partB);
+            CS_LAUNCH_CHECK();
+            store_sum_kernel<<<1, 32, 0, s>>>(c.partB, &c.sc->rr[0]);
+            CS_LAUNCH_CHECK();
+            for (int m = 0; m < pd.M; ++m) CS_PROPAGATE(cg_iter(cc, maps, C, nullptr, 0, x, ws->r, ws->pv, ws->hp, m & 1, nullptr));
+            if (iters) {
+                copy_iter_kernel<<<g, kRedThreads, 0, s>>>(x, iters, ws->tdev, 0, D);
+                CS_LAUNCH_CHECK();
+            }
+            inc_kernel<<<1, 32, 0, s>>>(ws->tdev);
+            CS_LAUNCH_CHECK();
+            return CS_OK;
+        };
+        CS_PROPAGATE(run_body(ws, use_graph, sig, K, st, body, &graph_used));
     } else if (fista) {
         // plain full-coil FISTA: K iterations in total
         if (!(sp->step > 0)) {
@@ -1048,8 +1264,11 @@ cs_status recon_solve(const cs_plan* p, const cs_problem* pr, const cs_solve_par
     CS_REQUIRE(pr->y && pr->maps && pr->C >= 1 && pr->C <= p->max_coils, CS_ERR_INVALID_ARG,
                "problem needs y, maps and 1 <= C <= max_coils");
     CS_REQUIRE(std::isfinite(pr->lambda) && pr->lambda >= 0, CS_ERR_INVALID_ARG, "lambda must be finite and >= 0");
-    CS_REQUIRE(pr->reg == CS_REG_L2 || pr->reg == CS_REG_L1_WAVELET, CS_ERR_INVALID_ARG, "bad regulariser");
-    CS_REQUIRE(sp->K >= 0 && sp->T >= 0, CS_ERR_INVALID_ARG, "negative iteration count");
+    CS_REQUIRE(pr->reg == CS_REG_L2 || pr->reg == CS_REG_L1_WAVELET || pr->reg == CS_REG_L1_TV, CS_ERR_INVALID_ARG,
+               "bad regulariser");
+    CS_REQUIRE(sp->K >= 0 && sp->T >= 0 && sp->cg_iters >= 0, CS_ERR_INVALID_ARG, "negative iteration count");
+    CS_REQUIRE(std::isfinite(sp->tv_tau) && sp->tv_tau >= 0 && std::isfinite(sp->tv_sigma) && sp->tv_sigma >= 0,
+               CS_ERR_INVALID_ARG, "PDHG steps must be finite and >= 0 (0 = default)");
     if (sp->sketch) {
         CS_REQUIRE(sp->V >= 0 && sp->S >= 0 && sp->V + sp->S <= pr->C && sp->V + sp->S >= 1, CS_ERR_INVALID_ARG,
                    "need 1 <= V + S <= C (V=%d S=%d C=%d)", sp->V, sp->S, pr->C);
@@ -1235,6 +1454,46 @@ cs_status soft_threshold(float* z, int64_t n, float tau, void* stream) {
     CS_REQUIRE(z && n >= 0 && tau >= 0, CS_ERR_INVALID_ARG, "bad soft_threshold arguments");
     if (n == 0) return CS_OK;
     soft_kernel<<<vec_grid(n), kRedThreads, 0, (cudaStream_t)stream>>>((float2*)z, n, 0.f, nullptr, tau);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+static cs_status tv_check(int ndim, const int* dims, TvDims* t) {
+    CS_REQUIRE((ndim == 2 || ndim == 3) && dims, CS_ERR_INVALID_ARG, "TV needs ndim 2 or 3 and dims");
+    int d3[3] = {1, 1, 1};
+    for (int a = 0; a < ndim; ++a) {
+        CS_REQUIRE(dims[a] >= 1, CS_ERR_INVALID_ARG, "TV dims must be positive");
+        d3[3 - ndim + a] = dims[a];
+    }
+    *t = tv_dims(ndim, d3);
+    CS_REQUIRE(t->D < ((int64_t)1 << 31), CS_ERR_UNSUPPORTED_SIZE, "TV image above 2^31 voxels");
+    return CS_OK;
+}
+
+cs_status tv_dual_update(const float* x, const float* x_prev, float* z, int ndim, const int* dims, float sigma,
+                         float lambda, void* stream) {
+    clear_error();
+    CS_REQUIRE(x && z, CS_ERR_INVALID_ARG, "null argument");
+    CS_REQUIRE(std::isfinite(sigma) && std::isfinite(lambda) && lambda >= 0, CS_ERR_INVALID_ARG, "bad sigma/lambda");
+    TvDims t;
+    CS_PROPAGATE(tv_check(ndim, dims, &t));
+    if (t.D == 0) return CS_OK;
+    tv_dual_kernel<<<tv_grid(t), 128, 0, (cudaStream_t)stream>>>((const float2*)x, (const float2*)x_prev, (float2*)z, t,
+                                                                   sigma, lambda);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status tv_rhs(const float* b0, const float* x, const float* z, int ndim, const int* dims, float inv_tau, float* rhs,
+                 float* x_prev_out, void* stream) {
+    clear_error();
+    CS_REQUIRE(x && z && rhs, CS_ERR_INVALID_ARG, "null argument");
+    CS_REQUIRE(std::isfinite(inv_tau), CS_ERR_INVALID_ARG, "bad 1/tau");
+    TvDims t;
+    CS_PROPAGATE(tv_check(ndim, dims, &t));
+    if (t.D == 0) return CS_OK;
+    tv_rhs_kernel<<<tv_grid(t), 128, 0, (cudaStream_t)stream>>>((const float2*)b0, (const float2*)x, (const float2*)z, t,
+                                                                  inv_tau, (float2*)rhs, (float2*)x_prev_out);
     CS_LAUNCH_CHECK();
     return CS_OK;
 }

@@ -6,6 +6,10 @@ stream), for profiling individual kernels with small launch counts.
   python -m paper_2305_06482_gb300.microbench normal [--config cones3d_128|cones3d_large] [--warmup W] [--iters N]
       sketched normal operator A_S^H A_S v + lambda v with V = 5 unsketched and S = 5 sketched coils
       (the inner-iteration operator of the sketched sub-problem), with the per-stage device times
+  python -m paper_2305_06482_gb300.microbench tv [--config cones3d_128|cones3d_large] [--iters N]
+      l1-TV by PDHG (data step: 5 CG iterations) on the cones workload, lambda 0.01: one coil-
+      sketched reconstruction (m = 4 = 3 PCA + 1 Rademacher, T = 3 outer x K = 10 PDHG) and 10
+      PDHG iterations of the plain full-coil solver, with the time per PDHG iteration of each
   python -m paper_2305_06482_gb300.microbench sketch [--voxels D] [--iters N]
       sketched maps (40 coils, V = 5, S = 5): FP32 CUDA cores vs BF16 split on the tensor cores
   python -m paper_2305_06482_gb300.microbench batched [--slices 64] [--iters N]
@@ -110,6 +114,37 @@ def normal(args):
     print(f"{args.config}: sketched normal apply (V={V}, S={S}): {ms_:.3f} ms; per stage: {parts}")
 
 
+def tv(args):
+    cfg = CONFIGS[args.config]
+    dev = torch.device("cuda")
+    img, grid, C = cfg["img"], cfg["grid"], cfg["nc"]
+    traj = synthdata.cones_trajectory(cfg["n_int"], 512)
+    dcf = synthdata.cones_dcf(traj, img, cfg["n_int"], 512)
+    plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=torch.from_numpy(traj).to(dev), dcf=torch.from_numpy(dcf).to(dev),
+                   grid=grid)
+    maps = synthdata.coil_maps_torch(img, C, device=dev)
+    y = cs.sense_fwd(plan, synthdata.phantom_torch(img, seed=1, device=dev), maps)
+    lam, T, K, M = 1e-2, 3, 10, 5
+    sk = cs.SolveParams(T=T, K=K, V=3, S=1, dist=cs.RADEMACHER, cg_iters=M, seed=4)
+    pl = cs.SolveParams(K=K, sketch=False, do_pca=False, cg_iters=M)
+    res = {}
+    for name, prm in (("sketched", sk), ("plain", pl)):
+        cs.recon_solve(plan, y, maps, lam, cs.REG_L1_TV, prm)            # warm-up
+        torch.cuda.synchronize()
+        a, b = _events()
+        a.record()
+        for _ in range(args.iters):
+            cs.recon_solve(plan, y, maps, lam, cs.REG_L1_TV, prm)
+        b.record()
+        torch.cuda.synchronize()
+        res[name] = a.elapsed_time(b) / args.iters
+    print(f"{args.config}: l1-TV PDHG, lambda {lam}, {M} CG iterations per data step")
+    print(f"  sketched recon (m=4, T={T}, K={K}): {res['sketched']:.1f} ms = "
+          f"{res['sketched'] / (T * K):.2f} ms per PDHG iteration (incl. PCA, sketches, true gradients)")
+    print(f"  plain full-coil ({C} coils), {K} PDHG iterations: {res['plain']:.1f} ms = "
+          f"{res['plain'] / K:.2f} ms per PDHG iteration")
+
+
 def sketch(args):
     dev = torch.device("cuda")
     C, V, S, D = 40, 5, 5, args.voxels
@@ -198,14 +233,14 @@ def batched(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["nufft", "normal", "sketch", "cart2d", "batched"])
+    ap.add_argument("what", choices=["nufft", "normal", "tv", "sketch", "cart2d", "batched"])
     ap.add_argument("--slices", type=int, default=64)
     ap.add_argument("--config", default="cones3d_128", choices=list(CONFIGS))
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--iters", type=int, default=5)
     ap.add_argument("--voxels", type=int, default=160 * 256 * 256)
     args = ap.parse_args()
-    {"nufft": nufft, "normal": normal, "sketch": sketch, "cart2d": cart2d, "batched": batched}[args.what](args)
+    {"nufft": nufft, "normal": normal, "tv": tv, "sketch": sketch, "cart2d": cart2d, "batched": batched}[args.what](args)
 
 
 if __name__ == "__main__":
