@@ -155,8 +155,8 @@ def plain_fista(fwd, adj, y, lam, eta, x0, iters, levels=4):
 
 def coil_sketching(op_factory, maps, y, lam, reg, sketches, V, K, x0=None, eta=None,
                    power_v0=None, power_iters=20, do_pca=True, levels=4, callback=None,
-                   cg_iters=5, tau=None, sigma=None):
-    """Algorithm 1 (no classical-sketch initialisation).
+                   cg_iters=5, tau=None, sigma=None, init_sketch=None):
+    """Algorithm 1, optionally with its classical-sketch initialisation.
 
     op_factory(maps) -> (fwd, adj) builds A for a set of maps (Cartesian or NUFFT).
     sketches: float [T, S, C-V] random blocks S~_S^t (given as inputs).
@@ -165,7 +165,13 @@ def coil_sketching(op_factory, maps, y, lam, reg, sketches, V, K, x0=None, eta=N
     started at power_v0, and reused for every sub-problem) or 'l1tv' (PDHG, K iterations with
     ``cg_iters`` CG iterations in each data step, steps tau/sigma (default ``pdhg_steps``); the
     dual variable starts at zero and is carried from one sub-problem to the next).
-    Returns x^T and the list of iterates.
+    init_sketch: optional random block S~_S^0 [S, C-V] of the initialisation, which solves
+    argmin_x 1/2 ||S^0 A x - S^0 y||^2 + g(x) from x^0 with the sub-problem's solver and K
+    iterations.  That problem is the sketched sub-problem at x^t = x^0 with the sketched
+    gradient d = (S^0 A)^H (S^0 A x^0 - S^0 y) in place of the true one (its objective differs
+    from the sub-problem's by a constant), so the same solver routine runs it.  The FISTA step
+    1/L comes from the first model built (the initialisation's when there is one).
+    Returns x^T and the list of iterates (the initialisation's result not included).
     """
     if do_pca:
         U, _ = coils.coil_pca(y)
@@ -181,11 +187,16 @@ def coil_sketching(op_factory, maps, y, lam, reg, sketches, V, K, x0=None, eta=N
         tau = t0 if tau is None else tau
         sigma = s0 if sigma is None else sigma
         zdual = np.zeros((x.ndim,) + x.shape, dtype=np.complex128)
-    for t in range(sketches.shape[0]):
-        d = adj(fwd(x) - y_r)                                   # true gradient
-        msk = coils.sketched_maps(sketches[t], maps_r, V)       # sketched model A_S^t
+    steps = [("init", init_sketch)] if init_sketch is not None else []
+    steps += [("outer", sketches[t]) for t in range(sketches.shape[0])]
+    for kind, S_t in steps:
+        msk = coils.sketched_maps(S_t, maps_r, V)               # sketched model A_S^t
         fs, ads = op_factory(msk)
         normal_S = lambda v: ads(fs(v))
+        if kind == "init":
+            d = ads(fs(x) - coils.sketch_data(S_t, y_r, V))     # sketched gradient at x^0
+        else:
+            d = adj(fwd(x) - y_r)                               # true gradient
         if reg == "l2":
             x = sketched_cg(normal_S, d, x, lam, K)
         elif reg == "l1tv":
@@ -195,7 +206,8 @@ def coil_sketching(op_factory, maps, y, lam, reg, sketches, V, K, x0=None, eta=N
                 L = power_iteration(normal_S, power_v0, power_iters)
                 eta = 1.0 / L
             x = sketched_fista(normal_S, d, x, lam, eta, K, levels)
-        iterates.append(x.copy())
-        if callback is not None:
-            callback(t, x)
+        if kind == "outer":
+            iterates.append(x.copy())
+            if callback is not None:
+                callback(len(iterates) - 1, x)
     return x, iterates

@@ -111,3 +111,33 @@ def test_coil_sketching_converges_to_the_full_solution():
                            callback=lambda t, x: errs.append(solvers.nrmse(x, xs)))
     assert errs[-1] < 1e-10 and errs[-1] < errs[0] * 1e-6, errs
     assert all(b < a for a, b in zip(errs[:8], errs[1:9]))
+
+
+def test_classical_sketch_initialisation_with_identity_sketch_is_the_plain_solver():
+    """Algorithm 1's initialisation solves 1/2 ||S^0 A x - S^0 y||^2 + g(x); with the identity
+    sketch (V = C) that is the full problem, so with CG it must equal K plain CG iterations from
+    x^0, and the outer loop then continues from that point."""
+    import synthdata
+    from oracle import fourier
+    shape, C, K, lam = (16, 16), 4, 6, 1e-2
+    mask = synthdata.poisson_disc_mask(shape, R=2.0, centre=6, seed=2)
+    idx = fourier.mask_indices(mask)
+    maps = synthdata.coil_maps(shape, C)
+    y = fourier.cartesian_fwd(synthdata.phantom(shape, seed=1), maps, idx)
+    ops = lambda m: (lambda v: fourier.cartesian_fwd(v, m, idx), lambda r: fourier.cartesian_adj(r, m, idx))
+    fwd, adj = ops(maps)
+    x0 = synthdata.random_complex(shape, 3) * 0.1
+    x_plain = solvers.plain_cg(fwd, adj, y, lam, x0, K)
+    empty = np.zeros((0, 0))
+    x_init_only, its = solvers.coil_sketching(ops, maps, y, lam, "l2", np.zeros((0, 0, 0)), C, K, x0=x0,
+                                              do_pca=False, init_sketch=empty)
+    assert its == [] and solvers.nrmse(x_init_only, x_plain) < 1e-10
+    # the initialisation uses the sketched data S^0 y: a random-block sketch changes the result
+    rng = np.random.default_rng(0)
+    blk = rng.standard_normal((2, C - 2))
+    x_sk, _ = solvers.coil_sketching(ops, maps, y, lam, "l2", np.zeros((0, 2, C - 2)), 2, K, x0=x0,
+                                     do_pca=False, init_sketch=blk)
+    fs, ads = ops(coils.sketched_maps(blk, maps, 2))
+    ys = coils.sketch_data(blk, y, 2)
+    x_direct = solvers.cg(lambda v: ads(fs(v)) + lam * v, ads(ys), x0, K)
+    assert solvers.nrmse(x_sk, x_direct) < 1e-10
