@@ -258,6 +258,12 @@ typedef struct {
     int cg_iters;            /* CS_REG_L1_TV: CG iterations per PDHG data step (0 = 5)         */
     float tv_tau, tv_sigma;  /* CS_REG_L1_TV: PDHG primal/dual steps; 0 = 0.99 / sqrt(4 ndim)
                                 each (tau sigma ||T||^2 < 1 with ||T||^2 = 4 ndim)            */
+    int init;                /* 1 = Algorithm 1's classical-sketch initialisation before the T
+                                outer iterations: x <- argmin 1/2 ||S^0 A x - S^0 y||^2 + g(x),
+                                K iterations of the sub-problem solver from x^0 (the sketched
+                                gradient in place of the true one); S^0 is sketch block T, so
+                                a caller-given `sketches` array then holds T + 1 blocks; the
+                                FISTA step comes from S^0's model.  Ignored without sketch.   */
 } cs_solve_params;
 
 typedef struct {

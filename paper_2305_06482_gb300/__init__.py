@@ -54,7 +54,7 @@ class _Params(ctypes.Structure):
                 ("sketches", ctypes.c_void_p), ("do_pca", ctypes.c_int), ("precision", ctypes.c_int),
                 ("step", ctypes.c_float), ("power_iters", ctypes.c_int), ("power_v0", ctypes.c_void_p),
                 ("use_graph", ctypes.c_int), ("iterates", ctypes.c_void_p), ("cg_iters", ctypes.c_int),
-                ("tv_tau", ctypes.c_float), ("tv_sigma", ctypes.c_float)]
+                ("tv_tau", ctypes.c_float), ("tv_sigma", ctypes.c_float), ("init", ctypes.c_int)]
 
 
 class _BatchItem(ctypes.Structure):
@@ -412,6 +412,7 @@ class SolveParams:
     cg_iters: int = 0          # l1-TV: CG iterations per PDHG data step (0 = 5)
     tv_tau: float = 0.0        # l1-TV: PDHG steps (0 = 0.99 / sqrt(4 ndim))
     tv_sigma: float = 0.0
+    init: bool = False         # classical-sketch initialisation (sketch block T; sketches hold T + 1)
 
 
 def recon_solve(plan: Plan, y, maps, lam, reg=REG_L2, params: SolveParams = None, x0=None, wavelet_levels=4,
@@ -439,7 +440,8 @@ def _params_struct(params: SolveParams):
                    power_v0=None if params.power_v0 is None else params.power_v0.data_ptr(),
                    use_graph=int(params.use_graph),
                    iterates=None if params.iterates is None else params.iterates.data_ptr(),
-                   cg_iters=int(params.cg_iters), tv_tau=float(params.tv_tau), tv_sigma=float(params.tv_sigma))
+                   cg_iters=int(params.cg_iters), tv_tau=float(params.tv_tau), tv_sigma=float(params.tv_sigma),
+                   init=int(params.init))
 
 
 def recon_solve_batched(items, lam, reg=REG_L2, params: SolveParams = None, wavelet_levels=4, stream=None):

@@ -237,6 +237,15 @@ __global__ void copy_iter_kernel(const float2* __restrict__ x, float2* __restric
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) o[i] = x[i];
 }
 
+__global__ void set_int_kernel(int* c, int v) {
+    if (threadIdx.x == 0) *c = v;
+}
+
+__global__ void add_inplace_kernel(float2* __restrict__ a, const float2* __restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = cadd(a[i], b[i]);
+}
+
 __global__ void inc_kernel(int* c) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *c += 1;
 }
@@ -606,6 +615,9 @@ struct SolverWS {
     int* tdev = nullptr;
     float2* tvz = nullptr;   // l1-TV dual variable [ndim][image] (PDHG), allocated on first use
     int64_t tvz_n = 0;
+    float2* ysk = nullptr;   // sketched k-space rows S~_S^0 y of the classical-sketch initialisation
+    int64_t ysk_n = 0;
+    int* tinit = nullptr;    // device index of the initialisation's sketch block
     std::vector<void*> allocs;
     cudaGraphExec_t gexec = nullptr;
     uint64_t gsig = 0;
@@ -618,6 +630,19 @@ struct SolverWS {
         allocs.clear();
         tvz = nullptr;
         tvz_n = 0;
+        ysk = nullptr;
+        ysk_n = 0;
+        tinit = nullptr;
+    }
+    cs_status ensure_init(int64_t n) {
+        if (ysk && ysk_n >= n && tinit) return CS_OK;
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        gsig = 0;
+        CS_PROPAGATE(get(&ysk, (size_t)std::max<int64_t>(n, 1)));
+        ysk_n = n;
+        if (!tinit) CS_PROPAGATE(get(&tinit, 1));
+        return CS_OK;
     }
     cs_status ensure_tv(int64_t n) {
         if (tvz && tvz_n >= n) return CS_OK;
@@ -904,9 +929,11 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
     const bool sketch = sp->sketch != 0;
     const int V = sketch ? sp->V : C, S = sketch ? sp->S : 0, Kc = C - V;
     const int T = sp->T, K = sp->K;
+    const int init = (sketch && sp->init) ? 1 : 0;   // classical-sketch initialisation (sketch block T)
     if (!p->solver_ws) p->solver_ws = new SolverWS();
     SolverWS* ws = static_cast<SolverWS*>(p->solver_ws);
-    CS_PROPAGATE(ws->ensure(D, N, C, S, Kc, T, K));
+    CS_PROPAGATE(ws->ensure(D, N, C, S, Kc, T + init, K));
+    if (init) CS_PROPAGATE(ws->ensure_init((int64_t)S * N));
     Ctx c;
     c.p = p;
     c.st = st;
@@ -971,7 +998,8 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
     uint64_t sig = 1469598103934665603ull;
     const void* ptrs[] = {p, x, pr->y, pr->maps, sp->sketches, sp->iterates, sp->power_v0};
     sig = fnv(sig, ptrs, sizeof(ptrs));
-    const int ints[] = {C, T, K, V, S, sp->dist, sp->norm, sp->do_pca, sp->precision, pr->reg, c.levels, (int)sketch};
+    const int ints[] = {C, T, K, V, S, sp->dist, sp->norm, sp->do_pca, sp->precision, pr->reg, c.levels, (int)sketch,
+                        init};
     sig = fnv(sig, ints, sizeof(ints));
     sig = fnv(sig, &pr->lambda, sizeof(float));
     sig = fnv(sig, &sp->step, sizeof(float));
@@ -988,16 +1016,44 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
     if (sketch) {
         const float* sk = sp->sketches;
         if (!sk && S > 0) {
-            CS_PROPAGATE(sketch_draw_impl(sp->seed, 0, T, C, V, S, sp->dist, sp->norm, ws->skd, st));
+            CS_PROPAGATE(sketch_draw_impl(sp->seed, 0, T + init, C, V, S, sp->dist, sp->norm, ws->skd, st));
             sk = ws->skd;
         }
         float2* msk = ws->msk;
-        if (fista && !(sp->step > 0) && T > 0) {
-            // FISTA step from the first sub-problem (reused by every sub-problem)
+        if (init) {
+            // S^0 A and S^0 y: block T of the sketch array, V rows in place + S combinations
+            set_int_kernel<<<1, 32, 0, st>>>(ws->tinit, T);
+            CS_LAUNCH_CHECK();
+            if (S > 0) {
+                CS_PROPAGATE(sketched_maps_impl(sk, ws->tinit, maps, D, C, V, S, sp->precision, msk, st));
+                CS_PROPAGATE(sketched_maps_impl(sk, ws->tinit, y, N, C, V, S, sp->precision, ws->ysk, st));
+            }
+        }
+        if (fista && !(sp->step > 0) && T + init > 0) {
+            // FISTA step from the first sketched model (the initialisation's when there is one),
+            // reused by every sub-problem
             CS_REQUIRE(sp->power_v0 != nullptr, CS_ERR_INVALID_ARG, "power_v0 is required when step == 0");
-            if (S > 0) CS_PROPAGATE(sketched_maps_impl(sk, ws->tdev, maps, D, C, V, S, sp->precision, msk, st));
+            if (S > 0 && !init) CS_PROPAGATE(sketched_maps_impl(sk, ws->tdev, maps, D, C, V, S, sp->precision, msk, st));
             CS_PROPAGATE(power_iteration(c, (const float2*)sp->power_v0, sp->power_iters > 0 ? sp->power_iters : 20,
                                          maps, V, msk, S, ws->u, ws->hp));
+        }
+        if (init) {
+            // argmin 1/2 ||S^0 A x - S^0 y||^2 + g(x) from x^0: the sub-problem at x^t = x^0 with
+            // the sketched gradient d = (S^0 A)^H (S^0 A x^0 - S^0 y)
+            if (V > 0) CS_PROPAGATE((cs_status)sense_grad(p, (const float*)x, (const float*)maps, V, (const float*)y,
+                                                          (float*)ws->d, st));
+            if (S > 0) {
+                float2* dst = (V > 0) ? ws->hp : ws->d;
+                CS_PROPAGATE((cs_status)sense_grad(p, (const float*)x, (const float*)msk, S, (const float*)ws->ysk,
+                                                   (float*)dst, st));
+                if (V > 0) {
+                    add_inplace_kernel<<<g, kRedThreads, 0, st>>>(ws->d, ws->hp, D);
+                    CS_LAUNCH_CHECK();
+                }
+            }
+            if (fista) CS_PROPAGATE(fista_sub(c, ws->d, x, K, maps, V, msk, S, theta, ws->z, ws->xp, ws->u, ws->gr, ws->xt));
+            else if (tvreg) CS_PROPAGATE(pdhg_sub(c, ws->d, x, maps, V, msk, S, pd));
+            else CS_PROPAGATE(cg_sub(c, ws->d, x, K, maps, V, msk, S, ws->r, ws->pv, ws->hp));
         }
         auto body = [&](cudaStream_t s) -> cs_status {
             Ctx cc = c;

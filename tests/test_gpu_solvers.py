@@ -195,3 +195,28 @@ def test_batched_slices_match_individual_solves(reg):
         for x, r, s in zip(xs, refs, sts):
             assert nrmse(h(x), r) < 1e-6
             assert s["graph_used"] == int(g)
+
+
+@pytest.mark.parametrize("reg", ["l2", "l1wav", "l1tv"])
+def test_coil_sketching_with_classical_sketch_initialisation(reg):
+    """Algorithm 1 with its classical-sketch initialisation (sketch block T) against the oracle,
+    for the CG, FISTA (step from the initialisation's model) and PDHG sub-problem solvers."""
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    shape = (64, 64)
+    idx, maps, y, ops = _cart_problem(shape, C=8)
+    C, V, S, T, K, M = 8, 4, 2, 3, 6, 4
+    lam = {"l2": 1e-2, "l1wav": 5e-3, "l1tv": 2e-3}[reg]
+    code = {"l2": cs.REG_L2, "l1wav": cs.REG_L1_WAVELET, "l1tv": cs.REG_L1_TV}[reg]
+    sk = philox.sketch_draw(9, 0, T + 1, C, V, S)
+    v0 = synthdata.random_complex(shape, 5)
+    x_ref, its = solvers.coil_sketching(ops, maps, y, lam, reg, sk[:T].astype(np.float64), V=V, K=K, power_v0=v0,
+                                        levels=3, cg_iters=M, init_sketch=sk[T].astype(np.float64))
+    plan = cs.Plan(cs.CARTESIAN, shape, C, mask_idx=t(idx, np.int32))
+    iters = torch.empty((T,) + shape, dtype=torch.complex64, device="cuda")
+    x, _ = cs.recon_solve(plan, t(y), t(maps), lam, code,
+                          cs.SolveParams(T=T, K=K, V=V, S=S, sketches=t(sk), power_v0=t(v0), cg_iters=M, init=True,
+                                         iterates=iters), wavelet_levels=3)
+    assert nrmse(h(x), x_ref) < 1e-4
+    for k in range(T):
+        assert nrmse(h(iters[k]), its[k]) < 1e-4
