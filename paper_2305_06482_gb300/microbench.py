@@ -10,6 +10,12 @@ stream), for profiling individual kernels with small launch counts.
       l1-TV by PDHG (data step: 5 CG iterations) on the cones workload, lambda 0.01: one coil-
       sketched reconstruction (m = 4 = 3 PCA + 1 Rademacher, T = 3 outer x K = 10 PDHG) and 10
       PDHG iterations of the plain full-coil solver, with the time per PDHG iteration of each
+  python -m paper_2305_06482_gb300.microbench ablation [--seeds R]
+      sketching-matrix design sweep on 2D radial data (256x256, 8 coils, 201 golden-angle spokes
+      x 256 = R 2 against 402 Nyquist spokes, noise 1e-3 max|y|, l1-db4 lambda 2e-3): for
+      C^ = 3 and 4, V = 0 .. C^, Gaussian (variance 1/S), Rademacher and the literal Gaussian
+      scaling (sigma = 1/S), R seeds each, coil sketching T = 10 x K = 10 FISTA; objective and
+      NRMSE to the phantom normalised by the full-coil solution's (mean and std over seeds)
   python -m paper_2305_06482_gb300.microbench sketch [--voxels D] [--iters N]
       sketched maps (40 coils, V = 5, S = 5): FP32 CUDA cores vs BF16 split on the tensor cores
   python -m paper_2305_06482_gb300.microbench batched [--slices 64] [--iters N]
@@ -145,6 +151,62 @@ def tv(args):
           f"{res['plain'] / K:.2f} ms per PDHG iteration")
 
 
+def ablation(args):
+    dev = torch.device("cuda")
+    img, grid, C, spokes, n_read, lam, levels = (256, 256), (320, 320), 8, 201, 256, 2e-3, 4
+    traj = synthdata.radial_trajectory(spokes, n_read)
+    dcf = synthdata.radial_dcf(traj, img, spokes, n_read)
+    plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=torch.from_numpy(traj).to(dev), dcf=torch.from_numpy(dcf).to(dev),
+                   grid=grid)
+    maps = torch.from_numpy(synthdata.coil_maps(img, C).astype(np.complex64)).to(dev)
+    x_true = torch.from_numpy(synthdata.phantom(img, seed=1).astype(np.complex64)).to(dev)
+    y = cs.sense_fwd(plan, x_true, maps)
+    noise = synthdata.complex_noise(tuple(y.shape), 1e-3 * float(y.abs().max()), seed=3)
+    y = y + torch.from_numpy(noise.astype(np.complex64)).to(dev)
+    v0 = torch.from_numpy(synthdata.random_complex(img, 5).astype(np.complex64)).to(dev)
+    yy = 0.5 * float(torch.sum(y.real.double() ** 2 + y.imag.double() ** 2))
+    d0 = cs.sense_adj(plan, y, maps)
+    d0 = -d0
+    zero = torch.zeros(img, dtype=torch.complex64, device=dev)
+
+    def objective(x):   # 1/2 ||A x - y||^2 + lambda ||Psi x||_1 (sub-problem objective at x^t = 0, d = -A^H y)
+        return cs.subproblem_objective(plan, x, zero, d0, maps, None, lam, cs.REG_L1_WAVELET, levels) + yy
+
+    def err(x):
+        return float(torch.linalg.vector_norm(x - x_true) / torch.linalg.vector_norm(x_true))
+
+    t0 = time.perf_counter()
+    x_base, _ = cs.recon_solve(plan, y, maps, lam, cs.REG_L1_WAVELET,
+                               cs.SolveParams(K=300, sketch=False, do_pca=False, power_v0=v0), wavelet_levels=levels)
+    f_base, e_base = objective(x_base), err(x_base)
+    print(f"2D radial 256^2, 8 coils, {spokes} spokes: full-coil FISTA (300 it) objective {f_base:.6g}, "
+          f"NRMSE to phantom {e_base:.4f}")
+    designs = [("gauss", cs.GAUSSIAN, cs.NORM_UNIT_VAR), ("rademacher", cs.RADEMACHER, cs.NORM_UNIT_VAR),
+               ("gauss-literal", cs.GAUSSIAN, cs.NORM_PAPER_LITERAL)]
+    print("C^  V  S  distribution     f/f_full mean  std       NRMSE/NRMSE_full mean  std")
+    for Ch in (3, 4):
+        for V in range(0, Ch + 1):
+            for name, dist, norm in designs:
+                if V == Ch and name != "gauss":
+                    continue                       # S = 0: no random block
+                fs, es = [], []
+                for seed in range(args.seeds):
+                    try:
+                        x, _ = cs.recon_solve(plan, y, maps, lam, cs.REG_L1_WAVELET,
+                                              cs.SolveParams(T=10, K=10, V=V, S=Ch - V, dist=dist, norm=norm,
+                                                             seed=1000 + seed, power_v0=v0), wavelet_levels=levels)
+                        f, e = objective(x), err(x)
+                    except cs.CoilSketchError:       # a diverged solve reports a non-finite reduction
+                        f, e = np.inf, np.inf
+                    fs.append(f / f_base if np.isfinite(f) else np.inf)
+                    es.append(e / e_base if np.isfinite(e) else np.inf)
+                fs, es = np.array(fs), np.array(es)
+                label = "(none)" if V == Ch else name
+                print(f"{Ch:2d} {V:2d} {Ch - V:2d}  {label:15s} {fs.mean():12.4g} {fs.std():9.3g}   "
+                      f"{es.mean():12.4g} {es.std():9.3g}")
+    print(f"sweep time {time.perf_counter() - t0:.1f} s")
+
+
 def sketch(args):
     dev = torch.device("cuda")
     C, V, S, D = 40, 5, 5, args.voxels
@@ -233,14 +295,15 @@ def batched(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["nufft", "normal", "tv", "sketch", "cart2d", "batched"])
+    ap.add_argument("what", choices=["nufft", "normal", "tv", "ablation", "sketch", "cart2d", "batched"])
+    ap.add_argument("--seeds", type=int, default=16)
     ap.add_argument("--slices", type=int, default=64)
     ap.add_argument("--config", default="cones3d_128", choices=list(CONFIGS))
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--iters", type=int, default=5)
     ap.add_argument("--voxels", type=int, default=160 * 256 * 256)
     args = ap.parse_args()
-    {"nufft": nufft, "normal": normal, "tv": tv, "sketch": sketch, "cart2d": cart2d, "batched": batched}[args.what](args)
+    {"nufft": nufft, "normal": normal, "tv": tv, "ablation": ablation, "sketch": sketch, "cart2d": cart2d, "batched": batched}[args.what](args)
 
 
 if __name__ == "__main__":
