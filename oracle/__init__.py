@@ -18,6 +18,7 @@ coils     Coil PCA (SVD-based coil compression, Sec. 3.1 and Alg. 1), structured
 philox    Philox4x32-10 counter-based generator and the sketch entry distributions (Sec. 3.2).
 wavelet   Periodised orthonormal Daubechies-4 (db4, 8 taps) multi-level DWT (Sec. 2.1, l1-wavelets).
 tv        Periodic first-order differences and the dual projection of l1-TV (Sec. 2.1).
+gfactor   Inverse g-factor by Monte Carlo pseudo-replicas and in closed form for SENSE (Sec. 3.2).
 solvers   CG, FISTA, PDHG, power iteration, the sketched sub-problem (Eq. 9-10) and Algorithm 1.
 
 Parity pins live in ``tests/test_oracle_*.py``: each function here is checked against

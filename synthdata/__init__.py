@@ -35,8 +35,9 @@ import math
 import numpy as np
 
 __all__ = [
-    "phantom", "phantom_torch", "coil_maps", "coil_maps_torch", "poisson_disc_mask", "line_mask", "cones_trajectory",
-    "cones_dcf", "complex_noise", "random_complex", "slice_sizes", "CONFIGS",
+    "phantom", "phantom_torch", "coil_maps", "coil_maps_torch", "poisson_disc_mask", "line_mask", "regular_mask",
+    "cones_trajectory", "cones_dcf", "radial_trajectory", "radial_dcf", "complex_noise", "random_complex",
+    "slice_sizes", "CONFIGS",
 ]
 
 
@@ -259,6 +260,15 @@ def cones_dcf(traj, img_shape, n_int, n_read=512):
     kmin = 0.5 * dk
     w = D * 4 * math.pi * np.maximum(kr, kmin) ** 2 * dk / n_int
     return w.astype(np.float32)
+
+
+def regular_mask(n, R=3, offset=0):
+    """Regular undersampling: every R-th phase-encode line (rows), readout fully sampled.
+    bool [ny, nx]."""
+    ny, nx = (int(n[0]), int(n[1])) if not isinstance(n, int) else (n, n)
+    m = np.zeros((ny, nx), dtype=bool)
+    m[offset::R, :] = True
+    return m
 
 
 def radial_trajectory(n_spokes, n_read=256):
