@@ -16,6 +16,11 @@ stream), for profiling individual kernels with small launch counts.
       C^ = 3 and 4, V = 0 .. C^, Gaussian (variance 1/S), Rademacher and the literal Gaussian
       scaling (sigma = 1/S), R seeds each, coil sketching T = 10 x K = 10 FISTA; objective and
       NRMSE to the phantom normalised by the full-coil solution's (mean and std over seeds)
+  python -m paper_2305_06482_gb300.microbench gfactor [--replicas 60]
+      inverse g-factor by pseudo-replicas: 256x256 Cartesian, 8 coils, every third line (R 3),
+      noise 1e-2 max|y|, l2 lambda 1e-3: the full-coil CG solver (30 iterations) on fully and
+      regularly undersampled data, and coil sketching (C^ 4 = 3 + 1 Rademacher, T 5 x K 10 CG)
+      on the undersampled data, each as one batched solve of all replicas in one CUDA graph
   python -m paper_2305_06482_gb300.microbench sketch [--voxels D] [--iters N]
       sketched maps (40 coils, V = 5, S = 5): FP32 CUDA cores vs BF16 split on the tensor cores
   python -m paper_2305_06482_gb300.microbench batched [--slices 64] [--iters N]
@@ -207,6 +212,41 @@ def ablation(args):
     print(f"sweep time {time.perf_counter() - t0:.1f} s")
 
 
+def gfactor(args):
+    from . import gfactor as gf
+    dev = torch.device("cuda")
+    shape, C, R, lam = (256, 256), 8, 3, 1e-3
+    idx = np.flatnonzero(synthdata.regular_mask(shape, R).ravel()).astype(np.int32)
+    full = np.arange(shape[0] * shape[1], dtype=np.int32)
+    maps = torch.from_numpy(synthdata.coil_maps(shape, C).astype(np.complex64)).to(dev)
+    x = torch.from_numpy(synthdata.phantom(shape, seed=1).astype(np.complex64)).to(dev)
+    res = {}
+    for name, ix, prm in (("full", full, cs.SolveParams(K=30, sketch=False, do_pca=False, use_graph=True)),
+                          ("R3", idx, cs.SolveParams(K=30, sketch=False, do_pca=False, use_graph=True)),
+                          ("R3 sketched", idx, cs.SolveParams(T=5, K=10, V=3, S=1, dist=cs.RADEMACHER, seed=4,
+                                                              use_graph=True))):
+        plan0 = cs.Plan(cs.CARTESIAN, shape, C, mask_idx=torch.from_numpy(ix).to(dev))
+        y = cs.sense_fwd(plan0, x, maps)
+        sig = 1e-2 * float(y.abs().max())
+        noise = torch.from_numpy(np.stack([synthdata.complex_noise(tuple(y.shape), sig, seed=1000 + k)
+                                           for k in range(args.replicas)]).astype(np.complex64)).to(dev)
+        ys = gf.replicas(y, noise)
+        xs, plans = gf.replica_reconstructions(shape, maps, torch.from_numpy(ix).to(dev), ys, lam, prm)   # capture
+        torch.cuda.synchronize()
+        a, b = _events()
+        a.record()
+        xs, _ = gf.replica_reconstructions(shape, maps, torch.from_numpy(ix).to(dev), ys, lam, prm, plans=plans)
+        b.record()
+        torch.cuda.synchronize()
+        res[name] = (xs, a.elapsed_time(b))
+        print(f"{name}: {args.replicas} replicas in one batched graph: {a.elapsed_time(b):.1f} ms")
+    inside = synthdata.phantom(shape, seed=1) != 0
+    for name in ("R3", "R3 sketched"):
+        ig = gf.inverse_gfactor(res[name][0], res["full"][0], R).cpu().numpy()
+        print(f"inverse g-factor ({name}) inside the object: mean {ig[inside].mean():.3f}, "
+              f"5th percentile {np.percentile(ig[inside], 5):.3f}")
+
+
 def sketch(args):
     dev = torch.device("cuda")
     C, V, S, D = 40, 5, 5, args.voxels
@@ -295,7 +335,8 @@ def batched(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["nufft", "normal", "tv", "ablation", "sketch", "cart2d", "batched"])
+    ap.add_argument("what", choices=["nufft", "normal", "tv", "ablation", "gfactor", "sketch", "cart2d", "batched"])
+    ap.add_argument("--replicas", type=int, default=60)
     ap.add_argument("--seeds", type=int, default=16)
     ap.add_argument("--slices", type=int, default=64)
     ap.add_argument("--config", default="cones3d_128", choices=list(CONFIGS))
@@ -303,7 +344,7 @@ def main():
     ap.add_argument("--iters", type=int, default=5)
     ap.add_argument("--voxels", type=int, default=160 * 256 * 256)
     args = ap.parse_args()
-    {"nufft": nufft, "normal": normal, "tv": tv, "ablation": ablation, "sketch": sketch, "cart2d": cart2d, "batched": batched}[args.what](args)
+    {"nufft": nufft, "normal": normal, "tv": tv, "ablation": ablation, "gfactor": gfactor, "sketch": sketch, "cart2d": cart2d, "batched": batched}[args.what](args)
 
 
 if __name__ == "__main__":
