@@ -151,6 +151,44 @@ def plain_fista(fwd, adj, y, lam, eta, x0, iters, levels=4):
 
 
 # ---------------------------------------------------------------------------------------
+# Comparators of Sec. 3.3: aggressive coil compression and AccProxSGD
+
+def coil_compressed(op_factory, maps, y, keep, solve):
+    """Coil PCA, keep the first ``keep`` virtual coils, then ``solve(fwd, adj, y_keep)``."""
+    U, _ = coils.coil_pca(y)
+    maps_r = coils.rotate(U, maps)[:keep]
+    y_r = coils.rotate(U, y)[:keep]
+    fwd, adj = op_factory(maps_r)
+    return solve(fwd, adj, y_r)
+
+
+def acc_prox_sgd(op_factory, maps, y, lam, batches, alpha0, beta, min_frac, x0, iters, levels=4):
+    """Accelerated proximal stochastic gradient over coils (Sec. 3.3; coil batches of size B):
+        g_k = (C/B) sum_{c in batch k} A_c^H (A_c z_k - y_c)          (unbiased for the full gradient)
+        alpha_k = max(beta^k alpha0, min_frac alpha0)                (the paper's decreasing rule)
+        x_{k+1} = prox_{alpha_k lam ||Psi .||_1}(z_k - alpha_k g_k)
+        z_{k+1} = x_{k+1} + ((t_k - 1)/t_{k+1}) (x_{k+1} - x_k)       (Nesterov / FISTA momentum)
+    batches: int [iters, B] coil indices (given as inputs)."""
+    C = maps.shape[0]
+    batches = np.asarray(batches)
+    B = batches.shape[1]
+    x_prev = np.array(x0, dtype=np.complex128, copy=True)
+    z = x_prev.copy()
+    t = 1.0
+    for k in range(iters):
+        idx = batches[k]
+        fwd, adj = op_factory(maps[idx])
+        g = (C / B) * adj(fwd(z) - y[idx])
+        alpha = max(beta ** k * alpha0, min_frac * alpha0)
+        x = wavelet.prox_l1_wavelet(z - alpha * g, alpha * lam, levels)
+        t_new = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
+        z = x + ((t - 1.0) / t_new) * (x - x_prev)
+        x_prev = x
+        t = t_new
+    return x_prev
+
+
+# ---------------------------------------------------------------------------------------
 # Algorithm 1
 
 def coil_sketching(op_factory, maps, y, lam, reg, sketches, V, K, x0=None, eta=None,

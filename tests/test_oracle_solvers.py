@@ -141,3 +141,51 @@ def test_classical_sketch_initialisation_with_identity_sketch_is_the_plain_solve
     ys = coils.sketch_data(blk, y, 2)
     x_direct = solvers.cg(lambda v: ads(fs(v)) + lam * v, ads(ys), x0, K)
     assert solvers.nrmse(x_sk, x_direct) < 1e-10
+
+
+def _tiny_cart(shape=(16, 16), C=4, seed=1):
+    mask = synthdata.poisson_disc_mask(shape, R=2.0, centre=6, seed=2)
+    idx = fourier.mask_indices(mask)
+    maps = synthdata.coil_maps(shape, C)
+    y = fourier.cartesian_fwd(synthdata.phantom(shape, seed=seed), maps, idx)
+    ops = lambda m: (lambda v: fourier.cartesian_fwd(v, m, idx), lambda r: fourier.cartesian_adj(r, m, idx))
+    return maps, y, ops
+
+
+def test_acc_prox_sgd_with_full_batches_is_fista():
+    maps, y, ops = _tiny_cart()
+    fwd, adj = ops(maps)
+    C, K, lam = 4, 12, 5e-3
+    L = solvers.power_iteration(lambda v: adj(fwd(v)), synthdata.random_complex((16, 16), 5), 30)
+    x0 = np.zeros((16, 16), complex)
+    full = np.tile(np.arange(C), (K, 1))
+    x_sgd = solvers.acc_prox_sgd(ops, maps, y, lam, full, 1 / L, 1.0, 0.1, x0, K, levels=2)
+    x_fista = solvers.plain_fista(fwd, adj, y, lam, 1 / L, x0, K, levels=2)
+    assert solvers.nrmse(x_sgd, x_fista) < 1e-12
+
+
+def test_coil_batch_gradient_is_unbiased():
+    from itertools import combinations
+    maps, y, ops = _tiny_cart(C=5)
+    fwd, adj = ops(maps)
+    z = synthdata.random_complex((16, 16), 6)
+    full = adj(fwd(z) - y)
+    B = 2
+    subsets = list(combinations(range(5), B))
+    mean = np.zeros_like(full)
+    for sb in subsets:
+        f, a = ops(maps[list(sb)])
+        mean += (5 / B) * a(f(z) - y[list(sb)])
+    mean /= len(subsets)
+    assert solvers.nrmse(mean, full) < 1e-12
+
+
+def test_coil_compression_keeping_every_coil_is_the_plain_solver():
+    maps, y, ops = _tiny_cart()
+    fwd, adj = ops(maps)
+    x0 = np.zeros((16, 16), complex)
+    ref = solvers.plain_cg(fwd, adj, y, 1e-2, x0, 10)
+    got = solvers.coil_compressed(ops, maps, y, 4, lambda f, a, yk: solvers.plain_cg(f, a, yk, 1e-2, x0, 10))
+    assert solvers.nrmse(got, ref) < 1e-10
+    fewer = solvers.coil_compressed(ops, maps, y, 2, lambda f, a, yk: solvers.plain_cg(f, a, yk, 1e-2, x0, 10))
+    assert solvers.nrmse(fewer, ref) > 1e-3          # dropping virtual coils changes the solution
