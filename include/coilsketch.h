@@ -264,6 +264,17 @@ typedef struct {
                                 gradient in place of the true one); S^0 is sketch block T, so
                                 a caller-given `sketches` array then holds T + 1 blocks; the
                                 FISTA step comes from S^0's model.  Ignored without sketch.   */
+    /* Comparators of the paper's Sec. 3.3 (plain solver, sketch = 0):                         */
+    int keep;                /* aggressive coil compression: solve with only the first `keep`
+                                (virtual, after do_pca) coils; 0 = all                         */
+    int sgd_batch;           /* > 0: AccProxSGD (l1-wavelets only) with coil batches of this size:
+                                K iterations x^{k+1} = prox(z - alpha_k (C'/B) sum_batch
+                                A_c^H (A_c z - y_c)), Nesterov (FISTA) momentum, alpha_k =
+                                max(sgd_beta^k, sgd_min) alpha_0, alpha_0 = 1/L of the C'-coil
+                                normal operator (power iteration, or 1/step), C' = coils used  */
+    const int* sgd_coils;    /* device int [K][sgd_batch]: the coil indices of every batch (in
+                                [0, C')), drawn by the caller; checked on the host              */
+    float sgd_beta, sgd_min; /* step decay and floor (fractions of alpha_0); 0 = 0.99 and 0.1    */
 } cs_solve_params;
 
 typedef struct {

@@ -54,7 +54,9 @@ class _Params(ctypes.Structure):
                 ("sketches", ctypes.c_void_p), ("do_pca", ctypes.c_int), ("precision", ctypes.c_int),
                 ("step", ctypes.c_float), ("power_iters", ctypes.c_int), ("power_v0", ctypes.c_void_p),
                 ("use_graph", ctypes.c_int), ("iterates", ctypes.c_void_p), ("cg_iters", ctypes.c_int),
-                ("tv_tau", ctypes.c_float), ("tv_sigma", ctypes.c_float), ("init", ctypes.c_int)]
+                ("tv_tau", ctypes.c_float), ("tv_sigma", ctypes.c_float), ("init", ctypes.c_int),
+                ("keep", ctypes.c_int), ("sgd_batch", ctypes.c_int), ("sgd_coils", ctypes.c_void_p),
+                ("sgd_beta", ctypes.c_float), ("sgd_min", ctypes.c_float)]
 
 
 class _BatchItem(ctypes.Structure):
@@ -413,6 +415,11 @@ class SolveParams:
     tv_tau: float = 0.0        # l1-TV: PDHG steps (0 = 0.99 / sqrt(4 ndim))
     tv_sigma: float = 0.0
     init: bool = False         # classical-sketch initialisation (sketch block T; sketches hold T + 1)
+    keep: int = 0              # plain solver on the first `keep` (virtual) coils (aggressive compression)
+    sgd_batch: int = 0         # > 0: AccProxSGD with coil batches of this size (l1-wavelets)
+    sgd_coils: Optional[torch.Tensor] = None   # int32 [K, sgd_batch] device coil indices
+    sgd_beta: float = 0.0      # step decay (0 = 0.99)
+    sgd_min: float = 0.0       # step floor as a fraction of alpha_0 (0 = 0.1)
 
 
 def recon_solve(plan: Plan, y, maps, lam, reg=REG_L2, params: SolveParams = None, x0=None, wavelet_levels=4,
@@ -441,7 +448,9 @@ def _params_struct(params: SolveParams):
                    use_graph=int(params.use_graph),
                    iterates=None if params.iterates is None else params.iterates.data_ptr(),
                    cg_iters=int(params.cg_iters), tv_tau=float(params.tv_tau), tv_sigma=float(params.tv_sigma),
-                   init=int(params.init))
+                   init=int(params.init), keep=int(params.keep), sgd_batch=int(params.sgd_batch),
+                   sgd_coils=None if params.sgd_coils is None else params.sgd_coils.data_ptr(),
+                   sgd_beta=float(params.sgd_beta), sgd_min=float(params.sgd_min))
 
 
 def recon_solve_batched(items, lam, reg=REG_L2, params: SolveParams = None, wavelet_levels=4, stream=None):

@@ -246,8 +246,40 @@ __global__ void add_inplace_kernel(float2* __restrict__ a, const float2* __restr
         a[i] = cadd(a[i], b[i]);
 }
 
+// AccProxSGD: rows of the coil batch of iteration *kdev: dst[j] = src[coils[k * B + j]], j < B
+__global__ void gather_coils_kernel(const float2* __restrict__ src, int64_t len, const int* __restrict__ coils, int B,
+                                    const int* __restrict__ kdev, float2* __restrict__ dst) {
+    const int k = *kdev;
+    for (int j = blockIdx.y; j < B; j += gridDim.y) {
+        const float2* s = src + (int64_t)coils[(int64_t)k * B + j] * len;
+        float2* d = dst + (int64_t)j * len;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+            d[i] = s[i];
+    }
+}
+
+// AccProxSGD step: alpha_k = max(beta^k alpha_0, min_frac alpha_0), alpha_0 = 1 / L (power iteration);
+// u = z - alpha_k ratio g (ratio = C / B makes the batch gradient unbiased); eta = alpha_k for the
+// proximal step that follows
+__global__ void sgd_step_kernel(const float2* __restrict__ z, const float2* __restrict__ g, Scal* sc,
+                                const int* __restrict__ kdev, double beta, double min_frac, float ratio, int64_t n,
+                                float2* __restrict__ u) {
+    const double a0 = 1.0 / sc->L;
+    const double alpha = fmax(pow(beta, (double)*kdev) * a0, min_frac * a0);
+    const float s = (float)alpha * ratio;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 zv = z[i], gv = g[i];
+        u[i] = make_float2(fmaf(-s, gv.x, zv.x), fmaf(-s, gv.y, zv.y));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->eta = alpha;
+}
+
 __global__ void inc_kernel(int* c) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *c += 1;
+}
+
+__global__ void set_L_kernel(Scal* sc, double L) {
+    if (threadIdx.x == 0) sc->L = L;
 }
 
 __global__ void set_eta_kernel(Scal* sc, double eta) {
@@ -618,6 +650,8 @@ struct SolverWS {
     float2* ysk = nullptr;   // sketched k-space rows S~_S^0 y of the classical-sketch initialisation
     int64_t ysk_n = 0;
     int* tinit = nullptr;    // device index of the initialisation's sketch block
+    float2 *bmaps = nullptr, *by = nullptr;   // AccProxSGD: the current coil batch's maps and data
+    int64_t bmaps_n = 0, by_n = 0;
     std::vector<void*> allocs;
     cudaGraphExec_t gexec = nullptr;
     uint64_t gsig = 0;
@@ -633,6 +667,19 @@ struct SolverWS {
         ysk = nullptr;
         ysk_n = 0;
         tinit = nullptr;
+        bmaps = by = nullptr;
+        bmaps_n = by_n = 0;
+    }
+    cs_status ensure_sgd(int64_t nm, int64_t ny) {
+        if (bmaps && bmaps_n >= nm && by && by_n >= ny) return CS_OK;
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        gsig = 0;
+        CS_PROPAGATE(get(&bmaps, (size_t)nm));
+        CS_PROPAGATE(get(&by, (size_t)ny));
+        bmaps_n = nm;
+        by_n = ny;
+        return CS_OK;
     }
     cs_status ensure_init(int64_t n) {
         if (ysk && ysk_n >= n && tinit) return CS_OK;
@@ -972,6 +1019,9 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
 
     const bool fista = pr->reg == CS_REG_L1_WAVELET;
     const bool tvreg = pr->reg == CS_REG_L1_TV;
+    // plain solvers: aggressive coil compression keeps the first `keep` (virtual) coils
+    const int Cp = (!sketch && sp->keep > 0) ? std::min(sp->keep, C) : C;
+    const bool sgd = !sketch && sp->sgd_batch > 0;
     PdhgArgs pd = {};
     if (tvreg) {
         CS_REQUIRE(K >= 1 && sp->cg_iters >= 0, CS_ERR_INVALID_ARG, "l1-TV needs K >= 1 and cg_iters >= 0");
@@ -999,8 +1049,12 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
     const void* ptrs[] = {p, x, pr->y, pr->maps, sp->sketches, sp->iterates, sp->power_v0};
     sig = fnv(sig, ptrs, sizeof(ptrs));
     const int ints[] = {C, T, K, V, S, sp->dist, sp->norm, sp->do_pca, sp->precision, pr->reg, c.levels, (int)sketch,
-                        init};
+                        init, Cp, sp->sgd_batch};
+    const void* ptrs2[] = {sp->sgd_coils};
+    const float sgdf[] = {sp->sgd_beta, sp->sgd_min};
     sig = fnv(sig, ints, sizeof(ints));
+    sig = fnv(sig, ptrs2, sizeof(ptrs2));
+    sig = fnv(sig, sgdf, sizeof(sgdf));
     sig = fnv(sig, &pr->lambda, sizeof(float));
     sig = fnv(sig, &sp->step, sizeof(float));
     if (tvreg) {
@@ -1077,7 +1131,7 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
     } else if (tvreg) {
         // plain full-coil l1-TV: K PDHG iterations in total, each with M CG iterations on the
         // full normal operator; b0 = A^H y
-        CS_PROPAGATE((cs_status)sense_adj(p, (const float*)y, (const float*)maps, C, (float*)ws->d, 0, st));
+        CS_PROPAGATE((cs_status)sense_adj(p, (const float*)y, (const float*)maps, Cp, (float*)ws->d, 0, st));
         pd.b0 = ws->d;
         pd.K = 1;
         CS_TRY_CUDA(cudaMemcpyAsync(ws->xp, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
@@ -1090,12 +1144,60 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
             CS_LAUNCH_CHECK();
             tv_rhs_kernel<<<tv_grid(tvd), 128, 0, s>>>(pd.b0, x, pd.zd, tvd, cc.lambda, pd.rhs, ws->xp);
             CS_LAUNCH_CHECK();
-            CS_PROPAGATE(normal_apply(cc, x, maps, C, nullptr, 0, cc.lambda, ws->hp));
+            CS_PROPAGATE(normal_apply(cc, x, maps, Cp, nullptr, 0, cc.lambda, ws->hp));
             cg_init2_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(pd.rhs, ws->hp, D, ws->r, ws->pv, c.partB);
             CS_LAUNCH_CHECK();
             store_sum_kernel<<<1, 32, 0, s>>>(c.partB, &c.sc->rr[0]);
             CS_LAUNCH_CHECK();
-            for (int m = 0; m < pd.M; ++m) CS_PROPAGATE(cg_iter(cc, maps, C, nullptr, 0, x, ws->r, ws->pv, ws->hp, m & 1, nullptr));
+            for (int m = 0; m < pd.M; ++m) CS_PROPAGATE(cg_iter(cc, maps, Cp, nullptr, 0, x, ws->r, ws->pv, ws->hp, m & 1, nullptr));
+            if (iters) {
+                copy_iter_kernel<<<g, kRedThreads, 0, s>>>(x, iters, ws->tdev, 0, D);
+                CS_LAUNCH_CHECK();
+            }
+            inc_kernel<<<1, 32, 0, s>>>(ws->tdev);
+            CS_LAUNCH_CHECK();
+            return CS_OK;
+        };
+        CS_PROPAGATE(run_body(ws, use_graph, sig, K, st, body, &graph_used));
+    } else if (sgd) {
+        // AccProxSGD (plain problem, l1-wavelets): per iteration a batch of B coils (given indices),
+        // unbiased batch gradient (Cp/B) sum_batch A_c^H (A_c z - y_c), step alpha_k =
+        // max(beta^k alpha_0, min alpha_0) with alpha_0 = 1/L of the full-coil normal operator,
+        // proximal step and Nesterov (FISTA) momentum
+        const int B = sp->sgd_batch;
+        CS_PROPAGATE(ws->ensure_sgd((int64_t)B * D, (int64_t)B * N));
+        if (sp->step > 0) {
+            set_L_kernel<<<1, 32, 0, st>>>(ws->sc, 1.0 / (double)sp->step);
+            CS_LAUNCH_CHECK();
+        } else {
+            CS_REQUIRE(sp->power_v0 != nullptr, CS_ERR_INVALID_ARG, "power_v0 is required when step == 0");
+            CS_PROPAGATE(power_iteration(c, (const float2*)sp->power_v0, sp->power_iters > 0 ? sp->power_iters : 20,
+                                         maps, Cp, nullptr, 0, ws->u, ws->hp));
+        }
+        theta_kernel<<<1, 32, 0, st>>>(ws->theta, std::max(K, 1));
+        CS_LAUNCH_CHECK();
+        CS_TRY_CUDA(cudaMemcpyAsync(ws->z, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
+        CS_TRY_CUDA(cudaMemcpyAsync(ws->xp, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
+        const double beta = sp->sgd_beta > 0 ? sp->sgd_beta : 0.99;
+        const double minf = sp->sgd_min > 0 ? sp->sgd_min : 0.1;
+        const float ratio = (float)Cp / (float)B;
+        auto body = [&](cudaStream_t s) -> cs_status {
+            Ctx cc = c;
+            cc.st = s;
+            const dim3 gg((unsigned)std::min<int64_t>(kRedBlocks, (std::max(D, N) + kRedThreads - 1) / kRedThreads),
+                          (unsigned)B);
+            gather_coils_kernel<<<gg, kRedThreads, 0, s>>>(maps, D, sp->sgd_coils, B, ws->tdev, ws->bmaps);
+            CS_LAUNCH_CHECK();
+            gather_coils_kernel<<<gg, kRedThreads, 0, s>>>(y, N, sp->sgd_coils, B, ws->tdev, ws->by);
+            CS_LAUNCH_CHECK();
+            CS_PROPAGATE((cs_status)sense_grad(p, (const float*)ws->z, (const float*)ws->bmaps, B, (const float*)ws->by,
+                                               (float*)ws->gr, s));
+            sgd_step_kernel<<<g, kRedThreads, 0, s>>>(ws->z, ws->gr, c.sc, ws->tdev, beta, minf, ratio, D, ws->u);
+            CS_LAUNCH_CHECK();
+            CS_PROPAGATE(prox_wavelet(cc, ws->u, x, c.sc, 0.f));
+            momentum_kernel<<<g, kRedThreads, 0, s>>>(x, ws->xp, 0.f, ws->theta, ws->tdev, D, ws->z);
+            CS_LAUNCH_CHECK();
+            CS_TRY_CUDA(cudaMemcpyAsync(ws->xp, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, s));
             if (iters) {
                 copy_iter_kernel<<<g, kRedThreads, 0, s>>>(x, iters, ws->tdev, 0, D);
                 CS_LAUNCH_CHECK();
@@ -1110,7 +1212,7 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
         if (!(sp->step > 0)) {
             CS_REQUIRE(sp->power_v0 != nullptr, CS_ERR_INVALID_ARG, "power_v0 is required when step == 0");
             CS_PROPAGATE(power_iteration(c, (const float2*)sp->power_v0, sp->power_iters > 0 ? sp->power_iters : 20,
-                                         maps, C, nullptr, 0, ws->u, ws->hp));
+                                         maps, Cp, nullptr, 0, ws->u, ws->hp));
         }
         theta_kernel<<<1, 32, 0, st>>>(ws->theta, std::max(K, 1));
         CS_LAUNCH_CHECK();
@@ -1119,7 +1221,7 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
         auto body = [&](cudaStream_t s) -> cs_status {
             Ctx cc = c;
             cc.st = s;
-            CS_PROPAGATE((cs_status)sense_grad(p, (const float*)ws->z, (const float*)maps, C, (const float*)y, (float*)ws->gr, s));
+            CS_PROPAGATE((cs_status)sense_grad(p, (const float*)ws->z, (const float*)maps, Cp, (const float*)y, (float*)ws->gr, s));
             fista_step_kernel<<<g, kRedThreads, 0, s>>>(ws->z, ws->gr, nullptr, c.sc, D, ws->u);
             CS_LAUNCH_CHECK();
             CS_PROPAGATE(prox_wavelet(cc, ws->u, x, c.sc, 0.f));
@@ -1137,8 +1239,8 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
         CS_PROPAGATE(run_body(ws, use_graph, sig, K, st, body, &graph_used));
     } else {
         // plain full-coil CG: (A^H A + lambda I) x = A^H y from x, K iterations in total
-        CS_PROPAGATE((cs_status)sense_adj(p, (const float*)y, (const float*)maps, C, (float*)ws->d, 0, st));   // b
-        CS_PROPAGATE(normal_apply(c, x, maps, C, nullptr, 0, c.lambda, ws->hp));                            // H x
+        CS_PROPAGATE((cs_status)sense_adj(p, (const float*)y, (const float*)maps, Cp, (float*)ws->d, 0, st));   // b
+        CS_PROPAGATE(normal_apply(c, x, maps, Cp, nullptr, 0, c.lambda, ws->hp));                            // H x
         cg_init2_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(ws->d, ws->hp, D, ws->r, ws->pv, c.partB);
         CS_LAUNCH_CHECK();
         store_sum_kernel<<<1, 32, 0, st>>>(c.partB, &c.sc->rr[0]);
@@ -1146,7 +1248,7 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
         auto body = [&](cudaStream_t s) -> cs_status {
             Ctx cc = c;
             cc.st = s;
-            CS_PROPAGATE(cg_iter(cc, maps, C, nullptr, 0, x, ws->r, ws->pv, ws->hp, 0, ws->tdev));
+            CS_PROPAGATE(cg_iter(cc, maps, Cp, nullptr, 0, x, ws->r, ws->pv, ws->hp, 0, ws->tdev));
             if (iters) {
                 copy_iter_kernel<<<g, kRedThreads, 0, s>>>(x, iters, ws->tdev, 0, D);
                 CS_LAUNCH_CHECK();
@@ -1330,6 +1432,23 @@ cs_status recon_solve(const cs_plan* p, const cs_problem* pr, const cs_solve_par
                    "need 1 <= V + S <= C (V=%d S=%d C=%d)", sp->V, sp->S, pr->C);
         CS_REQUIRE(sp->S == 0 || sp->V < pr->C, CS_ERR_INVALID_ARG, "S > 0 needs V < C");
     }
+    CS_REQUIRE(sp->keep >= 0 && sp->sgd_batch >= 0, CS_ERR_INVALID_ARG, "keep and sgd_batch must be >= 0");
+    if (!sp->sketch && sp->sgd_batch > 0) {
+        const int Cp = sp->keep > 0 ? std::min(sp->keep, pr->C) : pr->C;
+        CS_REQUIRE(pr->reg == CS_REG_L1_WAVELET, CS_ERR_INVALID_ARG, "AccProxSGD is implemented for l1-wavelets");
+        CS_REQUIRE(sp->sgd_batch <= Cp && sp->sgd_coils != nullptr, CS_ERR_INVALID_ARG,
+                   "AccProxSGD needs 1 <= sgd_batch <= coils and the coil index array");
+        CS_REQUIRE(std::isfinite(sp->sgd_beta) && sp->sgd_beta >= 0 && sp->sgd_beta <= 1 && std::isfinite(sp->sgd_min) &&
+                       sp->sgd_min >= 0 && sp->sgd_min <= 1,
+                   CS_ERR_INVALID_ARG, "sgd_beta and sgd_min must lie in [0, 1]");
+        // every batch index must name one of the Cp coils (checked on the host before anything runs)
+        std::vector<int> h((size_t)sp->K * sp->sgd_batch);
+        if (!h.empty()) {
+            CS_TRY_CUDA(cudaMemcpy(h.data(), sp->sgd_coils, sizeof(int) * h.size(), cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < h.size(); ++i)
+                CS_REQUIRE(h[i] >= 0 && h[i] < Cp, CS_ERR_INVALID_ARG, "sgd_coils[%zu] = %d outside [0, %d)", i, h[i], Cp);
+        }
+    }
     return recon_solve_impl(const_cast<cs_plan*>(p), pr, sp, (float2*)x_inout, stats, (cudaStream_t)stream);
 }
 
@@ -1352,6 +1471,7 @@ cs_status recon_solve_batched(int nslices, const cs_batch_item* items, const cs_
         CS_REQUIRE(params->sketches == nullptr, CS_ERR_INVALID_ARG, "batched solves draw their own sketches");
     }
     CS_REQUIRE(params->iterates == nullptr, CS_ERR_INVALID_ARG, "batched solves do not record iterates");
+    CS_REQUIRE(params->sgd_batch == 0, CS_ERR_INVALID_ARG, "batched solves do not run AccProxSGD");
     return recon_batched_impl(nslices, items, params, stats, (cudaStream_t)stream);
 }
 

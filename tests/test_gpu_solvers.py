@@ -220,3 +220,52 @@ def test_coil_sketching_with_classical_sketch_initialisation(reg):
     assert nrmse(h(x), x_ref) < 1e-4
     for k in range(T):
         assert nrmse(h(iters[k]), its[k]) < 1e-4
+
+
+def test_aggressive_coil_compression_matches_oracle():
+    """Plain FISTA on the first C^ virtual coils after coil PCA (the comparator of Sec. 3.3)."""
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    shape = (64, 64)
+    idx, maps, y, ops = _cart_problem(shape, C=8)
+    keep, K, lam = 4, 15, 1e-2
+    v0 = synthdata.random_complex(shape, 5)
+
+    def solve(f, a, yk):
+        L = solvers.power_iteration(lambda v: a(f(v)), v0, 20)
+        return solvers.plain_fista(f, a, yk, lam, 1 / L, np.zeros(shape, complex), K, levels=3)
+
+    x_ref = solvers.coil_compressed(ops, maps, y, keep, solve)
+    plan = cs.Plan(cs.CARTESIAN, shape, 8, mask_idx=t(idx, np.int32))
+    x, _ = cs.recon_solve(plan, t(y), t(maps), lam, cs.REG_L1_WAVELET,
+                          cs.SolveParams(K=K, sketch=False, do_pca=True, keep=keep, power_v0=t(v0)), wavelet_levels=3)
+    assert nrmse(h(x), x_ref) < 1e-4
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_acc_prox_sgd_matches_oracle(use_graph):
+    """AccProxSGD with given coil batches against the oracle (coil PCA off: batches index the
+    caller's coils)."""
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    shape = (64, 64)
+    idx, maps, y, ops = _cart_problem(shape, C=8)
+    B, K, lam, beta, floor = 3, 14, 5e-3, 0.95, 0.2
+    rng = np.random.default_rng(9)
+    batches = np.stack([rng.permutation(8)[:B] for _ in range(K)]).astype(np.int32)
+    v0 = synthdata.random_complex(shape, 5)
+    fwd, adj = ops(maps)
+    L = solvers.power_iteration(lambda v: adj(fwd(v)), v0, 20)
+    x_ref = solvers.acc_prox_sgd(ops, maps, y, lam, batches, 1 / L, beta, floor, np.zeros(shape, complex), K, levels=3)
+    plan = cs.Plan(cs.CARTESIAN, shape, 8, mask_idx=t(idx, np.int32))
+    prm = cs.SolveParams(K=K, sketch=False, do_pca=False, sgd_batch=B, sgd_coils=t(batches, np.int32), sgd_beta=beta,
+                         sgd_min=floor, power_v0=t(v0), use_graph=use_graph)
+    x, st = cs.recon_solve(plan, t(y), t(maps), lam, cs.REG_L1_WAVELET, prm, wavelet_levels=3)
+    assert abs(st["L"] - L) < 1e-5 * L
+    assert nrmse(h(x), x_ref) < 1e-4
+    bad = batches.copy()
+    bad[3, 1] = 8
+    with pytest.raises(cs.CoilSketchError):
+        cs.recon_solve(plan, t(y), t(maps), lam, cs.REG_L1_WAVELET,
+                       cs.SolveParams(K=K, sketch=False, do_pca=False, sgd_batch=B, sgd_coils=t(bad, np.int32),
+                                      power_v0=t(v0)), wavelet_levels=3)
