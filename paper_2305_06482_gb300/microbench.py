@@ -21,6 +21,12 @@ stream), for profiling individual kernels with small launch counts.
       noise 1e-2 max|y|, l2 lambda 1e-3: the full-coil CG solver (30 iterations) on fully and
       regularly undersampled data, and coil sketching (C^ 4 = 3 + 1 Rademacher, T 5 x K 10 CG)
       on the undersampled data, each as one batched solve of all replicas in one CUDA graph
+  python -m paper_2305_06482_gb300.microbench compare [--config cones3d_128|cones3d_large]
+      the method against the comparators of its evaluation on the cones workload (l1-db4,
+      lambda 2e-3): full-coil FISTA, aggressive coil compression to 8 virtual coils (lambda
+      halved, as the evaluation re-tuned it), AccProxSGD with batches of 8 coils (beta 0.99,
+      floor 0.1) and coil sketching (m = 8 = 7 PCA + 1 Rademacher, K = 10); distance to x_inf
+      (300 full-coil FISTA iterations) against device time, and the time to reach 5%
   python -m paper_2305_06482_gb300.microbench sketch [--voxels D] [--iters N]
       sketched maps (40 coils, V = 5, S = 5): FP32 CUDA cores vs BF16 split on the tensor cores
   python -m paper_2305_06482_gb300.microbench batched [--slices 64] [--iters N]
@@ -247,6 +253,54 @@ def gfactor(args):
               f"5th percentile {np.percentile(ig[inside], 5):.3f}")
 
 
+def compare(args):
+    cfg = CONFIGS[args.config]
+    dev = torch.device("cuda")
+    img, grid, C = cfg["img"], cfg["grid"], cfg["nc"]
+    traj = synthdata.cones_trajectory(cfg["n_int"], 512)
+    dcf = synthdata.cones_dcf(traj, img, cfg["n_int"], 512)
+    plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=torch.from_numpy(traj).to(dev), dcf=torch.from_numpy(dcf).to(dev),
+                   grid=grid)
+    maps = synthdata.coil_maps_torch(img, C, device=dev)
+    y = cs.sense_fwd(plan, synthdata.phantom_torch(img, seed=1, device=dev), maps)
+    y += 1e-3 * float(y.abs().max()) * torch.from_numpy(
+        synthdata.complex_noise(tuple(y.shape), 1.0, seed=3).astype(np.complex64)).to(dev)
+    v0 = synthdata.phantom_torch(img, seed=5, device=dev)
+    lam, levels = 2e-3, 4
+    x_inf, _ = cs.recon_solve(plan, y, maps, lam, cs.REG_L1_WAVELET,
+                              cs.SolveParams(K=300, sketch=False, do_pca=False, power_v0=v0), wavelet_levels=levels)
+    n_inf = float(torch.linalg.vector_norm(x_inf))
+
+    def run(name, lam_m, prm, n_it):
+        its = torch.empty((n_it,) + tuple(img), dtype=torch.complex64, device=dev)
+        prm.iterates = its
+        cs.recon_solve(plan, y, maps, lam_m, cs.REG_L1_WAVELET, prm, wavelet_levels=levels)   # warm-up
+        torch.cuda.synchronize()
+        a, b = _events()
+        a.record()
+        cs.recon_solve(plan, y, maps, lam_m, cs.REG_L1_WAVELET, prm, wavelet_levels=levels)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        d = [float(torch.linalg.vector_norm(its[k] - x_inf)) / n_inf for k in range(n_it)]
+        hit = [k for k, e in enumerate(d) if e <= 0.05]
+        t5 = f"{(hit[0] + 1) * ms / n_it:.0f} ms" if hit else "not reached"
+        print(f"{name:32s} {n_it:3d} steps, {ms:7.0f} ms ({ms / n_it:6.1f} ms/step); distance to x_inf: "
+              f"after 1/4 {d[n_it // 4 - 1]:.4f}, 1/2 {d[n_it // 2 - 1]:.4f}, end {d[-1]:.4f}; 5%: {t5}")
+
+    K = 60
+    rng = np.random.default_rng(11)
+    batches = torch.from_numpy(np.stack([rng.permutation(C)[:8] for _ in range(K)]).astype(np.int32)).to(dev)
+    print(f"{args.config}: l1-db4 lambda {lam}, {C} coils")
+    run("full-coil FISTA", lam, cs.SolveParams(K=K, sketch=False, do_pca=False, power_v0=v0), K)
+    run("coil compression to 8 (lam/2)", lam / 2, cs.SolveParams(K=K, sketch=False, do_pca=True, keep=8,
+                                                                 power_v0=v0), K)
+    run("AccProxSGD, batches of 8", lam, cs.SolveParams(K=K, sketch=False, do_pca=False, sgd_batch=8,
+                                                        sgd_coils=batches, power_v0=v0), K)
+    run("coil sketching m=8 (7+1 Rad.)", lam, cs.SolveParams(T=20, K=10, V=7, S=1, dist=cs.RADEMACHER, seed=4,
+                                                            power_v0=v0), 20)
+
+
 def sketch(args):
     dev = torch.device("cuda")
     C, V, S, D = 40, 5, 5, args.voxels
@@ -335,7 +389,8 @@ def batched(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["nufft", "normal", "tv", "ablation", "gfactor", "sketch", "cart2d", "batched"])
+    ap.add_argument("what", choices=["nufft", "normal", "tv", "ablation", "gfactor", "compare", "sketch", "cart2d",
+                                     "batched"])
     ap.add_argument("--replicas", type=int, default=60)
     ap.add_argument("--seeds", type=int, default=16)
     ap.add_argument("--slices", type=int, default=64)
@@ -344,7 +399,8 @@ def main():
     ap.add_argument("--iters", type=int, default=5)
     ap.add_argument("--voxels", type=int, default=160 * 256 * 256)
     args = ap.parse_args()
-    {"nufft": nufft, "normal": normal, "tv": tv, "ablation": ablation, "gfactor": gfactor, "sketch": sketch, "cart2d": cart2d, "batched": batched}[args.what](args)
+    {"nufft": nufft, "normal": normal, "tv": tv, "ablation": ablation, "gfactor": gfactor, "compare": compare,
+     "sketch": sketch, "cart2d": cart2d, "batched": batched}[args.what](args)
 
 
 if __name__ == "__main__":
