@@ -376,7 +376,7 @@ def run_native(args, w, rank, world, local_rank):
 # cones, 10-coil sketched normal operator (spread and interpolation: the whole launch; strided
 # passes: mean of the forward y and z passes; writes still dirty in L2 at kernel end are not
 # counted there).  Traffic grows in proportion to the algorithmic bytes, so the bench scales it.
-TRAFFIC_RATIO = {"spread": 1.040, "interp": 0.832, "fft_plain": 0.90}
+TRAFFIC_RATIO = {"spread": 1.043, "interp": 0.823, "fft_plain": 0.90}
 
 
 def stage_bytes(stage, w, T, steps):

@@ -271,15 +271,16 @@ __device__ float2* fft_lines(float2* a, float2* b, const float2* tw, int n, cons
 // for every axis, including x.  Thread t of a CTA owns line l = t mod kLines for the loads, the
 // butterflies and the stores (element rows jt = t / kLines, jt + kJ, ...), so its addresses are
 // one base plus a stride; per-line quantities of the x passes are computed once per CTA.
-enum PassMode { EXPAND_X = 0, PLAIN = 1, GATHER_Y = 2, SCATTER_Y = 3, MASK_Y = 4, REDUCE_X = 5 };
+// (the strided middle passes run in fft_plain_tma_kernel below)
+enum PassMode { EXPAND_X = 0, GATHER_Y = 2, SCATTER_Y = 3, MASK_Y = 4, REDUCE_X = 5 };
 
 struct PassArgs {
     int n, nrad;
     int4 st[kMaxRadices];
     const float2* tw;
     int sign;
-    int64_t outer;   // PLAIN / Y modes: outer index count
-    int64_t inner;   // PLAIN / Y modes: stride of the FFT axis in elements (includes the coil count)
+    int64_t outer;   // Y modes: outer index count
+    int64_t inner;   // Y modes: stride of the FFT axis in elements (includes the coil count)
     int n_in, in_off, n_out, out_off;
     const float2* in;
     float2* out;
@@ -483,10 +484,8 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
         i0 = (int64_t)blockIdx.x * kLines;
         const int64_t i = i0 + l;
         iv = i < A.inner;
-        if (MODE != PLAIN) {
-            px = (int)(i / A.C);
-            cc = (int)(i - (int64_t)px * A.C);
-        }
+        px = (int)(i / A.C);
+        cc = (int)(i - (int64_t)px * A.C);
         constexpr int LB = 8;   // loads in flight per thread
         if (MODE == SCATTER_Y) {
             for (int k0 = jt; k0 < n; k0 += kJ * LB) {
