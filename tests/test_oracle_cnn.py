@@ -52,3 +52,55 @@ def test_network_gradients_match_finite_differences():
             pm[pi].ravel()[j] -= h
             fd = (loss(pp) - loss(pm)) / (2 * h)
             assert abs(fd - grads[pi].ravel()[j]) <= 1e-6 * max(1.0, abs(fd)), (pi, j)
+
+
+def test_maxpool_and_transposed_convolution_match_loops():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((4, 2, 6, 3))
+    out, idx = cnn.maxpool2(x)
+    for z in range(2):
+        for y in range(1):
+            for xx in range(3):
+                for ch in range(3):
+                    block = [x[2 * z + dz, 2 * y + dy, 2 * xx + dx, ch] for dz, dy, dx in cnn.sub8()]
+                    assert out[z, y, xx, ch] == max(block) and idx[z, y, xx, ch] == int(np.argmax(block))
+    w = rng.standard_normal((2, 8, 3))
+    b = rng.standard_normal(2)
+    u = cnn.upconv2(out, w, b)
+    for z in range(4):
+        for y in range(2):
+            for xx in range(6):
+                a = 4 * (z % 2) + 2 * (y % 2) + (xx % 2)
+                assert np.allclose(u[z, y, xx], b + w[:, a, :] @ out[z // 2, y // 2, xx // 2])
+
+
+def test_unet_gradients_match_finite_differences():
+    rng = np.random.default_rng(3)
+    shapes = cnn.unet_shapes(2, 3, 4)
+    params = [rng.standard_normal(s) * (0.4 if len(s) > 1 else 0.1) for s in shapes]
+    f = rng.standard_normal((4, 4, 8, 4))
+    tgt = rng.standard_normal((4, 4, 8, 2))
+    out, cache = cnn.unet_forward(params, f)
+    idx = (cache["i1"], cache["i2"])
+
+    def loss(ps):
+        o, _ = cnn.unet_forward(ps, f, pool_idx=idx)     # the pools' decisions held fixed
+        return cnn.mse(o, tgt)[0]
+
+    _, g = cnn.mse(out, tgt)
+    grads = cnn.unet_backward(params, cache, g)
+    h = 1e-6
+    for pi in range(26):
+        flat = params[pi].ravel()
+        for j in rng.choice(flat.size, size=min(3, flat.size), replace=False):
+            pp = [q.copy() for q in params]
+            pm = [q.copy() for q in params]
+            pp[pi].ravel()[j] += h
+            pm[pi].ravel()[j] -= h
+            fd = (loss(pp) - loss(pm)) / (2 * h)
+            assert abs(fd - grads[pi].ravel()[j]) <= 1e-5 * max(1.0, abs(fd)), (pi, j)
+
+
+def test_unet_parameter_count():
+    n = sum(int(np.prod(s)) for s in cnn.unet_shapes())
+    assert 330_000 < n < 350_000        # the configured network's ~0.34 M weights
