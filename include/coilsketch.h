@@ -330,7 +330,7 @@ cs_status cs_power_iteration(const cs_plan* plan, const float* v0, const float* 
                              const float* maps_s, int S, int iters, double* L, void* stream);
 
 /* ------------------------------------------------------------------------------------------
- * Learned warm start (not in the paper): a small 3D CNN maps the sub-problem's (x^t, d) to a
+ * Learned warm start (not in the paper): a 3D U-Net maps the sub-problem's (x^t, d) to a
  * correction of x^t; its prediction is used as the sub-problem's starting point only when the
  * sub-problem objective confirms it.  Activations are voxel-major, channels fastest, FP32.
  * cs_nn_conv3d: 3x3x3 convolution, zero padding 1, as a BF16 implicit GEMM on the tensor cores
@@ -345,6 +345,15 @@ cs_status cs_power_iteration(const cs_plan* plan, const float* v0, const float* 
  *   (x^t, eta d) (ss receives ||x^t||^2 + eta^2 ||d||^2), training target (x_sub - x^t) / s,
  *   prediction x^t + s delta.
  * cs_nn_status: synchronise and report a bounded tensor-core wait that gave up.
+ * U-Net pieces (coarse sizes nz, ny, nx; fine = 2x each; child a = 4 dz + 2 dy + dx):
+ * cs_nn_maxpool2: out[v][c] = max over the 2x2x2 children of v of in, idx[v][c] = the first child
+ *   reaching it; cs_nn_maxpool2_bwd: gin (fine) = g routed to the argmax child, zero elsewhere.
+ * cs_nn_upconv2: stride-2 transposed convolution (kernel 2): out[child a of v][coff + co] =
+ *   b[co] + sum_ci in[v][ci] w[co][a][ci] (w [cout][8][cin], FP32 on CUDA cores);
+ *   cs_nn_upconv2_bwd: gin[v][ci] = sum_{a, co} gout[child a][goff + co] w[co][a][ci] (if gin),
+ *   gw[co][a][ci] += sum_v gout[child a][goff + co] in[v][ci] and gb += sum gout (if gw).
+ * cs_nn_slice: dst[v][doff + j] (+)= src[v][soff + j] for j < n (concatenation and its split).
+ * cs_nn_conv3d_wgrad and cs_nn_upconv2_bwd take cin, cout <= 128.
  * ---------------------------------------------------------------------------------------- */
 cs_status cs_nn_pack_weights(const float* w, int cout, int cin, int transpose, unsigned short* packed,
                              int npad, int kpad, void* stream);
@@ -366,6 +375,16 @@ cs_status cs_nn_features(const float* xt, const float* d, int64_t n, float eta, 
 cs_status cs_nn_target(const float* xt, const float* xs, int64_t n, const float* ss, float* tgt, void* stream);
 cs_status cs_nn_apply(const float* xt, const float* delta, int64_t n, const float* ss, float* out, void* stream);
 cs_status cs_nn_status(void* stream);
+cs_status cs_nn_maxpool2(const float* in, int nz, int ny, int nx, int C, float* out, unsigned char* idx,
+                         void* stream);
+cs_status cs_nn_maxpool2_bwd(const float* g, const unsigned char* idx, int nz, int ny, int nx, int C, float* gin,
+                             void* stream);
+cs_status cs_nn_upconv2(const float* in, int nz, int ny, int nx, int cin, const float* w, const float* b,
+                        int cout, float* out, int ldo, int coff, void* stream);
+cs_status cs_nn_upconv2_bwd(const float* in, const float* gout, int ldg, int goff, int nz, int ny, int nx,
+                            int cin, const float* w, int cout, float* gin, float* gw, float* gb, void* stream);
+cs_status cs_nn_slice(const float* src, int lds, int soff, int n, float* dst, int ldd, int doff, int64_t nvox,
+                      int accumulate, void* stream);
 
 /* ------------------------------------------------------------------------------------------
  * Regulariser building blocks (Sec. 2.1, l1-wavelets with a unitary Psi), exposed for testing:

@@ -77,6 +77,7 @@ EXPORTED = [
     "sketched_subproblem_solve", "cs_subproblem_objective", "cs_power_iteration", "cs_nn_pack_weights",
     "cs_nn_conv3d", "cs_nn_conv3d_wgrad", "cs_nn_relu_bwd", "cs_nn_conv1", "cs_nn_conv1_bwd", "cs_nn_mse",
     "cs_nn_adam", "cs_nn_features", "cs_nn_target", "cs_nn_apply", "cs_nn_status", "tv_dual_update", "tv_rhs",
+    "cs_nn_maxpool2", "cs_nn_maxpool2_bwd", "cs_nn_upconv2", "cs_nn_upconv2_bwd", "cs_nn_slice",
 ]
 STAGES = {"spread": 0, "interp": 1, "fft_plain": 2, "expand": 3, "reduce": 4}
 
@@ -120,6 +121,10 @@ def lib():
             "cs_nn_features": ([vp, vp, i64, f, vp, vp, vp], i), "cs_nn_target": ([vp, vp, i64, vp, vp, vp], i),
             "cs_nn_apply": ([vp, vp, i64, vp, vp, vp], i), "cs_nn_status": ([vp], i),
             "tv_dual_update": ([vp, vp, vp, i, vp, f, f, vp], i),
+            "cs_nn_maxpool2": ([vp, i, i, i, i, vp, vp, vp], i), "cs_nn_maxpool2_bwd": ([vp, vp, i, i, i, i, vp, vp], i),
+            "cs_nn_upconv2": ([vp, i, i, i, i, vp, vp, i, vp, i, i, vp], i),
+            "cs_nn_upconv2_bwd": ([vp, vp, i, i, i, i, i, i, vp, i, vp, vp, vp, vp], i),
+            "cs_nn_slice": ([vp, i, i, i, vp, i, i, i64, i, vp], i),
             "tv_rhs": ([vp, vp, vp, i, vp, f, vp, vp, vp], i),
         }
         for name, (args, res) in sig.items():

@@ -200,6 +200,7 @@ __global__ void wgrad_kernel(const float* __restrict__ in, const float* __restri
     const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
     const int64_t nvox = (int64_t)nz * ny * nx;
     const int pairs = cout * cin;
+    const int pbase = blockIdx.z * 4 * blockDim.x;   // this block's chunk of (co, ci) pairs
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     float bacc = 0.f;
     for (int64_t v0 = (int64_t)blockIdx.x * kWgVox; v0 < nvox; v0 += (int64_t)gridDim.x * kWgVox) {
@@ -221,7 +222,7 @@ __global__ void wgrad_kernel(const float* __restrict__ in, const float* __restri
         }
         __syncthreads();
         for (int q = 0; q < 4; ++q) {
-            const int pr = threadIdx.x + q * blockDim.x;
+            const int pr = pbase + threadIdx.x + q * blockDim.x;
             if (pr < pairs) {
                 const int co = pr / cin, ci = pr % cin;
                 float a = 0.f;
@@ -229,17 +230,17 @@ __global__ void wgrad_kernel(const float* __restrict__ in, const float* __restri
                 acc[q] += a;
             }
         }
-        if (tap == 13 && threadIdx.x < cout)
+        if (tap == 13 && blockIdx.z == 0 && threadIdx.x < cout)
             for (int t = 0; t < kWgVox; ++t) bacc += sg[t * cout + threadIdx.x];
     }
     for (int q = 0; q < 4; ++q) {
-        const int pr = threadIdx.x + q * blockDim.x;
+        const int pr = pbase + threadIdx.x + q * blockDim.x;
         if (pr < pairs) {
             const int co = pr / cin, ci = pr % cin;
             atomicAdd(&gw[((int64_t)co * 27 + tap) * cin + ci], acc[q]);
         }
     }
-    if (tap == 13 && threadIdx.x < cout && gb) atomicAdd(&gb[threadIdx.x], bacc);
+    if (tap == 13 && blockIdx.z == 0 && threadIdx.x < cout && gb) atomicAdd(&gb[threadIdx.x], bacc);
 }
 
 // g *= (act > 0)
@@ -353,6 +354,156 @@ __global__ void target_kernel(const float2* __restrict__ xt, const float2* __res
     }
 }
 
+// ---- U-Net pieces.  Child a = 4 dz + 2 dy + dx of a 2x2x2 block; coarse sizes (nz, ny, nx). ----
+
+// 2x2x2 max-pool: out[v][c] = max over the children of v; idx = first child reaching the maximum
+__global__ void maxpool2_kernel(const float* __restrict__ in, int nz, int ny, int nx, int C, float* __restrict__ out,
+                                unsigned char* __restrict__ idx) {
+    const int64_t n = (int64_t)nz * ny * nx * C;
+    const int64_t fy = 2 * nx, fz = (int64_t)4 * ny * nx;   // fine strides in voxels
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % C);
+        const int64_t v = e / C;
+        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
+        const int64_t base = (int64_t)(2 * z) * fz + (int64_t)(2 * y) * fy + 2 * x;
+        float best = 0.f;
+        int arg = 0;
+        for (int a = 0; a < 8; ++a) {
+            const int64_t f = base + (a >> 2) * fz + ((a >> 1) & 1) * fy + (a & 1);
+            const float val = in[f * C + c];
+            if (a == 0 || val > best) {
+                best = val;
+                arg = a;
+            }
+        }
+        out[e] = best;
+        idx[e] = (unsigned char)arg;
+    }
+}
+
+// gin (fine) = the pooled gradient routed to each block's argmax child, zero elsewhere
+__global__ void maxpool2_bwd_kernel(const float* __restrict__ g, const unsigned char* __restrict__ idx, int nz, int ny,
+                                    int nx, int C, float* __restrict__ gin) {
+    const int64_t n = (int64_t)nz * ny * nx * C;
+    const int64_t fy = 2 * nx, fz = (int64_t)4 * ny * nx;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % C);
+        const int64_t v = e / C;
+        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
+        const int64_t base = (int64_t)(2 * z) * fz + (int64_t)(2 * y) * fy + 2 * x;
+        const int arg = idx[e];
+        const float gv = g[e];
+        for (int a = 0; a < 8; ++a) {
+            const int64_t f = base + (a >> 2) * fz + ((a >> 1) & 1) * fy + (a & 1);
+            gin[f * C + c] = (a == arg) ? gv : 0.f;
+        }
+    }
+}
+
+// stride-2 transposed convolution (kernel 2): out[child a of v][coff + co] = b[co] + sum_ci in[v][ci] w[co][a][ci]
+__global__ void upconv2_kernel(const float* __restrict__ in, int nz, int ny, int nx, int cin, const float* __restrict__ w,
+                               const float* __restrict__ b, int cout, float* __restrict__ out, int ldo, int coff) {
+    const int64_t n = (int64_t)8 * nz * ny * nx * cout;     // fine voxels x cout
+    const int Fx = 2 * nx, Fy = 2 * ny;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int co = (int)(e % cout);
+        const int64_t f = e / cout;
+        const int X = (int)(f % Fx), Y = (int)((f / Fx) % Fy), Z = (int)(f / ((int64_t)Fx * Fy));
+        const int a = ((Z & 1) << 2) | ((Y & 1) << 1) | (X & 1);
+        const int64_t v = ((int64_t)(Z >> 1) * ny + (Y >> 1)) * nx + (X >> 1);
+        const float* iv = in + v * cin;
+        const float* wv = w + ((int64_t)co * 8 + a) * cin;
+        float acc = b ? b[co] : 0.f;
+        for (int ci = 0; ci < cin; ++ci) acc = fmaf(iv[ci], wv[ci], acc);
+        out[f * ldo + coff + co] = acc;
+    }
+}
+
+// data gradient of upconv2: gin[v][ci] = sum_{a, co} gout[child a of v][goff + co] w[co][a][ci]
+__global__ void upconv2_bwd_kernel(const float* __restrict__ gout, int ldg, int goff, int nz, int ny, int nx, int cin,
+                                   const float* __restrict__ w, int cout, float* __restrict__ gin) {
+    const int64_t n = (int64_t)nz * ny * nx * cin;
+    const int64_t fy = 2 * nx, fz = (int64_t)4 * ny * nx;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int ci = (int)(e % cin);
+        const int64_t v = e / cin;
+        const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
+        const int64_t base = (int64_t)(2 * z) * fz + (int64_t)(2 * y) * fy + 2 * x;
+        float acc = 0.f;
+        for (int a = 0; a < 8; ++a) {
+            const float* gf = gout + (base + (a >> 2) * fz + ((a >> 1) & 1) * fy + (a & 1)) * ldg + goff;
+            for (int co = 0; co < cout; ++co) acc = fmaf(gf[co], w[((int64_t)co * 8 + a) * cin + ci], acc);
+        }
+        gin[e] = acc;
+    }
+}
+
+// weight gradient of upconv2: gw[co][a][ci] += sum_v gout[child a of v][goff + co] in[v][ci];
+// gb[co] += sum over fine voxels of gout (blocks with blockIdx.z == 0 only).  Grid (x, 8 = a, pair chunks).
+__global__ void upconv2_wgrad_kernel(const float* __restrict__ in, const float* __restrict__ gout, int ldg, int goff, int nz,
+                                     int ny, int nx, int cin, int cout, float* __restrict__ gw, float* __restrict__ gb) {
+    extern __shared__ float usm[];
+    float* sg = usm;                      // [kWgVox][cout]
+    float* si = usm + kWgVox * cout;      // [kWgVox][cin]
+    const int a = blockIdx.y;
+    const int64_t nvox = (int64_t)nz * ny * nx;
+    const int64_t fy = 2 * nx, fz = (int64_t)4 * ny * nx;
+    const int pairs = cout * cin;
+    const int pbase = blockIdx.z * 4 * blockDim.x;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float bacc = 0.f;
+    for (int64_t v0 = (int64_t)blockIdx.x * kWgVox; v0 < nvox; v0 += (int64_t)gridDim.x * kWgVox) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kWgVox * cout; e += blockDim.x) {
+            const int64_t v = v0 + e / cout;
+            float val = 0.f;
+            if (v < nvox) {
+                const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
+                const int64_t f = (int64_t)(2 * z + (a >> 2)) * fz + (int64_t)(2 * y + ((a >> 1) & 1)) * fy + 2 * x + (a & 1);
+                val = gout[f * ldg + goff + e % cout];
+            }
+            sg[e] = val;
+        }
+        for (int e = threadIdx.x; e < kWgVox * cin; e += blockDim.x) {
+            const int64_t v = v0 + e / cin;
+            si[e] = (v < nvox) ? in[v * cin + e % cin] : 0.f;
+        }
+        __syncthreads();
+        for (int q = 0; q < 4; ++q) {
+            const int pr = pbase + threadIdx.x + q * blockDim.x;
+            if (pr < pairs) {
+                const int co = pr / cin, ci = pr % cin;
+                float s = 0.f;
+                for (int t = 0; t < kWgVox; ++t) s = fmaf(sg[t * cout + co], si[t * cin + ci], s);
+                acc[q] += s;
+            }
+        }
+        if (blockIdx.z == 0 && threadIdx.x < cout)
+            for (int t = 0; t < kWgVox; ++t) bacc += sg[t * cout + threadIdx.x];
+    }
+    for (int q = 0; q < 4; ++q) {
+        const int pr = pbase + threadIdx.x + q * blockDim.x;
+        if (pr < pairs) {
+            const int co = pr / cin, ci = pr % cin;
+            atomicAdd(&gw[((int64_t)co * 8 + a) * cin + ci], acc[q]);
+        }
+    }
+    if (blockIdx.z == 0 && threadIdx.x < cout && gb) atomicAdd(&gb[threadIdx.x], bacc);
+}
+
+// channel slices: dst[v][doff + j] (+)= src[v][soff + j], j < n
+__global__ void slice_kernel(const float* __restrict__ src, int lds, int soff, int n, float* __restrict__ dst, int ldd,
+                             int doff, int64_t nvox, int accumulate) {
+    const int64_t tot = nvox * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e % n);
+        const int64_t v = e / n;
+        const float s = src[v * lds + soff + j];
+        float* d = dst + v * ldd + doff + j;
+        *d = accumulate ? *d + s : s;
+    }
+}
+
 static int nn_grid(int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
 }
@@ -364,6 +515,22 @@ cs_status nn_init_attrs() {
                                      kNnChunk * kNnABytes + kNnChunk * 32 * 32));
     CS_TRY_CUDA(cudaFuncSetAttribute(conv3_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      kNnChunk * kNnABytes + kNnChunk * 64 * 32));
+    // weight gradients stage kWgVox voxels of cin + cout <= 256 channels
+    CS_TRY_CUDA(cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(float) * kWgVox * 256));
+    CS_TRY_CUDA(cudaFuncSetAttribute(upconv2_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sizeof(float) * kWgVox * 256));
+    return CS_OK;
+}
+
+static cs_status nn_attrs_once() {
+    static bool init[128] = {false};
+    int dev = 0;
+    CS_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 128 && !init[dev]) {
+        CS_PROPAGATE(nn_init_attrs());
+        init[dev] = true;
+    }
     return CS_OK;
 }
 
@@ -405,13 +572,9 @@ cs_status cs_nn_conv3d(const float* in, int nz, int ny, int nx, int cin, const u
     CS_REQUIRE(in && packed && out && nz > 0 && ny > 0 && nx > 0 && cin >= 1 && nout >= 1 && nout <= npad &&
                    coff >= 0 && coff + nout <= ldo && kpad >= 27 * cin && kpad % 16 == 0,
                CS_ERR_INVALID_ARG, "bad conv3d arguments");
-    static bool init[128] = {false};
+    CS_PROPAGATE(nn_attrs_once());
     int dev = 0;
     CS_TRY_CUDA(cudaGetDevice(&dev));
-    if (dev >= 0 && dev < 128 && !init[dev]) {
-        CS_PROPAGATE(nn_init_attrs());
-        init[dev] = true;
-    }
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nvox = (int64_t)nz * ny * nx;
     const int64_t tiles = (nvox + kNnM - 1) / kNnM;
@@ -432,11 +595,14 @@ cs_status cs_nn_conv3d(const float* in, int nz, int ny, int nx, int cin, const u
 cs_status cs_nn_conv3d_wgrad(const float* in, const float* gout, int nz, int ny, int nx, int cin, int cout, float* gw,
                              float* gb, void* stream) {
     clear_error();
-    CS_REQUIRE(in && gout && gw && cin >= 1 && cout >= 1 && cin * cout <= 1024, CS_ERR_INVALID_ARG, "bad wgrad arguments");
+    CS_REQUIRE(in && gout && gw && cin >= 1 && cout >= 1 && cin <= 128 && cout <= 128, CS_ERR_INVALID_ARG,
+               "bad wgrad arguments");
+    CS_PROPAGATE(nn_attrs_once());
     const int64_t nvox = (int64_t)nz * ny * nx;
     const size_t sm = sizeof(float) * kWgVox * (cin + cout);
     const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((nvox + kWgVox - 1) / kWgVox, 64));
-    wgrad_kernel<<<dim3(gx, 27), 256, sm, (cudaStream_t)stream>>>(in, gout, nz, ny, nx, cin, cout, gw, gb);
+    const int chunks = (cin * cout + 1023) / 1024;   // 256 threads x 4 pairs per block
+    wgrad_kernel<<<dim3(gx, 27, chunks), 256, sm, (cudaStream_t)stream>>>(in, gout, nz, ny, nx, cin, cout, gw, gb);
     CS_LAUNCH_CHECK();
     return CS_OK;
 }
@@ -513,6 +679,71 @@ cs_status cs_nn_apply(const float* xt, const float* delta, int64_t n, const floa
     clear_error();
     CS_REQUIRE(xt && delta && ss && out && n > 0, CS_ERR_INVALID_ARG, "bad apply arguments");
     apply_delta_kernel<<<nn_grid(n), 256, 0, (cudaStream_t)stream>>>((const float2*)xt, delta, n, ss, (float2*)out);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status cs_nn_maxpool2(const float* in, int nz, int ny, int nx, int C, float* out, unsigned char* idx, void* stream) {
+    clear_error();
+    CS_REQUIRE(in && out && idx && nz >= 1 && ny >= 1 && nx >= 1 && C >= 1, CS_ERR_INVALID_ARG,
+               "bad maxpool arguments (coarse sizes)");
+    const int64_t n = (int64_t)nz * ny * nx * C;
+    maxpool2_kernel<<<nn_grid(n), 256, 0, (cudaStream_t)stream>>>(in, nz, ny, nx, C, out, idx);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status cs_nn_maxpool2_bwd(const float* g, const unsigned char* idx, int nz, int ny, int nx, int C, float* gin,
+                             void* stream) {
+    clear_error();
+    CS_REQUIRE(g && idx && gin && nz >= 1 && ny >= 1 && nx >= 1 && C >= 1, CS_ERR_INVALID_ARG, "bad maxpool_bwd arguments");
+    const int64_t n = (int64_t)nz * ny * nx * C;
+    maxpool2_bwd_kernel<<<nn_grid(n), 256, 0, (cudaStream_t)stream>>>(g, idx, nz, ny, nx, C, gin);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status cs_nn_upconv2(const float* in, int nz, int ny, int nx, int cin, const float* w, const float* b, int cout,
+                        float* out, int ldo, int coff, void* stream) {
+    clear_error();
+    CS_REQUIRE(in && w && out && nz >= 1 && ny >= 1 && nx >= 1 && cin >= 1 && cout >= 1 && coff >= 0 && coff + cout <= ldo,
+               CS_ERR_INVALID_ARG, "bad upconv arguments");
+    const int64_t n = (int64_t)8 * nz * ny * nx * cout;
+    upconv2_kernel<<<nn_grid(n), 256, 0, (cudaStream_t)stream>>>(in, nz, ny, nx, cin, w, b, cout, out, ldo, coff);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status cs_nn_upconv2_bwd(const float* in, const float* gout, int ldg, int goff, int nz, int ny, int nx, int cin,
+                            const float* w, int cout, float* gin, float* gw, float* gb, void* stream) {
+    clear_error();
+    CS_REQUIRE(in && gout && w && nz >= 1 && ny >= 1 && nx >= 1 && cin >= 1 && cout >= 1 && cin <= 128 && cout <= 128 &&
+                   goff >= 0 && goff + cout <= ldg,
+               CS_ERR_INVALID_ARG, "bad upconv_bwd arguments");
+    CS_PROPAGATE(nn_attrs_once());
+    cudaStream_t st = (cudaStream_t)stream;
+    if (gin) {
+        const int64_t n = (int64_t)nz * ny * nx * cin;
+        upconv2_bwd_kernel<<<nn_grid(n), 256, 0, st>>>(gout, ldg, goff, nz, ny, nx, cin, w, cout, gin);
+        CS_LAUNCH_CHECK();
+    }
+    if (gw) {
+        const int64_t nvox = (int64_t)nz * ny * nx;
+        const size_t sm = sizeof(float) * kWgVox * (cin + cout);
+        const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((nvox + kWgVox - 1) / kWgVox, 64));
+        const int chunks = (cin * cout + 1023) / 1024;
+        upconv2_wgrad_kernel<<<dim3(gx, 8, chunks), 256, sm, st>>>(in, gout, ldg, goff, nz, ny, nx, cin, cout, gw, gb);
+        CS_LAUNCH_CHECK();
+    }
+    return CS_OK;
+}
+
+cs_status cs_nn_slice(const float* src, int lds, int soff, int n, float* dst, int ldd, int doff, int64_t nvox,
+                      int accumulate, void* stream) {
+    clear_error();
+    CS_REQUIRE(src && dst && n >= 1 && soff >= 0 && soff + n <= lds && doff >= 0 && doff + n <= ldd && nvox >= 0,
+               CS_ERR_INVALID_ARG, "bad slice arguments");
+    slice_kernel<<<nn_grid(nvox * n), 256, 0, (cudaStream_t)stream>>>(src, lds, soff, n, dst, ldd, doff, nvox, accumulate);
     CS_LAUNCH_CHECK();
     return CS_OK;
 }
