@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(const float* __restrict__
     const int kblocks = kpad / 16;
     const int64_t ntiles = (nvox + kNnM - 1) / kNnM;
     const int sgn = flip ? -1 : 1;
+    const bool vec4 = (cin & 3) == 0 && ((reinterpret_cast<uintptr_t>(in) & 15) == 0);
     bool failed = false;
     for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
         const int64_t v = tile * kNnM + tid;
@@ -82,26 +83,50 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(const float* __restrict__
         }
         for (int c0 = 0; c0 < kblocks; c0 += kNnChunk) {
             const int nkb = min(kNnChunk, kblocks - c0);
-            // A: this thread's voxel row of the implicit im2col matrix
+            // A: this thread's voxel row of the implicit im2col matrix.  With cin a multiple of 4
+            // every group of 4 consecutive k is 4 channels of one tap: one float4 load each, and
+            // 8 consecutive k are one 16-byte row of a core matrix.
             for (int kb = 0; kb < nkb; ++kb) {
-                for (int kk = 0; kk < 16; ++kk) {
-                    const int k = (c0 + kb) * 16 + kk;
-                    float val = 0.f;
-                    if (vv && k < ktot) {
-                        const int tap = k / cin, ci = k - tap * cin;
-                        const int zz = z + sgn * (tap / 9 - 1), yy = y + sgn * ((tap / 3) % 3 - 1), xx = x + sgn * (tap % 3 - 1);
-                        if (zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx)
-                            val = in[(((int64_t)zz * ny + yy) * nx + xx) * cin + ci];
+                unsigned char* arow = a_sm + kb * kNnABytes + nn_kmajor_off(tid, 0);
+                if (vec4) {
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int k = (c0 + kb) * 16 + 4 * q;
+                        float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (vv && k < ktot) {
+                            const int tap = k / cin, ci = k - tap * cin;
+                            const int zz = z + sgn * (tap / 9 - 1), yy = y + sgn * ((tap / 3) % 3 - 1),
+                                      xx = x + sgn * (tap % 3 - 1);
+                            if (zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx)
+                                val = *reinterpret_cast<const float4*>(in + (((int64_t)zz * ny + yy) * nx + xx) * cin + ci);
+                        }
+                        pk[2 * q] = (uint32_t)nn_bf16(val.x) | ((uint32_t)nn_bf16(val.y) << 16);
+                        pk[2 * q + 1] = (uint32_t)nn_bf16(val.z) | ((uint32_t)nn_bf16(val.w) << 16);
                     }
-                    *reinterpret_cast<unsigned short*>(a_sm + kb * kNnABytes + nn_kmajor_off(tid, kk)) = nn_bf16(val);
+                    *reinterpret_cast<uint4*>(arow) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    *reinterpret_cast<uint4*>(arow + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                } else {
+                    for (int kk = 0; kk < 16; ++kk) {
+                        const int k = (c0 + kb) * 16 + kk;
+                        float val = 0.f;
+                        if (vv && k < ktot) {
+                            const int tap = k / cin, ci = k - tap * cin;
+                            const int zz = z + sgn * (tap / 9 - 1), yy = y + sgn * ((tap / 3) % 3 - 1),
+                                      xx = x + sgn * (tap % 3 - 1);
+                            if (zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx)
+                                val = in[(((int64_t)zz * ny + yy) * nx + xx) * cin + ci];
+                        }
+                        *reinterpret_cast<unsigned short*>(a_sm + kb * kNnABytes + nn_kmajor_off(tid, kk)) = nn_bf16(val);
+                    }
                 }
             }
-            // B: the packed BF16 weights of these k-blocks
-            for (int e = tid; e < NPAD * nkb * 16; e += blockDim.x) {
-                const int n = e / (nkb * 16), kr = e % (nkb * 16);
-                const int kb = kr / 16, kk = kr % 16;
-                *reinterpret_cast<unsigned short*>(b_sm + kb * kBBytes + nn_kmajor_off(n, kk)) =
-                    wpk[(int64_t)n * kpad + (c0 + kb) * 16 + kk];
+            // B: the packed BF16 weights of these k-blocks, 8 k (16 bytes) per copy
+            for (int e = tid; e < NPAD * nkb * 2; e += blockDim.x) {
+                const int n = e / (nkb * 2), kr = e % (nkb * 2);
+                const int kb = kr >> 1, h = kr & 1;
+                *reinterpret_cast<uint4*>(b_sm + kb * kBBytes + nn_kmajor_off(n, 8 * h)) =
+                    *reinterpret_cast<const uint4*>(wpk + (int64_t)n * kpad + (c0 + kb) * 16 + 8 * h);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -168,6 +193,213 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(const float* __restrict__
     }
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kCols));
+}
+
+// ---- halo-brick implicit GEMM (cin a multiple of 4) ----
+// A CTA tile is TZ planes x 8 rows x 14 columns of output voxels.  The input brick around it,
+// (TZ + 2) x 10 x 16 voxels, is staged once per 16 input channels as BF16 in two 8-channel slabs
+// whose voxels sit 16 bytes apart, x fastest, rows 256 bytes apart.  Then the 128 rows
+// (8 rows x 16 columns) of one plane, shifted by a tap (dz, dy, dx), are one K-major operand
+// with 8-row core-matrix groups 128 bytes apart (SBO) and the two slabs as its two K halves
+// (LBO = slab size): each tap is one MMA straight from the brick, no im2col copy.  Columns 0
+// and 15 of each row see a neighbouring row through the shift and are discarded, so 14 of 16
+// columns are outputs.  Weights of all 27 taps for the 16 channels are staged beside the brick.
+constexpr int kBrX = 16, kBrY = 10, kTileX = 14, kTileY = 8, kBrTZ = 4;
+constexpr int kBrGuard = 128;    // shifted rows reach 16 bytes before the brick
+
+template <int NPAD, int TZ>
+struct BrickCfg {
+    static constexpr int kSlab = (TZ + 2) * kBrY * kBrX * 16;     // bytes of one 8-channel slab
+    static constexpr int kWTap = NPAD * 16 * 2;                   // bytes of one tap's B operand
+    static constexpr int kSmem = kBrGuard + 2 * kSlab + 27 * kWTap + 128;
+    static constexpr uint32_t kColsNeed = (uint32_t)(TZ * NPAD);
+    static constexpr uint32_t kCols = kColsNeed <= 32 ? 32u : kColsNeed <= 64 ? 64u : kColsNeed <= 128 ? 128u
+                                      : kColsNeed <= 256 ? 256u : 512u;
+};
+
+__device__ __forceinline__ uint64_t nn_desc2(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+template <int NPAD, int TZ>
+__global__ void __launch_bounds__(128, 1) conv3_brick_kernel(const float* __restrict__ in, int nz, int ny, int nx,
+                                                          int cin, const unsigned short* __restrict__ wpk, int kpad,
+                                                          int nout, const float* __restrict__ bias, int relu, int flip,
+                                                          float* __restrict__ out, int ldo, int coff) {
+    using Cfg = BrickCfg<NPAD, TZ>;
+    constexpr int kSlab = Cfg::kSlab, kWTap = Cfg::kWTap;
+    constexpr int kBz = TZ + 2;
+    constexpr int kVox = kBz * kBrY * kBrX;
+    constexpr int kItems = kVox * 4;
+    constexpr int kBrBatch = 8;
+    constexpr int kItemsPerThread = (kItems + 127) / 128;
+    constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NPAD >> 3) << 17) | ((uint32_t)(kNnM >> 4) << 24);
+    extern __shared__ __align__(1024) unsigned char nsm[];
+    unsigned char* brick = nsm + kBrGuard;                 // slab 0, then slab 1
+    unsigned char* wsm = brick + 2 * kSlab + 128;          // 27 taps x [NPAD][16] bf16
+    __shared__ uint32_t s_taddr;
+    __shared__ __align__(8) uint64_t s_mbar;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(nn_smem_u32(&s_taddr)),
+                     "r"(Cfg::kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(nn_smem_u32(&s_mbar)), "r"(1u));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // the guard bytes before the brick and the gap after it are read by discarded rows only;
+    // clear them once so that they hold finite values
+    for (int e = tid; e < kBrGuard / 4; e += blockDim.x) reinterpret_cast<uint32_t*>(nsm)[e] = 0u;
+    for (int e = tid; e < 128 / 4; e += blockDim.x) reinterpret_cast<uint32_t*>(brick + 2 * kSlab)[e] = 0u;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = s_taddr, mbar = nn_smem_u32(&s_mbar);
+    uint32_t phase = 0;
+    const int tx = (nx + kTileX - 1) / kTileX, ty = (ny + kTileY - 1) / kTileY, tz = (nz + TZ - 1) / TZ;
+    const int64_t ntiles = (int64_t)tx * ty * tz;
+    const int kpairs = (cin + 15) / 16;
+    const bool wvec = (cin & 15) == 0;
+    const bool vec_out = ((ldo | coff) & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+    bool failed = false;
+    for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+        const int itx = (int)(tile % tx), ity = (int)((tile / tx) % ty), itz = (int)(tile / ((int64_t)tx * ty));
+        const int x0 = itx * kTileX - 1, y0 = ity * kTileY - 1, z0 = itz * TZ - 1;   // brick origin
+        for (int kp = 0; kp < kpairs; ++kp) {
+            // input brick of channels kp*16 .. kp*16+15, zero outside the volume / channel range:
+            // item i = 4 channels (q = i & 3) of brick voxel i >> 2, loaded in batches so that
+            // each thread has kBrBatch loads in flight
+            for (int j0 = 0; j0 < kItemsPerThread; j0 += kBrBatch) {
+                float4 v[kBrBatch];
+#pragma unroll
+                for (int j = 0; j < kBrBatch; ++j) {
+                    const int i = tid + 128 * (j0 + j);
+                    v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const int vb = i >> 2, q = i & 3;
+                    if (i < kItems && kp * 16 + 4 * q < cin) {
+                        const int bx = vb % kBrX, by = (vb / kBrX) % kBrY, bz = vb / (kBrX * kBrY);
+                        const int gx = x0 + bx, gy = y0 + by, gz = z0 + bz;
+                        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
+                            v[j] = *reinterpret_cast<const float4*>(in + (((int64_t)gz * ny + gy) * nx + gx) * cin + kp * 16 + 4 * q);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kBrBatch; ++j) {
+                    const int i = tid + 128 * (j0 + j);
+                    if (i < kItems) {
+                        const int vb = i >> 2, q = i & 3;
+                        *reinterpret_cast<uint2*>(brick + (q >> 1) * kSlab + vb * 16 + (q & 1) * 8) =
+                            make_uint2((uint32_t)nn_bf16(v[j].x) | ((uint32_t)nn_bf16(v[j].y) << 16),
+                                       (uint32_t)nn_bf16(v[j].z) | ((uint32_t)nn_bf16(v[j].w) << 16));
+                    }
+                }
+            }
+            // B operands of the 27 taps for these channels (tap slot t holds tap 26 - t when flipped)
+            if (wvec) {
+                for (int e = tid; e < 27 * NPAD * 2; e += blockDim.x) {
+                    const int h = e & 1, n = (e >> 1) % NPAD, t = (e >> 1) / NPAD;
+                    const int ts = flip ? 26 - t : t;
+                    *reinterpret_cast<uint4*>(wsm + t * kWTap + nn_kmajor_off(n, 8 * h)) =
+                        *reinterpret_cast<const uint4*>(wpk + (int64_t)n * kpad + ts * cin + kp * 16 + 8 * h);
+                }
+            } else {
+                for (int e = tid; e < 27 * NPAD * 16; e += blockDim.x) {
+                    const int c = e & 15, n = (e >> 4) % NPAD, t = (e >> 4) / NPAD;
+                    const int ts = flip ? 26 - t : t;
+                    const int ch = kp * 16 + c;
+                    *reinterpret_cast<unsigned short*>(wsm + t * kWTap + nn_kmajor_off(n, c)) =
+                        ch < cin ? wpk[(int64_t)n * kpad + ts * cin + ch] : (unsigned short)0;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (tid == 0) {
+                const uint32_t b0 = nn_smem_u32(brick), w0 = nn_smem_u32(wsm);
+                for (int p = 0; p < TZ; ++p) {
+                    for (int t = 0; t < 27; ++t) {
+                        const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+                        const uint32_t aaddr = b0 + (uint32_t)((p + dz + 1) * (kBrY * kBrX * 16) + (dy + 1) * (kBrX * 16) + dx * 16);
+                        const uint64_t ad = nn_desc2(aaddr, (uint32_t)kSlab, 128u);
+                        const uint64_t bd = nn_desc2(w0 + (uint32_t)(t * kWTap), 128u, 256u);
+                        const uint32_t acc = (kp > 0 || t > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr + (uint32_t)(p * NPAD)),
+                            "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                             : "memory");
+            }
+            long long spins = 0;
+            uint32_t done = 0;
+            while (!done) {
+                asm volatile(
+                    "{\n.reg .pred P1;\nmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\nselp.b32 %0, 1, 0, P1;\n}\n"
+                    : "=r"(done)
+                    : "r"(mbar), "r"(phase)
+                    : "memory");
+                if (!done && ++spins > kNnSpin) break;
+            }
+            if (__syncthreads_or(!done)) {
+                if (tid == 0) atomicExch(&g_nn_error, 1);
+                failed = true;
+                break;
+            }
+            phase ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        if (failed) break;
+        // epilogue: TMEM lane = row r = 16 y + c of the plane, columns p * NPAD + channel
+        const int yy = tid >> 4, cc = tid & 15;
+        const int gx = x0 + cc, gy = y0 + 1 + yy;
+        const bool colok = cc >= 1 && cc <= kTileX && gx < nx && gy < ny;
+        for (int p = 0; p < TZ; ++p) {
+            const int gz = z0 + 1 + p;
+            const bool ok = colok && gz < nz;
+#pragma unroll
+            for (int j = 0; j < NPAD / 16; ++j) {
+                uint32_t r[16];
+                const uint32_t a = taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(p * NPAD + j * 16);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                    : "r"(a));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (ok) {
+                    float* o = out + (((int64_t)gz * ny + gy) * nx + gx) * ldo + coff;
+                    float vals[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int n = j * 16 + q;
+                        float val = __uint_as_float(r[q]) + ((bias && n < nout) ? bias[n] : 0.f);
+                        vals[q] = relu ? fmaxf(val, 0.f) : val;
+                    }
+                    if (vec_out && j * 16 + 16 <= nout) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            *reinterpret_cast<float4*>(o + j * 16 + 4 * q) =
+                                make_float4(vals[4 * q], vals[4 * q + 1], vals[4 * q + 2], vals[4 * q + 3]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q)
+                            if (j * 16 + q < nout) o[j * 16 + q] = vals[q];
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(Cfg::kCols));
 }
 
 // packed BF16 weights [npad][kpad]: forward rows co with k = tap*cin + ci; transposed (data
@@ -400,22 +632,70 @@ __global__ void maxpool2_bwd_kernel(const float* __restrict__ g, const unsigned 
     }
 }
 
-// stride-2 transposed convolution (kernel 2): out[child a of v][coff + co] = b[co] + sum_ci in[v][ci] w[co][a][ci]
-__global__ void upconv2_kernel(const float* __restrict__ in, int nz, int ny, int nx, int cin, const float* __restrict__ w,
-                               const float* __restrict__ b, int cout, float* __restrict__ out, int ldo, int coff) {
-    const int64_t n = (int64_t)8 * nz * ny * nx * cout;     // fine voxels x cout
-    const int Fx = 2 * nx, Fy = 2 * ny;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int co = (int)(e % cout);
-        const int64_t f = e / cout;
-        const int X = (int)(f % Fx), Y = (int)((f / Fx) % Fy), Z = (int)(f / ((int64_t)Fx * Fy));
-        const int a = ((Z & 1) << 2) | ((Y & 1) << 1) | (X & 1);
-        const int64_t v = ((int64_t)(Z >> 1) * ny + (Y >> 1)) * nx + (X >> 1);
-        const float* iv = in + v * cin;
-        const float* wv = w + ((int64_t)co * 8 + a) * cin;
-        float acc = b ? b[co] : 0.f;
-        for (int ci = 0; ci < cin; ++ci) acc = fmaf(iv[ci], wv[ci], acc);
-        out[f * ldo + coff + co] = acc;
+// stride-2 transposed convolution (kernel 2): out[child a of v][coff + co] = b[co] + sum_ci in[v][ci] w[co][a][ci].
+// A thread takes one coarse voxel and one group of 4 output channels (blockIdx.y) for all 8
+// children; the block's 4 x 8 weight rows sit in shared memory and are read as broadcasts.
+constexpr int kUpThreads = 256;
+__global__ void __launch_bounds__(kUpThreads) upconv2_kernel(const float* __restrict__ in, int nz, int ny, int nx, int cin,
+                                                             const float* __restrict__ w, const float* __restrict__ b,
+                                                             int cout, float* __restrict__ out, int ldo, int coff, int vec) {
+    extern __shared__ float4 usw[];            // [cin / 4][4 r][8 a] float4 (vec) or [cin][4][8] floats
+    float* uss = reinterpret_cast<float*>(usw);
+    const int co0 = blockIdx.y * 4;
+    const int nr = min(4, cout - co0);
+    for (int e = threadIdx.x; e < cin * 32; e += blockDim.x) {
+        const int ci = e / 32, ra = e % 32, r = ra / 8, a = ra % 8;
+        const float val = r < nr ? w[((int64_t)(co0 + r) * 8 + a) * cin + ci] : 0.f;
+        if (vec)
+            uss[(((ci >> 2) * 4 + r) * 8 + a) * 4 + (ci & 3)] = val;
+        else
+            uss[(ci * 4 + r) * 8 + a] = val;
+    }
+    __syncthreads();
+    const int64_t nvox = (int64_t)nz * ny * nx;
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nvox) return;
+    float acc[8][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const float bb = (b && r < nr) ? b[co0 + r] : 0.f;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) acc[a][r] = bb;
+    }
+    const float* iv = in + v * cin;
+    if (vec) {
+        for (int c4 = 0; c4 < cin / 4; ++c4) {
+            const float4 xi = *reinterpret_cast<const float4*>(iv + 4 * c4);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    const float4 wv = usw[(c4 * 4 + r) * 8 + a];
+                    acc[a][r] = fmaf(xi.x, wv.x, fmaf(xi.y, wv.y, fmaf(xi.z, wv.z, fmaf(xi.w, wv.w, acc[a][r]))));
+                }
+            }
+        }
+    } else {
+        for (int ci = 0; ci < cin; ++ci) {
+            const float xi = iv[ci];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int a = 0; a < 8; ++a) acc[a][r] = fmaf(xi, uss[(ci * 4 + r) * 8 + a], acc[a][r]);
+        }
+    }
+    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int64_t f = ((int64_t)(2 * z + (a >> 2)) * (2 * ny) + (2 * y + ((a >> 1) & 1))) * (2 * nx) + 2 * x + (a & 1);
+        float* o = out + f * ldo + coff + co0;
+        if (nr == 4 && (reinterpret_cast<uintptr_t>(o) & 15) == 0) {
+            *reinterpret_cast<float4*>(o) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (r < nr) o[r] = acc[a][r];
+        }
     }
 }
 
@@ -491,16 +771,29 @@ __global__ void upconv2_wgrad_kernel(const float* __restrict__ in, const float* 
     if (blockIdx.z == 0 && threadIdx.x < cout && gb) atomicAdd(&gb[threadIdx.x], bacc);
 }
 
-// channel slices: dst[v][doff + j] (+)= src[v][soff + j], j < n
+// channel slices: dst[v][doff + j] (+)= src[v][soff + j], j < n; with n, the offsets and strides
+// multiples of 4 (and aligned pointers) a thread moves 4 channels
 __global__ void slice_kernel(const float* __restrict__ src, int lds, int soff, int n, float* __restrict__ dst, int ldd,
-                             int doff, int64_t nvox, int accumulate) {
-    const int64_t tot = nvox * n;
+                             int doff, int64_t nvox, int accumulate, int vec) {
+    const int per = vec ? n >> 2 : n;
+    const int64_t tot = nvox * per;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(e % n);
-        const int64_t v = e / n;
-        const float s = src[v * lds + soff + j];
-        float* d = dst + v * ldd + doff + j;
-        *d = accumulate ? *d + s : s;
+        const int64_t v = e / per;
+        const int j = (int)(e - v * per);
+        if (vec) {
+            const float4 sv = *reinterpret_cast<const float4*>(src + v * lds + soff + 4 * j);
+            float4* d = reinterpret_cast<float4*>(dst + v * ldd + doff + 4 * j);
+            if (accumulate) {
+                const float4 dv = *d;
+                *d = make_float4(dv.x + sv.x, dv.y + sv.y, dv.z + sv.z, dv.w + sv.w);
+            } else {
+                *d = sv;
+            }
+        } else {
+            const float sv = src[v * lds + soff + j];
+            float* d = dst + v * ldd + doff + j;
+            *d = accumulate ? *d + sv : sv;
+        }
     }
 }
 
@@ -515,6 +808,15 @@ cs_status nn_init_attrs() {
                                      kNnChunk * kNnABytes + kNnChunk * 32 * 32));
     CS_TRY_CUDA(cudaFuncSetAttribute(conv3_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      kNnChunk * kNnABytes + kNnChunk * 64 * 32));
+    CS_TRY_CUDA(cudaFuncSetAttribute(conv3_brick_kernel<16, kBrTZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     BrickCfg<16, kBrTZ>::kSmem));
+    CS_TRY_CUDA(cudaFuncSetAttribute(conv3_brick_kernel<16, kBrTZ>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    CS_TRY_CUDA(cudaFuncSetAttribute(conv3_brick_kernel<32, kBrTZ>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    CS_TRY_CUDA(cudaFuncSetAttribute(conv3_brick_kernel<64, kBrTZ>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    CS_TRY_CUDA(cudaFuncSetAttribute(conv3_brick_kernel<32, kBrTZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     BrickCfg<32, kBrTZ>::kSmem));
+    CS_TRY_CUDA(cudaFuncSetAttribute(conv3_brick_kernel<64, kBrTZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     BrickCfg<64, kBrTZ>::kSmem));
     // weight gradients stage kWgVox voxels of cin + cout <= 256 channels
     CS_TRY_CUDA(cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sizeof(float) * kWgVox * 256));
@@ -531,6 +833,21 @@ static cs_status nn_attrs_once() {
         CS_PROPAGATE(nn_init_attrs());
         init[dev] = true;
     }
+    return CS_OK;
+}
+
+// persistent grid: as many CTAs per SM as shared memory and tensor memory (512 columns) allow
+template <int NPAD>
+static cs_status launch_brick(int64_t tiles, int sms, const float* in, int nz, int ny, int nx, int cin,
+                              const unsigned short* packed, int kpad, int nout, const float* bias, int relu, int flip,
+                              float* out, int ldo, int coff, cudaStream_t st) {
+    using Cfg = BrickCfg<NPAD, kBrTZ>;
+    // 228 KB of shared memory per SM, 1 KB of it reserved per CTA, plus this kernel's static 1 KB
+    const int per_sm = std::max(1, std::min(233472 / (Cfg::kSmem + 2048), (int)(512u / Cfg::kCols)));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)std::max(sms, 1) * per_sm));
+    conv3_brick_kernel<NPAD, kBrTZ><<<grid, 128, Cfg::kSmem, st>>>(in, nz, ny, nx, cin, packed, kpad, nout, bias, relu,
+                                                                   flip, out, ldo, coff);
+    CS_LAUNCH_CHECK();
     return CS_OK;
 }
 
@@ -570,7 +887,8 @@ cs_status cs_nn_conv3d(const float* in, int nz, int ny, int nx, int cin, const u
                        int nout, const float* bias, int relu, int flip, float* out, int ldo, int coff, void* stream) {
     clear_error();
     CS_REQUIRE(in && packed && out && nz > 0 && ny > 0 && nx > 0 && cin >= 1 && nout >= 1 && nout <= npad &&
-                   coff >= 0 && coff + nout <= ldo && kpad >= 27 * cin && kpad % 16 == 0,
+                   coff >= 0 && coff + nout <= ldo && kpad >= 27 * cin && kpad % 16 == 0 &&
+                   (reinterpret_cast<uintptr_t>(packed) & 15) == 0,
                CS_ERR_INVALID_ARG, "bad conv3d arguments");
     CS_PROPAGATE(nn_attrs_once());
     int dev = 0;
@@ -581,6 +899,16 @@ cs_status cs_nn_conv3d(const float* in, int nz, int ny, int nx, int cin, const u
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)std::max(sms, 1) * 4));
+    if ((cin & 3) == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0) {
+        const int64_t btiles = (int64_t)((nx + kTileX - 1) / kTileX) * ((ny + kTileY - 1) / kTileY) *
+                               ((nz + kBrTZ - 1) / kBrTZ);
+        switch (npad) {
+            case 16: return launch_brick<16>(btiles, sms, in, nz, ny, nx, cin, packed, kpad, nout, bias, relu, flip, out, ldo, coff, st);
+            case 32: return launch_brick<32>(btiles, sms, in, nz, ny, nx, cin, packed, kpad, nout, bias, relu, flip, out, ldo, coff, st);
+            case 64: return launch_brick<64>(btiles, sms, in, nz, ny, nx, cin, packed, kpad, nout, bias, relu, flip, out, ldo, coff, st);
+            default: set_error("npad must be 16, 32 or 64"); return CS_ERR_INVALID_ARG;
+        }
+    }
     const size_t sm = (size_t)kNnChunk * kNnABytes + (size_t)kNnChunk * npad * 32;
     switch (npad) {
         case 16: conv3_tc_kernel<16><<<grid, 128, sm, st>>>(in, nz, ny, nx, cin, packed, kpad, nout, bias, relu, flip, out, ldo, coff); break;
@@ -708,8 +1036,14 @@ cs_status cs_nn_upconv2(const float* in, int nz, int ny, int nx, int cin, const 
     clear_error();
     CS_REQUIRE(in && w && out && nz >= 1 && ny >= 1 && nx >= 1 && cin >= 1 && cout >= 1 && coff >= 0 && coff + cout <= ldo,
                CS_ERR_INVALID_ARG, "bad upconv arguments");
-    const int64_t n = (int64_t)8 * nz * ny * nx * cout;
-    upconv2_kernel<<<nn_grid(n), 256, 0, (cudaStream_t)stream>>>(in, nz, ny, nx, cin, w, b, cout, out, ldo, coff);
+    CS_REQUIRE(cin <= 1024 && (cout + 3) / 4 <= 65535, CS_ERR_UNSUPPORTED_SIZE, "upconv: cin above 1024");
+    const int groups = (cout + 3) / 4;
+    const int vec = (cin % 4 == 0) && (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+    const int64_t nvox = (int64_t)nz * ny * nx;
+    const size_t sm = sizeof(float) * 32 * (size_t)cin;
+    if (sm > 48 * 1024) CS_TRY_CUDA(cudaFuncSetAttribute(upconv2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const dim3 grid((unsigned)((nvox + kUpThreads - 1) / kUpThreads), (unsigned)groups);
+    upconv2_kernel<<<grid, kUpThreads, sm, (cudaStream_t)stream>>>(in, nz, ny, nx, cin, w, b, cout, out, ldo, coff, vec);
     CS_LAUNCH_CHECK();
     return CS_OK;
 }
@@ -743,7 +1077,10 @@ cs_status cs_nn_slice(const float* src, int lds, int soff, int n, float* dst, in
     clear_error();
     CS_REQUIRE(src && dst && n >= 1 && soff >= 0 && soff + n <= lds && doff >= 0 && doff + n <= ldd && nvox >= 0,
                CS_ERR_INVALID_ARG, "bad slice arguments");
-    slice_kernel<<<nn_grid(nvox * n), 256, 0, (cudaStream_t)stream>>>(src, lds, soff, n, dst, ldd, doff, nvox, accumulate);
+    const int vec = n % 4 == 0 && lds % 4 == 0 && ldd % 4 == 0 && soff % 4 == 0 && doff % 4 == 0 &&
+                    (reinterpret_cast<uintptr_t>(src) & 15) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+    slice_kernel<<<nn_grid(nvox * (vec ? n / 4 : n)), 256, 0, (cudaStream_t)stream>>>(src, lds, soff, n, dst, ldd, doff,
+                                                                                    nvox, accumulate, vec);
     CS_LAUNCH_CHECK();
     return CS_OK;
 }

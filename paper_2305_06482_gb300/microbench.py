@@ -33,6 +33,10 @@ stream), for profiling individual kernels with small launch counts.
       64 2D Cartesian slices of uneven size (256..384 squared), 16 coils, line mask R = 6 with
       24 centre lines, l1-db4 FISTA (lambda 5e-3), sketch m = 6 (3 PCA + 3 Gaussian), T = 10, K = 10:
       one slice after another vs all slices forked and joined vs all slices in one CUDA graph
+  python -m paper_2305_06482_gb300.microbench warmnet [--config cones3d_128|cones3d_large] [--iters N]
+      the warm-start U-Net (16/32/64 channels): every 3x3x3 convolution alone on random inputs of
+      its shape (BF16 implicit GEMM on the tensor cores), one whole inference on the image size of
+      the workload, and one training step (forward, backward, Adam) on a 64^3 crop
   python -m paper_2305_06482_gb300.microbench cart2d [--iters N]
       128x128 Cartesian coil-sketched CG reconstruction (8 coils, m = 4, T = 5, K = 10),
       eager launches vs a replayed CUDA graph
@@ -387,10 +391,129 @@ def batched(args):
         print(f"batched slices ({len(sizes)} slices, {D_total / 1e6:.2f} M pixels, 16 coils): {name}: {dt * 1e3:.1f} ms")
 
 
+def _bf16_peak():
+    import json
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
+def warmnet(args):
+    import paper_2305_06482_gb300.warmstart as ws
+    img = CONFIGS[args.config]["img"]
+    dev = torch.device("cuda")
+    gen = torch.Generator(device=dev).manual_seed(0)
+    net = ws.WarmNet(seed=0)
+    net.pack()
+    peak, src = _bf16_peak()
+    c1, c2, c3 = ws.WIDTHS
+    lv = [tuple(img), tuple(v // 2 for v in img), tuple(v // 4 for v in img)]
+    total_flops = 0.0
+    print(f"warm-start U-Net on {img}: tensor-core convolutions (FLOPs 2 V 27 cin cout; peak bf16 {peak:.0f} "
+          f"TFLOP/s, {src})")
+    for pi, kind, cin, cout in net.layers:
+        if kind != "conv":
+            continue
+        level = {0: 0, 2: 0, 4: 1, 6: 1, 8: 2, 10: 2, 14: 1, 16: 1, 20: 0, 22: 0}[pi]
+        dims = lv[level]
+        V = int(np.prod(dims))
+        x = torch.randn((V, cin), generator=gen, device=dev)
+        out = torch.empty((V, cout), device=dev)
+        for _ in range(args.warmup):
+            net._conv(x, dims, pi, cin, cout, None, out=out, ldo=cout)
+        a, b = _events()
+        a.record()
+        for _ in range(args.iters):
+            net._conv(x, dims, pi, cin, cout, None, out=out, ldo=cout)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.iters
+        fl = 2.0 * V * 27 * cin * cout
+        total_flops += fl
+        print(f"  layer {pi:2d} {cin:2d}->{cout:2d} on {dims}: {ms:.3f} ms, {fl / ms / 1e9:.1f} TFLOP/s "
+              f"({fl / ms / 1e9 / peak:.3f} of peak)")
+        del x, out
+    # the CUDA-core layers of the forward pass
+    L = cs.lib()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        a, b = _events()
+        a.record()
+        for _ in range(args.iters):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / args.iters
+
+    for pi, cdims, cin, cout in ((12, lv[2], c3, c2), (18, lv[1], c2, c1)):
+        Vc = int(np.prod(cdims))
+        x = torch.randn((Vc, cin), generator=gen, device=dev)
+        cat = torch.empty((8 * Vc, 2 * cout), device=dev)
+        ms = timed(lambda: net._up(x, cdims, pi, cin, cout, cat, 2 * cout, None))
+        byt = 4.0 * (Vc * cin + 8 * Vc * cout)
+        print(f"  transposed conv {cin}->{cout} to {tuple(2 * v for v in cdims)}: {ms:.3f} ms, {byt / ms / 1e6:.0f} GB/s")
+        src = torch.randn((8 * Vc, cout), generator=gen, device=dev)
+        ms = timed(lambda: net._slice(src, cout, 0, cout, cat, 2 * cout, cout, 8 * Vc, False, None))
+        print(f"  skip copy of {cout} channels: {ms:.3f} ms, {8.0 * 8 * Vc * cout / ms / 1e6:.0f} GB/s")
+        del x, cat, src
+    for dims, C in ((lv[0], c1), (lv[1], c2)):
+        V = int(np.prod(dims))
+        x = torch.randn((V, C), generator=gen, device=dev)
+        ms = timed(lambda: net._pool(x, dims, C, None))
+        print(f"  max-pool of {C} channels on {dims}: {ms:.3f} ms, {4.0 * V * C * (1 + 1 / 8 + 1 / 32) / ms / 1e6:.0f} GB/s")
+        del x
+    x = torch.randn((int(np.prod(lv[0])), c1), generator=gen, device=dev)
+    y = torch.empty((x.shape[0], 2), device=dev)
+    ms = timed(lambda: cs._check(L.cs_nn_conv1(cs._ptr(x), x.shape[0], c1, 2, cs._ptr(net.params[24]),
+                                               cs._ptr(net.params[25]), cs._ptr(y), None)))
+    print(f"  1x1x1 output layer {c1}->2: {ms:.3f} ms, {4.0 * x.shape[0] * (c1 + 2) / ms / 1e6:.0f} GB/s")
+    del x, y
+    V1 = int(np.prod(img))
+    f = torch.randn((V1, 4), generator=gen, device=dev)
+    for _ in range(args.warmup):
+        net.forward(f, img)
+    a, b = _events()
+    a.record()
+    for _ in range(args.iters):
+        net.forward(f, img)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.iters
+    print(f"  inference (whole U-Net, {total_flops / 1e12:.2f} TFLOP in the 3x3x3 layers): {ms:.2f} ms, "
+          f"{total_flops / ms / 1e9:.1f} TFLOP/s")
+    del f
+    crop = (64, 64, 64)
+    Vc = int(np.prod(crop))
+    fc = torch.randn((Vc, 4), generator=gen, device=dev)
+    tg = torch.randn((Vc, 2), generator=gen, device=dev)
+
+    def step():
+        o = net.forward(fc, crop, keep=True)
+        _, g = net.loss_and_grad(o, tg)
+        net.backward(g, crop)
+        net.adam(lr=1e-4)
+
+    for _ in range(args.warmup):
+        step()
+    a, b = _events()
+    a.record()
+    for _ in range(args.iters):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    print(f"  training step on a 64^3 crop (forward, backward, Adam): {a.elapsed_time(b) / args.iters:.2f} ms")
+    cs._check(cs.lib().cs_nn_status(None))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["nufft", "normal", "tv", "ablation", "gfactor", "compare", "sketch", "cart2d",
-                                     "batched"])
+                                     "batched", "warmnet"])
     ap.add_argument("--replicas", type=int, default=60)
     ap.add_argument("--seeds", type=int, default=16)
     ap.add_argument("--slices", type=int, default=64)
@@ -400,7 +523,7 @@ def main():
     ap.add_argument("--voxels", type=int, default=160 * 256 * 256)
     args = ap.parse_args()
     {"nufft": nufft, "normal": normal, "tv": tv, "ablation": ablation, "gfactor": gfactor, "compare": compare,
-     "sketch": sketch, "cart2d": cart2d, "batched": batched}[args.what](args)
+     "sketch": sketch, "cart2d": cart2d, "batched": batched, "warmnet": warmnet}[args.what](args)
 
 
 if __name__ == "__main__":

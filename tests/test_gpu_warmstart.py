@@ -27,6 +27,79 @@ def _rel(a, b):
     return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30)
 
 
+@pytest.mark.parametrize("cin,cout,flip,dims", [
+    (16, 16, 0, (5, 11, 30)),     # brick kernel: ragged tiles in every axis
+    (4, 16, 0, (6, 8, 14)),       # 4 input channels (zero-padded to 16)
+    (32, 64, 1, (3, 9, 17)),      # data gradient (flipped taps, transposed weights)
+    (64, 32, 0, (2, 3, 29)),      # 4 channel pairs, fewer planes than a tile
+    (20, 24, 0, (4, 7, 15)),      # channels not a multiple of 16
+    (3, 5, 0, (4, 7, 9)),         # channels not a multiple of 4: the im2col kernel
+])
+def test_conv3d_matches_reference(cin, cout, flip, dims):
+    """One 3x3x3 convolution through cs_nn_pack_weights / cs_nn_conv3d against the FP64
+    reference on the same BF16 operands, written into a channel slice of a wider output."""
+    import ctypes
+    import paper_2305_06482_gb300 as cs
+    import paper_2305_06482_gb300.warmstart as ws
+    rng = np.random.default_rng(cin * 100 + cout)
+    x = rng.standard_normal(dims + (cin,)).astype(np.float32)
+    # layer weights [co][27][ci]; the data gradient convolves with the layer whose output has cin channels
+    w = (rng.standard_normal((cin, 27, cout) if flip else (cout, 27, cin)) * 0.2).astype(np.float32)
+    b = None if flip else rng.standard_normal(cout).astype(np.float32)
+    if flip:
+        wr = cnn._r(w, True)
+        gp = np.pad(cnn._r(x, True), ((1, 1), (1, 1), (1, 1), (0, 0)))
+        ref = np.zeros(dims + (cout,))
+        for t, (dz, dy, dx) in enumerate(cnn.taps()):
+            ref += gp[1 - dz:1 - dz + dims[0], 1 - dy:1 - dy + dims[1], 1 - dx:1 - dx + dims[2]] @ wr[:, t, :]
+    else:
+        ref = np.maximum(cnn.conv3d(x, w, b, bf16=True), 0.0)
+    npad = ws._npad(cout)
+    kpad = ws._kpad(27 * cin)
+    wt = torch.from_numpy(w).cuda()
+    packed = torch.empty((npad, kpad), dtype=torch.int16, device="cuda")
+    rows, cols = (cout, cin) if not flip else (cin, cout)    # cs_nn_pack_weights takes the layer's (cout, cin)
+    cs._check(cs.lib().cs_nn_pack_weights(cs._ptr(wt), rows, cols, int(flip), cs._ptr(packed), npad, kpad, None))
+    ldo, coff = cout + 8, 4
+    out = torch.full((int(np.prod(dims)), ldo), 7.0, device="cuda")
+    xt = torch.from_numpy(x.reshape(-1, cin)).cuda()
+    bt = None if b is None else torch.from_numpy(b).cuda()
+    cs._check(cs.lib().cs_nn_conv3d(cs._ptr(xt), *dims, cin, cs._ptr(packed), npad, kpad, cout, cs._ptr(bt),
+                                    0 if flip else 1, int(flip), cs._ptr(out), ldo, coff, None))
+    cs._check(cs.lib().cs_nn_status(None))
+    o = out.cpu().numpy()
+    assert np.all(o[:, :coff] == 7.0) and np.all(o[:, coff + cout:] == 7.0)
+    got = o[:, coff:coff + cout].reshape(ref.shape)
+    assert _rel(got, ref) < 1e-5
+
+
+def test_upconv_and_slice_general_paths():
+    """The transposed convolution and the channel slice on channel counts and offsets that are not
+    multiples of 4 (their scalar paths), against the reference and numpy."""
+    import paper_2305_06482_gb300 as cs
+    rng = np.random.default_rng(5)
+    cd = (3, 5, 7)
+    cin, cout, ldo, coff = 3, 5, 9, 1
+    x = rng.standard_normal(cd + (cin,)).astype(np.float32)
+    w = rng.standard_normal((cout, 8, cin)).astype(np.float32)
+    b = rng.standard_normal(cout).astype(np.float32)
+    Vf = 8 * int(np.prod(cd))
+    out = torch.full((Vf, ldo), 3.0, device="cuda")
+    xt, wt, bt = (torch.from_numpy(a).cuda() for a in (x.reshape(-1, cin), w, b))
+    cs._check(cs.lib().cs_nn_upconv2(cs._ptr(xt), *cd, cin, cs._ptr(wt), cs._ptr(bt), cout, cs._ptr(out), ldo, coff,
+                                     None))
+    o = out.cpu().numpy()
+    ref = cnn.upconv2(x, w, b).reshape(Vf, cout)
+    assert _rel(o[:, coff:coff + cout], ref) < 1e-6
+    assert np.all(o[:, :coff] == 3.0) and np.all(o[:, coff + cout:] == 3.0)
+    src = torch.from_numpy(rng.standard_normal((Vf, 6)).astype(np.float32)).cuda()
+    before = out.clone()
+    cs._check(cs.lib().cs_nn_slice(cs._ptr(src), 6, 2, 3, cs._ptr(out), ldo, 5, Vf, 1, None))
+    exp = before.cpu().numpy()
+    exp[:, 5:8] += src.cpu().numpy()[:, 2:5]
+    assert np.array_equal(out.cpu().numpy(), exp)
+
+
 def test_network_forward_backward_match_reference():
     """Every layer against the FP64 reference on the GPU's own inputs to that layer (tight: only
     the FP32 accumulation differs), the wiring between layers exactly, and the whole network end
