@@ -1,4 +1,4 @@
-// Building blocks of the learned warm start: a small 3D CNN that maps (x^t, d) of a sketched
+// Building blocks of the learned warm start: a 3D U-Net that maps (x^t, d) of a sketched
 // sub-problem (Eq. 9-10) to a correction of x^t.  Activations are voxel-major with channels
 // fastest ([nz][ny][nx][C], FP32); 3x3x3 convolutions (zero padding 1, stride 1) run as BF16
 // implicit GEMMs on the tensor cores with FP32 accumulation in tensor memory:
@@ -6,7 +6,8 @@
 //             (GEMM M = 128 voxels, N = C_out padded to 16/32/64, K = 27 C_in padded to 16)
 //   data gradient: the same kernel with the taps flipped and the weights transposed,
 //             gin[v][ci] = sum_{tap, co} gout[v - off(tap)][co] w[co][tap][ci]
-// Weight gradients, the 1x1x1 output layer, ReLU masks, the loss and Adam run on CUDA cores.
+// Max-pools, stride-2 transposed convolutions, channel slices (skip concatenation), weight
+// gradients, the 1x1x1 output layer, ReLU masks, the loss and Adam run on CUDA cores.
 #include <cstdio>
 
 #include "cs_internal.cuh"
