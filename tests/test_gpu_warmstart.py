@@ -71,6 +71,18 @@ def test_conv3d_matches_reference(cin, cout, flip, dims):
     assert np.all(o[:, :coff] == 7.0) and np.all(o[:, coff + cout:] == 7.0)
     got = o[:, coff:coff + cout].reshape(ref.shape)
     assert _rel(got, ref) < 1e-5
+    if not flip:
+        # weight gradient of the same layer for a random output gradient (register-tiled kernel
+        # when both channel counts are multiples of 4, else the per-pair kernel)
+        go = rng.standard_normal(dims + (cout,)).astype(np.float32)
+        _, gw_ref, gb_ref = cnn.conv3d_bwd(x, w, go, bf16=True)
+        gw = torch.zeros((cout, 27, cin), device="cuda")
+        gb = torch.zeros(cout, device="cuda")
+        got = torch.from_numpy(go.reshape(-1, cout)).cuda()
+        cs._check(cs.lib().cs_nn_conv3d_wgrad(cs._ptr(xt), cs._ptr(got), *dims, cin, cout, cs._ptr(gw), cs._ptr(gb),
+                                              None))
+        assert _rel(gw.cpu().numpy(), gw_ref) < 1e-5
+        assert _rel(gb.cpu().numpy(), gb_ref) < 1e-5
 
 
 def test_upconv_and_slice_general_paths():
