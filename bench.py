@@ -54,6 +54,14 @@ def nufft_model_bytes(w, C):
     return 2 * C * (8 * D + 48 * G + 8 * N) + 2 * (16 * N + 16 * D)
 
 
+def nufft_compulsory_bytes(w, C):
+    """Compulsory bytes of one multicoil forward + adjoint (maps and samples once per coil and
+    direction, trajectory + dcf, image in and out): C (8D + 8N) 2 + 16N + 16D."""
+    D = int(np.prod(w["img"]))
+    N = w["n_int"] * w["n_read"]
+    return C * (8 * D + 8 * N) * 2 + 16 * N + 16 * D
+
+
 # ------------------------------------------------------------------------------------------
 def sample_clocks_start(out_path, dev_index):
     cmd = ["nvidia-smi", f"--id={dev_index}",
@@ -319,7 +327,9 @@ def run_native(args, w, rank, world, local_rank):
                 "bytes_per_launch": per_launch_bytes,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
                 "nufft_fwd_adj_gbs": op_gbs, "nufft_fwd_adj_frac": op_gbs / hbm_peak,
-                "nufft_fwd_adj_ms": op_ms, "stage_ms": {k: v[0] / args.steps for k, v in prof.items()}}
+                "nufft_fwd_adj_ms": op_ms, "nufft_fwd_adj_model_gb": nufft_model_bytes(w, C) / 1e9,
+                "nufft_fwd_adj_compulsory_gb": nufft_compulsory_bytes(w, C) / 1e9,
+                "stage_ms": {k: v[0] / args.steps for k, v in prof.items()}}
 
     # end to end: pinned host inputs -> device, recon through the C ABI, result back to the host
     y_h = y.to("cpu").pin_memory()
