@@ -353,7 +353,10 @@ cs_status cs_power_iteration(const cs_plan* plan, const float* v0, const float* 
  *   cs_nn_upconv2_bwd: gin[v][ci] = sum_{a, co} gout[child a][goff + co] w[co][a][ci] (if gin),
  *   gw[co][a][ci] += sum_v gout[child a][goff + co] in[v][ci] and gb += sum gout (if gw).
  * cs_nn_slice: dst[v][doff + j] (+)= src[v][soff + j] for j < n (concatenation and its split).
- * cs_nn_conv3d_wgrad and cs_nn_upconv2_bwd take cin, cout <= 128.
+ * cs_nn_conv3d_wgrad and cs_nn_upconv2_bwd take cin, cout <= 128; cs_nn_upconv2 takes cin <= 1024
+ * (CS_ERR_UNSUPPORTED_SIZE above).  The 3x3x3 convolution reads a halo brick per tile when cin is
+ * a multiple of 4 and `in` is 16-byte aligned, else builds the im2col rows per voxel; both give
+ * the same result.
  * ---------------------------------------------------------------------------------------- */
 cs_status cs_nn_pack_weights(const float* w, int cout, int cin, int transpose, unsigned short* packed,
                              int npad, int kpad, void* stream);
