@@ -1,5 +1,8 @@
 """Pins for the Philox4x32-10 generator (published known-answer vectors of Salmon et al. 2011,
-Random123 distribution) and the sketch entry distributions (Sec. 3.2)."""
+Random123 distribution; fixture tests/golden/philox4x32_10_kat.txt) and the sketch entry
+distributions (Sec. 3.2)."""
+import os
+
 import numpy as np
 import pytest
 from scipy import stats
@@ -7,12 +10,19 @@ from scipy import stats
 from oracle import philox
 
 
-@pytest.mark.parametrize("ctr,key,want", [
-    ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
-    ((0xFFFFFFFF,) * 4, (0xFFFFFFFF, 0xFFFFFFFF), (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
-    ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
-     (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
-])
+def _kat():
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = []
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        w = [int(t, 16) for t in line.split()]
+        rows.append((tuple(w[0:4]), tuple(w[4:6]), tuple(w[6:10])))
+    return rows
+
+
+@pytest.mark.parametrize("ctr,key,want", _kat())
 def test_philox_known_answers(ctr, key, want):
     assert philox.philox4x32_10(ctr, key) == want
 
