@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -244,8 +245,7 @@ def run_native(args, w, rank, world, local_rank):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv"
+    clk_path = os.environ.get("CS_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(), f"cs_clocks_rank{rank}.csv")
     proc, fh = sample_clocks_start(clk_path, local_rank)
     cs.profile(True)
     launches0 = cs.launch_count()
