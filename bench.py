@@ -174,6 +174,7 @@ def run_native(args, w, rank, world, local_rank):
     import paper_2305_06482_gb300 as cs
     import synthdata
     from paper_2305_06482_gb300 import build as _build
+    from paper_2305_06482_gb300 import replicas
 
     if not os.path.exists(cs.LIB_PATH):
         _build.build()
@@ -188,7 +189,7 @@ def run_native(args, w, rank, world, local_rank):
 
     img, grid, C = w["img"], w["grid"], w["nc"]
     m = w["V"] + w["S"]
-    seed = w["seed"] + 17 * rank
+    seed = replicas.replica_seed(w["seed"], rank)
     t_setup = time.perf_counter()
     traj = synthdata.cones_trajectory(w["n_int"], w["n_read"])
     dcf = synthdata.cones_dcf(traj, img, w["n_int"], w["n_read"])
@@ -265,12 +266,9 @@ def run_native(args, w, rank, world, local_rank):
     prof = {k: cs.profile_read(k) for k in cs.STAGES}
     cs.profile(False)
     clocks = sample_clocks_stop(proc, fh, clk_path)
-    if dist:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = replicas.slowest_ms(ms_total, dist, dev)
     ms_step = ms_total / args.steps
-    value = ms_total / 1e3 / (args.steps * world)           # seconds per recon, whole job
+    value = replicas.seconds_per_recon(ms_total, args.steps, world)   # seconds per recon, whole job
     nrmse_timed = nrmse(x_last, x_inf)
 
     # plain full-coil solver for the same NRMSE (k_star iterations), timed
