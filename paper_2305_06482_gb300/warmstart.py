@@ -137,7 +137,8 @@ class WarmNet:
         d1 = tuple(dims)
         d2 = tuple(v // 2 for v in d1)
         d3 = tuple(v // 2 for v in d2)
-        assert all(v % 4 == 0 for v in d1), "U-Net volume sizes must be divisible by 4"
+        if any(v % 4 for v in d1):
+            raise ValueError(f"U-Net volume sizes must be divisible by 4, got {d1}")
         V1, V2 = d1[0] * d1[1] * d1[2], d2[0] * d2[1] * d2[2]
         a = {"f": feat}
         a["e1a"] = self._conv(feat, d1, 0, 4, c1, stream)
