@@ -390,6 +390,39 @@ cs_status cs_nn_slice(const float* src, int lds, int soff, int n, float* dst, in
                       int accumulate, void* stream);
 
 /* ------------------------------------------------------------------------------------------
+ * The warm-start network as a library object (built from the pieces above; not in the paper).
+ * ws_net_create: a U-Net of widths c1/c2/c3 (multiples of 4, c1, c2 <= 32, c3 <= 64; the
+ *   survey's 16/32/64), He-normal weights from a Mersenne twister seeded by `seed` (Box-Muller),
+ *   zero biases and zero Adam state, on the current device.  The handle owns all its device
+ *   memory (parameters, gradients, Adam moments, packed BF16 weights, activation buffers sized
+ *   for the last volume) and ws_net_destroy frees it.
+ * ws_net_infer: xhat = x^t + s U-Net([x^t / s, eta d / s]) with s the RMS of (x^t, eta d); xt,
+ *   d, xhat complex64 [nz][ny][nx] device arrays, dims = {nz, ny, nx} on the host, each a
+ *   positive multiple of 4 (else CS_ERR_UNSUPPORTED_SIZE).  Asynchronous on `stream`.
+ * ws_net_train_step: one Adam step (lr; beta 0.9 / 0.999, eps 1e-8) on the mean squared error
+ *   between the network output and (x_target - x^t) / s for one volume (x_target: complex64,
+ *   the sub-problem solved tightly from x^t); `loss` (device float, nullable) receives the loss
+ *   before the step.  Asynchronous on `stream`.
+ * ws_net_param: parameter `index` (0..25: the (w, b) pairs of e1a, e1b, e2a, e2b, b1, b2,
+ *   u2, d2a, d2b, u1, d1a, d1b, out; w [cout][27][cin], [cout][8][cin] or [2][c1]) of array
+ *   `which` (0 parameters, 1 last gradients, 2 / 3 Adam first / second moments): copied from
+ *   the device array `src` when non-null, then to `dst` when non-null; *numel receives its size.
+ * ws_net_save / ws_net_load: parameters, Adam moments and step count in a binary file (magic
+ *   "CSUNET1", widths, step, then every array); loading checks the widths.  Synchronous.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct cs_unet cs_unet;
+cs_status ws_net_create(int c1, int c2, int c3, uint64_t seed, cs_unet** out);
+cs_status ws_net_destroy(cs_unet* net);
+cs_status ws_net_infer(cs_unet* net, const float* xt, const float* d, const int* dims, float eta, float* xhat,
+                       void* stream);
+cs_status ws_net_train_step(cs_unet* net, const float* xt, const float* d, const float* target, const int* dims,
+                            float eta, float lr, float* loss, void* stream);
+cs_status ws_net_param(cs_unet* net, int which, int index, const float* src, float* dst, int64_t* numel,
+                       void* stream);
+cs_status ws_net_save(cs_unet* net, const char* path);
+cs_status ws_net_load(cs_unet* net, const char* path);
+
+/* ------------------------------------------------------------------------------------------
  * Regulariser building blocks (Sec. 2.1, l1-wavelets with a unitary Psi), exposed for testing:
  * periodised orthonormal db4 analysis/synthesis over all axes of an image, `levels` levels,
  * Mallat corner layout, and the complex soft threshold z max(0, 1 - tau/|z|).

@@ -78,6 +78,8 @@ EXPORTED = [
     "cs_nn_conv3d", "cs_nn_conv3d_wgrad", "cs_nn_relu_bwd", "cs_nn_conv1", "cs_nn_conv1_bwd", "cs_nn_mse",
     "cs_nn_adam", "cs_nn_features", "cs_nn_target", "cs_nn_apply", "cs_nn_status", "tv_dual_update", "tv_rhs",
     "cs_nn_maxpool2", "cs_nn_maxpool2_bwd", "cs_nn_upconv2", "cs_nn_upconv2_bwd", "cs_nn_slice",
+    "ws_net_create", "ws_net_destroy", "ws_net_infer", "ws_net_train_step", "ws_net_param", "ws_net_save",
+    "ws_net_load",
 ]
 STAGES = {"spread": 0, "interp": 1, "fft_plain": 2, "expand": 3, "reduce": 4}
 
@@ -126,6 +128,11 @@ def lib():
             "cs_nn_upconv2_bwd": ([vp, vp, i, i, i, i, i, i, vp, i, vp, vp, vp, vp], i),
             "cs_nn_slice": ([vp, i, i, i, vp, i, i, i64, i, vp], i),
             "tv_rhs": ([vp, vp, vp, i, vp, f, vp, vp, vp], i),
+            "ws_net_create": ([i, i, i, u64, vp], i), "ws_net_destroy": ([vp], i),
+            "ws_net_infer": ([vp, vp, vp, vp, f, vp, vp], i),
+            "ws_net_train_step": ([vp, vp, vp, vp, vp, f, f, vp, vp], i),
+            "ws_net_param": ([vp, i, i, vp, vp, vp, vp], i),
+            "ws_net_save": ([vp, ctypes.c_char_p], i), "ws_net_load": ([vp, ctypes.c_char_p], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)

@@ -402,42 +402,15 @@ def _bf16_peak():
 
 
 def warmnet(args):
+    import ctypes
     import paper_2305_06482_gb300.warmstart as ws
     img = CONFIGS[args.config]["img"]
     dev = torch.device("cuda")
     gen = torch.Generator(device=dev).manual_seed(0)
-    net = ws.WarmNet(seed=0)
-    net.pack()
+    L = cs.lib()
     peak, src = _bf16_peak()
     c1, c2, c3 = ws.WIDTHS
     lv = [tuple(img), tuple(v // 2 for v in img), tuple(v // 4 for v in img)]
-    total_flops = 0.0
-    print(f"warm-start U-Net on {img}: tensor-core convolutions (FLOPs 2 V 27 cin cout; peak bf16 {peak:.0f} "
-          f"TFLOP/s, {src})")
-    for pi, kind, cin, cout in net.layers:
-        if kind != "conv":
-            continue
-        level = {0: 0, 2: 0, 4: 1, 6: 1, 8: 2, 10: 2, 14: 1, 16: 1, 20: 0, 22: 0}[pi]
-        dims = lv[level]
-        V = int(np.prod(dims))
-        x = torch.randn((V, cin), generator=gen, device=dev)
-        out = torch.empty((V, cout), device=dev)
-        for _ in range(args.warmup):
-            net._conv(x, dims, pi, cin, cout, None, out=out, ldo=cout)
-        a, b = _events()
-        a.record()
-        for _ in range(args.iters):
-            net._conv(x, dims, pi, cin, cout, None, out=out, ldo=cout)
-        b.record()
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / args.iters
-        fl = 2.0 * V * 27 * cin * cout
-        total_flops += fl
-        print(f"  layer {pi:2d} {cin:2d}->{cout:2d} on {dims}: {ms:.3f} ms, {fl / ms / 1e9:.1f} TFLOP/s "
-              f"({fl / ms / 1e9 / peak:.3f} of peak)")
-        del x, out
-    # the CUDA-core layers of the forward pass
-    L = cs.lib()
 
     def timed(fn):
         for _ in range(args.warmup):
@@ -450,64 +423,76 @@ def warmnet(args):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / args.iters
 
-    for pi, cdims, cin, cout in ((12, lv[2], c3, c2), (18, lv[1], c2, c1)):
+    total_flops = 0.0
+    print(f"warm-start U-Net on {img}: tensor-core convolutions (FLOPs 2 V 27 cin cout; peak bf16 {peak:.0f} "
+          f"TFLOP/s, {src})")
+    for name, level, cin, cout in (("e1a", 0, 4, c1), ("e1b", 0, c1, c1), ("e2a", 1, c1, c2), ("e2b", 1, c2, c2),
+                                   ("b1", 2, c2, c3), ("b2", 2, c3, c3), ("d2a", 1, 2 * c2, c2), ("d2b", 1, c2, c2),
+                                   ("d1a", 0, 2 * c1, c1), ("d1b", 0, c1, c1)):
+        dims = lv[level]
+        V = int(np.prod(dims))
+        npad, kpad = (16 if cout <= 16 else 32 if cout <= 32 else 64), (27 * cin + 15) // 16 * 16
+        w = torch.randn((cout, 27, cin), generator=gen, device=dev) * 0.1
+        bias = torch.zeros(cout, device=dev)
+        packed = torch.empty((npad, kpad), dtype=torch.int16, device=dev)
+        cs._check(L.cs_nn_pack_weights(cs._ptr(w), cout, cin, 0, cs._ptr(packed), npad, kpad, None))
+        x = torch.randn((V, cin), generator=gen, device=dev)
+        out = torch.empty((V, cout), device=dev)
+        ms = timed(lambda: cs._check(L.cs_nn_conv3d(cs._ptr(x), *dims, cin, cs._ptr(packed), npad, kpad, cout,
+                                                    cs._ptr(bias), 1, 0, cs._ptr(out), cout, 0, None)))
+        fl = 2.0 * V * 27 * cin * cout
+        total_flops += fl
+        print(f"  layer {name:3s} {cin:2d}->{cout:2d} on {dims}: {ms:.3f} ms, {fl / ms / 1e9:.1f} TFLOP/s "
+              f"({fl / ms / 1e9 / peak:.3f} of peak)")
+        del x, out
+    for cdims, cin, cout in ((lv[2], c3, c2), (lv[1], c2, c1)):
         Vc = int(np.prod(cdims))
         x = torch.randn((Vc, cin), generator=gen, device=dev)
+        w = torch.randn((cout, 8, cin), generator=gen, device=dev) * 0.1
+        bias = torch.zeros(cout, device=dev)
         cat = torch.empty((8 * Vc, 2 * cout), device=dev)
-        ms = timed(lambda: net._up(x, cdims, pi, cin, cout, cat, 2 * cout, None))
+        ms = timed(lambda: cs._check(L.cs_nn_upconv2(cs._ptr(x), *cdims, cin, cs._ptr(w), cs._ptr(bias), cout,
+                                                     cs._ptr(cat), 2 * cout, 0, None)))
         byt = 4.0 * (Vc * cin + 8 * Vc * cout)
         print(f"  transposed conv {cin}->{cout} to {tuple(2 * v for v in cdims)}: {ms:.3f} ms, {byt / ms / 1e6:.0f} GB/s")
-        src = torch.randn((8 * Vc, cout), generator=gen, device=dev)
-        ms = timed(lambda: net._slice(src, cout, 0, cout, cat, 2 * cout, cout, 8 * Vc, False, None))
+        srcs = torch.randn((8 * Vc, cout), generator=gen, device=dev)
+        ms = timed(lambda: cs._check(L.cs_nn_slice(cs._ptr(srcs), cout, 0, cout, cs._ptr(cat), 2 * cout, cout, 8 * Vc,
+                                                   0, None)))
         print(f"  skip copy of {cout} channels: {ms:.3f} ms, {8.0 * 8 * Vc * cout / ms / 1e6:.0f} GB/s")
-        del x, cat, src
+        del x, cat, srcs
     for dims, C in ((lv[0], c1), (lv[1], c2)):
         V = int(np.prod(dims))
         x = torch.randn((V, C), generator=gen, device=dev)
-        ms = timed(lambda: net._pool(x, dims, C, None))
+        po = torch.empty((V // 8, C), device=dev)
+        pi = torch.empty((V // 8, C), dtype=torch.uint8, device=dev)
+        cd = tuple(v // 2 for v in dims)
+        ms = timed(lambda: cs._check(L.cs_nn_maxpool2(cs._ptr(x), *cd, C, cs._ptr(po), cs._ptr(pi), None)))
         print(f"  max-pool of {C} channels on {dims}: {ms:.3f} ms, {4.0 * V * C * (1 + 1 / 8 + 1 / 32) / ms / 1e6:.0f} GB/s")
-        del x
+        del x, po, pi
     x = torch.randn((int(np.prod(lv[0])), c1), generator=gen, device=dev)
+    w = torch.randn((2, c1), generator=gen, device=dev)
+    bias = torch.zeros(2, device=dev)
     y = torch.empty((x.shape[0], 2), device=dev)
-    ms = timed(lambda: cs._check(L.cs_nn_conv1(cs._ptr(x), x.shape[0], c1, 2, cs._ptr(net.params[24]),
-                                               cs._ptr(net.params[25]), cs._ptr(y), None)))
+    ms = timed(lambda: cs._check(L.cs_nn_conv1(cs._ptr(x), x.shape[0], c1, 2, cs._ptr(w), cs._ptr(bias), cs._ptr(y),
+                                               None)))
     print(f"  1x1x1 output layer {c1}->2: {ms:.3f} ms, {4.0 * x.shape[0] * (c1 + 2) / ms / 1e6:.0f} GB/s")
     del x, y
-    V1 = int(np.prod(img))
-    f = torch.randn((V1, 4), generator=gen, device=dev)
-    for _ in range(args.warmup):
-        net.forward(f, img)
-    a, b = _events()
-    a.record()
-    for _ in range(args.iters):
-        net.forward(f, img)
-    b.record()
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / args.iters
+    # the library's network object: one inference on the image size, one training step on a 64^3 crop
+    net = ws.UNet(seed=0)
+    cplx = lambda shape: torch.complex(torch.randn(shape, generator=gen, device=dev),
+                                       torch.randn(shape, generator=gen, device=dev))
+    xt, d = cplx(img), cplx(img)
+    xh = torch.empty_like(xt)
+    ms = timed(lambda: net.infer(xt, d, 0.5, out=xh))
     print(f"  inference (whole U-Net, {total_flops / 1e12:.2f} TFLOP in the 3x3x3 layers): {ms:.2f} ms, "
           f"{total_flops / ms / 1e9:.1f} TFLOP/s")
-    del f
+    del xt, d, xh
     crop = (64, 64, 64)
-    Vc = int(np.prod(crop))
-    fc = torch.randn((Vc, 4), generator=gen, device=dev)
-    tg = torch.randn((Vc, 2), generator=gen, device=dev)
-
-    def step():
-        o = net.forward(fc, crop, keep=True)
-        _, g = net.loss_and_grad(o, tg)
-        net.backward(g, crop)
-        net.adam(lr=1e-4)
-
-    for _ in range(args.warmup):
-        step()
-    a, b = _events()
-    a.record()
-    for _ in range(args.iters):
-        step()
-    b.record()
-    torch.cuda.synchronize()
-    print(f"  training step on a 64^3 crop (forward, backward, Adam): {a.elapsed_time(b) / args.iters:.2f} ms")
-    cs._check(cs.lib().cs_nn_status(None))
+    xc, dc, tc = cplx(crop), cplx(crop), cplx(crop)
+    ms = timed(lambda: net.train_step(xc, dc, tc, 0.5, 1e-5))
+    print(f"  training step on a 64^3 crop (forward, backward, Adam): {ms:.2f} ms")
+    cs._check(L.cs_nn_status(None))
+    net.close()
 
 
 def main():

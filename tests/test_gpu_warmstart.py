@@ -24,7 +24,10 @@ def _net_params(net):
 
 
 def _rel(a, b):
-    return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30)
+    a, b = np.asarray(a), np.asarray(b)
+    dt = np.complex128 if np.iscomplexobj(a) or np.iscomplexobj(b) else np.float64
+    a, b = a.astype(dt), b.astype(dt)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
 @pytest.mark.parametrize("cin,cout,flip,dims", [
@@ -40,7 +43,7 @@ def test_conv3d_matches_reference(cin, cout, flip, dims):
     reference on the same BF16 operands, written into a channel slice of a wider output."""
     import ctypes
     import paper_2305_06482_gb300 as cs
-    import paper_2305_06482_gb300.warmstart as ws
+    from tests._unet_layers import _kpad, _npad
     rng = np.random.default_rng(cin * 100 + cout)
     x = rng.standard_normal(dims + (cin,)).astype(np.float32)
     # layer weights [co][27][ci]; the data gradient convolves with the layer whose output has cin channels
@@ -54,8 +57,8 @@ def test_conv3d_matches_reference(cin, cout, flip, dims):
             ref += gp[1 - dz:1 - dz + dims[0], 1 - dy:1 - dy + dims[1], 1 - dx:1 - dx + dims[2]] @ wr[:, t, :]
     else:
         ref = np.maximum(cnn.conv3d(x, w, b, bf16=True), 0.0)
-    npad = ws._npad(cout)
-    kpad = ws._kpad(27 * cin)
+    npad = _npad(cout)
+    kpad = _kpad(27 * cin)
     wt = torch.from_numpy(w).cuda()
     packed = torch.empty((npad, kpad), dtype=torch.int16, device="cuda")
     rows, cols = (cout, cin) if not flip else (cin, cout)    # cs_nn_pack_weights takes the layer's (cout, cin)
@@ -120,11 +123,12 @@ def test_network_forward_backward_match_reference():
     BF16 ulp (2^-8 relative) and the differences grow layer by layer (ten 3x3x3 layers deep), so
     that comparison only bounds the result to a few BF16 ulps."""
     import paper_2305_06482_gb300.warmstart as ws
+    from tests._unet_layers import LayeredUNet
     c1, c2, c3 = ws.WIDTHS
     d1 = (8, 12, 20)
     d2 = tuple(v // 2 for v in d1)
     d3 = tuple(v // 2 for v in d2)
-    net = ws.WarmNet(seed=3)
+    net = LayeredUNet(seed=3)
     assert [tuple(p.shape) for p in net.params] == cnn.unet_shapes(*ws.WIDTHS)
     # non-trivial biases and output layer, from a generator of the test's own (the global one's
     # state depends on which tests ran before)
@@ -206,6 +210,68 @@ def test_network_forward_backward_match_reference():
         net.forward(ft[: 6 * 12 * 20].contiguous(), (6, 12, 20))
 
 
+def test_library_network_matches_layered_sequence(tmp_path):
+    """The library's network object (ws_net_*) against the same kernels sequenced layer by layer
+    from Python: inference, one training step (loss, gradients, Adam update), save / load, and
+    the size checks."""
+    import paper_2305_06482_gb300 as cs
+    import paper_2305_06482_gb300.warmstart as ws
+    from tests._unet_layers import LayeredUNet
+    dims = (8, 12, 20)
+    ref = LayeredUNet(seed=3)
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    for i in range(1, 26, 2):
+        ref.params[i].normal_(0, 0.05, generator=gen)
+    net = ws.UNet(seed=5)
+    for i, p in enumerate(ref.params):
+        net.set_param(i, p.reshape(-1))
+    rng = np.random.default_rng(4)
+    cplx = lambda: torch.from_numpy((rng.standard_normal(dims) + 1j * rng.standard_normal(dims)).astype(np.complex64)).cuda()
+    xt, d, xs = cplx(), cplx(), cplx()
+    eta = 0.7
+    xhat = net.infer(xt, d, eta)
+    f, ss = ws.features(xt, d, eta)
+    xh_ref = ws.apply(xt, ref.forward(f, dims), ss)
+    # same kernels in the same order; only the atomically summed normaliser s can differ in its
+    # last bits
+    assert _rel(xhat.cpu().numpy(), xh_ref.cpu().numpy()) < 1e-6
+    before = [net.param(i).cpu().numpy() for i in range(26)]
+    loss = float(net.train_step(xt, d, xs, eta, 1e-3).item())
+    out = ref.forward(f, dims, keep=True)
+    lref, g = ref.loss_and_grad(out, ws.target(xt, xs, ss))
+    ref.backward(g, dims)
+    ref.adam(lr=1e-3)
+    assert abs(loss - float(lref.item())) <= 1e-5 * abs(float(lref.item()))
+    for i in range(26):
+        gr = ref.grads[i].reshape(-1).cpu().numpy()
+        assert _rel(net.param(i, which=1).cpu().numpy(), gr) < 1e-4, i
+        step_n = net.param(i).cpu().numpy() - before[i]
+        step_r = ref.params[i].reshape(-1).cpu().numpy() - before[i]
+        # Adam's first step is about lr * sign(g): equal wherever the gradient is clearly nonzero;
+        # a component whose gradient is ~0 may take the other sign (the sums are atomic)
+        assert np.abs(step_n - step_r).max() <= 2.1e-3, i
+        gmax = np.abs(gr).max()
+        if gmax > 0:
+            big = np.abs(gr) > 1e-3 * gmax
+            assert np.abs(step_n - step_r)[big].max() <= 1e-6, i
+    path = tmp_path / "unet.bin"
+    net.save(path)
+    other = ws.UNet(seed=9)
+    other.load(path)
+    for i in range(26):
+        for which in (0, 2, 3):
+            assert torch.equal(other.param(i, which), net.param(i, which)), (i, which)
+    assert torch.equal(other.infer(xt, d, eta), net.infer(xt, d, eta)) or \
+        _rel(other.infer(xt, d, eta).cpu().numpy(), net.infer(xt, d, eta).cpu().numpy()) < 1e-6
+    with pytest.raises(cs.CoilSketchError):
+        net.infer(xt[:6].contiguous(), d[:6].contiguous(), eta)       # 6 is not a multiple of 4
+    with pytest.raises(cs.CoilSketchError):
+        ws.UNet(seed=0, widths=(8, 16, 32)).load(path)                 # widths differ
+    with pytest.raises(cs.CoilSketchError):
+        ws.UNet(seed=0, widths=(16, 64, 64))                           # concatenation too wide
+    cs._check(cs.lib().cs_nn_status(None))
+
+
 def _problem(seed, img=(32, 48, 48), grid=(40, 60, 60), C=8, n_int=1500, n_read=128):
     import paper_2305_06482_gb300 as cs
     dev = torch.device("cuda")
@@ -230,8 +296,8 @@ def test_training_and_warm_start_in_algorithm_1():
         su = ws.setup(plan, y, maps, lam, V, S, T, seed, synthdata.phantom_torch(img, seed=seed + 50), levels)
         _, pr, _ = ws.run(su, T, K, record_pairs=1, tight_K=40)
         pairs += pr
-    net = ws.WarmNet(seed=0)
-    hist = ws.train(net, pairs, img, steps=300, lr=2e-3)
+    net = ws.UNet(seed=0)
+    hist = ws.train(net, pairs, steps=300, lr=2e-3)
     first, last = np.mean(hist[:20]), np.mean(hist[-20:])
     assert last < first, (first, last)
     # held-out phantom: convergence with and without the warm start
