@@ -1,6 +1,6 @@
 """One rank of the world-size-2 replica test (launched by torchrun with the gloo backend on CPU):
-combines a rank-dependent duration, checks the reference arm's rank rule and prints one JSON
-line per rank."""
+combines a rank-dependent duration, checks the reference arm's rank rule and writes one JSON
+file per rank into $CS_REPLICA_OUT."""
 import json
 import os
 import sys
@@ -34,8 +34,9 @@ def main():
             bench.run_reference(None, dict(bench.WORKLOAD), rank, world)
         ref_silent = buf.getvalue() == ""
     dist.barrier()
-    print(json.dumps({"rank": rank, "world": world, "slowest_ms": ms, "value": value, "seeds": seeds,
-                      "ref_silent": ref_silent}), flush=True)
+    with open(os.path.join(os.environ["CS_REPLICA_OUT"], f"rank{rank}.json"), "w") as fh:
+        json.dump({"rank": rank, "world": world, "slowest_ms": ms, "value": value, "seeds": seeds,
+                   "ref_silent": ref_silent}, fh)
     dist.destroy_process_group()
 
 

@@ -3,27 +3,19 @@ Each rank keeps its own duration; the job's time is the slowest rank's, the thro
 every rank's reconstructions, seeds differ per rank, and the reference arm runs on rank 0 only."""
 import json
 import os
-import socket
 import subprocess
 import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _free_port():
-    with socket.socket() as s:
-        s.bind(("127.0.0.1", 0))
-        return s.getsockname()[1]
-
-
-def test_two_rank_replicas_with_gloo():
-    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node=2",
-           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
-           os.path.join(ROOT, "tests", "_replica_worker.py")]
-    env = dict(os.environ, OMP_NUM_THREADS="1")
+def test_two_rank_replicas_with_gloo(tmp_path):
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--standalone", "--local-addr", "127.0.0.1",
+           "--nnodes=1", "--nproc-per-node=2", os.path.join(ROOT, "tests", "_replica_worker.py")]
+    env = dict(os.environ, OMP_NUM_THREADS="1", CS_REPLICA_OUT=str(tmp_path))
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
-    lines = [json.loads(t) for t in r.stdout.splitlines() if t.startswith("{")]
+    lines = [json.loads(open(tmp_path / f"rank{k}.json").read()) for k in range(2)]
     assert sorted(d["rank"] for d in lines) == [0, 1]
     for d in lines:
         assert d["world"] == 2
