@@ -335,14 +335,20 @@ def run_native(args, w, rank, world, local_rank):
     x_h = torch.empty(img, dtype=torch.complex64).pin_memory()
     y_d = torch.empty_like(y)
     maps_d = torch.empty_like(maps)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
+
+    def e2e_step():
         y_d.copy_(y_h, non_blocking=True)
         maps_d.copy_(maps_h, non_blocking=True)
         xo, _ = cs.recon_solve(plan, y_d, maps_d, w["lam"], cs.REG_L1_WAVELET, params_t, wavelet_levels=w["levels"])
         x_h.copy_(xo, non_blocking=True)
         torch.cuda.synchronize()
+
+    # one untimed step: the outer-iteration graph is captured for these buffers once, as for the
+    # device-resident runs above
+    e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
     e2e_s = (time.perf_counter() - t0) / args.steps
     h2d = y.numel() * 8 + maps.numel() * 8
     d2h = int(np.prod(img)) * 8
