@@ -386,6 +386,10 @@ cs_status cs_nn_upconv2(const float* in, int nz, int ny, int nx, int cin, const 
                         int cout, float* out, int ldo, int coff, void* stream);
 cs_status cs_nn_upconv2_bwd(const float* in, const float* gout, int ldg, int goff, int nz, int ny, int nx,
                             int cin, const float* w, int cout, float* gin, float* gw, float* gb, void* stream);
+/* cs_crop3d: dst = the box [origin, origin + box) of a complex64 volume src of size dims (host
+ * int[3] each, z, y, x); the box must lie inside the volume (CS_ERR_INVALID_ARG otherwise).  Used
+ * to train the warm start on crops of large volumes. */
+cs_status cs_crop3d(const float* src, const int* dims, const int* origin, const int* box, float* dst, void* stream);
 cs_status cs_nn_slice(const float* src, int lds, int soff, int n, float* dst, int ldd, int doff, int64_t nvox,
                       int accumulate, void* stream);
 

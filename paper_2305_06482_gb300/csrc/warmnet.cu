@@ -864,6 +864,18 @@ __global__ void slice_kernel(const float* __restrict__ src, int lds, int soff, i
     }
 }
 
+// box crop of a complex volume: dst[z][y][x] = src[oz + z][oy + y][ox + x] (the box lies inside src)
+__global__ void crop3d_kernel(const float2* __restrict__ src, int ny, int nx, int oz, int oy, int ox, int cz, int cy,
+                              int cx, float2* __restrict__ dst) {
+    const int64_t n = (int64_t)cz * cy * cx;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(e % cx);
+        const int64_t r = e / cx;
+        const int y = (int)(r % cy), z = (int)(r / cy);
+        dst[e] = src[((int64_t)(oz + z) * ny + (oy + y)) * nx + (ox + x)];
+    }
+}
+
 static int nn_grid(int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096));
 }
@@ -1156,6 +1168,20 @@ cs_status cs_nn_slice(const float* src, int lds, int soff, int n, float* dst, in
                     (reinterpret_cast<uintptr_t>(src) & 15) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
     slice_kernel<<<nn_grid(nvox * (vec ? n / 4 : n)), 256, 0, (cudaStream_t)stream>>>(src, lds, soff, n, dst, ldd, doff,
                                                                                     nvox, accumulate, vec);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status cs_crop3d(const float* src, const int* dims, const int* origin, const int* box, float* dst, void* stream) {
+    clear_error();
+    CS_REQUIRE(src && dims && origin && box && dst, CS_ERR_INVALID_ARG, "null pointer");
+    for (int a = 0; a < 3; ++a)
+        CS_REQUIRE(dims[a] >= 1 && box[a] >= 1 && origin[a] >= 0 && origin[a] + box[a] <= dims[a], CS_ERR_INVALID_ARG,
+                   "crop box [%d, %d) outside axis %d of size %d", origin[a], origin[a] + box[a], a, dims[a]);
+    const int64_t n = (int64_t)box[0] * box[1] * box[2];
+    crop3d_kernel<<<nn_grid(n), 256, 0, (cudaStream_t)stream>>>((const float2*)src, dims[1], dims[2], origin[0],
+                                                                origin[1], origin[2], box[0], box[1], box[2],
+                                                                (float2*)dst);
     CS_LAUNCH_CHECK();
     return CS_OK;
 }

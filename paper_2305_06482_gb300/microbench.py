@@ -37,6 +37,12 @@ stream), for profiling individual kernels with small launch counts.
       the warm-start U-Net (16/32/64 channels): every 3x3x3 convolution alone on random inputs of
       its shape (BF16 implicit GEMM on the tensor cores), one whole inference on the image size of
       the workload, and one training step (forward, backward, Adam) on a 64^3 crop
+  python -m paper_2305_06482_gb300.microbench warmtrain [--config cones3d_128] [--phantoms P] [--train-steps N]
+      the warm start trained as configured but smaller: training pairs (x^t, d, sub-problem
+      solved with 40 FISTA iterations) from Algorithm 1 on P seeded phantoms (l1-db4 lambda 2e-3,
+      m = 8 = 4 PCA + 4 Gaussian, T = 6, K = 4), N Adam steps on random 64^3 crops, then a
+      held-out phantom with and without the warm start: NRMSE to x_inf per outer iteration,
+      acceptances, device time per reconstruction
   python -m paper_2305_06482_gb300.microbench cart2d [--iters N]
       128x128 Cartesian coil-sketched CG reconstruction (8 coils, m = 4, T = 5, K = 10),
       eager launches vs a replayed CUDA graph
@@ -495,10 +501,66 @@ def warmnet(args):
     net.close()
 
 
+def warmtrain(args):
+    import paper_2305_06482_gb300.warmstart as ws
+    cfg = CONFIGS[args.config]
+    dev = torch.device("cuda")
+    img, grid, C = cfg["img"], cfg["grid"], cfg["nc"]
+    traj = synthdata.cones_trajectory(cfg["n_int"], 512)
+    dcf = synthdata.cones_dcf(traj, img, cfg["n_int"], 512)
+    plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=torch.from_numpy(traj).to(dev), dcf=torch.from_numpy(dcf).to(dev),
+                   grid=grid)
+    maps = synthdata.coil_maps_torch(img, C, device=dev)
+    lam, V, S, T, K, levels = 2e-3, 4, 4, 6, 4, 4
+    t0 = time.perf_counter()
+    pairs = []
+    for k in range(args.phantoms):
+        seed = 101 + k
+        y = cs.sense_fwd(plan, synthdata.phantom_torch(img, seed=seed, device=dev), maps)
+        su = ws.setup(plan, y, maps, lam, V, S, T, seed, synthdata.phantom_torch(img, seed=seed + 50, device=dev), levels)
+        _, pr, _ = ws.run(su, T, K, record_pairs=1, tight_K=40)
+        pairs += pr
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    net = ws.UNet(seed=0)
+    a, b = _events()
+    a.record()
+    hist = ws.train(net, pairs, steps=args.train_steps, lr=2e-3, crop=(64, 64, 64))
+    b.record()
+    torch.cuda.synchronize()
+    t_train = a.elapsed_time(b) / 1e3
+    # held-out phantom
+    seed = 199
+    y = cs.sense_fwd(plan, synthdata.phantom_torch(img, seed=seed, device=dev), maps)
+    v0 = synthdata.phantom_torch(img, seed=seed + 50, device=dev)
+    x_inf, _ = cs.recon_solve(plan, y, maps, lam, cs.REG_L1_WAVELET,
+                              cs.SolveParams(K=300, sketch=False, do_pca=False, power_v0=v0), wavelet_levels=levels)
+    su = ws.setup(plan, y, maps, lam, V, S, T, seed, v0, levels)
+    res = {}
+    for name, n in (("without", None), ("with", net)):
+        errs = []
+        ws.run(su, T, K, net=n)                      # warm-up
+        torch.cuda.synchronize()
+        a, b = _events()
+        a.record()
+        _, _, acc = ws.run(su, T, K, net=n, callback=lambda t, x: errs.append(x))
+        b.record()
+        torch.cuda.synchronize()
+        res[name] = ([float((x - x_inf).norm() / x_inf.norm()) for x in errs], acc, a.elapsed_time(b))
+    print(f"warm start on {args.config} ({img}, {C} coils): {len(pairs)} training pairs from {args.phantoms} "
+          f"phantoms in {t_pairs:.1f} s; {args.train_steps} Adam steps on 64^3 crops in {t_train:.2f} s "
+          f"(loss {np.mean(hist[:10]):.3e} -> {np.mean(hist[-10:]):.3e})")
+    for name in ("without", "with"):
+        e, acc, ms = res[name]
+        extra = f", accepted {sum(acc)}/{len(acc)}" if acc else ""
+        print(f"  held-out, {name} warm start: NRMSE to x_inf " + " ".join(f"{v:.3e}" for v in e) +
+              f"; {ms:.0f} ms per reconstruction{extra}")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["nufft", "normal", "tv", "ablation", "gfactor", "compare", "sketch", "cart2d",
-                                     "batched", "warmnet"])
+                                     "batched", "warmnet", "warmtrain"])
     ap.add_argument("--replicas", type=int, default=60)
     ap.add_argument("--seeds", type=int, default=16)
     ap.add_argument("--slices", type=int, default=64)
@@ -506,9 +568,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--iters", type=int, default=5)
     ap.add_argument("--voxels", type=int, default=160 * 256 * 256)
+    ap.add_argument("--phantoms", type=int, default=4)
+    ap.add_argument("--train-steps", type=int, default=300)
     args = ap.parse_args()
     {"nufft": nufft, "normal": normal, "tv": tv, "ablation": ablation, "gfactor": gfactor, "compare": compare,
-     "sketch": sketch, "cart2d": cart2d, "batched": batched, "warmnet": warmnet}[args.what](args)
+     "sketch": sketch, "cart2d": cart2d, "batched": batched, "warmnet": warmnet, "warmtrain": warmtrain}[args.what](args)
 
 
 if __name__ == "__main__":

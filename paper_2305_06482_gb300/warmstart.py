@@ -171,12 +171,28 @@ def run(su: SketchSetup, T, K, net: Optional[UNet] = None, x0=None, record_pairs
     return x, pairs, accepted
 
 
-def train(net: UNet, pairs, steps=200, lr=1e-3, seed=0):
-    """Adam on random pairs (x^t, d, x_target, eta), one volume per step; returns the loss history."""
+def crop3d(x, origin, box, out=None, stream=None):
+    """The box [origin, origin + box) of a complex64 [nz, ny, nx] CUDA volume (library kernel)."""
+    out = torch.empty(tuple(box), dtype=x.dtype, device=x.device) if out is None else out
+    i3 = ctypes.c_int * 3
+    _check(lib().cs_crop3d(_ptr(x), i3(*x.shape), i3(*origin), i3(*box), _ptr(out), _stream(stream)))
+    return out
+
+
+def train(net: UNet, pairs, steps=200, lr=1e-3, seed=0, crop=None):
+    """Adam on random pairs (x^t, d, x_target, eta), one volume per step; with crop = (cz, cy, cx)
+    (multiples of 4) each step uses a random box of that size from the pair's volumes.  Returns
+    the loss history."""
     rng = np.random.default_rng(seed)
     hist = []
+    bufs = None
     for _ in range(steps):
         xt, d, xs, eta = pairs[int(rng.integers(len(pairs)))]
+        if crop is not None:
+            o = [int(rng.integers(0, n - c + 1)) for n, c in zip(xt.shape, crop)]
+            if bufs is None:
+                bufs = [torch.empty(tuple(crop), dtype=torch.complex64, device=xt.device) for _ in range(3)]
+            xt, d, xs = (crop3d(a, o, crop, out=b) for a, b in zip((xt, d, xs), bufs))
         hist.append(float(net.train_step(xt, d, xs, eta, lr).item()))
     _check(lib().cs_nn_status(_stream()))
     return hist

@@ -272,6 +272,25 @@ def test_library_network_matches_layered_sequence(tmp_path):
     cs._check(cs.lib().cs_nn_status(None))
 
 
+def test_crop_and_crop_training():
+    """cs_crop3d against slicing (and its range check); training steps on random crops run and
+    stay finite."""
+    import paper_2305_06482_gb300 as cs
+    import paper_2305_06482_gb300.warmstart as ws
+    rng = np.random.default_rng(2)
+    dims = (12, 20, 28)
+    vol = lambda: torch.from_numpy((rng.standard_normal(dims) + 1j * rng.standard_normal(dims)).astype(np.complex64)).cuda()
+    x = vol()
+    c = ws.crop3d(x, (3, 5, 7), (8, 12, 16))
+    assert torch.equal(c, x[3:11, 5:17, 7:23])
+    with pytest.raises(cs.CoilSketchError):
+        ws.crop3d(x, (5, 0, 0), (8, 12, 16))                     # 5 + 8 > 12
+    pairs = [(vol(), vol(), vol(), 0.5) for _ in range(2)]
+    net = ws.UNet(seed=1)
+    hist = ws.train(net, pairs, steps=6, lr=1e-3, crop=(8, 12, 16))
+    assert len(hist) == 6 and all(np.isfinite(hist))
+
+
 def _problem(seed, img=(32, 48, 48), grid=(40, 60, 60), C=8, n_int=1500, n_read=128):
     import paper_2305_06482_gb300 as cs
     dev = torch.device("cuda")
