@@ -393,6 +393,14 @@ cs_status cs_crop3d(const float* src, const int* dims, const int* origin, const 
 cs_status cs_nn_slice(const float* src, int lds, int soff, int n, float* dst, int ldd, int doff, int64_t nvox,
                       int accumulate, void* stream);
 
+/* Self-test of the bounded-wait protocol of the kernels that wait on mbarriers (tensor-core
+ * contractions and convolutions, tensor-copy FFT passes): one block waits on a barrier, polling
+ * at most `limit` times (1 .. 2^24); with arrive = 1 the barrier completes and the call returns
+ * CS_OK, with arrive = 0 nothing arrives, the wait gives up on its own, the block records it in
+ * a device flag and exits normally, and the call returns CS_ERR_TIMEOUT (the context stays
+ * usable).  Synchronous. */
+cs_status cs_wait_selftest(int arrive, int64_t limit, void* stream);
+
 /* ------------------------------------------------------------------------------------------
  * The warm-start network as a library object (built from the pieces above; not in the paper).
  * ws_net_create: a U-Net of widths c1/c2/c3 (multiples of 4, c1, c2 <= 32, c3 <= 64; the

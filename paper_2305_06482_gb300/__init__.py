@@ -79,7 +79,7 @@ EXPORTED = [
     "cs_nn_adam", "cs_nn_features", "cs_nn_target", "cs_nn_apply", "cs_nn_status", "tv_dual_update", "tv_rhs",
     "cs_nn_maxpool2", "cs_nn_maxpool2_bwd", "cs_nn_upconv2", "cs_nn_upconv2_bwd", "cs_nn_slice",
     "ws_net_create", "ws_net_destroy", "ws_net_infer", "ws_net_train_step", "ws_net_param", "ws_net_save",
-    "ws_net_load", "cs_crop3d",
+    "ws_net_load", "cs_crop3d", "cs_wait_selftest",
 ]
 STAGES = {"spread": 0, "interp": 1, "fft_plain": 2, "expand": 3, "reduce": 4}
 
@@ -133,7 +133,7 @@ def lib():
             "ws_net_train_step": ([vp, vp, vp, vp, vp, f, f, vp, vp], i),
             "ws_net_param": ([vp, i, i, vp, vp, vp, vp], i),
             "ws_net_save": ([vp, ctypes.c_char_p], i), "ws_net_load": ([vp, ctypes.c_char_p], i),
-            "cs_crop3d": ([vp, vp, vp, vp, vp, vp], i),
+            "cs_crop3d": ([vp, vp, vp, vp, vp, vp], i), "cs_wait_selftest": ([i, i64, vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
