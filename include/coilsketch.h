@@ -404,7 +404,7 @@ cs_status cs_wait_selftest(int arrive, int64_t limit, void* stream);
 /* ------------------------------------------------------------------------------------------
  * The warm-start network as a library object (built from the pieces above; not in the paper).
  * ws_net_create: a U-Net of widths c1/c2/c3 (multiples of 4, c1, c2 <= 32, c3 <= 64; the
- *   survey's 16/32/64), He-normal weights from a Mersenne twister seeded by `seed` (Box-Muller),
+ *   default 16/32/64), He-normal weights from a Mersenne twister seeded by `seed` (Box-Muller),
  *   zero biases and zero Adam state, on the current device.  The handle owns all its device
  *   memory (parameters, gradients, Adam moments, packed BF16 weights, activation buffers sized
  *   for the last volume) and ws_net_destroy frees it.
