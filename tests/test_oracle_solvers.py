@@ -189,3 +189,20 @@ def test_coil_compression_keeping_every_coil_is_the_plain_solver():
     assert solvers.nrmse(got, ref) < 1e-10
     fewer = solvers.coil_compressed(ops, maps, y, 2, lambda f, a, yk: solvers.plain_cg(f, a, yk, 1e-2, x0, 10))
     assert solvers.nrmse(fewer, ref) > 1e-3          # dropping virtual coils changes the solution
+
+
+def test_algorithm_1_resumes_from_an_outer_iterate():
+    """Algorithm 1 depends on the past only through x^t and the sketch sequence (counter-based
+    on (seed, t)): stopping after t outer iterations and restarting from x^t with the remaining
+    sketch blocks reproduces the uninterrupted run exactly (CG and FISTA with a given step)."""
+    maps, idx, y = _cart_problem(shape=(16, 16), C=6, seed=7)
+    C, V, S, T = 6, 2, 2, 5
+    sk = philox.sketch_draw(11, 0, T, C, V, S)
+    for reg, extra in (("l2", {}), ("l1wav", {"eta": 0.3, "levels": 2})):
+        x_full, its_full = solvers.coil_sketching(_ops(idx), maps, y, 1e-2, reg, sk, V, 4, **extra)
+        x_2, its_a = solvers.coil_sketching(_ops(idx), maps, y, 1e-2, reg, sk[:2], V, 4, **extra)
+        x_res, its_b = solvers.coil_sketching(_ops(idx), maps, y, 1e-2, reg, sk[2:], V, 4, x0=x_2, **extra)
+        assert np.array_equal(x_res, x_full), reg
+        assert all(np.array_equal(a, b) for a, b in zip(its_a + its_b, its_full)), reg
+        # and the sketch blocks of a resumed run are the uninterrupted run's, drawn from (seed, t)
+        assert np.array_equal(philox.sketch_draw(11, 2, T - 2, C, V, S), sk[2:])
