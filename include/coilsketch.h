@@ -105,6 +105,20 @@ cs_status cs_plan_destroy(cs_plan* plan);
 cs_status cs_plan_binning(const cs_plan* plan, int32_t* perm, int32_t* tile_off, int32_t* j0,
                           int* ntiles_out, void* stream);
 
+/* Gridding launch parameters of a non-Cartesian plan: coils per warp of the interpolation (1..32)
+ * and of the spreading (1..16), consecutive sorted samples per warp of each (1..4096).  Plans
+ * start at 16 / 64 / 16 / 64.  Any values give the same results; only the speed changes.
+ * cs_plan_autotune: times the interpolation and the spreading of `ncoils` coils (reps timed
+ * launches after one untimed, CUDA events on `stream`) for coils per warp in {8, 16, 32} (interp)
+ * or {8, 16} (spread) and samples per warp in {32, 64, 128}, on the plan's own scratch buffers
+ * (their contents are overwritten), and keeps the fastest of each in the plan.  choice[4]
+ * (nullable) receives (interp coils, interp chunk, spread coils, spread chunk); ms[4] (nullable)
+ * the best interp and spread ms per launch and those of the configuration before tuning.
+ * Synchronous.  Cartesian plans have nothing to tune (returns CS_OK, ms zero). */
+cs_status cs_plan_set_gridding(cs_plan* plan, int interp_coils, int interp_chunk, int spread_coils,
+                               int spread_chunk);
+cs_status cs_plan_autotune(cs_plan* plan, int ncoils, int reps, int* choice, float* ms, void* stream);
+
 /* ------------------------------------------------------------------------------------------
  * sense_fwd: y = A x for `ncoils` maps (Eq. 1, Eq. 5): y_c = w^1/2 (.) F{c_c (.) x}.
  *   x [image] complex64, maps [ncoils][image] complex64, y [ncoils][N] complex64.

@@ -79,7 +79,7 @@ EXPORTED = [
     "cs_nn_adam", "cs_nn_features", "cs_nn_target", "cs_nn_apply", "cs_nn_status", "tv_dual_update", "tv_rhs",
     "cs_nn_maxpool2", "cs_nn_maxpool2_bwd", "cs_nn_upconv2", "cs_nn_upconv2_bwd", "cs_nn_slice",
     "ws_net_create", "ws_net_destroy", "ws_net_infer", "ws_net_train_step", "ws_net_param", "ws_net_save",
-    "ws_net_load", "cs_crop3d", "cs_wait_selftest",
+    "ws_net_load", "cs_crop3d", "cs_wait_selftest", "cs_plan_set_gridding", "cs_plan_autotune",
 ]
 STAGES = {"spread": 0, "interp": 1, "fft_plain": 2, "expand": 3, "reduce": 4}
 
@@ -134,6 +134,7 @@ def lib():
             "ws_net_param": ([vp, i, i, vp, vp, vp, vp], i),
             "ws_net_save": ([vp, ctypes.c_char_p], i), "ws_net_load": ([vp, ctypes.c_char_p], i),
             "cs_crop3d": ([vp, vp, vp, vp, vp, vp], i), "cs_wait_selftest": ([i, i64, vp], i),
+            "cs_plan_set_gridding": ([vp, i, i, i, i], i), "cs_plan_autotune": ([vp, i, i, vp, vp, vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -218,6 +219,19 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def set_gridding(self, interp_coils, interp_chunk, spread_coils, spread_chunk):
+        """Coils and samples per warp of the gridding kernels (non-Cartesian plans)."""
+        _check(lib().cs_plan_set_gridding(self._h, interp_coils, interp_chunk, spread_coils, spread_chunk))
+
+    def autotune(self, ncoils, reps=3, stream=None):
+        """Time the gridding candidates for `ncoils` coils and keep the fastest; returns
+        ((interp coils, interp chunk, spread coils, spread chunk), (best interp ms, best spread ms,
+        interp ms before, spread ms before))."""
+        choice = (ctypes.c_int * 4)()
+        ms = (ctypes.c_float * 4)()
+        _check(lib().cs_plan_autotune(self._h, ncoils, reps, choice, ms, _stream(stream)))
+        return tuple(choice), tuple(float(v) for v in ms)
 
     def binning(self):
         N = self.nsamples

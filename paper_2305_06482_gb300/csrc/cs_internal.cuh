@@ -152,6 +152,7 @@ cs_status nufft_records(cs_plan* p, cudaStream_t st);
 cs_status nufft_interp(const cs_plan* p, int ncoils, float2* y, const float2* ysub, cudaStream_t st);
 cs_status nufft_spread(const cs_plan* p, int ncoils, const float2* y, int sorted_in, cudaStream_t st);
 cs_status nufft_interp_spread(const cs_plan* p, int ncoils, cudaStream_t st);
+cs_status nufft_interp_sorted(const cs_plan* p, int ncoils, cudaStream_t st);   // ktmp = w^1/2 interp(grid)
 
 // Reductions and vector kernels (solve.cu)
 int reduce_blocks();

@@ -730,6 +730,11 @@ cs_status nufft_spread(const cs_plan* p, int ncoils, const float2* y, int sorted
     return launch_grid_op<true>(p, ncoils, 0, nullptr, nullptr, sorted_in ? p->ktmp : y, sorted_in, st);
 }
 
+// ktmp (sorted, coil-interleaved) = w^1/2 interp(grid)
+cs_status nufft_interp_sorted(const cs_plan* p, int ncoils, cudaStream_t st) {
+    return launch_grid_op<false>(p, ncoils, OUT_SORTED, nullptr, p->ktmp, nullptr, 0, st);
+}
+
 // normal operator on the grid: ktmp = w^1/2 interp(grid) (sorted), then grid = spread(w^1/2 ktmp)
 cs_status nufft_interp_spread(const cs_plan* p, int ncoils, cudaStream_t st) {
     CS_PROPAGATE(launch_grid_op<false>(p, ncoils, OUT_SORTED, nullptr, p->ktmp, nullptr, 0, st));

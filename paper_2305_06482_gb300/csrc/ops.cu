@@ -408,4 +408,99 @@ cs_status sketched_normal_apply(const cs_plan* p, const float* v, const float* m
     return fft_to_image(p, mv, V, ms, S, (float2*)z, 0, (const float2*)v, lambda, st);
 }
 
+cs_status cs_plan_set_gridding(cs_plan* p, int interp_coils, int interp_chunk, int spread_coils, int spread_chunk) {
+    clear_error();
+    CS_REQUIRE(p, CS_ERR_INVALID_ARG, "null plan");
+    CS_REQUIRE(interp_coils >= 1 && interp_coils <= 32 && spread_coils >= 1 && spread_coils <= 16 && interp_chunk >= 1 &&
+                   interp_chunk <= 4096 && spread_chunk >= 1 && spread_chunk <= 4096,
+               CS_ERR_INVALID_ARG, "gridding parameters out of range");
+    p->interp_coils = interp_coils;
+    p->interp_chunk = interp_chunk;
+    p->spread_coils = spread_coils;
+    p->spread_chunk = spread_chunk;
+    return CS_OK;
+}
+
+// Times the interpolation and spreading launches of `ncoils` coils for each candidate (coils per
+// warp, samples per warp) on the plan's own scratch buffers and keeps the fastest of each.
+cs_status cs_plan_autotune(cs_plan* p, int ncoils, int reps, int* choice, float* ms, void* stream) {
+    clear_error();
+    CS_REQUIRE(p && ncoils >= 1 && ncoils <= p->max_coils && reps >= 1 && reps <= 100, CS_ERR_INVALID_ARG,
+               "bad autotune arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    float best_i = 0.f, best_s = 0.f, def_i = 0.f, def_s = 0.f;
+    if (p->kind == CS_NONCARTESIAN) {
+        cudaEvent_t e0, e1;
+        CS_TRY_CUDA(cudaEventCreate(&e0));
+        CS_TRY_CUDA(cudaEventCreate(&e1));
+        cs_status rc = CS_OK;
+        auto timed = [&](bool spread, float& out) -> cs_status {
+            for (int r = 0; r <= reps; ++r) {
+                if (r == 1) CS_TRY_CUDA(cudaEventRecord(e0, st));
+                if (spread) CS_PROPAGATE(nufft_spread(p, ncoils, nullptr, 1, st));
+                else CS_PROPAGATE(nufft_interp_sorted(p, ncoils, st));
+            }
+            CS_TRY_CUDA(cudaEventRecord(e1, st));
+            CS_TRY_CUDA(cudaEventSynchronize(e1));
+            CS_TRY_CUDA(cudaEventElapsedTime(&out, e0, e1));
+            out /= reps;
+            return CS_OK;
+        };
+        const int coils_i[] = {8, 16, 32}, coils_s[] = {8, 16}, chunks[] = {32, 64, 128};
+        int bi_c = p->interp_coils, bi_k = p->interp_chunk, bs_c = p->spread_coils, bs_k = p->spread_chunk;
+        rc = timed(false, def_i);
+        if (rc == CS_OK) rc = timed(true, def_s);
+        best_i = def_i;
+        best_s = def_s;
+        for (int c : coils_i) {
+            for (int k : chunks) {
+                if (rc != CS_OK) break;
+                p->interp_coils = c;
+                p->interp_chunk = k;
+                float t = 0.f;
+                rc = timed(false, t);
+                if (rc == CS_OK && t < best_i) {
+                    best_i = t;
+                    bi_c = c;
+                    bi_k = k;
+                }
+            }
+        }
+        for (int c : coils_s) {
+            for (int k : chunks) {
+                if (rc != CS_OK) break;
+                p->spread_coils = c;
+                p->spread_chunk = k;
+                float t = 0.f;
+                rc = timed(true, t);
+                if (rc == CS_OK && t < best_s) {
+                    best_s = t;
+                    bs_c = c;
+                    bs_k = k;
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        p->interp_coils = bi_c;
+        p->interp_chunk = bi_k;
+        p->spread_coils = bs_c;
+        p->spread_chunk = bs_k;
+        if (rc != CS_OK) return rc;
+    }
+    if (choice) {
+        choice[0] = p->interp_coils;
+        choice[1] = p->interp_chunk;
+        choice[2] = p->spread_coils;
+        choice[3] = p->spread_chunk;
+    }
+    if (ms) {
+        ms[0] = best_i;
+        ms[1] = best_s;
+        ms[2] = def_i;
+        ms[3] = def_s;
+    }
+    return CS_OK;
+}
+
 }  // extern "C"

@@ -1,8 +1,9 @@
 """Micro-benchmarks of single operators on synthetic inputs (CUDA-event timing on the current
 stream), for profiling individual kernels with small launch counts.
 
-  python -m paper_2305_06482_gb300.microbench nufft  [--config cones3d_128|cones3d_large] [--warmup W] [--iters N]
-      multicoil NUFFT forward (sense_fwd) and adjoint (sense_adj), all coils
+  python -m paper_2305_06482_gb300.microbench nufft  [--config cones3d_128|cones3d_large] [--warmup W] [--iters N] [--autotune]
+      multicoil NUFFT forward (sense_fwd) and adjoint (sense_adj), all coils (optionally after
+      cs_plan_autotune has chosen the gridding launch parameters for all coils)
   python -m paper_2305_06482_gb300.microbench normal [--config cones3d_128|cones3d_large] [--warmup W] [--iters N]
       sketched normal operator A_S^H A_S v + lambda v with V = 5 unsketched and S = 5 sketched coils
       (the inner-iteration operator of the sketched sub-problem), with the per-stage device times
@@ -86,6 +87,11 @@ def nufft(args):
     maps = synthdata.coil_maps_torch(img, C, device=dev)
     y = torch.empty((C, traj.shape[0]), dtype=torch.complex64, device=dev)
     xa = torch.empty(img, dtype=torch.complex64, device=dev)
+    if args.autotune:
+        choice, ms = plan.autotune(C)
+        print(f"autotune for {C} coils: interp {choice[0]} coils x {choice[1]} samples per warp "
+              f"({ms[2]:.3f} -> {ms[0]:.3f} ms per launch), spread {choice[2]} x {choice[3]} "
+              f"({ms[3]:.3f} -> {ms[1]:.3f} ms)")
     for _ in range(args.warmup):
         cs.sense_fwd(plan, x, maps, y)
         cs.sense_adj(plan, y, maps, xa)
@@ -569,6 +575,7 @@ def main():
     ap.add_argument("--iters", type=int, default=5)
     ap.add_argument("--voxels", type=int, default=160 * 256 * 256)
     ap.add_argument("--phantoms", type=int, default=4)
+    ap.add_argument("--autotune", action="store_true", help="nufft: tune the gridding launches first")
     ap.add_argument("--train-steps", type=int, default=300)
     args = ap.parse_args()
     {"nufft": nufft, "normal": normal, "tv": tv, "ablation": ablation, "gfactor": gfactor, "compare": compare,

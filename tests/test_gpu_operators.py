@@ -135,6 +135,36 @@ def test_nufft_coil_chunks(C):
     assert nrmse(h(xa), nufft.sense_adj(op, yy, maps, dcf)) < TOL
 
 
+def test_gridding_parameters_and_autotune():
+    """Every gridding configuration the autotuner tries (coils per warp 8 / 16 / 32 for the
+    interpolation, 8 / 16 for the spreading, 32 / 64 / 128 samples per warp) against the FP64
+    oracle, with 20 coils (chunks of 7, 10 and 20), then the autotuner itself."""
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    img, grid, C = (16, 16, 16), (20, 20, 20), 20
+    traj, dcf, maps, x = _nufft_case(img, grid, C, 80, 64, seed=2)
+    plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=t(traj), dcf=t(dcf), grid=grid)
+    op = nufft.Plan(traj, img, grid)
+    y_ref = nufft.sense_fwd(op, x, maps, dcf)
+    yy = synthdata.random_complex((C, traj.shape[0]), 8)
+    xa_ref = nufft.sense_adj(op, yy, maps, dcf)
+    for ic in (8, 16, 32):
+        for sc in (8, 16):
+            for k in (32, 64, 128):
+                plan.set_gridding(ic, k, sc, k)
+                assert nrmse(h(cs.sense_fwd(plan, t(x), t(maps))), y_ref) < TOL, (ic, sc, k)
+                assert nrmse(h(cs.sense_adj(plan, t(yy), t(maps))), xa_ref) < TOL, (ic, sc, k)
+    with pytest.raises(cs.CoilSketchError):
+        plan.set_gridding(0, 64, 16, 64)
+    with pytest.raises(cs.CoilSketchError):
+        plan.set_gridding(16, 64, 32, 64)          # spreading takes at most 16 coils per warp
+    choice, ms = plan.autotune(C, reps=2)
+    assert choice[0] in (8, 16, 32) and choice[2] in (8, 16) and choice[1] in (32, 64, 128) and choice[3] in (32, 64, 128)
+    assert all(v > 0 for v in ms) and ms[0] <= ms[2] and ms[1] <= ms[3]
+    assert nrmse(h(cs.sense_fwd(plan, t(x), t(maps))), y_ref) < TOL
+    assert nrmse(h(cs.sense_adj(plan, t(yy), t(maps))), xa_ref) < TOL
+
+
 def test_nufft_binning_bit_exact():
     import paper_2305_06482_gb300 as cs
     from tests._gpu import t
