@@ -92,3 +92,23 @@ def test_jacobi_degenerate_spectrum(cs):
     P1 = V[:, :2] @ V[:, :2].conj().T
     P2 = Q[:, :2] @ Q[:, :2].conj().T
     assert np.allclose(P1, P2, atol=1e-12)
+
+
+def test_host_side_argument_checks(cs):
+    """Entry points refuse bad arguments on the host, before any device work (no GPU needed)."""
+    import ctypes
+    L = cs.lib()
+    i3 = ctypes.c_int * 3
+    fake = ctypes.c_void_p(0x1000)       # never dereferenced: the checks fail first
+    assert L.cs_plan_set_gridding(None, 16, 64, 16, 64) == 1
+    assert L.cs_plan_autotune(None, 4, 3, None, None, None) == 1
+    assert L.cs_wait_selftest(0, 0, None) == 1                       # poll limit out of range
+    assert L.cs_wait_selftest(0, (1 << 24) + 1, None) == 1
+    h = ctypes.c_void_p()
+    assert L.ws_net_create(6, 16, 32, ctypes.c_uint64(0), ctypes.byref(h)) == 2   # width not a multiple of 4
+    assert L.ws_net_create(16, 64, 64, ctypes.c_uint64(0), ctypes.byref(h)) == 2  # concatenation too wide
+    assert L.ws_net_create(16, 32, 64, ctypes.c_uint64(0), None) == 1
+    assert L.ws_net_infer(None, fake, fake, i3(8, 8, 8), ctypes.c_float(1.0), fake, None) == 1
+    assert L.cs_crop3d(fake, i3(8, 8, 8), i3(4, 0, 0), i3(8, 8, 8), fake, None) == 1  # box leaves the volume
+    assert L.cs_crop3d(fake, i3(8, 8, 8), i3(-1, 0, 0), i3(4, 4, 4), fake, None) == 1
+    assert b"crop box" in L.cs_last_error()
