@@ -206,3 +206,42 @@ def test_algorithm_1_resumes_from_an_outer_iterate():
         assert all(np.array_equal(a, b) for a, b in zip(its_a + its_b, its_full)), reg
         # and the sketch blocks of a resumed run are the uninterrupted run's, drawn from (seed, t)
         assert np.array_equal(philox.sketch_draw(11, 2, T - 2, C, V, S), sk[2:])
+
+
+# ---------------------------------------------------------------------------------------
+# Iterates worked out by hand from the published recursions, so that a wrong momentum index,
+# step schedule or extrapolation (which still converges to the same fixed point) fails.
+
+def test_fista_momentum_matches_hand_iterates():
+    """Beck & Teboulle (2009) on f(x) = 1/2 (x - 1)^2 with eta = 1/2 from x_0 = 0.  Worked by
+    hand: t_0 = 1, t_1 = (1 + sqrt 5)/2, t_2 = (1 + sqrt(7 + 2 sqrt 5))/2 = 2.1935270853...;
+    identity prox: x_1 = 1/2 (momentum (t_0 - 1)/t_1 = 0, so z_1 = x_1), x_2 = 3/4,
+    z_2 = 3/4 + (t_1 - 1)/t_2 (1/4) = 0.8204383812..., x_3 = (z_2 + 1)/2 = 0.9102191906...;
+    ridge prox v / (1 + eta) (prox of eta x^2/2): x_1 = 1/3, x_2 = 4/9, x_3 = 0.4919167972..."""
+    grad = lambda z: z - 1.0
+    one = np.zeros(1, complex)
+    hand_id = [0.5, 0.75, 0.9102191906406651]
+    hand_ridge = [1 / 3, 4 / 9, 0.49191679722686373]
+    for k in range(1, 4):
+        got = solvers.fista(grad, lambda v: v, one, 0.5, k)
+        assert abs(got[0] - hand_id[k - 1]) < 1e-15
+        got = solvers.fista(grad, lambda v: v / 1.5, one, 0.5, k)
+        assert abs(got[0] - hand_ridge[k - 1]) < 1e-15
+
+
+def test_acc_prox_sgd_step_schedule_matches_hand_iterates():
+    """AccProxSGD with a decaying step (beta = 1/2 < 1) and its floor (min_frac = 1/5) on two
+    image-domain coils A_c = m_c I, m = (1, 2), data y_c = m_c (x = 1), batches of one coil
+    alternating 0, 1, 0, 1, lambda = 0 (identity prox), alpha_0 = 1/10.  By hand:
+    alpha_k = 1/10, 1/20, 1/40, then the floor 1/50; g_k = (C/B) m_c^2 (z_k - 1);
+    x_1 = 1/5, x_2 = 13/25, x_3 = 0.6296530716..., x_4 = 0.7288876446..."""
+    m = np.array([1.0, 2.0])
+    maps = m[:, None, None] * np.ones((2, 4, 4))
+    y = maps.copy().astype(complex)
+    ops = lambda mm: (lambda v: mm * v, lambda r: np.sum(np.conj(mm) * r, axis=0))
+    batches = np.array([[0], [1], [0], [1]])
+    hand = [0.2, 0.52, 0.62965307163809753, 0.72888764463353636]
+    for k in range(1, 5):
+        x = solvers.acc_prox_sgd(ops, maps, y, 0.0, batches[:k], 0.1, 0.5, 0.2, np.zeros((4, 4), complex), k,
+                                 levels=1)
+        assert np.abs(x - hand[k - 1]).max() < 1e-13

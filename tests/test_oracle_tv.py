@@ -158,3 +158,20 @@ def test_algorithm1_with_pdhg_approaches_the_tv_solution():
     e = [solvers.nrmse(xi, x_ref) for xi in its]
     assert e[-1] < 0.1 * e[0] and e[-1] < 2e-2
     assert all(b < a * 1.05 for a, b in zip(e, e[1:]))
+
+
+def test_pdhg_over_relaxation_matches_hand_iterates():
+    """Chambolle & Pock with theta = 1 (xbar = 2 x_{k+1} - x_k) on a periodic two-pixel signal,
+    f(x) = 1/2 ||x - b||^2 with b = (1, 0) (prox_{tau f}(v) = (v + tau b)/(1 + tau)), lambda = 1/4,
+    tau = sigma = 1/2, x_0 = z_0 = 0.  By hand: x_1 = (1/3, 0); xbar_1 = (2/3, 0),
+    z_2 = proj((-1/3, 1/3)) = (-1/4, 1/4), T^H z = (1/2, -1/2), x_2 = (7/18, 1/6);
+    xbar_2 = (4/9, 1/3), z_3 = (-1/4, 1/4), x_3 = (23/54, 5/18).  Without the over-relaxation
+    (xbar = x) z_2 = (-1/6, 1/6) would stay inside the disc and x_2 would differ."""
+    b = np.array([1.0, 0.0])
+    tau = sigma = 0.5
+    prox_f = lambda v, xw: (v + tau * b) / (1 + tau)
+    hand = [(1 / 3, 0.0), (7 / 18, 1 / 6), (23 / 54, 5 / 18)]
+    for k in range(1, 4):
+        x, z = solvers.pdhg(prox_f, 0.25, np.zeros(2, complex), np.zeros((1, 2), complex), tau, sigma, k)
+        assert np.abs(x - np.array(hand[k - 1])).max() < 1e-15
+    assert np.abs(z[0] - np.array([-0.25, 0.25])).max() < 1e-15
