@@ -20,6 +20,7 @@ wavelet   Periodised orthonormal Daubechies-4 (db4, 8 taps) multi-level DWT (Sec
 tv        Periodic first-order differences and the dual projection of l1-TV (Sec. 2.1).
 gfactor   Inverse g-factor by Monte Carlo pseudo-replicas and in closed form for SENSE (Sec. 3.2).
 solvers   CG, FISTA, PDHG, power iteration, the sketched sub-problem (Eq. 9-10) and Algorithm 1.
+fftlib    The DFT library calls (scipy.fft with a thread count, else numpy.fft).
 
 Parity pins live in ``tests/test_oracle_*.py``: each function here is checked against
 something other than itself (dense matrices built from Eq. 1, closed forms, invariants,

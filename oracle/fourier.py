@@ -11,15 +11,17 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import fftlib
+
 
 def centred_fft(u, axes):
     """Centred orthonormal DFT: fftshift(fftn(ifftshift(u), norm='ortho'))."""
-    return np.fft.fftshift(np.fft.fftn(np.fft.ifftshift(u, axes=axes), axes=axes, norm="ortho"), axes=axes)
+    return np.fft.fftshift(fftlib.fftn(np.fft.ifftshift(u, axes=axes), axes=axes, norm="ortho"), axes=axes)
 
 
 def centred_ifft(k, axes):
     """Adjoint (= inverse) of centred_fft."""
-    return np.fft.fftshift(np.fft.ifftn(np.fft.ifftshift(k, axes=axes), axes=axes, norm="ortho"), axes=axes)
+    return np.fft.fftshift(fftlib.ifftn(np.fft.ifftshift(k, axes=axes), axes=axes, norm="ortho"), axes=axes)
 
 
 def mask_indices(mask):

@@ -23,7 +23,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import binning
+from . import binning, fftlib
 
 W = binning.KB_WIDTH
 
@@ -66,7 +66,7 @@ def _cdft(u, axes, inverse):
     """Centred unnormalised DFT (inverse: its conjugate transpose) over ``axes``."""
     scale = np.sqrt(np.prod([u.shape[a] for a in axes]))
     sh = np.fft.ifftshift(u, axes=axes)
-    t = np.fft.ifftn(sh, axes=axes, norm="ortho") if inverse else np.fft.fftn(sh, axes=axes, norm="ortho")
+    t = fftlib.ifftn(sh, axes=axes, norm="ortho") if inverse else fftlib.fftn(sh, axes=axes, norm="ortho")
     return np.fft.fftshift(t, axes=axes) * scale
 
 
