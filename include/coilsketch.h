@@ -237,17 +237,36 @@ cs_status sketched_maps(const float* S, const float* maps_rot, int64_t D, int C,
  * params:  T outer iterations, K inner iterations, V, S, sketch distribution/normalisation,
  *          seed (or a caller-given sketch array), whether to run coil PCA first, the FISTA
  *          step (0 = estimate 1/L by `power_iters` power iterations on the first sketched
- *          normal operator, from the caller's start vector), and whether to capture one outer
- *          iteration as a CUDA graph.
+ *          normal operator, from the caller's start vector), whether to capture one outer
+ *          iteration as a CUDA graph, an optional learned warm start and an optional trace.
  * x_inout: initial estimate on input (x^0), x^T on output.
- * workspace: the solver allocates its vectors on the device once per call.
+ * workspace: the solver's device vectors live in a workspace owned by the plan; it is
+ *          allocated on the first call and grown when a later call needs more (every call on a
+ *          plan shares it, so calls on one plan must not overlap).  cs_plan_destroy frees it.
  * ---------------------------------------------------------------------------------------- */
+typedef struct cs_unet cs_unet;   /* the warm-start network (ws_net_create, below) */
+
+/* Fields of one trace record (cs_solve_params.trace): one record per outer iteration of
+ * Algorithm 1 (plain solver: one per iteration), written on the device inside the loop.      */
+enum {
+    CS_TRACE_GRAD2 = 0,      /* ||d||^2 of the true gradient d = A^H (A x^t - y) at x^t (plain
+                                solver: ||gradient||^2 at the point the iteration evaluates it) */
+    CS_TRACE_OBJECTIVE = 1,  /* 1/2 ||A x^t - y||^2 + g(x^t) at the start of the outer iteration
+                                (plain FISTA: at its gradient point); NaN unless trace_objective,
+                                and NaN for l1-TV                                              */
+    CS_TRACE_ACCEPT = 2,     /* warm start: 1 accepted, 0 rejected; -1 without a warm start    */
+    CS_TRACE_DIST2 = 3,      /* ||x^{t+1} - x_ref||^2 / ||x_ref||^2 after the iteration; -1
+                                without x_ref                                                 */
+    CS_TRACE_TIME_NS = 4,    /* device clock (%globaltimer, ns) at the end of the iteration    */
+    CS_TRACE_FIELDS = 5
+};
+
 typedef struct {
     const float* y;          /* [C][N]                                                       */
     const float* maps;       /* [C][image]                                                   */
     int C;
     float lambda;
-    int reg;                 /* CS_REG_L2 | CS_REG_L1_WAVELET                                 */
+    int reg;                 /* CS_REG_L2 | CS_REG_L1_WAVELET | CS_REG_L1_TV                  */
     int wavelet_levels;      /* db4 levels for CS_REG_L1_WAVELET (every axis divisible by 2^levels) */
 } cs_problem;
 
@@ -289,6 +308,21 @@ typedef struct {
     const int* sgd_coils;    /* device int [K][sgd_batch]: the coil indices of every batch (in
                                 [0, C')), drawn by the caller; checked on the host              */
     float sgd_beta, sgd_min; /* step decay and floor (fractions of alpha_0); 0 = 0.99 and 0.1    */
+    /* Learned warm start (not in the paper; sketched l1-wavelet solves only): at every outer
+     * iteration the network predicts a start x^ from (x^t, d); the sub-problem objective of
+     * Eq. 9-10 is evaluated at x^ and at x^t on the device, and FISTA starts from x^ only when
+     * its objective is lower, else from x^t (Algorithm 1 unchanged).  The decision never leaves
+     * the device, so the outer iteration stays one captured graph.  Image sizes must be
+     * multiples of 4 (the network pools twice).  NULL = no warm start.                       */
+    cs_unet* warm;
+    /* Optional trace (any solver): x_ref (device [image], may be NULL) is the reference of the
+     * CS_TRACE_DIST2 field; trace (HOST array of [T][CS_TRACE_FIELDS] doubles for the sketched
+     * solver, [K][CS_TRACE_FIELDS] for the plain solver) receives the records when recon_solve
+     * returns; trace_objective = 1 adds the objective field (one extra full forward operator per
+     * record).  NULL trace = nothing recorded and nothing extra launched.                    */
+    const float* x_ref;
+    double* trace;
+    int trace_objective;
 } cs_solve_params;
 
 typedef struct {
@@ -298,6 +332,7 @@ typedef struct {
     int graph_used;          /* 1 if the loop body ran as a replayed CUDA graph              */
     double ms_total;         /* device time of the whole solve (CUDA events)                 */
     double ms_pca;           /* device time of coil PCA + rotations                           */
+    int warm_accepted;       /* outer iterations whose warm start was accepted               */
 } cs_stats;
 
 cs_status recon_solve(const cs_plan* plan, const cs_problem* problem, const cs_solve_params* params,
@@ -436,7 +471,6 @@ cs_status cs_wait_selftest(int arrive, int64_t limit, void* stream);
  * ws_net_save / ws_net_load: parameters, Adam moments and step count in a binary file (magic
  *   "CSUNET1", widths, step, then every array); loading checks the widths.  Synchronous.
  * ---------------------------------------------------------------------------------------- */
-typedef struct cs_unet cs_unet;
 cs_status ws_net_create(int c1, int c2, int c3, uint64_t seed, cs_unet** out);
 cs_status ws_net_destroy(cs_unet* net);
 cs_status ws_net_infer(cs_unet* net, const float* xt, const float* d, const int* dims, float eta, float* xhat,

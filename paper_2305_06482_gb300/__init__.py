@@ -28,6 +28,8 @@ GAUSSIAN, RADEMACHER = 0, 1
 NORM_UNIT_VAR, NORM_PAPER_LITERAL = 0, 1
 PREC_FP32, PREC_BF16_SPLIT = 0, 1
 REG_L2, REG_L1_WAVELET, REG_L1_TV = 0, 1, 2
+# fields of a recon_solve trace record (include/coilsketch.h, CS_TRACE_*)
+TRACE_GRAD2, TRACE_OBJECTIVE, TRACE_ACCEPT, TRACE_DIST2, TRACE_TIME_NS, TRACE_FIELDS = 0, 1, 2, 3, 4, 5
 
 
 class CoilSketchError(RuntimeError):
@@ -56,7 +58,8 @@ class _Params(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("iterates", ctypes.c_void_p), ("cg_iters", ctypes.c_int),
                 ("tv_tau", ctypes.c_float), ("tv_sigma", ctypes.c_float), ("init", ctypes.c_int),
                 ("keep", ctypes.c_int), ("sgd_batch", ctypes.c_int), ("sgd_coils", ctypes.c_void_p),
-                ("sgd_beta", ctypes.c_float), ("sgd_min", ctypes.c_float)]
+                ("sgd_beta", ctypes.c_float), ("sgd_min", ctypes.c_float), ("warm", ctypes.c_void_p),
+                ("x_ref", ctypes.c_void_p), ("trace", ctypes.c_void_p), ("trace_objective", ctypes.c_int)]
 
 
 class _BatchItem(ctypes.Structure):
@@ -66,7 +69,8 @@ class _BatchItem(ctypes.Structure):
 
 class _Stats(ctypes.Structure):
     _fields_ = [("L", ctypes.c_double), ("final_rr", ctypes.c_double), ("outer_done", ctypes.c_int),
-                ("graph_used", ctypes.c_int), ("ms_total", ctypes.c_double), ("ms_pca", ctypes.c_double)]
+                ("graph_used", ctypes.c_int), ("ms_total", ctypes.c_double), ("ms_pca", ctypes.c_double),
+                ("warm_accepted", ctypes.c_int)]
 
 
 EXPORTED = [
@@ -447,6 +451,10 @@ class SolveParams:
     sgd_coils: Optional[torch.Tensor] = None   # int32 [K, sgd_batch] device coil indices
     sgd_beta: float = 0.0      # step decay (0 = 0.99)
     sgd_min: float = 0.0       # step floor as a fraction of alpha_0 (0 = 0.1)
+    warm: Optional[object] = None          # warmstart.UNet: learned warm start (sketched l1-wavelet, 3D)
+    x_ref: Optional[torch.Tensor] = None   # reference image for the trace's distance field
+    trace: bool = False                    # record one trace row per outer iteration (plain: per iteration)
+    trace_objective: bool = False          # add the objective to the trace (one extra forward per row)
 
 
 def recon_solve(plan: Plan, y, maps, lam, reg=REG_L2, params: SolveParams = None, x0=None, wavelet_levels=4,
@@ -458,11 +466,17 @@ def recon_solve(plan: Plan, y, maps, lam, reg=REG_L2, params: SolveParams = None
     pr = _Problem(y=y.data_ptr(), maps=maps.data_ptr(), C=C, lam=float(lam), reg=int(reg),
                   wavelet_levels=int(wavelet_levels))
     sp = _params_struct(params)
+    tr = None
+    if params.trace:
+        import numpy as np
+        rows = params.T if params.sketch else params.K
+        tr = np.full((max(rows, 1), TRACE_FIELDS), np.nan, dtype=np.float64)
+        sp.trace = tr.ctypes.data
     st = _Stats()
     _check(lib().recon_solve(plan.handle, ctypes.byref(pr), ctypes.byref(sp), _ptr(x), ctypes.byref(st),
                              _stream(stream)))
     return x, {"L": st.L, "final_rr": st.final_rr, "outer_done": st.outer_done, "graph_used": st.graph_used,
-               "ms_total": st.ms_total, "ms_pca": st.ms_pca}
+               "ms_total": st.ms_total, "ms_pca": st.ms_pca, "warm_accepted": st.warm_accepted, "trace": tr}
 
 
 def _params_struct(params: SolveParams):
@@ -477,7 +491,10 @@ def _params_struct(params: SolveParams):
                    cg_iters=int(params.cg_iters), tv_tau=float(params.tv_tau), tv_sigma=float(params.tv_sigma),
                    init=int(params.init), keep=int(params.keep), sgd_batch=int(params.sgd_batch),
                    sgd_coils=None if params.sgd_coils is None else params.sgd_coils.data_ptr(),
-                   sgd_beta=float(params.sgd_beta), sgd_min=float(params.sgd_min))
+                   sgd_beta=float(params.sgd_beta), sgd_min=float(params.sgd_min),
+                   warm=None if params.warm is None else params.warm._h.value,
+                   x_ref=None if params.x_ref is None else params.x_ref.data_ptr(),
+                   trace=None, trace_objective=int(params.trace_objective))
 
 
 def recon_solve_batched(items, lam, reg=REG_L2, params: SolveParams = None, wavelet_levels=4, stream=None):

@@ -166,6 +166,18 @@ cs_status tc_init_attrs();
 cs_status wavelet_init_constants();
 cs_status coil_init_attrs();
 
+// Warm-start network pieces used by recon_solve (warmnet.cu, unet.cu).  The network input scale
+// is a fixed-order FP64 sum over kFeatBlocks block partials (part), so inference is reproducible.
+constexpr int kFeatBlocks = 296;
+cs_status nn_features_det(const float2* xt, const float2* d, int64_t n, float eta, const double* eta_dev, double* part,
+                          float* ss, float* f, cudaStream_t st);
+// buffers for `dims` and packed weights, done outside any stream capture; *gen changes whenever the
+// network's activation buffers are reallocated (a captured graph holding the old ones is stale)
+cs_status unet_prepare(cs_unet* net, const int* dims, cudaStream_t st, uint64_t* gen);
+// xhat = x^t + s U-Net(x^t / s, eta d / s) with eta read on the device (capturable after unet_prepare)
+cs_status unet_infer_dev(cs_unet* net, const float2* xt, const float2* d, const int* dims, const double* eta_dev,
+                         float2* xhat, cudaStream_t st);
+
 // Jacobi eigensolver (shared host/device algorithm, coil.cu)
 void hermitian_eig_serial(double* A, int n, double* V, double* evals);
 

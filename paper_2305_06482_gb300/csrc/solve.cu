@@ -68,7 +68,9 @@ struct Scal {
     double L;         // power iteration: largest eigenvalue estimate
     double eta;       // FISTA step
     int nonfinite;
-    int pad;
+    int naccept;      // warm starts accepted in this solve
+    double fhat, ft;  // warm start: sub-problem objective at the prediction and at x^t
+    double refn2;     // trace: ||x_ref||^2
 };
 
 // CG start for the sub-problem: r = -(d + lambda x), p = r, partials of ||r||^2
@@ -284,6 +286,100 @@ __global__ void set_L_kernel(Scal* sc, double L) {
 
 __global__ void set_eta_kernel(Scal* sc, double eta) {
     if (threadIdx.x == 0 && blockIdx.x == 0) sc->eta = eta;
+}
+
+// ---- per-iteration trace (records of CS_TRACE_FIELDS doubles, row *tdev) ----
+__global__ void trace_init_kernel(double* __restrict__ tr, int rows) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * CS_TRACE_FIELDS) return;
+    const int f = i % CS_TRACE_FIELDS;
+    tr[i] = (f == CS_TRACE_ACCEPT || f == CS_TRACE_DIST2) ? -1.0 : __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// tr[row][field] = scale * (sum of the partials in a fixed order) / (denom ? *denom : 1) (+ the
+// second partial set times scale2 when part2 is given)
+__global__ void trace_store_kernel(const double* __restrict__ part, double scale, const double* __restrict__ part2,
+                                   double scale2, const double* __restrict__ denom, double* __restrict__ tr,
+                                   const int* __restrict__ tdev, int field) {
+    if (threadIdx.x < 32) {
+        double a = 0, b = 0;
+        for (int i = threadIdx.x; i < kRedBlocks; i += 32) {
+            a += part[i];
+            if (part2) b += part2[i];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+        if (threadIdx.x == 0) {
+            double v = scale * a + (part2 ? scale2 * b : 0.0);
+            if (denom) v /= *denom;
+            tr[(int64_t)(*tdev) * CS_TRACE_FIELDS + field] = v;
+        }
+    }
+}
+
+__global__ void trace_time_kernel(double* __restrict__ tr, const int* __restrict__ tdev) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    tr[(int64_t)(*tdev) * CS_TRACE_FIELDS + CS_TRACE_TIME_NS] = (double)t;
+}
+
+// partials of ||a - b||^2
+__global__ void __launch_bounds__(kRedThreads) diff2_kernel(const float2* __restrict__ a, const float2* __restrict__ b,
+                                                            int64_t n, double* __restrict__ part) {
+    double acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float dx = a[i].x - b[i].x, dy = a[i].y - b[i].y;
+        acc += (double)fmaf(dx, dx, dy * dy);
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// partials of sum |c_i| (complex moduli)
+__global__ void l1_kernel(const float2* __restrict__ c, int64_t n, double* __restrict__ part) {
+    double acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = c[i];
+        acc += (double)sqrtf(v.x * v.x + v.y * v.y);
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// warm start: *dst = 0.5 quad + lin + lambda reg from three partial sets (quad may be null: 0)
+__global__ void subobj_kernel(const double* __restrict__ pq, const double* __restrict__ pl, const double* __restrict__ pr,
+                              double lambda, double* __restrict__ dst) {
+    if (threadIdx.x < 32) {
+        double q = 0, l = 0, r = 0;
+        for (int i = threadIdx.x; i < kRedBlocks; i += 32) {
+            if (pq) q += pq[i];
+            l += pl[i];
+            r += pr[i];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            q += __shfl_down_sync(0xffffffffu, q, o);
+            l += __shfl_down_sync(0xffffffffu, l, o);
+            r += __shfl_down_sync(0xffffffffu, r, o);
+        }
+        if (threadIdx.x == 0) *dst = 0.5 * q + l + lambda * r;
+    }
+}
+
+// warm start: keep the prediction as the sub-problem's start when its objective is lower (x = xhat),
+// else leave x = x^t; record the decision in the trace (if any) and the accept count
+__global__ void warm_select_kernel(Scal* __restrict__ sc, const float2* __restrict__ xhat, float2* __restrict__ x,
+                                   int64_t n, double* __restrict__ tr, const int* __restrict__ tdev) {
+    const double fh = sc->fhat, ft = sc->ft;
+    const bool ok = isfinite(fh) && isfinite(ft) && fh < ft;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (ok) sc->naccept += 1;
+        if (tr) tr[(int64_t)(*tdev) * CS_TRACE_FIELDS + CS_TRACE_ACCEPT] = ok ? 1.0 : 0.0;
+    }
+    if (!ok) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = xhat[i];
 }
 
 // FISTA momentum coefficients theta_k = (t_{k-1} - 1) / t_k, t_0 = 1, t_k = (1 + sqrt(1 + 4 t_{k-1}^2)) / 2
@@ -652,6 +748,12 @@ struct SolverWS {
     int* tinit = nullptr;    // device index of the initialisation's sketch block
     float2 *bmaps = nullptr, *by = nullptr;   // AccProxSGD: the current coil batch's maps and data
     int64_t bmaps_n = 0, by_n = 0;
+    double* trace = nullptr;   // device trace records [trace_rows][CS_TRACE_FIELDS]
+    int trace_rows = 0;
+    float2* kres = nullptr;    // trace objective: full forward operator output [C][N]
+    int64_t kres_n = 0;
+    float2 *xt0 = nullptr, *xhat = nullptr;   // warm start: saved x^t and the prediction
+    double* partC = nullptr;
     std::vector<void*> allocs;
     cudaGraphExec_t gexec = nullptr;
     uint64_t gsig = 0;
@@ -669,6 +771,39 @@ struct SolverWS {
         tinit = nullptr;
         bmaps = by = nullptr;
         bmaps_n = by_n = 0;
+        trace = nullptr;
+        trace_rows = 0;
+        kres = nullptr;
+        kres_n = 0;
+        xt0 = xhat = nullptr;
+        partC = nullptr;
+    }
+    void drop_graph() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        gsig = 0;
+    }
+    cs_status ensure_trace(int rows) {
+        if (trace && trace_rows >= rows) return CS_OK;
+        drop_graph();
+        CS_PROPAGATE(get(&trace, (size_t)rows * CS_TRACE_FIELDS));
+        trace_rows = rows;
+        return CS_OK;
+    }
+    cs_status ensure_kres(int64_t n) {
+        if (kres && kres_n >= n) return CS_OK;
+        drop_graph();
+        CS_PROPAGATE(get(&kres, (size_t)n));
+        kres_n = n;
+        return CS_OK;
+    }
+    cs_status ensure_warm() {
+        if (xt0 && xhat && partC) return CS_OK;
+        drop_graph();
+        CS_PROPAGATE(get(&xt0, (size_t)D));
+        CS_PROPAGATE(get(&xhat, (size_t)D));
+        CS_PROPAGATE(get(&partC, (size_t)kRedBlocks));
+        return CS_OK;
     }
     cs_status ensure_sgd(int64_t nm, int64_t ny) {
         if (bmaps && bmaps_n >= nm && by && by_n >= ny) return CS_OK;
@@ -1043,6 +1178,75 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
     }
     const std::vector<float> theta = fista_thetas(std::max(K, 1));
     const bool use_graph = sp->use_graph != 0 && allow_graph;
+    // optional trace (one record per outer iteration, or per iteration of the plain solver) and
+    // optional learned warm start; both run entirely on the device inside the loop body
+    const bool tracing = sp->trace != nullptr;
+    const bool trace_obj = tracing && sp->trace_objective != 0 && !tvreg;
+    if (tracing) {
+        const int rows = sketch ? T : K;
+        CS_REQUIRE(rows >= 1, CS_ERR_INVALID_ARG, "a trace needs at least one iteration");
+        CS_PROPAGATE(ws->ensure_trace(rows));
+        trace_init_kernel<<<(rows * CS_TRACE_FIELDS + 255) / 256, 256, 0, st>>>(ws->trace, rows);
+        CS_LAUNCH_CHECK();
+        if (sp->x_ref) {
+            dot_kernel<<<kRedBlocks, kRedThreads, 0, st>>>((const float2*)sp->x_ref, (const float2*)sp->x_ref, D, c.partA);
+            CS_LAUNCH_CHECK();
+            store_sum_kernel<<<1, 32, 0, st>>>(c.partA, &ws->sc->refn2);
+            CS_LAUNCH_CHECK();
+        }
+        if (trace_obj) CS_PROPAGATE(ws->ensure_kres((int64_t)C * N));
+    }
+    const bool warm = sp->warm != nullptr;
+    uint64_t wgen = 0;
+    if (warm) {
+        CS_REQUIRE(sketch && fista && p->ndim == 3, CS_ERR_INVALID_ARG,
+                   "the warm start serves sketched l1-wavelet (FISTA) solves of 3D images");
+        CS_PROPAGATE(ws->ensure_warm());
+        CS_PROPAGATE(unet_prepare(sp->warm, p->img, st, &wgen));
+    }
+    // ||v||^2 into the trace field of the current row
+    auto trace_norm2 = [&](cudaStream_t s, const float2* v, int field) -> cs_status {
+        dot_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(v, v, D, ws->partA);
+        CS_LAUNCH_CHECK();
+        trace_store_kernel<<<1, 32, 0, s>>>(ws->partA, 1.0, nullptr, 0.0, nullptr, ws->trace, ws->tdev, field);
+        CS_LAUNCH_CHECK();
+        return CS_OK;
+    };
+    // 1/2 ||A u - y||^2 + g(u) with the first Cn coils (a forward operator into kres); `scr` is a
+    // free image-sized buffer for the wavelet coefficients
+    auto trace_objective = [&](cudaStream_t s, const float2* u, const float2* mp, int Cn, const float2* yv,
+                               float2* scr) -> cs_status {
+        CS_PROPAGATE((cs_status)sense_fwd(p, (const float*)u, (const float*)mp, Cn, (float*)ws->kres, s));
+        diff2_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(ws->kres, yv, (int64_t)Cn * N, ws->partA);
+        CS_LAUNCH_CHECK();
+        double rscale = 0.5 * c.lambda;
+        if (fista) {
+            CS_TRY_CUDA(cudaMemcpyAsync(scr, u, sizeof(float2) * D, cudaMemcpyDeviceToDevice, s));
+            CS_PROPAGATE(wavelet_apply(scr, c.dims3, c.nd, c.levels, 0, s));
+            l1_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(scr, D, ws->partB);
+            rscale = c.lambda;
+        } else {
+            dot_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(u, u, D, ws->partB);
+        }
+        CS_LAUNCH_CHECK();
+        trace_store_kernel<<<1, 32, 0, s>>>(ws->partA, 0.5, ws->partB, rscale, nullptr, ws->trace, ws->tdev,
+                                            CS_TRACE_OBJECTIVE);
+        CS_LAUNCH_CHECK();
+        return CS_OK;
+    };
+    // after an iteration: distance to x_ref and the device clock
+    auto trace_end = [&](cudaStream_t s) -> cs_status {
+        if (sp->x_ref) {
+            diff2_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(x, (const float2*)sp->x_ref, D, ws->partA);
+            CS_LAUNCH_CHECK();
+            trace_store_kernel<<<1, 32, 0, s>>>(ws->partA, 1.0, nullptr, 0.0, &ws->sc->refn2, ws->trace, ws->tdev,
+                                                CS_TRACE_DIST2);
+            CS_LAUNCH_CHECK();
+        }
+        trace_time_kernel<<<1, 1, 0, s>>>(ws->trace, ws->tdev);
+        CS_LAUNCH_CHECK();
+        return CS_OK;
+    };
     int graph_used = 0;
     // signature of everything a captured body depends on
     uint64_t sig = 1469598103934665603ull;
@@ -1064,6 +1268,13 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
         sig = fnv(sig, tvf, sizeof(tvf));
     }
     sig = fnv(sig, &sp->seed, sizeof(uint64_t));
+    {
+        const void* tp[] = {sp->warm, sp->x_ref};
+        const int ti[] = {(int)tracing, (int)trace_obj};
+        sig = fnv(sig, tp, sizeof(tp));
+        sig = fnv(sig, ti, sizeof(ti));
+        sig = fnv(sig, &wgen, sizeof(wgen));
+    }
     const int g = vec_grid(D);
     float2* iters = (float2*)sp->iterates;
 
@@ -1112,13 +1323,52 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
         auto body = [&](cudaStream_t s) -> cs_status {
             Ctx cc = c;
             cc.st = s;
+            if (trace_obj) CS_PROPAGATE(trace_objective(s, x, maps, C, y, ws->u));
             // true gradient with all C coils
             CS_PROPAGATE((cs_status)sense_grad(p, (const float*)x, (const float*)maps, C, (const float*)y, (float*)ws->d, s));
+            if (tracing) CS_PROPAGATE(trace_norm2(s, ws->d, CS_TRACE_GRAD2));
             // sketched model: V virtual coils in place + S random combinations of the rest
             if (S > 0) CS_PROPAGATE(sketched_maps_impl(sk, ws->tdev, maps, D, C, V, S, sp->precision, msk, s));
-            if (fista) CS_PROPAGATE(fista_sub(cc, ws->d, x, K, maps, V, msk, S, theta, ws->z, ws->xp, ws->u, ws->gr, ws->xt));
-            else if (tvreg) CS_PROPAGATE(pdhg_sub(cc, ws->d, x, maps, V, msk, S, pd));
-            else CS_PROPAGATE(cg_sub(cc, ws->d, x, K, maps, V, msk, S, ws->r, ws->pv, ws->hp));
+            if (fista && warm) {
+                // learned warm start: prediction xhat from (x^t, d); the sub-problem objective of
+                // Eq. 9-10, F(u) = 1/2 ||A_S (u - x^t)||^2 + Re<u, d> + lambda ||Psi u||_1, at xhat
+                // and at x^t decides on the device which one FISTA starts from
+                CS_TRY_CUDA(cudaMemcpyAsync(ws->xt0, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, s));
+                CS_PROPAGATE(unet_infer_dev(sp->warm, ws->xt0, ws->d, p->img, &ws->sc->eta, ws->xhat, s));
+                sub_kernel<<<g, kRedThreads, 0, s>>>(ws->xhat, ws->xt0, D, ws->z);
+                CS_LAUNCH_CHECK();
+                CS_PROPAGATE(normal_apply(cc, ws->z, maps, V, msk, S, 0.f, ws->hp));
+                dot_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(ws->z, ws->hp, D, ws->partA);
+                CS_LAUNCH_CHECK();
+                dot_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(ws->xhat, ws->d, D, ws->partB);
+                CS_LAUNCH_CHECK();
+                CS_TRY_CUDA(cudaMemcpyAsync(ws->u, ws->xhat, sizeof(float2) * D, cudaMemcpyDeviceToDevice, s));
+                CS_PROPAGATE(wavelet_apply(ws->u, c.dims3, c.nd, c.levels, 0, s));
+                l1_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(ws->u, D, ws->partC);
+                CS_LAUNCH_CHECK();
+                subobj_kernel<<<1, 32, 0, s>>>(ws->partA, ws->partB, ws->partC, (double)c.lambda, &ws->sc->fhat);
+                CS_LAUNCH_CHECK();
+                dot_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(ws->xt0, ws->d, D, ws->partB);
+                CS_LAUNCH_CHECK();
+                CS_TRY_CUDA(cudaMemcpyAsync(ws->u, ws->xt0, sizeof(float2) * D, cudaMemcpyDeviceToDevice, s));
+                CS_PROPAGATE(wavelet_apply(ws->u, c.dims3, c.nd, c.levels, 0, s));
+                l1_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(ws->u, D, ws->partC);
+                CS_LAUNCH_CHECK();
+                subobj_kernel<<<1, 32, 0, s>>>(nullptr, ws->partB, ws->partC, (double)c.lambda, &ws->sc->ft);
+                CS_LAUNCH_CHECK();
+                warm_select_kernel<<<g, kRedThreads, 0, s>>>(ws->sc, ws->xhat, x, D, tracing ? ws->trace : nullptr,
+                                                             ws->tdev);
+                CS_LAUNCH_CHECK();
+                CS_PROPAGATE(fista_sub(cc, ws->d, x, K, maps, V, msk, S, theta, ws->z, ws->xp, ws->u, ws->gr, ws->xt,
+                                       ws->xt0));
+            } else if (fista) {
+                CS_PROPAGATE(fista_sub(cc, ws->d, x, K, maps, V, msk, S, theta, ws->z, ws->xp, ws->u, ws->gr, ws->xt));
+            } else if (tvreg) {
+                CS_PROPAGATE(pdhg_sub(cc, ws->d, x, maps, V, msk, S, pd));
+            } else {
+                CS_PROPAGATE(cg_sub(cc, ws->d, x, K, maps, V, msk, S, ws->r, ws->pv, ws->hp));
+            }
+            if (tracing) CS_PROPAGATE(trace_end(s));
             if (iters) {
                 copy_iter_kernel<<<g, kRedThreads, 0, s>>>(x, iters, ws->tdev, 0, D);
                 CS_LAUNCH_CHECK();
@@ -1150,6 +1400,7 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
             store_sum_kernel<<<1, 32, 0, s>>>(c.partB, &c.sc->rr[0]);
             CS_LAUNCH_CHECK();
             for (int m = 0; m < pd.M; ++m) CS_PROPAGATE(cg_iter(cc, maps, Cp, nullptr, 0, x, ws->r, ws->pv, ws->hp, m & 1, nullptr));
+            if (tracing) CS_PROPAGATE(trace_end(s));
             if (iters) {
                 copy_iter_kernel<<<g, kRedThreads, 0, s>>>(x, iters, ws->tdev, 0, D);
                 CS_LAUNCH_CHECK();
@@ -1190,14 +1441,17 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
             CS_LAUNCH_CHECK();
             gather_coils_kernel<<<gg, kRedThreads, 0, s>>>(y, N, sp->sgd_coils, B, ws->tdev, ws->by);
             CS_LAUNCH_CHECK();
+            if (trace_obj) CS_PROPAGATE(trace_objective(s, ws->z, maps, Cp, y, ws->hp));
             CS_PROPAGATE((cs_status)sense_grad(p, (const float*)ws->z, (const float*)ws->bmaps, B, (const float*)ws->by,
                                                (float*)ws->gr, s));
+            if (tracing) CS_PROPAGATE(trace_norm2(s, ws->gr, CS_TRACE_GRAD2));
             sgd_step_kernel<<<g, kRedThreads, 0, s>>>(ws->z, ws->gr, c.sc, ws->tdev, beta, minf, ratio, D, ws->u);
             CS_LAUNCH_CHECK();
             CS_PROPAGATE(prox_wavelet(cc, ws->u, x, c.sc, 0.f));
             momentum_kernel<<<g, kRedThreads, 0, s>>>(x, ws->xp, 0.f, ws->theta, ws->tdev, D, ws->z);
             CS_LAUNCH_CHECK();
             CS_TRY_CUDA(cudaMemcpyAsync(ws->xp, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, s));
+            if (tracing) CS_PROPAGATE(trace_end(s));
             if (iters) {
                 copy_iter_kernel<<<g, kRedThreads, 0, s>>>(x, iters, ws->tdev, 0, D);
                 CS_LAUNCH_CHECK();
@@ -1221,13 +1475,16 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
         auto body = [&](cudaStream_t s) -> cs_status {
             Ctx cc = c;
             cc.st = s;
+            if (trace_obj) CS_PROPAGATE(trace_objective(s, ws->z, maps, Cp, y, ws->hp));
             CS_PROPAGATE((cs_status)sense_grad(p, (const float*)ws->z, (const float*)maps, Cp, (const float*)y, (float*)ws->gr, s));
+            if (tracing) CS_PROPAGATE(trace_norm2(s, ws->gr, CS_TRACE_GRAD2));
             fista_step_kernel<<<g, kRedThreads, 0, s>>>(ws->z, ws->gr, nullptr, c.sc, D, ws->u);
             CS_LAUNCH_CHECK();
             CS_PROPAGATE(prox_wavelet(cc, ws->u, x, c.sc, 0.f));
             momentum_kernel<<<g, kRedThreads, 0, s>>>(x, ws->xp, 0.f, ws->theta, ws->tdev, D, ws->z);
             CS_LAUNCH_CHECK();
             CS_TRY_CUDA(cudaMemcpyAsync(ws->xp, x, sizeof(float2) * D, cudaMemcpyDeviceToDevice, s));
+            if (tracing) CS_PROPAGATE(trace_end(s));
             if (iters) {
                 copy_iter_kernel<<<g, kRedThreads, 0, s>>>(x, iters, ws->tdev, 0, D);
                 CS_LAUNCH_CHECK();
@@ -1249,6 +1506,10 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
             Ctx cc = c;
             cc.st = s;
             CS_PROPAGATE(cg_iter(cc, maps, Cp, nullptr, 0, x, ws->r, ws->pv, ws->hp, 0, ws->tdev));
+            if (tracing) {
+                CS_PROPAGATE(trace_norm2(s, ws->r, CS_TRACE_GRAD2));
+                CS_PROPAGATE(trace_end(s));
+            }
             if (iters) {
                 copy_iter_kernel<<<g, kRedThreads, 0, s>>>(x, iters, ws->tdev, 0, D);
                 CS_LAUNCH_CHECK();
@@ -1284,6 +1545,11 @@ static cs_status recon_finish(cs_plan* p, const cs_solve_params* sp, cudaStream_
         stats->graph_used = ev ? ev->graph_used : 0;
         stats->ms_total = ms_all;
         stats->ms_pca = ms_pca;
+        stats->warm_accepted = h.naccept;
+    }
+    if (sp->trace && ws->trace) {
+        const int rows = sp->sketch ? sp->T : sp->K;
+        CS_TRY_CUDA(cudaMemcpy(sp->trace, ws->trace, sizeof(double) * CS_TRACE_FIELDS * rows, cudaMemcpyDeviceToHost));
     }
     CS_PROPAGATE(fft_check_and_clear());
     CS_PROPAGATE(tc_check_and_clear());
@@ -1449,6 +1715,8 @@ cs_status recon_solve(const cs_plan* p, const cs_problem* pr, const cs_solve_par
                 CS_REQUIRE(h[i] >= 0 && h[i] < Cp, CS_ERR_INVALID_ARG, "sgd_coils[%zu] = %d outside [0, %d)", i, h[i], Cp);
         }
     }
+    CS_REQUIRE(sp->trace_objective == 0 || sp->trace_objective == 1, CS_ERR_INVALID_ARG, "trace_objective is 0 or 1");
+    CS_REQUIRE(!sp->trace || (sp->sketch ? sp->T : sp->K) >= 1, CS_ERR_INVALID_ARG, "a trace needs iterations");
     return recon_solve_impl(const_cast<cs_plan*>(p), pr, sp, (float2*)x_inout, stats, (cudaStream_t)stream);
 }
 
@@ -1456,6 +1724,8 @@ cs_status recon_solve_batched(int nslices, const cs_batch_item* items, const cs_
                               void* stream) {
     clear_error();
     CS_REQUIRE(nslices >= 1 && items && params, CS_ERR_INVALID_ARG, "bad batched solve arguments");
+    CS_REQUIRE(!params->warm && !params->trace && !params->x_ref, CS_ERR_INVALID_ARG,
+               "batched solves take no warm start, trace or reference");
     for (int i = 0; i < nslices; ++i) {
         const cs_batch_item& it = items[i];
         CS_REQUIRE(it.plan && it.x_inout && it.problem.y && it.problem.maps && it.problem.C >= 1 &&
@@ -1523,16 +1793,6 @@ cs_status sketched_subproblem_solve(const cs_plan* plan, const float* d, const f
                                same ? nullptr : (const float2*)xt));
     }
     return CS_OK;
-}
-
-__global__ void l1_kernel(const float2* __restrict__ c, int64_t n, double* __restrict__ part) {
-    double acc = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float2 v = c[i];
-        acc += (double)sqrtf(v.x * v.x + v.y * v.y);
-    }
-    const double s = block_sum(acc);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 // F(u) = 1/2 ||A_S (u - x^t)||^2 + Re<u, d> + g(u), g = lambda/2 ||u||^2 or lambda ||Psi u||_1 (Eq. 9-10)

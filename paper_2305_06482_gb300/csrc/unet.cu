@@ -51,6 +51,8 @@ struct cs_unet {
     float *b1 = nullptr, *b2 = nullptr, *cat2 = nullptr, *d2a = nullptr, *d2 = nullptr, *cat1 = nullptr;
     float *d1a = nullptr, *d1 = nullptr, *out = nullptr, *tgt = nullptr, *gout = nullptr, *ss = nullptr;
     unsigned char *i1 = nullptr, *i2 = nullptr;
+    double* fpart = nullptr;   // kFeatBlocks partial sums of the input scale
+    uint64_t gen = 0;          // bumped whenever the buffers above are reallocated
     float *gA1 = nullptr, *gB1 = nullptr, *ge1 = nullptr, *gcat1 = nullptr, *gA2 = nullptr, *gB2 = nullptr;
     float *ge2 = nullptr, *gp1 = nullptr, *gcat2 = nullptr, *gA3 = nullptr, *gB3 = nullptr, *gp2 = nullptr;
 };
@@ -99,6 +101,8 @@ cs_status ensure_bufs(cs_unet* n, const int* dims, bool bwd) {
     CS_PROPAGATE(alloc(n, n->d1, V1 * c1));
     CS_PROPAGATE(alloc(n, n->out, V1 * 2));
     CS_PROPAGATE(alloc(n, n->ss, 2));
+    CS_PROPAGATE(alloc(n, n->fpart, kFeatBlocks));
+    n->gen += 1;
     if (bwd) {
         CS_PROPAGATE(alloc(n, n->tgt, V1 * 2));
         CS_PROPAGATE(alloc(n, n->gout, V1 * 2));
@@ -233,6 +237,26 @@ void destroy(cs_unet* n) {
 constexpr char kMagic[8] = {'C', 'S', 'U', 'N', 'E', 'T', '1', '\0'};
 
 }  // namespace
+
+cs_status unet_prepare(cs_unet* net, const int* dims, cudaStream_t st, uint64_t* gen) {
+    CS_REQUIRE(net, CS_ERR_INVALID_ARG, "null warm-start network");
+    CS_PROPAGATE(check_dims(net, dims));
+    CS_PROPAGATE(ensure_bufs(net, dims, false));
+    CS_PROPAGATE(pack_all(net, st));
+    *gen = net->gen;
+    return CS_OK;
+}
+
+cs_status unet_infer_dev(cs_unet* net, const float2* xt, const float2* d, const int* dims, const double* eta_dev,
+                         float2* xhat, cudaStream_t st) {
+    CS_REQUIRE(net->dims[0] == dims[0] && net->dims[1] == dims[1] && net->dims[2] == dims[2] && net->packed,
+               CS_ERR_INVALID_ARG, "warm-start network not prepared for this volume");
+    const int64_t n = (int64_t)dims[0] * dims[1] * dims[2];
+    CS_PROPAGATE(nn_features_det(xt, d, n, 0.f, eta_dev, net->fpart, net->ss, net->f, st));
+    CS_PROPAGATE(forward(net, st));
+    return cs_nn_apply((const float*)xt, net->out, n, net->ss, (float*)xhat, st);
+}
+
 }  // namespace cs
 
 using namespace cs;
@@ -344,7 +368,8 @@ cs_status ws_net_infer(cs_unet* net, const float* xt, const float* d, const int*
     CS_PROPAGATE(check_dims(net, dims));
     CS_PROPAGATE(ensure_bufs(net, dims, false));
     const int64_t n = (int64_t)dims[0] * dims[1] * dims[2];
-    CS_PROPAGATE(cs_nn_features(xt, d, n, eta, net->ss, net->f, stream));
+    CS_PROPAGATE(nn_features_det((const float2*)xt, (const float2*)d, n, eta, nullptr, net->fpart, net->ss, net->f,
+                                 (cudaStream_t)stream));
     CS_PROPAGATE(forward(net, stream));
     return cs_nn_apply(xt, net->out, n, net->ss, xhat, stream);
 }
@@ -357,7 +382,7 @@ cs_status ws_net_train_step(cs_unet* net, const float* xt, const float* d, const
     CS_PROPAGATE(ensure_bufs(net, dims, true));
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = (int64_t)dims[0] * dims[1] * dims[2];
-    CS_PROPAGATE(cs_nn_features(xt, d, n, eta, net->ss, net->f, stream));
+    CS_PROPAGATE(nn_features_det((const float2*)xt, (const float2*)d, n, eta, nullptr, net->fpart, net->ss, net->f, st));
     CS_PROPAGATE(cs_nn_target(xt, target, n, net->ss, net->tgt, stream));
     CS_PROPAGATE(forward(net, stream));
     float* lacc = net->ss + 1;

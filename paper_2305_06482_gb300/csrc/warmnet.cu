@@ -635,6 +635,51 @@ __global__ void features_kernel(const float2* __restrict__ x, const float2* __re
     }
 }
 
+// The same input scaling with a reproducible sum: per-block FP64 partials over a fixed grid of
+// kFeatBlocks blocks, summed in block order by every consumer, so the network input (and with it
+// the prediction) is bit-identical from run to run.  eta is read from eta_dev when that is given
+// (the solver's step lives on the device), else the host value is used.
+__global__ void feat_part_kernel(const float2* __restrict__ x, const float2* __restrict__ d, float eta_h,
+                                 const double* __restrict__ eta_dev, int64_t n, double* __restrict__ part) {
+    __shared__ double red[8];
+    const float eta = eta_dev ? (float)*eta_dev : eta_h;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 a = x[i], b = d[i];
+        acc += (double)(a.x * a.x + a.y * a.y) + (double)(eta * eta) * (double)(b.x * b.x + b.y * b.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        part[blockIdx.x] = s;
+    }
+}
+
+__global__ void features_det_kernel(const float2* __restrict__ x, const float2* __restrict__ d, int64_t n, float eta_h,
+                                    const double* __restrict__ eta_dev, const double* __restrict__ part,
+                                    float* __restrict__ ss, float* __restrict__ f) {
+    __shared__ float s_inv;
+    const float eta = eta_dev ? (float)*eta_dev : eta_h;
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int b = 0; b < kFeatBlocks; ++b) tot += part[b];
+        const float ssf = (float)tot;
+        if (blockIdx.x == 0) ss[0] = ssf;
+        s_inv = 1.f / (sqrtf(ssf / (float)n) + 1e-12f);
+    }
+    __syncthreads();
+    const float inv = s_inv;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        f[4 * i + 0] = x[i].x * inv;
+        f[4 * i + 1] = x[i].y * inv;
+        f[4 * i + 2] = d[i].x * eta * inv;
+        f[4 * i + 3] = d[i].y * eta * inv;
+    }
+}
+
 // out = x + s * delta (delta [n][2] in units of s)
 __global__ void apply_delta_kernel(const float2* __restrict__ x, const float* __restrict__ delta, int64_t n,
                                    const float* __restrict__ ss, float2* __restrict__ out) {
@@ -1081,6 +1126,21 @@ cs_status cs_nn_features(const float* xt, const float* d, int64_t n, float eta, 
     CS_LAUNCH_CHECK();
     return CS_OK;
 }
+
+}  // extern "C"
+
+namespace cs {
+cs_status nn_features_det(const float2* xt, const float2* d, int64_t n, float eta, const double* eta_dev, double* part,
+                          float* ss, float* f, cudaStream_t st) {
+    feat_part_kernel<<<kFeatBlocks, 256, 0, st>>>(xt, d, eta, eta_dev, n, part);
+    CS_LAUNCH_CHECK();
+    features_det_kernel<<<nn_grid(n), 256, 0, st>>>(xt, d, n, eta, eta_dev, part, ss, f);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+}  // namespace cs
+
+extern "C" {
 
 cs_status cs_nn_target(const float* xt, const float* xs, int64_t n, const float* ss, float* tgt, void* stream) {
     clear_error();

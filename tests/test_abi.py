@@ -112,3 +112,41 @@ def test_host_side_argument_checks(cs):
     assert L.cs_crop3d(fake, i3(8, 8, 8), i3(4, 0, 0), i3(8, 8, 8), fake, None) == 1  # box leaves the volume
     assert L.cs_crop3d(fake, i3(8, 8, 8), i3(-1, 0, 0), i3(4, 4, 4), fake, None) == 1
     assert b"crop box" in L.cs_last_error()
+
+
+def test_ctypes_structs_match_the_c_layout(tmp_path):
+    """Every struct of include/coilsketch.h that the binding mirrors has the same size and field
+    offsets in C (compiled here with the host compiler) and in ctypes."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    import paper_2305_06482_gb300 as cs
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    mirrors = {"cs_geom": cs._Geom, "cs_problem": cs._Problem, "cs_solve_params": cs._Params,
+               "cs_stats": cs._Stats, "cs_batch_item": cs._BatchItem}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "coilsketch.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            cfield = "lambda" if fname == "lam" else fname
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {cfield}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln.strip():
+            a, b, v = ln.split()
+            got[(a, b)] = int(v)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

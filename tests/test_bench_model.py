@@ -1,6 +1,7 @@
 """Host logic of the benchmark: the launch and byte model of one sketched reconstruction on the
 large cones workload against the counts of the ncu launch list of the same command (spread and
-interpolation 280 launches each, strided passes 960, x passes 240 each, for T = 20), and the
+interpolation 280 launches each, strided passes 960, x passes 240 each, for T = 20 outer
+iterations of K = 10 with m = 10 sketched coils), and the
 NUFFT byte models against their closed forms."""
 import bench
 
@@ -10,10 +11,10 @@ def test_launch_model_matches_the_measured_launch_list():
     T = 20
     expect = {"spread": 280, "interp": 280, "fft_plain": 960, "expand": 240, "reduce": 240}
     for stage, n in expect.items():
-        _, launches = bench.stage_bytes(stage, w, T, 1)
+        _, launches = bench.stage_bytes(stage, w, T, 10, 10, 1)
         assert launches == n, stage
-    b1, _ = bench.stage_bytes("spread", w, T, 1)
-    b3, _ = bench.stage_bytes("spread", w, T, 3)
+    b1, _ = bench.stage_bytes("spread", w, T, 10, 10, 1)
+    b3, _ = bench.stage_bytes("spread", w, T, 10, 10, 3)
     assert b3 == 3 * b1
 
 

@@ -269,3 +269,53 @@ def test_acc_prox_sgd_matches_oracle(use_graph):
         cs.recon_solve(plan, t(y), t(maps), lam, cs.REG_L1_WAVELET,
                        cs.SolveParams(K=K, sketch=False, do_pca=False, sgd_batch=B, sgd_coils=t(bad, np.int32),
                                       power_v0=t(v0)), wavelet_levels=3)
+
+
+def test_trace_records_match_the_oracle():
+    """The per-outer trace of Algorithm 1 (FISTA, graph and eager) against the FP64 oracle on the
+    same inputs: ||d^t||^2 of the true gradient at every x^t, the objective 1/2 ||A x^t - y||^2 +
+    lambda ||Psi x^t||_1, the distance of every iterate to a reference, no warm start (-1), and an
+    increasing device clock; the plain solver's trace records its iterate distances."""
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    shape, levels = (64, 64), 3
+    idx, maps, y, ops = _cart_problem(shape, C=8)
+    C, V, S, T, K, lam = 8, 3, 3, 4, 6, 5e-3
+    sk = philox.sketch_draw(11, 0, T, C, V, S)
+    v0 = synthdata.random_complex(shape, 5)
+    x_ref, its = solvers.coil_sketching(ops, maps, y, lam, "l1wav", sk.astype(np.float64), V=V, K=K, power_v0=v0,
+                                        levels=levels)
+    fwd, adj = ops(maps)
+    starts = [np.zeros(shape, complex)] + its[:-1]
+    g2 = [np.linalg.norm(adj(fwd(u) - y)) ** 2 for u in starts]
+    obj = [0.5 * np.linalg.norm(fwd(u) - y) ** 2 + lam * np.abs(wavelet.wavedec(u, levels)).sum() for u in starts]
+    ref = synthdata.random_complex(shape, 9)
+    dist = [np.linalg.norm(u - ref) ** 2 / np.linalg.norm(ref) ** 2 for u in its]
+    plan = cs.Plan(cs.CARTESIAN, shape, C, mask_idx=t(idx, np.int32))
+    for graph in (False, True):
+        x, st = cs.recon_solve(plan, t(y), t(maps), lam, cs.REG_L1_WAVELET,
+                               cs.SolveParams(T=T, K=K, V=V, S=S, sketches=t(sk), power_v0=t(v0), use_graph=graph,
+                                              x_ref=t(ref), trace=True, trace_objective=True), wavelet_levels=levels)
+        tr = st["trace"]
+        assert nrmse(h(x), x_ref) < 1e-4
+        assert tr.shape == (T, cs.TRACE_FIELDS)
+        assert np.allclose(tr[:, cs.TRACE_GRAD2], g2, rtol=1e-4)
+        assert np.allclose(tr[:, cs.TRACE_OBJECTIVE], obj, rtol=1e-5)
+        assert np.all(tr[:, cs.TRACE_ACCEPT] == -1)
+        assert np.allclose(tr[:, cs.TRACE_DIST2], dist, rtol=1e-4)
+        assert np.all(np.diff(tr[:, cs.TRACE_TIME_NS]) > 0)
+    # without the objective flag the field stays NaN; without x_ref the distance is -1
+    _, st = cs.recon_solve(plan, t(y), t(maps), lam, cs.REG_L1_WAVELET,
+                           cs.SolveParams(T=T, K=K, V=V, S=S, sketches=t(sk), power_v0=t(v0), trace=True),
+                           wavelet_levels=levels)
+    assert np.isnan(st["trace"][:, cs.TRACE_OBJECTIVE]).all() and np.all(st["trace"][:, cs.TRACE_DIST2] == -1)
+    # plain FISTA: one record per iteration, distances of the stored iterates
+    Kp = 7
+    iters = torch.empty((Kp,) + shape, dtype=torch.complex64, device="cuda")
+    _, st = cs.recon_solve(plan, t(y), t(maps), lam, cs.REG_L1_WAVELET,
+                           cs.SolveParams(K=Kp, sketch=False, do_pca=False, power_v0=t(v0), iterates=iters,
+                                          x_ref=t(ref), trace=True), wavelet_levels=levels)
+    hi = h(iters)
+    want = [np.linalg.norm(hi[k] - ref) ** 2 / np.linalg.norm(ref) ** 2 for k in range(Kp)]
+    assert np.allclose(st["trace"][:, cs.TRACE_DIST2], want, rtol=1e-5)
+    assert np.all(st["trace"][:, cs.TRACE_GRAD2] > 0)

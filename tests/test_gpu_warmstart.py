@@ -337,3 +337,46 @@ def test_training_and_warm_start_in_algorithm_1():
     # gradients are summed atomically), so only convergence to the same neighbourhood is required
     assert len(acc) == len(e_warm) == len(e_plain) == T
     assert np.isfinite(e_warm).all() and e_warm[-1] <= 2.0 * e_plain[-1]
+
+
+def test_warm_start_decided_on_the_device_matches_the_host_loop():
+    """recon_solve with the network as its warm start (prediction, two sub-problem objectives and
+    the choice of FISTA's start all on the device) takes the same accept decisions and reaches the
+    same iterates as the host-driven loop that reads the two objectives on the host; the captured
+    outer iteration replays to the eager result."""
+    import paper_2305_06482_gb300 as cs
+    import paper_2305_06482_gb300.warmstart as ws
+    img = (32, 48, 48)
+    lam, V, S, T, K, levels = 2e-3, 2, 2, 5, 4, 2
+    pairs = []
+    for seed in (101, 102):
+        plan, y, maps = _problem(seed)
+        su = ws.setup(plan, y, maps, lam, V, S, T, seed, synthdata.phantom_torch(img, seed=seed + 50), levels)
+        pairs += ws.run(su, T, K, record_pairs=1, tight_K=40)[1]
+    net = ws.UNet(seed=0)
+    ws.train(net, pairs, steps=150, lr=2e-3)
+    plan, y, maps = _problem(999)
+    v0 = synthdata.phantom_torch(img, seed=1049)
+    su = ws.setup(plan, y, maps, lam, V, S, T, 999, v0, levels)
+    host = []
+    _, _, acc = ws.run(su, T, K, net=net, callback=lambda t, x: host.append(x.clone()))
+    runs = []
+    for graph in (False, True):
+        iters = torch.empty((T,) + img, dtype=torch.complex64, device="cuda")
+        x, st = cs.recon_solve(plan, y, maps, lam, cs.REG_L1_WAVELET,
+                               cs.SolveParams(T=T, K=K, V=V, S=S, seed=999, power_v0=v0, warm=net, use_graph=graph,
+                                              iterates=iters, trace=True), wavelet_levels=levels)
+        dec = st["trace"][:, cs.TRACE_ACCEPT]
+        assert list(dec.astype(int)) == [int(a) for a in acc], (dec, acc)
+        assert st["warm_accepted"] == sum(acc)
+        # the two paths' FP32 steps differ at the 1e-7 level (the host loop passes the step as a
+        # float, the spreading sums in a different order); an accepted prediction goes through the
+        # network's BF16 convolutions, which amplify that, so the iterates are held to the
+        # final-image tolerance
+        for k in range(T):
+            assert float((iters[k] - host[k]).norm() / host[k].norm()) < 1e-4
+        runs.append(x)
+    assert float((runs[0] - runs[1]).norm() / runs[0].norm()) < 1e-6
+    print(f"\\nwarm starts accepted {sum(acc)}/{T}")
+    with pytest.raises(cs.CoilSketchError):          # the warm start serves sketched FISTA only
+        cs.recon_solve(plan, y, maps, lam, cs.REG_L2, cs.SolveParams(T=2, K=2, V=V, S=S, warm=net))
