@@ -90,24 +90,28 @@ typedef struct {
     float alpha;         /* oversampling ratio used for the Kaiser-Bessel beta (1.25)         */
     const float* traj;   /* device, [N][ndim] cycles/pixel                                    */
     const float* dcf;    /* device, [N] density compensation w (the operator applies sqrt w)  */
-    int tile[3];         /* tile size per axis for binning; 0 = library default / autotuned   */
+    int tile[3];         /* tile size per axis for binning (>= 4); 0 = library default (16)  */
 } cs_geom;
 /* Size limits: image sizes even, nx <= 512; grid sizes even, >= the image and <= 800 (the FFT
  * length limit) with prime factors in {2, 3, 5, 7, 11}; non-Cartesian plans need grid points x
- * max_coils < 2^31.  Violations return CS_ERR_UNSUPPORTED_SIZE. */
+ * max_coils < 2^31 and at most 49152 tiles.  Violations return CS_ERR_UNSUPPORTED_SIZE.
+ * Samples are ordered by tile and, inside a tile, by halo class (the set of upper neighbour tiles
+ * their kernel box reaches), each run in acquisition order. */
 
 cs_status cs_plan_create(const cs_geom* g, void* stream, cs_plan** out);
 cs_status cs_plan_destroy(cs_plan* plan);
 
 /* Read back the binning of a non-Cartesian plan (device outputs; tests compare them bit-exactly
- * with the CPU restatement): perm[N] sorted position -> sample index, tile_off[ntiles+1],
- * j0[N][ndim] first kernel-box index per axis (unwrapped), ntiles_out[3] tiles per axis. */
+ * with the CPU restatement): perm[N] sorted position -> sample index (stable by tile, then halo
+ * class), tile_off[ntiles+1], j0[N][ndim] first kernel-box index per axis (unwrapped), ntiles_out[3]
+ * tiles per axis (a remainder narrower than 4 widens the last tile). */
 cs_status cs_plan_binning(const cs_plan* plan, int32_t* perm, int32_t* tile_off, int32_t* j0,
                           int* ntiles_out, void* stream);
 
 /* Gridding launch parameters of a non-Cartesian plan: coils per warp of the interpolation (1..32)
  * and of the spreading (1..16), consecutive sorted samples per warp of each (1..4096).  Plans
- * start at 16 / 64 / 16 / 64.  Any values give the same results; only the speed changes.
+ * start at 16 / 64 / 16 / 64.  Any values give results equal up to rounding order; only the speed
+ * changes.
  * cs_plan_autotune: times the interpolation and the spreading of `ncoils` coils (reps timed
  * launches after one untimed, CUDA events on `stream`) for coils per warp in {8, 16, 32} (interp)
  * or {8, 16} (spread) and samples per warp in {32, 64, 128}, on the plan's own scratch buffers
@@ -118,6 +122,21 @@ cs_status cs_plan_binning(const cs_plan* plan, int32_t* perm, int32_t* tile_off,
 cs_status cs_plan_set_gridding(cs_plan* plan, int interp_coils, int interp_chunk, int spread_coils,
                                int spread_chunk);
 cs_status cs_plan_autotune(cs_plan* plan, int ncoils, int reps, int* choice, float* ms, void* stream);
+
+/* Spreading mode of a non-Cartesian plan (the adjoint's first step, Sec. 2.1 gridding).
+ * on = 0 (default): producer-computes - one warp per run of sorted samples, rows, columns and
+ *   planes leaving its sliding window added to the grid with atomic adds; fastest, results equal
+ *   up to the rounding order of those additions, which depends on scheduling.
+ * on = 1: owner-computes - atomics-free and bit-reproducible: every tile of the grid is
+ *   accumulated by one warp at a time from its own samples and the samples of its lower
+ *   neighbour tiles whose kernel box reaches it (the halo classes of the binning), in a fixed
+ *   order; a tile with more than item_visits sample visits (64..2^20; 0 = keep the current value,
+ *   initially 4096) is split into work items whose sums go to private partial slots that a
+ *   second kernel adds to the grid in slot order.  Slower (every sample is visited by the owners
+ *   of all tiles its box touches).  Building the work items is synchronous and allocates the
+ *   partial slots on the device.  Cartesian plans ignore the call (their sampling adjoint has no
+ *   accumulation). */
+cs_status cs_plan_set_deterministic(cs_plan* plan, int on, int item_visits);
 
 /* ------------------------------------------------------------------------------------------
  * sense_fwd: y = A x for `ncoils` maps (Eq. 1, Eq. 5): y_c = w^1/2 (.) F{c_c (.) x}.

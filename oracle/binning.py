@@ -8,8 +8,14 @@ al. 2005) and gives no discretisation details; these are the readings used on bo
   on CPU and GPU;
 * kernel box of width W = 4: the W grid indices j0 .. j0+W-1 with j0 = floor(g) - 1
   (= floor(g - W/2) + 1 for even W), wrapped modulo G;
-* tile of a sample: floor(wrap(j0) / T) per axis, linearised (z, y, x) with x fastest;
-* samples are ordered by a stable counting sort on the tile id.
+* tile of a sample: floor(wrap(j0) / T) per axis, linearised (z, y, x) with x fastest; an axis
+  whose last tile would be narrower than the kernel (G mod T in 1..W-1) folds that remainder
+  into the previous tile, so that no box spans more than two tiles;
+* halo class of a sample: bit a (z = 4, y = 2, x = 1) is set when its box reaches past its own
+  tile into the next tile along axis a (wrapping), i.e. wrap(j0) - tile start >= tile width - W + 1,
+  and only on axes with more than one tile.  Each tile's grid points are accumulated from its own
+  samples and from the samples of its lower neighbours whose class reaches it;
+* samples are ordered by a stable counting sort on the key tile * 8 + class.
 """
 from __future__ import annotations
 
@@ -58,17 +64,51 @@ def kernel_box_start(g):
     return np.floor(np.asarray(g, dtype=np.float64)).astype(np.int64) - (KB_WIDTH // 2 - 1)
 
 
-def tile_ids(j0, grid, tile):
-    """Linear tile id of each sample from its wrapped box start, (z, y, x) with x fastest."""
+def tiles_per_axis(grid, tile):
+    """Tiles along each axis: ceil(G / T), or floor(G / T) when the remainder is narrower than
+    the kernel (it then widens the last tile)."""
     grid = np.asarray(grid, dtype=np.int64)
     tile = np.asarray(tile, dtype=np.int64)
+    rem = grid % tile
+    return np.where((rem > 0) & (rem < KB_WIDTH) & (grid >= tile), grid // tile, -(-grid // tile))
+
+
+def _axis_tiles(j0, grid, tile):
+    grid = np.asarray(grid, dtype=np.int64)
+    tile = np.asarray(tile, dtype=np.int64)
+    nt = tiles_per_axis(grid, tile)
     jw = np.mod(j0, grid[None, :])
-    t = jw // tile[None, :]
-    ntiles = -(-grid // tile)
+    t = np.minimum(jw // tile[None, :], nt[None, :] - 1)
+    start = t * tile[None, :]
+    width = np.where(t == nt[None, :] - 1, grid[None, :] - start, tile[None, :])
+    return t, nt, jw, start, width
+
+
+def tile_ids(j0, grid, tile):
+    """Linear tile id of each sample from its wrapped box start, (z, y, x) with x fastest."""
+    t, ntiles, _, _, _ = _axis_tiles(j0, grid, tile)
     lin = np.zeros(j0.shape[0], dtype=np.int64)
     for ax in range(j0.shape[1]):
         lin = lin * ntiles[ax] + t[:, ax]
     return lin, ntiles
+
+
+def halo_class(j0, grid, tile):
+    """Bits (z = 4, y = 2, x = 1 for 3D; y = 2, x = 1 for 2D) of the axes along which a sample's box
+    reaches into the next tile (only axes with more than one tile)."""
+    t, nt, jw, start, width = _axis_tiles(j0, grid, tile)
+    nd = j0.shape[1]
+    cls = np.zeros(j0.shape[0], dtype=np.int64)
+    for ax in range(nd):
+        reach = (jw[:, ax] - start[:, ax] >= width[:, ax] - (KB_WIDTH - 1)) & (nt[ax] > 1)
+        cls |= reach.astype(np.int64) << (nd - 1 - ax)
+    return cls
+
+
+def sort_keys(j0, grid, tile):
+    """Sort key tile * 8 + halo class of every sample, and the tiles per axis."""
+    lin, nt = tile_ids(j0, grid, tile)
+    return lin * 8 + halo_class(j0, grid, tile), nt
 
 
 def tile_sort(tid, n_tiles_total):
@@ -91,3 +131,15 @@ def tile_sort_fast(tid, n_tiles_total):
     offsets = np.zeros(n_tiles_total + 1, dtype=np.int64)
     offsets[1:] = np.cumsum(counts)
     return perm, offsets
+
+
+def sample_order(j0, grid, tile):
+    """The plan's sample order: permutation (sorted position -> sample index) by the stable key
+    tile * 8 + halo class, and the per-tile offsets [ntiles + 1]."""
+    key, nt = sort_keys(j0, grid, tile)
+    ntot = int(np.prod(nt))
+    perm = np.argsort(key, kind="stable")
+    counts = np.bincount(key // 8, minlength=ntot)
+    offsets = np.zeros(ntot + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(counts)
+    return perm, offsets, nt

@@ -84,6 +84,7 @@ EXPORTED = [
     "cs_nn_maxpool2", "cs_nn_maxpool2_bwd", "cs_nn_upconv2", "cs_nn_upconv2_bwd", "cs_nn_slice",
     "ws_net_create", "ws_net_destroy", "ws_net_infer", "ws_net_train_step", "ws_net_param", "ws_net_save",
     "ws_net_load", "cs_crop3d", "cs_wait_selftest", "cs_plan_set_gridding", "cs_plan_autotune",
+    "cs_plan_set_deterministic",
 ]
 STAGES = {"spread": 0, "interp": 1, "fft_plain": 2, "expand": 3, "reduce": 4}
 
@@ -139,6 +140,7 @@ def lib():
             "ws_net_save": ([vp, ctypes.c_char_p], i), "ws_net_load": ([vp, ctypes.c_char_p], i),
             "cs_crop3d": ([vp, vp, vp, vp, vp, vp], i), "cs_wait_selftest": ([i, i64, vp], i),
             "cs_plan_set_gridding": ([vp, i, i, i, i], i), "cs_plan_autotune": ([vp, i, i, vp, vp, vp], i),
+            "cs_plan_set_deterministic": ([vp, i, i], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -227,6 +229,11 @@ class Plan:
     def set_gridding(self, interp_coils, interp_chunk, spread_coils, spread_chunk):
         """Coils and samples per warp of the gridding kernels (non-Cartesian plans)."""
         _check(lib().cs_plan_set_gridding(self._h, interp_coils, interp_chunk, spread_coils, spread_chunk))
+
+    def set_deterministic(self, on=True, item_visits=0):
+        """Owner-computes (atomics-free, bit-reproducible) spreading on or off; item_visits caps the
+        sample visits of one spreading work item (0 = keep)."""
+        _check(lib().cs_plan_set_deterministic(self.handle, int(bool(on)), int(item_visits)))
 
     def autotune(self, ncoils, reps=3, stream=None):
         """Time the gridding candidates for `ncoils` coils and keep the fastest; returns

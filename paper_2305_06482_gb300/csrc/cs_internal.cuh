@@ -91,6 +91,23 @@ constexpr int kLinePad = 17;
 constexpr int kPassThreads = 256;
 
 // ------------------------------------------------------------------------------------------
+// Owner-computes spreading (nufft.cu): every tile of the grid is accumulated by exactly one warp at
+// a time, from its own samples and the samples of its lower neighbour tiles whose kernel box
+// reaches it; a tile with more sample visits than the plan's item size is split into items whose
+// sums land in private partial slots, added to the grid afterwards in a fixed order.
+struct GItem {
+    int tile;      // linear tile id (z, y, x; x fastest)
+    int slot;      // partial slot, or -1: the item writes the grid itself
+    int r0, r1;    // its sample ranges [r0, r1) in the plan's range list
+};
+struct GRange {
+    int start, count;   // consecutive sorted samples
+};
+struct GRed {
+    int tile, s0, ns;   // the tile's partial slots s0 .. s0 + ns - 1, added in this order
+};
+
+// ------------------------------------------------------------------------------------------
 // Plan
 }  // namespace cs
 
@@ -120,11 +137,22 @@ struct cs_plan {
     int32_t* perm = nullptr;      // [N] sorted position -> sample index
     int32_t* j0 = nullptr;        // [N][3] unwrapped first box index (user order), for tests
     int32_t* tile_off = nullptr;  // [ntiles + 1]
+    int32_t* class_off = nullptr; // [ntiles * 8 + 1] offsets of every (tile, halo class) run
     int tile[3] = {1, 1, 1};
-    int ntiles[3] = {1, 1, 1};
+    int ntiles[3] = {1, 1, 1};    // a remainder narrower than the kernel widens the last tile
+    int wmax[3] = {1, 1, 1};      // widest tile per axis (the partial-slot geometry)
     int64_t ntiles_total = 0;
     int interp_chunk = 0;         // consecutive sorted samples per warp, interpolation
-    int spread_chunk = 0;         // consecutive sorted samples per warp, spreading
+    int spread_chunk = 0;         // consecutive sorted samples per warp, producer spreading
+    int deterministic = 0;        // 1: owner-computes spreading (atomics-free, bit-reproducible)
+    int owner_item = 4096;        // largest sample visits of one owner-computes work item
+    cs::GItem* gitems = nullptr;  // spreading work items, longest first
+    int n_gitems = 0;
+    cs::GRange* granges = nullptr;
+    cs::GRed* greds = nullptr;    // tiles with partial slots
+    int n_greds = 0;
+    int n_slots = 0;
+    float2* gpart = nullptr;      // partial slots [n_slots][wmax z][wmax y][wmax x][<= 16 coils]
     int interp_coils = 16;        // coils per warp in interpolation (8, 16 or 32)
     int spread_coils = 16;        // coils per warp in spreading (8 or 16)
     float* phi = nullptr;         // KB kernel table [2049] on [0, 2]
@@ -149,6 +177,8 @@ cs_status fft_to_image(const cs_plan* p, const float2* maps_v, int V, const floa
 // NUFFT binning / interpolation / spreading (nufft.cu)
 cs_status nufft_bin(cs_plan* p, const float* traj, const float* dcf, cudaStream_t st);
 cs_status nufft_records(cs_plan* p, cudaStream_t st);
+cs_status nufft_owner_build(cs_plan* p);   // spreading work items from the class offsets (synchronous)
+void nufft_owner_free(cs_plan* p);
 cs_status nufft_interp(const cs_plan* p, int ncoils, float2* y, const float2* ysub, cudaStream_t st);
 cs_status nufft_spread(const cs_plan* p, int ncoils, const float2* y, int sorted_in, cudaStream_t st);
 cs_status nufft_interp_spread(const cs_plan* p, int ncoils, cudaStream_t st);

@@ -12,6 +12,8 @@
 #include <cmath>
 #include <cstdio>
 #include <type_traits>
+#include <algorithm>
+#include <vector>
 
 #include "cs_internal.cuh"
 
@@ -26,12 +28,28 @@ __device__ __forceinline__ int wrapi(int j, int G) {
 
 // ------------------------------------------------------------------------------------------
 // binning
+//
+// Every sample gets a tile (floor(wrap(j0) / T) per axis; a remainder narrower than the kernel
+// widens the last tile) and a halo class (bit a: its box reaches the next tile along axis a,
+// z = 4, y = 2, x = 1; only axes with more than one tile).  Samples are stable-sorted by the key
+// tile * 8 + class in two stable counting-sort passes (least significant key first: class, then
+// tile), so that every tile's samples come in class runs, each in acquisition order.
+__device__ __forceinline__ void tile_of(int jw, int G, int T, int nt, int* t, int* start, int* width) {
+    int tt = jw / T;
+    tt = tt < nt - 1 ? tt : nt - 1;
+    *t = tt;
+    *start = tt * T;
+    *width = (tt == nt - 1) ? G - tt * T : T;
+}
+
 __global__ void bin_keys_kernel(const float* __restrict__ traj, int64_t N, int nd, int3 G, int3 T, int3 nt,
-                                float* __restrict__ gout, int32_t* __restrict__ j0out, int32_t* __restrict__ key) {
+                                float* __restrict__ gout, int32_t* __restrict__ j0out, int32_t* __restrict__ tkey,
+                                int32_t* __restrict__ ckey) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     int Gs[3] = {G.x, G.y, G.z}, Ts[3] = {T.x, T.y, T.z}, nts[3] = {nt.x, nt.y, nt.z};
     int64_t lin = 0;
+    int cls = 0;
     for (int ax = 0; ax < 3; ++ax) {
         int jj = 0;
         float g = 0.f;
@@ -44,22 +62,26 @@ __global__ void bin_keys_kernel(const float* __restrict__ traj, int64_t N, int n
             j0out[i * nd + a] = jj;
         }
         gout[i * 3 + ax] = g;
-        const int t = wrapi(jj, Gs[ax]) / Ts[ax];
+        int t, st, w;
+        const int jw = wrapi(jj, Gs[ax]);
+        tile_of(jw, Gs[ax], Ts[ax], nts[ax], &t, &st, &w);
         lin = lin * nts[ax] + t;
+        if (ax >= 3 - nd && nts[ax] > 1 && jw - st >= w - (kW - 1)) cls |= 1 << (2 - ax);
     }
-    key[i] = (int32_t)lin;
+    tkey[i] = (int32_t)lin;
+    ckey[i] = cls;
 }
 
-constexpr int kRankChunk = 2048;
+constexpr int kRankChunk = 8192;
 
-// One warp per chunk of kRankChunk consecutive samples: stable rank of each sample among the
-// chunk's samples of the same tile (warp match + prefix popcount, processed in index order).
-__global__ void chunk_rank_kernel(const int32_t* __restrict__ key, int64_t N, int ntiles,
+// One warp per chunk of kRankChunk consecutive entries: stable rank of each entry among the
+// chunk's entries of the same key (warp match + prefix popcount, processed in index order).
+__global__ void chunk_rank_kernel(const int32_t* __restrict__ key, int64_t N, int nkeys,
                                   int32_t* __restrict__ lrank, int32_t* __restrict__ counts) {
     extern __shared__ int32_t running[];
     const int lane = threadIdx.x;
     const int64_t chunk = blockIdx.x;
-    for (int t = lane; t < ntiles; t += 32) running[t] = 0;
+    for (int t = lane; t < nkeys; t += 32) running[t] = 0;
     __syncwarp();
     const int64_t s0 = chunk * kRankChunk;
     const unsigned lt = (1u << lane) - 1u;
@@ -77,28 +99,28 @@ __global__ void chunk_rank_kernel(const int32_t* __restrict__ key, int64_t N, in
         if (valid && lane == leader) running[k] = base + __popc(peers);
         __syncwarp();
     }
-    for (int t = lane; t < ntiles; t += 32) counts[chunk * (int64_t)ntiles + t] = running[t];
+    for (int t = lane; t < nkeys; t += 32) counts[chunk * (int64_t)nkeys + t] = running[t];
 }
 
-// per tile: exclusive scan over chunks (in place) and the tile total
-__global__ void chunk_scan_kernel(int32_t* __restrict__ counts, int64_t nchunks, int ntiles, int32_t* __restrict__ total) {
+// per key: exclusive scan over chunks (in place) and the key total
+__global__ void chunk_scan_kernel(int32_t* __restrict__ counts, int64_t nchunks, int nkeys, int32_t* __restrict__ total) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ntiles) return;
+    if (t >= nkeys) return;
     int32_t run = 0;
     for (int64_t c = 0; c < nchunks; ++c) {
-        const int32_t v = counts[c * ntiles + t];
-        counts[c * ntiles + t] = run;
+        const int32_t v = counts[c * nkeys + t];
+        counts[c * nkeys + t] = run;
         run += v;
     }
     total[t] = run;
 }
 
-// single-CTA exclusive scan of tile totals -> tile_off[ntiles + 1]
-__global__ void tile_scan_kernel(const int32_t* __restrict__ total, int ntiles, int32_t* __restrict__ off) {
+// single-CTA exclusive scan of key totals -> off[nkeys + 1]
+__global__ void key_scan_kernel(const int32_t* __restrict__ total, int nkeys, int32_t* __restrict__ off) {
     __shared__ int32_t part[1024];
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int per = (ntiles + nt - 1) / nt;
-    const int b = tid * per, e = min(ntiles, b + per);
+    const int per = (nkeys + nt - 1) / nt;
+    const int b = tid * per, e = min(nkeys, b + per);
     int32_t s = 0;
     for (int i = b; i < e; ++i) s += total[i];
     part[tid] = s;
@@ -110,7 +132,7 @@ __global__ void tile_scan_kernel(const int32_t* __restrict__ total, int ntiles, 
             part[i] = run;
             run += v;
         }
-        off[ntiles] = run;
+        off[nkeys] = run;
     }
     __syncthreads();
     int32_t run = part[tid];
@@ -120,20 +142,56 @@ __global__ void tile_scan_kernel(const int32_t* __restrict__ total, int ntiles, 
     }
 }
 
-__global__ void bin_scatter_kernel(const int32_t* __restrict__ key, const int32_t* __restrict__ lrank,
-                                   const int32_t* __restrict__ cbase, const int32_t* __restrict__ toff, int ntiles,
-                                   const float* __restrict__ g, const float* __restrict__ dcf, int64_t N,
-                                   int32_t* __restrict__ perm, float* __restrict__ gs, float* __restrict__ ws) {
+// sorted position of entry i: key offset + rank of its chunk + rank inside the chunk
+__global__ void rank_scatter_kernel(const int32_t* __restrict__ key, const int32_t* __restrict__ lrank,
+                                    const int32_t* __restrict__ cbase, const int32_t* __restrict__ koff, int nkeys,
+                                    int64_t N, int32_t* __restrict__ order) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int k = key[i];
     const int64_t chunk = i / kRankChunk;
-    const int64_t pos = (int64_t)toff[k] + cbase[chunk * ntiles + k] + lrank[i];
-    perm[pos] = (int32_t)i;
-    gs[pos * 3 + 0] = g[i * 3 + 0];
-    gs[pos * 3 + 1] = g[i * 3 + 1];
-    gs[pos * 3 + 2] = g[i * 3 + 2];
+    order[(int64_t)koff[k] + cbase[chunk * nkeys + k] + lrank[i]] = (int32_t)i;
+}
+
+__global__ void gather_i32_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ idx, int64_t N,
+                                  int32_t* __restrict__ dst) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) dst[i] = src[idx[i]];
+}
+
+// final order: perm[pos] = sample; sorted grid coordinates, sqrt(dcf) and keys
+__global__ void bin_final_kernel(const int32_t* __restrict__ perm1, const int32_t* __restrict__ perm2,
+                                 const float* __restrict__ g, const float* __restrict__ dcf,
+                                 const int32_t* __restrict__ tkey, const int32_t* __restrict__ ckey, int64_t N,
+                                 int32_t* __restrict__ perm, float* __restrict__ gs, float* __restrict__ ws,
+                                 int32_t* __restrict__ skey) {
+    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= N) return;
+    const int32_t i = perm1[perm2[pos]];
+    perm[pos] = i;
+    gs[pos * 3 + 0] = g[(int64_t)i * 3 + 0];
+    gs[pos * 3 + 1] = g[(int64_t)i * 3 + 1];
+    gs[pos * 3 + 2] = g[(int64_t)i * 3 + 2];
     ws[pos] = sqrtf(dcf[i]);
+    skey[pos] = tkey[i] * 8 + ckey[i];
+}
+
+// off[k] = first sorted position whose key is >= k (k = 0 .. nkeys), by binary search
+__global__ void lower_bound_kernel(const int32_t* __restrict__ skey, int64_t N, int nkeys, int32_t* __restrict__ off) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > nkeys) return;
+    int64_t lo = 0, hi = N;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (skey[mid] < k) lo = mid + 1;
+        else hi = mid;
+    }
+    off[k] = (int32_t)lo;
+}
+
+__global__ void tile_off_kernel(const int32_t* __restrict__ coff, int ntiles, int32_t* __restrict__ toff) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t <= ntiles) toff[t] = coff[(int64_t)t * 8];
 }
 
 cs_status nufft_bin(cs_plan* p, const float* traj, const float* dcf, cudaStream_t st) {
@@ -143,14 +201,20 @@ cs_status nufft_bin(cs_plan* p, const float* traj, const float* dcf, cudaStream_
     CS_REQUIRE(ntiles <= 49152, CS_ERR_UNSUPPORTED_SIZE, "too many tiles (%d); use a larger tile", ntiles);
     const int64_t nchunks = (N + kRankChunk - 1) / kRankChunk;
     float* g = nullptr;
-    int32_t *key = nullptr, *lrank = nullptr, *counts = nullptr, *total = nullptr;
-    cs_status rc = CS_OK;
+    int32_t *tkey = nullptr, *ckey = nullptr, *lrank = nullptr, *counts = nullptr, *total = nullptr, *koff = nullptr;
+    int32_t *perm1 = nullptr, *key2 = nullptr, *perm2 = nullptr, *skey = nullptr;
     auto cleanup = [&]() {
         cudaFree(g);
-        cudaFree(key);
+        cudaFree(tkey);
+        cudaFree(ckey);
         cudaFree(lrank);
         cudaFree(counts);
         cudaFree(total);
+        cudaFree(koff);
+        cudaFree(perm1);
+        cudaFree(key2);
+        cudaFree(perm2);
+        cudaFree(skey);
     };
 #define BIN_TRY(call)                                                                   \
     do {                                                                                \
@@ -162,31 +226,51 @@ cs_status nufft_bin(cs_plan* p, const float* traj, const float* dcf, cudaStream_
         }                                                                               \
     } while (0)
     BIN_TRY(cudaMalloc(&g, sizeof(float) * 3 * N));
-    BIN_TRY(cudaMalloc(&key, sizeof(int32_t) * N));
+    BIN_TRY(cudaMalloc(&tkey, sizeof(int32_t) * N));
+    BIN_TRY(cudaMalloc(&ckey, sizeof(int32_t) * N));
     BIN_TRY(cudaMalloc(&lrank, sizeof(int32_t) * N));
-    BIN_TRY(cudaMalloc(&counts, sizeof(int32_t) * nchunks * ntiles));
-    BIN_TRY(cudaMalloc(&total, sizeof(int32_t) * ntiles));
+    const int nkmax = ntiles > 8 ? ntiles : 8;   // the class pass has 8 keys
+    BIN_TRY(cudaMalloc(&counts, sizeof(int32_t) * nchunks * nkmax));
+    BIN_TRY(cudaMalloc(&total, sizeof(int32_t) * nkmax));
+    BIN_TRY(cudaMalloc(&koff, sizeof(int32_t) * (nkmax + 1)));
+    BIN_TRY(cudaMalloc(&perm1, sizeof(int32_t) * N));
+    BIN_TRY(cudaMalloc(&key2, sizeof(int32_t) * N));
+    BIN_TRY(cudaMalloc(&perm2, sizeof(int32_t) * N));
+    BIN_TRY(cudaMalloc(&skey, sizeof(int32_t) * N));
     const int3 G3 = make_int3(p->grid[0], p->grid[1], p->grid[2]);
     const int3 T3 = make_int3(p->tile[0], p->tile[1], p->tile[2]);
     const int3 nt3 = make_int3(p->ntiles[0], p->ntiles[1], p->ntiles[2]);
     const unsigned nb = (unsigned)((N + 255) / 256);
-    bin_keys_kernel<<<nb, 256, 0, st>>>(traj, N, nd, G3, T3, nt3, g, p->j0, key);
+    bin_keys_kernel<<<nb, 256, 0, st>>>(traj, N, nd, G3, T3, nt3, g, p->j0, tkey, ckey);
     BIN_TRY(cudaGetLastError());
-    const size_t rsm = sizeof(int32_t) * ntiles;
-    BIN_TRY(cudaFuncSetAttribute(chunk_rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
-    chunk_rank_kernel<<<(unsigned)nchunks, 32, rsm, st>>>(key, N, ntiles, lrank, counts);
+    // one stable counting-sort pass: order[pos] = index of the entry at sorted position pos
+    auto pass = [&](const int32_t* key, int nkeys, int32_t* order) -> cudaError_t {
+        const size_t rsm = sizeof(int32_t) * nkeys;
+        cudaError_t e = cudaFuncSetAttribute(chunk_rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm);
+        if (e != cudaSuccess) return e;
+        chunk_rank_kernel<<<(unsigned)nchunks, 32, rsm, st>>>(key, N, nkeys, lrank, counts);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        chunk_scan_kernel<<<(nkeys + 127) / 128, 128, 0, st>>>(counts, nchunks, nkeys, total);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        key_scan_kernel<<<1, 1024, 0, st>>>(total, nkeys, koff);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        rank_scatter_kernel<<<nb, 256, 0, st>>>(key, lrank, counts, koff, nkeys, N, order);
+        return cudaGetLastError();
+    };
+    BIN_TRY(pass(ckey, 8, perm1));                                   // by class (stable)
+    gather_i32_kernel<<<nb, 256, 0, st>>>(tkey, perm1, N, key2);
     BIN_TRY(cudaGetLastError());
-    chunk_scan_kernel<<<(ntiles + 127) / 128, 128, 0, st>>>(counts, nchunks, ntiles, total);
+    BIN_TRY(pass(key2, ntiles, perm2));                              // then by tile (stable)
+    bin_final_kernel<<<nb, 256, 0, st>>>(perm1, perm2, g, dcf, tkey, ckey, N, p->perm, p->gsorted, p->wsorted, skey);
     BIN_TRY(cudaGetLastError());
-    tile_scan_kernel<<<1, 1024, 0, st>>>(total, ntiles, p->tile_off);
+    lower_bound_kernel<<<(ntiles * 8 + 1 + 255) / 256, 256, 0, st>>>(skey, N, ntiles * 8, p->class_off);
     BIN_TRY(cudaGetLastError());
-    bin_scatter_kernel<<<nb, 256, 0, st>>>(key, lrank, counts, p->tile_off, ntiles, g, dcf, N, p->perm,
-                                           p->gsorted, p->wsorted);
+    tile_off_kernel<<<(ntiles + 1 + 255) / 256, 256, 0, st>>>(p->class_off, ntiles, p->tile_off);
     BIN_TRY(cudaGetLastError());
     BIN_TRY(cudaStreamSynchronize(st));   // the scratch buffers are freed below
     cleanup();
 #undef BIN_TRY
-    return rc;
+    return CS_OK;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -277,9 +361,9 @@ __global__ void sample_record_kernel(const float* __restrict__ gs, const float* 
 }
 
 // Stage the records of samples [base, base + n) (n <= kStage) into the warp's shared buffer.
-__device__ __forceinline__ void stage_records(const GridArgs& A, int64_t base, int n, float* wrec, int lane) {
+__device__ __forceinline__ void stage_records(const float* __restrict__ rec, int64_t base, int n, float* wrec, int lane) {
     __syncwarp();
-    const float4* src = reinterpret_cast<const float4*>(A.rec + base * kRec);
+    const float4* src = reinterpret_cast<const float4*>(rec + base * kRec);
     float4* dst = reinterpret_cast<float4*>(wrec);
     float4 t[kStage * kRec / 4 / 32];
 #pragma unroll
@@ -357,8 +441,8 @@ __device__ __forceinline__ void set_offsets(int (&off)[kW], int j0, int G, int s
 #ifndef CS_SPREAD_MINB_P2
 #define CS_SPREAD_MINB_P2 4
 #endif
-// decode the next sample's record head one sample ahead (measured: helps the spreading, not the
-// interpolation, whose registers are tighter)
+// decode the next sample's record head one sample ahead in the interpolation (off: its registers
+// are tight)
 #ifndef CS_INTERP_HEAD_PREFETCH
 #define CS_INTERP_HEAD_PREFETCH 0
 #endif
@@ -401,7 +485,7 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
     int cy = kNoPlane, cx = kNoPlane;
     for (int base = s0; base < s1; base += kStage) {
         const int n = min(kStage, s1 - base);
-        stage_records(A, base, n, wrec, lane);
+        stage_records(A.rec, base, n, wrec, lane);
 #if CS_INTERP_HEAD_PREFETCH
         BoxHead Bn = box_head(wrec);
 #endif
@@ -512,6 +596,10 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
     }
 }
 
+// Producer-computes spreading (the default): one sample stream per warp, leaving rows, columns and
+// planes added to the grid with float2 atomics, so the order of the additions to a grid point
+// depends on scheduling (results equal up to rounding order).  The owner-computes kernel below is
+// the deterministic alternative.
 template <int S, int P>
 __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
     spread_kernel(GridArgs A, const float2* __restrict__ yin, int sorted_in) {
@@ -559,7 +647,7 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
     };
     for (int base = s0; base < s1; base += kStage) {
         const int n = min(kStage, s1 - base);
-        stage_records(A, base, n, wrec, lane);
+        stage_records(A.rec, base, n, wrec, lane);
         float2 vnext = load_v(base, wrec);
 #if CS_SPREAD_HEAD_PREFETCH
         BoxHead Bn = box_head(wrec);
@@ -651,6 +739,258 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
     for (int p = 0; p < P; ++p) flush_plane(p);
 }
 
+// Owner-computes spreading.  One warp runs one work item: a tile of the grid (its region) and a
+// list of sorted-sample ranges (the tile's own samples and those of its lower neighbours whose box
+// reaches it, or a chunk of that list).  The warp keeps the same residue-indexed sliding window as
+// the interpolation; when a row, column or plane leaves the window, the points of it that lie in
+// the region are added to the target by a plain read-modify-write - the region belongs to this
+// warp alone, so no other thread touches those points while it runs, and every point receives its
+// contributions in the fixed order of the item's sample list.  Points outside the region are
+// dropped (their owner adds them).  The target is the grid itself (item slot -1) or the item's
+// private partial slot, laid out [z][y][x][coil] over the widest tile; owner_reduce_kernel later
+// adds a tile's slots to the grid in slot order.  Lanes are (coil, z-slice) as in the
+// interpolation; a grid plane always belongs to the same lane (see launch_spread for the z sizes
+// that need the 2-lane mapping), and rows and columns stay within a lane.
+struct OwnerArgs {
+    float2* grid;          // [G][C] (coil-interleaved)
+    int C;                 // interleave stride = coils of the operator call
+    int c0, gsize;         // coil chunk handled by this launch
+    int Gz, Gy, Gx;
+    int Tz, Ty, Tx, ntz, nty, ntx;
+    const float* rec;      // [N][16] per-sample records (sorted order)
+    int64_t Nsamp;         // samples per coil (user-order input y [C][N])
+    const GItem* items;
+    int nitems;
+    const GRange* ranges;
+    float2* part;          // partial slots
+    int wz, wy, wx;        // slot geometry (widest tile per axis)
+};
+
+__device__ __forceinline__ void tile_region(const OwnerArgs& A, int tile, int* o, int* w) {
+    const int tx = tile % A.ntx, ty = (tile / A.ntx) % A.nty, tz = tile / (A.ntx * A.nty);
+    o[0] = tz * A.Tz;
+    o[1] = ty * A.Ty;
+    o[2] = tx * A.Tx;
+    w[0] = (tz == A.ntz - 1) ? A.Gz - o[0] : A.Tz;
+    w[1] = (ty == A.nty - 1) ? A.Gy - o[1] : A.Ty;
+    w[2] = (tx == A.ntx - 1) ? A.Gx - o[2] : A.Tx;
+}
+
+// offsets (from the target's base b) and region membership of the 4 residues of a box starting at
+// unwrapped j0 along one axis: residue r holds position j0 + ((r - j0) & 3)
+__device__ __forceinline__ void set_offsets_owned(int (&off)[kW], int& in, int j0, int G, int stride, int o, int w,
+                                                  int b) {
+    in = 0;
+#pragma unroll
+    for (int r = 0; r < kW; ++r) {
+        const int j = wrapc(j0 + ((r - j0) & 3), G);
+        off[r] = (j - b) * stride;
+        in |= ((unsigned)(j - o) < (unsigned)w) << r;
+    }
+}
+
+template <int S, int P>
+__global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
+    spread_owner_kernel(OwnerArgs A, const float2* __restrict__ yin, int sorted_in) {
+    __shared__ __align__(16) float srec[kGridWarps * kStage * kRec];
+    const int lane = threadIdx.x & 31;
+    const int coil_l = lane / S, slice = lane % S;
+    const bool active = coil_l < A.gsize;
+    const int c = A.c0 + (active ? coil_l : 0);
+    const int item_i = blockIdx.x * kGridWarps + (threadIdx.x >> 5);
+    if (item_i >= A.nitems) return;                // whole warp exits together
+    const GItem it = A.items[item_i];
+    int o[3], w[3];
+    tile_region(A, it.tile, o, w);
+    // target base and strides: the grid (absolute offsets) or the item's slot (offsets from o)
+    float2* tgt;
+    int b[3], sz, sy, sx;
+    if (it.slot < 0) {
+        tgt = A.grid + c;
+        b[0] = b[1] = b[2] = 0;
+        sx = A.C;
+        sy = A.Gx * A.C;
+        sz = A.Gy * A.Gx * A.C;
+    } else {
+        tgt = A.part + (int64_t)it.slot * A.wz * A.wy * A.wx * A.gsize + (active ? coil_l : 0);
+        b[0] = o[0];
+        b[1] = o[1];
+        b[2] = o[2];
+        sx = A.gsize;
+        sy = A.wx * A.gsize;
+        sz = A.wy * A.wx * A.gsize;
+    }
+    float* wrec = srec + (threadIdx.x >> 5) * (kStage * kRec);
+    Win<P> W;
+    int zin = 0, yin_m = 0, xin_m = 0;   // region membership: planes (bit p), rows and columns (bit r)
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        W.zc[p] = kNoPlane;
+        W.zoff[p] = 0;
+#pragma unroll
+        for (int bb = 0; bb < kW; ++bb)
+#pragma unroll
+            for (int d = 0; d < kW; ++d) W.v[p][bb][d] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < kW; ++r) W.yoff[r] = W.xoff[r] = 0;
+    int cy = kNoPlane, cx = kNoPlane;
+    // a flush adds 4 points at a time: their 4 loads are issued together, then the 4 stores
+    auto flush_plane = [&](int p) {
+        if (active && ((zin >> p) & 1) && W.zc[p] != kNoPlane) {
+#pragma unroll
+            for (int bb = 0; bb < kW; ++bb) {
+                if (!((yin_m >> bb) & 1)) continue;
+                float2 old[kW];
+#pragma unroll
+                for (int d = 0; d < kW; ++d)
+                    if ((xin_m >> d) & 1) old[d] = tgt[W.zoff[p] + W.yoff[bb] + W.xoff[d]];
+#pragma unroll
+                for (int d = 0; d < kW; ++d)
+                    if ((xin_m >> d) & 1)
+                        tgt[W.zoff[p] + W.yoff[bb] + W.xoff[d]] =
+                            make_float2(old[d].x + W.v[p][bb][d].x, old[d].y + W.v[p][bb][d].y);
+            }
+        }
+#pragma unroll
+        for (int bb = 0; bb < kW; ++bb)
+#pragma unroll
+            for (int d = 0; d < kW; ++d) W.v[p][bb][d] = make_float2(0.f, 0.f);
+    };
+    for (int ri = it.r0; ri < it.r1; ++ri) {
+        const GRange rg = A.ranges[ri];
+        const int rend = rg.start + rg.count;
+        for (int base = rg.start; base < rend; base += kStage) {
+            const int n = min(kStage, rend - base);
+            stage_records(A.rec, base, n, wrec, lane);
+#pragma unroll 1
+            for (int i = 0; i < n; ++i) {
+                const float* r = wrec + i * kRec;
+                const BoxHead B = box_head(r);
+                float2 v = make_float2(0.f, 0.f);
+                if (active) v = sorted_in ? yin[(int64_t)(base + i) * A.C + c] : yin[(int64_t)c * A.Nsamp + B.perm];
+                const int dy = B.jy - cy, dx = B.jx - cx;
+                if ((unsigned)(dy + 1) > 2u || (unsigned)(dx + 1) > 2u) {   // not a step of -1, 0 or +1
+#pragma unroll
+                    for (int p = 0; p < P; ++p) flush_plane(p);
+                    set_offsets_owned(W.yoff, yin_m, B.jy, A.Gy, sy, o[1], w[1], b[1]);
+                    set_offsets_owned(W.xoff, xin_m, B.jx, A.Gx, sx, o[2], w[2], b[2]);
+                } else {
+                    if (dy != 0) {
+                        // add the leaving row (old start for a step up, old end for a step down) to
+                        // the target; its registers and residue pass to the entering row
+                        const int rr = (dy > 0) ? (cy & 3) : ((cy + 3) & 3);
+                        const int ynew = (dy > 0) ? cy + 4 : cy - 1;
+                        with_residue(rr, [&](auto RC) {
+                            constexpr int R = decltype(RC)::value;
+                            const bool rowin = (yin_m >> R) & 1;
+#pragma unroll
+                            for (int p = 0; p < P; ++p) {
+                                if (active && rowin && ((zin >> p) & 1) && W.zc[p] != kNoPlane) {
+                                    float2 old[kW];
+#pragma unroll
+                                    for (int d = 0; d < kW; ++d)
+                                        if ((xin_m >> d) & 1) old[d] = tgt[W.zoff[p] + W.yoff[R] + W.xoff[d]];
+#pragma unroll
+                                    for (int d = 0; d < kW; ++d)
+                                        if ((xin_m >> d) & 1)
+                                            tgt[W.zoff[p] + W.yoff[R] + W.xoff[d]] =
+                                                make_float2(old[d].x + W.v[p][R][d].x, old[d].y + W.v[p][R][d].y);
+                                }
+#pragma unroll
+                                for (int d = 0; d < kW; ++d) W.v[p][R][d] = make_float2(0.f, 0.f);
+                            }
+                            const int jw = wrapc(ynew, A.Gy);
+                            W.yoff[R] = (jw - b[1]) * sy;
+                            yin_m = (yin_m & ~(1 << R)) | (((unsigned)(jw - o[1]) < (unsigned)w[1]) << R);
+                        });
+                    }
+                    if (dx != 0) {
+                        const int rr = (dx > 0) ? (cx & 3) : ((cx + 3) & 3);
+                        const int xnew = (dx > 0) ? cx + 4 : cx - 1;
+                        with_residue(rr, [&](auto RC) {
+                            constexpr int R = decltype(RC)::value;
+                            const bool colin = (xin_m >> R) & 1;
+#pragma unroll
+                            for (int p = 0; p < P; ++p) {
+                                if (active && colin && ((zin >> p) & 1) && W.zc[p] != kNoPlane) {
+                                    float2 old[kW];
+#pragma unroll
+                                    for (int bb = 0; bb < kW; ++bb)
+                                        if ((yin_m >> bb) & 1) old[bb] = tgt[W.zoff[p] + W.yoff[bb] + W.xoff[R]];
+#pragma unroll
+                                    for (int bb = 0; bb < kW; ++bb)
+                                        if ((yin_m >> bb) & 1)
+                                            tgt[W.zoff[p] + W.yoff[bb] + W.xoff[R]] =
+                                                make_float2(old[bb].x + W.v[p][bb][R].x, old[bb].y + W.v[p][bb][R].y);
+                                }
+#pragma unroll
+                                for (int bb = 0; bb < kW; ++bb) W.v[p][bb][R] = make_float2(0.f, 0.f);
+                            }
+                            const int jw = wrapc(xnew, A.Gx);
+                            W.xoff[R] = (jw - b[2]) * sx;
+                            xin_m = (xin_m & ~(1 << R)) | (((unsigned)(jw - o[2]) < (unsigned)w[2]) << R);
+                        });
+                    }
+                }
+                cy = B.jy;
+                cx = B.jx;
+                v = cscale(v, B.sw);
+                const float4 wy = *reinterpret_cast<const float4*>(r + 4);
+                const float4 wx = *reinterpret_cast<const float4*>(r + 8);
+                const float wyv[kW] = {wy.x, wy.y, wy.z, wy.w};
+                const float2 wx2[kW] = {make_float2(wx.x, wx.x), make_float2(wx.y, wx.y), make_float2(wx.z, wx.z),
+                                        make_float2(wx.w, wx.w)};
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const int q = slice + p * S;
+                    const int zq = B.jz + ((q - B.jz) & 3);
+                    if (zq != W.zc[p]) {
+                        flush_plane(p);
+                        W.zc[p] = zq;
+                        const int jw = wrapc(zq, A.Gz);
+                        W.zoff[p] = (jw - b[0]) * sz;
+                        zin = (zin & ~(1 << p)) | (((unsigned)(jw - o[0]) < (unsigned)w[0]) << p);
+                    }
+                    const float2 va = cscale(v, r[q]);
+#pragma unroll
+                    for (int bb = 0; bb < kW; ++bb) {
+                        const float2 vb = cscale(va, wyv[bb]);
+#pragma unroll
+                        for (int d = 0; d < kW; ++d) W.v[p][bb][d] = __ffma2_rn(wx2[d], vb, W.v[p][bb][d]);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) flush_plane(p);
+}
+
+// grid (tile region, this launch's coils) += the tile's partial slots in slot order
+__global__ void owner_reduce_kernel(OwnerArgs A, const GRed* __restrict__ reds) {
+    const GRed rd = reds[blockIdx.x];
+    int o[3], w[3];
+    tile_region(A, rd.tile, o, w);
+    const int g = A.gsize;
+    const int64_t n = (int64_t)w[0] * w[1] * w[2] * g;
+    const int64_t slot = (int64_t)A.wz * A.wy * A.wx * g;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+        const int cc = (int)(e % g);
+        const int64_t v = e / g;
+        const int lx = (int)(v % w[2]), ly = (int)((v / w[2]) % w[1]), lz = (int)(v / ((int64_t)w[2] * w[1]));
+        float2* dst = A.grid + (((int64_t)(o[0] + lz) * A.Gy + (o[1] + ly)) * A.Gx + (o[2] + lx)) * A.C + A.c0 + cc;
+        const int64_t loc = (((int64_t)lz * A.wy + ly) * A.wx + lx) * g + cc;
+        float2 acc = *dst;
+        for (int k = 0; k < rd.ns; ++k) {
+            const float2 q = A.part[(rd.s0 + k) * slot + loc];
+            acc.x += q.x;
+            acc.y += q.y;
+        }
+        *dst = acc;
+    }
+}
+
 static float2* grid_buffer(const cs_plan* p) { return p->ndim == 3 ? p->bufA : p->bufB; }
 
 static GridArgs make_grid_args(const cs_plan* p, int ncoils) {
@@ -668,42 +1008,219 @@ static GridArgs make_grid_args(const cs_plan* p, int ncoils) {
     return A;
 }
 
-// Launch one kernel per coil chunk: a chunk of g <= 8 coils uses 4 lanes per coil holding one
-// plane each (P = 1), g <= 16 two lanes with two planes, g <= 32 one lane with all 4 planes;
-// always one sample stream per warp.
-template <bool SPREAD>
-static cs_status launch_grid_op(const cs_plan* p, int ncoils, int mode, const float2* ysub, float2* out,
-                                const float2* yin, int sorted_in, cudaStream_t st) {
-    GridArgs A = make_grid_args(p, ncoils);
-    A.chunk = SPREAD ? p->spread_chunk : p->interp_chunk;
-    const int64_t warps = (p->N + A.chunk - 1) / A.chunk;
-    const unsigned nb = (unsigned)((warps + kGridWarps - 1) / kGridWarps);
-    if (nb == 0) return CS_OK;
-    const int cmax = SPREAD ? p->spread_coils : p->interp_coils;   // 8, 16 or 32 coils per warp
+// Coil chunks of a gridding launch: a chunk of g <= 8 coils uses 4 lanes per coil holding one
+// plane each (P = 1), g <= 16 two lanes with two planes, g <= 32 one lane with all 4 planes.
+template <class F>
+static cs_status for_coil_chunks(const cs_plan* p, int ncoils, int cmax, F&& f) {
     const int nch = (ncoils + cmax - 1) / cmax;
     const int cbal = (ncoils + nch - 1) / nch;                      // balanced chunk size
     for (int c0 = 0; c0 < ncoils; c0 += cbal) {
         const int g = std::min(cbal, ncoils - c0);
-        A.c0 = c0;
-        A.gsize = g;
         int P = 1;
         if (p->ndim == 3) P = (g <= 8) ? 1 : (g <= 16 ? 2 : 4);
-        prof_begin(SPREAD ? ST_SPREAD : ST_INTERP, st);
-        if (p->ndim == 2) {
-            if (SPREAD) spread_kernel<1, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
-            else interp_kernel<1, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
-        } else if (P == 1) {
-            if (SPREAD) spread_kernel<4, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
-            else interp_kernel<4, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
-        } else if (P == 2) {
-            if (SPREAD) spread_kernel<2, 2><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
-            else interp_kernel<2, 2><<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
-        } else {
-            if (SPREAD) spread_kernel<1, 4><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
-            else interp_kernel<1, 4><<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
-        }
+        CS_PROPAGATE(f(c0, g, P));
+    }
+    return CS_OK;
+}
+
+// Interpolation: one sample stream (interp_chunk consecutive sorted samples) per warp.
+static cs_status launch_interp(const cs_plan* p, int ncoils, int mode, const float2* ysub, float2* out,
+                               cudaStream_t st) {
+    GridArgs A = make_grid_args(p, ncoils);
+    A.chunk = p->interp_chunk;
+    const int64_t warps = (p->N + A.chunk - 1) / A.chunk;
+    const unsigned nb = (unsigned)((warps + kGridWarps - 1) / kGridWarps);
+    if (nb == 0) return CS_OK;
+    return for_coil_chunks(p, ncoils, p->interp_coils, [&](int c0, int g, int P) -> cs_status {
+        A.c0 = c0;
+        A.gsize = g;
+        prof_begin(ST_INTERP, st);
+        if (p->ndim == 2) interp_kernel<1, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
+        else if (P == 1) interp_kernel<4, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
+        else if (P == 2) interp_kernel<2, 2><<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
+        else interp_kernel<1, 4><<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
         CS_LAUNCH_CHECK();
-        prof_end(SPREAD ? ST_SPREAD : ST_INTERP, st);
+        prof_end(ST_INTERP, st);
+        return CS_OK;
+    });
+}
+
+// Producer-computes spreading (default): one sample stream (spread_chunk sorted samples) per warp.
+static cs_status launch_spread_producer(const cs_plan* p, int ncoils, const float2* yin, int sorted_in,
+                                        cudaStream_t st) {
+    GridArgs A = make_grid_args(p, ncoils);
+    A.chunk = p->spread_chunk;
+    const int64_t warps = (p->N + A.chunk - 1) / A.chunk;
+    const unsigned nb = (unsigned)((warps + kGridWarps - 1) / kGridWarps);
+    if (nb == 0) return CS_OK;
+    return for_coil_chunks(p, ncoils, p->spread_coils, [&](int c0, int g, int P) -> cs_status {
+        A.c0 = c0;
+        A.gsize = g;
+        prof_begin(ST_SPREAD, st);
+        if (p->ndim == 2) spread_kernel<1, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
+        else if (P == 1) spread_kernel<4, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
+        else spread_kernel<2, 2><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
+        CS_LAUNCH_CHECK();
+        prof_end(ST_SPREAD, st);
+        return CS_OK;
+    });
+}
+
+// Owner-computes spreading (deterministic mode): per coil chunk one launch over the work items
+// (one warp each), then the fixed-order addition of the partial slots.  The grid is cleared first
+// (items add into it).
+static cs_status launch_spread(const cs_plan* p, int ncoils, const float2* yin, int sorted_in, cudaStream_t st) {
+    if (!p->deterministic) return launch_spread_producer(p, ncoils, yin, sorted_in, st);
+    OwnerArgs A;
+    A.grid = grid_buffer(p);
+    A.C = ncoils;
+    A.Gz = p->grid[0];
+    A.Gy = p->grid[1];
+    A.Gx = p->grid[2];
+    A.Tz = p->tile[0];
+    A.Ty = p->tile[1];
+    A.Tx = p->tile[2];
+    A.ntz = p->ntiles[0];
+    A.nty = p->ntiles[1];
+    A.ntx = p->ntiles[2];
+    A.rec = p->rec;
+    A.Nsamp = p->N;
+    A.items = p->gitems;
+    A.nitems = p->n_gitems;
+    A.ranges = p->granges;
+    A.part = p->gpart;
+    A.wz = p->wmax[0];
+    A.wy = p->wmax[1];
+    A.wx = p->wmax[2];
+    if (p->n_gitems == 0) return CS_OK;
+    const unsigned nb = (unsigned)((p->n_gitems + kGridWarps - 1) / kGridWarps);
+    return for_coil_chunks(p, ncoils, p->spread_coils, [&](int c0, int g, int P) -> cs_status {
+        A.c0 = c0;
+        A.gsize = g;
+        prof_begin(ST_SPREAD, st);
+        if (p->n_slots > 0)
+            CS_TRY_CUDA(cudaMemsetAsync(p->gpart, 0,
+                                        sizeof(float2) * (size_t)p->n_slots * p->wmax[0] * p->wmax[1] * p->wmax[2] * g, st));
+        // a grid plane must stay with one lane: with 4 lanes per coil (one z residue each) that needs a
+        // z size that is a multiple of 4; for z sizes of 2 mod 4 the 2-lane mapping (residues r and
+        // r + 2 in one lane, which a wrap maps onto each other) is used
+        if (p->ndim == 2) spread_owner_kernel<1, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
+        else if (P == 1 && p->grid[0] % 4 == 0) spread_owner_kernel<4, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
+        else spread_owner_kernel<2, 2><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
+        CS_LAUNCH_CHECK();
+        if (p->n_greds > 0) {
+            owner_reduce_kernel<<<p->n_greds, 256, 0, st>>>(A, p->greds);
+            CS_LAUNCH_CHECK();
+        }
+        prof_end(ST_SPREAD, st);
+        return CS_OK;
+    });
+}
+
+void nufft_owner_free(cs_plan* p) {
+    cudaFree(p->gitems);
+    cudaFree(p->granges);
+    cudaFree(p->greds);
+    cudaFree(p->gpart);
+    p->gitems = nullptr;
+    p->granges = nullptr;
+    p->greds = nullptr;
+    p->gpart = nullptr;
+    p->n_gitems = p->n_greds = p->n_slots = 0;
+}
+
+// Work items of the owner-computes spreading from the (tile, halo class) offsets: tile t takes its
+// own samples and, for every non-empty set e of axes (z = 4, y = 2, x = 1) that have more than one
+// tile, the samples of tile t - e whose class contains e.  The concatenated list is cut into items
+// of at most owner_item visits; the first writes the grid, the others own partial slots.  Items
+// are ordered longest first.  Synchronous (copies the offsets to the host).
+cs_status nufft_owner_build(cs_plan* p) {
+    nufft_owner_free(p);
+    const int nt[3] = {p->ntiles[0], p->ntiles[1], p->ntiles[2]};
+    const int64_t ntot = p->ntiles_total;
+    std::vector<int32_t> coff((size_t)ntot * 8 + 1);
+    CS_TRY_CUDA(cudaMemcpy(coff.data(), p->class_off, sizeof(int32_t) * coff.size(), cudaMemcpyDeviceToHost));
+    const int nd = p->ndim;
+    std::vector<GItem> items;
+    std::vector<GRange> ranges;
+    std::vector<GRed> reds;
+    std::vector<GRange> list;
+    int slots = 0;
+    const int64_t Q = std::max(1, p->owner_item);
+    for (int64_t t = 0; t < ntot; ++t) {
+        const int tz = (int)(t / ((int64_t)nt[1] * nt[2])), ty = (int)((t / nt[2]) % nt[1]), tx = (int)(t % nt[2]);
+        list.clear();
+        int64_t visits = 0;
+        for (int e = 0; e < 8; ++e) {
+            // bits of e on the axes this plan uses; a neighbour exists only with more than one tile
+            const int ez = (e >> 2) & 1, ey = (e >> 1) & 1, ex = e & 1;
+            if ((ez && (nd < 3 || nt[0] == 1)) || (ey && nt[1] == 1) || (ex && nt[2] == 1)) continue;
+            const int sz_ = (tz - ez + nt[0]) % nt[0], sy_ = (ty - ey + nt[1]) % nt[1], sx_ = (tx - ex + nt[2]) % nt[2];
+            const int64_t src = ((int64_t)sz_ * nt[1] + sy_) * nt[2] + sx_;
+            for (int cl = 0; cl < 8; ++cl) {
+                if ((cl & e) != e) continue;
+                const int32_t a = coff[src * 8 + cl], b = coff[src * 8 + cl + 1];
+                if (b > a) {
+                    list.push_back(GRange{a, b - a});
+                    visits += b - a;
+                }
+            }
+        }
+        if (visits == 0) continue;
+        const int nchunks = (int)((visits + Q - 1) / Q);
+        size_t li = 0;
+        int64_t inpos = 0;   // position inside list[li]
+        for (int k = 0; k < nchunks; ++k) {
+            GItem it;
+            it.tile = (int)t;
+            it.slot = (k == 0) ? -1 : slots + k - 1;
+            it.r0 = (int)ranges.size();
+            int64_t need = std::min<int64_t>(Q, visits - (int64_t)k * Q);
+            while (need > 0) {
+                const int64_t take = std::min<int64_t>(need, list[li].count - inpos);
+                ranges.push_back(GRange{(int)(list[li].start + inpos), (int)take});
+                need -= take;
+                inpos += take;
+                if (inpos == list[li].count) {
+                    ++li;
+                    inpos = 0;
+                }
+            }
+            it.r1 = (int)ranges.size();
+            items.push_back(it);
+        }
+        if (nchunks > 1) {
+            reds.push_back(GRed{(int)t, slots, nchunks - 1});
+            slots += nchunks - 1;
+        }
+    }
+    // longest first (by visits), ties in tile order, so that the long items start first
+    std::vector<int64_t> len(items.size());
+    for (size_t i = 0; i < items.size(); ++i) {
+        int64_t v = 0;
+        for (int r = items[i].r0; r < items[i].r1; ++r) v += ranges[r].count;
+        len[i] = v;
+    }
+    std::vector<size_t> ord(items.size());
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return len[a] > len[b]; });
+    std::vector<GItem> sorted(items.size());
+    for (size_t i = 0; i < ord.size(); ++i) sorted[i] = items[ord[i]];
+    auto upload = [&](auto& vec, auto** dst) -> cs_status {
+        if (vec.empty()) return CS_OK;
+        CS_TRY_CUDA(cudaMalloc((void**)dst, sizeof(vec[0]) * vec.size()));
+        CS_TRY_CUDA(cudaMemcpy(*dst, vec.data(), sizeof(vec[0]) * vec.size(), cudaMemcpyHostToDevice));
+        return CS_OK;
+    };
+    CS_PROPAGATE(upload(sorted, &p->gitems));
+    CS_PROPAGATE(upload(ranges, &p->granges));
+    CS_PROPAGATE(upload(reds, &p->greds));
+    p->n_gitems = (int)sorted.size();
+    p->n_greds = (int)reds.size();
+    p->n_slots = slots;
+    if (slots > 0) {
+        const size_t n = (size_t)slots * p->wmax[0] * p->wmax[1] * p->wmax[2] * 16;   // <= 16 coils per launch
+        CS_TRY_CUDA(cudaMalloc(&p->gpart, sizeof(float2) * n));
     }
     return CS_OK;
 }
@@ -718,8 +1235,8 @@ cs_status nufft_records(cs_plan* p, cudaStream_t st) {
 
 // y (user order) = sqrt(w) interp(grid); with ysub: ktmp (sorted) = sqrt(w) interp(grid) - y
 cs_status nufft_interp(const cs_plan* p, int ncoils, float2* y, const float2* ysub, cudaStream_t st) {
-    if (ysub) return launch_grid_op<false>(p, ncoils, OUT_RESID, ysub, p->ktmp, nullptr, 0, st);
-    return launch_grid_op<false>(p, ncoils, OUT_USER, nullptr, y, nullptr, 0, st);
+    if (ysub) return launch_interp(p, ncoils, OUT_RESID, ysub, p->ktmp, st);
+    return launch_interp(p, ncoils, OUT_USER, nullptr, y, st);
 }
 
 // grid = spread(sqrt(w) y); y in user order (sorted_in = 0) or the sorted scratch ktmp
@@ -727,17 +1244,17 @@ cs_status nufft_spread(const cs_plan* p, int ncoils, const float2* y, int sorted
     float2* grid = grid_buffer(p);
     CS_TRY_CUDA(cudaMemsetAsync(grid, 0, sizeof(float2) * (size_t)p->G * ncoils, st));
     if (ncoils == 0) return CS_OK;
-    return launch_grid_op<true>(p, ncoils, 0, nullptr, nullptr, sorted_in ? p->ktmp : y, sorted_in, st);
+    return launch_spread(p, ncoils, sorted_in ? p->ktmp : y, sorted_in, st);
 }
 
 // ktmp (sorted, coil-interleaved) = w^1/2 interp(grid)
 cs_status nufft_interp_sorted(const cs_plan* p, int ncoils, cudaStream_t st) {
-    return launch_grid_op<false>(p, ncoils, OUT_SORTED, nullptr, p->ktmp, nullptr, 0, st);
+    return launch_interp(p, ncoils, OUT_SORTED, nullptr, p->ktmp, st);
 }
 
 // normal operator on the grid: ktmp = w^1/2 interp(grid) (sorted), then grid = spread(w^1/2 ktmp)
 cs_status nufft_interp_spread(const cs_plan* p, int ncoils, cudaStream_t st) {
-    CS_PROPAGATE(launch_grid_op<false>(p, ncoils, OUT_SORTED, nullptr, p->ktmp, nullptr, 0, st));
+    CS_PROPAGATE(launch_interp(p, ncoils, OUT_SORTED, nullptr, p->ktmp, st));
     return nufft_spread(p, ncoils, nullptr, 1, st);
 }
 

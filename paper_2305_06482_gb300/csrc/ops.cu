@@ -127,6 +127,8 @@ static void plan_free(cs_plan* p) {
     cudaFree(p->perm);
     cudaFree(p->j0);
     cudaFree(p->tile_off);
+    cudaFree(p->class_off);
+    nufft_owner_free(p);
     cudaFree(p->phi);
     cudaFree(p->rec);
     cudaFree(p->bufA);
@@ -230,8 +232,13 @@ static cs_status plan_build(cs_plan* p, const cs_geom* g, cudaStream_t st) {
         int t = (a >= 3 - nd) ? g->tile[a - (3 - nd)] : 1;
         if (t <= 0) t = 16;
         t = std::min(t, p->grid[a]);
+        CS_REQUIRE(a < 3 - nd || t >= 4 || t == p->grid[a], CS_ERR_UNSUPPORTED_SIZE,
+                   "tiles narrower than the kernel width (%d) are not supported", t);
         p->tile[a] = t;
-        p->ntiles[a] = (p->grid[a] + t - 1) / t;
+        const int rem = p->grid[a] % t;
+        // a remainder narrower than the kernel widens the last tile instead of forming its own
+        p->ntiles[a] = (rem > 0 && rem < 4 && p->grid[a] >= t) ? p->grid[a] / t : (p->grid[a] + t - 1) / t;
+        p->wmax[a] = std::max(t, p->grid[a] - (p->ntiles[a] - 1) * t);
     }
     p->ntiles_total = (int64_t)p->ntiles[0] * p->ntiles[1] * p->ntiles[2];
     p->spread_chunk = 64;
@@ -258,6 +265,7 @@ static cs_status plan_build(cs_plan* p, const cs_geom* g, cudaStream_t st) {
     CS_TRY_CUDA(cudaMalloc(&p->perm, sizeof(int32_t) * p->N));
     CS_TRY_CUDA(cudaMalloc(&p->j0, sizeof(int32_t) * nd * p->N));
     CS_TRY_CUDA(cudaMalloc(&p->tile_off, sizeof(int32_t) * (p->ntiles_total + 1)));
+    CS_TRY_CUDA(cudaMalloc(&p->class_off, sizeof(int32_t) * (p->ntiles_total * 8 + 1)));
     CS_PROPAGATE(nufft_bin(p, g->traj, g->dcf, st));
     CS_PROPAGATE(nufft_records(p, st));
     CS_TRY_CUDA(cudaStreamSynchronize(st));
@@ -418,6 +426,22 @@ cs_status cs_plan_set_gridding(cs_plan* p, int interp_coils, int interp_chunk, i
     p->interp_chunk = interp_chunk;
     p->spread_coils = spread_coils;
     p->spread_chunk = spread_chunk;
+    return CS_OK;
+}
+
+cs_status cs_plan_set_deterministic(cs_plan* p, int on, int item_visits) {
+    clear_error();
+    CS_REQUIRE(p && (on == 0 || on == 1) && (item_visits == 0 || (item_visits >= 64 && item_visits <= (1 << 20))),
+               CS_ERR_INVALID_ARG, "bad deterministic-spreading arguments");
+    if (p->kind != CS_NONCARTESIAN) return CS_OK;
+    const int q = item_visits > 0 ? item_visits : p->owner_item;
+    if (on && (q != p->owner_item || !p->gitems)) {
+        CS_TRY_CUDA(cudaDeviceSynchronize());      // work items and partial slots are (re)built
+        p->owner_item = q;
+        CS_PROPAGATE(nufft_owner_build(p));
+    }
+    p->owner_item = q;
+    p->deterministic = on;
     return CS_OK;
 }
 

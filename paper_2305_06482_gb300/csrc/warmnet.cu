@@ -422,7 +422,9 @@ __global__ void pack_weights_kernel(const float* __restrict__ w, int cout, int c
     pk[e] = nn_bf16(v);
 }
 
-// weight gradient: gw[co][tap][ci] += sum_v gout[v][co] in[v + off(tap)][ci], gb[co] += sum_v gout[v][co]
+// weight gradient: gw[co][tap][ci] += sum_v gout[v][co] in[v + off(tap)][ci], gb[co] += sum_v gout[v][co].
+// Every block of voxels writes its own partial sums (gw, gb here point at the [gridDim.x] partial
+// arrays); wsum_kernel adds them in block order, so the gradient is bit-reproducible.
 constexpr int kWgVox = 128;
 __global__ void wgrad_kernel(const float* __restrict__ in, const float* __restrict__ gout, int nz, int ny, int nx, int cin,
                              int cout, float* __restrict__ gw, float* __restrict__ gb) {
@@ -466,14 +468,16 @@ __global__ void wgrad_kernel(const float* __restrict__ in, const float* __restri
         if (tap == 13 && blockIdx.z == 0 && threadIdx.x < cout)
             for (int t = 0; t < kWgVox; ++t) bacc += sg[t * cout + threadIdx.x];
     }
+    // this voxel block's partial sums; wsum_kernel adds the blocks in block order
+    float* pw = gw + (int64_t)blockIdx.x * cout * 27 * cin;
     for (int q = 0; q < 4; ++q) {
         const int pr = pbase + threadIdx.x + q * blockDim.x;
         if (pr < pairs) {
             const int co = pr / cin, ci = pr % cin;
-            atomicAdd(&gw[((int64_t)co * 27 + tap) * cin + ci], acc[q]);
+            pw[((int64_t)co * 27 + tap) * cin + ci] = acc[q];
         }
     }
-    if (tap == 13 && blockIdx.z == 0 && threadIdx.x < cout && gb) atomicAdd(&gb[threadIdx.x], bacc);
+    if (tap == 13 && blockIdx.z == 0 && threadIdx.x < cout && gb) gb[blockIdx.x * cout + threadIdx.x] = bacc;
 }
 
 // The same weight gradient with register tiles, for cin and cout multiples of 4: a thread owns a
@@ -533,13 +537,30 @@ __global__ void wgrad_tiled_kernel(const float* __restrict__ in, const float* __
         if (tap == 13 && blockIdx.z == 0 && threadIdx.x < cout)
             for (int t = 0; t < kWgVox; ++t) bacc += sg[t * cout + threadIdx.x];
     }
+    // the vsplit threads of a tile add their shares in split order, then the block's partial sums
+    // go to its slot (wsum_kernel adds the blocks in block order)
+    __syncthreads();
+    float* red = sg;                               // [vsplit][tiles_here][16], reuses the staging area
     if (owner) {
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) atomicAdd(&gw[((int64_t)(co0 + a) * 27 + tap) * cin + ci0 + b], acc[a][b]);
+            for (int b = 0; b < 4; ++b) red[((int64_t)vs * tiles_here + (tile - blockIdx.z * blockDim.x)) * 16 + a * 4 + b] = acc[a][b];
     }
-    if (tap == 13 && blockIdx.z == 0 && threadIdx.x < cout && gb) atomicAdd(&gb[threadIdx.x], bacc);
+    __syncthreads();
+    if (owner && vs == 0) {
+        float* pw = gw + (int64_t)blockIdx.x * cout * 27 * cin;
+        const int ti = tile - blockIdx.z * blockDim.x;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                float tot = 0.f;
+                for (int k = 0; k < vsplit; ++k) tot += red[((int64_t)k * tiles_here + ti) * 16 + a * 4 + b];
+                pw[((int64_t)(co0 + a) * 27 + tap) * cin + ci0 + b] = tot;
+            }
+    }
+    if (tap == 13 && blockIdx.z == 0 && threadIdx.x < cout && gb) gb[blockIdx.x * cout + threadIdx.x] = bacc;
 }
 
 // g *= (act > 0)
@@ -560,33 +581,52 @@ __global__ void conv1_fwd_kernel(const float* __restrict__ in, int64_t nvox, int
     }
 }
 
-// 1x1x1 layer backward: gin[v][c] = sum_o w[o][c] gout[v][o]; gw[o][c] += sum_v gout[v][o] in[v][c]; gb[o] += sum_v gout
-__global__ void conv1_bwd_kernel(const float* __restrict__ in, const float* __restrict__ gout, int64_t nvox, int cin,
-                                 int cout, const float* __restrict__ w, float* __restrict__ gin, float* __restrict__ gw,
-                                 float* __restrict__ gb) {
-    __shared__ float part[64 * 4 + 4];
-    for (int i = threadIdx.x; i < cout * cin + cout; i += blockDim.x) part[i] = 0.f;
-    __syncthreads();
+// 1x1x1 layer backward: gin[v][c] = sum_o w[o][c] gout[v][o]
+__global__ void conv1_gin_kernel(const float* __restrict__ gout, int64_t nvox, int cin, int cout, const float* __restrict__ w,
+                                 float* __restrict__ gin) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (int64_t)gridDim.x * blockDim.x) {
         for (int c = 0; c < cin; ++c) {
             float a = 0.f;
             for (int o = 0; o < cout; ++o) a = fmaf(w[o * cin + c], gout[v * cout + o], a);
             gin[v * cin + c] = a;
         }
-        for (int o = 0; o < cout; ++o) {
-            const float g = gout[v * cout + o];
-            atomicAdd(&part[cout * cin + o], g);
-            for (int c = 0; c < cin; ++c) atomicAdd(&part[o * cin + c], g * in[v * cin + c]);
-        }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < cout * cin; i += blockDim.x) atomicAdd(&gw[i], part[i]);
-    for (int i = threadIdx.x; i < cout; i += blockDim.x) atomicAdd(&gb[i], part[cout * cin + i]);
 }
 
-// mean squared error: loss += sum (out - tgt)^2 / n, g = 2 (out - tgt) / n
+// 1x1x1 layer weight partials: block b sums its contiguous voxel chunk in voxel order; thread e
+// owns gw entry e (< cout cin) or bias entry e - cout cin.  part [gridDim.x][cout cin + cout].
+__global__ void conv1_wpart_kernel(const float* __restrict__ in, const float* __restrict__ gout, int64_t nvox, int cin,
+                                   int cout, float* __restrict__ part) {
+    const int nw = cout * cin + cout;
+    const int e = threadIdx.x;
+    if (e >= nw) return;
+    const int64_t chunk = (nvox + gridDim.x - 1) / gridDim.x;
+    const int64_t v0 = (int64_t)blockIdx.x * chunk, v1 = min(nvox, v0 + chunk);
+    float acc = 0.f;
+    if (e < cout * cin) {
+        const int o = e / cin, c = e % cin;
+        for (int64_t v = v0; v < v1; ++v) acc = fmaf(gout[v * cout + o], in[v * cin + c], acc);
+    } else {
+        const int o = e - cout * cin;
+        for (int64_t v = v0; v < v1; ++v) acc += gout[v * cout + o];
+    }
+    part[(int64_t)blockIdx.x * nw + e] = acc;
+}
+
+// dst[i] += sum over the nb partial rows (in row order) of part[b * stride + i], i < n
+__global__ void wsum_kernel(const float* __restrict__ part, int nb, int64_t stride, int64_t n, float* __restrict__ dst) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int b = 0; b < nb; ++b) acc += part[(int64_t)b * stride + i];
+        dst[i] += acc;
+    }
+}
+
+// mean squared error: g = 2 (out - tgt) / n and the block partials of sum (out - tgt)^2 / n
+// (part[blockIdx.x]; the loss is their sum in block order)
 __global__ void mse_kernel(const float* __restrict__ out, const float* __restrict__ tgt, int64_t n, float* __restrict__ g,
-                           float* __restrict__ loss) {
+                           float* __restrict__ part) {
+    __shared__ float red[8];
     float acc = 0.f;
     const float inv = 1.0f / (float)n;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -595,7 +635,13 @@ __global__ void mse_kernel(const float* __restrict__ out, const float* __restric
         acc += d * d * inv;
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        part[blockIdx.x] = s;
+    }
 }
 
 // Adam (Kingma & Ba) with bias correction; step is 1-based
@@ -612,30 +658,9 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
     }
 }
 
-// network input: [Re x^t, Im x^t] / s and [Re d, Im d] * eta / s with s the RMS of (x^t, eta d)
-// over the voxels (non-zero from the first outer iteration, where x^t = 0)
-__global__ void feat_norm_kernel(const float2* __restrict__ x, const float2* __restrict__ d, float eta, int64_t n,
-                                 float* __restrict__ ss) {
-    float acc = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        acc += x[i].x * x[i].x + x[i].y * x[i].y + eta * eta * (d[i].x * d[i].x + d[i].y * d[i].y);
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(ss, acc);
-}
-
-__global__ void features_kernel(const float2* __restrict__ x, const float2* __restrict__ d, int64_t n, float eta,
-                                const float* __restrict__ ss, float* __restrict__ f) {
-    const float s = sqrtf(ss[0] / (float)n) + 1e-12f;
-    const float inv = 1.f / s;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        f[4 * i + 0] = x[i].x * inv;
-        f[4 * i + 1] = x[i].y * inv;
-        f[4 * i + 2] = d[i].x * eta * inv;
-        f[4 * i + 3] = d[i].y * eta * inv;
-    }
-}
-
-// The same input scaling with a reproducible sum: per-block FP64 partials over a fixed grid of
+// Network input: [Re x^t, Im x^t] / s and [Re d, Im d] * eta / s with s the RMS of (x^t, eta d)
+// over the voxels (non-zero from the first outer iteration, where x^t = 0), summed reproducibly:
+// per-block FP64 partials over a fixed grid of
 // kFeatBlocks blocks, summed in block order by every consumer, so the network input (and with it
 // the prediction) is bit-identical from run to run.  eta is read from eta_dev when that is given
 // (the solver's step lives on the device), else the host value is used.
@@ -873,14 +898,15 @@ __global__ void upconv2_wgrad_kernel(const float* __restrict__ in, const float* 
         if (blockIdx.z == 0 && threadIdx.x < cout)
             for (int t = 0; t < kWgVox; ++t) bacc += sg[t * cout + threadIdx.x];
     }
+    float* pw = gw + (int64_t)blockIdx.x * cout * 8 * cin;   // this voxel block's partial sums
     for (int q = 0; q < 4; ++q) {
         const int pr = pbase + threadIdx.x + q * blockDim.x;
         if (pr < pairs) {
             const int co = pr / cin, ci = pr % cin;
-            atomicAdd(&gw[((int64_t)co * 8 + a) * cin + ci], acc[q]);
+            pw[((int64_t)co * 8 + a) * cin + ci] = acc[q];
         }
     }
-    if (blockIdx.z == 0 && threadIdx.x < cout && gb) atomicAdd(&gb[threadIdx.x], bacc);
+    if (blockIdx.z == 0 && threadIdx.x < cout && gb) gb[((int64_t)blockIdx.x * 8 + a) * cout + threadIdx.x] = bacc;
 }
 
 // channel slices: dst[v][doff + j] (+)= src[v][soff + j], j < n; with n, the offsets and strides
@@ -1053,17 +1079,32 @@ cs_status cs_nn_conv3d_wgrad(const float* in, const float* gout, int nz, int ny,
                "bad wgrad arguments");
     CS_PROPAGATE(nn_attrs_once());
     const int64_t nvox = (int64_t)nz * ny * nx;
-    const size_t sm = sizeof(float) * kWgVox * (cin + cout);
     const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((nvox + kWgVox - 1) / kWgVox, 64));
+    cudaStream_t st = (cudaStream_t)stream;
+    // per-voxel-block partial sums (scratch from the stream-ordered pool), added in block order
+    const int64_t wsize = (int64_t)cout * 27 * cin;
+    float* part = nullptr;
+    CS_TRY_CUDA(cudaMallocAsync((void**)&part, sizeof(float) * (size_t)gx * (wsize + cout), st));
+    float* pb = part + (int64_t)gx * wsize;
     if (cin % 4 == 0 && cout % 4 == 0) {
+        // staging area, also the in-block reduction area of up to 256 tiles x 16 values
+        const size_t sm = sizeof(float) * std::max<size_t>((size_t)kWgVox * (cin + cout), 256 * 16);
         const int chunks = ((cin / 4) * (cout / 4) + 255) / 256;   // 256 register tiles per block
-        wgrad_tiled_kernel<<<dim3(gx, 27, chunks), 256, sm, (cudaStream_t)stream>>>(in, gout, nz, ny, nx, cin, cout, gw,
-                                                                                    gb);
+        wgrad_tiled_kernel<<<dim3(gx, 27, chunks), 256, sm, st>>>(in, gout, nz, ny, nx, cin, cout, part,
+                                                                  gb ? pb : nullptr);
     } else {
+        const size_t sm = sizeof(float) * kWgVox * (cin + cout);
         const int chunks = (cin * cout + 1023) / 1024;   // 256 threads x 4 pairs per block
-        wgrad_kernel<<<dim3(gx, 27, chunks), 256, sm, (cudaStream_t)stream>>>(in, gout, nz, ny, nx, cin, cout, gw, gb);
+        wgrad_kernel<<<dim3(gx, 27, chunks), 256, sm, st>>>(in, gout, nz, ny, nx, cin, cout, part, gb ? pb : nullptr);
     }
     CS_LAUNCH_CHECK();
+    wsum_kernel<<<nn_grid(wsize), 256, 0, st>>>(part, gx, wsize, wsize, gw);
+    CS_LAUNCH_CHECK();
+    if (gb) {
+        wsum_kernel<<<1, 256, 0, st>>>(pb, gx, cout, cout, gb);
+        CS_LAUNCH_CHECK();
+    }
+    CS_TRY_CUDA(cudaFreeAsync(part, st));
     return CS_OK;
 }
 
@@ -1090,16 +1131,33 @@ cs_status cs_nn_conv1_bwd(const float* in, const float* gout, int64_t nvox, int 
     clear_error();
     CS_REQUIRE(in && gout && w && gin && gw && gb && cin * cout + cout <= 64 * 4 + 4, CS_ERR_INVALID_ARG,
                "bad conv1_bwd arguments");
-    conv1_bwd_kernel<<<nn_grid(nvox), 256, 0, (cudaStream_t)stream>>>(in, gout, nvox, cin, cout, w, gin, gw, gb);
+    cudaStream_t st = (cudaStream_t)stream;
+    conv1_gin_kernel<<<nn_grid(nvox), 256, 0, st>>>(gout, nvox, cin, cout, w, gin);
     CS_LAUNCH_CHECK();
+    const int nw = cout * cin + cout, nb = kFeatBlocks;
+    float* part = nullptr;
+    CS_TRY_CUDA(cudaMallocAsync((void**)&part, sizeof(float) * (size_t)nb * nw, st));
+    conv1_wpart_kernel<<<nb, 288, 0, st>>>(in, gout, nvox, cin, cout, part);
+    CS_LAUNCH_CHECK();
+    wsum_kernel<<<1, 256, 0, st>>>(part, nb, nw, (int64_t)cout * cin, gw);
+    CS_LAUNCH_CHECK();
+    wsum_kernel<<<1, 256, 0, st>>>(part + (int64_t)cout * cin, nb, nw, cout, gb);
+    CS_LAUNCH_CHECK();
+    CS_TRY_CUDA(cudaFreeAsync(part, st));
     return CS_OK;
 }
 
 cs_status cs_nn_mse(const float* out, const float* tgt, int64_t n, float* g, float* loss, void* stream) {
     clear_error();
     CS_REQUIRE(out && tgt && g && loss && n > 0, CS_ERR_INVALID_ARG, "bad mse arguments");
-    mse_kernel<<<nn_grid(n), 256, 0, (cudaStream_t)stream>>>(out, tgt, n, g, loss);
+    cudaStream_t st = (cudaStream_t)stream;
+    float* part = nullptr;
+    CS_TRY_CUDA(cudaMallocAsync((void**)&part, sizeof(float) * kFeatBlocks, st));
+    mse_kernel<<<kFeatBlocks, 256, 0, st>>>(out, tgt, n, g, part);
     CS_LAUNCH_CHECK();
+    wsum_kernel<<<1, 32, 0, st>>>(part, kFeatBlocks, 1, 1, loss);
+    CS_LAUNCH_CHECK();
+    CS_TRY_CUDA(cudaFreeAsync(part, st));
     return CS_OK;
 }
 
@@ -1119,11 +1177,10 @@ cs_status cs_nn_features(const float* xt, const float* d, int64_t n, float eta, 
     clear_error();
     CS_REQUIRE(xt && d && ss && f && n > 0, CS_ERR_INVALID_ARG, "bad features arguments");
     cudaStream_t st = (cudaStream_t)stream;
-    CS_TRY_CUDA(cudaMemsetAsync(ss, 0, sizeof(float), st));
-    feat_norm_kernel<<<nn_grid(n), 256, 0, st>>>((const float2*)xt, (const float2*)d, eta, n, ss);
-    CS_LAUNCH_CHECK();
-    features_kernel<<<nn_grid(n), 256, 0, st>>>((const float2*)xt, (const float2*)d, n, eta, ss, f);
-    CS_LAUNCH_CHECK();
+    double* part = nullptr;
+    CS_TRY_CUDA(cudaMallocAsync((void**)&part, sizeof(double) * kFeatBlocks, st));
+    CS_PROPAGATE(nn_features_det((const float2*)xt, (const float2*)d, n, eta, nullptr, part, ss, f, st));
+    CS_TRY_CUDA(cudaFreeAsync(part, st));
     return CS_OK;
 }
 
@@ -1213,8 +1270,20 @@ cs_status cs_nn_upconv2_bwd(const float* in, const float* gout, int ldg, int gof
         const size_t sm = sizeof(float) * kWgVox * (cin + cout);
         const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((nvox + kWgVox - 1) / kWgVox, 64));
         const int chunks = (cin * cout + 1023) / 1024;
-        upconv2_wgrad_kernel<<<dim3(gx, 8, chunks), 256, sm, st>>>(in, gout, ldg, goff, nz, ny, nx, cin, cout, gw, gb);
+        const int64_t wsize = (int64_t)cout * 8 * cin;
+        float* part = nullptr;     // per-voxel-block partials: weights [gx][wsize], bias [gx][8][cout]
+        CS_TRY_CUDA(cudaMallocAsync((void**)&part, sizeof(float) * (size_t)gx * (wsize + 8 * cout), st));
+        float* pb = part + (int64_t)gx * wsize;
+        upconv2_wgrad_kernel<<<dim3(gx, 8, chunks), 256, sm, st>>>(in, gout, ldg, goff, nz, ny, nx, cin, cout, part,
+                                                                   gb ? pb : nullptr);
         CS_LAUNCH_CHECK();
+        wsum_kernel<<<nn_grid(wsize), 256, 0, st>>>(part, gx, wsize, wsize, gw);
+        CS_LAUNCH_CHECK();
+        if (gb) {
+            wsum_kernel<<<1, 256, 0, st>>>(pb, gx * 8, cout, cout, gb);
+            CS_LAUNCH_CHECK();
+        }
+        CS_TRY_CUDA(cudaFreeAsync(part, st));
     }
     return CS_OK;
 }

@@ -38,12 +38,14 @@ stream), for profiling individual kernels with small launch counts.
       the warm-start U-Net (16/32/64 channels): every 3x3x3 convolution alone on random inputs of
       its shape (BF16 implicit GEMM on the tensor cores), one whole inference on the image size of
       the workload, and one training step (forward, backward, Adam) on a 64^3 crop
-  python -m paper_2305_06482_gb300.microbench warmtrain [--config cones3d_128] [--phantoms P] [--train-steps N]
-      the warm start trained as configured but smaller: training pairs (x^t, d, sub-problem
-      solved with 40 FISTA iterations) from Algorithm 1 on P seeded phantoms (l1-db4 lambda 2e-3,
-      m = 8 = 4 PCA + 4 Gaussian, T = 6, K = 4), N Adam steps on random 64^3 crops, then a
-      held-out phantom with and without the warm start: NRMSE to x_inf per outer iteration,
-      acceptances, device time per reconstruction
+  python -m paper_2305_06482_gb300.microbench warmtrain [--config cones3d_128|cones3d_large] [--phantoms P]
+          [--outer T] [--K K] [--tight M] [--train-steps N] [--ref-iters R] [--save PATH]
+      the warm start trained on the method's own pairs: (x^t, d, sub-problem solved with M FISTA
+      iterations) from T outer iterations of Algorithm 1 (K inner) on P seeded phantoms (l1-db4
+      lambda 2e-3, m = 8 = 4 PCA + 4 Gaussian on cones3d_128, m = 10 = 5 + 5 on cones3d_large),
+      N Adam steps on random 64^3 crops, optionally saved; then a held-out phantom through
+      recon_solve with and without the warm start (decision on the device): NRMSE to x_inf (R
+      plain iterations) per outer iteration, acceptances, device time per reconstruction
   python -m paper_2305_06482_gb300.microbench cart2d [--iters N]
       128x128 Cartesian coil-sketched CG reconstruction (8 coils, m = 4, T = 5, K = 10),
       eager launches vs a replayed CUDA graph
@@ -508,23 +510,28 @@ def warmnet(args):
 
 
 def warmtrain(args):
+    """Warm-start training on pairs of the method itself, then a held-out reconstruction with and
+    without the network through recon_solve (the acceptance decided on the device)."""
     import paper_2305_06482_gb300.warmstart as ws
     cfg = CONFIGS[args.config]
     dev = torch.device("cuda")
     img, grid, C = cfg["img"], cfg["grid"], cfg["nc"]
+    large = args.config == "cones3d_large"
     traj = synthdata.cones_trajectory(cfg["n_int"], 512)
     dcf = synthdata.cones_dcf(traj, img, cfg["n_int"], 512)
     plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=torch.from_numpy(traj).to(dev), dcf=torch.from_numpy(dcf).to(dev),
                    grid=grid)
     maps = synthdata.coil_maps_torch(img, C, device=dev)
-    lam, V, S, T, K, levels = 2e-3, 4, 4, 6, 4, 4
+    lam, levels = 2e-3, 4
+    V, S = (5, 5) if large else (4, 4)
+    T, K, tight = args.outer, args.K, args.tight
     t0 = time.perf_counter()
     pairs = []
     for k in range(args.phantoms):
         seed = 101 + k
         y = cs.sense_fwd(plan, synthdata.phantom_torch(img, seed=seed, device=dev), maps)
         su = ws.setup(plan, y, maps, lam, V, S, T, seed, synthdata.phantom_torch(img, seed=seed + 50, device=dev), levels)
-        _, pr, _ = ws.run(su, T, K, record_pairs=1, tight_K=40)
+        _, pr, _ = ws.run(su, T, K, record_pairs=1, tight_K=tight)
         pairs += pr
     torch.cuda.synchronize()
     t_pairs = time.perf_counter() - t0
@@ -535,32 +542,40 @@ def warmtrain(args):
     b.record()
     torch.cuda.synchronize()
     t_train = a.elapsed_time(b) / 1e3
-    # held-out phantom
+    del pairs
+    torch.cuda.empty_cache()
+    if args.save:
+        os.makedirs(os.path.dirname(os.path.abspath(args.save)), exist_ok=True)
+        net.save(args.save)
+    # held-out phantom: Algorithm 1 through recon_solve with and without the warm start
     seed = 199
     y = cs.sense_fwd(plan, synthdata.phantom_torch(img, seed=seed, device=dev), maps)
     v0 = synthdata.phantom_torch(img, seed=seed + 50, device=dev)
     x_inf, _ = cs.recon_solve(plan, y, maps, lam, cs.REG_L1_WAVELET,
-                              cs.SolveParams(K=300, sketch=False, do_pca=False, power_v0=v0), wavelet_levels=levels)
-    su = ws.setup(plan, y, maps, lam, V, S, T, seed, v0, levels)
+                              cs.SolveParams(K=args.ref_iters, sketch=False, do_pca=False, power_v0=v0),
+                              wavelet_levels=levels)
     res = {}
     for name, n in (("without", None), ("with", net)):
-        errs = []
-        ws.run(su, T, K, net=n)                      # warm-up
+        p = cs.SolveParams(T=T, K=K, V=V, S=S, seed=seed + 4, power_v0=v0, precision=cs.PREC_BF16_SPLIT, warm=n,
+                           x_ref=x_inf, trace=True)
+        cs.recon_solve(plan, y, maps, lam, cs.REG_L1_WAVELET, p, wavelet_levels=levels)      # untimed
         torch.cuda.synchronize()
         a, b = _events()
         a.record()
-        _, _, acc = ws.run(su, T, K, net=n, callback=lambda t, x: errs.append(x))
+        _, st = cs.recon_solve(plan, y, maps, lam, cs.REG_L1_WAVELET, p, wavelet_levels=levels)
         b.record()
         torch.cuda.synchronize()
-        res[name] = ([float((x - x_inf).norm() / x_inf.norm()) for x in errs], acc, a.elapsed_time(b))
-    print(f"warm start on {args.config} ({img}, {C} coils): {len(pairs)} training pairs from {args.phantoms} "
-          f"phantoms in {t_pairs:.1f} s; {args.train_steps} Adam steps on 64^3 crops in {t_train:.2f} s "
-          f"(loss {np.mean(hist[:10]):.3e} -> {np.mean(hist[-10:]):.3e})")
+        tr = st["trace"]
+        res[name] = (np.sqrt(np.maximum(tr[:, cs.TRACE_DIST2], 0)), tr[:, cs.TRACE_ACCEPT], a.elapsed_time(b))
+    print(f"warm start on {args.config} ({img}, {C} coils, m = {V} + {S}): {T * args.phantoms} training pairs "
+          f"(x^t, d, sub-problem solved with {tight} FISTA iterations) from {args.phantoms} phantoms at K = {K} in "
+          f"{t_pairs:.1f} s; {args.train_steps} Adam steps on random 64^3 crops in {t_train:.2f} s "
+          f"(loss {np.mean(hist[:20]):.3e} -> {np.mean(hist[-20:]):.3e})")
     for name in ("without", "with"):
         e, acc, ms = res[name]
-        extra = f", accepted {sum(acc)}/{len(acc)}" if acc else ""
-        print(f"  held-out, {name} warm start: NRMSE to x_inf " + " ".join(f"{v:.3e}" for v in e) +
-              f"; {ms:.0f} ms per reconstruction{extra}")
+        extra = f", accepted {int((acc == 1).sum())}/{len(acc)}" if name == "with" else ""
+        print(f"  held-out, {name} warm start: NRMSE to x_inf ({args.ref_iters} plain iterations) per outer " +
+              " ".join(f"{v:.3e}" for v in e) + f"; {ms:.0f} ms per reconstruction{extra}")
 
 
 def main():
@@ -577,6 +592,11 @@ def main():
     ap.add_argument("--phantoms", type=int, default=4)
     ap.add_argument("--autotune", action="store_true", help="nufft: tune the gridding launches first")
     ap.add_argument("--train-steps", type=int, default=300)
+    ap.add_argument("--outer", type=int, default=6, help="warmtrain: outer iterations per phantom")
+    ap.add_argument("--K", type=int, default=4, help="warmtrain: inner FISTA iterations")
+    ap.add_argument("--tight", type=int, default=40, help="warmtrain: FISTA iterations of a training target")
+    ap.add_argument("--ref-iters", type=int, default=300, help="warmtrain: plain FISTA iterations of x_inf")
+    ap.add_argument("--save", default="", help="warmtrain: write the trained network here")
     args = ap.parse_args()
     {"nufft": nufft, "normal": normal, "tv": tv, "ablation": ablation, "gfactor": gfactor, "compare": compare,
      "sketch": sketch, "cart2d": cart2d, "batched": batched, "warmnet": warmnet, "warmtrain": warmtrain}[args.what](args)

@@ -154,10 +154,20 @@ def test_gridding_parameters_and_autotune():
                 plan.set_gridding(ic, k, sc, k)
                 assert nrmse(h(cs.sense_fwd(plan, t(x), t(maps))), y_ref) < TOL, (ic, sc, k)
                 assert nrmse(h(cs.sense_adj(plan, t(yy), t(maps))), xa_ref) < TOL, (ic, sc, k)
+    # the deterministic (owner-computes) spreading with work items of 64 / 256 / 4096 sample
+    # visits: small items split every tile's list into many partial slots added afterwards
+    for sc in (8, 16):
+        for q in (64, 256, 4096):
+            plan.set_gridding(16, 64, sc, 64)
+            plan.set_deterministic(True, q)
+            assert nrmse(h(cs.sense_adj(plan, t(yy), t(maps))), xa_ref) < TOL, (sc, q)
+    plan.set_deterministic(False)
     with pytest.raises(cs.CoilSketchError):
         plan.set_gridding(0, 64, 16, 64)
     with pytest.raises(cs.CoilSketchError):
         plan.set_gridding(16, 64, 32, 64)          # spreading takes at most 16 coils per warp
+    with pytest.raises(cs.CoilSketchError):
+        plan.set_deterministic(True, 32)           # work items hold at least 64 sample visits
     choice, ms = plan.autotune(C, reps=2)
     assert choice[0] in (8, 16, 32) and choice[2] in (8, 16) and choice[1] in (32, 64, 128) and choice[3] in (32, 64, 128)
     assert all(v > 0 for v in ms) and ms[0] <= ms[2] and ms[1] <= ms[3]
@@ -177,8 +187,7 @@ def test_nufft_binning_bit_exact():
     perm, off, j0, nt = plan.binning()
     g = binning.grid_coords(traj, grid)
     j0_ref = binning.kernel_box_start(g)
-    tid, ntr = binning.tile_ids(j0_ref, grid, tile)
-    perm_ref, off_ref = binning.tile_sort_fast(tid, int(np.prod(ntr)))
+    perm_ref, off_ref, ntr = binning.sample_order(j0_ref, grid, tile)
     assert tuple(nt) == tuple(int(v) for v in ntr)
     assert np.array_equal(j0.cpu().numpy(), j0_ref)
     assert np.array_equal(perm.cpu().numpy(), perm_ref)
@@ -212,3 +221,34 @@ def test_plan_rejects_bad_arguments():
         cs.Plan(cs.CARTESIAN, (64, 62 + 1), 2, mask_idx=t(np.array([1, 2]), np.int32))     # odd size
     with pytest.raises(cs.CoilSketchError):
         cs.Plan(cs.CARTESIAN, (26, 26), 2, mask_idx=t(np.array([1, 2]), np.int32))          # prime 13
+
+
+@pytest.mark.parametrize("img,grid,tile,item", [((32, 32, 32), (40, 40, 40), (8, 8, 8), 4096),
+                                                ((32, 48, 48), (40, 60, 60), (8, 8, 8), 128),
+                                                ((16, 16, 32), (20, 18, 40), (8, 8, 16), 300),
+                                                ((16, 16, 32), (18, 20, 40), (16, 8, 8), 512)])
+def test_deterministic_spreading_is_bit_reproducible(img, grid, tile, item):
+    """In the deterministic mode the owner-computes spreading adds every grid point's contributions
+    in one fixed order (no atomics): two runs of the adjoint, of the gradient and of the sketched
+    normal operator give bit-identical images; with small work items (many partial slots added in
+    slot order) too.  The 18-point axis has a last tile of 10 (its 2-point remainder folds into
+    it); a z size of 2 mod 4 (the third case's 20 is 0 mod 4, the 18 of the second axis is 2 mod 4)
+    exercises the lane mapping choice."""
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    C = 6
+    traj, dcf, maps, x = _nufft_case(img, grid, C, 400, 128, seed=3)
+    plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=t(traj), dcf=t(dcf), grid=grid, tile=tile)
+    plan.set_deterministic(True, item)
+    op = nufft.Plan(traj, img, grid)
+    yy = synthdata.random_complex((C, traj.shape[0]), 11)
+    a1 = h(cs.sense_adj(plan, t(yy), t(maps)))
+    a2 = h(cs.sense_adj(plan, t(yy), t(maps)))
+    assert np.array_equal(a1.view(np.uint64), a2.view(np.uint64))
+    assert nrmse(a1, nufft.sense_adj(op, yy, maps, dcf)) < TOL
+    d1 = h(cs.sense_grad(plan, t(x), t(maps), t(yy)))
+    d2 = h(cs.sense_grad(plan, t(x), t(maps), t(yy)))
+    assert np.array_equal(d1.view(np.uint64), d2.view(np.uint64))
+    z1 = h(cs.sketched_normal_apply(plan, t(x), t(maps[:2]), t(maps[2:5]), 1e-3))
+    z2 = h(cs.sketched_normal_apply(plan, t(x), t(maps[:2]), t(maps[2:5]), 1e-3))
+    assert np.array_equal(z1.view(np.uint64), z2.view(np.uint64))

@@ -305,6 +305,11 @@ def _problem(seed, img=(32, 48, 48), grid=(40, 60, 60), C=8, n_int=1500, n_read=
 
 
 def test_training_and_warm_start_in_algorithm_1():
+    """Training on the method's own pairs lowers the loss, and on a held-out phantom the trained
+    network's accepted predictions bring the first two outer iterates of Algorithm 1 strictly closer
+    to x_inf than the method without it (recon_solve, decision on the device).  Everything runs
+    bit-reproducibly (deterministic spreading, fixed-order weight-gradient and loss sums), so the
+    measured gain is the same on every run."""
     import paper_2305_06482_gb300 as cs
     import paper_2305_06482_gb300.warmstart as ws
     img = (32, 48, 48)
@@ -312,6 +317,7 @@ def test_training_and_warm_start_in_algorithm_1():
     pairs = []
     for seed in (101, 102, 103, 104):
         plan, y, maps = _problem(seed)
+        plan.set_deterministic(True)
         su = ws.setup(plan, y, maps, lam, V, S, T, seed, synthdata.phantom_torch(img, seed=seed + 50), levels)
         _, pr, _ = ws.run(su, T, K, record_pairs=1, tight_K=40)
         pairs += pr
@@ -321,22 +327,25 @@ def test_training_and_warm_start_in_algorithm_1():
     assert last < first, (first, last)
     # held-out phantom: convergence with and without the warm start
     plan, y, maps = _problem(999)
+    plan.set_deterministic(True)
     v0 = synthdata.phantom_torch(img, seed=1049)
     x_inf, _ = cs.recon_solve(plan, y, maps, lam, cs.REG_L1_WAVELET,
                               cs.SolveParams(K=400, sketch=False, do_pca=False, power_v0=v0), wavelet_levels=levels)
-    su = ws.setup(plan, y, maps, lam, V, S, T, 999, v0, levels)
-    e_plain, e_warm = [], []
-    ws.run(su, T, K, callback=lambda t, x: e_plain.append(float((x - x_inf).norm() / x_inf.norm())))
-    _, _, acc = ws.run(su, T, K, net=net, callback=lambda t, x: e_warm.append(float((x - x_inf).norm() / x_inf.norm())))
-    print(f"\\nwarm-start training loss {first:.3e} -> {last:.3e}; accepted {sum(acc)}/{len(acc)}")
-    print("NRMSE vs x_inf without warm start:", ["%.2e" % e for e in e_plain])
-    print("NRMSE vs x_inf with warm start:   ", ["%.2e" % e for e in e_warm])
-    # the acceptance test only admits predictions that lower the current sub-problem's objective;
-    # with K = 4 inexact inner iterations that does not make every later iterate better (the
-    # trained network, and so which predictions pass, varies from run to run: its weight
-    # gradients are summed atomically), so only convergence to the same neighbourhood is required
-    assert len(acc) == len(e_warm) == len(e_plain) == T
-    assert np.isfinite(e_warm).all() and e_warm[-1] <= 2.0 * e_plain[-1]
+    curves, acc = {}, None
+    for name, n in (("plain", None), ("warm", net)):
+        _, st = cs.recon_solve(plan, y, maps, lam, cs.REG_L1_WAVELET,
+                               cs.SolveParams(T=T, K=K, V=V, S=S, seed=999, power_v0=v0, warm=n, x_ref=x_inf, trace=True),
+                               wavelet_levels=levels)
+        curves[name] = np.sqrt(st["trace"][:, cs.TRACE_DIST2])
+        if n is not None:
+            acc = st["trace"][:, cs.TRACE_ACCEPT]
+    e_plain, e_warm = curves["plain"], curves["warm"]
+    print(f"\nwarm-start training loss {first:.3e} -> {last:.3e}; accepted {int((acc == 1).sum())}/{T}")
+    print("NRMSE vs x_inf without warm start:", ["%.3e" % e for e in e_plain])
+    print("NRMSE vs x_inf with warm start:   ", ["%.3e" % e for e in e_warm])
+    assert acc[0] == 1
+    assert e_warm[0] < e_plain[0] and e_warm[1] < e_plain[1]
+    assert np.isfinite(e_warm).all()
 
 
 def test_warm_start_decided_on_the_device_matches_the_host_loop():
@@ -356,6 +365,7 @@ def test_warm_start_decided_on_the_device_matches_the_host_loop():
     net = ws.UNet(seed=0)
     ws.train(net, pairs, steps=150, lr=2e-3)
     plan, y, maps = _problem(999)
+    plan.set_deterministic(True)          # bit-reproducible spreading: graph replay == eager exactly
     v0 = synthdata.phantom_torch(img, seed=1049)
     su = ws.setup(plan, y, maps, lam, V, S, T, 999, v0, levels)
     host = []
@@ -376,7 +386,7 @@ def test_warm_start_decided_on_the_device_matches_the_host_loop():
         for k in range(T):
             assert float((iters[k] - host[k]).norm() / host[k].norm()) < 1e-4
         runs.append(x)
-    assert float((runs[0] - runs[1]).norm() / runs[0].norm()) < 1e-6
+    assert torch.equal(runs[0], runs[1])
     print(f"\\nwarm starts accepted {sum(acc)}/{T}")
     with pytest.raises(cs.CoilSketchError):          # the warm start serves sketched FISTA only
         cs.recon_solve(plan, y, maps, lam, cs.REG_L2, cs.SolveParams(T=2, K=2, V=V, S=S, warm=net))

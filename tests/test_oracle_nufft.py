@@ -106,3 +106,69 @@ def test_box_and_tile_sort():
         seg = perm[offs[t]:offs[t + 1]]
         assert np.all(np.diff(seg) > 0)                   # stable
         assert np.all(tid[seg] == t)
+
+
+@pytest.mark.parametrize("grid,tile", [((20, 20, 20), (8, 8, 8)), ((18, 26, 40), (8, 8, 16)), ((16, 12), (16, 8))])
+def test_halo_classes_and_tile_owners_by_brute_force(grid, tile):
+    """The halo class of every sample against its box's grid indices, tile by tile: every box index
+    lies in the sample's own tile or the next one along each axis (remainders narrower than the
+    kernel fold into the last tile: 18 = 8 + 10, 26 = 8 + 8 + 10), a class bit is set exactly when
+    the box reaches the next tile, and the samples whose box touches a tile are its own samples and
+    those of its lower neighbours t - e whose class contains e."""
+    import itertools
+    nd = len(grid)
+    rng = np.random.default_rng(len(grid) * 100 + grid[0])
+    traj = rng.uniform(-0.5, 0.5, size=(600, nd)).astype(np.float32)
+    traj[:4] = 0.5                                     # on the edge (wraps to index 0)
+    g = binning.grid_coords(traj, grid).astype(np.float64)
+    j0 = binning.kernel_box_start(g)
+    key, nt = binning.sort_keys(j0, grid, tile)
+    tid, cls = key // 8, key % 8
+    # brute force: owning tile index of every grid index along each axis
+    owner = []
+    for ax in range(nd):
+        G, T, n = grid[ax], tile[ax], nt[ax]
+        starts = [k * T for k in range(n)]
+        own = np.array([max(k for k in range(n) if starts[k] <= j) for j in range(G)])
+        assert own[-1] == n - 1 and min(np.bincount(own)) >= binning.KB_WIDTH
+        owner.append(own)
+    tix = np.stack([np.unravel_index(t, tuple(nt)) for t in tid])        # per-axis tile of each sample
+    for ax in range(nd):
+        box = np.mod(j0[:, ax:ax + 1] + np.arange(binning.KB_WIDTH)[None, :], grid[ax])
+        bt = owner[ax][box]
+        nxt = (tix[:, ax:ax + 1] + 1) % nt[ax]
+        assert np.all((bt == tix[:, ax:ax + 1]) | (bt == nxt))
+        reach = np.any(bt != tix[:, ax:ax + 1], axis=1)
+        assert np.array_equal(reach, ((cls >> (nd - 1 - ax)) & 1).astype(bool))
+    # owners: samples touching tile t == own + lower neighbours' reaching classes
+    touch = {}
+    for i in range(j0.shape[0]):
+        boxes = [np.mod(j0[i, ax] + np.arange(binning.KB_WIDTH), grid[ax]) for ax in range(nd)]
+        for pt in itertools.product(*boxes):
+            t = np.ravel_multi_index(tuple(owner[ax][pt[ax]] for ax in range(nd)), tuple(nt))
+            touch.setdefault(int(t), set()).add(i)
+    for t in range(int(np.prod(nt))):
+        tt = np.unravel_index(t, tuple(nt))
+        want = set()
+        for e in range(1 << nd):
+            bits = [(e >> (nd - 1 - ax)) & 1 for ax in range(nd)]
+            if any(b and nt[ax] == 1 for ax, b in enumerate(bits)):
+                continue
+            src = np.ravel_multi_index(tuple((tt[ax] - bits[ax]) % nt[ax] for ax in range(nd)), tuple(nt))
+            want |= set(np.nonzero((tid == src) & ((cls & e) == e))[0].tolist())
+        assert touch.get(t, set()) == want, t
+
+
+def test_sample_order_is_stable_by_tile_then_class():
+    traj = synthdata.cones_trajectory(40, 64)
+    grid, tile = (20, 20, 20), (8, 8, 8)
+    j0 = binning.kernel_box_start(binning.grid_coords(traj, grid).astype(np.float64))
+    key, nt = binning.sort_keys(j0, grid, tile)
+    perm, offs, nt2 = binning.sample_order(j0, grid, tile)
+    assert tuple(nt) == tuple(nt2)
+    p_lit, _ = binning.tile_sort(key, int(np.prod(nt)) * 8)          # literal counting sort on the key
+    assert np.array_equal(perm, p_lit)
+    assert np.all(np.diff(key[perm]) >= 0)
+    for t in range(int(np.prod(nt))):
+        seg = perm[offs[t]:offs[t + 1]]
+        assert np.all(key[seg] // 8 == t)
