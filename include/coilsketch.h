@@ -379,6 +379,17 @@ cs_status recon_solve_batched(int nslices, const cs_batch_item* items, const cs_
                               cs_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------------------------------
+ * Pseudo-replica noise statistics (the paper's Sec. 3.2 inverse g-factor analysis, after
+ * Pruessmann et al. and Robson et al.): recons are K reconstructions of noisy copies of one
+ * acquisition, complex64 [K][D] device arrays.  cs_noise_std: std_out[i] = sqrt(mean_k |x_k[i] -
+ * mean_k x_k[i]|^2) (float [D]); cs_inverse_gfactor: inv_g[i] = std_full[i] sqrt(R) / std_R[i]
+ * (float [D]).  Computed in FP64 per pixel, summing the replicas in order.  Asynchronous.
+ * ---------------------------------------------------------------------------------------- */
+cs_status cs_noise_std(const float* recons, int K, int64_t D, float* std_out, void* stream);
+cs_status cs_inverse_gfactor(const float* recons_R, const float* recons_full, int K, int64_t D, float R, float* inv_g,
+                             void* stream);
+
+/* ------------------------------------------------------------------------------------------
  * Sub-problem pieces for callers that drive Algorithm 1 themselves (e.g. with a warm start).
  * sketched_subproblem_solve: K iterations (CG for CS_REG_L2, FISTA with step `step` for
  *   CS_REG_L1_WAVELET) on the sketched sub-problem of Eq. 9-10,

@@ -84,7 +84,7 @@ EXPORTED = [
     "cs_nn_maxpool2", "cs_nn_maxpool2_bwd", "cs_nn_upconv2", "cs_nn_upconv2_bwd", "cs_nn_slice",
     "ws_net_create", "ws_net_destroy", "ws_net_infer", "ws_net_train_step", "ws_net_param", "ws_net_save",
     "ws_net_load", "cs_crop3d", "cs_wait_selftest", "cs_plan_set_gridding", "cs_plan_autotune",
-    "cs_plan_set_deterministic",
+    "cs_plan_set_deterministic", "cs_noise_std", "cs_inverse_gfactor",
 ]
 STAGES = {"spread": 0, "interp": 1, "fft_plain": 2, "expand": 3, "reduce": 4}
 
@@ -141,6 +141,7 @@ def lib():
             "cs_crop3d": ([vp, vp, vp, vp, vp, vp], i), "cs_wait_selftest": ([i, i64, vp], i),
             "cs_plan_set_gridding": ([vp, i, i, i, i], i), "cs_plan_autotune": ([vp, i, i, vp, vp, vp], i),
             "cs_plan_set_deterministic": ([vp, i, i], i),
+            "cs_noise_std": ([vp, i, i64, vp, vp], i), "cs_inverse_gfactor": ([vp, vp, i, i64, f, vp, vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)

@@ -31,7 +31,13 @@ def _needs_build(srcs, headers):
     return any(os.path.getmtime(f) > t for f in srcs + headers + [__file__])
 
 
-def build(verbose=False, force=False, extra_flags=()):
+def build(verbose=False, force=False, extra_flags=(), checked=False):
+    """Compile and link the library (only when a source is newer, unless force).  checked=True
+    builds the bounds-checked variant (-DCS_CHECK_BOUNDS): every guarded device access checks its
+    index, and a violation is reported as CS_ERR_BOUNDS instead of touching memory."""
+    if checked:
+        extra_flags = tuple(extra_flags) + ("-DCS_CHECK_BOUNDS",)
+        force = True
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(HERE, "..", "include", "coilsketch.h")]
     if not force and not _needs_build(srcs, headers):
@@ -61,4 +67,4 @@ def build(verbose=False, force=False, extra_flags=()):
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, force="--force" in sys.argv))
+    print(build(verbose=True, force="--force" in sys.argv, checked="--checked" in sys.argv))

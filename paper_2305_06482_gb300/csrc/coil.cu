@@ -498,6 +498,12 @@ static cs_status coil_attrs_once() {
     return CS_OK;
 }
 
+// the device-side index checks of every translation unit with guarded accesses (checked builds)
+cs_status bounds_check_all() {
+    CS_PROPAGATE(nufft_bounds_check());
+    return fft_bounds_check();
+}
+
 cs_status coil_pca_impl(const float2* y, int C, int64_t N, float2* U, double* eig, double* Rws, cudaStream_t st) {
     CS_TRY_CUDA(cudaMemsetAsync(Rws, 0, sizeof(double) * 2 * C * C, st));
     const int nb = (C + 3) / 4;
@@ -650,6 +656,7 @@ cs_status cs_device_status(void* stream) {
     clear_error();
     CS_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     CS_PROPAGATE(fft_check_and_clear());
+    CS_PROPAGATE(bounds_check_all());
     return tc_check_and_clear();
 }
 

@@ -55,6 +55,40 @@ void prof_end(int stage, cudaStream_t st);
     } while (0)
 
 // ------------------------------------------------------------------------------------------
+// Bounds-checked builds (compiled with -DCS_CHECK_BOUNDS, build(checked=True)): every guarded
+// global access checks its element index against the length of its buffer; an index outside
+// skips the access (a guarded load reads zero) and sets the error word of its translation unit,
+// which cs_device_status and recon_solve report as CS_ERR_BOUNDS.  Nothing traps: the context
+// stays usable.  In normal builds a guard is the constant true and compiles away.
+#ifdef CS_CHECK_BOUNDS
+static __device__ unsigned int cs_bounds_word = 0;
+__device__ __forceinline__ bool cs_inb(long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    atomicOr(&cs_bounds_word, 1u);
+    return false;
+}
+#define CS_INB(i, n) ::cs::cs_inb((long long)(i), (long long)(n))
+#define CS_BOUNDS_READER(fn)                                                                  \
+    cs_status fn() {                                                                          \
+        unsigned int v = 0;                                                                   \
+        CS_TRY_CUDA(cudaMemcpyFromSymbol(&v, cs_bounds_word, sizeof(v)));                     \
+        if (!v) return CS_OK;                                                                 \
+        const unsigned int zero = 0;                                                          \
+        cudaMemcpyToSymbol(cs_bounds_word, &zero, sizeof(zero));                              \
+        set_error("a device-side index check failed (%s)", #fn);                             \
+        return CS_ERR_BOUNDS;                                                                 \
+    }
+#else
+#define CS_INB(i, n) true
+#define CS_BOUNDS_READER(fn) \
+    cs_status fn() { return CS_OK; }
+#endif
+// readers of the translation units with guarded accesses (after the caller synchronised)
+cs_status nufft_bounds_check();
+cs_status fft_bounds_check();
+cs_status bounds_check_all();
+
+// ------------------------------------------------------------------------------------------
 // complex helpers (complex64 = float2)
 __host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }

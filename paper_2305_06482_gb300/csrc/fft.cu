@@ -388,8 +388,10 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
                 const bool ok = srow[l] >= 0;
                 const float2* p = A.in + sbase[l] + (int64_t)jt * A.C;
                 const int64_t step = (int64_t)kJ * A.C;
+                const int64_t inlim = A.rows * n * A.C;
+                (void)inlim;
                 for (int k = jt; k < n; k += kJ, p += step) {
-                    if (ok) cp8(&bufa[k * kLinePad + l], p);
+                    if (ok && CS_INB(sbase[l] + (int64_t)k * A.C, inlim)) cp8(&bufa[k * kLinePad + l], p);
                     else bufa[k * kLinePad + l] = make_float2(0.f, 0.f);
                 }
                 cp_wait_all();
@@ -401,7 +403,7 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
             float2* mp = (res == bufa) ? bufb : bufa;
             for (int e = tid; e < R * cw * nx; e += kPassThreads) {
                 const int ln = div_nx(A, e), i = e - ln * nx;
-                if (smp[ln]) cp8(&mp[e], smp[ln] + i);
+                if (smp[ln] && CS_INB((int64_t)srow[ln] * nx + i, A.D)) cp8(&mp[e], smp[ln] + i);
             }
             cp_wait_all();
             __syncthreads();
@@ -424,9 +426,11 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
                 const float ap = A.apz[z] * A.apy[yy] * A.apx[i];
                 float2 r = cscale(acc[e], ap);
                 const int64_t g = (int64_t)row * nx + i;
-                if (A.addv) r = cadd(r, cscale(A.addv[g], A.lambda));
-                if (A.accumulate) r = cadd(r, A.xo[g]);
-                A.xo[g] = r;
+                if (CS_INB(g, A.D)) {
+                    if (A.addv) r = cadd(r, cscale(A.addv[g], A.lambda));
+                    if (A.accumulate) r = cadd(r, A.xo[g]);
+                    A.xo[g] = r;
+                }
             }
         }
         return;
@@ -463,7 +467,7 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
         for (int e = tid; e < kLines * nx; e += kPassThreads) {
             const int le = div_nx(A, e), i = e - le * nx;
             float2* da = &bufa[(i + A.in_off) * kLinePad + le];
-            if (sxp[le]) {
+            if (sxp[le] && CS_INB((int64_t)srow[le] * nx + i, A.D)) {
                 cp8(da, sxp[le] + i);
                 cp8(&bufb[i * kLinePad + le], smp[le] + i);
             } else {
@@ -494,10 +498,12 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
 #pragma unroll
                 for (int b = 0; b < LB; ++b) {
                     const int k = k0 + b * kJ;
-                    f[b] = (iv && k < n) ? A.idxmap[(int64_t)k * A.nxi + px] : -1;
+                    f[b] = (iv && k < n && CS_INB((int64_t)k * A.nxi + px, A.D)) ? A.idxmap[(int64_t)k * A.nxi + px] : -1;
                 }
 #pragma unroll
-                for (int b = 0; b < LB; ++b) t[b] = (f[b] >= 0) ? A.yk[(int64_t)cc * A.N + f[b]] : make_float2(0.f, 0.f);
+                for (int b = 0; b < LB; ++b)
+                    t[b] = (f[b] >= 0 && CS_INB((int64_t)cc * A.N + f[b], (int64_t)A.C * A.N)) ? A.yk[(int64_t)cc * A.N + f[b]]
+                                                                                             : make_float2(0.f, 0.f);
 #pragma unroll
                 for (int b = 0; b < LB; ++b) {
                     const int k = k0 + b * kJ;
@@ -516,7 +522,9 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
 #pragma unroll
                 for (int b = 0; b < LB; ++b) {
                     const int kk = k0 + b * kJ;
-                    t[b] = (iv && kk < A.n_in) ? pk[(int64_t)b * kJ * A.inner] : make_float2(0.f, 0.f);
+                    t[b] = (iv && kk < A.n_in && CS_INB((o0 * A.n_in + kk) * A.inner + i, A.outer * A.n_in * A.inner))
+                               ? pk[(int64_t)b * kJ * A.inner]
+                               : make_float2(0.f, 0.f);
                 }
 #pragma unroll
                 for (int b = 0; b < LB; ++b) {
@@ -534,11 +542,11 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
         // U^H U (minus data) between the forward and the inverse transform
         for (int k = jt; k < n; k += kJ) {
             float2 v = make_float2(0.f, 0.f);
-            if (iv) {
+            if (iv && CS_INB((int64_t)k * A.nxi + px, A.D)) {
                 const int32_t f = A.idxmap[(int64_t)k * A.nxi + px];
                 if (f >= 0) {
                     v = res[k * kLinePad + l];
-                    if (A.residual) {
+                    if (A.residual && CS_INB((int64_t)cc * A.N + f, (int64_t)A.C * A.N)) {
                         float2 yv = A.yk[(int64_t)cc * A.N + f];
                         if (cart_neg(k, px, n, A.nxi)) yv = make_float2(-yv.x, -yv.y);
                         v = csub(v, yv);
@@ -556,14 +564,17 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
         if (srow[l] >= 0) {
             float2* p = A.out + sbase[l] + (int64_t)jt * A.C;
             const int64_t step = (int64_t)kJ * A.C;
+            const int64_t outlim = A.rows * n * A.C;
+            (void)outlim;
 #pragma unroll 4
-            for (int k = jt; k < n; k += kJ, p += step) *p = res[k * kLinePad + l];
+            for (int k = jt; k < n; k += kJ, p += step)
+                if (CS_INB(sbase[l] + (int64_t)k * A.C, outlim)) *p = res[k * kLinePad + l];
         }
     } else if (MODE == GATHER_Y) {
         if (iv) {
             for (int k = jt; k < n; k += kJ) {
-                const int32_t f = A.idxmap[(int64_t)k * A.nxi + px];
-                if (f >= 0) {
+                const int32_t f = CS_INB((int64_t)k * A.nxi + px, A.D) ? A.idxmap[(int64_t)k * A.nxi + px] : -1;
+                if (f >= 0 && CS_INB((int64_t)cc * A.N + f, (int64_t)A.C * A.N)) {
                     float2 v = res[k * kLinePad + l];
                     if (cart_neg(k, px, n, A.nxi)) v = make_float2(-v.x, -v.y);
                     A.yko[(int64_t)cc * A.N + f] = v;
@@ -573,7 +584,9 @@ __global__ void __launch_bounds__(kPassThreads, 3) fft_pass_kernel(PassArgs A) {
     } else if (iv) {
         float2* p = A.out + o0 * A.n_out * A.inner + i0 + l;
 #pragma unroll 4
-        for (int kk = jt; kk < A.n_out; kk += kJ) p[(int64_t)kk * A.inner] = res[(kk + A.out_off) * kLinePad + l];
+        for (int kk = jt; kk < A.n_out; kk += kJ)
+            if (CS_INB((o0 * A.n_out + kk) * A.inner + i0 + l, A.outer * A.n_out * A.inner))
+                p[(int64_t)kk * A.inner] = res[(kk + A.out_off) * kLinePad + l];
     }
 }
 
@@ -813,6 +826,16 @@ static cs_status pass_plain(const cs_plan* p, int axis, int sign, const float2* 
     CS_REQUIRE(A.iblocks < (int64_t)1 << 31 && outer <= 65535 && inner < (int64_t)1 << 31,
                CS_ERR_UNSUPPORTED_SIZE, "pass grid too large");
     const dim3 blocks((unsigned)A.iblocks, (unsigned)outer);
+    // the copy unit clips every tensor copy to its tensor map; the maps must not describe more
+    // than the plan buffers they address
+    auto capacity = [&](const float2* b) -> int64_t {
+        if (b == p->bufA) return (int64_t)p->max_coils * p->G;
+        if (b == p->bufB) return (int64_t)p->max_coils * p->img[0] * p->grid[1] * p->grid[2];
+        return -1;
+    };
+    const int64_t cin_ = capacity(in), cout_ = capacity(out);
+    CS_REQUIRE((cin_ < 0 || inner * n_in * outer <= cin_) && (cout_ < 0 || inner * n_out * outer <= cout_), CS_ERR_BOUNDS,
+               "a tensor-copy pass would address beyond its buffer");
     CUtensorMap tin, tout;
     CS_PROPAGATE(encode_3d(&tin, in, inner, n_in, outer, A.h_in));
     CS_PROPAGATE(encode_3d(&tout, out, inner, n_out, outer, A.h_out));
@@ -825,6 +848,8 @@ static cs_status pass_plain(const cs_plan* p, int axis, int sign, const float2* 
     prof_end(ST_FFT_PLAIN, st);
     return CS_OK;
 }
+
+CS_BOUNDS_READER(fft_bounds_check)
 
 // reads and clears the flag of a tensor-copy wait that gave up (after the caller synchronised)
 cs_status fft_check_and_clear() {
@@ -889,6 +914,7 @@ static cs_status pass_cart_y(const cs_plan* p, int mode, int C, const float2* yk
     const int sign = (mode == SCATTER_Y) ? +1 : -1;
     fill_fft(A, p->fft[1], sign);
     A.C = C;
+    A.D = p->D;
     A.nxi = p->img[2];
     A.outer = 1;
     A.inner = (int64_t)p->img[2] * C;

@@ -361,7 +361,8 @@ __global__ void sample_record_kernel(const float* __restrict__ gs, const float* 
 }
 
 // Stage the records of samples [base, base + n) (n <= kStage) into the warp's shared buffer.
-__device__ __forceinline__ void stage_records(const float* __restrict__ rec, int64_t base, int n, float* wrec, int lane) {
+__device__ __forceinline__ void stage_records(const float* __restrict__ rec, int64_t base, int n, float* wrec, int lane,
+                                              int64_t N) {
     __syncwarp();
     const float4* src = reinterpret_cast<const float4*>(rec + base * kRec);
     float4* dst = reinterpret_cast<float4*>(wrec);
@@ -369,7 +370,8 @@ __device__ __forceinline__ void stage_records(const float* __restrict__ rec, int
 #pragma unroll
     for (int k = 0; k < kStage * kRec / 4 / 32; ++k) {
         const int i = lane + 32 * k;
-        if (i < n * (kRec / 4)) t[k] = __ldg(src + i);
+        if (i < n * (kRec / 4))
+            t[k] = CS_INB(base * (kRec / 4) + i, N * (kRec / 4)) ? __ldg(src + i) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
     for (int k = 0; k < kStage * kRec / 4 / 32; ++k) {
@@ -454,6 +456,11 @@ __device__ __forceinline__ void set_offsets(int (&off)[kW], int j0, int G, int s
 
 // S lanes per coil, P planes per lane: S * P = 4 for 3D plans, S = P = 1 for 2D plans (one plane
 // z = 0 whose z weight is 1).
+// grid value at element offset off of coil c (g = grid + c); guarded in checked builds
+__device__ __forceinline__ float2 gridld(const float2* __restrict__ g, int c, int off, int64_t glim) {
+    return CS_INB((int64_t)c + off, glim) ? __ldg(g + off) : make_float2(0.f, 0.f);
+}
+
 template <int S, int P>
 __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
     interp_kernel(GridArgs A, int mode, const float2* __restrict__ ysub, float2* __restrict__ out) {
@@ -470,6 +477,8 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
     float* wrec = srec + (threadIdx.x >> 5) * (kStage * kRec);
     const int sy = A.Gx * A.C, sz = A.Gy * A.Gx * A.C;
     const float2* g = A.grid + c;
+    const int64_t glim = (int64_t)A.Gz * A.Gy * A.Gx * A.C;
+    (void)glim;
     Win<P> W;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -485,7 +494,7 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
     int cy = kNoPlane, cx = kNoPlane;
     for (int base = s0; base < s1; base += kStage) {
         const int n = min(kStage, s1 - base);
-        stage_records(A.rec, base, n, wrec, lane);
+        stage_records(A.rec, base, n, wrec, lane, A.N);
 #if CS_INTERP_HEAD_PREFETCH
         BoxHead Bn = box_head(wrec);
 #endif
@@ -518,7 +527,7 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
                             for (int p = 0; p < P; ++p)
                                 if (W.zc[p] != kNoPlane) {
 #pragma unroll
-                                    for (int d = 0; d < kW; ++d) W.v[p][R][d] = __ldg(g + (W.zoff[p] + W.yoff[R] + W.xoff[d]));
+                                    for (int d = 0; d < kW; ++d) W.v[p][R][d] = gridld(g, c, W.zoff[p] + W.yoff[R] + W.xoff[d], glim);
                                 }
                         }
                     });
@@ -534,7 +543,7 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
                             for (int p = 0; p < P; ++p)
                                 if (W.zc[p] != kNoPlane) {
 #pragma unroll
-                                    for (int b = 0; b < kW; ++b) W.v[p][b][R] = __ldg(g + (W.zoff[p] + W.yoff[b] + W.xoff[R]));
+                                    for (int b = 0; b < kW; ++b) W.v[p][b][R] = gridld(g, c, W.zoff[p] + W.yoff[b] + W.xoff[R], glim);
                                 }
                         }
                     });
@@ -560,7 +569,7 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
 #pragma unroll
                         for (int b = 0; b < kW; ++b)
 #pragma unroll
-                            for (int d = 0; d < kW; ++d) W.v[p][b][d] = __ldg(g + (W.zoff[p] + W.yoff[b] + W.xoff[d]));
+                            for (int d = 0; d < kW; ++d) W.v[p][b][d] = gridld(g, c, W.zoff[p] + W.yoff[b] + W.xoff[d], glim);
                     }
                 }
                 const float wzp = r[q];
@@ -584,12 +593,14 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
             if (active && slice == 0) {
                 const int64_t s = (int64_t)base + i;
                 acc = cscale(acc, B.sw);
+                const int64_t lim = (int64_t)A.C * A.N;
                 if (mode == OUT_USER) {
-                    out[(int64_t)c * A.N + B.perm] = acc;
+                    if (CS_INB((int64_t)c * A.N + B.perm, lim)) out[(int64_t)c * A.N + B.perm] = acc;
                 } else if (mode == OUT_RESID) {
-                    out[s * A.C + c] = csub(acc, ysub[(int64_t)c * A.N + B.perm]);
+                    if (CS_INB(s * A.C + c, lim) && CS_INB((int64_t)c * A.N + B.perm, lim))
+                        out[s * A.C + c] = csub(acc, ysub[(int64_t)c * A.N + B.perm]);
                 } else {
-                    out[s * A.C + c] = acc;
+                    if (CS_INB(s * A.C + c, lim)) out[s * A.C + c] = acc;
                 }
             }
         }
@@ -615,6 +626,8 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
     float* wrec = srec + (threadIdx.x >> 5) * (kStage * kRec);
     const int sy = A.Gx * A.C, sz = A.Gy * A.Gx * A.C;
     float2* g = A.grid + c;
+    const int64_t glim = (int64_t)A.Gz * A.Gy * A.Gx * A.C;
+    (void)glim;
     Win<P> W;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -633,7 +646,8 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
 #pragma unroll
             for (int b = 0; b < kW; ++b)
 #pragma unroll
-                for (int d = 0; d < kW; ++d) atomicAdd(g + (W.zoff[p] + W.yoff[b] + W.xoff[d]), W.v[p][b][d]);
+                for (int d = 0; d < kW; ++d)
+                    if (CS_INB((int64_t)c + W.zoff[p] + W.yoff[b] + W.xoff[d], glim)) atomicAdd(g + (W.zoff[p] + W.yoff[b] + W.xoff[d]), W.v[p][b][d]);
         }
 #pragma unroll
         for (int b = 0; b < kW; ++b)
@@ -643,11 +657,12 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
     // the sample value: sorted scratch [N][C] or user order [C][N]
     auto load_v = [&](int s, const float* r) -> float2 {
         if (!active) return make_float2(0.f, 0.f);
-        return sorted_in ? yin[(int64_t)s * A.C + c] : yin[(int64_t)c * A.N + __float_as_int(r[14])];
+        const int64_t i = sorted_in ? (int64_t)s * A.C + c : (int64_t)c * A.N + __float_as_int(r[14]);
+        return CS_INB(i, (int64_t)A.C * A.N) ? yin[i] : make_float2(0.f, 0.f);
     };
     for (int base = s0; base < s1; base += kStage) {
         const int n = min(kStage, s1 - base);
-        stage_records(A.rec, base, n, wrec, lane);
+        stage_records(A.rec, base, n, wrec, lane, A.N);
         float2 vnext = load_v(base, wrec);
 #if CS_SPREAD_HEAD_PREFETCH
         BoxHead Bn = box_head(wrec);
@@ -681,7 +696,8 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
                         for (int p = 0; p < P; ++p) {
                             if (active && W.zc[p] != kNoPlane) {
 #pragma unroll
-                                for (int d = 0; d < kW; ++d) atomicAdd(g + (W.zoff[p] + W.yoff[R] + W.xoff[d]), W.v[p][R][d]);
+                                for (int d = 0; d < kW; ++d)
+                                    if (CS_INB((int64_t)c + W.zoff[p] + W.yoff[R] + W.xoff[d], glim)) atomicAdd(g + (W.zoff[p] + W.yoff[R] + W.xoff[d]), W.v[p][R][d]);
                             }
 #pragma unroll
                             for (int d = 0; d < kW; ++d) W.v[p][R][d] = make_float2(0.f, 0.f);
@@ -698,7 +714,8 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
                         for (int p = 0; p < P; ++p) {
                             if (active && W.zc[p] != kNoPlane) {
 #pragma unroll
-                                for (int b = 0; b < kW; ++b) atomicAdd(g + (W.zoff[p] + W.yoff[b] + W.xoff[R]), W.v[p][b][R]);
+                                for (int b = 0; b < kW; ++b)
+                                    if (CS_INB((int64_t)c + W.zoff[p] + W.yoff[b] + W.xoff[R], glim)) atomicAdd(g + (W.zoff[p] + W.yoff[b] + W.xoff[R]), W.v[p][b][R]);
                             }
 #pragma unroll
                             for (int b = 0; b < kW; ++b) W.v[p][b][R] = make_float2(0.f, 0.f);
@@ -763,6 +780,7 @@ struct OwnerArgs {
     int nitems;
     const GRange* ranges;
     float2* part;          // partial slots
+    int nslots;
     int wz, wy, wx;        // slot geometry (widest tile per axis)
 };
 
@@ -805,13 +823,18 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
     // target base and strides: the grid (absolute offsets) or the item's slot (offsets from o)
     float2* tgt;
     int b[3], sz, sy, sx;
+    int64_t tbase, tlim;   // element offset of tgt in its buffer and the buffer length (checked builds)
     if (it.slot < 0) {
+        tbase = c;
+        tlim = (int64_t)A.Gz * A.Gy * A.Gx * A.C;
         tgt = A.grid + c;
         b[0] = b[1] = b[2] = 0;
         sx = A.C;
         sy = A.Gx * A.C;
         sz = A.Gy * A.Gx * A.C;
     } else {
+        tbase = (int64_t)it.slot * A.wz * A.wy * A.wx * A.gsize + (active ? coil_l : 0);
+        tlim = (int64_t)A.nslots * A.wz * A.wy * A.wx * A.gsize;
         tgt = A.part + (int64_t)it.slot * A.wz * A.wy * A.wx * A.gsize + (active ? coil_l : 0);
         b[0] = o[0];
         b[1] = o[1];
@@ -844,10 +867,11 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
                 float2 old[kW];
 #pragma unroll
                 for (int d = 0; d < kW; ++d)
-                    if ((xin_m >> d) & 1) old[d] = tgt[W.zoff[p] + W.yoff[bb] + W.xoff[d]];
+                    if (((xin_m >> d) & 1) && CS_INB(tbase + W.zoff[p] + W.yoff[bb] + W.xoff[d], tlim))
+                        old[d] = tgt[W.zoff[p] + W.yoff[bb] + W.xoff[d]];
 #pragma unroll
                 for (int d = 0; d < kW; ++d)
-                    if ((xin_m >> d) & 1)
+                    if (((xin_m >> d) & 1) && CS_INB(tbase + W.zoff[p] + W.yoff[bb] + W.xoff[d], tlim))
                         tgt[W.zoff[p] + W.yoff[bb] + W.xoff[d]] =
                             make_float2(old[d].x + W.v[p][bb][d].x, old[d].y + W.v[p][bb][d].y);
             }
@@ -862,13 +886,16 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
         const int rend = rg.start + rg.count;
         for (int base = rg.start; base < rend; base += kStage) {
             const int n = min(kStage, rend - base);
-            stage_records(A.rec, base, n, wrec, lane);
+            stage_records(A.rec, base, n, wrec, lane, A.Nsamp);
 #pragma unroll 1
             for (int i = 0; i < n; ++i) {
                 const float* r = wrec + i * kRec;
                 const BoxHead B = box_head(r);
                 float2 v = make_float2(0.f, 0.f);
-                if (active) v = sorted_in ? yin[(int64_t)(base + i) * A.C + c] : yin[(int64_t)c * A.Nsamp + B.perm];
+                if (active) {
+                    const int64_t vi = sorted_in ? (int64_t)(base + i) * A.C + c : (int64_t)c * A.Nsamp + B.perm;
+                    if (CS_INB(vi, (int64_t)A.C * A.Nsamp)) v = yin[vi];
+                }
                 const int dy = B.jy - cy, dx = B.jx - cx;
                 if ((unsigned)(dy + 1) > 2u || (unsigned)(dx + 1) > 2u) {   // not a step of -1, 0 or +1
 #pragma unroll
@@ -890,10 +917,11 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
                                     float2 old[kW];
 #pragma unroll
                                     for (int d = 0; d < kW; ++d)
-                                        if ((xin_m >> d) & 1) old[d] = tgt[W.zoff[p] + W.yoff[R] + W.xoff[d]];
+                                        if (((xin_m >> d) & 1) && CS_INB(tbase + W.zoff[p] + W.yoff[R] + W.xoff[d], tlim))
+                                            old[d] = tgt[W.zoff[p] + W.yoff[R] + W.xoff[d]];
 #pragma unroll
                                     for (int d = 0; d < kW; ++d)
-                                        if ((xin_m >> d) & 1)
+                                        if (((xin_m >> d) & 1) && CS_INB(tbase + W.zoff[p] + W.yoff[R] + W.xoff[d], tlim))
                                             tgt[W.zoff[p] + W.yoff[R] + W.xoff[d]] =
                                                 make_float2(old[d].x + W.v[p][R][d].x, old[d].y + W.v[p][R][d].y);
                                 }
@@ -917,10 +945,11 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
                                     float2 old[kW];
 #pragma unroll
                                     for (int bb = 0; bb < kW; ++bb)
-                                        if ((yin_m >> bb) & 1) old[bb] = tgt[W.zoff[p] + W.yoff[bb] + W.xoff[R]];
+                                        if (((yin_m >> bb) & 1) && CS_INB(tbase + W.zoff[p] + W.yoff[bb] + W.xoff[R], tlim))
+                                            old[bb] = tgt[W.zoff[p] + W.yoff[bb] + W.xoff[R]];
 #pragma unroll
                                     for (int bb = 0; bb < kW; ++bb)
-                                        if ((yin_m >> bb) & 1)
+                                        if (((yin_m >> bb) & 1) && CS_INB(tbase + W.zoff[p] + W.yoff[bb] + W.xoff[R], tlim))
                                             tgt[W.zoff[p] + W.yoff[bb] + W.xoff[R]] =
                                                 make_float2(old[bb].x + W.v[p][bb][R].x, old[bb].y + W.v[p][bb][R].y);
                                 }
@@ -979,15 +1008,18 @@ __global__ void owner_reduce_kernel(OwnerArgs A, const GRed* __restrict__ reds) 
         const int cc = (int)(e % g);
         const int64_t v = e / g;
         const int lx = (int)(v % w[2]), ly = (int)((v / w[2]) % w[1]), lz = (int)(v / ((int64_t)w[2] * w[1]));
-        float2* dst = A.grid + (((int64_t)(o[0] + lz) * A.Gy + (o[1] + ly)) * A.Gx + (o[2] + lx)) * A.C + A.c0 + cc;
+        const int64_t di = (((int64_t)(o[0] + lz) * A.Gy + (o[1] + ly)) * A.Gx + (o[2] + lx)) * A.C + A.c0 + cc;
         const int64_t loc = (((int64_t)lz * A.wy + ly) * A.wx + lx) * g + cc;
-        float2 acc = *dst;
+        if (!CS_INB(di, (int64_t)A.Gz * A.Gy * A.Gx * A.C)) continue;
+        float2 acc = A.grid[di];
         for (int k = 0; k < rd.ns; ++k) {
-            const float2 q = A.part[(rd.s0 + k) * slot + loc];
+            const int64_t pi = (rd.s0 + k) * slot + loc;
+            if (!CS_INB(pi, (int64_t)A.nslots * slot)) continue;
+            const float2 q = A.part[pi];
             acc.x += q.x;
             acc.y += q.y;
         }
-        *dst = acc;
+        A.grid[di] = acc;
     }
 }
 
@@ -1089,6 +1121,7 @@ static cs_status launch_spread(const cs_plan* p, int ncoils, const float2* yin, 
     A.nitems = p->n_gitems;
     A.ranges = p->granges;
     A.part = p->gpart;
+    A.nslots = p->n_slots;
     A.wz = p->wmax[0];
     A.wy = p->wmax[1];
     A.wx = p->wmax[2];
@@ -1253,6 +1286,8 @@ cs_status nufft_interp_sorted(const cs_plan* p, int ncoils, cudaStream_t st) {
 }
 
 // normal operator on the grid: ktmp = w^1/2 interp(grid) (sorted), then grid = spread(w^1/2 ktmp)
+CS_BOUNDS_READER(nufft_bounds_check)
+
 cs_status nufft_interp_spread(const cs_plan* p, int ncoils, cudaStream_t st) {
     CS_PROPAGATE(launch_interp(p, ncoils, OUT_SORTED, nullptr, p->ktmp, st));
     return nufft_spread(p, ncoils, nullptr, 1, st);

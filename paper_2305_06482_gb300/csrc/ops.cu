@@ -310,7 +310,11 @@ cs_status cs_profile_read(int stage, double* total_ms, long long* launches) {
     *launches = g_prof_n[stage];
     return CS_OK;
 }
-const char* cs_version(void) { return "coilsketch-gb300 0.1 (sm_103a)"; }
+#ifdef CS_CHECK_BOUNDS
+const char* cs_version(void) { return "coilsketch-gb300 0.2 (sm_103a, bounds-checked)"; }
+#else
+const char* cs_version(void) { return "coilsketch-gb300 0.2 (sm_103a)"; }
+#endif
 
 cs_status cs_plan_create(const cs_geom* g, void* stream, cs_plan** out) {
     clear_error();

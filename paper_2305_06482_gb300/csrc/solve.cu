@@ -1553,6 +1553,7 @@ static cs_status recon_finish(cs_plan* p, const cs_solve_params* sp, cudaStream_
     }
     CS_PROPAGATE(fft_check_and_clear());
     CS_PROPAGATE(tc_check_and_clear());
+    CS_PROPAGATE(bounds_check_all());
     CS_REQUIRE(!h.nonfinite, CS_ERR_NONFINITE, "a solver reduction produced a non-finite value");
     return CS_OK;
 }
@@ -1746,6 +1747,38 @@ cs_status recon_solve_batched(int nslices, const cs_batch_item* items, const cs_
 }
 
 // ---------------------------------------------------------------------------------------------
+// Pseudo-replica noise statistics (the inverse g-factor of Sec. 3.2): per pixel, in FP64 and in
+// replica order, std = sqrt(mean_k |x_k - mean|^2); 1/g = std_full sqrt(R) / std_R.
+__device__ __forceinline__ double replica_std(const float2* __restrict__ x, int K, int64_t D, int64_t i) {
+    double mr = 0, mi = 0;
+    for (int k = 0; k < K; ++k) {
+        const float2 v = x[(int64_t)k * D + i];
+        mr += v.x;
+        mi += v.y;
+    }
+    mr /= K;
+    mi /= K;
+    double acc = 0;
+    for (int k = 0; k < K; ++k) {
+        const float2 v = x[(int64_t)k * D + i];
+        const double dr = v.x - mr, di = v.y - mi;
+        acc += dr * dr + di * di;
+    }
+    return sqrt(acc / K);
+}
+
+__global__ void noise_std_kernel(const float2* __restrict__ x, int K, int64_t D, float* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < D; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)replica_std(x, K, D, i);
+}
+
+__global__ void inv_gfactor_kernel(const float2* __restrict__ xr, const float2* __restrict__ xf, int K, int64_t D,
+                                   double sqrtR, float* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < D; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)(replica_std(xf, K, D, i) * sqrtR / replica_std(xr, K, D, i));
+}
+
+// ---------------------------------------------------------------------------------------------
 // Sub-problem pieces for callers that drive Algorithm 1 themselves (e.g. with a warm start).
 
 static cs_status make_ctx(cs_plan* p, float lambda, int levels, cudaStream_t st, Ctx& c, SolverWS*& ws, int C, int S, int K) {
@@ -1860,6 +1893,27 @@ cs_status cs_power_iteration(const cs_plan* plan, const float* v0, const float* 
     CS_TRY_CUDA(cudaMemcpyAsync(&h, ws->sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
     CS_TRY_CUDA(cudaStreamSynchronize(st));
     *L = h.L;
+    return CS_OK;
+}
+
+cs_status cs_noise_std(const float* recons, int K, int64_t D, float* std_out, void* stream) {
+    clear_error();
+    CS_REQUIRE(recons && std_out && K >= 1 && D >= 0, CS_ERR_INVALID_ARG, "bad noise_std arguments");
+    if (D == 0) return CS_OK;
+    noise_std_kernel<<<vec_grid(D), kRedThreads, 0, (cudaStream_t)stream>>>((const float2*)recons, K, D, std_out);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+cs_status cs_inverse_gfactor(const float* recons_R, const float* recons_full, int K, int64_t D, float R, float* inv_g,
+                             void* stream) {
+    clear_error();
+    CS_REQUIRE(recons_R && recons_full && inv_g && K >= 1 && D >= 0 && R > 0, CS_ERR_INVALID_ARG,
+               "bad inverse g-factor arguments");
+    if (D == 0) return CS_OK;
+    inv_gfactor_kernel<<<vec_grid(D), kRedThreads, 0, (cudaStream_t)stream>>>(
+        (const float2*)recons_R, (const float2*)recons_full, K, D, std::sqrt((double)R), inv_g);
+    CS_LAUNCH_CHECK();
     return CS_OK;
 }
 

@@ -9,11 +9,11 @@ The noise realisations are inputs (device tensors [replicas][C][N]); the solver 
 """
 from __future__ import annotations
 
-import math
+import ctypes
 
 import torch
 
-from . import CARTESIAN, REG_L2, Plan, SolveParams, recon_solve_batched
+from . import CARTESIAN, REG_L2, Plan, SolveParams, _check, _ptr, _stream, lib, recon_solve_batched
 
 
 def replicas(y, noise):
@@ -32,12 +32,20 @@ def replica_reconstructions(shape, maps, mask_idx, ys, lam, params: SolveParams,
     return torch.stack(xs), plans
 
 
-def noise_std(recons):
-    """Per-pixel sqrt(mean_k |x_k - mean|^2) over the first axis."""
-    mu = recons.mean(dim=0, keepdim=True)
-    return torch.sqrt(torch.mean((recons - mu).abs() ** 2, dim=0))
+def noise_std(recons, stream=None):
+    """Per-pixel sqrt(mean_k |x_k - mean|^2) over the first axis (library kernel, FP64 per pixel)."""
+    K = recons.shape[0]
+    D = recons[0].numel()
+    out = torch.empty(recons.shape[1:], dtype=torch.float32, device=recons.device)
+    _check(lib().cs_noise_std(_ptr(recons), K, D, _ptr(out), _stream(stream)))
+    return out
 
 
-def inverse_gfactor(recons_R, recons_full, R):
-    """1/g = std_full sqrt(R) / std_R."""
-    return noise_std(recons_full) * math.sqrt(R) / noise_std(recons_R)
+def inverse_gfactor(recons_R, recons_full, R, stream=None):
+    """1/g = std_full sqrt(R) / std_R (library kernel)."""
+    K = recons_R.shape[0]
+    D = recons_R[0].numel()
+    out = torch.empty(recons_R.shape[1:], dtype=torch.float32, device=recons_R.device)
+    _check(lib().cs_inverse_gfactor(_ptr(recons_R.contiguous()), _ptr(recons_full.contiguous()), K, D,
+                                    ctypes.c_float(R), _ptr(out), _stream(stream)))
+    return out

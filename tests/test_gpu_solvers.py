@@ -319,3 +319,33 @@ def test_trace_records_match_the_oracle():
     want = [np.linalg.norm(hi[k] - ref) ** 2 / np.linalg.norm(ref) ** 2 for k in range(Kp)]
     assert np.allclose(st["trace"][:, cs.TRACE_DIST2], want, rtol=1e-5)
     assert np.all(st["trace"][:, cs.TRACE_GRAD2] > 0)
+
+
+def test_batched_slices_of_the_2d_workload_match_the_oracle():
+    """The batched 2D workload's slice shapes against the FP64 oracle: one recon_solve_batched call
+    (one captured graph) with 288^2, 352^2 and 384^2 slices, 16 coils, line masks R = 6 with 24
+    centre lines, l1-db4 lambda 5e-3 by FISTA, m = 6 = 3 PCA + 3 Gaussian; every slice's final
+    image within 1e-4 of oracle.solvers.coil_sketching on the same inputs and sketch blocks."""
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    C, V, S, T, K, lam, seed = 16, 3, 3, 4, 8, 5e-3, 9
+    sk = philox.sketch_draw(seed, 0, T, C, V, S).astype(np.float64)
+    items, refs = [], []
+    for k, n in enumerate((288, 352, 384)):
+        shape = (n, n)
+        mask = synthdata.line_mask(shape, R=6.0, centre_lines=24, seed=60 + k)
+        idx = fourier.mask_indices(mask)
+        maps = synthdata.coil_maps(shape, C)
+        y = fourier.cartesian_fwd(synthdata.phantom(shape, seed=70 + k), maps, idx)
+        y = y + synthdata.complex_noise(y.shape, 1e-3 * np.abs(y).max(), seed=75 + k)
+        v0 = synthdata.random_complex(shape, 80 + k)
+        ops = lambda m, idx=idx: (lambda v: fourier.cartesian_fwd(v, m, idx), lambda r: fourier.cartesian_adj(r, m, idx))
+        x_ref, _ = solvers.coil_sketching(ops, maps, y, lam, "l1wav", sk, V=V, K=K, power_v0=v0, levels=4)
+        refs.append(x_ref)
+        plan = cs.Plan(cs.CARTESIAN, shape, C, mask_idx=t(idx, np.int32))
+        items.append(dict(plan=plan, y=t(y), maps=t(maps), power_v0=t(v0)))
+    xs, sts = cs.recon_solve_batched(items, lam, cs.REG_L1_WAVELET,
+                                     cs.SolveParams(T=T, K=K, V=V, S=S, seed=seed, use_graph=True), wavelet_levels=4)
+    for x, r, st in zip(xs, refs, sts):
+        assert nrmse(h(x), r) < 1e-4
+        assert st["graph_used"] == 1
