@@ -123,6 +123,25 @@ cs_status cs_plan_set_gridding(cs_plan* plan, int interp_coils, int interp_chunk
                                int spread_chunk);
 cs_status cs_plan_autotune(cs_plan* plan, int ncoils, int reps, int* choice, float* ms, void* stream);
 
+/* Tile sizes of a non-Cartesian plan's binning (Sec. 2.1 gridding; the sort order of the samples,
+ * not the operator).  cs_plan_set_tile: tile[ndim] (z, y, x order; each >= 4, or the grid size;
+ * larger values are clipped to the grid) re-bins the plan exactly as cs_plan_create would with that
+ * `tile`: same keys, same stable order.  The per-sample records are rewritten in place, the
+ * deterministic-spreading work items rebuilt if the plan has them.  Results of every operator are
+ * equal up to rounding order; cs_plan_binning returns the new order.  Synchronous (waits for
+ * `stream`); CS_ERR_UNSUPPORTED_SIZE for more than 49152 tiles (the plan is unchanged); after
+ * any other error the plan must be destroyed.
+ * cs_plan_autotune_tile: re-bins the plan with every cubic candidate cand[ncand] (each >= 4,
+ * ncand <= 16), times the interpolation plus the spreading of `ncoils` coils (reps timed rounds
+ * after one untimed, CUDA events on `stream`, the plan's scratch buffers overwritten) and leaves
+ * the plan binned with the fastest; *best (nullable) receives it and ms[ncand] (nullable) each
+ * candidate's ms per round.  Synchronous.
+ * Changing the tiles, the gridding parameters or the spreading mode invalidates the CUDA graphs
+ * that recon_solve / recon_solve_batched cached for the plan (they are captured again). */
+cs_status cs_plan_set_tile(cs_plan* plan, const int* tile, void* stream);
+cs_status cs_plan_autotune_tile(cs_plan* plan, int ncoils, int reps, const int* cand, int ncand, int* best,
+                                float* ms, void* stream);
+
 /* Spreading mode of a non-Cartesian plan (the adjoint's first step, Sec. 2.1 gridding).
  * on = 0 (default): producer-computes - one warp per run of sorted samples, rows, columns and
  *   planes leaving its sliding window added to the grid with atomic adds; fastest, results equal

@@ -84,7 +84,7 @@ EXPORTED = [
     "cs_nn_maxpool2", "cs_nn_maxpool2_bwd", "cs_nn_upconv2", "cs_nn_upconv2_bwd", "cs_nn_slice",
     "ws_net_create", "ws_net_destroy", "ws_net_infer", "ws_net_train_step", "ws_net_param", "ws_net_save",
     "ws_net_load", "cs_crop3d", "cs_wait_selftest", "cs_plan_set_gridding", "cs_plan_autotune",
-    "cs_plan_set_deterministic", "cs_noise_std", "cs_inverse_gfactor",
+    "cs_plan_set_deterministic", "cs_noise_std", "cs_inverse_gfactor", "cs_plan_set_tile", "cs_plan_autotune_tile",
 ]
 STAGES = {"spread": 0, "interp": 1, "fft_plain": 2, "expand": 3, "reduce": 4}
 
@@ -141,6 +141,7 @@ def lib():
             "cs_crop3d": ([vp, vp, vp, vp, vp, vp], i), "cs_wait_selftest": ([i, i64, vp], i),
             "cs_plan_set_gridding": ([vp, i, i, i, i], i), "cs_plan_autotune": ([vp, i, i, vp, vp, vp], i),
             "cs_plan_set_deterministic": ([vp, i, i], i),
+            "cs_plan_set_tile": ([vp, vp, vp], i), "cs_plan_autotune_tile": ([vp, i, i, vp, i, vp, vp, vp], i),
             "cs_noise_std": ([vp, i, i64, vp, vp], i), "cs_inverse_gfactor": ([vp, vp, i, i64, f, vp, vp], i),
         }
         for name, (args, res) in sig.items():
@@ -244,6 +245,21 @@ class Plan:
         ms = (ctypes.c_float * 4)()
         _check(lib().cs_plan_autotune(self._h, ncoils, reps, choice, ms, _stream(stream)))
         return tuple(choice), tuple(float(v) for v in ms)
+
+    def set_tile(self, tile, stream=None):
+        """Re-bin a non-Cartesian plan for new tile sizes (one per axis, z y x order)."""
+        t = (ctypes.c_int * len(tile))(*[int(v) for v in tile])
+        _check(lib().cs_plan_set_tile(self._h, t, _stream(stream)))
+
+    def autotune_tile(self, ncoils, candidates=(8, 16, 32), reps=3, stream=None):
+        """Time interpolation + spreading of `ncoils` coils for each cubic tile candidate and keep
+        the fastest; returns (best tile, ms per candidate)."""
+        cand = (ctypes.c_int * len(candidates))(*[int(v) for v in candidates])
+        ms = (ctypes.c_float * len(candidates))()
+        best = ctypes.c_int(0)
+        _check(lib().cs_plan_autotune_tile(self._h, ncoils, reps, cand, len(candidates), ctypes.byref(best), ms,
+                                           _stream(stream)))
+        return best.value, tuple(float(v) for v in ms)
 
     def binning(self):
         N = self.nsamples

@@ -191,6 +191,8 @@ struct cs_plan {
     int spread_coils = 16;        // coils per warp in spreading (8 or 16)
     float* phi = nullptr;         // KB kernel table [2049] on [0, 2]
     float* rec = nullptr;         // [N][16] per-sample gridding records (sorted order)
+    uint64_t layout_gen = 0;      // bumped when the sample order, the records or the gridding launch
+                                  // parameters change; part of every captured graph's signature
 
     // workspace (per coil up to max_coils)
     float2* bufA = nullptr;       // grid-sized per coil   [max_coils][G] (also the first-pass buffer)
@@ -209,7 +211,13 @@ cs_status fft_to_image(const cs_plan* p, const float2* maps_v, int V, const floa
                        float2* x, int accumulate, const float2* addv, float lambda, cudaStream_t st);
 
 // NUFFT binning / interpolation / spreading (nufft.cu)
-cs_status nufft_bin(cs_plan* p, const float* traj, const float* dcf, cudaStream_t st);
+// tile sizes (per axis z, y, x; validated) -> tile, ntiles, wmax, ntiles_total
+cs_status nufft_set_tiles(cs_plan* p, const int* tile3);
+// binning from the user's trajectory (from_grid = 0: coords = traj [N][ndim], w = dcf) or from
+// grid coordinates in user order (from_grid = 1: coords [N][3], w = sqrt(dcf))
+cs_status nufft_bin(cs_plan* p, const float* coords, const float* w, int from_grid, cudaStream_t st);
+// re-bins a non-Cartesian plan for new tile sizes (records rewritten in place)
+cs_status nufft_retile(cs_plan* p, const int* tile3, cudaStream_t st);
 cs_status nufft_records(cs_plan* p, cudaStream_t st);
 cs_status nufft_owner_build(cs_plan* p);   // spreading work items from the class offsets (synchronous)
 void nufft_owner_free(cs_plan* p);

@@ -42,9 +42,11 @@ __device__ __forceinline__ void tile_of(int jw, int G, int T, int nt, int* t, in
     *width = (tt == nt - 1) ? G - tt * T : T;
 }
 
-__global__ void bin_keys_kernel(const float* __restrict__ traj, int64_t N, int nd, int3 G, int3 T, int3 nt,
-                                float* __restrict__ gout, int32_t* __restrict__ j0out, int32_t* __restrict__ tkey,
-                                int32_t* __restrict__ ckey) {
+// coords: the trajectory [N][nd] in cycles/pixel (from_grid = 0) or grid coordinates [N][3] in
+// user order (from_grid = 1, as a plan stores them)
+__global__ void bin_keys_kernel(const float* __restrict__ coords, int from_grid, int64_t N, int nd, int3 G, int3 T,
+                                int3 nt, float* __restrict__ gout, int32_t* __restrict__ j0out,
+                                int32_t* __restrict__ tkey, int32_t* __restrict__ ckey) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     int Gs[3] = {G.x, G.y, G.z}, Ts[3] = {T.x, T.y, T.z}, nts[3] = {nt.x, nt.y, nt.z};
@@ -55,9 +57,13 @@ __global__ void bin_keys_kernel(const float* __restrict__ traj, int64_t N, int n
         float g = 0.f;
         if (ax >= 3 - nd) {
             const int a = ax - (3 - nd);
-            const float f = traj[i * nd + a];
-            const float Gf = (float)Gs[ax];
-            g = __fmaf_rn(f, Gf, 0.5f * Gf);
+            if (from_grid) {
+                g = coords[i * 3 + ax];
+            } else {
+                const float f = coords[i * nd + a];
+                const float Gf = (float)Gs[ax];
+                g = __fmaf_rn(f, Gf, 0.5f * Gf);
+            }
             jj = (int)floorf(g) - (kW / 2 - 1);
             j0out[i * nd + a] = jj;
         }
@@ -161,7 +167,7 @@ __global__ void gather_i32_kernel(const int32_t* __restrict__ src, const int32_t
 
 // final order: perm[pos] = sample; sorted grid coordinates, sqrt(dcf) and keys
 __global__ void bin_final_kernel(const int32_t* __restrict__ perm1, const int32_t* __restrict__ perm2,
-                                 const float* __restrict__ g, const float* __restrict__ dcf,
+                                 const float* __restrict__ g, const float* __restrict__ w, int w_is_sqrt,
                                  const int32_t* __restrict__ tkey, const int32_t* __restrict__ ckey, int64_t N,
                                  int32_t* __restrict__ perm, float* __restrict__ gs, float* __restrict__ ws,
                                  int32_t* __restrict__ skey) {
@@ -172,7 +178,7 @@ __global__ void bin_final_kernel(const int32_t* __restrict__ perm1, const int32_
     gs[pos * 3 + 0] = g[(int64_t)i * 3 + 0];
     gs[pos * 3 + 1] = g[(int64_t)i * 3 + 1];
     gs[pos * 3 + 2] = g[(int64_t)i * 3 + 2];
-    ws[pos] = sqrtf(dcf[i]);
+    ws[pos] = w_is_sqrt ? w[i] : sqrtf(w[i]);
     skey[pos] = tkey[i] * 8 + ckey[i];
 }
 
@@ -194,7 +200,47 @@ __global__ void tile_off_kernel(const int32_t* __restrict__ coff, int ntiles, in
     if (t <= ntiles) toff[t] = coff[(int64_t)t * 8];
 }
 
-cs_status nufft_bin(cs_plan* p, const float* traj, const float* dcf, cudaStream_t st) {
+// a plan's sorted grid coordinates and sqrt(dcf) back in user order (input of a re-binning)
+__global__ void unsort_kernel(const int32_t* __restrict__ perm, const float* __restrict__ gs,
+                              const float* __restrict__ ws, int64_t N, float* __restrict__ gu, float* __restrict__ wu) {
+    const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= N) return;
+    const int64_t i = perm[pos];
+    if (!CS_INB(i, N)) return;
+    gu[i * 3 + 0] = gs[pos * 3 + 0];
+    gu[i * 3 + 1] = gs[pos * 3 + 1];
+    gu[i * 3 + 2] = gs[pos * 3 + 2];
+    wu[i] = ws[pos];
+}
+
+cs_status nufft_set_tiles(cs_plan* p, const int* tile3) {
+    int t[3], nt[3], wm[3];
+    int64_t tot = 1;
+    const int nd = p->ndim;
+    for (int a = 0; a < 3; ++a) {
+        int v = (a >= 3 - nd) ? tile3[a] : 1;
+        if (v <= 0) v = 16;
+        v = std::min(v, p->grid[a]);
+        CS_REQUIRE(a < 3 - nd || v >= kW || v == p->grid[a], CS_ERR_UNSUPPORTED_SIZE,
+                   "tiles narrower than the kernel width (%d) are not supported", v);
+        t[a] = v;
+        const int rem = p->grid[a] % v;
+        // a remainder narrower than the kernel widens the last tile instead of forming its own
+        nt[a] = (rem > 0 && rem < kW && p->grid[a] >= v) ? p->grid[a] / v : (p->grid[a] + v - 1) / v;
+        wm[a] = std::max(v, p->grid[a] - (nt[a] - 1) * v);
+        tot *= nt[a];
+    }
+    CS_REQUIRE(tot <= 49152, CS_ERR_UNSUPPORTED_SIZE, "too many tiles (%lld); use a larger tile", (long long)tot);
+    for (int a = 0; a < 3; ++a) {
+        p->tile[a] = t[a];
+        p->ntiles[a] = nt[a];
+        p->wmax[a] = wm[a];
+    }
+    p->ntiles_total = tot;
+    return CS_OK;
+}
+
+cs_status nufft_bin(cs_plan* p, const float* coords, const float* w, int from_grid, cudaStream_t st) {
     const int64_t N = p->N;
     const int nd = p->ndim;
     const int ntiles = (int)p->ntiles_total;
@@ -241,7 +287,7 @@ cs_status nufft_bin(cs_plan* p, const float* traj, const float* dcf, cudaStream_
     const int3 T3 = make_int3(p->tile[0], p->tile[1], p->tile[2]);
     const int3 nt3 = make_int3(p->ntiles[0], p->ntiles[1], p->ntiles[2]);
     const unsigned nb = (unsigned)((N + 255) / 256);
-    bin_keys_kernel<<<nb, 256, 0, st>>>(traj, N, nd, G3, T3, nt3, g, p->j0, tkey, ckey);
+    bin_keys_kernel<<<nb, 256, 0, st>>>(coords, from_grid, N, nd, G3, T3, nt3, g, p->j0, tkey, ckey);
     BIN_TRY(cudaGetLastError());
     // one stable counting-sort pass: order[pos] = index of the entry at sorted position pos
     auto pass = [&](const int32_t* key, int nkeys, int32_t* order) -> cudaError_t {
@@ -261,7 +307,7 @@ cs_status nufft_bin(cs_plan* p, const float* traj, const float* dcf, cudaStream_
     gather_i32_kernel<<<nb, 256, 0, st>>>(tkey, perm1, N, key2);
     BIN_TRY(cudaGetLastError());
     BIN_TRY(pass(key2, ntiles, perm2));                              // then by tile (stable)
-    bin_final_kernel<<<nb, 256, 0, st>>>(perm1, perm2, g, dcf, tkey, ckey, N, p->perm, p->gsorted, p->wsorted, skey);
+    bin_final_kernel<<<nb, 256, 0, st>>>(perm1, perm2, g, w, from_grid, tkey, ckey, N, p->perm, p->gsorted, p->wsorted, skey);
     BIN_TRY(cudaGetLastError());
     lower_bound_kernel<<<(ntiles * 8 + 1 + 255) / 256, 256, 0, st>>>(skey, N, ntiles * 8, p->class_off);
     BIN_TRY(cudaGetLastError());
@@ -1258,8 +1304,48 @@ cs_status nufft_owner_build(cs_plan* p) {
     return CS_OK;
 }
 
+// Re-binning for new tile sizes: the plan's sorted grid coordinates and sqrt(dcf) go back to user
+// order and are binned again exactly as at plan creation (same keys, same stable order), the
+// records are rewritten in the same buffer, and the deterministic-spreading work items are rebuilt
+// if the plan has them.  Synchronous.  On an error after the first step the plan is unusable.
+cs_status nufft_retile(cs_plan* p, const int* tile3, cudaStream_t st) {
+    const int keep_t[3] = {p->tile[0], p->tile[1], p->tile[2]};
+    CS_PROPAGATE(nufft_set_tiles(p, tile3));
+    const int64_t N = p->N;
+    float *gu = nullptr, *wu = nullptr;
+    int32_t *toff = nullptr, *coff = nullptr;
+    cudaError_t e = cudaMalloc(&gu, sizeof(float) * 3 * N);
+    if (e == cudaSuccess) e = cudaMalloc(&wu, sizeof(float) * N);
+    if (e == cudaSuccess) e = cudaMalloc(&toff, sizeof(int32_t) * (p->ntiles_total + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&coff, sizeof(int32_t) * (p->ntiles_total * 8 + 1));
+    if (e != cudaSuccess) {
+        cudaFree(gu);
+        cudaFree(wu);
+        cudaFree(toff);
+        cudaFree(coff);
+        nufft_set_tiles(p, keep_t);   // the plan is unchanged
+        set_error("re-binning: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? CS_ERR_OOM : CS_ERR_CUDA;
+    }
+    CS_TRY_CUDA(cudaStreamSynchronize(st));    // nothing queued still reads the old order
+    unsort_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(p->perm, p->gsorted, p->wsorted, N, gu, wu);
+    cudaFree(p->tile_off);
+    cudaFree(p->class_off);
+    p->tile_off = toff;
+    p->class_off = coff;
+    cs_status rc = nufft_bin(p, gu, wu, 1, st);
+    cudaFree(gu);
+    cudaFree(wu);
+    CS_PROPAGATE(rc);
+    CS_PROPAGATE(nufft_records(p, st));
+    CS_TRY_CUDA(cudaStreamSynchronize(st));
+    if (p->gitems) CS_PROPAGATE(nufft_owner_build(p));
+    p->layout_gen++;
+    return CS_OK;
+}
+
 cs_status nufft_records(cs_plan* p, cudaStream_t st) {
-    CS_TRY_CUDA(cudaMalloc(&p->rec, sizeof(float) * kRec * (size_t)p->N));
+    if (!p->rec) CS_TRY_CUDA(cudaMalloc(&p->rec, sizeof(float) * kRec * (size_t)p->N));   // rewritten in place
     sample_record_kernel<<<(unsigned)((p->N + 255) / 256), 256, 0, st>>>(p->gsorted, p->wsorted, p->perm, p->phi, p->N,
                                                                       p->ndim, p->grid[0], p->grid[1], p->grid[2], p->rec);
     CS_LAUNCH_CHECK();

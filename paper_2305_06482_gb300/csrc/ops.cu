@@ -228,19 +228,11 @@ static cs_status plan_build(cs_plan* p, const cs_geom* g, cudaStream_t st) {
     const int64_t bsz = (nd == 3) ? (int64_t)p->img[0] * p->grid[1] * p->grid[2] : p->G;
     CS_TRY_CUDA(cudaMalloc(&p->bufB, sizeof(float2) * C * bsz));
     CS_TRY_CUDA(cudaMalloc(&p->ktmp, sizeof(float2) * C * p->N));
-    for (int a = 0; a < 3; ++a) {
-        int t = (a >= 3 - nd) ? g->tile[a - (3 - nd)] : 1;
-        if (t <= 0) t = 16;
-        t = std::min(t, p->grid[a]);
-        CS_REQUIRE(a < 3 - nd || t >= 4 || t == p->grid[a], CS_ERR_UNSUPPORTED_SIZE,
-                   "tiles narrower than the kernel width (%d) are not supported", t);
-        p->tile[a] = t;
-        const int rem = p->grid[a] % t;
-        // a remainder narrower than the kernel widens the last tile instead of forming its own
-        p->ntiles[a] = (rem > 0 && rem < 4 && p->grid[a] >= t) ? p->grid[a] / t : (p->grid[a] + t - 1) / t;
-        p->wmax[a] = std::max(t, p->grid[a] - (p->ntiles[a] - 1) * t);
+    {
+        int t3[3] = {1, 1, 1};
+        for (int a = 3 - nd; a < 3; ++a) t3[a] = g->tile[a - (3 - nd)];
+        CS_PROPAGATE(nufft_set_tiles(p, t3));
     }
-    p->ntiles_total = (int64_t)p->ntiles[0] * p->ntiles[1] * p->ntiles[2];
     p->spread_chunk = 64;
     p->interp_chunk = 64;
     // tuning knobs (coils per warp of the gridding kernels, samples per warp)
@@ -266,7 +258,7 @@ static cs_status plan_build(cs_plan* p, const cs_geom* g, cudaStream_t st) {
     CS_TRY_CUDA(cudaMalloc(&p->j0, sizeof(int32_t) * nd * p->N));
     CS_TRY_CUDA(cudaMalloc(&p->tile_off, sizeof(int32_t) * (p->ntiles_total + 1)));
     CS_TRY_CUDA(cudaMalloc(&p->class_off, sizeof(int32_t) * (p->ntiles_total * 8 + 1)));
-    CS_PROPAGATE(nufft_bin(p, g->traj, g->dcf, st));
+    CS_PROPAGATE(nufft_bin(p, g->traj, g->dcf, 0, st));
     CS_PROPAGATE(nufft_records(p, st));
     CS_TRY_CUDA(cudaStreamSynchronize(st));
     return CS_OK;
@@ -430,6 +422,7 @@ cs_status cs_plan_set_gridding(cs_plan* p, int interp_coils, int interp_chunk, i
     p->interp_chunk = interp_chunk;
     p->spread_coils = spread_coils;
     p->spread_chunk = spread_chunk;
+    p->layout_gen++;
     return CS_OK;
 }
 
@@ -446,6 +439,7 @@ cs_status cs_plan_set_deterministic(cs_plan* p, int on, int item_visits) {
     }
     p->owner_item = q;
     p->deterministic = on;
+    p->layout_gen++;
     return CS_OK;
 }
 
@@ -514,6 +508,7 @@ cs_status cs_plan_autotune(cs_plan* p, int ncoils, int reps, int* choice, float*
         p->interp_chunk = bi_k;
         p->spread_coils = bs_c;
         p->spread_chunk = bs_k;
+        p->layout_gen++;
         if (rc != CS_OK) return rc;
     }
     if (choice) {
@@ -528,6 +523,71 @@ cs_status cs_plan_autotune(cs_plan* p, int ncoils, int reps, int* choice, float*
         ms[2] = def_i;
         ms[3] = def_s;
     }
+    return CS_OK;
+}
+
+cs_status cs_plan_set_tile(cs_plan* p, const int* tile, void* stream) {
+    clear_error();
+    CS_REQUIRE(p && tile, CS_ERR_INVALID_ARG, "null argument");
+    CS_REQUIRE(p->kind == CS_NONCARTESIAN, CS_ERR_INVALID_ARG, "needs a non-Cartesian plan");
+    int t3[3] = {1, 1, 1};
+    for (int a = 3 - p->ndim; a < 3; ++a) {
+        t3[a] = tile[a - (3 - p->ndim)];
+        CS_REQUIRE(t3[a] >= 1, CS_ERR_INVALID_ARG, "tile sizes must be positive");
+    }
+    return nufft_retile(p, t3, (cudaStream_t)stream);
+}
+
+// Times interpolation + spreading of `ncoils` coils for every cubic tile candidate (the plan is
+// re-binned for each) and leaves the plan binned with the fastest.
+cs_status cs_plan_autotune_tile(cs_plan* p, int ncoils, int reps, const int* cand, int ncand, int* best, float* ms,
+                                void* stream) {
+    clear_error();
+    CS_REQUIRE(p && cand && ncand >= 1 && ncand <= 16 && ncoils >= 1 && ncoils <= p->max_coils && reps >= 1 &&
+                   reps <= 100,
+               CS_ERR_INVALID_ARG, "bad tile autotune arguments");
+    CS_REQUIRE(p->kind == CS_NONCARTESIAN, CS_ERR_INVALID_ARG, "needs a non-Cartesian plan");
+    for (int i = 0; i < ncand; ++i) CS_REQUIRE(cand[i] >= 4, CS_ERR_INVALID_ARG, "tile candidates must be >= 4");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    CS_TRY_CUDA(cudaEventCreate(&e0));
+    CS_TRY_CUDA(cudaEventCreate(&e1));
+    cs_status rc = CS_OK;
+    int bi = -1;
+    float bt = 0.f;
+    auto timed = [&](float& out) -> cs_status {
+        for (int r = 0; r <= reps; ++r) {
+            if (r == 1) CS_TRY_CUDA(cudaEventRecord(e0, st));
+            CS_PROPAGATE(nufft_interp_sorted(p, ncoils, st));
+            CS_PROPAGATE(nufft_spread(p, ncoils, nullptr, 1, st));
+        }
+        CS_TRY_CUDA(cudaEventRecord(e1, st));
+        CS_TRY_CUDA(cudaEventSynchronize(e1));
+        CS_TRY_CUDA(cudaEventElapsedTime(&out, e0, e1));
+        out /= reps;
+        return CS_OK;
+    };
+    for (int i = 0; i < ncand && rc == CS_OK; ++i) {
+        const int t3[3] = {cand[i], cand[i], cand[i]};
+        rc = nufft_retile(p, t3, st);
+        float t = 0.f;
+        if (rc == CS_OK) rc = timed(t);
+        if (rc == CS_OK) {
+            if (ms) ms[i] = t;
+            if (bi < 0 || t < bt) {
+                bi = i;
+                bt = t;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != CS_OK) return rc;
+    if (bi != ncand - 1) {
+        const int t3[3] = {cand[bi], cand[bi], cand[bi]};
+        CS_PROPAGATE(nufft_retile(p, t3, st));
+    }
+    if (best) *best = cand[bi];
     return CS_OK;
 }
 

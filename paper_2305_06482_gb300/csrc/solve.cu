@@ -1268,6 +1268,7 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
         sig = fnv(sig, tvf, sizeof(tvf));
     }
     sig = fnv(sig, &sp->seed, sizeof(uint64_t));
+    sig = fnv(sig, &p->layout_gen, sizeof(uint64_t));     // sample order, records, gridding launches
     {
         const void* tp[] = {sp->warm, sp->x_ref};
         const int ti[] = {(int)tracing, (int)trace_obj};
@@ -1633,6 +1634,7 @@ static cs_status recon_batched_impl(int n, const cs_batch_item* items, const cs_
         uint64_t sig = 1469598103934665603ull;
         sig = fnv(sig, items, sizeof(cs_batch_item) * n);
         sig = fnv(sig, sp, sizeof(cs_solve_params));
+        for (int i = 0; i < n; ++i) sig = fnv(sig, &items[i].plan->layout_gen, sizeof(uint64_t));
         if (!bc.gexec || bc.sig != sig) {
             if (bc.gexec) cudaGraphExecDestroy(bc.gexec);
             bc.gexec = nullptr;

@@ -1,10 +1,11 @@
 """Micro-benchmarks of single operators on synthetic inputs (CUDA-event timing on the current
 stream), for profiling individual kernels with small launch counts.
 
-  python -m paper_2305_06482_gb300.microbench nufft  [--config cones3d_128|cones3d_large] [--warmup W] [--iters N] [--autotune]
+  python -m paper_2305_06482_gb300.microbench nufft  [--config cones3d_128|cones3d_large] [--warmup W] [--iters N] [--autotune] [--autotune-tile]
       multicoil NUFFT forward (sense_fwd) and adjoint (sense_adj), all coils (optionally after
-      cs_plan_autotune has chosen the gridding launch parameters for all coils)
-  python -m paper_2305_06482_gb300.microbench normal [--config cones3d_128|cones3d_large] [--warmup W] [--iters N]
+      cs_plan_autotune_tile has chosen the binning tile among 8, 12, 16, 24, 32 and / or
+      cs_plan_autotune the gridding launch parameters for all coils)
+  python -m paper_2305_06482_gb300.microbench normal [--config cones3d_128|cones3d_large] [--warmup W] [--iters N] [--autotune-tile]
       sketched normal operator A_S^H A_S v + lambda v with V = 5 unsketched and S = 5 sketched coils
       (the inner-iteration operator of the sketched sub-problem), with the per-stage device times
   python -m paper_2305_06482_gb300.microbench tv [--config cones3d_128|cones3d_large] [--iters N]
@@ -77,6 +78,15 @@ def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
+TILE_CANDIDATES = (8, 12, 16, 24, 32)
+
+
+def _tile_tune(plan, C):
+    best, ms = plan.autotune_tile(C, TILE_CANDIDATES)
+    print(f"tile autotune for {C} coils (interp + spread ms per round): "
+          + ", ".join(f"{t}^3 {m:.3f}" for t, m in zip(TILE_CANDIDATES, ms)) + f" -> {best}^3", flush=True)
+
+
 def nufft(args):
     cfg = CONFIGS[args.config]
     dev = torch.device("cuda")
@@ -89,6 +99,8 @@ def nufft(args):
     maps = synthdata.coil_maps_torch(img, C, device=dev)
     y = torch.empty((C, traj.shape[0]), dtype=torch.complex64, device=dev)
     xa = torch.empty(img, dtype=torch.complex64, device=dev)
+    if args.autotune_tile:
+        _tile_tune(plan, C)
     if args.autotune:
         choice, ms = plan.autotune(C)
         print(f"autotune for {C} coils: interp {choice[0]} coils x {choice[1]} samples per warp "
@@ -129,6 +141,8 @@ def normal(args):
     maps = synthdata.coil_maps_torch(img, V + S, device=dev)
     mv, ms = maps[:V].contiguous(), maps[V:].contiguous()
     z = torch.empty(img, dtype=torch.complex64, device=dev)
+    if args.autotune_tile:
+        _tile_tune(plan, V + S)
     for _ in range(args.warmup):
         cs.sketched_normal_apply(plan, v, mv, ms, 1e-3, z)
     torch.cuda.synchronize()
@@ -591,6 +605,7 @@ def main():
     ap.add_argument("--voxels", type=int, default=160 * 256 * 256)
     ap.add_argument("--phantoms", type=int, default=4)
     ap.add_argument("--autotune", action="store_true", help="nufft: tune the gridding launches first")
+    ap.add_argument("--autotune-tile", action="store_true", help="nufft, normal: tune the binning tile first")
     ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--outer", type=int, default=6, help="warmtrain: outer iterations per phantom")
     ap.add_argument("--K", type=int, default=4, help="warmtrain: inner FISTA iterations")

@@ -252,3 +252,56 @@ def test_deterministic_spreading_is_bit_reproducible(img, grid, tile, item):
     z1 = h(cs.sketched_normal_apply(plan, t(x), t(maps[:2]), t(maps[2:5]), 1e-3))
     z2 = h(cs.sketched_normal_apply(plan, t(x), t(maps[:2]), t(maps[2:5]), 1e-3))
     assert np.array_equal(z1.view(np.uint64), z2.view(np.uint64))
+
+
+def test_retile_matches_a_fresh_plan_and_the_oracle():
+    """cs_plan_set_tile re-bins a plan exactly as a plan created with those tiles (same order, bit
+    for bit, against the CPU restatement of the sort); the operators stay within the FP64 oracle's
+    tolerance for every tile; the tile autotuner returns one of its candidates and leaves the plan
+    binned with it; deterministic spreading stays bit-reproducible after a re-binning; a solve with
+    a captured graph, re-run after the tiles change, is captured again and agrees with the first."""
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    img, grid, C = (32, 32, 32), (40, 40, 40), 5
+    traj, dcf, maps, x = _nufft_case(img, grid, C, 300, 128, seed=4)
+    op = nufft.Plan(traj, img, grid)
+    yy = synthdata.random_complex((C, traj.shape[0]), 12)
+    adj_ref = nufft.sense_adj(op, yy, maps, dcf)
+    fwd_ref = nufft.sense_fwd(op, x, maps, dcf)
+    plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=t(traj), dcf=t(dcf), grid=grid)
+    j0_ref = binning.kernel_box_start(binning.grid_coords(traj, grid))
+    for tile in ((8, 8, 8), (16, 8, 32), (40, 40, 40), (4, 12, 20), (16, 16, 16)):
+        plan.set_tile(tile)
+        perm, off, j0, nt = plan.binning()
+        perm_ref, off_ref, ntr = binning.sample_order(j0_ref, grid, tile)
+        assert tuple(nt) == tuple(int(v) for v in ntr), tile
+        assert np.array_equal(perm.cpu().numpy(), perm_ref), tile
+        assert np.array_equal(off.cpu().numpy(), off_ref), tile
+        assert np.array_equal(j0.cpu().numpy(), j0_ref), tile
+        assert nrmse(h(cs.sense_adj(plan, t(yy), t(maps))), adj_ref) < TOL, tile
+        assert nrmse(h(cs.sense_fwd(plan, t(x), t(maps))), fwd_ref) < TOL, tile
+    best, ms = plan.autotune_tile(C, candidates=(8, 16, 32), reps=2)
+    assert best in (8, 16, 32) and len(ms) == 3 and all(v > 0 for v in ms)
+    assert ms[(8, 16, 32).index(best)] == min(ms)
+    perm, off, _, nt = plan.binning()
+    perm_ref, off_ref, ntr = binning.sample_order(j0_ref, grid, (best,) * 3)
+    assert np.array_equal(perm.cpu().numpy(), perm_ref) and np.array_equal(off.cpu().numpy(), off_ref)
+    plan.set_deterministic(True, 256)
+    plan.set_tile((8, 16, 8))
+    a1 = h(cs.sense_adj(plan, t(yy), t(maps)))
+    a2 = h(cs.sense_adj(plan, t(yy), t(maps)))
+    assert np.array_equal(a1.view(np.uint64), a2.view(np.uint64))
+    assert nrmse(a1, adj_ref) < TOL
+    plan.set_deterministic(False)
+    y = t(nufft.sense_fwd(op, synthdata.phantom(img, seed=8), maps, dcf))
+    res = []
+    for tile in ((16, 16, 16), (8, 8, 8)):
+        plan.set_tile(tile)
+        xs, st = cs.recon_solve(plan, y, t(maps), 1e-3, cs.REG_L2,
+                                cs.SolveParams(T=2, K=3, V=2, S=2, seed=3, use_graph=True))
+        res.append(h(xs))
+    assert nrmse(res[1], res[0]) < 1e-4
+    with pytest.raises(cs.CoilSketchError):
+        plan.set_tile((2, 8, 8))                    # narrower than the kernel
+    with pytest.raises(cs.CoilSketchError):
+        plan.autotune_tile(C, candidates=(3,))
