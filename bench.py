@@ -47,6 +47,7 @@ WORKLOAD = dict(name="cones3d_large", img=(160, 256, 256), grid=(200, 320, 320),
 T_MEASURED = 9
 METRIC = "time-to-NRMSE 1e-3 per recon (s), sketched vs full-coil; NUFFT fwd+adj GB/s"
 WEIGHTS = os.path.join(ROOT, "paper_2305_06482_gb300", "weights", "unet_cones3d_large.bin")
+TILE_CANDIDATES = (16, 32, 64)   # binning tiles timed before the run (cs_plan_autotune_tile)
 
 
 def workload_desc(w):
@@ -296,6 +297,11 @@ def run_native(args, w, rank, world, local_rank):
     plan_s = time.perf_counter() - t_plan
     del traj_d, dcf_d
     y = cs.sense_fwd(plan, x_true, maps)
+    # binning tile tuned for the sketched operator's coil count (re-bins the plan; untimed, once per
+    # trajectory like the plan itself)
+    t_tile = time.perf_counter()
+    tile, tile_ms = plan.autotune_tile(w["V"] + w["S"], TILE_CANDIDATES, reps=3)
+    tile_s = time.perf_counter() - t_tile
     gen = torch.Generator(device=dev).manual_seed(seed + 3)
     sig = 1e-3 * y.abs().max().item()
     y += (sig / math.sqrt(2)) * torch.complex(torch.randn(y.shape, generator=gen, device=dev),
@@ -504,7 +510,9 @@ def run_native(args, w, rank, world, local_rank):
                "sketched_over_plain_time": (recon_s * world / plain_s) if (reached and k_star) else None,
                "legs": leg_out,
                "x_inf": f"plain full-coil FISTA, {w['ref_iters']} iterations ({ref_s:.1f} s untimed)",
-               "plan_s": plan_s, "setup_s": setup_s, "L_full": st_inf["L"], "e2e_steps": e2e_steps}
+               "plan_s": plan_s, "tile": tile, "tile_candidates_ms": dict(zip(map(str, TILE_CANDIDATES),
+                                                                             [round(v, 3) for v in tile_ms])),
+               "tile_tune_s": tile_s, "setup_s": setup_s, "L_full": st_inf["L"], "e2e_steps": e2e_steps}
         line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
@@ -517,11 +525,13 @@ def run_native(args, w, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-# DRAM bytes (read + write) over algorithmic bytes of one launch, measured with ncu on the 128^3
-# cones, 10-coil sketched normal operator (spread and interpolation: the whole launch; strided
-# passes: mean of the forward y and z passes; writes still dirty in L2 at kernel end are not
-# counted there).  Traffic grows in proportion to the algorithmic bytes, so the bench scales it.
-TRAFFIC_RATIO = {"spread": 1.043, "interp": 0.823, "fft_plain": 0.90}
+# DRAM bytes (read + write) over algorithmic bytes of one launch (the model of stage_bytes), measured
+# with ncu on the 128^3 cones, 10-coil sketched normal operator with 64^3 binning tiles (spread and
+# interpolation: the whole launch, whose DRAM bytes include the plan's 64-byte per-sample records
+# where the model counts the 16 bytes of trajectory and density; strided passes: mean of the
+# forward y and z passes; writes still dirty in L2 at kernel end are not counted there).  Traffic
+# grows in proportion to the algorithmic bytes, so the bench scales it.
+TRAFFIC_RATIO = {"spread": 1.303, "interp": 1.024, "fft_plain": 0.90}
 
 
 def stage_bytes(stage, w, T, K, m, steps):

@@ -1,11 +1,11 @@
 """Micro-benchmarks of single operators on synthetic inputs (CUDA-event timing on the current
 stream), for profiling individual kernels with small launch counts.
 
-  python -m paper_2305_06482_gb300.microbench nufft  [--config cones3d_128|cones3d_large] [--warmup W] [--iters N] [--autotune] [--autotune-tile]
+  python -m paper_2305_06482_gb300.microbench nufft  [--config cones3d_128|cones3d_large] [--warmup W] [--iters N] [--tile T] [--autotune] [--autotune-tile]
       multicoil NUFFT forward (sense_fwd) and adjoint (sense_adj), all coils (optionally after
       cs_plan_autotune_tile has chosen the binning tile among 8, 12, 16, 24, 32 and / or
       cs_plan_autotune the gridding launch parameters for all coils)
-  python -m paper_2305_06482_gb300.microbench normal [--config cones3d_128|cones3d_large] [--warmup W] [--iters N] [--autotune-tile]
+  python -m paper_2305_06482_gb300.microbench normal [--config cones3d_128|cones3d_large] [--warmup W] [--iters N] [--tile T] [--autotune-tile]
       sketched normal operator A_S^H A_S v + lambda v with V = 5 unsketched and S = 5 sketched coils
       (the inner-iteration operator of the sketched sub-problem), with the per-stage device times
   python -m paper_2305_06482_gb300.microbench tv [--config cones3d_128|cones3d_large] [--iters N]
@@ -35,6 +35,9 @@ stream), for profiling individual kernels with small launch counts.
       64 2D Cartesian slices of uneven size (256..384 squared), 16 coils, line mask R = 6 with
       24 centre lines, l1-db4 FISTA (lambda 5e-3), sketch m = 6 (3 PCA + 3 Gaussian), T = 10, K = 10:
       one slice after another vs all slices forked and joined vs all slices in one CUDA graph
+  python -m paper_2305_06482_gb300.microbench recon [--config cones3d_128|cones3d_large] [--outer T] [--K K] [--tile T]
+      one coil-sketched reconstruction in the benchmark's configuration (T outer x K inner FISTA,
+      m = 10, BF16-split maps), no reference solve: the kernel mix of the timed reconstruction
   python -m paper_2305_06482_gb300.microbench warmnet [--config cones3d_128|cones3d_large] [--iters N]
       the warm-start U-Net (16/32/64 channels): every 3x3x3 convolution alone on random inputs of
       its shape (BF16 implicit GEMM on the tensor cores), one whole inference on the image size of
@@ -81,10 +84,14 @@ def _events():
 TILE_CANDIDATES = (8, 12, 16, 24, 32)
 
 
-def _tile_tune(plan, C):
-    best, ms = plan.autotune_tile(C, TILE_CANDIDATES)
+def _tiles(args):
+    return tuple(int(v) for v in args.tiles.split(",")) if args.tiles else TILE_CANDIDATES
+
+
+def _tile_tune(plan, C, cands=TILE_CANDIDATES):
+    best, ms = plan.autotune_tile(C, cands)
     print(f"tile autotune for {C} coils (interp + spread ms per round): "
-          + ", ".join(f"{t}^3 {m:.3f}" for t, m in zip(TILE_CANDIDATES, ms)) + f" -> {best}^3", flush=True)
+          + ", ".join(f"{t}^3 {m:.3f}" for t, m in zip(cands, ms)) + f" -> {best}^3", flush=True)
 
 
 def nufft(args):
@@ -99,8 +106,10 @@ def nufft(args):
     maps = synthdata.coil_maps_torch(img, C, device=dev)
     y = torch.empty((C, traj.shape[0]), dtype=torch.complex64, device=dev)
     xa = torch.empty(img, dtype=torch.complex64, device=dev)
+    if args.tile:
+        plan.set_tile((args.tile,) * 3)
     if args.autotune_tile:
-        _tile_tune(plan, C)
+        _tile_tune(plan, C, _tiles(args))
     if args.autotune:
         choice, ms = plan.autotune(C)
         print(f"autotune for {C} coils: interp {choice[0]} coils x {choice[1]} samples per warp "
@@ -141,8 +150,10 @@ def normal(args):
     maps = synthdata.coil_maps_torch(img, V + S, device=dev)
     mv, ms = maps[:V].contiguous(), maps[V:].contiguous()
     z = torch.empty(img, dtype=torch.complex64, device=dev)
+    if args.tile:
+        plan.set_tile((args.tile,) * 3)
     if args.autotune_tile:
-        _tile_tune(plan, V + S)
+        _tile_tune(plan, V + S, _tiles(args))
     for _ in range(args.warmup):
         cs.sketched_normal_apply(plan, v, mv, ms, 1e-3, z)
     torch.cuda.synchronize()
@@ -592,10 +603,46 @@ def warmtrain(args):
               " ".join(f"{v:.3e}" for v in e) + f"; {ms:.0f} ms per reconstruction{extra}")
 
 
+def recon(args):
+    """One coil-sketched reconstruction in the benchmark's configuration (l1-db4 lambda 2e-3, 4
+    levels, FISTA, m = 10 = 5 PCA + 5 Gaussian, BF16-split sketched maps, noise 1e-3 max|y|) with
+    --outer T outer and --K inner iterations; no reference solve.  Every outer iteration runs the
+    same kernels, so a short run gives the kernel shares of the full reconstruction."""
+    import math
+    cfg = CONFIGS[args.config]
+    dev = torch.device("cuda")
+    img, grid, C = cfg["img"], cfg["grid"], cfg["nc"]
+    traj = synthdata.cones_trajectory(cfg["n_int"], 512)
+    dcf = synthdata.cones_dcf(traj, img, cfg["n_int"], 512)
+    plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=torch.from_numpy(traj).to(dev), dcf=torch.from_numpy(dcf).to(dev),
+                   grid=grid)
+    maps = synthdata.coil_maps_torch(img, C, device=dev)
+    y = cs.sense_fwd(plan, synthdata.phantom_torch(img, seed=1, device=dev), maps)
+    if args.tile:
+        plan.set_tile((args.tile,) * 3)
+    gen = torch.Generator(device=dev).manual_seed(4)
+    sig = 1e-3 * y.abs().max().item()
+    y += (sig / math.sqrt(2)) * torch.complex(torch.randn(y.shape, generator=gen, device=dev),
+                                              torch.randn(y.shape, generator=gen, device=dev))
+    v0 = synthdata.phantom_torch(img, seed=6, device=dev)
+    p = cs.SolveParams(T=args.outer, K=args.K, V=5, S=5, seed=5, power_v0=v0, precision=cs.PREC_BF16_SPLIT)
+    for _ in range(args.warmup):
+        cs.recon_solve(plan, y, maps, 2e-3, cs.REG_L1_WAVELET, p, wavelet_levels=4)
+    torch.cuda.synchronize()
+    n0 = cs.launch_count()
+    a, b = _events()
+    a.record()
+    _, st = cs.recon_solve(plan, y, maps, 2e-3, cs.REG_L1_WAVELET, p, wavelet_levels=4)
+    b.record()
+    torch.cuda.synchronize()
+    print(f"{args.config}: coil-sketched reconstruction T = {args.outer}, K = {args.K}: {a.elapsed_time(b):.1f} ms, "
+          f"{cs.launch_count() - n0} library kernel launches")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["nufft", "normal", "tv", "ablation", "gfactor", "compare", "sketch", "cart2d",
-                                     "batched", "warmnet", "warmtrain"])
+                                     "batched", "warmnet", "warmtrain", "recon"])
     ap.add_argument("--replicas", type=int, default=60)
     ap.add_argument("--seeds", type=int, default=16)
     ap.add_argument("--slices", type=int, default=64)
@@ -606,15 +653,18 @@ def main():
     ap.add_argument("--phantoms", type=int, default=4)
     ap.add_argument("--autotune", action="store_true", help="nufft: tune the gridding launches first")
     ap.add_argument("--autotune-tile", action="store_true", help="nufft, normal: tune the binning tile first")
+    ap.add_argument("--tiles", default="", help="tile candidates of --autotune-tile, comma-separated")
+    ap.add_argument("--tile", type=int, default=0, help="nufft, normal: binning tile (cubic; 0 = plan default)")
     ap.add_argument("--train-steps", type=int, default=300)
-    ap.add_argument("--outer", type=int, default=6, help="warmtrain: outer iterations per phantom")
-    ap.add_argument("--K", type=int, default=4, help="warmtrain: inner FISTA iterations")
+    ap.add_argument("--outer", type=int, default=6, help="warmtrain: outer iterations per phantom; recon: T")
+    ap.add_argument("--K", type=int, default=4, help="warmtrain, recon: inner FISTA iterations")
     ap.add_argument("--tight", type=int, default=40, help="warmtrain: FISTA iterations of a training target")
     ap.add_argument("--ref-iters", type=int, default=300, help="warmtrain: plain FISTA iterations of x_inf")
     ap.add_argument("--save", default="", help="warmtrain: write the trained network here")
     args = ap.parse_args()
     {"nufft": nufft, "normal": normal, "tv": tv, "ablation": ablation, "gfactor": gfactor, "compare": compare,
-     "sketch": sketch, "cart2d": cart2d, "batched": batched, "warmnet": warmnet, "warmtrain": warmtrain}[args.what](args)
+     "sketch": sketch, "cart2d": cart2d, "batched": batched, "warmnet": warmnet, "warmtrain": warmtrain,
+     "recon": recon}[args.what](args)
 
 
 if __name__ == "__main__":
