@@ -256,7 +256,8 @@ def legs(w, have_weights):
     m = w["V"] + w["S"]
     out = [("configured", dict(V=w["V"], S=w["S"], dist=GAUSSIAN, K=w["K"])),
            ("paper_design_rademacher_V9_S1", dict(V=m - 1, S=1, dist=RADEMACHER, K=w["K"])),
-           ("configured_K10", dict(V=w["V"], S=w["S"], dist=GAUSSIAN, K=10, T_cap=20))]
+           ("configured_K10", dict(V=w["V"], S=w["S"], dist=GAUSSIAN, K=10, T_cap=20)),
+           ("configured_step_per_outer", dict(V=w["V"], S=w["S"], dist=GAUSSIAN, K=w["K"], step_per_outer=5))]
     if have_weights:
         out.append(("configured_warm_start", dict(V=w["V"], S=w["S"], dist=GAUSSIAN, K=w["K"], warm=True)))
     return out
@@ -358,7 +359,9 @@ def run_native(args, w, rank, world, local_rank):
         entry = {"reached_target": t_star is not None, "outer_iters": t_star if t_star else T_cap,
                  "K": ov["K"], "V": ov["V"], "S": ov["S"], "dist": "rademacher" if ov["dist"] else "gaussian",
                  "nrmse_curve": [round(float(e), 7) for e in curve], "warm_start": use_warm,
-                 "warm_accepted": st["warm_accepted"] if use_warm else None}
+                 "warm_accepted": st["warm_accepted"] if use_warm else None,
+                 "step_per_outer": ov.get("step_per_outer", 0),
+                 "L_t": [round(float(v), 5) for v in st["trace"][:, cs.TRACE_STEP_L]]}
         entry["params"] = dict(base, T=entry["outer_iters"])
         if name == "configured":
             head = entry

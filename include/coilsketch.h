@@ -37,7 +37,8 @@ enum {
     CS_ERR_CUDA = 3,             /* a CUDA runtime call failed                              */
     CS_ERR_OOM = 4,              /* device allocation failed                                */
     CS_ERR_NONFINITE = 5,        /* a solver reduction produced NaN or Inf                  */
-    CS_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up                      */
+    CS_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up; the outputs of the
+                                    calls since the last status check are invalid            */
     CS_ERR_BOUNDS = 7            /* a device-side index check failed (checked builds)       */
 };
 
@@ -296,7 +297,9 @@ enum {
     CS_TRACE_DIST2 = 3,      /* ||x^{t+1} - x_ref||^2 / ||x_ref||^2 after the iteration; -1
                                 without x_ref                                                 */
     CS_TRACE_TIME_NS = 4,    /* device clock (%globaltimer, ns) at the end of the iteration    */
-    CS_TRACE_FIELDS = 5
+    CS_TRACE_STEP_L = 5,     /* FISTA: the eigenvalue estimate L whose 1/L is the iteration's step
+                                (constant unless step_per_outer); 0 when the step was given    */
+    CS_TRACE_FIELDS = 6
 };
 
 typedef struct {
@@ -361,6 +364,12 @@ typedef struct {
     const float* x_ref;
     double* trace;
     int trace_objective;
+    /* Sketched FISTA with step = 0: the step 1/L comes from power_iters power iterations on the
+     * first sub-problem's sketched normal operator and is reused (Sec. 3.3).  step_per_outer > 0
+     * re-estimates L at every outer iteration instead, by that many power iterations on the
+     * iteration's own sketched operator started from the previous eigenvector estimate (on the
+     * device, inside the captured outer iteration).  0 = reuse (default).                     */
+    int step_per_outer;
 } cs_solve_params;
 
 typedef struct {

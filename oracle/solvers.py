@@ -51,6 +51,11 @@ def cg(H, b, x0, iters):
 
 def power_iteration(H, v0, iters=20):
     """Largest eigenvalue of Hermitian PSD H: v <- H v / ||H v||, L = ||H v|| at the last step."""
+    return power_iteration_vec(H, v0, iters)[0]
+
+
+def power_iteration_vec(H, v0, iters):
+    """The power iteration of power_iteration, returning (L, v) with v the last normalised iterate."""
     v = np.asarray(v0, dtype=np.complex128)
     v = v / np.linalg.norm(v.ravel())
     L = 0.0
@@ -58,7 +63,7 @@ def power_iteration(H, v0, iters=20):
         w = H(v)
         L = float(np.linalg.norm(w.ravel()))
         v = w / L
-    return L
+    return L, v
 
 
 def fista(grad, prox, x0, eta, iters):
@@ -193,7 +198,7 @@ def acc_prox_sgd(op_factory, maps, y, lam, batches, alpha0, beta, min_frac, x0, 
 
 def coil_sketching(op_factory, maps, y, lam, reg, sketches, V, K, x0=None, eta=None,
                    power_v0=None, power_iters=20, do_pca=True, levels=4, callback=None,
-                   cg_iters=5, tau=None, sigma=None, init_sketch=None):
+                   cg_iters=5, tau=None, sigma=None, init_sketch=None, step_per_outer=0, L_out=None):
     """Algorithm 1, optionally with its classical-sketch initialisation.
 
     op_factory(maps) -> (fwd, adj) builds A for a set of maps (Cartesian or NUFFT).
@@ -209,6 +214,10 @@ def coil_sketching(op_factory, maps, y, lam, reg, sketches, V, K, x0=None, eta=N
     gradient d = (S^0 A)^H (S^0 A x^0 - S^0 y) in place of the true one (its objective differs
     from the sub-problem's by a constant), so the same solver routine runs it.  The FISTA step
     1/L comes from the first model built (the initialisation's when there is one).
+    step_per_outer > 0 (FISTA with eta None; not in the paper, whose Sec. 3.3 reuses the first
+    step): every outer iteration re-estimates L with that many further power iterations on its
+    own sketched normal operator, continuing from the previous eigenvector estimate; L_out (a
+    list) receives the L of every outer iteration's step.
     Returns x^T and the list of iterates (the initialisation's result not included).
     """
     if do_pca:
@@ -225,6 +234,7 @@ def coil_sketching(op_factory, maps, y, lam, reg, sketches, V, K, x0=None, eta=N
         tau = t0 if tau is None else tau
         sigma = s0 if sigma is None else sigma
         zdual = np.zeros((x.ndim,) + x.shape, dtype=np.complex128)
+    veig = None
     steps = [("init", init_sketch)] if init_sketch is not None else []
     steps += [("outer", sketches[t]) for t in range(sketches.shape[0])]
     for kind, S_t in steps:
@@ -240,9 +250,14 @@ def coil_sketching(op_factory, maps, y, lam, reg, sketches, V, K, x0=None, eta=N
         elif reg == "l1tv":
             x, zdual = sketched_pdhg(normal_S, d, x, lam, zdual, tau, sigma, K, cg_iters)
         else:
-            if eta is None:
-                L = power_iteration(normal_S, power_v0, power_iters)
+            if eta is None or (step_per_outer and veig is None):
+                L, veig = power_iteration_vec(normal_S, power_v0, power_iters)
                 eta = 1.0 / L
+            if step_per_outer and kind == "outer":
+                L, veig = power_iteration_vec(normal_S, veig, step_per_outer)
+                eta = 1.0 / L
+            if L_out is not None and kind == "outer":
+                L_out.append(1.0 / eta)
             x = sketched_fista(normal_S, d, x, lam, eta, K, levels)
         if kind == "outer":
             iterates.append(x.copy())

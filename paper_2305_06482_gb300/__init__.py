@@ -29,7 +29,7 @@ NORM_UNIT_VAR, NORM_PAPER_LITERAL = 0, 1
 PREC_FP32, PREC_BF16_SPLIT = 0, 1
 REG_L2, REG_L1_WAVELET, REG_L1_TV = 0, 1, 2
 # fields of a recon_solve trace record (include/coilsketch.h, CS_TRACE_*)
-TRACE_GRAD2, TRACE_OBJECTIVE, TRACE_ACCEPT, TRACE_DIST2, TRACE_TIME_NS, TRACE_FIELDS = 0, 1, 2, 3, 4, 5
+TRACE_GRAD2, TRACE_OBJECTIVE, TRACE_ACCEPT, TRACE_DIST2, TRACE_TIME_NS, TRACE_STEP_L, TRACE_FIELDS = 0, 1, 2, 3, 4, 5, 6
 
 
 class CoilSketchError(RuntimeError):
@@ -59,7 +59,8 @@ class _Params(ctypes.Structure):
                 ("tv_tau", ctypes.c_float), ("tv_sigma", ctypes.c_float), ("init", ctypes.c_int),
                 ("keep", ctypes.c_int), ("sgd_batch", ctypes.c_int), ("sgd_coils", ctypes.c_void_p),
                 ("sgd_beta", ctypes.c_float), ("sgd_min", ctypes.c_float), ("warm", ctypes.c_void_p),
-                ("x_ref", ctypes.c_void_p), ("trace", ctypes.c_void_p), ("trace_objective", ctypes.c_int)]
+                ("x_ref", ctypes.c_void_p), ("trace", ctypes.c_void_p), ("trace_objective", ctypes.c_int),
+                ("step_per_outer", ctypes.c_int)]
 
 
 class _BatchItem(ctypes.Structure):
@@ -479,6 +480,7 @@ class SolveParams:
     x_ref: Optional[torch.Tensor] = None   # reference image for the trace's distance field
     trace: bool = False                    # record one trace row per outer iteration (plain: per iteration)
     trace_objective: bool = False          # add the objective to the trace (one extra forward per row)
+    step_per_outer: int = 0                # sketched FISTA: re-estimate L with this many power iterations per outer
 
 
 def recon_solve(plan: Plan, y, maps, lam, reg=REG_L2, params: SolveParams = None, x0=None, wavelet_levels=4,
@@ -518,7 +520,8 @@ def _params_struct(params: SolveParams):
                    sgd_beta=float(params.sgd_beta), sgd_min=float(params.sgd_min),
                    warm=None if params.warm is None else params.warm._h.value,
                    x_ref=None if params.x_ref is None else params.x_ref.data_ptr(),
-                   trace=None, trace_objective=int(params.trace_objective))
+                   trace=None, trace_objective=int(params.trace_objective),
+                   step_per_outer=int(params.step_per_outer))
 
 
 def recon_solve_batched(items, lam, reg=REG_L2, params: SolveParams = None, wavelet_levels=4, stream=None):

@@ -721,7 +721,16 @@ __global__ void __launch_bounds__(kPassThreads, 4)
         if (!done && ++spins > kTmaSpinLimit) break;
     }
     if (__syncthreads_or(!done)) {
+        // gave up: the flag makes the host report CS_ERR_TIMEOUT; this CTA's lines are not written,
+        // so every output of the call (and of a solve that contains it) is invalid.  Before the CTA
+        // leaves, wait once more (bounded) for the tile copy in flight into its shared memory.
         if (tid == 0) atomicExch(&g_fft_error, 1);
+        for (long long k = 0; !done && k < kTmaSpinLimit; ++k)
+            asm volatile(
+                "{\n.reg .pred P1;\nmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\nselp.b32 %0, 1, 0, P1;\n}\n"
+                : "=r"(done)
+                : "r"(smem_addr(&mbar)), "r"(0u)
+                : "memory");
         return;
     }
     float2* res = fft_lines<SIGN, kLines>(bufa, bufb, stw, n, sst, A.nrad, l, jt);

@@ -146,6 +146,13 @@ __global__ void __launch_bounds__(128) sketch_tc_kernel(const float* __restrict_
         // one decision for the whole CTA: give up together if any thread timed out
         if (__syncthreads_or(!done)) {
             if (tid == 0) atomicExch(&g_tc_error, 1);
+            // drain: wait once more (bounded) for the MMAs in flight before the tensor memory is freed
+            for (long long k = 0; !done && k < kSpinLimit; ++k)
+                asm volatile(
+                    "{\n.reg .pred P1;\nmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\nselp.b32 %0, 1, 0, P1;\n}\n"
+                    : "=r"(done)
+                    : "r"(mbar), "r"(phase)
+                    : "memory");
             failed = true;
             break;
         }

@@ -319,10 +319,12 @@ __global__ void trace_store_kernel(const double* __restrict__ part, double scale
     }
 }
 
-__global__ void trace_time_kernel(double* __restrict__ tr, const int* __restrict__ tdev) {
+__global__ void trace_time_kernel(double* __restrict__ tr, const int* __restrict__ tdev, const Scal* __restrict__ sc,
+                                  int have_L) {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     tr[(int64_t)(*tdev) * CS_TRACE_FIELDS + CS_TRACE_TIME_NS] = (double)t;
+    tr[(int64_t)(*tdev) * CS_TRACE_FIELDS + CS_TRACE_STEP_L] = have_L ? sc->L : 0.0;
 }
 
 // partials of ||a - b||^2
@@ -754,6 +756,7 @@ struct SolverWS {
     int64_t kres_n = 0;
     float2 *xt0 = nullptr, *xhat = nullptr;   // warm start: saved x^t and the prediction
     double* partC = nullptr;
+    float2* peig = nullptr;    // step re-estimation: the eigenvector estimate carried across outer iterations
     std::vector<void*> allocs;
     cudaGraphExec_t gexec = nullptr;
     uint64_t gsig = 0;
@@ -777,6 +780,7 @@ struct SolverWS {
         kres_n = 0;
         xt0 = xhat = nullptr;
         partC = nullptr;
+        peig = nullptr;
     }
     void drop_graph() {
         if (gexec) cudaGraphExecDestroy(gexec);
@@ -796,6 +800,11 @@ struct SolverWS {
         CS_PROPAGATE(get(&kres, (size_t)n));
         kres_n = n;
         return CS_OK;
+    }
+    cs_status ensure_peig() {
+        if (peig) return CS_OK;
+        drop_graph();
+        return get(&peig, (size_t)D);
     }
     cs_status ensure_warm() {
         if (xt0 && xhat && partC) return CS_OK;
@@ -1157,6 +1166,13 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
     // plain solvers: aggressive coil compression keeps the first `keep` (virtual) coils
     const int Cp = (!sketch && sp->keep > 0) ? std::min(sp->keep, C) : C;
     const bool sgd = !sketch && sp->sgd_batch > 0;
+    // FISTA step re-estimated at every outer iteration (power iterations on that iteration's
+    // sketched operator, warm-started from the previous eigenvector)
+    const int pso = sp->step_per_outer;
+    CS_REQUIRE(pso >= 0 && (pso == 0 || (sketch && fista && !(sp->step > 0))), CS_ERR_INVALID_ARG,
+               "step_per_outer needs a sketched l1-wavelet (FISTA) solve with step = 0");
+    if (pso > 0) CS_PROPAGATE(ws->ensure_peig());
+    const int have_L = (fista && !(sp->step > 0)) ? 1 : 0;
     PdhgArgs pd = {};
     if (tvreg) {
         CS_REQUIRE(K >= 1 && sp->cg_iters >= 0, CS_ERR_INVALID_ARG, "l1-TV needs K >= 1 and cg_iters >= 0");
@@ -1243,7 +1259,7 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
                                                 CS_TRACE_DIST2);
             CS_LAUNCH_CHECK();
         }
-        trace_time_kernel<<<1, 1, 0, s>>>(ws->trace, ws->tdev);
+        trace_time_kernel<<<1, 1, 0, s>>>(ws->trace, ws->tdev, ws->sc, have_L);
         CS_LAUNCH_CHECK();
         return CS_OK;
     };
@@ -1253,7 +1269,7 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
     const void* ptrs[] = {p, x, pr->y, pr->maps, sp->sketches, sp->iterates, sp->power_v0};
     sig = fnv(sig, ptrs, sizeof(ptrs));
     const int ints[] = {C, T, K, V, S, sp->dist, sp->norm, sp->do_pca, sp->precision, pr->reg, c.levels, (int)sketch,
-                        init, Cp, sp->sgd_batch};
+                        init, Cp, sp->sgd_batch, pso};
     const void* ptrs2[] = {sp->sgd_coils};
     const float sgdf[] = {sp->sgd_beta, sp->sgd_min};
     sig = fnv(sig, ints, sizeof(ints));
@@ -1302,6 +1318,7 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
             if (S > 0 && !init) CS_PROPAGATE(sketched_maps_impl(sk, ws->tdev, maps, D, C, V, S, sp->precision, msk, st));
             CS_PROPAGATE(power_iteration(c, (const float2*)sp->power_v0, sp->power_iters > 0 ? sp->power_iters : 20,
                                          maps, V, msk, S, ws->u, ws->hp));
+            if (pso > 0) CS_TRY_CUDA(cudaMemcpyAsync(ws->peig, ws->u, sizeof(float2) * D, cudaMemcpyDeviceToDevice, st));
         }
         if (init) {
             // argmin 1/2 ||S^0 A x - S^0 y||^2 + g(x) from x^0: the sub-problem at x^t = x^0 with
@@ -1330,6 +1347,10 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
             if (tracing) CS_PROPAGATE(trace_norm2(s, ws->d, CS_TRACE_GRAD2));
             // sketched model: V virtual coils in place + S random combinations of the rest
             if (S > 0) CS_PROPAGATE(sketched_maps_impl(sk, ws->tdev, maps, D, C, V, S, sp->precision, msk, s));
+            if (pso > 0) {
+                CS_PROPAGATE(power_iteration(cc, ws->peig, pso, maps, V, msk, S, ws->u, ws->hp));
+                CS_TRY_CUDA(cudaMemcpyAsync(ws->peig, ws->u, sizeof(float2) * D, cudaMemcpyDeviceToDevice, s));
+            }
             if (fista && warm) {
                 // learned warm start: prediction xhat from (x^t, d); the sub-problem objective of
                 // Eq. 9-10, F(u) = 1/2 ||A_S (u - x^t)||^2 + Re<u, d> + lambda ||Psi u||_1, at xhat

@@ -158,6 +158,13 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(const float* __restrict__
             }
             if (__syncthreads_or(!done)) {
                 if (tid == 0) atomicExch(&g_nn_error, 1);
+                // drain: wait once more (bounded) for the MMAs in flight before the tensor memory is freed
+                for (long long k = 0; !done && k < kNnSpin; ++k)
+                    asm volatile(
+                        "{\n.reg .pred P1;\nmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\nselp.b32 %0, 1, 0, P1;\n}\n"
+                        : "=r"(done)
+                        : "r"(mbar), "r"(phase)
+                        : "memory");
                 failed = true;
                 break;
             }
@@ -349,6 +356,13 @@ __global__ void __launch_bounds__(128, 1) conv3_brick_kernel(const float* __rest
             }
             if (__syncthreads_or(!done)) {
                 if (tid == 0) atomicExch(&g_nn_error, 1);
+                // drain: wait once more (bounded) for the MMAs in flight before the tensor memory is freed
+                for (long long k = 0; !done && k < kNnSpin; ++k)
+                    asm volatile(
+                        "{\n.reg .pred P1;\nmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\nselp.b32 %0, 1, 0, P1;\n}\n"
+                        : "=r"(done)
+                        : "r"(mbar), "r"(phase)
+                        : "memory");
                 failed = true;
                 break;
             }

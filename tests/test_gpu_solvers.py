@@ -106,6 +106,36 @@ def test_coil_sketching_fista_cartesian():
     assert nrmse(h(x), x_ref) < 1e-4
 
 
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_coil_sketching_fista_with_the_step_re_estimated_every_outer_iteration(use_graph):
+    """step_per_outer = 4: every outer iteration continues the power iteration on its own sketched
+    operator and uses 1/L_t; the trace's step field matches the oracle's L_t, and every iterate
+    and the final image match the oracle run with the same option."""
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    shape = (128, 128)
+    idx, maps, y, ops = _cart_problem(shape, C=8)
+    C, V, S, T, K, lam = 8, 3, 3, 4, 8, 5e-3
+    sk = philox.sketch_draw(12, 0, T, C, V, S)
+    v0 = synthdata.random_complex(shape, 6)
+    L_ref = []
+    x_ref, its = solvers.coil_sketching(ops, maps, y, lam, "l1wav", sk.astype(np.float64), V=V, K=K, power_v0=v0,
+                                        step_per_outer=4, L_out=L_ref)
+    assert np.ptp(L_ref) > 1e-3 * max(L_ref)          # the blocks' operators do differ
+    plan = cs.Plan(cs.CARTESIAN, shape, C, mask_idx=t(idx, np.int32))
+    iters = torch.empty((T,) + shape, dtype=torch.complex64, device="cuda")
+    x, st = cs.recon_solve(plan, t(y), t(maps), lam, cs.REG_L1_WAVELET,
+                           cs.SolveParams(T=T, K=K, V=V, S=S, sketches=t(sk), power_v0=t(v0), step_per_outer=4,
+                                          iterates=iters, trace=True, use_graph=use_graph))
+    assert np.allclose(st["trace"][:, cs.TRACE_STEP_L], L_ref, rtol=1e-5, atol=0)
+    assert nrmse(h(x), x_ref) < 1e-4
+    for k in range(T):
+        assert nrmse(h(iters[k]), its[k]) < 1e-4
+    with pytest.raises(cs.CoilSketchError):          # needs FISTA with the step from power iterations
+        cs.recon_solve(plan, t(y), t(maps), lam, cs.REG_L2,
+                       cs.SolveParams(T=T, K=K, V=V, S=S, sketches=t(sk), step_per_outer=4))
+
+
 def test_coil_sketching_cg_nufft():
     import paper_2305_06482_gb300 as cs
     from tests._gpu import t, h, nrmse
@@ -304,6 +334,7 @@ def test_trace_records_match_the_oracle():
         assert np.all(tr[:, cs.TRACE_ACCEPT] == -1)
         assert np.allclose(tr[:, cs.TRACE_DIST2], dist, rtol=1e-4)
         assert np.all(np.diff(tr[:, cs.TRACE_TIME_NS]) > 0)
+        assert np.all(tr[:, cs.TRACE_STEP_L] == st["L"])       # the first sub-problem's step, reused
     # without the objective flag the field stays NaN; without x_ref the distance is -1
     _, st = cs.recon_solve(plan, t(y), t(maps), lam, cs.REG_L1_WAVELET,
                            cs.SolveParams(T=T, K=K, V=V, S=S, sketches=t(sk), power_v0=t(v0), trace=True),

@@ -245,3 +245,40 @@ def test_acc_prox_sgd_step_schedule_matches_hand_iterates():
         x = solvers.acc_prox_sgd(ops, maps, y, 0.0, batches[:k], 0.1, 0.5, 0.2, np.zeros((4, 4), complex), k,
                                  levels=1)
         assert np.abs(x - hand[k - 1]).max() < 1e-13
+
+
+def test_per_outer_step_tracks_each_sketched_operators_largest_eigenvalue():
+    """With step_per_outer the FISTA step of every outer iteration is 1/L_t, L_t from power
+    iterations on that iteration's own sketched normal operator continued from the previous
+    eigenvector.  Image-domain coils A_c = diag(m_c) make A_S^H A_S = diag(sum_i |m~_i|^2), whose
+    largest eigenvalue is the largest diagonal entry; the maps give one voxel a clear lead, so the
+    power iteration converges and L_t must equal that entry of each sketch block (blocks differing
+    from one another).  The first L_t is the first model's power iteration run power_iters +
+    step_per_outer times; without the option the first step is reused."""
+    rng = np.random.default_rng(8)
+    C, V, S, T = 4, 2, 1, 3
+    maps = rng.uniform(0.2, 1.0, (C, 4, 4)) * np.exp(1j * rng.uniform(0, 2 * np.pi, (C, 4, 4)))
+    maps[0, 0, 0] = 3.0
+    ops = lambda mm: (lambda v: mm * v, lambda r: np.sum(np.conj(mm) * r, axis=0))
+    y = ops(maps)[0](synthdata.phantom((4, 4), seed=2))
+    sk = rng.standard_normal((T, S, C - V))
+    v0 = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))
+    diag = [np.sum(np.abs(coils.sketched_maps(sk[t], maps, V)) ** 2, axis=0) for t in range(T)]
+    for w in diag:
+        top2 = np.sort(w.ravel())[-2:]
+        assert top2[0] < 0.7 * top2[1] and np.argmax(w) == 0
+    eig = [w.max() for w in diag]
+    assert np.ptp(eig) > 1e-2 * max(eig)
+    Ls = []
+    solvers.coil_sketching(ops, maps, y, 1e-2, "l1wav", sk, V, 2, power_v0=v0, power_iters=20, do_pca=False,
+                           levels=1, step_per_outer=200, L_out=Ls)
+    assert np.allclose(Ls, eig, rtol=1e-12, atol=0)
+    L1 = []
+    solvers.coil_sketching(ops, maps, y, 1e-2, "l1wav", sk, V, 2, power_v0=v0, power_iters=20, do_pca=False,
+                           levels=1, step_per_outer=3, L_out=L1)
+    fs, ads = ops(coils.sketched_maps(sk[0], maps, V))
+    assert L1[0] == solvers.power_iteration(lambda v: ads(fs(v)), v0, 23)
+    L0 = []
+    solvers.coil_sketching(ops, maps, y, 1e-2, "l1wav", sk, V, 2, power_v0=v0, power_iters=20, do_pca=False,
+                           levels=1, L_out=L0)
+    assert L0 == [L0[0]] * T and L0[0] == solvers.power_iteration(lambda v: ads(fs(v)), v0, 20)
