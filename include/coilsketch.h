@@ -445,7 +445,10 @@ cs_status cs_power_iteration(const cs_plan* plan, const float* v0, const float* 
  *   sum_{tap, c} in[v + s off(tap)][c] W[n][tap * cin + c] (+ ReLU), s = -1 when flip (the data
  *   gradient, with weights packed transposed), else +1.  `packed` is [npad][kpad] BF16 from
  *   cs_nn_pack_weights (npad in {16, 32, 64}, kpad >= 27 cin, multiple of 16; 16-byte aligned).
- * cs_nn_conv3d_wgrad: gw[co][tap][ci] += sum_v gout[v][co] in[v + off(tap)][ci]; gb += sum_v gout.
+ * cs_nn_conv3d_wgrad: gw[co][tap][ci] += sum_v gout[v][co] in[v + off(tap)][ci] as a BF16 implicit
+ *   GEMM on the tensor cores (in and gout rounded to BF16, FP32 accumulation; voxels are the
+ *   reduction, partial sums added in a fixed order, so the result is bit-reproducible); gb += sum_v
+ *   gout in FP32.
  * cs_nn_conv1(_bwd): 1x1x1 layer; cs_nn_relu_bwd: g *= (act > 0); cs_nn_mse: loss += mean sq.
  *   error, g = its gradient; cs_nn_adam: one Adam step (step >= 1).
  * cs_nn_features / target / apply: network input [x^t / s, d eta / s] with s the RMS of

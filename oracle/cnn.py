@@ -35,18 +35,19 @@ def conv3d(x, w, b, bf16=False):
 
 
 def conv3d_bwd(x, w, gout, bf16=False):
-    """(gx, gw, gb) of conv3d.  gx uses the rounded weights and gout (as the data-gradient
-    convolution does); gw uses the FP32 input and gradient (computed on CUDA cores)."""
+    """(gx, gw, gb) of conv3d.  With bf16=True both products see BF16 operands, as the tensor-core
+    kernels do: gx the rounded weights and gout (the data-gradient convolution), gw the rounded
+    input and gout (the weight-gradient implicit GEMM); gb sums the unrounded gout."""
     nz, ny, nx, cin = x.shape
     wr = _r(w, bf16)
     gr = _r(gout, bf16)
     gxp = np.zeros((nz + 2, ny + 2, nx + 2, cin))
-    xp = np.pad(np.asarray(x, np.float64), ((1, 1), (1, 1), (1, 1), (0, 0)))
+    xp = np.pad(_r(x, bf16), ((1, 1), (1, 1), (1, 1), (0, 0)))
     gw = np.zeros_like(np.asarray(w, np.float64))
     g64 = np.asarray(gout, np.float64)
     for t, (dz, dy, dx) in enumerate(taps()):
         sl = xp[1 + dz:1 + dz + nz, 1 + dy:1 + dy + ny, 1 + dx:1 + dx + nx]
-        gw[:, t, :] = np.einsum("zyxo,zyxc->oc", g64, sl)
+        gw[:, t, :] = np.einsum("zyxo,zyxc->oc", gr, sl)
         gxp[1 + dz:1 + dz + nz, 1 + dy:1 + dy + ny, 1 + dx:1 + dx + nx] += gr @ wr[:, t, :]
     return gxp[1:-1, 1:-1, 1:-1], gw, g64.sum(axis=(0, 1, 2))
 

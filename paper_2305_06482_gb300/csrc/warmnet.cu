@@ -6,8 +6,10 @@
 //             (GEMM M = 128 voxels, N = C_out padded to 16/32/64, K = 27 C_in padded to 16)
 //   data gradient: the same kernel with the taps flipped and the weights transposed,
 //             gin[v][ci] = sum_{tap, co} gout[v - off(tap)][co] w[co][tap][ci]
-// Max-pools, stride-2 transposed convolutions, channel slices (skip concatenation), weight
-// gradients, the 1x1x1 output layer, ReLU masks, the loss and Adam run on CUDA cores.
+//   weight gradient: gw[co][tap][ci] = sum_v gout[v][co] in[v + off(tap)][ci]
+//             (GEMM M = 27 C_in rows of the transposed im2col, N = C_out padded, K = voxels)
+// Max-pools, stride-2 transposed convolutions, channel slices (skip concatenation), the 1x1x1
+// output layer, ReLU masks, the loss and Adam run on CUDA cores.
 #include <cstdio>
 
 #include "cs_internal.cuh"
@@ -437,144 +439,199 @@ __global__ void pack_weights_kernel(const float* __restrict__ w, int cout, int c
 }
 
 // weight gradient: gw[co][tap][ci] += sum_v gout[v][co] in[v + off(tap)][ci], gb[co] += sum_v gout[v][co].
-// Every block of voxels writes its own partial sums (gw, gb here point at the [gridDim.x] partial
-// arrays); wsum_kernel adds them in block order, so the gradient is bit-reproducible.
-constexpr int kWgVox = 128;
-__global__ void wgrad_kernel(const float* __restrict__ in, const float* __restrict__ gout, int nz, int ny, int nx, int cin,
-                             int cout, float* __restrict__ gw, float* __restrict__ gb) {
-    extern __shared__ float wsm[];
-    float* sg = wsm;                     // [kWgVox][cout]
-    float* si = wsm + kWgVox * cout;     // [kWgVox][cin]
-    const int tap = blockIdx.y;
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+constexpr int kWgVox = 128;    // voxels staged per round by the transposed convolution's weight gradient
+
+// Weight gradient of the 3x3x3 convolution as a BF16 implicit GEMM on the tensor cores:
+//   gw[co][m] += sum_v gout[v][co] in[v + off(tap_m)][ci_m],   m = tap * cin + ci,
+// with the rows m of the transposed im2col matrix of the input as GEMM rows (tiles of 128), the
+// output channels as columns (N = NPAD) and the voxels as the reduction (k-blocks of 16).  Both
+// operands are rounded to BF16 as they are staged in the same K-major core-matrix layout as the
+// forward kernel's, and the products accumulate in FP32 in tensor memory.  A CTA takes up to
+// kWtTiles row tiles (one accumulator each) and one contiguous range of voxel rounds; it writes its
+// accumulators to its own partial-sum slot [blockIdx.x][row][NPAD], and wgrad_sum_kernel adds the
+// slots in slot order, so the gradient is bit-reproducible.
+constexpr int kWtKB = 4;                  // k-blocks (16 voxels each) per MMA round
+constexpr int kWtTiles = 4;               // row tiles (accumulators) per CTA
+constexpr int kWtVox = 16 * kWtKB;        // voxels per round
+
+template <int NPAD>
+__global__ void __launch_bounds__(128) wgrad_tc_kernel(const float* __restrict__ in, const float* __restrict__ gout, int nz,
+                                                       int ny, int nx, int cin, int cout, int mtiles,
+                                                       int rounds_per_cta, float* __restrict__ part) {
+    constexpr int kBBytes = NPAD * 16 * 2;
+    constexpr uint32_t kCols = (uint32_t)(kWtTiles * NPAD);    // 64 .. 512, a power of two
+    constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NPAD >> 3) << 17) | ((uint32_t)(kNnM >> 4) << 24);
+    extern __shared__ __align__(1024) unsigned char nsm[];
+    unsigned char* a_sm = nsm;                                  // [kWtTiles][kWtKB] blocks of 128 x 16
+    unsigned char* b_sm = nsm + kWtTiles * kWtKB * kNnABytes;    // [kWtKB] blocks of NPAD x 16
+    __shared__ int s_vz[kWtVox], s_vy[kWtVox], s_vx[kWtVox];
+    __shared__ uint32_t s_taddr;
+    __shared__ __align__(8) uint64_t s_mbar;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(nn_smem_u32(&s_taddr)),
+                     "r"(kCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(nn_smem_u32(&s_mbar)), "r"(1u));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = s_taddr, mbar = nn_smem_u32(&s_mbar);
+    uint32_t phase = 0;
     const int64_t nvox = (int64_t)nz * ny * nx;
-    const int pairs = cout * cin;
-    const int pbase = blockIdx.z * 4 * blockDim.x;   // this block's chunk of (co, ci) pairs
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    float bacc = 0.f;
-    for (int64_t v0 = (int64_t)blockIdx.x * kWgVox; v0 < nvox; v0 += (int64_t)gridDim.x * kWgVox) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < kWgVox * cout; e += blockDim.x) {
-            const int64_t v = v0 + e / cout;
-            sg[e] = (v < nvox) ? gout[v * cout + e % cout] : 0.f;
-        }
-        for (int e = threadIdx.x; e < kWgVox * cin; e += blockDim.x) {
-            const int64_t v = v0 + e / cin;
-            float val = 0.f;
-            if (v < nvox) {
-                const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
-                const int zz = z + dz, yy = y + dy, xx = x + dx;
-                if (zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx)
-                    val = in[(((int64_t)zz * ny + yy) * nx + xx) * cin + e % cin];
-            }
-            si[e] = val;
+    const int64_t rounds = (nvox + kWtVox - 1) / kWtVox;
+    const int64_t r0 = (int64_t)blockIdx.x * rounds_per_cta;
+    const int64_t r1 = min(rounds, r0 + rounds_per_cta);
+    const int rows = 27 * cin;
+    const int tile0 = blockIdx.y * kWtTiles;
+    const int nt = min(kWtTiles, mtiles - tile0);
+    bool failed = false;
+    for (int64_t r = r0; r < r1 && !failed; ++r) {
+        const int64_t v0 = r * kWtVox;
+        if (tid < kWtVox) {
+            const int64_t v = v0 + tid;
+            const bool ok = v < nvox;
+            s_vx[tid] = ok ? (int)(v % nx) : -4;       // out-of-range voxels fail every bounds test
+            s_vy[tid] = ok ? (int)((v / nx) % ny) : -4;
+            s_vz[tid] = ok ? (int)(v / ((int64_t)nx * ny)) : -4;
         }
         __syncthreads();
-        for (int q = 0; q < 4; ++q) {
-            const int pr = pbase + threadIdx.x + q * blockDim.x;
-            if (pr < pairs) {
-                const int co = pr / cin, ci = pr % cin;
-                float a = 0.f;
-                for (int t = 0; t < kWgVox; ++t) a = fmaf(sg[t * cout + co], si[t * cin + ci], a);
-                acc[q] += a;
+        // B: the output gradient of the round's voxels, row n = output channel, k = voxel
+        for (int e = tid; e < NPAD * kWtKB * 2; e += blockDim.x) {
+            const int n = e % NPAD, kh = e / NPAD, kb = kh >> 1, h = kh & 1;
+            uint32_t pk[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = kb * 16 + h * 8 + 2 * q;
+                const float g0 = (n < cout && v0 + j < nvox) ? gout[(v0 + j) * cout + n] : 0.f;
+                const float g1 = (n < cout && v0 + j + 1 < nvox) ? gout[(v0 + j + 1) * cout + n] : 0.f;
+                pk[q] = (uint32_t)nn_bf16(g0) | ((uint32_t)nn_bf16(g1) << 16);
+            }
+            *reinterpret_cast<uint4*>(b_sm + kb * kBBytes + nn_kmajor_off(n, 8 * h)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+        // A: this thread's row m of each of the CTA's tiles, the input at the row's tap for every voxel
+        for (int i = 0; i < nt; ++i) {
+            const int m = (tile0 + i) * kNnM + tid;
+            const bool mv = m < rows;
+            const int tap = mv ? m / cin : 13, ci = mv ? m - tap * cin : 0;
+            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+            for (int kb = 0; kb < kWtKB; ++kb) {
+                uint32_t pk[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float a2[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int j = kb * 16 + 2 * q + u;
+                        const int zz = s_vz[j] + dz, yy = s_vy[j] + dy, xx = s_vx[j] + dx;
+                        a2[u] = (mv && zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx)
+                                    ? in[(((int64_t)zz * ny + yy) * nx + xx) * cin + ci]
+                                    : 0.f;
+                    }
+                    pk[q] = (uint32_t)nn_bf16(a2[0]) | ((uint32_t)nn_bf16(a2[1]) << 16);
+                }
+                unsigned char* arow = a_sm + (i * kWtKB + kb) * kNnABytes + nn_kmajor_off(tid, 0);
+                *reinterpret_cast<uint4*>(arow) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4*>(arow + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
             }
         }
-        if (tap == 13 && blockIdx.z == 0 && threadIdx.x < cout)
-            for (int t = 0; t < kWgVox; ++t) bacc += sg[t * cout + threadIdx.x];
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            for (int i = 0; i < nt; ++i) {
+                for (int kb = 0; kb < kWtKB; ++kb) {
+                    const uint64_t ad = nn_desc(nn_smem_u32(a_sm + (i * kWtKB + kb) * kNnABytes));
+                    const uint64_t bd = nn_desc(nn_smem_u32(b_sm + kb * kBBytes));
+                    const uint32_t acc = (r > r0 || kb > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr + (uint32_t)(i * NPAD)),
+                        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                         : "memory");
+        }
+        long long spins = 0;
+        uint32_t done = 0;
+        while (!done) {
+            asm volatile(
+                "{\n.reg .pred P1;\nmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\nselp.b32 %0, 1, 0, P1;\n}\n"
+                : "=r"(done)
+                : "r"(mbar), "r"(phase)
+                : "memory");
+            if (!done && ++spins > kNnSpin) break;
+        }
+        if (__syncthreads_or(!done)) {
+            if (tid == 0) atomicExch(&g_nn_error, 1);
+            // drain: wait once more (bounded) for the MMAs in flight before the tensor memory is freed
+            for (long long k = 0; !done && k < kNnSpin; ++k)
+                asm volatile(
+                    "{\n.reg .pred P1;\nmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\nselp.b32 %0, 1, 0, P1;\n}\n"
+                    : "=r"(done)
+                    : "r"(mbar), "r"(phase)
+                    : "memory");
+            failed = true;
+            break;
+        }
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    // this voxel block's partial sums; wsum_kernel adds the blocks in block order
-    float* pw = gw + (int64_t)blockIdx.x * cout * 27 * cin;
-    for (int q = 0; q < 4; ++q) {
-        const int pr = pbase + threadIdx.x + q * blockDim.x;
-        if (pr < pairs) {
-            const int co = pr / cin, ci = pr % cin;
-            pw[((int64_t)co * 27 + tap) * cin + ci] = acc[q];
+    if (!failed && r0 < r1) {
+        // accumulators -> this CTA's partial-sum slot: TMEM lane = row m, columns = output channels
+        const int64_t mrows = (int64_t)mtiles * kNnM;
+        for (int i = 0; i < nt; ++i) {
+            const int m = (tile0 + i) * kNnM + warp * 32 + lane;
+#pragma unroll
+            for (int j = 0; j < NPAD / 16; ++j) {
+                uint32_t rr[16];
+                const uint32_t ta = taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(i * NPAD + j * 16);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                    : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]), "=r"(rr[7]),
+                      "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]), "=r"(rr[15])
+                    : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (m < rows) {
+                    float* dst = part + ((int64_t)blockIdx.x * mrows + m) * NPAD + j * 16;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) dst[q] = __uint_as_float(rr[q]);
+                }
+            }
         }
     }
-    if (tap == 13 && blockIdx.z == 0 && threadIdx.x < cout && gb) gb[blockIdx.x * cout + threadIdx.x] = bacc;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(kCols));
 }
 
-// The same weight gradient with register tiles, for cin and cout multiples of 4: a thread owns a
-// 4 x 4 block of (co, ci) and a share (1 / vsplit) of the staged voxels, reading float4 rows of
-// the staged gradient and input (8 FMA per shared load).  Grid (x, 27 taps, chunks of 256 tiles).
-__global__ void wgrad_tiled_kernel(const float* __restrict__ in, const float* __restrict__ gout, int nz, int ny, int nx,
-                                   int cin, int cout, float* __restrict__ gw, float* __restrict__ gb) {
-    extern __shared__ float4 wsm4[];
-    float* sg = reinterpret_cast<float*>(wsm4);   // [kWgVox][cout]
-    float* si = sg + kWgVox * cout;               // [kWgVox][cin]
-    const int tap = blockIdx.y;
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const int64_t nvox = (int64_t)nz * ny * nx;
-    const int cq = cin >> 2, tiles = (cout >> 2) * cq;
-    const int tiles_here = min(tiles - (int)blockIdx.z * (int)blockDim.x, (int)blockDim.x);
-    const int vsplit = max(1, (int)blockDim.x / tiles_here);
-    const int tile = blockIdx.z * blockDim.x + (int)threadIdx.x % tiles_here;
-    const int vs = (int)threadIdx.x / tiles_here;
-    const bool owner = vs < vsplit;
-    const int co0 = (tile / cq) * 4, ci0 = (tile % cq) * 4;
-    float acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-    float bacc = 0.f;
-    for (int64_t v0 = (int64_t)blockIdx.x * kWgVox; v0 < nvox; v0 += (int64_t)gridDim.x * kWgVox) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < kWgVox * cout; e += blockDim.x) {
-            const int64_t v = v0 + e / cout;
-            sg[e] = (v < nvox) ? gout[v * cout + e % cout] : 0.f;
-        }
-        for (int e = threadIdx.x; e < kWgVox * cin; e += blockDim.x) {
-            const int64_t v = v0 + e / cin;
-            float val = 0.f;
-            if (v < nvox) {
-                const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
-                const int zz = z + dz, yy = y + dy, xx = x + dx;
-                if (zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx)
-                    val = in[(((int64_t)zz * ny + yy) * nx + xx) * cin + e % cin];
-            }
-            si[e] = val;
-        }
-        __syncthreads();
-        if (owner) {
-            for (int t = vs; t < kWgVox; t += vsplit) {
-                const float4 gv = *reinterpret_cast<const float4*>(sg + t * cout + co0);
-                const float4 xv = *reinterpret_cast<const float4*>(si + t * cin + ci0);
-                const float g4[4] = {gv.x, gv.y, gv.z, gv.w};
-                const float x4[4] = {xv.x, xv.y, xv.z, xv.w};
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(g4[a], x4[b], acc[a][b]);
-            }
-        }
-        if (tap == 13 && blockIdx.z == 0 && threadIdx.x < cout)
-            for (int t = 0; t < kWgVox; ++t) bacc += sg[t * cout + threadIdx.x];
+// gw[co][m] += sum over the partial-sum slots (in slot order) of part[slot][m][co]
+__global__ void wgrad_sum_kernel(const float* __restrict__ part, int nslots, int64_t mrows, int npad, int rows, int cout,
+                                 float* __restrict__ gw) {
+    const int64_t n = (int64_t)rows * cout;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int co = (int)(e / rows), m = (int)(e % rows);
+        float acc = 0.f;
+        for (int s = 0; s < nslots; ++s) acc += part[((int64_t)s * mrows + m) * npad + co];
+        gw[e] += acc;
     }
-    // the vsplit threads of a tile add their shares in split order, then the block's partial sums
-    // go to its slot (wsum_kernel adds the blocks in block order)
-    __syncthreads();
-    float* red = sg;                               // [vsplit][tiles_here][16], reuses the staging area
-    if (owner) {
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) red[((int64_t)vs * tiles_here + (tile - blockIdx.z * blockDim.x)) * 16 + a * 4 + b] = acc[a][b];
+}
+
+// bias gradient partials: part[block][co] = sum of gout[v][co] over the block's contiguous voxel range
+__global__ void bias_part_kernel(const float* __restrict__ gout, int64_t nvox, int cout, int64_t per_block,
+                                 float* __restrict__ part) {
+    const int64_t v0 = (int64_t)blockIdx.x * per_block, v1 = min(nvox, v0 + per_block);
+    for (int co = threadIdx.x; co < cout; co += blockDim.x) {
+        float acc = 0.f;
+        for (int64_t v = v0; v < v1; ++v) acc += gout[v * cout + co];
+        part[(int64_t)blockIdx.x * cout + co] = acc;
     }
-    __syncthreads();
-    if (owner && vs == 0) {
-        float* pw = gw + (int64_t)blockIdx.x * cout * 27 * cin;
-        const int ti = tile - blockIdx.z * blockDim.x;
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                float tot = 0.f;
-                for (int k = 0; k < vsplit; ++k) tot += red[((int64_t)k * tiles_here + ti) * 16 + a * 4 + b];
-                pw[((int64_t)(co0 + a) * 27 + tap) * cin + ci0 + b] = tot;
-            }
-    }
-    if (tap == 13 && blockIdx.z == 0 && threadIdx.x < cout && gb) gb[blockIdx.x * cout + threadIdx.x] = bacc;
 }
 
 // g *= (act > 0)
@@ -981,11 +1038,16 @@ cs_status nn_init_attrs() {
                                      BrickCfg<32, kBrTZ>::kSmem));
     CS_TRY_CUDA(cudaFuncSetAttribute(conv3_brick_kernel<64, kBrTZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      BrickCfg<64, kBrTZ>::kSmem));
-    // weight gradients stage kWgVox voxels of cin + cout <= 256 channels
-    CS_TRY_CUDA(cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sizeof(float) * kWgVox * 256));
-    CS_TRY_CUDA(cudaFuncSetAttribute(wgrad_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)sizeof(float) * kWgVox * 256));
+    // weight gradients: kWtTiles x kWtKB row blocks and kWtKB gradient blocks per round
+    CS_TRY_CUDA(cudaFuncSetAttribute(wgrad_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kWtTiles * kWtKB * kNnABytes + kWtKB * 16 * 32));
+    CS_TRY_CUDA(cudaFuncSetAttribute(wgrad_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kWtTiles * kWtKB * kNnABytes + kWtKB * 32 * 32));
+    CS_TRY_CUDA(cudaFuncSetAttribute(wgrad_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kWtTiles * kWtKB * kNnABytes + kWtKB * 64 * 32));
+    CS_TRY_CUDA(cudaFuncSetAttribute(wgrad_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kWtTiles * kWtKB * kNnABytes + kWtKB * 128 * 32));
+    // the transposed convolution's weight gradient stages kWgVox voxels of cin + cout <= 256 channels
     CS_TRY_CUDA(cudaFuncSetAttribute(upconv2_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sizeof(float) * kWgVox * 256));
     return CS_OK;
@@ -1089,33 +1151,41 @@ cs_status cs_nn_conv3d(const float* in, int nz, int ny, int nx, int cin, const u
 cs_status cs_nn_conv3d_wgrad(const float* in, const float* gout, int nz, int ny, int nx, int cin, int cout, float* gw,
                              float* gb, void* stream) {
     clear_error();
-    CS_REQUIRE(in && gout && gw && cin >= 1 && cout >= 1 && cin <= 128 && cout <= 128, CS_ERR_INVALID_ARG,
-               "bad wgrad arguments");
+    CS_REQUIRE(in && gout && gw && cin >= 1 && cout >= 1 && cin <= 128 && cout <= 128 && nz >= 1 && ny >= 1 && nx >= 1,
+               CS_ERR_INVALID_ARG, "bad wgrad arguments");
     CS_PROPAGATE(nn_attrs_once());
     const int64_t nvox = (int64_t)nz * ny * nx;
-    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((nvox + kWgVox - 1) / kWgVox, 64));
     cudaStream_t st = (cudaStream_t)stream;
-    // per-voxel-block partial sums (scratch from the stream-ordered pool), added in block order
-    const int64_t wsize = (int64_t)cout * 27 * cin;
+    const int rows = 27 * cin;
+    const int mtiles = (rows + kNnM - 1) / kNnM;
+    const int groups = (mtiles + kWtTiles - 1) / kWtTiles;
+    const int npad = cout <= 16 ? 16 : cout <= 32 ? 32 : cout <= 64 ? 64 : 128;
+    // voxel rounds split so that about two CTAs per SM run; every CTA gets at least one round
+    const int64_t rounds = (nvox + kWtVox - 1) / kWtVox;
+    const int64_t want = std::max<int64_t>(1, (2 * 152 + groups - 1) / groups);
+    const int64_t per = (rounds + std::min(rounds, want) - 1) / std::min(rounds, want);
+    const int nslots = (int)((rounds + per - 1) / per);
+    const int64_t mrows = (int64_t)mtiles * kNnM;
+    const int nbias = (int)std::min<int64_t>(nvox, 64);
+    const int64_t bper = (nvox + nbias - 1) / nbias;
     float* part = nullptr;
-    CS_TRY_CUDA(cudaMallocAsync((void**)&part, sizeof(float) * (size_t)gx * (wsize + cout), st));
-    float* pb = part + (int64_t)gx * wsize;
-    if (cin % 4 == 0 && cout % 4 == 0) {
-        // staging area, also the in-block reduction area of up to 256 tiles x 16 values
-        const size_t sm = sizeof(float) * std::max<size_t>((size_t)kWgVox * (cin + cout), 256 * 16);
-        const int chunks = ((cin / 4) * (cout / 4) + 255) / 256;   // 256 register tiles per block
-        wgrad_tiled_kernel<<<dim3(gx, 27, chunks), 256, sm, st>>>(in, gout, nz, ny, nx, cin, cout, part,
-                                                                  gb ? pb : nullptr);
-    } else {
-        const size_t sm = sizeof(float) * kWgVox * (cin + cout);
-        const int chunks = (cin * cout + 1023) / 1024;   // 256 threads x 4 pairs per block
-        wgrad_kernel<<<dim3(gx, 27, chunks), 256, sm, st>>>(in, gout, nz, ny, nx, cin, cout, part, gb ? pb : nullptr);
+    CS_TRY_CUDA(cudaMallocAsync((void**)&part, sizeof(float) * ((size_t)nslots * mrows * npad + (size_t)nbias * cout), st));
+    float* pb = part + (int64_t)nslots * mrows * npad;
+    const dim3 grid((unsigned)nslots, (unsigned)groups);
+    const size_t sm = (size_t)kWtTiles * kWtKB * kNnABytes + (size_t)kWtKB * npad * 32;
+    switch (npad) {
+        case 16: wgrad_tc_kernel<16><<<grid, 128, sm, st>>>(in, gout, nz, ny, nx, cin, cout, mtiles, (int)per, part); break;
+        case 32: wgrad_tc_kernel<32><<<grid, 128, sm, st>>>(in, gout, nz, ny, nx, cin, cout, mtiles, (int)per, part); break;
+        case 64: wgrad_tc_kernel<64><<<grid, 128, sm, st>>>(in, gout, nz, ny, nx, cin, cout, mtiles, (int)per, part); break;
+        default: wgrad_tc_kernel<128><<<grid, 128, sm, st>>>(in, gout, nz, ny, nx, cin, cout, mtiles, (int)per, part); break;
     }
     CS_LAUNCH_CHECK();
-    wsum_kernel<<<nn_grid(wsize), 256, 0, st>>>(part, gx, wsize, wsize, gw);
+    wgrad_sum_kernel<<<nn_grid((int64_t)rows * cout), 256, 0, st>>>(part, nslots, mrows, npad, rows, cout, gw);
     CS_LAUNCH_CHECK();
     if (gb) {
-        wsum_kernel<<<1, 256, 0, st>>>(pb, gx, cout, cout, gb);
+        bias_part_kernel<<<nbias, 128, 0, st>>>(gout, nvox, cout, bper, pb);
+        CS_LAUNCH_CHECK();
+        wsum_kernel<<<1, 256, 0, st>>>(pb, nbias, cout, cout, gb);
         CS_LAUNCH_CHECK();
     }
     CS_TRY_CUDA(cudaFreeAsync(part, st));

@@ -88,6 +88,41 @@ def test_conv3d_matches_reference(cin, cout, flip, dims):
         assert _rel(gb.cpu().numpy(), gb_ref) < 1e-5
 
 
+@pytest.mark.parametrize("cin,cout,dims", [
+    (16, 16, (5, 11, 30)),      # 4 row tiles, one tile group
+    (4, 16, (6, 8, 14)),        # one partial row tile (108 rows)
+    (32, 64, (7, 9, 17)),       # 7 row tiles: two tile groups
+    (64, 32, (16, 20, 24)),     # 14 row tiles, 120 voxel rounds over many partial-sum slots
+    (128, 100, (3, 5, 9)),      # 27 row tiles, 128-column accumulators, ragged channels
+    (3, 5, (4, 7, 9)),          # channels not a multiple of 4
+])
+def test_conv3d_weight_gradient_on_tensor_cores(cin, cout, dims):
+    """cs_nn_conv3d_wgrad (BF16 implicit GEMM on tcgen05, voxels as the reduction) against the FP64
+    weight gradient of the same BF16-rounded operands, accumulated into a non-zero gw; the bias
+    gradient in FP32; two runs bit-identical (partial sums added in slot order)."""
+    import paper_2305_06482_gb300 as cs
+    rng = np.random.default_rng(cin * 1000 + cout)
+    x = rng.standard_normal(dims + (cin,)).astype(np.float32)
+    go = rng.standard_normal(dims + (cout,)).astype(np.float32)
+    w = np.zeros((cout, 27, cin), np.float32)
+    _, gw_ref, gb_ref = cnn.conv3d_bwd(x, w, go, bf16=True)
+    gw0 = rng.standard_normal((cout, 27, cin)).astype(np.float32)
+    gb0 = rng.standard_normal(cout).astype(np.float32)
+    xt = torch.from_numpy(x.reshape(-1, cin)).cuda()
+    gt = torch.from_numpy(go.reshape(-1, cout)).cuda()
+    outs = []
+    for _ in range(2):
+        gw = torch.from_numpy(gw0.copy()).cuda()
+        gb = torch.from_numpy(gb0.copy()).cuda()
+        cs._check(cs.lib().cs_nn_conv3d_wgrad(cs._ptr(xt), cs._ptr(gt), *dims, cin, cout, cs._ptr(gw), cs._ptr(gb),
+                                              None))
+        cs._check(cs.lib().cs_nn_status(None))
+        outs.append((gw.cpu().numpy(), gb.cpu().numpy()))
+    assert _rel(outs[0][0] - gw0, gw_ref) < 1e-5
+    assert _rel(outs[0][1] - gb0, gb_ref) < 1e-5
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
 def test_upconv_and_slice_general_paths():
     """The transposed convolution and the channel slice on channel counts and offsets that are not
     multiples of 4 (their scalar paths), against the reference and numpy."""

@@ -104,3 +104,20 @@ def test_unet_gradients_match_finite_differences():
 def test_unet_parameter_count():
     n = sum(int(np.prod(s)) for s in cnn.unet_shapes())
     assert 330_000 < n < 350_000        # the configured network's ~0.34 M weights
+
+
+def test_bf16_weight_gradient_is_the_fp64_gradient_of_the_rounded_operands():
+    """conv3d_bwd with bf16=True: the weight gradient is the exact gradient taken at the BF16-
+    rounded input and output gradient (the tensor-core GEMM's operands), the data gradient uses the
+    rounded weights and output gradient, and the bias gradient the unrounded output gradient."""
+    from oracle.philox import round_to_bf16
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((3, 4, 5, 6)).astype(np.float32)
+    w = rng.standard_normal((7, 27, 6)).astype(np.float32)
+    g = rng.standard_normal((3, 4, 5, 7)).astype(np.float32)
+    r = lambda a: round_to_bf16(a).astype(np.float32)
+    gx, gw, gb = cnn.conv3d_bwd(x, w, g, bf16=True)
+    gx0, gw0, _ = cnn.conv3d_bwd(r(x), r(w), r(g), bf16=False)
+    _, _, gb0 = cnn.conv3d_bwd(x, w, g, bf16=False)
+    assert np.array_equal(gw, gw0) and np.array_equal(gx, gx0) and np.array_equal(gb, gb0)
+    assert np.abs(gw - cnn.conv3d_bwd(x, w, g)[1]).max() > 0       # the rounding is visible
