@@ -43,11 +43,12 @@ stream), for profiling individual kernels with small launch counts.
       its shape (BF16 implicit GEMM on the tensor cores), one whole inference on the image size of
       the workload, and one training step (forward, backward, Adam) on a 64^3 crop
   python -m paper_2305_06482_gb300.microbench warmtrain [--config cones3d_128|cones3d_large] [--phantoms P]
-          [--outer T] [--K K] [--tight M] [--train-steps N] [--ref-iters R] [--save PATH]
+          [--outer T] [--K K] [--tight M] [--train-steps N] [--crops Q] [--ref-iters R] [--save PATH]
       the warm start trained on the method's own pairs: (x^t, d, sub-problem solved with M FISTA
       iterations) from T outer iterations of Algorithm 1 (K inner) on P seeded phantoms (l1-db4
       lambda 2e-3, m = 8 = 4 PCA + 4 Gaussian on cones3d_128, m = 10 = 5 + 5 on cones3d_large),
-      N Adam steps on random 64^3 crops, optionally saved; then a held-out phantom through
+      N Adam steps on random 64^3 crops (with Q > 0: on Q stored crops drawn once), optionally
+      saved; then a held-out phantom through
       recon_solve with and without the warm start (decision on the device): NRMSE to x_inf (R
       plain iterations) per outer iteration, acceptances, device time per reconstruction
   python -m paper_2305_06482_gb300.microbench cart2d [--iters N]
@@ -560,10 +561,16 @@ def warmtrain(args):
         pairs += pr
     torch.cuda.synchronize()
     t_pairs = time.perf_counter() - t0
+    npairs = len(pairs)
+    if args.crops > 0:
+        # the training set stored as fixed 64^3 crops of the volume pairs
+        pairs = ws.make_crops(pairs, args.crops, (64, 64, 64), seed=7)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
     net = ws.UNet(seed=0)
     a, b = _events()
     a.record()
-    hist = ws.train(net, pairs, steps=args.train_steps, lr=2e-3, crop=(64, 64, 64))
+    hist = ws.train(net, pairs, steps=args.train_steps, lr=2e-3, crop=None if args.crops > 0 else (64, 64, 64))
     b.record()
     torch.cuda.synchronize()
     t_train = a.elapsed_time(b) / 1e3
@@ -592,9 +599,10 @@ def warmtrain(args):
         torch.cuda.synchronize()
         tr = st["trace"]
         res[name] = (np.sqrt(np.maximum(tr[:, cs.TRACE_DIST2], 0)), tr[:, cs.TRACE_ACCEPT], a.elapsed_time(b))
-    print(f"warm start on {args.config} ({img}, {C} coils, m = {V} + {S}): {T * args.phantoms} training pairs "
+    crops = f"{args.crops} stored 64^3 crops of them" if args.crops > 0 else "random 64^3 crops"
+    print(f"warm start on {args.config} ({img}, {C} coils, m = {V} + {S}): {npairs} training pairs "
           f"(x^t, d, sub-problem solved with {tight} FISTA iterations) from {args.phantoms} phantoms at K = {K} in "
-          f"{t_pairs:.1f} s; {args.train_steps} Adam steps on random 64^3 crops in {t_train:.2f} s "
+          f"{t_pairs:.1f} s; {args.train_steps} Adam steps on {crops} in {t_train:.2f} s "
           f"(loss {np.mean(hist[:20]):.3e} -> {np.mean(hist[-20:]):.3e})")
     for name in ("without", "with"):
         e, acc, ms = res[name]
@@ -661,6 +669,8 @@ def main():
     ap.add_argument("--tight", type=int, default=40, help="warmtrain: FISTA iterations of a training target")
     ap.add_argument("--ref-iters", type=int, default=300, help="warmtrain: plain FISTA iterations of x_inf")
     ap.add_argument("--save", default="", help="warmtrain: write the trained network here")
+    ap.add_argument("--crops", type=int, default=0, help="warmtrain: train on this many stored 64^3 crops (0 = "
+                                                       "a fresh random crop every step)")
     args = ap.parse_args()
     {"nufft": nufft, "normal": normal, "tv": tv, "ablation": ablation, "gfactor": gfactor, "compare": compare,
      "sketch": sketch, "cart2d": cart2d, "batched": batched, "warmnet": warmnet, "warmtrain": warmtrain,

@@ -179,6 +179,19 @@ def crop3d(x, origin, box, out=None, stream=None):
     return out
 
 
+def make_crops(pairs, n, crop, seed=0):
+    """n training pairs stored as random boxes of size crop = (cz, cy, cx) of the given volume pairs
+    (x^t, d, x_target, eta): pair and box origin drawn from a seeded generator, every box copied to
+    its own device buffers."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        xt, d, xs, eta = pairs[int(rng.integers(len(pairs)))]
+        o = [int(rng.integers(0, m - c + 1)) for m, c in zip(xt.shape, crop)]
+        out.append(tuple(crop3d(a, o, crop) for a in (xt, d, xs)) + (eta,))
+    return out
+
+
 def train(net: UNet, pairs, steps=200, lr=1e-3, seed=0, crop=None):
     """Adam on random pairs (x^t, d, x_target, eta), one volume per step; with crop = (cz, cy, cx)
     (multiples of 4) each step uses a random box of that size from the pair's volumes.  Returns
