@@ -40,6 +40,13 @@ __device__ __forceinline__ unsigned short nn_bf16(float f) {
     return (unsigned short)(b >> 16);
 }
 
+// two floats rounded to the nearest BF16 (ties to even) and packed, lo in the low half
+__device__ __forceinline__ uint32_t nn_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
 template <int NPAD>
 __global__ void __launch_bounds__(128) conv3_tc_kernel(const float* __restrict__ in, int nz, int ny, int nx, int cin,
                                                        const unsigned short* __restrict__ wpk, int kpad, int nout,
@@ -456,15 +463,18 @@ constexpr int kWtVox = 16 * kWtKB;        // voxels per round
 
 template <int NPAD>
 __global__ void __launch_bounds__(128) wgrad_tc_kernel(const float* __restrict__ in, const float* __restrict__ gout, int nz,
-                                                       int ny, int nx, int cin, int cout, int mtiles,
+                                                       int ny, int nx, int cin, int cout, int mtiles, int tpc,
                                                        int rounds_per_cta, float* __restrict__ part) {
     constexpr int kBBytes = NPAD * 16 * 2;
-    constexpr uint32_t kCols = (uint32_t)(kWtTiles * NPAD);    // 64 .. 512, a power of two
+    // tensor-memory columns: tpc accumulators of NPAD columns, rounded up to a power of two >= 32
+    uint32_t kCols = 32;
+    while (kCols < (uint32_t)(tpc * NPAD)) kCols <<= 1;
     constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NPAD >> 3) << 17) | ((uint32_t)(kNnM >> 4) << 24);
     extern __shared__ __align__(1024) unsigned char nsm[];
-    unsigned char* a_sm = nsm;                                  // [kWtTiles][kWtKB] blocks of 128 x 16
-    unsigned char* b_sm = nsm + kWtTiles * kWtKB * kNnABytes;    // [kWtKB] blocks of NPAD x 16
-    __shared__ int s_vz[kWtVox], s_vy[kWtVox], s_vx[kWtVox];
+    unsigned char* a_sm = nsm;                                  // [tpc][kWtKB] blocks of 128 x 16
+    unsigned char* b_sm = nsm + tpc * kWtKB * kNnABytes;         // [kWtKB] blocks of NPAD x 16
+    __shared__ int s_vlin[kWtVox];          // linear voxel index of the round's voxels
+    __shared__ uint32_t s_vmask[kWtVox];    // bit tap: the voxel exists and its tap neighbour is inside
     __shared__ uint32_t s_taddr;
     __shared__ __align__(8) uint64_t s_mbar;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -487,17 +497,23 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(const float* __restrict__
     const int64_t r0 = (int64_t)blockIdx.x * rounds_per_cta;
     const int64_t r1 = min(rounds, r0 + rounds_per_cta);
     const int rows = 27 * cin;
-    const int tile0 = blockIdx.y * kWtTiles;
-    const int nt = min(kWtTiles, mtiles - tile0);
+    const int tile0 = blockIdx.y * tpc;
+    const int nt = min(tpc, mtiles - tile0);
     bool failed = false;
     for (int64_t r = r0; r < r1 && !failed; ++r) {
         const int64_t v0 = r * kWtVox;
         if (tid < kWtVox) {
             const int64_t v = v0 + tid;
-            const bool ok = v < nvox;
-            s_vx[tid] = ok ? (int)(v % nx) : -4;       // out-of-range voxels fail every bounds test
-            s_vy[tid] = ok ? (int)((v / nx) % ny) : -4;
-            s_vz[tid] = ok ? (int)(v / ((int64_t)nx * ny)) : -4;
+            uint32_t mask = 0;
+            if (v < nvox) {
+                const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((int64_t)nx * ny));
+                for (int t = 0; t < 27; ++t) {
+                    const int zz = z + t / 9 - 1, yy = y + (t / 3) % 3 - 1, xx = x + t % 3 - 1;
+                    if (zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx) mask |= 1u << t;
+                }
+            }
+            s_vlin[tid] = (int)(v < nvox ? v : 0);   // volumes hold fewer than 2^31 voxels
+            s_vmask[tid] = mask;
         }
         __syncthreads();
         // B: the output gradient of the round's voxels, row n = output channel, k = voxel
@@ -509,7 +525,7 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(const float* __restrict__
                 const int j = kb * 16 + h * 8 + 2 * q;
                 const float g0 = (n < cout && v0 + j < nvox) ? gout[(v0 + j) * cout + n] : 0.f;
                 const float g1 = (n < cout && v0 + j + 1 < nvox) ? gout[(v0 + j + 1) * cout + n] : 0.f;
-                pk[q] = (uint32_t)nn_bf16(g0) | ((uint32_t)nn_bf16(g1) << 16);
+                pk[q] = nn_bf16x2(g0, g1);
             }
             *reinterpret_cast<uint4*>(b_sm + kb * kBBytes + nn_kmajor_off(n, 8 * h)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
@@ -518,7 +534,9 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(const float* __restrict__
             const int m = (tile0 + i) * kNnM + tid;
             const bool mv = m < rows;
             const int tap = mv ? m / cin : 13, ci = mv ? m - tap * cin : 0;
-            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+            const int toff = ((tap / 9 - 1) * ny + (tap / 3) % 3 - 1) * nx + tap % 3 - 1;   // linear tap offset
+            const uint32_t bit = mv ? 1u << tap : 0u;
+            const float* src = in + ci;
             for (int kb = 0; kb < kWtKB; ++kb) {
                 uint32_t pk[8];
 #pragma unroll
@@ -527,12 +545,9 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(const float* __restrict__
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         const int j = kb * 16 + 2 * q + u;
-                        const int zz = s_vz[j] + dz, yy = s_vy[j] + dy, xx = s_vx[j] + dx;
-                        a2[u] = (mv && zz >= 0 && zz < nz && yy >= 0 && yy < ny && xx >= 0 && xx < nx)
-                                    ? in[(((int64_t)zz * ny + yy) * nx + xx) * cin + ci]
-                                    : 0.f;
+                        a2[u] = (s_vmask[j] & bit) ? src[(int64_t)(s_vlin[j] + toff) * cin] : 0.f;
                     }
-                    pk[q] = (uint32_t)nn_bf16(a2[0]) | ((uint32_t)nn_bf16(a2[1]) << 16);
+                    pk[q] = nn_bf16x2(a2[0], a2[1]);
                 }
                 unsigned char* arow = a_sm + (i * kWtKB + kb) * kNnABytes + nn_kmajor_off(tid, 0);
                 *reinterpret_cast<uint4*>(arow) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
@@ -1158,11 +1173,18 @@ cs_status cs_nn_conv3d_wgrad(const float* in, const float* gout, int nz, int ny,
     cudaStream_t st = (cudaStream_t)stream;
     const int rows = 27 * cin;
     const int mtiles = (rows + kNnM - 1) / kNnM;
-    const int groups = (mtiles + kWtTiles - 1) / kWtTiles;
+    const int tpc = std::min(kWtTiles, mtiles);                 // row tiles per CTA
+    const int groups = (mtiles + tpc - 1) / tpc;
     const int npad = cout <= 16 ? 16 : cout <= 32 ? 32 : cout <= 64 ? 64 : 128;
-    // voxel rounds split so that about two CTAs per SM run; every CTA gets at least one round
+    const size_t sm = (size_t)tpc * kWtKB * kNnABytes + (size_t)kWtKB * npad * 32;
+    int cols = 32;
+    while (cols < tpc * npad) cols <<= 1;
+    // resident CTAs per SM allowed by shared and tensor memory (at most 8); the voxel rounds are
+    // split so that that many CTAs per SM run, every CTA with at least one round
+    const int per_sm = (int)std::max<size_t>(
+        1, std::min<size_t>(std::min<size_t>(8, (size_t)(220 * 1024) / (sm + 2048)), (size_t)(512 / cols)));
     const int64_t rounds = (nvox + kWtVox - 1) / kWtVox;
-    const int64_t want = std::max<int64_t>(1, (2 * 152 + groups - 1) / groups);
+    const int64_t want = std::max<int64_t>(1, ((int64_t)per_sm * 152 + groups - 1) / groups);
     const int64_t per = (rounds + std::min(rounds, want) - 1) / std::min(rounds, want);
     const int nslots = (int)((rounds + per - 1) / per);
     const int64_t mrows = (int64_t)mtiles * kNnM;
@@ -1172,12 +1194,11 @@ cs_status cs_nn_conv3d_wgrad(const float* in, const float* gout, int nz, int ny,
     CS_TRY_CUDA(cudaMallocAsync((void**)&part, sizeof(float) * ((size_t)nslots * mrows * npad + (size_t)nbias * cout), st));
     float* pb = part + (int64_t)nslots * mrows * npad;
     const dim3 grid((unsigned)nslots, (unsigned)groups);
-    const size_t sm = (size_t)kWtTiles * kWtKB * kNnABytes + (size_t)kWtKB * npad * 32;
     switch (npad) {
-        case 16: wgrad_tc_kernel<16><<<grid, 128, sm, st>>>(in, gout, nz, ny, nx, cin, cout, mtiles, (int)per, part); break;
-        case 32: wgrad_tc_kernel<32><<<grid, 128, sm, st>>>(in, gout, nz, ny, nx, cin, cout, mtiles, (int)per, part); break;
-        case 64: wgrad_tc_kernel<64><<<grid, 128, sm, st>>>(in, gout, nz, ny, nx, cin, cout, mtiles, (int)per, part); break;
-        default: wgrad_tc_kernel<128><<<grid, 128, sm, st>>>(in, gout, nz, ny, nx, cin, cout, mtiles, (int)per, part); break;
+        case 16: wgrad_tc_kernel<16><<<grid, 128, sm, st>>>(in, gout, nz, ny, nx, cin, cout, mtiles, tpc, (int)per, part); break;
+        case 32: wgrad_tc_kernel<32><<<grid, 128, sm, st>>>(in, gout, nz, ny, nx, cin, cout, mtiles, tpc, (int)per, part); break;
+        case 64: wgrad_tc_kernel<64><<<grid, 128, sm, st>>>(in, gout, nz, ny, nx, cin, cout, mtiles, tpc, (int)per, part); break;
+        default: wgrad_tc_kernel<128><<<grid, 128, sm, st>>>(in, gout, nz, ny, nx, cin, cout, mtiles, tpc, (int)per, part); break;
     }
     CS_LAUNCH_CHECK();
     wgrad_sum_kernel<<<nn_grid((int64_t)rows * cout), 256, 0, st>>>(part, nslots, mrows, npad, rows, cout, gw);

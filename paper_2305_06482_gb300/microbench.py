@@ -484,7 +484,12 @@ def warmnet(args):
         total_flops += fl
         print(f"  layer {name:3s} {cin:2d}->{cout:2d} on {dims}: {ms:.3f} ms, {fl / ms / 1e9:.1f} TFLOP/s "
               f"({fl / ms / 1e9 / peak:.3f} of peak)")
-        del x, out
+        gw = torch.zeros((cout, 27, cin), device=dev)
+        gb = torch.zeros(cout, device=dev)
+        msw = timed(lambda: cs._check(L.cs_nn_conv3d_wgrad(cs._ptr(x), cs._ptr(out), *dims, cin, cout, cs._ptr(gw),
+                                                           cs._ptr(gb), None)))
+        print(f"        weight gradient: {msw:.3f} ms, {fl / msw / 1e9:.1f} TFLOP/s ({fl / msw / 1e9 / peak:.3f} of peak)")
+        del x, out, gw, gb
     for cdims, cin, cout in ((lv[2], c3, c2), (lv[1], c2, c1)):
         Vc = int(np.prod(cdims))
         x = torch.randn((Vc, cin), generator=gen, device=dev)
