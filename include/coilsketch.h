@@ -189,7 +189,8 @@ cs_status sketched_normal_apply(const cs_plan* plan, const float* v, const float
 /* ------------------------------------------------------------------------------------------
  * coil_pca: SVD-based coil compression of the k-space data (Sec. 3.1, Algorithm 1 "perform
  * coil compression").  R = Y Y^H over all N samples of y [C][N] (complex64 data, FP32 blocked
- * accumulation, FP64 block sums), then a FP64 cyclic Jacobi eigendecomposition on the GPU.
+ * accumulation, FP64 block sums added in a fixed order, so R and U are bit-reproducible), then
+ * a FP64 cyclic Jacobi eigendecomposition on the GPU.  recon_solve's PCA is the same.
  *   U    [C][C] complex64 (column k = eigenvector k; row-major U[c*C + k]), eigenvalues
  *        descending, each column's largest-magnitude entry made real positive;
  *   eig  [C] float64 eigenvalues, descending.

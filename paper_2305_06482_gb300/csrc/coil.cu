@@ -78,11 +78,14 @@ __global__ void sketch_draw_kernel(uint32_t k0, uint32_t k1, int t0, int T, int 
 
 // ------------------------------------------------------------------------------------------
 // coil covariance R = Y Y^H: 4x4 coil blocks per thread, FP32 within a 128-sample tile, FP64
-// across tiles and CTAs (atomicAdd on doubles into R, complex128 [C][C], upper blocks only).
+// across tiles and CTAs, complex128 [C][C], upper blocks only.  With part == nullptr the thread
+// sums go into R with atomic adds (order of the additions set by scheduling); otherwise every
+// thread writes its 4x4 block to its own slot part[CTA][thread][16][2] and cov_reduce_kernel adds
+// the slots in a fixed order, so R is bit-reproducible.
 constexpr int kCovTile = 128;
 
 __global__ void __launch_bounds__(256) cov_kernel(const float2* __restrict__ y, int C, int64_t N,
-                                                  double* __restrict__ R) {
+                                                  double* __restrict__ R, double* __restrict__ part) {
     extern __shared__ float2 tile[];  // [C][kCovTile]
     const int nb = (C + 3) / 4;
     const int npairs = nb * (nb + 1) / 2;
@@ -144,6 +147,17 @@ __global__ void __launch_bounds__(256) cov_kernel(const float2* __restrict__ y, 
             }
     }
     if (!active) return;
+    if (part) {
+        double* slot = part + ((int64_t)blockIdx.x * blockDim.x + tid) * 32;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                slot[(a * 4 + b) * 2 + 0] = accd[a][b][0];
+                slot[(a * 4 + b) * 2 + 1] = accd[a][b][1];
+            }
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -154,6 +168,31 @@ __global__ void __launch_bounds__(256) cov_kernel(const float2* __restrict__ y, 
                 atomicAdd(&R[2 * (ca * C + cb) + 1], accd[a][b][1]);
             }
         }
+}
+
+// R[ca][cb] (ca <= cb) = sum over CTAs, then over the thread groups of a CTA, of the slots that
+// hold block pair (ca / 4, cb / 4), in that order
+__global__ void cov_reduce_kernel(const double* __restrict__ part, int nblocks, int threads, int C,
+                                  double* __restrict__ R) {
+    const int nb = (C + 3) / 4;
+    const int npairs = nb * (nb + 1) / 2;
+    const int groups = max(1, threads / npairs);
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= C * C) return;
+    const int ca = e / C, cb = e % C;
+    if (ca > cb) return;
+    const int bi = ca / 4, bj = cb / 4, a = ca % 4, b = cb % 4;
+    int pair = bj - bi;                      // the kernel's pair numbering: row bi, column bj >= bi
+    for (int i = 0; i < bi; ++i) pair += nb - i;
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < nblocks; ++k)
+        for (int g = 0; g < groups; ++g) {
+            const double* slot = part + ((int64_t)k * threads + g * npairs + pair) * 32 + (a * 4 + b) * 2;
+            re += slot[0];
+            im += slot[1];
+        }
+    R[2 * e + 0] = re;
+    R[2 * e + 1] = im;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -504,16 +543,47 @@ cs_status bounds_check_all() {
     return fft_bounds_check();
 }
 
-cs_status coil_pca_impl(const float2* y, int C, int64_t N, float2* U, double* eig, double* Rws, cudaStream_t st) {
-    CS_TRY_CUDA(cudaMemsetAsync(Rws, 0, sizeof(double) * 2 * C * C, st));
+static void cov_launch_shape(int C, int64_t N, int* threads, int* grid) {
     const int nb = (C + 3) / 4;
     const int npairs = nb * (nb + 1) / 2;
-    const int threads = npairs > 256 ? ((npairs + 31) / 32) * 32 : 256;
+    *threads = npairs > 256 ? ((npairs + 31) / 32) * 32 : 256;
+    const int64_t tiles = (N + kCovTile - 1) / kCovTile;
+    *grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sm_count() * 4));
+}
+
+// doubles of the slot array of the bit-reproducible covariance
+int64_t coil_cov_part_size(int C, int64_t N) {
+    int threads = 0, grid = 0;
+    cov_launch_shape(C, N, &threads, &grid);
+    return (int64_t)grid * threads * 32;
+}
+
+// coil PCA with the covariance accumulated by atomic adds (no slot array; coil_pca_noalloc)
+cs_status coil_pca_impl(const float2* y, int C, int64_t N, float2* U, double* eig, double* Rws, cudaStream_t st) {
+    CS_TRY_CUDA(cudaMemsetAsync(Rws, 0, sizeof(double) * 2 * C * C, st));
+    int threads = 0, grid = 0;
+    cov_launch_shape(C, N, &threads, &grid);
     CS_REQUIRE(threads <= 1024, CS_ERR_UNSUPPORTED_SIZE, "too many coils for coil_pca");
     const size_t sm = sizeof(float2) * C * kCovTile;
-    int64_t tiles = (N + kCovTile - 1) / kCovTile;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sm_count() * 4));
-    cov_kernel<<<grid, threads, sm, st>>>(y, C, N, Rws);
+    cov_kernel<<<grid, threads, sm, st>>>(y, C, N, Rws, nullptr);
+    CS_LAUNCH_CHECK();
+    const size_t jsm = sizeof(double) * 4 * C * C;
+    jacobi_kernel<<<1, 256, jsm, st>>>(Rws, C, U, eig);
+    CS_LAUNCH_CHECK();
+    return CS_OK;
+}
+
+// coil PCA with the bit-reproducible covariance: `part` holds coil_cov_part_size(C, N) doubles
+cs_status coil_pca_det_impl(const float2* y, int C, int64_t N, float2* U, double* eig, double* Rws, double* part,
+                            cudaStream_t st) {
+    int threads = 0, grid = 0;
+    cov_launch_shape(C, N, &threads, &grid);
+    CS_REQUIRE(threads <= 1024, CS_ERR_UNSUPPORTED_SIZE, "too many coils for coil_pca");
+    CS_TRY_CUDA(cudaMemsetAsync(Rws, 0, sizeof(double) * 2 * C * C, st));
+    const size_t sm = sizeof(float2) * C * kCovTile;
+    cov_kernel<<<grid, threads, sm, st>>>(y, C, N, Rws, part);
+    CS_LAUNCH_CHECK();
+    cov_reduce_kernel<<<(C * C + 255) / 256, 256, 0, st>>>(part, grid, threads, C, Rws);
     CS_LAUNCH_CHECK();
     const size_t jsm = sizeof(double) * 4 * C * C;
     jacobi_kernel<<<1, 256, jsm, st>>>(Rws, C, U, eig);
@@ -636,8 +706,9 @@ cs_status coil_pca(const float* y, int C, int64_t N, float* U, double* eig, void
     cudaStream_t st = (cudaStream_t)stream;
     CS_PROPAGATE(coil_attrs_once());
     double* R = nullptr;
-    CS_TRY_CUDA(cudaMallocAsync(&R, sizeof(double) * 2 * C * C, st));
-    cs_status rc = coil_pca_impl((const float2*)y, C, N, (float2*)U, eig, R, st);
+    const int64_t np = coil_cov_part_size(C, N);
+    CS_TRY_CUDA(cudaMallocAsync(&R, sizeof(double) * (2 * C * C + np), st));
+    cs_status rc = coil_pca_det_impl((const float2*)y, C, N, (float2*)U, eig, R, R + 2 * C * C, st);
     cudaFreeAsync(R, st);
     return rc;
 }

@@ -17,7 +17,9 @@ cs_status sketch_draw_impl(uint64_t seed, int t0, int T, int C, int V, int S, in
                            cudaStream_t st);
 cs_status sketched_maps_impl(const float* S, const int* tsel, const float2* mrot, int64_t D, int C, int V, int Sn,
                              int precision, float2* out, cudaStream_t st);
-cs_status coil_pca_impl(const float2* y, int C, int64_t N, float2* U, double* eig, double* Rws, cudaStream_t st);
+cs_status coil_pca_det_impl(const float2* y, int C, int64_t N, float2* U, double* eig, double* Rws, double* part,
+                            cudaStream_t st);
+int64_t coil_cov_part_size(int C, int64_t N);
 cs_status coil_rotate_impl(const float2* U, const float2* in, int C, int Cout, int64_t L, float2* out, cudaStream_t st);
 cs_status tc_check_and_clear();
 
@@ -876,7 +878,8 @@ struct SolverWS {
         CS_PROPAGATE(get(&partB, kRedBlocks));
         CS_PROPAGATE(get(&U, (size_t)C * C));
         CS_PROPAGATE(get(&eig, (size_t)C));
-        CS_PROPAGATE(get(&Rws, (size_t)2 * C * C));
+        // the FP64 covariance followed by the slot array of its fixed-order reduction
+        CS_PROPAGATE(get(&Rws, (size_t)(2 * C * C + coil_cov_part_size(C, N))));
         CS_PROPAGATE(get(&maps_r, (size_t)C * D));
         CS_PROPAGATE(get(&y_r, (size_t)C * N));
         for (float2** v : {&d, &hp, &u, &z, &xp, &gr, &xt, &r, &pv}) CS_PROPAGATE(get(v, (size_t)D));
@@ -1153,7 +1156,7 @@ static cs_status recon_enqueue(cs_plan* p, const cs_problem* pr, const cs_solve_
     const float2* maps = (const float2*)pr->maps;
     const float2* y = (const float2*)pr->y;
     if (sp->do_pca) {
-        CS_PROPAGATE(coil_pca_impl(y, C, N, ws->U, ws->eig, ws->Rws, st));
+        CS_PROPAGATE(coil_pca_det_impl(y, C, N, ws->U, ws->eig, ws->Rws, ws->Rws + 2 * C * C, st));
         CS_PROPAGATE(coil_rotate_impl(ws->U, maps, C, C, D, ws->maps_r, st));
         CS_PROPAGATE(coil_rotate_impl(ws->U, y, C, C, N, ws->y_r, st));
         maps = ws->maps_r;

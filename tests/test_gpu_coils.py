@@ -29,6 +29,9 @@ def test_coil_pca(C, N):
     # distinct eigenvalues: eigenvectors agree after the shared phase convention
     assert np.abs(Ug - Ur).max() < 1e-3
     assert np.allclose(Ug.conj().T @ Ug, np.eye(C), atol=1e-5)
+    # the FP64 block sums are added in a fixed order: a second call is bit-identical
+    U2, eig2 = cs.coil_pca(t(y))
+    assert torch.equal(U2, U) and torch.equal(eig2, eig)
 
 
 def test_coil_rotate():
