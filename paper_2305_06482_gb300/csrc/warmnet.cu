@@ -629,23 +629,36 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(const float* __restrict__
 // gw[co][m] += sum over the partial-sum slots (in slot order) of part[slot][m][co]
 __global__ void wgrad_sum_kernel(const float* __restrict__ part, int nslots, int64_t mrows, int npad, int rows, int cout,
                                  float* __restrict__ gw) {
+    // one warp per gw entry: lane l adds slots l, l + 32, ... in order, then a fixed shuffle tree
+    const int lane = threadIdx.x & 31;
     const int64_t n = (int64_t)rows * cout;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < n;
+         e += ((int64_t)gridDim.x * blockDim.x) >> 5) {
         const int co = (int)(e / rows), m = (int)(e % rows);
         float acc = 0.f;
-        for (int s = 0; s < nslots; ++s) acc += part[((int64_t)s * mrows + m) * npad + co];
-        gw[e] += acc;
+        for (int s = lane; s < nslots; s += 32) acc += part[((int64_t)s * mrows + m) * npad + co];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) gw[e] += acc;
     }
 }
 
-// bias gradient partials: part[block][co] = sum of gout[v][co] over the block's contiguous voxel range
+// bias gradient partials: part[block][co] = sum of gout[v][co] over the block's contiguous voxel
+// range; the block's lanes (threads with the same co) take voxels in turn and are added in lane order
 __global__ void bias_part_kernel(const float* __restrict__ gout, int64_t nvox, int cout, int64_t per_block,
                                  float* __restrict__ part) {
+    __shared__ float red[256];
+    const int lanes = max(1, (int)blockDim.x / cout);
+    const int co = threadIdx.x % cout, l = threadIdx.x / cout;
     const int64_t v0 = (int64_t)blockIdx.x * per_block, v1 = min(nvox, v0 + per_block);
-    for (int co = threadIdx.x; co < cout; co += blockDim.x) {
-        float acc = 0.f;
-        for (int64_t v = v0; v < v1; ++v) acc += gout[v * cout + co];
-        part[(int64_t)blockIdx.x * cout + co] = acc;
+    float acc = 0.f;
+    if (l < lanes)
+        for (int64_t v = v0 + l; v < v1; v += lanes) acc += gout[v * cout + co];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < cout) {
+        float t = 0.f;
+        for (int k = 0; k < lanes; ++k) t += red[k * cout + threadIdx.x];
+        part[(int64_t)blockIdx.x * cout + threadIdx.x] = t;
     }
 }
 
@@ -1188,7 +1201,7 @@ cs_status cs_nn_conv3d_wgrad(const float* in, const float* gout, int nz, int ny,
     const int64_t per = (rounds + std::min(rounds, want) - 1) / std::min(rounds, want);
     const int nslots = (int)((rounds + per - 1) / per);
     const int64_t mrows = (int64_t)mtiles * kNnM;
-    const int nbias = (int)std::min<int64_t>(nvox, 64);
+    const int nbias = (int)std::max<int64_t>(1, std::min<int64_t>((nvox + 511) / 512, 1024));
     const int64_t bper = (nvox + nbias - 1) / nbias;
     float* part = nullptr;
     CS_TRY_CUDA(cudaMallocAsync((void**)&part, sizeof(float) * ((size_t)nslots * mrows * npad + (size_t)nbias * cout), st));
@@ -1201,10 +1214,11 @@ cs_status cs_nn_conv3d_wgrad(const float* in, const float* gout, int nz, int ny,
         default: wgrad_tc_kernel<128><<<grid, 128, sm, st>>>(in, gout, nz, ny, nx, cin, cout, mtiles, tpc, (int)per, part); break;
     }
     CS_LAUNCH_CHECK();
-    wgrad_sum_kernel<<<nn_grid((int64_t)rows * cout), 256, 0, st>>>(part, nslots, mrows, npad, rows, cout, gw);
+    wgrad_sum_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)rows * cout + 7) / 8, 4096)), 256, 0,
+                       st>>>(part, nslots, mrows, npad, rows, cout, gw);
     CS_LAUNCH_CHECK();
     if (gb) {
-        bias_part_kernel<<<nbias, 128, 0, st>>>(gout, nvox, cout, bper, pb);
+        bias_part_kernel<<<nbias, 256, 0, st>>>(gout, nvox, cout, bper, pb);
         CS_LAUNCH_CHECK();
         wsum_kernel<<<1, 256, 0, st>>>(pb, nbias, cout, cout, gb);
         CS_LAUNCH_CHECK();
