@@ -481,6 +481,16 @@ def run_native(args, w, rank, world, local_rank):
         x_h.copy_(xo, non_blocking=True)
         torch.cuda.synchronize()
 
+    # the host link alone: the same pinned host-to-device copies, timed with CUDA events
+    ce0, ce1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    y_d.copy_(y_h, non_blocking=True)
+    torch.cuda.synchronize()
+    ce0.record(stream)
+    y_d.copy_(y_h, non_blocking=True)
+    maps_d.copy_(maps_h, non_blocking=True)
+    ce1.record(stream)
+    torch.cuda.synchronize()
+    h2d_copy_ms = ce0.elapsed_time(ce1)
     e2e_steps = max(1, min(args.steps, 2))
     e2e_step()
     t0 = time.perf_counter()
@@ -515,7 +525,9 @@ def run_native(args, w, rank, world, local_rank):
                "x_inf": f"plain full-coil FISTA, {w['ref_iters']} iterations ({ref_s:.1f} s untimed)",
                "plan_s": plan_s, "tile": tile, "tile_candidates_ms": dict(zip(map(str, TILE_CANDIDATES),
                                                                              [round(v, 3) for v in tile_ms])),
-               "tile_tune_s": tile_s, "setup_s": setup_s, "L_full": st_inf["L"], "e2e_steps": e2e_steps}
+               "tile_tune_s": tile_s, "setup_s": setup_s, "L_full": st_inf["L"], "e2e_steps": e2e_steps,
+               "h2d_copy_ms": h2d_copy_ms,
+               "h2d_copy_gbs": (y.numel() + maps.numel()) * 8 / (h2d_copy_ms * 1e-3) / 1e9}
         line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
