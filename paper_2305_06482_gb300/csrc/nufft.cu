@@ -802,6 +802,274 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
     for (int p = 0; p < P; ++p) flush_plane(p);
 }
 
+// Two coils per lane (3D plans, chunks of 10 .. 16 coils with even coil offsets and an even
+// interleave stride): lanes are (coil pair, z-slice), 4 lanes per pair with one plane each.  The
+// two coils of a pair are adjacent in the coil-interleaved grid, so every window point is one
+// 16-byte value: a leaving row or column is written with half as many (vector) atomic adds, an
+// entering one read with half as many loads, for the same lanes and registers as two planes of
+// one coil.  Value layout (x, y) = coil c, (z, w) = coil c + 1.
+__device__ __forceinline__ float4 f4scale(float4 a, float s) { return make_float4(a.x * s, a.y * s, a.z * s, a.w * s); }
+__device__ __forceinline__ float4 f4fma(float w, float4 v, float4 acc) {
+    const float2 ww = make_float2(w, w);
+    const float2 lo = __ffma2_rn(ww, make_float2(v.x, v.y), make_float2(acc.x, acc.y));
+    const float2 hi = __ffma2_rn(ww, make_float2(v.z, v.w), make_float2(acc.z, acc.w));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+__device__ __forceinline__ float4 gridld4(const float2* __restrict__ g, int c, int off, int64_t glim) {
+    return CS_INB((int64_t)c + 1 + off, glim) ? __ldg(reinterpret_cast<const float4*>(g + off))
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+struct Win4 {
+    float4 v[kW][kW];
+    int zc, zoff;
+    int yoff[kW], xoff[kW];
+};
+
+__global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB_P2)
+    interp_pair_kernel(GridArgs A, int mode, const float2* __restrict__ ysub, float2* __restrict__ out) {
+    __shared__ __align__(16) float srec[kGridWarps * kStage * kRec];
+    const int lane = threadIdx.x & 31;
+    const int pair_l = lane >> 2, slice = lane & 3;
+    const bool active = 2 * pair_l < A.gsize;
+    const int c = A.c0 + 2 * (active ? pair_l : 0);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t s0l = warp * A.chunk;
+    if (s0l >= A.N) return;
+    const int s0 = (int)s0l, s1 = (int)min(A.N, s0l + A.chunk);
+    float* wrec = srec + (threadIdx.x >> 5) * (kStage * kRec);
+    const int sy = A.Gx * A.C, sz = A.Gy * A.Gx * A.C;
+    const float2* g = A.grid + c;
+    const int64_t glim = (int64_t)A.Gz * A.Gy * A.Gx * A.C;
+    (void)glim;
+    Win4 W;
+    W.zc = kNoPlane;
+    W.zoff = 0;
+#pragma unroll
+    for (int b = 0; b < kW; ++b)
+#pragma unroll
+        for (int d = 0; d < kW; ++d) W.v[b][d] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < kW; ++r) W.yoff[r] = W.xoff[r] = 0;
+    int cy = kNoPlane, cx = kNoPlane;
+    for (int base = s0; base < s1; base += kStage) {
+        const int n = min(kStage, s1 - base);
+        stage_records(A.rec, base, n, wrec, lane, A.N);
+#pragma unroll 1
+        for (int i = 0; i < n; ++i) {
+            const float* r = wrec + i * kRec;
+            const BoxHead B = box_head(r);
+            const int dy = B.jy - cy, dx = B.jx - cx;
+            if ((unsigned)(dy + 1) > 2u || (unsigned)(dx + 1) > 2u) {
+                set_offsets(W.yoff, B.jy, A.Gy, sy);
+                set_offsets(W.xoff, B.jx, A.Gx, A.C);
+                W.zc = kNoPlane;
+            } else {
+                if (dy != 0) {
+                    const int rr = (dy > 0) ? (cy & 3) : ((cy + 3) & 3);
+                    const int ynew = (dy > 0) ? cy + 4 : cy - 1;
+                    with_residue(rr, [&](auto RC) {
+                        constexpr int R = decltype(RC)::value;
+                        W.yoff[R] = wrapc(ynew, A.Gy) * sy;
+                        if (active && W.zc != kNoPlane) {
+#pragma unroll
+                            for (int d = 0; d < kW; ++d) W.v[R][d] = gridld4(g, c, W.zoff + W.yoff[R] + W.xoff[d], glim);
+                        }
+                    });
+                }
+                if (dx != 0) {
+                    const int rr = (dx > 0) ? (cx & 3) : ((cx + 3) & 3);
+                    const int xnew = (dx > 0) ? cx + 4 : cx - 1;
+                    with_residue(rr, [&](auto RC) {
+                        constexpr int R = decltype(RC)::value;
+                        W.xoff[R] = wrapc(xnew, A.Gx) * A.C;
+                        if (active && W.zc != kNoPlane) {
+#pragma unroll
+                            for (int b = 0; b < kW; ++b) W.v[b][R] = gridld4(g, c, W.zoff + W.yoff[b] + W.xoff[R], glim);
+                        }
+                    });
+                }
+            }
+            cy = B.jy;
+            cx = B.jx;
+            const int zq = B.jz + ((slice - B.jz) & 3);
+            if (zq != W.zc) {
+                W.zc = zq;
+                W.zoff = wrapc(zq, A.Gz) * sz;
+                if (active) {
+#pragma unroll
+                    for (int b = 0; b < kW; ++b)
+#pragma unroll
+                        for (int d = 0; d < kW; ++d) W.v[b][d] = gridld4(g, c, W.zoff + W.yoff[b] + W.xoff[d], glim);
+                }
+            }
+            const float4 wy = *reinterpret_cast<const float4*>(r + 4);
+            const float4 wx = *reinterpret_cast<const float4*>(r + 8);
+            const float wyv[kW] = {wy.x, wy.y, wy.z, wy.w};
+            const float wxv[kW] = {wx.x, wx.y, wx.z, wx.w};
+            float4 pa = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int b = 0; b < kW; ++b) {
+                float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int d = 0; d < kW; ++d) t = f4fma(wxv[d], W.v[b][d], t);
+                pa = f4fma(wyv[b], t, pa);
+            }
+            float4 acc = f4scale(pa, r[slice]);
+#pragma unroll
+            for (int o = 1; o < 4; o <<= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+                acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+                acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+            }
+            if (active && slice == 0) {
+                const int64_t s = (int64_t)base + i;
+                acc = f4scale(acc, B.sw);
+                const int64_t lim = (int64_t)A.C * A.N;
+                if (mode == OUT_USER) {
+                    if (CS_INB((int64_t)(c + 1) * A.N + B.perm, lim)) {
+                        out[(int64_t)c * A.N + B.perm] = make_float2(acc.x, acc.y);
+                        out[(int64_t)(c + 1) * A.N + B.perm] = make_float2(acc.z, acc.w);
+                    }
+                } else if (mode == OUT_RESID) {
+                    if (CS_INB(s * A.C + c + 1, lim) && CS_INB((int64_t)(c + 1) * A.N + B.perm, lim)) {
+                        const float2 y0 = ysub[(int64_t)c * A.N + B.perm], y1 = ysub[(int64_t)(c + 1) * A.N + B.perm];
+                        *reinterpret_cast<float4*>(out + s * A.C + c) = make_float4(acc.x - y0.x, acc.y - y0.y, acc.z - y1.x, acc.w - y1.y);
+                    }
+                } else {
+                    if (CS_INB(s * A.C + c + 1, lim)) *reinterpret_cast<float4*>(out + s * A.C + c) = acc;
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB_P2)
+    spread_pair_kernel(GridArgs A, const float2* __restrict__ yin, int sorted_in) {
+    __shared__ __align__(16) float srec[kGridWarps * kStage * kRec];
+    const int lane = threadIdx.x & 31;
+    const int pair_l = lane >> 2, slice = lane & 3;
+    const bool active = 2 * pair_l < A.gsize;
+    const int c = A.c0 + 2 * (active ? pair_l : 0);
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t s0l = warp * A.chunk;
+    if (s0l >= A.N) return;
+    const int s0 = (int)s0l, s1 = (int)min(A.N, s0l + A.chunk);
+    float* wrec = srec + (threadIdx.x >> 5) * (kStage * kRec);
+    const int sy = A.Gx * A.C, sz = A.Gy * A.Gx * A.C;
+    float2* g = A.grid + c;
+    const int64_t glim = (int64_t)A.Gz * A.Gy * A.Gx * A.C;
+    (void)glim;
+    Win4 W;
+    W.zc = kNoPlane;
+    W.zoff = 0;
+#pragma unroll
+    for (int b = 0; b < kW; ++b)
+#pragma unroll
+        for (int d = 0; d < kW; ++d) W.v[b][d] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < kW; ++r) W.yoff[r] = W.xoff[r] = 0;
+    int cy = kNoPlane, cx = kNoPlane;
+    auto add4 = [&](int off, float4 v) {
+        if (CS_INB((int64_t)c + 1 + off, glim)) atomicAdd(reinterpret_cast<float4*>(g + off), v);
+    };
+    auto flush_plane = [&]() {
+        if (active && W.zc != kNoPlane) {
+#pragma unroll
+            for (int b = 0; b < kW; ++b)
+#pragma unroll
+                for (int d = 0; d < kW; ++d) add4(W.zoff + W.yoff[b] + W.xoff[d], W.v[b][d]);
+        }
+#pragma unroll
+        for (int b = 0; b < kW; ++b)
+#pragma unroll
+            for (int d = 0; d < kW; ++d) W.v[b][d] = make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    // the pair's two sample values: sorted scratch [N][C] (one 16-byte load) or user order [C][N]
+    auto load_v = [&](int s, const float* r) -> float4 {
+        if (!active) return make_float4(0.f, 0.f, 0.f, 0.f);
+        if (sorted_in) {
+            const int64_t i = (int64_t)s * A.C + c;
+            return CS_INB(i + 1, (int64_t)A.C * A.N) ? *reinterpret_cast<const float4*>(yin + i)
+                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const int64_t i = (int64_t)c * A.N + __float_as_int(r[14]);
+        if (!CS_INB(i + A.N, (int64_t)A.C * A.N)) return make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2 a = yin[i], b = yin[i + A.N];
+        return make_float4(a.x, a.y, b.x, b.y);
+    };
+    for (int base = s0; base < s1; base += kStage) {
+        const int n = min(kStage, s1 - base);
+        stage_records(A.rec, base, n, wrec, lane, A.N);
+        float4 vnext = load_v(base, wrec);
+        BoxHead Bn = box_head(wrec);
+#pragma unroll 1
+        for (int i = 0; i < n; ++i) {
+            const float* r = wrec + i * kRec;
+            const BoxHead B = Bn;
+            if (i + 1 < n) Bn = box_head(r + kRec);
+            float4 v = vnext;
+            if (i + 1 < n) vnext = load_v(base + i + 1, r + kRec);
+            const int dy = B.jy - cy, dx = B.jx - cx;
+            if ((unsigned)(dy + 1) > 2u || (unsigned)(dx + 1) > 2u) {
+                flush_plane();
+                set_offsets(W.yoff, B.jy, A.Gy, sy);
+                set_offsets(W.xoff, B.jx, A.Gx, A.C);
+            } else {
+                if (dy != 0) {
+                    const int rr = (dy > 0) ? (cy & 3) : ((cy + 3) & 3);
+                    const int ynew = (dy > 0) ? cy + 4 : cy - 1;
+                    with_residue(rr, [&](auto RC) {
+                        constexpr int R = decltype(RC)::value;
+                        if (active && W.zc != kNoPlane) {
+#pragma unroll
+                            for (int d = 0; d < kW; ++d) add4(W.zoff + W.yoff[R] + W.xoff[d], W.v[R][d]);
+                        }
+#pragma unroll
+                        for (int d = 0; d < kW; ++d) W.v[R][d] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        W.yoff[R] = wrapc(ynew, A.Gy) * sy;
+                    });
+                }
+                if (dx != 0) {
+                    const int rr = (dx > 0) ? (cx & 3) : ((cx + 3) & 3);
+                    const int xnew = (dx > 0) ? cx + 4 : cx - 1;
+                    with_residue(rr, [&](auto RC) {
+                        constexpr int R = decltype(RC)::value;
+                        if (active && W.zc != kNoPlane) {
+#pragma unroll
+                            for (int b = 0; b < kW; ++b) add4(W.zoff + W.yoff[b] + W.xoff[R], W.v[b][R]);
+                        }
+#pragma unroll
+                        for (int b = 0; b < kW; ++b) W.v[b][R] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        W.xoff[R] = wrapc(xnew, A.Gx) * A.C;
+                    });
+                }
+            }
+            cy = B.jy;
+            cx = B.jx;
+            const int zq = B.jz + ((slice - B.jz) & 3);
+            if (zq != W.zc) {
+                flush_plane();
+                W.zc = zq;
+                W.zoff = wrapc(zq, A.Gz) * sz;
+            }
+            const float4 wy = *reinterpret_cast<const float4*>(r + 4);
+            const float4 wx = *reinterpret_cast<const float4*>(r + 8);
+            const float wyv[kW] = {wy.x, wy.y, wy.z, wy.w};
+            const float wxv[kW] = {wx.x, wx.y, wx.z, wx.w};
+            const float4 va = f4scale(f4scale(v, B.sw), r[slice]);
+#pragma unroll
+            for (int b = 0; b < kW; ++b) {
+                const float4 vb = f4scale(va, wyv[b]);
+#pragma unroll
+                for (int d = 0; d < kW; ++d) W.v[b][d] = f4fma(wxv[d], vb, W.v[b][d]);
+            }
+        }
+    }
+    flush_plane();
+}
+
 // Owner-computes spreading.  One warp runs one work item: a tile of the grid (its region) and a
 // list of sorted-sample ranges (the tile's own samples and those of its lower neighbours whose box
 // reaches it, or a chunk of that list).  The warp keeps the same residue-indexed sliding window as
@@ -1101,6 +1369,14 @@ static cs_status for_coil_chunks(const cs_plan* p, int ncoils, int cmax, F&& f) 
     return CS_OK;
 }
 
+// The two-coils-per-lane kernels need 16-byte alignment of every coil pair: an even interleave
+// stride, an even first coil and an even chunk, a 16-byte aligned grid (and sorted k-space
+// array, when one is read or written as pairs).
+static bool pair_ok(const GridArgs& A, const float2* sorted) {
+    return A.C % 2 == 0 && A.c0 % 2 == 0 && A.gsize % 2 == 0 && (reinterpret_cast<uintptr_t>(A.grid) & 15) == 0 &&
+           (sorted == nullptr || (reinterpret_cast<uintptr_t>(sorted) & 15) == 0);
+}
+
 // Interpolation: one sample stream (interp_chunk consecutive sorted samples) per warp.
 static cs_status launch_interp(const cs_plan* p, int ncoils, int mode, const float2* ysub, float2* out,
                                cudaStream_t st) {
@@ -1114,6 +1390,7 @@ static cs_status launch_interp(const cs_plan* p, int ncoils, int mode, const flo
         A.gsize = g;
         prof_begin(ST_INTERP, st);
         if (p->ndim == 2) interp_kernel<1, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
+        else if (P == 2 && pair_ok(A, out)) interp_pair_kernel<<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
         else if (P == 1) interp_kernel<4, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
         else if (P == 2) interp_kernel<2, 2><<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
         else interp_kernel<1, 4><<<nb, 32 * kGridWarps, 0, st>>>(A, mode, ysub, out);
@@ -1136,6 +1413,7 @@ static cs_status launch_spread_producer(const cs_plan* p, int ncoils, const floa
         A.gsize = g;
         prof_begin(ST_SPREAD, st);
         if (p->ndim == 2) spread_kernel<1, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
+        else if (P == 2 && pair_ok(A, sorted_in ? yin : nullptr)) spread_pair_kernel<<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
         else if (P == 1) spread_kernel<4, 1><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
         else spread_kernel<2, 2><<<nb, 32 * kGridWarps, 0, st>>>(A, yin, sorted_in);
         CS_LAUNCH_CHECK();

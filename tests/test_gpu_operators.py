@@ -212,6 +212,28 @@ def test_nufft_grad_and_sketched_normal():
     assert nrmse(h(z), z_ref) < TOL
 
 
+def test_two_coils_per_lane_gridding_paths():
+    """Chunks of 10 .. 16 coils at even offsets run the two-coils-per-lane gridding kernels: forward
+    (user-order output), adjoint (user-order input), gradient (residual into the sorted scratch)
+    and sketched normal operator (sorted output and input) with 12 and 14 coils against the FP64
+    oracle; 13 coils (odd chunk) and 24 coils (chunks of 12) beside them."""
+    import paper_2305_06482_gb300 as cs
+    from tests._gpu import t, h, nrmse
+    img, grid = (24, 32, 32), (30, 40, 40)
+    for C in (12, 13, 14, 24):
+        traj, dcf, maps, x = _nufft_case(img, grid, C, 300, 128, seed=C)
+        op = nufft.Plan(traj, img, grid)
+        plan = cs.Plan(cs.NONCARTESIAN, img, C, traj=t(traj), dcf=t(dcf), grid=grid)
+        yy = synthdata.random_complex((C, traj.shape[0]), C + 1)
+        assert nrmse(h(cs.sense_fwd(plan, t(x), t(maps))), nufft.sense_fwd(op, x, maps, dcf)) < TOL, C
+        assert nrmse(h(cs.sense_adj(plan, t(yy), t(maps))), nufft.sense_adj(op, yy, maps, dcf)) < TOL, C
+        d_ref = nufft.sense_adj(op, nufft.sense_fwd(op, x, maps, dcf) - yy, maps, dcf)
+        assert nrmse(h(cs.sense_grad(plan, t(x), t(maps), t(yy))), d_ref) < TOL, C
+        V = C // 2
+        z_ref = nufft.sense_adj(op, nufft.sense_fwd(op, x, maps, dcf), maps, dcf) + 1e-3 * x
+        assert nrmse(h(cs.sketched_normal_apply(plan, t(x), t(maps[:V]), t(maps[V:]), 1e-3)), z_ref) < TOL, C
+
+
 def test_plan_rejects_bad_arguments():
     import paper_2305_06482_gb300 as cs
     from tests._gpu import t
