@@ -214,10 +214,31 @@ def cpu_c1_full_recon():
     return time.perf_counter() - t0
 
 
-def cpu_baseline_entry(w, T, c1=None, sub=16):
+def cpu_c2_slice_recon():
+    """One slice of the batched 2D workload (256x256, 16 coils, line mask R = 6 with 24 centre
+    lines, l1-db4 lambda = 5e-3 with 4 levels, m = 6 = 3 PCA + 3 Gaussian, 10 outer x 10 FISTA)
+    reconstructed in full by the oracle; measured."""
+    import synthdata
+    from oracle import fourier, philox, solvers
+    shape, C = (256, 256), 16
+    mask = synthdata.line_mask(shape, R=6.0, centre_lines=24, seed=200)
+    idx = fourier.mask_indices(mask)
+    maps = synthdata.coil_maps(shape, C)
+    y = fourier.cartesian_fwd(synthdata.phantom(shape, seed=300), maps, idx)
+    y = y + synthdata.complex_noise(y.shape, 1e-3 * np.abs(y).max(), seed=3)
+    sk = philox.sketch_draw(4, 0, 10, C, 3, 3).astype(np.float64)
+    ops = lambda mm: (lambda v: fourier.cartesian_fwd(v, mm, idx), lambda k: fourier.cartesian_adj(k, mm, idx))
+    t0 = time.perf_counter()
+    solvers.coil_sketching(ops, maps, y, 5e-3, "l1wav", sk, V=3, K=10, power_v0=synthdata.phantom(shape, seed=500),
+                           levels=4)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_entry(w, T, c1=None, sub=16, c2=None):
     t, nsub, cores = cpu_reference_step(w, sub)
     est = cpu_recon_estimate(w, T, t)
     c1 = cpu_c1_full_recon() if c1 is None else c1
+    c2 = cpu_c2_slice_recon() if c2 is None else c2
     sample = (f"extrapolated from the FP64 oracle's per-operation times on bounded samples: one coil's gridding "
               f"fwd+adj on every {sub}th interleave ({nsub} samples, x{sub}) + a full-grid centred DFT pair and map "
               f"products; a full-size db4 prox and FISTA vector updates; coil PCA and rotations on 1/{sub} of the "
@@ -226,16 +247,20 @@ def cpu_baseline_entry(w, T, c1=None, sub=16):
     return {"value": est, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample,
             "per_op_s": {k: round(v, 4) for k, v in t.items()},
             "c1_full_recon_s": round(c1, 4),
-            "c1_note": "128x128 Cartesian, 8 coils, m=4, 5x10 CG: measured, not extrapolated"}
+            "c1_note": "128x128 Cartesian, 8 coils, m=4, 5x10 CG: measured, not extrapolated",
+            "c2_slice_recon_s": round(c2, 4) if c2 is not None else None,
+            "c2_note": "one 256x256 slice of the 64-slice batched workload (16 coils, m=6, 10x10 FISTA, l1-db4): "
+                       "measured, not extrapolated"}
 
 
 def run_reference(args, w, rank, world):
     if rank != 0:
         return
     c1 = cpu_c1_full_recon()
+    c2 = cpu_c2_slice_recon()
     vals, entry = [], None
     for i in range(args.warmup + args.steps):
-        entry = cpu_baseline_entry(w, T_MEASURED, c1=c1, sub=32)
+        entry = cpu_baseline_entry(w, T_MEASURED, c1=c1, sub=32, c2=c2)
         if i >= args.warmup:
             vals.append(entry["value"])
     v = float(np.mean(vals))
