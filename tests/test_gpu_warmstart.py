@@ -343,8 +343,8 @@ def test_training_and_warm_start_in_algorithm_1():
     """Training on the method's own pairs lowers the loss, and on a held-out phantom the trained
     network's accepted predictions bring the first two outer iterates of Algorithm 1 strictly closer
     to x_inf than the method without it (recon_solve, decision on the device).  Everything runs
-    bit-reproducibly (deterministic spreading, fixed-order weight-gradient and loss sums), so the
-    measured gain is the same on every run."""
+    bit-reproducibly (fixed-order coil covariance, deterministic spreading, fixed-order weight-
+    gradient and loss sums), so the measured gain is the same on every run and in any test order."""
     import paper_2305_06482_gb300 as cs
     import paper_2305_06482_gb300.warmstart as ws
     img = (32, 48, 48)
