@@ -373,6 +373,11 @@ __device__ __forceinline__ int wrapc(int j, int G) {   // j in [-G, 2G)
 // the (-1)^(j + G/2) sign of the centred DFT folded in; word 12 packs the unwrapped box starts
 // plus 2 (10 bits per axis, z lowest), word 13 is sqrt(w) and word 14 the user index.
 constexpr int kRec = 16;
+// word 15: the window move from the previous sorted sample.  Bits 0-1 the y step (1 up, 2 down),
+// 2-3 the x step, bit 4 a jump (a step of more than one along y or x, or the first sample), bit 5
+// a z change, bits 6-7 / 8-9 the residue of the leaving row / column, bits 10-19 / 20-29 the
+// wrapped grid index of the entering row / column.
+constexpr int kMvJump = 1 << 4, kMvZ = 1 << 5;
 
 __global__ void sample_record_kernel(const float* __restrict__ gs, const float* __restrict__ ws,
                                      const int32_t* __restrict__ perm, const float* __restrict__ tab_g, int64_t N,
@@ -403,7 +408,29 @@ __global__ void sample_record_kernel(const float* __restrict__ gs, const float* 
     r[12] = __int_as_float(jb[0] | (jb[1] << 10) | (jb[2] << 20));
     r[13] = ws[s];
     r[14] = __int_as_float(perm[s]);
-    r[15] = 0.f;
+    // the window move from the previous sorted sample (word 15): a run of samples is walked in
+    // sorted order, so this is the move a warp makes unless the sample starts its run
+    int code = kMvJump;
+    if (s > 0) {
+        int jp[3] = {0, 0, 0};
+        for (int ax = 3 - nd; ax < 3; ++ax) jp[ax] = (int)floorf(gs[(s - 1) * 3 + ax]) - (kW / 2 - 1);
+        const int j0[3] = {jb[0] - 2, jb[1] - 2, jb[2] - 2};
+        const int dz = j0[0] - jp[0], dy = j0[1] - jp[1], dx = j0[2] - jp[2];
+        if ((unsigned)(dy + 1) <= 2u && (unsigned)(dx + 1) <= 2u) {
+            code = (dz != 0) ? kMvZ : 0;
+            if (dy != 0) {
+                const int rr = (dy > 0) ? (jp[1] & 3) : ((jp[1] + 3) & 3);
+                const int yn = wrapc((dy > 0) ? jp[1] + 4 : jp[1] - 1, Gy);
+                code |= ((dy > 0) ? 1 : 2) | (rr << 6) | (yn << 10);
+            }
+            if (dx != 0) {
+                const int rr = (dx > 0) ? (jp[2] & 3) : ((jp[2] + 3) & 3);
+                const int xn = wrapc((dx > 0) ? jp[2] + 4 : jp[2] - 1, Gx);
+                code |= (((dx > 0) ? 1 : 2) << 2) | (rr << 8) | (xn << 20);
+            }
+        }
+    }
+    r[15] = __int_as_float(code);
 }
 
 // Stage the records of samples [base, base + n) (n <= kStage) into the warp's shared buffer.
@@ -537,37 +564,29 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
     }
 #pragma unroll
     for (int r = 0; r < kW; ++r) W.yoff[r] = W.xoff[r] = 0;
-    int cy = kNoPlane, cx = kNoPlane;
     for (int base = s0; base < s1; base += kStage) {
         const int n = min(kStage, s1 - base);
         stage_records(A.rec, base, n, wrec, lane, A.N);
-#if CS_INTERP_HEAD_PREFETCH
-        BoxHead Bn = box_head(wrec);
-#endif
 #pragma unroll 1
         for (int i = 0; i < n; ++i) {
             const float* r = wrec + i * kRec;
-#if CS_INTERP_HEAD_PREFETCH
-            const BoxHead B = Bn;
-            if (i + 1 < n) Bn = box_head(r + kRec);
-#else
-            const BoxHead B = box_head(r);
-#endif
-            const int dy = B.jy - cy, dx = B.jx - cx;
-            if ((unsigned)(dy + 1) > 2u || (unsigned)(dx + 1) > 2u) {   // not a step of -1, 0 or +1
-                set_offsets(W.yoff, B.jy, A.Gy, sy);
-                set_offsets(W.xoff, B.jx, A.Gx, A.C);
+            // the window move was decoded at plan time (record word 15); a run's first sample jumps
+            const float4 hd = *reinterpret_cast<const float4*>(r + 12);
+            const int mv = __float_as_int(hd.w);
+            const bool jump = (mv & kMvJump) || (i == 0 && base == s0);
+            if (jump) {
+                const int pk = __float_as_int(hd.x);
+                set_offsets(W.yoff, ((pk >> 10) & 1023) - 2, A.Gy, sy);
+                set_offsets(W.xoff, ((pk >> 20) & 1023) - 2, A.Gx, A.C);
 #pragma unroll
                 for (int p = 0; p < P; ++p) W.zc[p] = kNoPlane;    // every plane reloads below
             } else {
-                if (dy != 0) {
-                    // the leaving row (old start for a step up, old end for a step down) takes the
-                    // entering row, whose grid index has the same residue
-                    const int rr = (dy > 0) ? (cy & 3) : ((cy + 3) & 3);
-                    const int ynew = (dy > 0) ? cy + 4 : cy - 1;
-                    with_residue(rr, [&](auto RC) {
+                if (mv & 3) {
+                    // the leaving row takes the entering row, whose grid index has the same residue
+                    const int yrow = (mv >> 10) & 1023;
+                    with_residue((mv >> 6) & 3, [&](auto RC) {
                         constexpr int R = decltype(RC)::value;
-                        W.yoff[R] = wrapc(ynew, A.Gy) * sy;
+                        W.yoff[R] = yrow * sy;
                         if (active) {
 #pragma unroll
                             for (int p = 0; p < P; ++p)
@@ -578,12 +597,11 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
                         }
                     });
                 }
-                if (dx != 0) {
-                    const int rr = (dx > 0) ? (cx & 3) : ((cx + 3) & 3);
-                    const int xnew = (dx > 0) ? cx + 4 : cx - 1;
-                    with_residue(rr, [&](auto RC) {
+                if (mv & 12) {
+                    const int xcol = (mv >> 20) & 1023;
+                    with_residue((mv >> 8) & 3, [&](auto RC) {
                         constexpr int R = decltype(RC)::value;
-                        W.xoff[R] = wrapc(xnew, A.Gx) * A.C;
+                        W.xoff[R] = xcol * A.C;
                         if (active) {
 #pragma unroll
                             for (int p = 0; p < P; ++p)
@@ -595,8 +613,26 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
                     });
                 }
             }
-            cy = B.jy;
-            cx = B.jx;
+            if (jump || (mv & kMvZ)) {
+                const int jz = (__float_as_int(hd.x) & 1023) - 2;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const int q = slice + p * S;                    // z residue held by this plane
+                    const int zq = jz + ((q - jz) & 3);
+                    if (zq != W.zc[p]) {
+                        W.zc[p] = zq;
+                        W.zoff[p] = wrapc(zq, A.Gz) * sz;
+                        if (active) {
+#pragma unroll
+                            for (int b = 0; b < kW; ++b)
+#pragma unroll
+                                for (int d = 0; d < kW; ++d) W.v[p][b][d] = gridld(g, c, W.zoff[p] + W.yoff[b] + W.xoff[d], glim);
+                        }
+                    }
+                }
+            }
+            const float sw = hd.y;
+            const int perm = __float_as_int(hd.z);
             float2 acc = make_float2(0.f, 0.f);
             const float4 wy = *reinterpret_cast<const float4*>(r + 4);
             const float4 wx = *reinterpret_cast<const float4*>(r + 8);
@@ -606,19 +642,7 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
                                     make_float2(wx.w, wx.w)};
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const int q = slice + p * S;                    // z residue held by this plane
-                const int zq = B.jz + ((q - B.jz) & 3);
-                if (zq != W.zc[p]) {
-                    W.zc[p] = zq;
-                    W.zoff[p] = wrapc(zq, A.Gz) * sz;
-                    if (active) {
-#pragma unroll
-                        for (int b = 0; b < kW; ++b)
-#pragma unroll
-                            for (int d = 0; d < kW; ++d) W.v[p][b][d] = gridld(g, c, W.zoff[p] + W.yoff[b] + W.xoff[d], glim);
-                    }
-                }
-                const float wzp = r[q];
+                const float wzp = r[slice + p * S];
                 float2 pa = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int b = 0; b < kW; ++b) {
@@ -638,13 +662,13 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB(P))
             }
             if (active && slice == 0) {
                 const int64_t s = (int64_t)base + i;
-                acc = cscale(acc, B.sw);
+                acc = cscale(acc, sw);
                 const int64_t lim = (int64_t)A.C * A.N;
                 if (mode == OUT_USER) {
-                    if (CS_INB((int64_t)c * A.N + B.perm, lim)) out[(int64_t)c * A.N + B.perm] = acc;
+                    if (CS_INB((int64_t)c * A.N + perm, lim)) out[(int64_t)c * A.N + perm] = acc;
                 } else if (mode == OUT_RESID) {
-                    if (CS_INB(s * A.C + c, lim) && CS_INB((int64_t)c * A.N + B.perm, lim))
-                        out[s * A.C + c] = csub(acc, ysub[(int64_t)c * A.N + B.perm]);
+                    if (CS_INB(s * A.C + c, lim) && CS_INB((int64_t)c * A.N + perm, lim))
+                        out[s * A.C + c] = csub(acc, ysub[(int64_t)c * A.N + perm]);
                 } else {
                     if (CS_INB(s * A.C + c, lim)) out[s * A.C + c] = acc;
                 }
@@ -686,7 +710,6 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
     }
 #pragma unroll
     for (int r = 0; r < kW; ++r) W.yoff[r] = W.xoff[r] = 0;
-    int cy = kNoPlane, cx = kNoPlane;
     auto flush_plane = [&](int p) {
         if (active && W.zc[p] != kNoPlane) {
 #pragma unroll
@@ -710,33 +733,26 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
         const int n = min(kStage, s1 - base);
         stage_records(A.rec, base, n, wrec, lane, A.N);
         float2 vnext = load_v(base, wrec);
-#if CS_SPREAD_HEAD_PREFETCH
-        BoxHead Bn = box_head(wrec);
-#endif
 #pragma unroll 1
         for (int i = 0; i < n; ++i) {
             const float* r = wrec + i * kRec;
-#if CS_SPREAD_HEAD_PREFETCH
-            const BoxHead B = Bn;
-            if (i + 1 < n) Bn = box_head(r + kRec);
-#else
-            const BoxHead B = box_head(r);
-#endif
             float2 v = vnext;
             if (i + 1 < n) vnext = load_v(base + i + 1, r + kRec);   // one sample ahead
-            const int dy = B.jy - cy, dx = B.jx - cx;
-            if ((unsigned)(dy + 1) > 2u || (unsigned)(dx + 1) > 2u) {   // not a step of -1, 0 or +1
+            // the window move was decoded at plan time (record word 15); a run's first sample jumps
+            const float4 hd = *reinterpret_cast<const float4*>(r + 12);
+            const int mv = __float_as_int(hd.w);
+            const bool jump = (mv & kMvJump) || (i == 0 && base == s0);
+            if (jump) {
+                const int pk = __float_as_int(hd.x);
 #pragma unroll
                 for (int p = 0; p < P; ++p) flush_plane(p);
-                set_offsets(W.yoff, B.jy, A.Gy, sy);
-                set_offsets(W.xoff, B.jx, A.Gx, A.C);
+                set_offsets(W.yoff, ((pk >> 10) & 1023) - 2, A.Gy, sy);
+                set_offsets(W.xoff, ((pk >> 20) & 1023) - 2, A.Gx, A.C);
             } else {
-                if (dy != 0) {
-                    // write out the leaving row (old start for a step up, old end for a step down);
-                    // its registers and residue pass to the entering row
-                    const int rr = (dy > 0) ? (cy & 3) : ((cy + 3) & 3);
-                    const int ynew = (dy > 0) ? cy + 4 : cy - 1;
-                    with_residue(rr, [&](auto RC) {
+                if (mv & 3) {
+                    // write out the leaving row; its registers and residue pass to the entering row
+                    const int yrow = (mv >> 10) & 1023;
+                    with_residue((mv >> 6) & 3, [&](auto RC) {
                         constexpr int R = decltype(RC)::value;
 #pragma unroll
                         for (int p = 0; p < P; ++p) {
@@ -748,13 +764,12 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
 #pragma unroll
                             for (int d = 0; d < kW; ++d) W.v[p][R][d] = make_float2(0.f, 0.f);
                         }
-                        W.yoff[R] = wrapc(ynew, A.Gy) * sy;
+                        W.yoff[R] = yrow * sy;
                     });
                 }
-                if (dx != 0) {
-                    const int rr = (dx > 0) ? (cx & 3) : ((cx + 3) & 3);
-                    const int xnew = (dx > 0) ? cx + 4 : cx - 1;
-                    with_residue(rr, [&](auto RC) {
+                if (mv & 12) {
+                    const int xcol = (mv >> 20) & 1023;
+                    with_residue((mv >> 8) & 3, [&](auto RC) {
                         constexpr int R = decltype(RC)::value;
 #pragma unroll
                         for (int p = 0; p < P; ++p) {
@@ -766,13 +781,24 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
 #pragma unroll
                             for (int b = 0; b < kW; ++b) W.v[p][b][R] = make_float2(0.f, 0.f);
                         }
-                        W.xoff[R] = wrapc(xnew, A.Gx) * A.C;
+                        W.xoff[R] = xcol * A.C;
                     });
                 }
             }
-            cy = B.jy;
-            cx = B.jx;
-            v = cscale(v, B.sw);
+            if (jump || (mv & kMvZ)) {
+                const int jz = (__float_as_int(hd.x) & 1023) - 2;
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const int q = slice + p * S;
+                    const int zq = jz + ((q - jz) & 3);
+                    if (zq != W.zc[p]) {
+                        flush_plane(p);
+                        W.zc[p] = zq;
+                        W.zoff[p] = wrapc(zq, A.Gz) * sz;
+                    }
+                }
+            }
+            v = cscale(v, hd.y);
             const float4 wy = *reinterpret_cast<const float4*>(r + 4);
             const float4 wx = *reinterpret_cast<const float4*>(r + 8);
             const float wyv[kW] = {wy.x, wy.y, wy.z, wy.w};
@@ -781,14 +807,7 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB(P))
                                     make_float2(wx.w, wx.w)};
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const int q = slice + p * S;
-                const int zq = B.jz + ((q - B.jz) & 3);
-                if (zq != W.zc[p]) {
-                    flush_plane(p);
-                    W.zc[p] = zq;
-                    W.zoff[p] = wrapc(zq, A.Gz) * sz;
-                }
-                const float2 va = cscale(v, r[q]);
+                const float2 va = cscale(v, r[slice + p * S]);
 #pragma unroll
                 for (int b = 0; b < kW; ++b) {
                     const float2 vb = cscale(va, wyv[b]);
@@ -851,38 +870,37 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB_P2)
         for (int d = 0; d < kW; ++d) W.v[b][d] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int r = 0; r < kW; ++r) W.yoff[r] = W.xoff[r] = 0;
-    int cy = kNoPlane, cx = kNoPlane;
     for (int base = s0; base < s1; base += kStage) {
         const int n = min(kStage, s1 - base);
         stage_records(A.rec, base, n, wrec, lane, A.N);
 #pragma unroll 1
         for (int i = 0; i < n; ++i) {
             const float* r = wrec + i * kRec;
-            const BoxHead B = box_head(r);
-            const int dy = B.jy - cy, dx = B.jx - cx;
-            if ((unsigned)(dy + 1) > 2u || (unsigned)(dx + 1) > 2u) {
-                set_offsets(W.yoff, B.jy, A.Gy, sy);
-                set_offsets(W.xoff, B.jx, A.Gx, A.C);
+            const float4 hd = *reinterpret_cast<const float4*>(r + 12);
+            const int mv = __float_as_int(hd.w);
+            const bool jump = (mv & kMvJump) || (i == 0 && base == s0);
+            if (jump) {
+                const int pk = __float_as_int(hd.x);
+                set_offsets(W.yoff, ((pk >> 10) & 1023) - 2, A.Gy, sy);
+                set_offsets(W.xoff, ((pk >> 20) & 1023) - 2, A.Gx, A.C);
                 W.zc = kNoPlane;
             } else {
-                if (dy != 0) {
-                    const int rr = (dy > 0) ? (cy & 3) : ((cy + 3) & 3);
-                    const int ynew = (dy > 0) ? cy + 4 : cy - 1;
-                    with_residue(rr, [&](auto RC) {
+                if (mv & 3) {
+                    const int yrow = (mv >> 10) & 1023;
+                    with_residue((mv >> 6) & 3, [&](auto RC) {
                         constexpr int R = decltype(RC)::value;
-                        W.yoff[R] = wrapc(ynew, A.Gy) * sy;
+                        W.yoff[R] = yrow * sy;
                         if (active && W.zc != kNoPlane) {
 #pragma unroll
                             for (int d = 0; d < kW; ++d) W.v[R][d] = gridld4(g, c, W.zoff + W.yoff[R] + W.xoff[d], glim);
                         }
                     });
                 }
-                if (dx != 0) {
-                    const int rr = (dx > 0) ? (cx & 3) : ((cx + 3) & 3);
-                    const int xnew = (dx > 0) ? cx + 4 : cx - 1;
-                    with_residue(rr, [&](auto RC) {
+                if (mv & 12) {
+                    const int xcol = (mv >> 20) & 1023;
+                    with_residue((mv >> 8) & 3, [&](auto RC) {
                         constexpr int R = decltype(RC)::value;
-                        W.xoff[R] = wrapc(xnew, A.Gx) * A.C;
+                        W.xoff[R] = xcol * A.C;
                         if (active && W.zc != kNoPlane) {
 #pragma unroll
                             for (int b = 0; b < kW; ++b) W.v[b][R] = gridld4(g, c, W.zoff + W.yoff[b] + W.xoff[R], glim);
@@ -890,19 +908,22 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB_P2)
                     });
                 }
             }
-            cy = B.jy;
-            cx = B.jx;
-            const int zq = B.jz + ((slice - B.jz) & 3);
-            if (zq != W.zc) {
-                W.zc = zq;
-                W.zoff = wrapc(zq, A.Gz) * sz;
-                if (active) {
+            if (jump || (mv & kMvZ)) {
+                const int jz = (__float_as_int(hd.x) & 1023) - 2;
+                const int zq = jz + ((slice - jz) & 3);
+                if (zq != W.zc) {
+                    W.zc = zq;
+                    W.zoff = wrapc(zq, A.Gz) * sz;
+                    if (active) {
 #pragma unroll
-                    for (int b = 0; b < kW; ++b)
+                        for (int b = 0; b < kW; ++b)
 #pragma unroll
-                        for (int d = 0; d < kW; ++d) W.v[b][d] = gridld4(g, c, W.zoff + W.yoff[b] + W.xoff[d], glim);
+                            for (int d = 0; d < kW; ++d) W.v[b][d] = gridld4(g, c, W.zoff + W.yoff[b] + W.xoff[d], glim);
+                    }
                 }
             }
+            const float sw = hd.y;
+            const int perm = __float_as_int(hd.z);
             const float4 wy = *reinterpret_cast<const float4*>(r + 4);
             const float4 wx = *reinterpret_cast<const float4*>(r + 8);
             const float wyv[kW] = {wy.x, wy.y, wy.z, wy.w};
@@ -925,16 +946,16 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_INTERP_MINB_P2)
             }
             if (active && slice == 0) {
                 const int64_t s = (int64_t)base + i;
-                acc = f4scale(acc, B.sw);
+                acc = f4scale(acc, sw);
                 const int64_t lim = (int64_t)A.C * A.N;
                 if (mode == OUT_USER) {
-                    if (CS_INB((int64_t)(c + 1) * A.N + B.perm, lim)) {
-                        out[(int64_t)c * A.N + B.perm] = make_float2(acc.x, acc.y);
-                        out[(int64_t)(c + 1) * A.N + B.perm] = make_float2(acc.z, acc.w);
+                    if (CS_INB((int64_t)(c + 1) * A.N + perm, lim)) {
+                        out[(int64_t)c * A.N + perm] = make_float2(acc.x, acc.y);
+                        out[(int64_t)(c + 1) * A.N + perm] = make_float2(acc.z, acc.w);
                     }
                 } else if (mode == OUT_RESID) {
-                    if (CS_INB(s * A.C + c + 1, lim) && CS_INB((int64_t)(c + 1) * A.N + B.perm, lim)) {
-                        const float2 y0 = ysub[(int64_t)c * A.N + B.perm], y1 = ysub[(int64_t)(c + 1) * A.N + B.perm];
+                    if (CS_INB(s * A.C + c + 1, lim) && CS_INB((int64_t)(c + 1) * A.N + perm, lim)) {
+                        const float2 y0 = ysub[(int64_t)c * A.N + perm], y1 = ysub[(int64_t)(c + 1) * A.N + perm];
                         *reinterpret_cast<float4*>(out + s * A.C + c) = make_float4(acc.x - y0.x, acc.y - y0.y, acc.z - y1.x, acc.w - y1.y);
                     }
                 } else {
@@ -970,7 +991,6 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB_P2)
         for (int d = 0; d < kW; ++d) W.v[b][d] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int r = 0; r < kW; ++r) W.yoff[r] = W.xoff[r] = 0;
-    int cy = kNoPlane, cx = kNoPlane;
     auto add4 = [&](int off, float4 v) {
         if (CS_INB((int64_t)c + 1 + off, glim)) atomicAdd(reinterpret_cast<float4*>(g + off), v);
     };
@@ -1003,24 +1023,23 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB_P2)
         const int n = min(kStage, s1 - base);
         stage_records(A.rec, base, n, wrec, lane, A.N);
         float4 vnext = load_v(base, wrec);
-        BoxHead Bn = box_head(wrec);
 #pragma unroll 1
         for (int i = 0; i < n; ++i) {
             const float* r = wrec + i * kRec;
-            const BoxHead B = Bn;
-            if (i + 1 < n) Bn = box_head(r + kRec);
             float4 v = vnext;
             if (i + 1 < n) vnext = load_v(base + i + 1, r + kRec);
-            const int dy = B.jy - cy, dx = B.jx - cx;
-            if ((unsigned)(dy + 1) > 2u || (unsigned)(dx + 1) > 2u) {
+            const float4 hd = *reinterpret_cast<const float4*>(r + 12);
+            const int mv = __float_as_int(hd.w);
+            const bool jump = (mv & kMvJump) || (i == 0 && base == s0);
+            if (jump) {
+                const int pk = __float_as_int(hd.x);
                 flush_plane();
-                set_offsets(W.yoff, B.jy, A.Gy, sy);
-                set_offsets(W.xoff, B.jx, A.Gx, A.C);
+                set_offsets(W.yoff, ((pk >> 10) & 1023) - 2, A.Gy, sy);
+                set_offsets(W.xoff, ((pk >> 20) & 1023) - 2, A.Gx, A.C);
             } else {
-                if (dy != 0) {
-                    const int rr = (dy > 0) ? (cy & 3) : ((cy + 3) & 3);
-                    const int ynew = (dy > 0) ? cy + 4 : cy - 1;
-                    with_residue(rr, [&](auto RC) {
+                if (mv & 3) {
+                    const int yrow = (mv >> 10) & 1023;
+                    with_residue((mv >> 6) & 3, [&](auto RC) {
                         constexpr int R = decltype(RC)::value;
                         if (active && W.zc != kNoPlane) {
 #pragma unroll
@@ -1028,13 +1047,12 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB_P2)
                         }
 #pragma unroll
                         for (int d = 0; d < kW; ++d) W.v[R][d] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        W.yoff[R] = wrapc(ynew, A.Gy) * sy;
+                        W.yoff[R] = yrow * sy;
                     });
                 }
-                if (dx != 0) {
-                    const int rr = (dx > 0) ? (cx & 3) : ((cx + 3) & 3);
-                    const int xnew = (dx > 0) ? cx + 4 : cx - 1;
-                    with_residue(rr, [&](auto RC) {
+                if (mv & 12) {
+                    const int xcol = (mv >> 20) & 1023;
+                    with_residue((mv >> 8) & 3, [&](auto RC) {
                         constexpr int R = decltype(RC)::value;
                         if (active && W.zc != kNoPlane) {
 #pragma unroll
@@ -1042,23 +1060,24 @@ __global__ void __launch_bounds__(32 * kGridWarps, CS_SPREAD_MINB_P2)
                         }
 #pragma unroll
                         for (int b = 0; b < kW; ++b) W.v[b][R] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        W.xoff[R] = wrapc(xnew, A.Gx) * A.C;
+                        W.xoff[R] = xcol * A.C;
                     });
                 }
             }
-            cy = B.jy;
-            cx = B.jx;
-            const int zq = B.jz + ((slice - B.jz) & 3);
-            if (zq != W.zc) {
-                flush_plane();
-                W.zc = zq;
-                W.zoff = wrapc(zq, A.Gz) * sz;
+            if (jump || (mv & kMvZ)) {
+                const int jz = (__float_as_int(hd.x) & 1023) - 2;
+                const int zq = jz + ((slice - jz) & 3);
+                if (zq != W.zc) {
+                    flush_plane();
+                    W.zc = zq;
+                    W.zoff = wrapc(zq, A.Gz) * sz;
+                }
             }
             const float4 wy = *reinterpret_cast<const float4*>(r + 4);
             const float4 wx = *reinterpret_cast<const float4*>(r + 8);
             const float wyv[kW] = {wy.x, wy.y, wy.z, wy.w};
             const float wxv[kW] = {wx.x, wx.y, wx.z, wx.w};
-            const float4 va = f4scale(f4scale(v, B.sw), r[slice]);
+            const float4 va = f4scale(f4scale(v, hd.y), r[slice]);
 #pragma unroll
             for (int b = 0; b < kW; ++b) {
                 const float4 vb = f4scale(va, wyv[b]);
