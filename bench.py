@@ -571,7 +571,7 @@ def run_native(args, w, rank, world, local_rank):
 # where the model counts the 16 bytes of trajectory and density; strided passes: mean of the
 # forward y and z passes; writes still dirty in L2 at kernel end are not counted there).  Traffic
 # grows in proportion to the algorithmic bytes, so the bench scales it.
-TRAFFIC_RATIO = {"spread": 1.297, "interp": 1.012, "fft_plain": 0.90}
+TRAFFIC_RATIO = {"spread": 1.287, "interp": 1.008, "fft_plain": 0.90}
 
 
 def stage_bytes(stage, w, T, K, m, steps):
